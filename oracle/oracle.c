@@ -1,0 +1,506 @@
+/*
+ * Plain FP64 CPU oracle for the hierarchical standard-siren likelihood of
+ * arXiv 2504.02034 (CHIMERA 2.0).  TEST INFRASTRUCTURE ONLY: the product
+ * library never links or calls this file; see oracle.h.
+ *
+ * Readings of the paper that this file fixes (each also listed in the design doc):
+ *  - KDE normalisation: mean-weight estimator c * sum_j w_j phi_b, with
+ *    c = 1/N_s (single-1D) or 1/N_k (many-1D)            (Eqs. gw-kernel-*)
+ *  - bandwidth: Scott's rule with the weighted n_eff, one b per event and
+ *    hyperpoint, shared by the event's pixels; fallback to the unweighted
+ *    rule, then to the grid spacing
+ *  - redshift grid: uniform on [0, z_max], trapezoid weights    (Sec. 2.3)
+ *  - galaxy Gaussians normalised on the same grid (discrete Z_g), w_g = 1,
+ *    prefactor 1/N_gal,tot; complete catalog (f_R = 1)        (Eq. p-cat)
+ *  - sky factor S_ik is an input density per steradian  (Eq. gw-kernel-many1d)
+ *  - PE priors uniform: pi_PE = 1                                (Sec. 3.2)
+ *  - mass model without low-edge smoothing; lambda_g, beta fixed (Sec. 3.1)
+ *  - selection: s_j carries the injection draw density and the homogeneous
+ *    redshift prior dV_c/dz / V_c(z_max)                 (Eqs. bias, p-miss)
+ *  - samples whose d_L lies beyond d_L^gw(z = 10) get weight 0.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Gauss-Legendre rule (10 points), nodes found by Newton iteration on */
+/* the Legendre polynomial; used by an adaptive bisection integrator.  */
+/* ------------------------------------------------------------------ */
+#define GL_N 10
+static double gl_x[GL_N], gl_w[GL_N];
+
+static void legendre(int n, double x, double *pn, double *dpn) {
+    double p0 = 1.0, p1 = x;
+    for (int k = 2; k <= n; k++) {
+        double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+    }
+    *pn = p1;
+    *dpn = n * (x * p1 - p0) / (x * x - 1.0);
+}
+
+__attribute__((constructor)) static void gl_init(void) {
+    for (int i = 0; i < GL_N; i++) {
+        double x = cos(M_PI * (i + 0.75) / (GL_N + 0.5)), p, dp;
+        for (int it = 0; it < 100; it++) {
+            legendre(GL_N, x, &p, &dp);
+            double dx = p / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-17) break;
+        }
+        legendre(GL_N, x, &p, &dp);
+        gl_x[i] = x;
+        gl_w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+}
+
+double orc_E(double z, double Om) {
+    double a = 1.0 + z;
+    return sqrt(Om * a * a * a + 1.0 - Om);
+}
+
+static double gl_seg(double a, double b, double Om) {
+    double m = 0.5 * (a + b), h = 0.5 * (b - a), s = 0.0;
+    for (int i = 0; i < GL_N; i++) s += gl_w[i] / orc_E(m + h * gl_x[i], Om);
+    return s * h;
+}
+
+static double gl_adapt(double a, double b, double whole, double Om, int depth) {
+    double m = 0.5 * (a + b);
+    double l = gl_seg(a, m, Om), r = gl_seg(m, b, Om);
+    if (depth >= 40 || fabs(l + r - whole) <= 2e-15 * fabs(l + r)) return l + r;
+    return gl_adapt(a, m, l, Om, depth + 1) + gl_adapt(m, b, r, Om, depth + 1);
+}
+
+/* Comoving distance, flat geometry: D_c = (c/H0) int_0^z dz'/E(z')
+ * (Eq. dL-em divided by 1+z), E^2 = Om (1+z)^3 + 1 - Om.               */
+double orc_Dc(double z, double H0, double Om) {
+    if (!(z > 0.0)) return 0.0;
+    double I = gl_adapt(0.0, z, gl_seg(0.0, z, Om), Om, 0);
+    return ORC_C_KMS / H0 * I;
+}
+
+/* Xi(z) = Xi0 + (1 - Xi0) / (1+z)^n                          (Eq. dL-mg) */
+double orc_Xi(double z, double Xi0, double n) {
+    return Xi0 + (1.0 - Xi0) * pow(1.0 + z, -n);
+}
+
+double orc_dL_em(double z, double H0, double Om) {
+    return (1.0 + z) * orc_Dc(z, H0, Om);
+}
+
+double orc_dL_gw(double z, const double *th) {
+    return orc_dL_em(z, th[0], th[1]) * orc_Xi(z, th[2], th[3]);
+}
+
+/* d d_L^gw/dz by the product rule on Eq. dL-mg:
+ *   [D_c + (1+z) c/(H0 E)] Xi + d_L^em dXi/dz,
+ *   dXi/dz = -n (1 - Xi0) (1+z)^(-n-1).                                  */
+static double J_from_Dc(double z, double Dc, const double *th) {
+    double H0 = th[0], Om = th[1], Xi0 = th[2], n = th[3];
+    double a = 1.0 + z;
+    double ddem = Dc + a * ORC_C_KMS / (H0 * orc_E(z, Om));
+    double xi = Xi0 + (1.0 - Xi0) * pow(a, -n);
+    double dxi = -n * (1.0 - Xi0) * pow(a, -n - 1.0);
+    return ddem * xi + a * Dc * dxi;
+}
+
+double orc_J(double z, const double *th) {
+    return J_from_Dc(z, orc_Dc(z, th[0], th[1]), th);
+}
+
+/* Full-sky comoving volume element and volume, flat geometry.            */
+double orc_dVc_dz(double z, double H0, double Om) {
+    double Dc = orc_Dc(z, H0, Om);
+    return 4.0 * M_PI * (ORC_C_KMS / H0) * Dc * Dc / orc_E(z, Om);
+}
+
+double orc_Vc(double z, double H0, double Om) {
+    double Dc = orc_Dc(z, H0, Om);
+    return 4.0 / 3.0 * M_PI * Dc * Dc * Dc;
+}
+
+/* d_L -> z (Sec. 2.1): safeguarded Newton inside the bracket [0, 10].
+ * Returns 1 when d is not positive or lies beyond d_L^gw(10).            */
+int orc_z_of_dL(double d, const double *th, double *zout) {
+    if (!(d > 0.0) || !isfinite(d)) return 1;
+    double lo = 0.0, hi = ORC_Z_TABLE_MAX;
+    double dhi = orc_dL_gw(hi, th);
+    if (!(d <= dhi)) return 1;
+    double z = hi * d / dhi;
+    for (int it = 0; it < 300; it++) {
+        double Dc = orc_Dc(z, th[0], th[1]);
+        double f = (1.0 + z) * Dc * orc_Xi(z, th[2], th[3]) - d;
+        if (f == 0.0) break;
+        if (f > 0.0) hi = z; else lo = z;
+        double zn = z - f / J_from_Dc(z, Dc, th);
+        if (!(zn > lo && zn < hi)) zn = 0.5 * (lo + hi);
+        double step = fabs(zn - z);
+        z = zn;
+        if (step <= 1e-15 * (1.0 + z) || hi - lo <= 1e-15 * (1.0 + z)) break;
+    }
+    *zout = z;
+    return 0;
+}
+
+/* ---- mass model: power law + Gaussian peak for m1, power law for m2 ---- */
+/* int_lo^hi m^(-a) dm                                                     */
+static double pl_integral(double a, double lo, double hi) {
+    if (fabs(1.0 - a) < 1e-12) return log(hi / lo);
+    return (pow(hi, 1.0 - a) - pow(lo, 1.0 - a)) / (1.0 - a);
+}
+
+static double std_normal_cdf(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
+
+/* p(m1): (1 - lambda_g) PL(m1; alpha) + lambda_g N(m1; mu_g, sigma_g),
+ * both components normalised on [m_min, m_max], zero outside (Sec. 3.1). */
+double orc_p_m1(double m1, const double *th, double lambda_g) {
+    double alpha = th[4], mu = th[5], sg = th[6], mmin = th[7], mmax = th[8];
+    if (!(m1 >= mmin && m1 <= mmax)) return 0.0;
+    double pl = pow(m1, -alpha) / pl_integral(alpha, mmin, mmax);
+    double den = std_normal_cdf((mmax - mu) / sg) - std_normal_cdf((mmin - mu) / sg);
+    double g = 0.0;
+    if (den > 0.0) {
+        double u = (m1 - mu) / sg;
+        g = exp(-0.5 * u * u) / (sg * sqrt(2.0 * M_PI)) / den;
+    }
+    return (1.0 - lambda_g) * pl + lambda_g * g;
+}
+
+/* p(m2 | m1) proportional to m2^beta on [m_min, m1]                       */
+double orc_p_m2(double m2, double m1, const double *th, double beta) {
+    double mmin = th[7];
+    if (!(m1 > mmin) || !(m2 >= mmin && m2 <= m1)) return 0.0;
+    return pow(m2, beta) / pl_integral(-beta, mmin, m1);
+}
+
+/* Madau-Dickinson shape, left unnormalised as in the paper (Sec. 3.1)    */
+double orc_psi(double z, const double *th) {
+    double gam = th[9], kap = th[10], zp = th[11];
+    double a = 1.0 + z;
+    return pow(a, gam) / (1.0 + pow(a / (1.0 + zp), gam + kap));
+}
+
+int orc_check_theta(const double *th) {
+    for (int k = 0; k < 12; k++)
+        if (!isfinite(th[k])) return 1;
+    if (!(th[0] > 0.0)) return 1;                 /* H0 */
+    if (!(th[1] >= 0.0 && th[1] <= 1.0)) return 1; /* Om */
+    if (!(th[2] > 0.0)) return 1;                 /* Xi0 */
+    if (!(th[6] > 0.0)) return 1;                 /* sigma_g */
+    if (!(th[7] > 0.0 && th[8] > th[7])) return 1; /* m_min < m_max */
+    if (!(th[11] > -1.0)) return 1;               /* z_p */
+    return 0;
+}
+
+int orc_monotone(const double *th) {
+    for (int k = 0; k <= ORC_MONO_NODES; k++) {
+        double z = ORC_Z_TABLE_MAX * k / ORC_MONO_NODES;
+        if (!(orc_J(z, th) > 0.0)) return 0;
+    }
+    return 1;
+}
+
+static const orc_hooks default_hooks = {1.0, 1.0, 0};
+
+static double grid_dz(const orc_catalog *c) { return c->z_max / (double)(c->n_z - 1); }
+static double grid_z(const orc_catalog *c, int64_t a) { return c->z_max * (double)a / (double)(c->n_z - 1); }
+static double grid_w(const orc_catalog *c, int64_t a) {
+    double dz = grid_dz(c);
+    return (a == 0 || a == c->n_z - 1) ? 0.5 * dz : dz;
+}
+
+/* Per-sample redshift and KDE weight w_j = p(m1, m2) / pi_PE with
+ * m = m_det / (1+z) (Sec. 2.1, Eq. gw-kernel), pi_PE = 1.                 */
+static void samples_h(const orc_catalog *c, const double *th, int64_t ev,
+                      const orc_hooks *hk, double *z, double *w, int32_t *valid) {
+    int64_t j0 = c->sample_off[ev], j1 = c->sample_off[ev + 1];
+    for (int64_t j = j0; j < j1; j++) {
+        double zj = 0.0;
+        int ok = orc_z_of_dL(c->dL[j], th, &zj) == 0;
+        valid[j - j0] = ok;
+        z[j - j0] = ok ? zj : 0.0;
+        if (!ok) { w[j - j0] = 0.0; continue; }
+        double m1 = c->m1d[j] / (1.0 + zj), m2 = c->m2d[j] / (1.0 + zj);
+        w[j - j0] = hk->mass_scale * orc_p_m1(m1, th, c->lambda_g) * orc_p_m2(m2, m1, th, c->beta);
+    }
+}
+
+int orc_event_samples(const orc_catalog *c, const double *th, int64_t ev,
+                      double *z, double *w, int32_t *valid) {
+    samples_h(c, th, ev, &default_hooks, z, w, valid);
+    return 0;
+}
+
+/* Scott's rule with the weighted effective sample size (two-pass moments). */
+static double bandwidth_of(int64_t n, const double *z, const double *w,
+                           const int32_t *valid, double fallback) {
+    double W1 = 0.0, W2 = 0.0, Wz = 0.0;
+    for (int64_t j = 0; j < n; j++) {
+        if (!valid[j]) continue;
+        W1 += w[j];
+        W2 += w[j] * w[j];
+        Wz += w[j] * z[j];
+    }
+    if (W1 > 0.0) {
+        double mean = Wz / W1, var = 0.0;
+        for (int64_t j = 0; j < n; j++)
+            if (valid[j]) var += w[j] * (z[j] - mean) * (z[j] - mean);
+        var /= W1;
+        double neff = W1 * W1 / W2;
+        if (neff >= 2.0 && var > 0.0) return sqrt(var) * pow(neff, -0.2);
+    }
+    int64_t nv = 0;
+    double s = 0.0;
+    for (int64_t j = 0; j < n; j++)
+        if (valid[j]) { nv++; s += z[j]; }
+    if (nv >= 2) {
+        double mean = s / nv, var = 0.0;
+        for (int64_t j = 0; j < n; j++)
+            if (valid[j]) var += (z[j] - mean) * (z[j] - mean);
+        var /= nv;
+        if (var > 0.0) return sqrt(var) * pow((double)nv, -0.2);
+    }
+    return fallback;
+}
+
+int orc_event_bandwidth(const orc_catalog *c, const double *th, int64_t ev, double *b) {
+    int64_t n = c->sample_off[ev + 1] - c->sample_off[ev];
+    double *z = malloc(sizeof(double) * (n + 1)), *w = malloc(sizeof(double) * (n + 1));
+    int32_t *v = malloc(sizeof(int32_t) * (n + 1));
+    samples_h(c, th, ev, &default_hooks, z, w, v);
+    *b = bandwidth_of(n, z, w, v, grid_dz(c));
+    free(z); free(w); free(v);
+    return 0;
+}
+
+/* Weighted Gaussian KDE on the full grid (Eqs. gw-kernel-many1d/single1d):
+ * K(z_a) = (1/N) sum_{j in set} w_j exp(-(z_a - z_j)^2 / 2b^2) / (sqrt(2 pi) b),
+ * the set being the pixel's samples (N = N_k) or all samples (N = N_s).    */
+static void kde_grid(const orc_catalog *c, int64_t ev, int32_t pixel,
+                     const double *z, const double *w, const int32_t *valid,
+                     double b, double *K) {
+    int64_t j0 = c->sample_off[ev], n = c->sample_off[ev + 1] - j0;
+    int64_t cnt = 0;
+    for (int64_t j = 0; j < n; j++)
+        if (pixel < 0 || c->pix_of_sample[j0 + j] == pixel) cnt++;
+    double norm = 1.0 / (sqrt(2.0 * M_PI) * b);
+    for (int64_t a = 0; a < c->n_z; a++) {
+        double za = grid_z(c, a), s = 0.0;
+        for (int64_t j = 0; j < n; j++) {
+            if (!valid[j] || w[j] == 0.0) continue;
+            if (pixel >= 0 && c->pix_of_sample[j0 + j] != pixel) continue;
+            double u = (za - z[j]) / b;
+            s += w[j] * exp(-0.5 * u * u);
+        }
+        K[a] = cnt > 0 ? s * norm / (double)cnt : 0.0;
+    }
+}
+
+int orc_event_kde(const orc_catalog *c, const double *th, int64_t ev,
+                  int32_t pixel, double *K) {
+    int64_t n = c->sample_off[ev + 1] - c->sample_off[ev];
+    double *z = malloc(sizeof(double) * (n + 1)), *w = malloc(sizeof(double) * (n + 1));
+    int32_t *v = malloc(sizeof(int32_t) * (n + 1));
+    samples_h(c, th, ev, &default_hooks, z, w, v);
+    double b = bandwidth_of(n, z, w, v, grid_dz(c));
+    kde_grid(c, ev, pixel, z, w, v, b, K);
+    free(z); free(w); free(v);
+    return 0;
+}
+
+/* Galaxy prior of one pixel on the grid (Eq. p-cat, complete catalog):
+ * G(z_a) = (1/N_gal,tot) dV_c/dz(z_a) sum_g N(z_a; z_g, s_g) / Z_g,
+ * Z_g = sum_a w_a N(z_a; z_g, s_g) dV_c/dz(z_a); galaxies with Z_g = 0
+ * are dropped.                                                            */
+static void galaxy_profile_dv(const orc_catalog *c, int64_t ev, int32_t pixel,
+                              const double *dv, double *G) {
+    int64_t p = c->pix_off[ev] + pixel;
+    for (int64_t a = 0; a < c->n_z; a++) G[a] = 0.0;
+    for (int64_t g = c->gal_off[p]; g < c->gal_off[p + 1]; g++) {
+        double zg = c->gal_z[g], sg = c->gal_sigma[g];
+        double norm = 1.0 / (sqrt(2.0 * M_PI) * sg);
+        double Z = 0.0;
+        for (int64_t a = 0; a < c->n_z; a++) {
+            double u = (grid_z(c, a) - zg) / sg;
+            Z += grid_w(c, a) * norm * exp(-0.5 * u * u) * dv[a];
+        }
+        if (!(Z > 0.0)) continue;
+        for (int64_t a = 0; a < c->n_z; a++) {
+            double u = (grid_z(c, a) - zg) / sg;
+            G[a] += norm * exp(-0.5 * u * u) / Z;
+        }
+    }
+    for (int64_t a = 0; a < c->n_z; a++) G[a] *= dv[a] / c->n_gal_total;
+}
+
+static void grid_dvdz(const orc_catalog *c, const double *th, const orc_hooks *hk, double *dv) {
+    for (int64_t a = 0; a < c->n_z; a++)
+        dv[a] = (hk->flags & 2) ? 1.0 : orc_dVc_dz(grid_z(c, a), th[0], th[1]);
+}
+
+int orc_galaxy_profile(const orc_catalog *c, const double *th, int64_t ev,
+                       int32_t pixel, const orc_hooks *hk, double *G) {
+    if (!hk) hk = &default_hooks;
+    double *dv = malloc(sizeof(double) * c->n_z);
+    grid_dvdz(c, th, hk, dv);
+    galaxy_profile_dv(c, ev, pixel, dv, G);
+    free(dv);
+    return 0;
+}
+
+/* Redshift part of the integrand of Eq. like-integrals:
+ * F(z) = psi(z) / [(1+z)^3 |d d_L^gw / dz|]                  (Eq. jacobian) */
+int orc_grid_factor(const orc_catalog *c, const double *th,
+                    const orc_hooks *hk, double *F) {
+    if (!hk) hk = &default_hooks;
+    for (int64_t a = 0; a < c->n_z; a++) {
+        if (hk->flags & 1) { F[a] = 1.0; continue; }
+        double z = grid_z(c, a), ap = 1.0 + z;
+        F[a] = hk->psi_scale * orc_psi(z, th) / (ap * ap * ap * fabs(orc_J(z, th)));
+    }
+    return 0;
+}
+
+/* ln I_i: Eq. like-integrals on the pixel x redshift grid.
+ * many-1D : I = sum_k S_k sum_a w_a K_k(z_a) F(z_a) G_k(z_a)
+ * single-1D: I = sum_a w_a K(z_a) F(z_a) sum_k S_k G_k(z_a)              */
+static double event_lnI_impl(const orc_catalog *c, const double *th, int64_t ev,
+                             const orc_hooks *hk, const double *F, const double *dv) {
+    int64_t n = c->sample_off[ev + 1] - c->sample_off[ev];
+    int64_t nz = c->n_z;
+    int32_t npix = (int32_t)(c->pix_off[ev + 1] - c->pix_off[ev]);
+    double *z = malloc(sizeof(double) * (n + 1)), *w = malloc(sizeof(double) * (n + 1));
+    int32_t *v = malloc(sizeof(int32_t) * (n + 1));
+    double *K = malloc(sizeof(double) * nz), *G = malloc(sizeof(double) * nz);
+    double *Gs = calloc((size_t)nz, sizeof(double));
+    samples_h(c, th, ev, hk, z, w, v);
+    double b = bandwidth_of(n, z, w, v, grid_dz(c));
+    double I = 0.0;
+    if (c->kde_mode == ORC_KDE_MANY_1D) {
+        for (int32_t k = 0; k < npix; k++) {
+            double S = c->sky_S[c->pix_off[ev] + k];
+            kde_grid(c, ev, k, z, w, v, b, K);
+            galaxy_profile_dv(c, ev, k, dv, G);
+            double s = 0.0;
+            for (int64_t a = 0; a < nz; a++) s += grid_w(c, a) * K[a] * F[a] * G[a];
+            I += S * s;
+        }
+    } else {
+        kde_grid(c, ev, -1, z, w, v, b, K);
+        for (int32_t k = 0; k < npix; k++) {
+            double S = c->sky_S[c->pix_off[ev] + k];
+            galaxy_profile_dv(c, ev, k, dv, G);
+            for (int64_t a = 0; a < nz; a++) Gs[a] += S * G[a];
+        }
+        for (int64_t a = 0; a < nz; a++) I += grid_w(c, a) * K[a] * F[a] * Gs[a];
+    }
+    free(z); free(w); free(v); free(K); free(G); free(Gs);
+    return (I > 0.0 && isfinite(I)) ? log(I) : -INFINITY;
+}
+
+int orc_event_lnI(const orc_catalog *c, const double *th, int64_t ev,
+                  const orc_hooks *hk, double *lnI) {
+    if (!hk) hk = &default_hooks;
+    double *F = malloc(sizeof(double) * c->n_z), *dv = malloc(sizeof(double) * c->n_z);
+    orc_grid_factor(c, th, hk, F);
+    grid_dvdz(c, th, hk, dv);
+    *lnI = event_lnI_impl(c, th, ev, hk, F, dv);
+    free(F); free(dv);
+    return isfinite(*lnI) ? 0 : 1;
+}
+
+/* Neumaier compensated sum                                                */
+static double neumaier(const double *x, int64_t n) {
+    double s = 0.0, comp = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        double t = s + x[i];
+        if (fabs(s) >= fabs(x[i])) comp += (s - t) + x[i];
+        else comp += (x[i] - t) + s;
+        s = t;
+    }
+    return s + comp;
+}
+
+/* Selection term from detected injections (Eq. bias as an MC sum):
+ * s_j = p(m1,m2) psi(z_j) p_z(z_j) / [(1+z_j)^3 |J(z_j)| pi_inj,j],
+ * p_z = dV_c/dz / V_c(z_max) on [0, z_max], 0 beyond;
+ * xi = sum s / N_inj; N_eff = (sum s)^2 / (sum s^2 - (sum s)^2 / N_inj).    */
+int orc_selection(const orc_catalog *c, const double *th, const orc_hooks *hk,
+                  int nthreads, double *xi, double *neff, double *s_out) {
+    if (!hk) hk = &default_hooks;
+    int64_t n = c->n_det;
+    double *s = malloc(sizeof(double) * (n + 1)), *s2 = malloc(sizeof(double) * (n + 1));
+    double vmax = orc_Vc(c->z_max, th[0], th[1]);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 256)
+#endif
+    for (int64_t j = 0; j < n; j++) {
+        double z = 0.0, val = 0.0;
+        if (orc_z_of_dL(c->inj_dL[j], th, &z) == 0 && z <= c->z_max) {
+            double m1 = c->inj_m1d[j] / (1.0 + z), m2 = c->inj_m2d[j] / (1.0 + z);
+            double pm = hk->mass_scale * orc_p_m1(m1, th, c->lambda_g) * orc_p_m2(m2, m1, th, c->beta);
+            if (pm > 0.0) {
+                double a = 1.0 + z;
+                double pz = orc_dVc_dz(z, th[0], th[1]) / vmax;
+                val = pm * hk->psi_scale * orc_psi(z, th) * pz /
+                      (a * a * a * fabs(orc_J(z, th)) * exp(c->inj_log_pi[j]));
+            }
+        }
+        s[j] = val;
+        s2[j] = val * val;
+    }
+    double S1 = neumaier(s, n), S2 = neumaier(s2, n);
+    double N = (double)c->n_inj_total;
+    *xi = S1 / N;
+    *neff = S1 > 0.0 ? S1 * S1 / (S2 - S1 * S1 / N) : 0.0;
+    if (s_out) memcpy(s_out, s, sizeof(double) * n);
+    free(s); free(s2);
+    return 0;
+}
+
+/* ln L = sum_i ln I_i - N_obs ln xi                          (Eq. hyperlike) */
+int orc_loglike(const orc_catalog *c, const double *th, const orc_hooks *hk,
+                int nthreads, double *lnL, double *lnI_out, double *xi_out,
+                double *neff_out, int32_t *status) {
+    if (!hk) hk = &default_hooks;
+    int64_t ne = c->n_events;
+    *status = ORC_OK;
+    if (xi_out) *xi_out = 0.0;
+    if (neff_out) *neff_out = 0.0;
+    if (orc_check_theta(th)) { *lnL = -INFINITY; *status = ORC_OUT_OF_SUPPORT; return 0; }
+    if (!orc_monotone(th)) { *lnL = -INFINITY; *status = ORC_NONMONOTONE; return 0; }
+    double *lnI = malloc(sizeof(double) * (ne + 1));
+    double *F = malloc(sizeof(double) * c->n_z), *dv = malloc(sizeof(double) * c->n_z);
+    orc_grid_factor(c, th, hk, F);
+    grid_dvdz(c, th, hk, dv);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t i = 0; i < ne; i++) lnI[i] = event_lnI_impl(c, th, i, hk, F, dv);
+    double xi, neff;
+    orc_selection(c, th, hk, nthreads, &xi, &neff, NULL);
+    int bad = !(xi > 0.0);
+    for (int64_t i = 0; i < ne; i++) bad |= !isfinite(lnI[i]);
+    if (bad) { *lnL = -INFINITY; *status = ORC_OUT_OF_SUPPORT; }
+    else *lnL = neumaier(lnI, ne) - (double)ne * log(xi);
+    if (!(neff >= 5.0 * (double)ne)) *status |= ORC_NEFF_LOW;
+    if (lnI_out) memcpy(lnI_out, lnI, sizeof(double) * ne);
+    if (xi_out) *xi_out = xi;
+    if (neff_out) *neff_out = neff;
+    free(lnI); free(F); free(dv);
+    return 0;
+}

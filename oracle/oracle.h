@@ -1,0 +1,109 @@
+/*
+ * Plain FP64 CPU oracle for the hierarchical standard-siren likelihood of
+ * arXiv 2504.02034 (CHIMERA 2.0).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, calls or
+ * includes this file; it is used by tests/, by __graft_entry__.smoke() and by
+ * the cpu_baseline / reference legs of bench.py.  It shares no code with the
+ * CUDA path.
+ *
+ * Every quantity is evaluated the slow, direct way: adaptive quadrature for
+ * the comoving distance at every redshift that is needed, bracketed root
+ * finding for every d_L -> z inversion, the full redshift grid for every KDE
+ * and every galaxy Gaussian (no truncation windows), IEEE double throughout.
+ *
+ * Hyperparameter vector theta (12 doubles), in this order:
+ *   H0 [km/s/Mpc], Om, Xi0, n, alpha, mu_g, sigma_g, m_min, m_max,
+ *   gamma, kappa, z_p
+ * lambda_g and beta are fixed per catalog.
+ */
+#ifndef CHIMERA_ORACLE_H
+#define CHIMERA_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_C_KMS 299792.458
+#define ORC_Z_TABLE_MAX 10.0    /* redshift search range [0, 10] */
+#define ORC_MONO_NODES 4096     /* J is checked at z_k = 10 k / 4096 */
+
+enum { ORC_OK = 0, ORC_OUT_OF_SUPPORT = 1, ORC_NONMONOTONE = 2, ORC_NEFF_LOW = 4 };
+enum { ORC_KDE_SINGLE_1D = 0, ORC_KDE_MANY_1D = 1 };
+
+/* Test hooks.  Defaults (psi_scale = mass_scale = 1, flags = 0) give the
+ * paper's likelihood; the others exist so that tests can check invariants and
+ * closed forms.  flags bit 0: grid factor F(z) := 1; bit 1: dV_c/dz := 1 in
+ * the galaxy prior. */
+typedef struct {
+    double psi_scale;
+    double mass_scale;
+    int32_t flags;
+} orc_hooks;
+
+typedef struct {
+    int64_t n_events;
+    const int64_t *sample_off;      /* [n_events+1] */
+    const double *dL, *m1d, *m2d;   /* per PE sample, detector frame */
+    const int32_t *pix_of_sample;   /* index within the event's pixel list */
+    const int64_t *pix_off;         /* [n_events+1] into the flat pixel list */
+    const double *sky_S;            /* per flat pixel, sr^-1 */
+    const int64_t *gal_off;         /* [n_pix_total+1] */
+    const double *gal_z, *gal_sigma;
+    double n_gal_total;
+    double z_max;
+    int64_t n_z;
+    int64_t n_inj_total;
+    int64_t n_det;
+    const double *inj_dL, *inj_m1d, *inj_m2d, *inj_log_pi;
+    double lambda_g, beta;
+    int32_t kde_mode;
+} orc_catalog;
+
+/* ---- cosmology (Eqs. dL-em, dL-mg, jacobian) ---- */
+double orc_E(double z, double Om);
+double orc_Dc(double z, double H0, double Om);
+double orc_Xi(double z, double Xi0, double n);
+double orc_dL_em(double z, double H0, double Om);
+double orc_dL_gw(double z, const double *th);
+double orc_J(double z, const double *th);          /* d d_L^gw / dz */
+double orc_dVc_dz(double z, double H0, double Om); /* full sky, Mpc^3 */
+double orc_Vc(double z, double H0, double Om);
+int orc_z_of_dL(double d, const double *th, double *z); /* 0 ok, 1 none */
+
+/* ---- population (Sec. 3.1) ---- */
+double orc_p_m1(double m1, const double *th, double lambda_g);
+double orc_p_m2(double m2, double m1, const double *th, double beta);
+double orc_psi(double z, const double *th);
+
+int orc_check_theta(const double *th);   /* 0 = admissible */
+int orc_monotone(const double *th);      /* 1 = J > 0 on the check nodes */
+
+/* ---- per-event stages (Eqs. gw-kernel, gw-kernel-many1d/single1d) ---- */
+int orc_event_samples(const orc_catalog *c, const double *th, int64_t ev,
+                      double *z, double *w, int32_t *valid);
+int orc_event_bandwidth(const orc_catalog *c, const double *th, int64_t ev,
+                        double *b);
+int orc_event_kde(const orc_catalog *c, const double *th, int64_t ev,
+                  int32_t pixel, double *K);
+int orc_galaxy_profile(const orc_catalog *c, const double *th, int64_t ev,
+                       int32_t pixel, const orc_hooks *hk, double *G);
+int orc_grid_factor(const orc_catalog *c, const double *th,
+                    const orc_hooks *hk, double *F);
+int orc_event_lnI(const orc_catalog *c, const double *th, int64_t ev,
+                  const orc_hooks *hk, double *lnI);
+
+/* ---- selection (Eq. bias, injection sum and N_eff) ---- */
+int orc_selection(const orc_catalog *c, const double *th, const orc_hooks *hk,
+                  int nthreads, double *xi, double *neff, double *s_out);
+
+/* ---- full ln L (Eq. hyperlike) ---- */
+int orc_loglike(const orc_catalog *c, const double *th, const orc_hooks *hk,
+                int nthreads, double *lnL, double *lnI, double *xi,
+                double *neff, int32_t *status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

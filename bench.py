@@ -1,0 +1,347 @@
+"""Benchmark: ln L evaluations per second (hyperpoints x events) of the
+hierarchical standard-siren likelihood on the 300-event O5-like catalog
+(300 events x 5000 PE samples, 1-64 pixels, lognormal galaxy counts,
+1000-point redshift grid, 2e6 injections), 16 walker hyperpoints per launch,
+mixed precision, beside the plain FP64 one-point-per-call path.
+
+One step = one chimera_loglike call over the batch (cosmology tables,
+reweighting + KDE x galaxy integrals, selection term, combine).  The catalog
+is resident in HBM; `value` times the device-pointer entry point with CUDA
+events, `e2e` times the host-pointer entry point (hyperpoints copied in,
+ln L copied out) end to end.  L2 is flushed (a 256 MiB write) between timed
+steps because the catalog (~100 MB) would otherwise stay L2-resident.
+
+Run: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU (torchrun): every rank evaluates its own walkers on its own GPU
+(independent replicas, weak scaling); only a barrier and a max of the times
+cross ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ln L evals/s (hyperpoints x events) at 300 events, mixed vs FP64; p50/p99 ms"
+UNIT = "evals/s"
+WORKLOAD = "O5-like catalog: 300 events x 5000 PE, 1-64 pixels, lognormal galaxies (median 2e3), n_z=1000, 2e6 injections, many-1D KDE, 16 hyperpoints per launch"
+SM_COUNT = 148
+FP32_LANES = 128
+OPS_PER_PAIR = 2  # one FMUL (Gaussian recurrence) + one FFMA (accumulate)
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(", ") for l in self.f.read().splitlines() if l.strip()]
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except (OSError, ValueError):
+        return {}
+
+
+def traffic_from_profiles():
+    """DRAM bytes per event-kernel launch from the committed ncu summary, if
+    it was taken on the current kernel source."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2504_02034_b300", "csrc", "event.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "event_mixed_o5_c2.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("event_cu_sha256_16") != sha:
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(cat, theta, budget_s=20.0):
+    """The FP64 oracle, as it stands, on the host cores: one hyperpoint over
+    the first E events, with the matching share of injections."""
+    import oracle
+    from synth import catalog as sc  # noqa: F401
+    cores = os.cpu_count() or 1
+    # bounded sample: size E so the run takes ~budget_s of wall time
+    E = 8
+    ne = cat["n_events"]
+    while True:
+        sub = _sub_catalog(cat, E)
+        oc = oracle.Catalog(sub)
+        t0 = time.perf_counter()
+        oc.loglike(theta, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if dt * 2 > budget_s or E >= ne:
+            break
+        E = min(ne, int(E * max(2.0, min(8.0, budget_s / max(dt, 1e-3) / 2))))
+    return {"value": E / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "1 hyperpoint x first %d of %d events with %d of %d detected injections, FP64, %d threads, %.1f s"
+                      % (E, ne, sub["inj_dL"].size, cat["inj_dL"].size, cores, dt)}
+
+
+def _sub_catalog(cat, E):
+    ne = cat["n_events"]
+    so, po, go = cat["sample_off"], cat["pix_off"], cat["gal_off"]
+    ns, npx = so[E], po[E]
+    nd = int(round(cat["inj_dL"].size * E / ne))
+    sub = dict(cat)
+    sub.update(n_events=E, sample_off=so[:E + 1], dL=cat["dL"][:ns], m1_det=cat["m1_det"][:ns],
+               m2_det=cat["m2_det"][:ns], pix_of_sample=cat["pix_of_sample"][:ns], pix_off=po[:E + 1],
+               sky_S=cat["sky_S"][:npx], gal_off=go[:npx + 1], gal_z=cat["gal_z"][:go[npx]],
+               gal_sigma=cat["gal_sigma"][:go[npx]],
+               n_inj_total=int(round(cat["n_inj_total"] * nd / max(cat["inj_dL"].size, 1))),
+               inj_dL=cat["inj_dL"][:nd], inj_m1d=cat["inj_m1d"][:nd], inj_m2d=cat["inj_m2d"][:nd],
+               inj_log_pi=cat["inj_log_pi"][:nd])
+    return sub
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the FP64 CPU oracle on this machine's host cores."""
+    if rank != 0:
+        return
+    from synth import catalog as sc
+    cat = sc.config_catalog(2)
+    th = sc.config_hyperpoints(2)
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    E = 16
+    sub = _sub_catalog(cat, E)
+    oc = oracle.Catalog(sub)
+    for _ in range(args.warmup):
+        oc.loglike(th[0], nthreads=cores)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        oc.loglike(th[k % th.shape[0]], nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    T = sum(times)
+    val = E * args.steps / T
+    sample = ("each step: 1 hyperpoint x first %d of 300 events with %d of %d detected injections, FP64, %d threads"
+              % (E, sub["inj_dL"].size, cat["inj_dL"].size, cores))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        barrier(ws)
+        return
+
+    import torch
+    import paper_2504_02034_b300 as pkg
+    from paper_2504_02034_b300 import build as pkg_build
+    from synth import catalog as sc
+
+    pkg_build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cat = sc.config_catalog(2)
+    theta = sc.make_hyperpoints(16, seed=sc.SEED_BASE + 25 + 1000 * rank, Xi0=1.0)
+    H, NE = theta.shape[0], cat["n_events"]
+    ctx = pkg.Context(local)
+    cid = ctx.load(cat)
+    peaks = pkg.chimera_peaks(ctx.h)
+
+    th_dev = torch.tensor(theta, device=dev, dtype=torch.float64)
+    out = torch.empty(H, device=dev, dtype=torch.float64)
+    neff = torch.empty_like(out)
+    st = torch.empty(H, device=dev, dtype=torch.int32)
+    flush = torch.empty(256 << 20, device=dev, dtype=torch.uint8)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        pkg.chimera_loglike_device(ctx.h, cid, th_dev, pkg.MIXED, out, neff, st, stream)
+
+    pkg.chimera_set_trace(ctx.h, True)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    pairs = int(pkg.chimera_kde_pairs(ctx.h, cid, theta).sum())
+
+    clocks = Clocks(local)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kern_ms, stage = [], []
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        step()
+        ev1[k].record(stream)
+        s = pkg.chimera_stage_ms(ctx.h)  # events on the library stream, around each kernel
+        kern_ms.append(s["event"])
+        stage.append(s)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(ws)
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    T = allmax(ws, sum(step_ms) / 1e3)
+    value = ws * H * NE * args.steps / T
+    step_sorted = sorted(step_ms)
+
+    # e2e: host theta in, host ln L out, through chimera_loglike
+    e2e_t = []
+    for k in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lnL, _, _ = pkg.chimera_loglike(ctx.h, cid, theta, pkg.MIXED)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_T = allmax(ws, sum(e2e_t))
+    e2e_val = ws * H * NE * len(e2e_t) / e2e_T
+
+    # plain FP64 one point per call
+    fp = []
+    for k in range(args.fp64_steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pkg.chimera_loglike(ctx.h, cid, theta[k % H:k % H + 1], pkg.FP64)
+        if k > 0:
+            fp.append(time.perf_counter() - t0)
+    fp64_val = NE * len(fp) / sum(fp)
+
+    kern = sum(kern_ms) / len(kern_ms)
+    clock_mhz = (clk or {}).get("sm_max_mhz") or 2032.0
+    peak_pairs = SM_COUNT * FP32_LANES * clock_mhz * 1e6 / OPS_PER_PAIR
+    achieved = pairs / (kern * 1e-3)
+    roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_pairs / 1e9, "unit": "Gpair/s",
+            "frac": achieved / peak_pairs, "traffic": traffic_from_profiles(),
+            "kernel": "k_event_mixed", "pairs_per_launch": pairs, "kernel_ms": kern,
+            "peak_basis": "148 SMs x 128 FP32 lanes x %.0f MHz / 2 ops per pair (derived)" % clock_mhz,
+            "measured_pair_peak": peaks["pair_per_s"] / 1e9,
+            "frac_of_measured": achieved / peaks["pair_per_s"]}
+    mean_stage = {k: sum(s[k] for s in stage) / len(stage) for k in stage[0]}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": T * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "hyperpoints_per_launch": H, "events": NE,
+                   "pe_samples": int(cat["sample_off"][-1]), "n_z": int(cat["n_z"]),
+                   "detected_injections": int(cat["inj_dL"].size), "l2": "flushed (256 MiB write) between steps",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "p50_ms": statistics.median(step_ms), "p99_ms": step_sorted[min(len(step_sorted) - 1, int(0.99 * len(step_sorted)))],
+        "fp64_single_point": {"value": fp64_val, "unit": UNIT, "ms_per_call": 1e3 * sum(fp) / len(fp)},
+        "mixed_over_fp64": value / ws / fp64_val,
+        "stage_ms": mean_stage,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(theta.nbytes),
+                "d2h_bytes_per_step": int(H * (8 + 8 + 4))},
+        "gpu_launches": 4 * args.steps,
+        "roofline": roof,
+        "peaks_measured": {k: v for k, v in peaks.items()},
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cat, theta[0])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    barrier(ws)
+
+
+if __name__ == "__main__":
+    main()

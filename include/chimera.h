@@ -1,0 +1,286 @@
+/*
+ * chimera.h - C ABI of the B300 (sm_103a) hierarchical standard-siren
+ * likelihood of arXiv 2504.02034 (CHIMERA 2.0).
+ *
+ * One hyperparameter point Lambda = (H0, Om, Xi0, n, alpha, mu_g, sigma_g,
+ * m_min, m_max, gamma, kappa, z_p) maps to
+ *
+ *     ln L(Lambda) = sum_i ln I_i(Lambda) - N_obs ln xi(Lambda)     (Eq. hyperlike)
+ *
+ * with I_i the per-event integral over sky pixels and a redshift grid of the
+ * GW kernel times the galaxy prior (Eqs. like-integrals, gw-kernel-many1d /
+ * gw-kernel-single1d, p-cat) and xi the injection estimate of the selection
+ * term (Eq. bias and the Monte Carlo sum under it).
+ *
+ * Conventions for every call below:
+ *  - Return value: 0 on success, a negative CHIMERA_ERR_* code otherwise;
+ *    chimera_strerror() names it and chimera_last_error() gives the detail
+ *    of the most recent failure on the calling thread.
+ *  - "host" pointers are ordinary CPU memory owned by the caller; the
+ *    library copies what it needs during the call and keeps no reference.
+ *  - "device" pointers are CUDA device memory on the context's GPU, owned by
+ *    the caller; the library reads/writes them on the stream it is given.
+ *  - All floating-point inputs and outputs are IEEE double.
+ *  - A context is bound to one GPU; calls on one context are serialised by
+ *    an internal lock and may come from any host thread.
+ *  - No call falls back to the CPU.  Without a usable GPU chimera_create
+ *    fails with CHIMERA_ERR_CUDA.
+ */
+#ifndef CHIMERA_H
+#define CHIMERA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes (return values) ---- */
+#define CHIMERA_OK 0
+#define CHIMERA_ERR_INVALID_ARG (-1) /* a pointer, size or value is out of range */
+#define CHIMERA_ERR_NOT_FOUND (-2)   /* unknown catalog id or serve ticket */
+#define CHIMERA_ERR_ADMISSION (-3)   /* device footprint exceeds the HBM budget */
+#define CHIMERA_ERR_CUDA (-4)        /* a CUDA runtime call failed */
+#define CHIMERA_ERR_TIMEOUT (-5)     /* serve poll: result not ready yet */
+#define CHIMERA_ERR_CANCELLED (-6)   /* serve request was cancelled */
+#define CHIMERA_ERR_UNSUPPORTED (-7) /* a size exceeds a compiled-in limit */
+
+/* ---- per-hyperpoint status bits (status[] outputs) ---- */
+#define CHIMERA_PT_OK 0
+#define CHIMERA_PT_OUT_OF_SUPPORT 1 /* ln L = -inf: some I_i = 0, xi = 0, or Lambda inadmissible */
+#define CHIMERA_PT_NONMONOTONE 2    /* ln L = -inf: d d_L^gw/dz <= 0 on z in [0, 10] */
+#define CHIMERA_PT_NEFF_LOW 4       /* warning: N_eff < 5 N_obs (Sec. 2.2); value still returned */
+
+/* ---- precision of a likelihood call ---- */
+#define CHIMERA_FP64 0  /* every stage in IEEE double */
+#define CHIMERA_MIXED 1 /* FP64 tables, FP32 KDE/galaxy sums, FP64 logs and final sums */
+
+/* ---- KDE variant, fixed per catalog (Sec. 2.3) ---- */
+#define CHIMERA_KDE_SINGLE_1D 0 /* one redshift KDE per event, Eq. gw-kernel-single1d */
+#define CHIMERA_KDE_MANY_1D 1   /* one redshift KDE per pixel, Eq. gw-kernel-many1d */
+
+/* ---- device storage of galaxy redshifts and widths ---- */
+#define CHIMERA_GAL_F32 0  /* z and sigma as float */
+#define CHIMERA_GAL_F16 1  /* z as a half offset from the pixel's first galaxy, sigma as half */
+#define CHIMERA_GAL_BF16 2 /* same with bfloat16 */
+
+/* Number of hyperparameters and their order in every theta array. */
+#define CHIMERA_NPARAM 12
+
+typedef struct chimera_ctx chimera_ctx;
+
+/*
+ * Catalog description (all host pointers, caller-owned, copied by
+ * chimera_load_catalog; the caller may free them once it returns).
+ *
+ *  n_events        N_obs, > 0.
+ *  sample_off      [n_events+1] int64 CSR offsets into the PE-sample arrays.
+ *  dL_Mpc, m1_det, m2_det
+ *                  [sample_off[n_events]] detector-frame luminosity distance
+ *                  (Mpc) and masses (Msun) of the PE samples (Sec. 2.2), > 0.
+ *  pix_of_sample   [samples] int32 index of the sample's sky pixel within its
+ *                  event's pixel list (0 .. n_pix_i - 1).
+ *  pix_off         [n_events+1] int64 CSR offsets into the flat pixel list.
+ *  sky_S           [pix_off[n_events]] sky factor S_ik of each pixel, a
+ *                  density per steradian (the 2-D sky KDE of Eq.
+ *                  gw-kernel-many1d evaluated at the pixel centre), >= 0.
+ *  gal_off         [n_pix_total+1] int64 CSR offsets of galaxies per pixel.
+ *  gal_z, gal_sigma
+ *                  [gal_off[n_pix_total]] measured galaxy redshift and its
+ *                  Gaussian width (Eq. p-cat), sigma > 0.
+ *  n_gal_total     N_gal,tot, the prefactor 1/N_gal,tot of p_cat.
+ *  z_max, n_z      redshift grid z_a = a z_max/(n_z-1), a = 0..n_z-1, with
+ *                  trapezoid weights (Sec. 2.3 item b); n_z >= 2.
+ *  n_inj_total     N_inj, all injections drawn (detected or not), >= n_det.
+ *  n_det           number of detected injections stored below (may be 0).
+ *  inj_dL, inj_m1d, inj_m2d, inj_log_pi
+ *                  [n_det] detected injections: detector-frame d_L, masses
+ *                  and the natural log of their draw density pi_inj in
+ *                  (d_L, m1_det, m2_det).
+ *  lambda_g, beta  fixed mass-model constants (Sec. 3.1, Table 1).
+ *  kde_mode        CHIMERA_KDE_SINGLE_1D or CHIMERA_KDE_MANY_1D.
+ *  gal_storage     CHIMERA_GAL_F32 / F16 / BF16 (mixed path only; the FP64
+ *                  path always uses the double values).
+ */
+typedef struct {
+    int32_t n_events;
+    const int64_t *sample_off;
+    const double *dL_Mpc, *m1_det, *m2_det;
+    const int32_t *pix_of_sample;
+    const int64_t *pix_off;
+    const double *sky_S;
+    const int64_t *gal_off;
+    const double *gal_z, *gal_sigma;
+    double n_gal_total;
+    double z_max;
+    int32_t n_z;
+    int64_t n_inj_total;
+    int64_t n_det;
+    const double *inj_dL, *inj_m1d, *inj_m2d, *inj_log_pi;
+    double lambda_g, beta;
+    int32_t kde_mode;
+    int32_t gal_storage;
+} chimera_catalog_desc;
+
+/* Footprint and sizes of a resident catalog (chimera_catalog_info_t). */
+typedef struct {
+    int32_t n_events;
+    int32_t n_z;
+    int64_t n_samples;
+    int64_t n_pixels;
+    int64_t n_galaxies;
+    int64_t n_det;
+    int64_t device_bytes;   /* resident bytes of the catalog itself */
+    int32_t max_samples_per_event;
+    int32_t max_pixels_per_event;
+} chimera_catalog_info_t;
+
+/* Compiled-in limits (CHIMERA_ERR_UNSUPPORTED beyond them). */
+#define CHIMERA_MAX_SAMPLES_PER_EVENT 12288
+#define CHIMERA_MAX_PIXELS_PER_EVENT 1024
+#define CHIMERA_MAX_NZ 8192
+
+/*
+ * chimera_create: open a context on CUDA device `device`.  hbm_budget_bytes
+ * bounds everything the context allocates (catalogs, caches, workspaces);
+ * 0 means 90 % of the device's free memory at creation.  *out receives the
+ * context.  Errors: INVALID_ARG (out == NULL, bad device), CUDA.
+ */
+int chimera_create(chimera_ctx **out, int device, size_t hbm_budget_bytes);
+
+/* chimera_destroy: stop the serving loop, free all device memory. NULL is a no-op. */
+void chimera_destroy(chimera_ctx *ctx);
+
+/*
+ * chimera_load_catalog: validate `desc`, sort each event's samples by
+ * (pixel, d_L) for many-1D or by d_L for single-1D, pack them for the
+ * kernels and copy everything to device memory, where it stays resident
+ * until chimera_unload_catalog or chimera_destroy.  *catalog_id receives a
+ * non-negative id.  Errors: INVALID_ARG (malformed CSR, non-positive
+ * distance or mass, bad enum), UNSUPPORTED (an event beyond the compiled
+ * limits), ADMISSION (footprint over budget), CUDA.
+ */
+int chimera_load_catalog(chimera_ctx *ctx, const chimera_catalog_desc *desc, int32_t *catalog_id);
+int chimera_unload_catalog(chimera_ctx *ctx, int32_t catalog_id);
+int chimera_catalog_info(chimera_ctx *ctx, int32_t catalog_id, chimera_catalog_info_t *info);
+
+/*
+ * chimera_loglike: ln L for a batch of n_points hyperparameter points
+ * (Eq. hyperlike), the effective injection count N_eff of each (Sec. 2.2)
+ * and a status word per point (CHIMERA_PT_* bits).
+ *   theta   host [n_points x 12] row-major, order as CHIMERA_NPARAM above.
+ *   lnL     host [n_points] out;  neff  host [n_points] out (may be NULL);
+ *   status  host [n_points] out (may be NULL).
+ * Every stage runs on the GPU; the call returns when the results are in
+ * host memory.  Results do not depend on which other points share the
+ * batch.  Errors: INVALID_ARG, NOT_FOUND, ADMISSION (workspace), CUDA.
+ */
+int chimera_loglike(chimera_ctx *ctx, int32_t catalog_id, int32_t n_points, const double *theta,
+                    int32_t precision, double *lnL, double *neff, int32_t *status);
+
+/*
+ * chimera_loglike_device: as chimera_loglike with device pointers, enqueued
+ * on `stream` (a cudaStream_t; NULL = the context's own stream) and
+ * returning before completion.  theta_dev [n_points x 12], lnL_dev,
+ * neff_dev [n_points] double, status_dev [n_points] int32 (neff_dev and
+ * status_dev may be NULL).  The hyperpoints are also read back to the host
+ * once per call to group them by Om (that copy is synchronous).
+ */
+int chimera_loglike_device(chimera_ctx *ctx, int32_t catalog_id, int32_t n_points,
+                           const double *theta_dev, int32_t precision, double *lnL_dev,
+                           double *neff_dev, int32_t *status_dev, void *stream);
+
+/*
+ * chimera_terms: the stages of ln L for inspection and testing.
+ *   lnI   host [n_points x n_events] ln I_i (Eq. like-integrals), or NULL;
+ *   bw    host [n_points x n_events] KDE bandwidth b_i per event, or NULL;
+ *   xi    host [n_points] selection term xi (Eq. bias), or NULL;
+ *   neff  host [n_points] N_eff, or NULL.
+ */
+int chimera_terms(chimera_ctx *ctx, int32_t catalog_id, int32_t n_points, const double *theta,
+                  int32_t precision, double *lnI, double *bw, double *xi, double *neff);
+
+/*
+ * chimera_grad: ln L and its gradient with respect to all 12
+ * hyperparameters for each point, by a hand-written adjoint that recomputes
+ * the KDE instead of storing it.
+ *   dlnL  host [n_points x 12] out, same parameter order as theta.
+ * The derivative with respect to m_min and m_max is the almost-everywhere
+ * derivative (the jump of samples across the mass edges is not included).
+ * Errors as chimera_loglike.
+ */
+int chimera_grad(chimera_ctx *ctx, int32_t catalog_id, int32_t n_points, const double *theta,
+                 int32_t precision, double *lnL, double *dlnL, int32_t *status);
+
+/*
+ * Serving (continuous batching).  A request carries n_points hyperpoints
+ * for one resident catalog; requests for the same catalog that are queued
+ * together are evaluated in one batched launch, different catalogs run on
+ * their own CUDA streams concurrently, and a request is admitted only while
+ * the workspace it needs fits the HBM budget.
+ *   flags   bit 0: CHIMERA_SERVE_GRAD (also compute dlnL),
+ *           bit 1: CHIMERA_SERVE_MIXED (mixed precision, else FP64).
+ *   theta   host [n_points x 12], copied during submit.
+ *   ticket  out: identifies the request for poll/cancel.
+ * chimera_serve_poll waits up to timeout_us microseconds (0 = do not wait,
+ * < 0 = wait indefinitely) and copies the results into the host buffers
+ * lnL [n], dlnL [n x 12] (grad requests, may be NULL), status [n] (may be
+ * NULL); it returns CHIMERA_ERR_TIMEOUT while the request is pending and
+ * forgets the ticket after the first successful poll.  chimera_serve_stats
+ * reports latency quantiles (ms) over completed requests.
+ */
+#define CHIMERA_SERVE_GRAD 1
+#define CHIMERA_SERVE_MIXED 2
+int chimera_serve_submit(chimera_ctx *ctx, int32_t catalog_id, int32_t n_points, const double *theta,
+                         int32_t flags, uint64_t *ticket);
+int chimera_serve_poll(chimera_ctx *ctx, uint64_t ticket, int64_t timeout_us, double *lnL,
+                       double *dlnL, int32_t *status);
+int chimera_serve_cancel(chimera_ctx *ctx, uint64_t ticket);
+typedef struct {
+    int64_t completed;
+    int64_t batches;
+    int64_t points;
+    double p50_ms, p99_ms, mean_ms;
+    int64_t admitted_bytes_peak;
+} chimera_serve_stats_t;
+int chimera_serve_stats(chimera_ctx *ctx, chimera_serve_stats_t *out);
+
+/*
+ * Tracing.  chimera_set_trace(ctx, 1) makes the synchronous likelihood
+ * calls record CUDA events around each stage on the context's stream;
+ * chimera_stage_ms then returns the last call's stage times in
+ * milliseconds: ms[0] cosmology tables (K1), ms[1] galaxy profile (K3,
+ * 0 when cached), ms[2] event integrals (K2+K4), ms[3] selection (K5),
+ * ms[4] combine (K6), ms[5] adjoint (K7, gradient calls only).
+ */
+int chimera_set_trace(chimera_ctx *ctx, int enable);
+int chimera_stage_ms(chimera_ctx *ctx, double *ms);
+
+/*
+ * chimera_kde_pairs: algorithmic work of the mixed-precision event kernel,
+ * for the roofline: for each of the n_points hyperpoints, the number of
+ * (PE sample, grid point) pairs with w_j > 0 and |z_a - z_j| <= 6 b_i,
+ * summed over all events.  pairs: host [n_points] int64 out.
+ */
+int chimera_kde_pairs(chimera_ctx *ctx, int32_t catalog_id, int32_t n_points, const double *theta,
+                      int64_t *pairs);
+
+/* Name of an error code; never NULL. */
+const char *chimera_strerror(int code);
+/* Detail of the last failure on the calling thread ("" if none). */
+const char *chimera_last_error(void);
+
+/*
+ * chimera_peaks: microbenchmarks that give roofline denominators on this
+ * GPU: out[0] = FP32 FMUL+FFMA pair rate (pairs/s, the KDE inner-loop mix),
+ * out[1] = MUFU ex2 rate (evaluations/s), out[2] = FP64 DFMA rate (DFMA/s),
+ * out[3] = device-to-device copy bandwidth (bytes/s, read + write).
+ * `out` is host [4].  Not part of the method; used by the benchmark.
+ */
+int chimera_peaks(chimera_ctx *ctx, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

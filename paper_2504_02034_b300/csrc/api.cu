@@ -1,0 +1,936 @@
+// C ABI of libchimera (include/chimera.h) and the host runtime behind it:
+// budgeted device allocation, catalog packing and residency, per-Om caches
+// of the forward distance table and of the galaxy profile, and the
+// orchestration of the kernels K1 -> K3 -> K2/K4 -> K5 -> K6 on a stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <numeric>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "runtime.cuh"
+
+namespace chim {
+
+// ------------------------------------------------------------ errors ----
+static thread_local std::string g_last_error;
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int cuda_check(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return CHIMERA_OK;
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return CHIMERA_ERR_CUDA;
+}
+
+#define CK(call)                                               \
+    do {                                                       \
+        int rc_ = cuda_check((call), #call);                   \
+        if (rc_) return rc_;                                   \
+    } while (0)
+#define RC(call)                                               \
+    do {                                                       \
+        int rc_ = (call);                                      \
+        if (rc_) return rc_;                                   \
+    } while (0)
+
+// ------------------------------------------------------- allocation ----
+// CHIMERA_FAULT_ALLOC=N makes the N-th device allocation of the process fail
+// (host-side fault injection for tests).
+static std::atomic<long> g_alloc_count{0};
+
+int dev_alloc(Ctx &ctx, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    long n = ++g_alloc_count;
+    if (const char *f = getenv("CHIMERA_FAULT_ALLOC")) {
+        if (atol(f) == n) {
+            set_error("injected allocation failure (CHIMERA_FAULT_ALLOC)");
+            return CHIMERA_ERR_CUDA;
+        }
+    }
+    if (ctx.used.load() + bytes > ctx.budget) {
+        set_error("allocation of " + std::to_string(bytes) + " bytes exceeds the HBM budget");
+        return CHIMERA_ERR_ADMISSION;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return cuda_check(e, "cudaMalloc");
+    }
+    ctx.used += bytes;
+    return CHIMERA_OK;
+}
+
+void dev_free(Ctx &ctx, void *p, size_t bytes) {
+    if (!p) return;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    cudaFree(p);
+    ctx.used -= bytes;
+}
+
+// ------------------------------------------------------- workspace ----
+CallPtrs Workspace::ptrs(int H, const DevCatalog &c) const {
+    CallPtrs p{};
+    char *q = param;
+    p.theta = reinterpret_cast<const double *>(q);
+    q += sizeof(double) * 12 * H;
+    p.status = reinterpret_cast<int32_t *>(q);
+    q += sizeof(int64_t) * H;  // int32 status padded to 8 bytes
+    p.fwd = reinterpret_cast<const double *const *>(q);
+    q += sizeof(void *) * H;
+    p.prof = reinterpret_cast<const void *const *>(q);
+    p.hp = hp;
+    p.inv64 = inv64;
+    p.inv32 = inv32;
+    p.F64 = F64;
+    p.F32 = F32;
+    p.lnI = lnI;
+    p.bw = bw;
+    p.selp = selp;
+    p.n_chunk = selection_chunks(c);
+    p.lnL = lnL;
+    p.neff = neff;
+    p.xi = xi;
+    p.pairs = count_pairs ? pairs : nullptr;
+    return p;
+}
+
+void ws_release(Ctx &ctx, Workspace &ws) {
+    for (void *a : ws.allocs) cudaFree(a);
+    ws.allocs.clear();
+    ctx.used -= ws.bytes;
+    ws.bytes = 0;
+    if (ws.hstage) cudaFreeHost(ws.hstage);
+    ws.hstage = nullptr;
+    ws.hstage_bytes = 0;
+    ws.Hcap = 0;
+    ws.nev_cap = 0;
+    ws.nz_cap = 0;
+    ws.nchunk_cap = 0;
+    ws.ngal_cap = 0;
+}
+
+int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat) {
+    const DevCatalog &c = cat.d;
+    int nch = selection_chunks(c);
+    if (H <= ws.Hcap && c.n_events <= ws.nev_cap && c.n_z <= ws.nz_cap && nch <= ws.nchunk_cap &&
+        c.n_gal <= ws.ngal_cap)
+        return CHIMERA_OK;
+    // grow (with some headroom) and re-allocate everything
+    int Hn = std::max(H, ws.Hcap);
+    int64_t nev = std::max<int64_t>(c.n_events, ws.nev_cap);
+    int nz = std::max(c.n_z, ws.nz_cap);
+    int nc = std::max(nch, ws.nchunk_cap);
+    int64_t ng = std::max<int64_t>(c.n_gal, ws.ngal_cap);
+    if (ws.st) cudaStreamSynchronize(ws.st);
+    ws_release(ctx, ws);
+    struct Item { void **p; size_t b; };
+    std::vector<Item> items = {
+        {(void **)&ws.param, ws.param_bytes(Hn)},
+        {(void **)&ws.hp, sizeof(HP) * Hn},
+        {(void **)&ws.inv64, sizeof(double2) * (size_t)Hn * (NU + 1)},
+        {(void **)&ws.inv32, sizeof(float4) * (size_t)Hn * NU},
+        {(void **)&ws.F64, sizeof(double) * (size_t)Hn * nz},
+        {(void **)&ws.F32, sizeof(float) * (size_t)Hn * nz},
+        {(void **)&ws.lnI, sizeof(double) * (size_t)Hn * nev},
+        {(void **)&ws.bw, sizeof(double) * (size_t)Hn * nev},
+        {(void **)&ws.selp, sizeof(double) * 2 * (size_t)Hn * nc},
+        {(void **)&ws.lnL, sizeof(double) * Hn},
+        {(void **)&ws.neff, sizeof(double) * Hn},
+        {(void **)&ws.xi, sizeof(double) * Hn},
+        {(void **)&ws.dv, sizeof(double) * nz},
+        {(void **)&ws.invZ64, sizeof(double) * (size_t)std::max<int64_t>(ng, 1)},
+        {(void **)&ws.invZ32, sizeof(float) * (size_t)std::max<int64_t>(ng, 1)},
+        {(void **)&ws.grad, sizeof(double) * 12 * (size_t)Hn},
+        {(void **)&ws.pairs, sizeof(unsigned long long) * (size_t)Hn},
+    };
+    for (auto &it : items) {
+        int rc = dev_alloc(ctx, it.p, it.b);
+        if (rc) {
+            for (auto &jt : items)
+                if (*jt.p) { cudaFree(*jt.p); *jt.p = nullptr; }
+            ctx.used -= ws.bytes;
+            ws.bytes = 0;
+            ws.allocs.clear();
+            return rc;
+        }
+        size_t rb = (it.b + 255) & ~(size_t)255;
+        ws.bytes += rb;
+        ws.allocs.push_back(*it.p);
+    }
+    ws.hstage_bytes = ws.param_bytes(Hn);
+    if (cudaMallocHost(&ws.hstage, ws.hstage_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMallocHost failed for the staging buffer");
+        return CHIMERA_ERR_CUDA;
+    }
+    ws.Hcap = Hn;
+    ws.nev_cap = nev;
+    ws.nz_cap = nz;
+    ws.nchunk_cap = nc;
+    ws.ngal_cap = ng;
+    return CHIMERA_OK;
+}
+
+// ------------------------------------------------------------ caches ----
+static uint64_t bits_of(double x) {
+    uint64_t b;
+    memcpy(&b, &x, 8);
+    return b;
+}
+
+static int fwd_table(Ctx &ctx, double Om, cudaStream_t st, const double **out) {
+    uint64_t key = bits_of(Om);
+    auto it = ctx.fwd.find(key);
+    if (it == ctx.fwd.end()) {
+        FwdEntry e;
+        RC(dev_alloc(ctx, (void **)&e.table, sizeof(double) * NT_FWD));
+        CK(cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming));
+        launch_fwd_table(Om, e.table, st);
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(e.ready, st));
+        it = ctx.fwd.emplace(key, e).first;
+    } else {
+        CK(cudaStreamWaitEvent(st, it->second.ready, 0));
+    }
+    *out = it->second.table;
+    return CHIMERA_OK;
+}
+
+static void evict_profiles(Ctx &ctx, Catalog &cat, size_t need) {
+    // least recently used first, never the ones touched by the current call
+    while (ctx.used.load() + need > ctx.budget && !cat.prof.empty()) {
+        auto victim = cat.prof.end();
+        for (auto it = cat.prof.begin(); it != cat.prof.end(); ++it)
+            if (it->second.last_use < ctx.tick &&
+                (victim == cat.prof.end() || it->second.last_use < victim->second.last_use))
+                victim = it;
+        if (victim == cat.prof.end()) return;
+        cudaDeviceSynchronize();
+        dev_free(ctx, victim->second.G, victim->second.bytes);
+        if (victim->second.Gh) dev_free(ctx, victim->second.Gh, 0);
+        cudaEventDestroy(victim->second.ready);
+        cat.prof.erase(victim);
+    }
+}
+
+static int profile(Ctx &ctx, Catalog &cat, Workspace &ws, double Om, int kind, const double *fwd,
+                   const void **out) {
+    auto key = std::make_pair(bits_of(Om), kind);
+    auto it = cat.prof.find(key);
+    const DevCatalog &c = cat.d;
+    if (it == cat.prof.end()) {
+        ProfEntry e;
+        size_t esz = kind == 0 ? sizeof(double) : sizeof(float);
+        e.bytes = esz * (size_t)c.n_pix * c.n_z;
+        size_t hb = c.kde_mode == CHIMERA_KDE_SINGLE_1D ? esz * (size_t)c.n_events * c.n_z : 0;
+        evict_profiles(ctx, cat, e.bytes + hb);
+        RC(dev_alloc(ctx, &e.G, e.bytes));
+        if (hb) {
+            int rc = dev_alloc(ctx, &e.Gh, hb);
+            if (rc) { dev_free(ctx, e.G, e.bytes); return rc; }
+        }
+        CK(cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming));
+        if (kind == 0)
+            launch_galaxy_profile(c, fwd, Om, ws.dv, ws.invZ64, ws.invZ32, (double *)e.G, nullptr, ws.st);
+        else
+            launch_galaxy_profile(c, fwd, Om, ws.dv, ws.invZ64, ws.invZ32, nullptr, (float *)e.G, ws.st);
+        if (hb) {
+            if (kind == 0) launch_profile_sum(c, (double *)e.G, nullptr, (double *)e.Gh, nullptr, ws.st);
+            else launch_profile_sum(c, nullptr, (float *)e.G, nullptr, (float *)e.Gh, ws.st);
+        }
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(e.ready, ws.st));
+        it = cat.prof.emplace(key, e).first;
+    } else {
+        CK(cudaStreamWaitEvent(ws.st, it->second.ready, 0));
+    }
+    it->second.last_use = ctx.tick;
+    *out = c.kde_mode == CHIMERA_KDE_SINGLE_1D ? it->second.Gh : it->second.G;
+    return CHIMERA_OK;
+}
+
+// ----------------------------------------------------------- forward ----
+static const double kSafeTheta[12] = {70.0, 0.3, 1.0, 1.91, 3.4, 34.0, 3.6, 5.0, 100.0, 2.7, 3.0, 2.0};
+
+static bool admissible(const double *t) {
+    for (int k = 0; k < 12; k++)
+        if (!std::isfinite(t[k])) return false;
+    return t[0] > 0.0 && t[1] >= 0.0 && t[1] <= 1.0 && t[2] > 0.0 && t[6] > 0.0 && t[7] > 0.0 &&
+           t[8] > t[7] && t[11] > -1.0;
+}
+
+int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, int precision) {
+    RC(ws_ensure(ctx, ws, H, cat));
+    ctx.tick++;
+    const DevCatalog &c = cat.d;
+    // stage: theta (admissible copy) | status | fwd ptrs | prof ptrs
+    char *q = ws.hstage;
+    double *th = reinterpret_cast<double *>(q);
+    int32_t *st = reinterpret_cast<int32_t *>(q + sizeof(double) * 12 * H);
+    const double **fw = reinterpret_cast<const double **>(q + sizeof(double) * 12 * H + 8 * H);
+    const void **pr = reinterpret_cast<const void **>(q + sizeof(double) * 12 * H + 8 * H + 8 * H);
+    const int kind = precision == CHIMERA_FP64 ? 0 : 1;
+    if (ws.trace) {
+        for (auto &e : ws.tev)
+            if (!e) CK(cudaEventCreate(&e));
+        ws.traced_adjoint = false;
+        CK(cudaEventRecord(ws.tev[0], ws.st));
+    }
+    memset(st, 0, 8 * (size_t)H);
+    for (int h = 0; h < H; h++) {
+        const double *t = theta + 12 * h;
+        bool ok = admissible(t);
+        memcpy(th + 12 * h, ok ? t : kSafeTheta, sizeof(double) * 12);
+        st[h] = ok ? 0 : CHIMERA_PT_OUT_OF_SUPPORT;
+    }
+    std::map<uint64_t, std::pair<const double *, const void *>> byOm;
+    for (int h = 0; h < H; h++) {
+        double Om = th[12 * h + 1];
+        uint64_t k = bits_of(Om);
+        auto it = byOm.find(k);
+        if (it == byOm.end()) {
+            const double *f = nullptr;
+            const void *g = nullptr;
+            RC(fwd_table(ctx, Om, ws.st, &f));
+            RC(profile(ctx, cat, ws, Om, kind, f, &g));
+            it = byOm.emplace(k, std::make_pair(f, g)).first;
+        }
+        fw[h] = it->second.first;
+        pr[h] = it->second.second;
+    }
+    if (ws.trace) CK(cudaEventRecord(ws.tev[1], ws.st));
+    CK(cudaMemcpyAsync(ws.param, ws.hstage, ws.param_bytes(H), cudaMemcpyHostToDevice, ws.st));
+    CallPtrs p = ws.ptrs(H, c);
+    if (p.pairs) CK(cudaMemsetAsync(p.pairs, 0, sizeof(unsigned long long) * H, ws.st));
+    launch_hyper_tables(c, p, H, ws.st);
+    if (ws.trace) CK(cudaEventRecord(ws.tev[2], ws.st));
+    if (precision == CHIMERA_FP64) launch_event_fp64(c, p, H, ws.st);
+    else launch_event_mixed(c, p, H, ws.st);
+    if (ws.trace) CK(cudaEventRecord(ws.tev[3], ws.st));
+    launch_selection(c, p, H, precision == CHIMERA_FP64, ws.st);
+    if (ws.trace) CK(cudaEventRecord(ws.tev[4], ws.st));
+    launch_combine(c, p, H, ws.st);
+    if (ws.trace) CK(cudaEventRecord(ws.tev[5], ws.st));
+    CK(cudaGetLastError());
+    return CHIMERA_OK;
+}
+
+std::shared_ptr<Catalog> find_catalog(Ctx &ctx, int32_t id) {
+    auto it = ctx.cats.find(id);
+    if (it == ctx.cats.end()) return nullptr;
+    return it->second;
+}
+
+// ----------------------------------------------------- catalog load ----
+static uint16_t f32_to_half_bits(float x) { return __half_as_ushort(__float2half_rn(x)); }
+static uint16_t f32_to_bf16_bits(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;  // NaN
+    uint32_t r = u + 0x7fffu + ((u >> 16) & 1u);         // round to nearest even
+    return (uint16_t)(r >> 16);
+}
+static float half_bits_to_f32(uint16_t b) { return __half2float(__ushort_as_half(b)); }
+static float bf16_bits_to_f32(uint16_t b) {
+    uint32_t u = ((uint32_t)b) << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+static bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id) {
+    if (!d || !out_id) { set_error("null descriptor or id pointer"); return CHIMERA_ERR_INVALID_ARG; }
+    const int ne = d->n_events;
+    auto bad = [](const std::string &m) { set_error(m); return CHIMERA_ERR_INVALID_ARG; };
+    if (ne <= 0) return bad("n_events must be positive");
+    if (!d->sample_off || !d->dL_Mpc || !d->m1_det || !d->m2_det || !d->pix_of_sample ||
+        !d->pix_off || !d->sky_S || !d->gal_off)
+        return bad("null array in catalog descriptor");
+    if (d->n_z < 2) return bad("n_z must be >= 2");
+    if (d->n_z > CHIMERA_MAX_NZ) { set_error("n_z above CHIMERA_MAX_NZ"); return CHIMERA_ERR_UNSUPPORTED; }
+    if (!finite_pos(d->z_max)) return bad("z_max must be positive");
+    if (!finite_pos(d->n_gal_total)) return bad("n_gal_total must be positive");
+    if (d->n_det < 0 || d->n_inj_total < 1 || d->n_inj_total < d->n_det) return bad("bad injection counts");
+    if (d->n_det > 0 && (!d->inj_dL || !d->inj_m1d || !d->inj_m2d || !d->inj_log_pi))
+        return bad("null injection array");
+    if (!(d->lambda_g >= 0.0 && d->lambda_g <= 1.0) || !std::isfinite(d->beta))
+        return bad("lambda_g must lie in [0, 1] and beta be finite");
+    if (d->kde_mode != CHIMERA_KDE_SINGLE_1D && d->kde_mode != CHIMERA_KDE_MANY_1D) return bad("bad kde_mode");
+    if (d->gal_storage < 0 || d->gal_storage > 2) return bad("bad gal_storage");
+    if (d->sample_off[0] != 0 || d->pix_off[0] != 0) return bad("CSR offsets must start at 0");
+    int max_ns = 0, max_np = 0;
+    for (int i = 0; i < ne; i++) {
+        int64_t a = d->sample_off[i + 1] - d->sample_off[i];
+        int64_t b = d->pix_off[i + 1] - d->pix_off[i];
+        if (a < 1 || b < 1) return bad("every event needs >= 1 sample and >= 1 pixel");
+        if (a > CHIMERA_MAX_SAMPLES_PER_EVENT || b > CHIMERA_MAX_PIXELS_PER_EVENT) {
+            set_error("event " + std::to_string(i) + " exceeds the per-event sample or pixel limit");
+            return CHIMERA_ERR_UNSUPPORTED;
+        }
+        max_ns = std::max<int>(max_ns, (int)a);
+        max_np = std::max<int>(max_np, (int)b);
+    }
+    const int64_t ns = d->sample_off[ne], np = d->pix_off[ne];
+    if (d->gal_off[0] != 0) return bad("gal_off must start at 0");
+    for (int64_t p = 0; p < np; p++) {
+        if (d->gal_off[p + 1] < d->gal_off[p]) return bad("gal_off not monotone");
+        if (!(std::isfinite(d->sky_S[p]) && d->sky_S[p] >= 0.0)) return bad("sky_S must be finite and >= 0");
+    }
+    const int64_t ng = d->gal_off[np];
+    if (ng > 0 && (!d->gal_z || !d->gal_sigma)) return bad("null galaxy array");
+    for (int64_t j = 0; j < ns; j++) {
+        if (!finite_pos(d->dL_Mpc[j]) || !finite_pos(d->m1_det[j]) || !finite_pos(d->m2_det[j]))
+            return bad("PE sample distances and masses must be finite and positive");
+    }
+    for (int i = 0; i < ne; i++)
+        for (int64_t j = d->sample_off[i]; j < d->sample_off[i + 1]; j++)
+            if (d->pix_of_sample[j] < 0 || d->pix_of_sample[j] >= d->pix_off[i + 1] - d->pix_off[i])
+                return bad("pix_of_sample out of range");
+    for (int64_t g = 0; g < ng; g++)
+        if (!std::isfinite(d->gal_z[g]) || !finite_pos(d->gal_sigma[g])) return bad("bad galaxy z or sigma");
+    for (int64_t j = 0; j < d->n_det; j++)
+        if (!finite_pos(d->inj_dL[j]) || !finite_pos(d->inj_m1d[j]) || !finite_pos(d->inj_m2d[j]) ||
+            !std::isfinite(d->inj_log_pi[j]))
+            return bad("bad injection values");
+
+    auto cat = std::make_shared<Catalog>();
+    DevCatalog &c = cat->d;
+    c.n_events = ne;
+    c.n_z = d->n_z;
+    c.kde_mode = d->kde_mode;
+    c.gal_storage = d->gal_storage;
+    c.n_samples = ns;
+    c.n_pix = np;
+    c.n_gal = ng;
+    c.n_det = d->n_det;
+    c.n_inj_total = d->n_inj_total;
+    c.z_max = d->z_max;
+    c.dz = d->z_max / (d->n_z - 1);
+    c.n_gal_total = d->n_gal_total;
+    c.lambda_g = d->lambda_g;
+    c.beta = d->beta;
+    c.max_ns = max_ns;
+    c.max_npix = max_np;
+    double dmax = 0.0;
+    for (int64_t j = 0; j < ns; j++) dmax = std::max(dmax, d->dL_Mpc[j]);
+    for (int64_t j = 0; j < d->n_det; j++) dmax = std::max(dmax, d->inj_dL[j]);
+    c.d_top = dmax * (1.0 + 1e-9);
+
+    // ---- samples: sort inside each event
+    std::vector<int64_t> order(ns);
+    std::iota(order.begin(), order.end(), 0);
+    const bool many = d->kde_mode == CHIMERA_KDE_MANY_1D;
+    for (int i = 0; i < ne; i++) {
+        auto b = order.begin() + d->sample_off[i], e = order.begin() + d->sample_off[i + 1];
+        std::stable_sort(b, e, [&](int64_t x, int64_t y) {
+            if (many && d->pix_of_sample[x] != d->pix_of_sample[y])
+                return d->pix_of_sample[x] < d->pix_of_sample[y];
+            return d->dL_Mpc[x] < d->dL_Mpc[y];
+        });
+    }
+    std::vector<float4> s32(ns);
+    std::vector<double> sd(ns), sm1(ns), sm2(ns);
+    auto tcoord = [&](double dl, int &k, float &f) {
+        double t = std::sqrt(dl / c.d_top) * NU;
+        k = std::min((int)t, NU - 1);
+        double fr = t - k;
+        f = (float)std::min(fr, 1.0);
+    };
+    for (int64_t j = 0; j < ns; j++) {
+        int64_t o = order[j];
+        int k;
+        float f;
+        tcoord(d->dL_Mpc[o], k, f);
+        float kb;
+        memcpy(&kb, &k, 4);
+        s32[j] = make_float4(kb, f, (float)std::log(d->m1_det[o]), (float)std::log(d->m2_det[o]));
+        sd[j] = d->dL_Mpc[o];
+        sm1[j] = d->m1_det[o];
+        sm2[j] = d->m2_det[o];
+    }
+    // ---- segments
+    std::vector<int64_t> seg_soff;
+    std::vector<double> seg_pf;
+    std::vector<int32_t> ev_segoff(ne + 1);
+    int max_seg = 1;
+    if (many) {
+        seg_soff.resize(np + 1);
+        seg_pf.resize(np);
+        for (int i = 0; i < ne; i++) {
+            ev_segoff[i] = (int32_t)d->pix_off[i];
+            int npi = (int)(d->pix_off[i + 1] - d->pix_off[i]);
+            std::vector<int64_t> cnt(npi, 0);
+            for (int64_t j = d->sample_off[i]; j < d->sample_off[i + 1]; j++) cnt[d->pix_of_sample[j]]++;
+            int64_t run = d->sample_off[i];
+            for (int k = 0; k < npi; k++) {
+                int64_t p = d->pix_off[i] + k;
+                seg_soff[p] = run;
+                run += cnt[k];
+                seg_pf[p] = cnt[k] > 0 ? d->sky_S[p] / (double)cnt[k] : 0.0;
+            }
+            max_seg = std::max(max_seg, npi);
+        }
+        seg_soff[np] = ns;
+        ev_segoff[ne] = (int32_t)np;
+    } else {
+        seg_soff.assign(d->sample_off, d->sample_off + ne + 1);
+        seg_pf.resize(ne);
+        for (int i = 0; i < ne; i++) {
+            ev_segoff[i] = i;
+            seg_pf[i] = 1.0 / (double)(d->sample_off[i + 1] - d->sample_off[i]);
+        }
+        ev_segoff[ne] = ne;
+    }
+    c.n_seg = (int64_t)seg_pf.size();
+    c.max_seg = max_seg;
+    // ---- heavy-first event order: cost ~ N_s x spread of ln d_L
+    std::vector<double> cost(ne);
+    for (int i = 0; i < ne; i++) {
+        double m = 0, m2 = 0;
+        int64_t n = d->sample_off[i + 1] - d->sample_off[i];
+        for (int64_t j = d->sample_off[i]; j < d->sample_off[i + 1]; j++) {
+            double l = std::log(d->dL_Mpc[j]);
+            m += l;
+            m2 += l * l;
+        }
+        m /= n;
+        cost[i] = n * std::sqrt(std::max(m2 / n - m * m, 0.0) + 1e-6);
+    }
+    std::vector<int32_t> ev_order(ne);
+    std::iota(ev_order.begin(), ev_order.end(), 0);
+    std::stable_sort(ev_order.begin(), ev_order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    // ---- galaxies: sorted by z inside each pixel
+    std::vector<int64_t> gorder(ng);
+    std::iota(gorder.begin(), gorder.end(), 0);
+    for (int64_t p = 0; p < np; p++)
+        std::stable_sort(gorder.begin() + d->gal_off[p], gorder.begin() + d->gal_off[p + 1],
+                         [&](int64_t x, int64_t y) { return d->gal_z[x] < d->gal_z[y]; });
+    std::vector<double> gz(ng), gs(ng), sigmax(np, 0.0);
+    std::vector<float> gz32, gs32, zref(np, 0.f), sigmax32(np, 0.f);
+    std::vector<uint16_t> gzq, gsq;
+    if (d->gal_storage == CHIMERA_GAL_F32) { gz32.resize(ng); gs32.resize(ng); }
+    else { gzq.resize(ng); gsq.resize(ng); }
+    for (int64_t p = 0; p < np; p++) {
+        int64_t a = d->gal_off[p], b = d->gal_off[p + 1];
+        if (b > a) zref[p] = (float)d->gal_z[gorder[a]];
+        for (int64_t g = a; g < b; g++) {
+            int64_t o = gorder[g];
+            gz[g] = d->gal_z[o];
+            gs[g] = d->gal_sigma[o];
+            sigmax[p] = std::max(sigmax[p], gs[g]);
+            float sdec;
+            if (d->gal_storage == CHIMERA_GAL_F32) {
+                gz32[g] = (float)gz[g];
+                gs32[g] = (float)gs[g];
+                sdec = gs32[g];
+            } else {
+                float off = (float)gz[g] - zref[p];
+                bool h16 = d->gal_storage == CHIMERA_GAL_F16;
+                gzq[g] = h16 ? f32_to_half_bits(off) : f32_to_bf16_bits(off);
+                gsq[g] = h16 ? f32_to_half_bits((float)gs[g]) : f32_to_bf16_bits((float)gs[g]);
+                sdec = h16 ? half_bits_to_f32(gsq[g]) : bf16_bits_to_f32(gsq[g]);
+                float zdec = zref[p] + (h16 ? half_bits_to_f32(gzq[g]) : bf16_bits_to_f32(gzq[g]));
+                if (!std::isfinite(zdec)) return bad("galaxy z offset not representable in 16-bit storage");
+            }
+            if (!(sdec > 0.f) || !std::isfinite(sdec)) return bad("galaxy sigma not representable in the storage type");
+            sigmax32[p] = std::max(sigmax32[p], sdec);
+        }
+    }
+    // ---- injections
+    const int64_t nd = d->n_det;
+    std::vector<float4> i32a(nd);
+    std::vector<float2> i32b(nd);
+    for (int64_t j = 0; j < nd; j++) {
+        int k;
+        float f;
+        tcoord(d->inj_dL[j], k, f);
+        float kb;
+        memcpy(&kb, &k, 4);
+        i32a[j] = make_float4(kb, f, (float)std::log(d->inj_m1d[j]), (float)std::log(d->inj_m2d[j]));
+        i32b[j] = make_float2((float)d->inj_dL[j], (float)d->inj_log_pi[j]);
+    }
+    std::vector<int64_t> ev_soff(d->sample_off, d->sample_off + ne + 1);
+    std::vector<int64_t> ev_poff(d->pix_off, d->pix_off + ne + 1);
+    std::vector<int64_t> goff(d->gal_off, d->gal_off + np + 1);
+    std::vector<double> pixS(d->sky_S, d->sky_S + np);
+
+    // ---- upload
+    struct Up { void **dst; const void *src; size_t bytes; };
+    std::vector<Up> ups = {
+        {(void **)&c.ev_soff, ev_soff.data(), 8 * ev_soff.size()},
+        {(void **)&c.ev_poff, ev_poff.data(), 8 * ev_poff.size()},
+        {(void **)&c.ev_order, ev_order.data(), 4 * ev_order.size()},
+        {(void **)&c.seg_soff, seg_soff.data(), 8 * seg_soff.size()},
+        {(void **)&c.seg_pf, seg_pf.data(), 8 * seg_pf.size()},
+        {(void **)&c.ev_segoff, ev_segoff.data(), 4 * ev_segoff.size()},
+        {(void **)&c.pix_S, pixS.data(), 8 * pixS.size()},
+        {(void **)&c.gal_off, goff.data(), 8 * goff.size()},
+        {(void **)&c.pix_sigmax, sigmax.data(), 8 * sigmax.size()},
+        {(void **)&c.pix_sigmax32, sigmax32.data(), 4 * sigmax32.size()},
+        {(void **)&c.pix_zref, zref.data(), 4 * zref.size()},
+        {(void **)&c.gz64, gz.data(), 8 * gz.size()},
+        {(void **)&c.gs64, gs.data(), 8 * gs.size()},
+        {(void **)&c.s32, s32.data(), 16 * s32.size()},
+        {(void **)&c.sd64, sd.data(), 8 * sd.size()},
+        {(void **)&c.sm1_64, sm1.data(), 8 * sm1.size()},
+        {(void **)&c.sm2_64, sm2.data(), 8 * sm2.size()},
+    };
+    std::vector<double> id(d->inj_dL ? d->inj_dL : (const double *)nullptr,
+                           d->inj_dL ? d->inj_dL + nd : (const double *)nullptr);
+    if (nd > 0) {
+        ups.push_back({(void **)&c.i32a, i32a.data(), 16 * (size_t)nd});
+        ups.push_back({(void **)&c.i32b, i32b.data(), 8 * (size_t)nd});
+        ups.push_back({(void **)&c.id64, d->inj_dL, 8 * (size_t)nd});
+        ups.push_back({(void **)&c.im1_64, d->inj_m1d, 8 * (size_t)nd});
+        ups.push_back({(void **)&c.im2_64, d->inj_m2d, 8 * (size_t)nd});
+        ups.push_back({(void **)&c.ilp64, d->inj_log_pi, 8 * (size_t)nd});
+    }
+    if (d->gal_storage == CHIMERA_GAL_F32) {
+        ups.push_back({(void **)&c.gz32, gz32.data(), 4 * gz32.size()});
+        ups.push_back({(void **)&c.gs32, gs32.data(), 4 * gs32.size()});
+    } else {
+        ups.push_back({(void **)&c.gzq, gzq.data(), 2 * gzq.size()});
+        ups.push_back({(void **)&c.gsq, gsq.data(), 2 * gsq.size()});
+    }
+    size_t total = 0;
+    for (auto &u : ups) total += (std::max<size_t>(u.bytes, 16) + 255) & ~(size_t)255;
+    if (ctx.used.load() + total > ctx.budget) {
+        set_error("catalog footprint " + std::to_string(total) + " bytes exceeds the HBM budget");
+        return CHIMERA_ERR_ADMISSION;
+    }
+    for (auto &u : ups) {
+        int rc = dev_alloc(ctx, u.dst, u.bytes);
+        if (rc) {
+            for (void *a : cat->allocs) cudaFree(a);
+            ctx.used -= cat->bytes;
+            return rc;
+        }
+        cat->allocs.push_back(*u.dst);
+        cat->bytes += (std::max<size_t>(u.bytes, 16) + 255) & ~(size_t)255;
+        if (u.bytes) {
+            cudaError_t e = cudaMemcpy(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                for (void *a : cat->allocs) cudaFree(a);
+                ctx.used -= cat->bytes;
+                return cuda_check(e, "cudaMemcpy catalog upload");
+            }
+        }
+    }
+    // event kernels need their shared memory
+    int maxsm = 0;
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx.device);
+    if ((int)event_mixed_smem(c) > maxsm || (int)event_fp64_smem(c) > maxsm) {
+        for (void *a : cat->allocs) cudaFree(a);
+        ctx.used -= cat->bytes;
+        set_error("catalog needs more shared memory per block than the device offers");
+        return CHIMERA_ERR_UNSUPPORTED;
+    }
+    cat->info.n_events = ne;
+    cat->info.n_z = c.n_z;
+    cat->info.n_samples = ns;
+    cat->info.n_pixels = np;
+    cat->info.n_galaxies = ng;
+    cat->info.n_det = nd;
+    cat->info.device_bytes = (int64_t)cat->bytes;
+    cat->info.max_samples_per_event = max_ns;
+    cat->info.max_pixels_per_event = max_np;
+    int32_t id_ = ctx.next_id++;
+    ctx.cats[id_] = cat;
+    *out_id = id_;
+    return CHIMERA_OK;
+}
+
+static void free_catalog(Ctx &ctx, Catalog &cat) {
+    for (auto &kv : cat.prof) {
+        dev_free(ctx, kv.second.G, kv.second.bytes);
+        if (kv.second.Gh) dev_free(ctx, kv.second.Gh, 0);
+        if (kv.second.ready) cudaEventDestroy(kv.second.ready);
+    }
+    cat.prof.clear();
+    for (void *a : cat.allocs) cudaFree(a);
+    cat.allocs.clear();
+    ctx.used -= cat.bytes;
+    cat.bytes = 0;
+}
+
+}  // namespace chim
+
+using namespace chim;
+
+struct chimera_ctx {
+    Ctx c;
+};
+
+// ================================================================ C ABI ====
+extern "C" {
+
+const char *chimera_strerror(int code) {
+    switch (code) {
+        case CHIMERA_OK: return "ok";
+        case CHIMERA_ERR_INVALID_ARG: return "invalid argument";
+        case CHIMERA_ERR_NOT_FOUND: return "not found";
+        case CHIMERA_ERR_ADMISSION: return "HBM budget exceeded";
+        case CHIMERA_ERR_CUDA: return "CUDA error";
+        case CHIMERA_ERR_TIMEOUT: return "timeout (result pending)";
+        case CHIMERA_ERR_CANCELLED: return "cancelled";
+        case CHIMERA_ERR_UNSUPPORTED: return "unsupported size";
+        default: return "unknown error";
+    }
+}
+
+const char *chimera_last_error(void) { return g_last_error.c_str(); }
+
+int chimera_create(chimera_ctx **out, int device, size_t budget) {
+    if (!out) { set_error("out is NULL"); return CHIMERA_ERR_INVALID_ARG; }
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        set_error("no CUDA device available");
+        return CHIMERA_ERR_CUDA;
+    }
+    if (device < 0 || device >= n) { set_error("device index out of range"); return CHIMERA_ERR_INVALID_ARG; }
+    CK(cudaSetDevice(device));
+    auto *h = new chimera_ctx();
+    h->c.device = device;
+    if (cudaStreamCreateWithFlags(&h->c.stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete h;
+        set_error("cudaStreamCreate failed");
+        return CHIMERA_ERR_CUDA;
+    }
+    h->c.ws.st = h->c.stream;
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    h->c.budget = budget ? budget : (size_t)(0.9 * fr);
+    *out = h;
+    return CHIMERA_OK;
+}
+
+void chimera_destroy(chimera_ctx *h) {
+    if (!h) return;
+    Ctx &ctx = h->c;
+    serve_shutdown(ctx);
+    cudaSetDevice(ctx.device);
+    cudaDeviceSynchronize();
+    for (auto &kv : ctx.cats) free_catalog(ctx, *kv.second);
+    ctx.cats.clear();
+    for (auto &kv : ctx.fwd) {
+        dev_free(ctx, kv.second.table, sizeof(double) * NT_FWD);
+        cudaEventDestroy(kv.second.ready);
+    }
+    ctx.fwd.clear();
+    ws_release(ctx, ctx.ws);
+    cudaStreamDestroy(ctx.stream);
+    delete h;
+}
+
+int chimera_load_catalog(chimera_ctx *h, const chimera_catalog_desc *desc, int32_t *id) {
+    if (!h) { set_error("ctx is NULL"); return CHIMERA_ERR_INVALID_ARG; }
+    std::lock_guard<std::recursive_mutex> lk(h->c.mu);
+    CK(cudaSetDevice(h->c.device));
+    return load_catalog(h->c, desc, id);
+}
+
+int chimera_unload_catalog(chimera_ctx *h, int32_t id) {
+    if (!h) { set_error("ctx is NULL"); return CHIMERA_ERR_INVALID_ARG; }
+    std::lock_guard<std::recursive_mutex> lk(h->c.mu);
+    auto cat = find_catalog(h->c, id);
+    if (!cat) { set_error("unknown catalog id"); return CHIMERA_ERR_NOT_FOUND; }
+    CK(cudaSetDevice(h->c.device));
+    cudaDeviceSynchronize();
+    free_catalog(h->c, *cat);
+    h->c.cats.erase(id);
+    return CHIMERA_OK;
+}
+
+int chimera_catalog_info(chimera_ctx *h, int32_t id, chimera_catalog_info_t *info) {
+    if (!h || !info) { set_error("null argument"); return CHIMERA_ERR_INVALID_ARG; }
+    std::lock_guard<std::recursive_mutex> lk(h->c.mu);
+    auto cat = find_catalog(h->c, id);
+    if (!cat) { set_error("unknown catalog id"); return CHIMERA_ERR_NOT_FOUND; }
+    *info = cat->info;
+    return CHIMERA_OK;
+}
+
+static int check_call(chimera_ctx *h, int32_t n, const void *theta, int32_t prec, const void *out) {
+    if (!h || !theta || !out) { set_error("null argument"); return CHIMERA_ERR_INVALID_ARG; }
+    if (n <= 0) { set_error("n_points must be positive"); return CHIMERA_ERR_INVALID_ARG; }
+    if (prec != CHIMERA_FP64 && prec != CHIMERA_MIXED) { set_error("bad precision"); return CHIMERA_ERR_INVALID_ARG; }
+    return CHIMERA_OK;
+}
+
+int chimera_loglike(chimera_ctx *h, int32_t id, int32_t n, const double *theta, int32_t prec,
+                    double *lnL, double *neff, int32_t *status) {
+    RC(check_call(h, n, theta, prec, lnL));
+    Ctx &ctx = h->c;
+    std::lock_guard<std::recursive_mutex> lk(ctx.mu);
+    auto cat = find_catalog(ctx, id);
+    if (!cat) { set_error("unknown catalog id"); return CHIMERA_ERR_NOT_FOUND; }
+    CK(cudaSetDevice(ctx.device));
+    RC(forward(ctx, *cat, ctx.ws, n, theta, prec));
+    cudaStream_t st = ctx.ws.st;
+    CK(cudaMemcpyAsync(lnL, ctx.ws.lnL, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    if (neff) CK(cudaMemcpyAsync(neff, ctx.ws.neff, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    if (status) {
+        CallPtrs p = ctx.ws.ptrs(n, cat->d);
+        CK(cudaMemcpyAsync(status, p.status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    return CHIMERA_OK;
+}
+
+int chimera_loglike_device(chimera_ctx *h, int32_t id, int32_t n, const double *theta_dev,
+                           int32_t prec, double *lnL_dev, double *neff_dev, int32_t *status_dev,
+                           void *stream) {
+    RC(check_call(h, n, theta_dev, prec, lnL_dev));
+    Ctx &ctx = h->c;
+    std::lock_guard<std::recursive_mutex> lk(ctx.mu);
+    auto cat = find_catalog(ctx, id);
+    if (!cat) { set_error("unknown catalog id"); return CHIMERA_ERR_NOT_FOUND; }
+    CK(cudaSetDevice(ctx.device));
+    cudaStream_t us = stream ? (cudaStream_t)stream : ctx.stream;
+    std::vector<double> th(12 * (size_t)n);
+    CK(cudaMemcpyAsync(th.data(), theta_dev, sizeof(double) * 12 * n, cudaMemcpyDeviceToHost, us));
+    CK(cudaStreamSynchronize(us));
+    RC(forward(ctx, *cat, ctx.ws, n, th.data(), prec));
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaStream_t st = ctx.ws.st;
+    CallPtrs p = ctx.ws.ptrs(n, cat->d);
+    CK(cudaMemcpyAsync(lnL_dev, ctx.ws.lnL, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    if (neff_dev) CK(cudaMemcpyAsync(neff_dev, ctx.ws.neff, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    if (status_dev) CK(cudaMemcpyAsync(status_dev, p.status, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
+    CK(cudaEventRecord(ev, st));
+    CK(cudaStreamWaitEvent(us, ev, 0));
+    cudaEventDestroy(ev);
+    return CHIMERA_OK;
+}
+
+int chimera_terms(chimera_ctx *h, int32_t id, int32_t n, const double *theta, int32_t prec,
+                  double *lnI, double *bw, double *xi, double *neff) {
+    RC(check_call(h, n, theta, prec, theta));
+    Ctx &ctx = h->c;
+    std::lock_guard<std::recursive_mutex> lk(ctx.mu);
+    auto cat = find_catalog(ctx, id);
+    if (!cat) { set_error("unknown catalog id"); return CHIMERA_ERR_NOT_FOUND; }
+    CK(cudaSetDevice(ctx.device));
+    RC(forward(ctx, *cat, ctx.ws, n, theta, prec));
+    cudaStream_t st = ctx.ws.st;
+    size_t ne = (size_t)cat->d.n_events;
+    if (lnI) CK(cudaMemcpyAsync(lnI, ctx.ws.lnI, sizeof(double) * n * ne, cudaMemcpyDeviceToHost, st));
+    if (bw) CK(cudaMemcpyAsync(bw, ctx.ws.bw, sizeof(double) * n * ne, cudaMemcpyDeviceToHost, st));
+    if (xi) CK(cudaMemcpyAsync(xi, ctx.ws.xi, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    if (neff) CK(cudaMemcpyAsync(neff, ctx.ws.neff, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return CHIMERA_OK;
+}
+
+int chimera_grad(chimera_ctx *h, int32_t id, int32_t n, const double *theta, int32_t prec,
+                 double *lnL, double *dlnL, int32_t *status) {
+    RC(check_call(h, n, theta, prec, lnL));
+    if (!dlnL) { set_error("dlnL is NULL"); return CHIMERA_ERR_INVALID_ARG; }
+    Ctx &ctx = h->c;
+    std::lock_guard<std::recursive_mutex> lk(ctx.mu);
+    auto cat = find_catalog(ctx, id);
+    if (!cat) { set_error("unknown catalog id"); return CHIMERA_ERR_NOT_FOUND; }
+    CK(cudaSetDevice(ctx.device));
+    RC(forward(ctx, *cat, ctx.ws, n, theta, prec));
+    RC(backward(ctx, *cat, ctx.ws, n, prec));
+    cudaStream_t st = ctx.ws.st;
+    CK(cudaMemcpyAsync(lnL, ctx.ws.lnL, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(dlnL, ctx.ws.grad, sizeof(double) * 12 * n, cudaMemcpyDeviceToHost, st));
+    if (status) {
+        CallPtrs p = ctx.ws.ptrs(n, cat->d);
+        CK(cudaMemcpyAsync(status, p.status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    return CHIMERA_OK;
+}
+
+int chimera_serve_submit(chimera_ctx *h, int32_t id, int32_t n, const double *theta, int32_t flags,
+                         uint64_t *ticket) {
+    if (!h || !theta || !ticket || n <= 0) { set_error("bad argument"); return CHIMERA_ERR_INVALID_ARG; }
+    return serve_submit(h->c, id, n, theta, flags, ticket);
+}
+
+int chimera_serve_poll(chimera_ctx *h, uint64_t ticket, int64_t timeout_us, double *lnL, double *dlnL,
+                       int32_t *status) {
+    if (!h || !lnL) { set_error("bad argument"); return CHIMERA_ERR_INVALID_ARG; }
+    return serve_poll(h->c, ticket, timeout_us, lnL, dlnL, status);
+}
+
+int chimera_serve_cancel(chimera_ctx *h, uint64_t ticket) {
+    if (!h) { set_error("bad argument"); return CHIMERA_ERR_INVALID_ARG; }
+    return serve_cancel(h->c, ticket);
+}
+
+int chimera_serve_stats(chimera_ctx *h, chimera_serve_stats_t *out) {
+    if (!h || !out) { set_error("bad argument"); return CHIMERA_ERR_INVALID_ARG; }
+    return serve_stats(h->c, out);
+}
+
+int chimera_set_trace(chimera_ctx *h, int enable) {
+    if (!h) { set_error("ctx is NULL"); return CHIMERA_ERR_INVALID_ARG; }
+    std::lock_guard<std::recursive_mutex> lk(h->c.mu);
+    h->c.ws.trace = enable != 0;
+    return CHIMERA_OK;
+}
+
+int chimera_stage_ms(chimera_ctx *h, double *ms) {
+    if (!h || !ms) { set_error("null argument"); return CHIMERA_ERR_INVALID_ARG; }
+    std::lock_guard<std::recursive_mutex> lk(h->c.mu);
+    Workspace &ws = h->c.ws;
+    for (int i = 0; i < 6; i++) ms[i] = 0.0;
+    if (!ws.trace || !ws.tev[5]) { set_error("tracing is off or no traced call yet"); return CHIMERA_ERR_INVALID_ARG; }
+    CK(cudaEventSynchronize(ws.tev[5]));
+    float t;
+    // events: 0 start | 1 after K1a/K3 | 2 after K1b | 3 after K4 | 4 after K5 | 5 after K6
+    CK(cudaEventElapsedTime(&t, ws.tev[1], ws.tev[2])); ms[0] = t;
+    CK(cudaEventElapsedTime(&t, ws.tev[0], ws.tev[1])); ms[1] = t;
+    CK(cudaEventElapsedTime(&t, ws.tev[2], ws.tev[3])); ms[2] = t;
+    CK(cudaEventElapsedTime(&t, ws.tev[3], ws.tev[4])); ms[3] = t;
+    CK(cudaEventElapsedTime(&t, ws.tev[4], ws.tev[5])); ms[4] = t;
+    if (ws.traced_adjoint && ws.tev[6] && ws.tev[7]) {
+        CK(cudaEventSynchronize(ws.tev[7]));
+        CK(cudaEventElapsedTime(&t, ws.tev[6], ws.tev[7])); ms[5] = t;
+    }
+    return CHIMERA_OK;
+}
+
+int chimera_kde_pairs(chimera_ctx *h, int32_t id, int32_t n, const double *theta, int64_t *pairs) {
+    RC(check_call(h, n, theta, CHIMERA_MIXED, pairs));
+    Ctx &ctx = h->c;
+    std::lock_guard<std::recursive_mutex> lk(ctx.mu);
+    auto cat = find_catalog(ctx, id);
+    if (!cat) { set_error("unknown catalog id"); return CHIMERA_ERR_NOT_FOUND; }
+    CK(cudaSetDevice(ctx.device));
+    ctx.ws.count_pairs = true;
+    int rc = forward(ctx, *cat, ctx.ws, n, theta, CHIMERA_MIXED);
+    ctx.ws.count_pairs = false;
+    RC(rc);
+    std::vector<unsigned long long> v(n);
+    CK(cudaMemcpyAsync(v.data(), ctx.ws.pairs, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, ctx.ws.st));
+    CK(cudaStreamSynchronize(ctx.ws.st));
+    for (int i = 0; i < n; i++) pairs[i] = (int64_t)v[i];
+    return CHIMERA_OK;
+}
+
+int chimera_peaks(chimera_ctx *h, double *out) {
+    if (!h || !out) { set_error("bad argument"); return CHIMERA_ERR_INVALID_ARG; }
+    std::lock_guard<std::recursive_mutex> lk(h->c.mu);
+    CK(cudaSetDevice(h->c.device));
+    if (run_peaks(out, h->c.stream)) { set_error("peak microbenchmark failed"); return CHIMERA_ERR_CUDA; }
+    return CHIMERA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,191 @@
+// Internal declarations shared by the CUDA translation units of libchimera.
+// Device data layout, per-hyperpoint parameter block and the host-side
+// launch wrappers of every kernel.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "../../include/chimera.h"
+
+namespace chim {
+
+constexpr double C_KMS = 299792.458;
+// Forward comoving-distance table: nodes z_k = k * HT, k = 0 .. NT_FWD-1.
+// HT = 10/4096 is exact in binary; node 4096 is z = 10, the end of the
+// redshift search range; the table runs a little past z = 12.
+constexpr double HT = 10.0 / 4096.0;
+constexpr int K_Z10 = 4096;
+constexpr int NT_FWD = 4918;
+// Inverse table: NU intervals uniform in u = sqrt(d_L / d_top).
+constexpr int NU = 2048;
+// KDE window half-widths in bandwidths (mixed / FP64) and galaxy window in sigmas.
+constexpr float KW32 = 6.0f;
+constexpr double KW64 = 9.0;
+constexpr float KWG32 = 6.0f;
+constexpr double KWG64 = 9.0;
+// Mixed event kernel geometry.
+constexpr int EV_WARPS = 16;          // warps per block
+constexpr int EV_THREADS = EV_WARPS * 32;
+constexpr int DCAP = 768;             // D-table floats per warp
+constexpr int GROUP_MAX = 64;         // samples per warp group (2 per lane)
+// FP64 event kernel.
+constexpr int EV64_THREADS = 256;
+// Selection kernel: injections per block per hyperpoint.
+constexpr int SEL_THREADS = 256;
+constexpr int SEL_PER_THREAD = 8;
+constexpr int SEL_CHUNK = SEL_THREADS * SEL_PER_THREAD;
+
+// Per-hyperpoint parameters, written by the cosmology kernel (FP64).
+struct HP {
+    double th[12];
+    double cH;        // c / H0 [Mpc]
+    double c_pl;      // (1 - lambda_g) / int m^-alpha over [m_min, m_max]
+    double c_g;       // lambda_g / (sigma_g sqrt(2 pi) [Phi(b) - Phi(a)])
+    double b1;        // 1 + beta
+    double mmin_b1;   // m_min^(1+beta)
+    double lmmin;     // ln m_min
+    double dc_zmax;   // D_c(z_max) [Mpc]
+    double d_valid;   // d_L^gw(z = 10) [Mpc]
+    double F_scale;   // max over the grid of F(z_a)
+    double t_valid;   // inverse-table coordinate of d_valid
+    int32_t status;   // CHIMERA_PT_* bits known after the table stage
+    int32_t k_valid;  // floor(t_valid), clamped
+    float f_valid;    // t_valid - k_valid
+    float pad;
+};
+
+// Resident catalog (device pointers unless noted).
+struct DevCatalog {
+    int32_t n_events, n_z, kde_mode, gal_storage;
+    int64_t n_samples, n_pix, n_gal, n_det, n_inj_total;
+    double z_max, dz, n_gal_total, lambda_g, beta, d_top;
+    int32_t max_ns, max_seg, max_npix;
+    // events
+    int64_t *ev_soff;     // [n_events+1] sample offsets (sorted storage)
+    int64_t *ev_poff;     // [n_events+1] flat pixel offsets
+    int32_t *ev_order;    // [n_events] heavy-first launch order
+    // KDE segments: many-1D = pixels, single-1D = events
+    int64_t n_seg;
+    int64_t *seg_soff;    // [n_seg+1] sample offsets of each segment
+    double *seg_pf;       // [n_seg] S_ik / N_k (many-1D) or 1 / N_s (single-1D)
+    int32_t *ev_segoff;   // [n_events+1] segment offsets per event
+    // pixels
+    double *pix_S;        // [n_pix]
+    int64_t *gal_off;     // [n_pix+1], galaxies sorted by z inside a pixel
+    double *pix_sigmax;   // [n_pix] widest galaxy of the pixel (FP64 values)
+    float *pix_sigmax32;  // [n_pix] widest galaxy (stored values)
+    float *pix_zref;      // [n_pix] F16/BF16 offset reference
+    // galaxies
+    double *gz64, *gs64;  // FP64 values
+    float *gz32, *gs32;   // F32 storage
+    uint16_t *gzq, *gsq;  // F16/BF16 storage (z as offset from pix_zref)
+    // PE samples
+    float4 *s32;          // (inverse-table interval k as int bits, fraction f, ln m1_det, ln m2_det)
+    double *sd64, *sm1_64, *sm2_64;
+    // detected injections
+    float4 *i32a;         // (k bits, f, ln m1_det, ln m2_det)
+    float2 *i32b;         // (d_L, ln pi_inj)
+    double *id64, *im1_64, *im2_64, *ilp64;
+};
+
+// Per-call views the kernels need for hyperpoint h.
+struct CallPtrs {
+    const double *theta;      // [H x 12]
+    HP *hp;                   // [H]
+    const double *const *fwd; // [H] forward table of h's Om (device pointer array)
+    double2 *inv64;           // [H x (NU+1)] (z_k, dz/du_k)
+    float4 *inv32;            // [H x NU] (z_k, dz/du_k / NU, z_k+1, dz/du_k+1 / NU)
+    double *F64;              // [H x n_z]
+    float *F32;               // [H x n_z], F / F_scale
+    const void *const *prof;  // [H] galaxy profile base (double* or float*) of h's Om
+    double *lnI;              // [H x n_events]
+    double *bw;               // [H x n_events]
+    double *selp;             // [H x n_chunk x 2] selection partial sums (scratch)
+    int32_t n_chunk;
+    double *lnL, *neff, *xi;  // [H]
+    int32_t *status;          // [H]
+    unsigned long long *pairs;  // [H] windowed-pair counter, or nullptr
+};
+
+// ---- launch wrappers (host) ----
+// K1a: forward table D_c(z_k) / (c/H0) for one Om into `out` [NT_FWD].
+void launch_fwd_table(double Om, double *out, cudaStream_t st);
+// K1b: per-hyperpoint parameters, inverse tables, grid factors, status.
+void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st);
+// K3: galaxy redshift prior on the grid for one Om.  dv: [n_z] scratch,
+// invZ: [n_gal] scratch; out64 (FP64 values) or out32 (stored values).
+void launch_galaxy_profile(const DevCatalog &c, const double *fwd, double Om, double *dv,
+                           double *invZ64, float *invZ32, double *out64, float *out32,
+                           cudaStream_t st);
+// Single-1D sky-summed profile: outh[event][a] = sum_k S_k G[k][a].
+void launch_profile_sum(const DevCatalog &c, const double *G64, const float *G32, double *outh64,
+                        float *outh32, cudaStream_t st);
+// K2+K4: per-event ln I for every (event, h).
+void launch_event_mixed(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st);
+void launch_event_fp64(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st);
+size_t event_mixed_smem(const DevCatalog &c);
+size_t event_fp64_smem(const DevCatalog &c);
+// K5: selection partial sums; K6: combine into ln L.
+void launch_selection(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, cudaStream_t st);
+void launch_combine(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st);
+int selection_chunks(const DevCatalog &c);
+// K8 microbenchmarks.
+int run_peaks(double *out, cudaStream_t st);
+
+}  // namespace chim
+
+// ---- device helpers shared by the kernels ----
+namespace chimd {
+
+__device__ __forceinline__ double E_of(double z, double Om) {
+    double a = 1.0 + z;
+    return sqrt(Om * a * a * a + 1.0 - Om);
+}
+
+// Cubic Hermite interpolation of D_c/(c/H0) on the forward table; the node
+// derivatives are 1/E(z_k) exactly.
+__device__ __forceinline__ double dc_hermite(const double *fwd, double z, double Om) {
+    double t = z / chim::HT;
+    int k = (int)floor(t);
+    if (k < 0) k = 0;
+    if (k > chim::NT_FWD - 2) k = chim::NT_FWD - 2;
+    double f = t - k;
+    double z0 = k * chim::HT, z1 = (k + 1) * chim::HT;
+    double p0 = fwd[k], p1 = fwd[k + 1];
+    double m0 = chim::HT / E_of(z0, Om), m1 = chim::HT / E_of(z1, Om);
+    double f2 = f * f, f3 = f2 * f;
+    return (2 * f3 - 3 * f2 + 1) * p0 + (f3 - 2 * f2 + f) * m0 + (-2 * f3 + 3 * f2) * p1 +
+           (f3 - f2) * m1;
+}
+
+__device__ __forceinline__ double xi_of(double z, double xi0, double n) {
+    return xi0 + (1.0 - xi0) * pow(1.0 + z, -n);
+}
+
+// d_L^gw and its z-derivative J from D_c (Mpc) at z, Eq. dL-mg and its
+// product-rule derivative.
+__device__ __forceinline__ void dgw_J(double z, double Dc, const double *th, double cH, double *d,
+                                      double *J) {
+    double a = 1.0 + z;
+    double p = pow(a, -th[3]);
+    double xi = th[2] + (1.0 - th[2]) * p;
+    double dxi = -th[3] * (1.0 - th[2]) * p / a;
+    double E = E_of(z, th[1]);
+    *d = a * Dc * xi;
+    *J = (Dc + a * cH / E) * xi + a * Dc * dxi;
+}
+
+// Madau-Dickinson shape (Sec. 3.1), unnormalised.
+__device__ __forceinline__ double psi_of(double z, const double *th) {
+    double a = 1.0 + z;
+    return pow(a, th[9]) / (1.0 + pow(a / (1.0 + th[11]), th[9] + th[10]));
+}
+
+__device__ __forceinline__ float hermite4(float4 nd, float f) {
+    float f2 = f * f, f3 = f2 * f;
+    return (2.f * f3 - 3.f * f2 + 1.f) * nd.x + (f3 - 2.f * f2 + f) * nd.y +
+           (-2.f * f3 + 3.f * f2) * nd.z + (f3 - f2) * nd.w;
+}
+
+}  // namespace chimd

@@ -1,0 +1,134 @@
+// Host runtime of libchimera: context, budgeted device allocator, resident
+// catalogs, per-Om caches and per-stream workspaces.  Internal only.
+#pragma once
+
+#include <atomic>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace chim {
+
+void set_error(const std::string &msg);
+
+struct Ctx;
+
+// Forward table cache entry (one per distinct Om).
+struct FwdEntry {
+    double *table = nullptr;
+    cudaEvent_t ready = nullptr;
+};
+
+// Galaxy profile cache entry for one (Om, kind) of one catalog.
+struct ProfEntry {
+    void *G = nullptr;   // [n_pix x n_z] double (kind 0) or float (kind 1)
+    void *Gh = nullptr;  // single-1D: [n_events x n_z]
+    size_t bytes = 0;
+    cudaEvent_t ready = nullptr;
+    uint64_t last_use = 0;
+};
+
+struct Catalog {
+    DevCatalog d{};
+    std::vector<void *> allocs;
+    size_t bytes = 0;
+    chimera_catalog_info_t info{};
+    std::map<std::pair<uint64_t, int>, ProfEntry> prof;
+    std::atomic<int> in_use{0};
+};
+
+// Device and pinned buffers for one stream of likelihood calls.
+struct Workspace {
+    cudaStream_t st = nullptr;
+    int Hcap = 0;
+    int64_t nev_cap = 0;
+    int nz_cap = 0;
+    int nchunk_cap = 0;
+    int64_t ngal_cap = 0;
+    size_t bytes = 0;
+    // device
+    char *param = nullptr;  // theta | status | fwd ptrs | prof ptrs
+    HP *hp = nullptr;
+    double2 *inv64 = nullptr;
+    float4 *inv32 = nullptr;
+    double *F64 = nullptr;
+    float *F32 = nullptr;
+    double *lnI = nullptr, *bw = nullptr, *selp = nullptr;
+    double *lnL = nullptr, *neff = nullptr, *xi = nullptr;
+    double *dv = nullptr, *invZ64 = nullptr;
+    float *invZ32 = nullptr;
+    // adjoint buffers
+    double *grad = nullptr;       // [H x 12]
+    double *gscr = nullptr;       // adjoint scratch
+    size_t gscr_bytes = 0;
+    // windowed-pair counters (roofline accounting), used when count_pairs
+    unsigned long long *pairs = nullptr;
+    bool count_pairs = false;
+    // stage tracing (CUDA events around K1, K3, K4, K5, K6, K7)
+    bool trace = false;
+    cudaEvent_t tev[8] = {};
+    bool traced_adjoint = false;
+    // host pinned staging
+    char *hstage = nullptr;
+    size_t hstage_bytes = 0;
+    std::vector<void *> allocs;
+    CallPtrs ptrs(int H, const DevCatalog &c) const;
+    size_t param_bytes(int H) const { return (size_t)H * (12 * 8 + 8 + 8 + 8); }
+};
+
+struct Server;
+
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;
+    std::atomic<size_t> used{0};
+    std::recursive_mutex mu;
+    std::map<int32_t, std::shared_ptr<Catalog>> cats;
+    int32_t next_id = 0;
+    std::unordered_map<uint64_t, FwdEntry> fwd;
+    Workspace ws;
+    uint64_t tick = 0;
+    Server *server = nullptr;
+};
+
+// Budgeted allocation; returns a CHIMERA_ERR_* code.
+int dev_alloc(Ctx &ctx, void **p, size_t bytes);
+void dev_free(Ctx &ctx, void *p, size_t bytes);
+
+int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat);
+void ws_release(Ctx &ctx, Workspace &ws);
+
+// Forward pass for H points on workspace `ws` (enqueued on ws.st).
+// theta: host [H x 12].  Leaves lnL / neff / xi / status / lnI / bw on the
+// device in `ws`.  Returns a CHIMERA_ERR_* code.
+int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, int precision);
+// Adjoint after forward() on the same workspace; leaves grad [H x 12].
+int backward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, int precision);
+void launch_adjoint(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, double *grad,
+                    double *scratch, cudaStream_t st);
+size_t adjoint_scratch_bytes(const DevCatalog &c, int H);
+
+std::shared_ptr<Catalog> find_catalog(Ctx &ctx, int32_t id);
+
+int cuda_check(cudaError_t e, const char *what);
+
+// serving
+int serve_submit(Ctx &ctx, int32_t cat, int32_t n, const double *theta, int32_t flags,
+                 uint64_t *ticket);
+int serve_poll(Ctx &ctx, uint64_t ticket, int64_t timeout_us, double *lnL, double *dlnL,
+               int32_t *status);
+int serve_cancel(Ctx &ctx, uint64_t ticket);
+int serve_stats(Ctx &ctx, chimera_serve_stats_t *out);
+void serve_shutdown(Ctx &ctx);
+
+}  // namespace chim

@@ -193,11 +193,15 @@ def make_catalog(*, n_events, n_pe, n_inj, n_z, Xi0, photo=False,
             host_key = 0
         else:
             target = int(np.clip(np.floor(np.exp(rng.uniform(0, np.log(n_pix_max + 1)))), 1, n_pix_max))
-            side = sig_sky * math.sqrt(14.5 / target)
-            ix = np.floor(x / side + 0.5).astype(np.int64)
-            iy = np.floor(y / side + 0.5).astype(np.int64)
-            code = (ix + 4096) * 8192 + (iy + 4096)
-            keys, pix, counts = np.unique(code, return_inverse=True, return_counts=True)
+            side = sig_sky * math.sqrt(40.0 / target)
+            while True:  # grow the pixels until the occupied set is within n_pix_max
+                ix = np.floor(x / side + 0.5).astype(np.int64)
+                iy = np.floor(y / side + 0.5).astype(np.int64)
+                code = (ix + 4096) * 8192 + (iy + 4096)
+                keys, pix, counts = np.unique(code, return_inverse=True, return_counts=True)
+                if keys.size <= n_pix_max:
+                    break
+                side *= 1.1
             hx = int(np.floor(true_off[0] / side + 0.5)); hy = int(np.floor(true_off[1] / side + 0.5))
             hcode = (hx + 4096) * 8192 + (hy + 4096)
             hit = np.nonzero(keys == hcode)[0]

@@ -35,7 +35,7 @@ UNIT = "evals/s"
 WORKLOAD = "O5-like catalog: 300 events x 5000 PE, 1-64 pixels, lognormal galaxies (median 2e3), n_z=1000, 2e6 injections, many-1D KDE, 16 hyperpoints per launch"
 SM_COUNT = 148
 FP32_LANES = 128
-OPS_PER_PAIR = 2  # one FMUL (Gaussian recurrence) + one FFMA (accumulate)
+OPS_PER_PAIR = 1  # one FFMA per (sample, grid point): Horner step in exp(2 u ds)
 
 
 def dist_setup():
@@ -222,6 +222,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--profile", action="store_true",
+                    help="run W warm-up launches and one more launch of the timed step, then exit (for ncu)")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -242,7 +244,7 @@ def main():
     H, NE = theta.shape[0], cat["n_events"]
     ctx = pkg.Context(local)
     cid = ctx.load(cat)
-    peaks = pkg.chimera_peaks(ctx.h)
+    peaks = None if args.profile else pkg.chimera_peaks(ctx.h)
 
     th_dev = torch.tensor(theta, device=dev, dtype=torch.float64)
     out = torch.empty(H, device=dev, dtype=torch.float64)
@@ -254,6 +256,12 @@ def main():
     def step():
         pkg.chimera_loglike_device(ctx.h, cid, th_dev, pkg.MIXED, out, neff, st, stream)
 
+    if args.profile:
+        for _ in range(args.warmup + 1):
+            step()
+        torch.cuda.synchronize()
+        ctx.close()
+        return
     pkg.chimera_set_trace(ctx.h, True)
     for _ in range(args.warmup):
         step()
@@ -312,7 +320,7 @@ def main():
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_pairs / 1e9, "unit": "Gpair/s",
             "frac": achieved / peak_pairs, "traffic": traffic_from_profiles(),
             "kernel": "k_event_mixed", "pairs_per_launch": pairs, "kernel_ms": kern,
-            "peak_basis": "148 SMs x 128 FP32 lanes x %.0f MHz / 2 ops per pair (derived)" % clock_mhz,
+            "peak_basis": "148 SMs x 128 FP32 lanes x %.0f MHz x 1 FFMA per pair (derived)" % clock_mhz,
             "measured_pair_peak": peaks["pair_per_s"] / 1e9,
             "frac_of_measured": achieved / peaks["pair_per_s"]}
     mean_stage = {k: sum(s[k] for s in stage) / len(stage) for k in stage[0]}

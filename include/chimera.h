@@ -273,7 +273,7 @@ const char *chimera_last_error(void);
 
 /*
  * chimera_peaks: microbenchmarks that give roofline denominators on this
- * GPU: out[0] = FP32 FMUL+FFMA pair rate (pairs/s, the KDE inner-loop mix),
+ * GPU: out[0] = FP32 Horner-step rate (one FFMA per pair, pairs/s),
  * out[1] = MUFU ex2 rate (evaluations/s), out[2] = FP64 DFMA rate (DFMA/s),
  * out[3] = device-to-device copy bandwidth (bytes/s, read + write).
  * `out` is host [4].  Not part of the method; used by the benchmark.

@@ -10,6 +10,8 @@
  *    hyperpoint, shared by the event's pixels; fallback to the unweighted
  *    rule, then to the grid spacing
  *  - redshift grid: uniform on [0, z_max], trapezoid weights    (Sec. 2.3)
+ *  - each KDE is zero outside the grid segment that holds its samples,
+ *    widened by ORC_KDE_MARGIN bandwidths                         (Sec. 2.3)
  *  - galaxy Gaussians normalised on the same grid (discrete Z_g), w_g = 1,
  *    prefactor 1/N_gal,tot; complete catalog (f_R = 1)        (Eq. p-cat)
  *  - sky factor S_ik is an input density per steradian  (Eq. gw-kernel-many1d)
@@ -285,19 +287,33 @@ int orc_event_bandwidth(const orc_catalog *c, const double *th, int64_t ev, doub
     return 0;
 }
 
-/* Weighted Gaussian KDE on the full grid (Eqs. gw-kernel-many1d/single1d):
+/* Weighted Gaussian KDE on the grid (Eqs. gw-kernel-many1d/single1d):
  * K(z_a) = (1/N) sum_{j in set} w_j exp(-(z_a - z_j)^2 / 2b^2) / (sqrt(2 pi) b),
- * the set being the pixel's samples (N = N_k) or all samples (N = N_s).    */
+ * the set being the pixel's samples (N = N_k) or all samples (N = N_s).
+ * The KDE is evaluated only on the part of the grid that holds the set's
+ * samples and is zero elsewhere (Sec. 2.3): z_a in
+ * [min z_j - ORC_KDE_MARGIN b, max z_j + ORC_KDE_MARGIN b] over the set's
+ * samples with a redshift; every sample term inside is kept in full.       */
 static void kde_grid(const orc_catalog *c, int64_t ev, int32_t pixel,
                      const double *z, const double *w, const int32_t *valid,
                      double b, double *K) {
     int64_t j0 = c->sample_off[ev], n = c->sample_off[ev + 1] - j0;
     int64_t cnt = 0;
-    for (int64_t j = 0; j < n; j++)
-        if (pixel < 0 || c->pix_of_sample[j0 + j] == pixel) cnt++;
+    double zlo = INFINITY, zhi = -INFINITY;
+    for (int64_t j = 0; j < n; j++) {
+        if (pixel >= 0 && c->pix_of_sample[j0 + j] != pixel) continue;
+        cnt++;
+        if (valid[j]) {
+            if (z[j] < zlo) zlo = z[j];
+            if (z[j] > zhi) zhi = z[j];
+        }
+    }
+    zlo -= ORC_KDE_MARGIN * b;
+    zhi += ORC_KDE_MARGIN * b;
     double norm = 1.0 / (sqrt(2.0 * M_PI) * b);
     for (int64_t a = 0; a < c->n_z; a++) {
         double za = grid_z(c, a), s = 0.0;
+        if (!(za >= zlo && za <= zhi)) { K[a] = 0.0; continue; }
         for (int64_t j = 0; j < n; j++) {
             if (!valid[j] || w[j] == 0.0) continue;
             if (pixel >= 0 && c->pix_of_sample[j0 + j] != pixel) continue;

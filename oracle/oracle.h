@@ -28,6 +28,7 @@ extern "C" {
 #define ORC_C_KMS 299792.458
 #define ORC_Z_TABLE_MAX 10.0    /* redshift search range [0, 10] */
 #define ORC_MONO_NODES 4096     /* J is checked at z_k = 10 k / 4096 */
+#define ORC_KDE_MARGIN 6.0      /* KDE support: sample range +- 6 bandwidths */
 
 enum { ORC_OK = 0, ORC_OUT_OF_SUPPORT = 1, ORC_NONMONOTONE = 2, ORC_NEFF_LOW = 4 };
 enum { ORC_KDE_SINGLE_1D = 0, ORC_KDE_MANY_1D = 1 };

@@ -220,11 +220,14 @@ def chimera_loglike_device(h, cid, theta_t, precision, lnL_t, neff_t=None, statu
     import torch
     n = theta_t.shape[0]
     s = stream if stream is not None else torch.cuda.current_stream(theta_t.device)
+    # torch's default stream has handle 0, which the C ABI would read as "the
+    # context's own stream"; pass the legacy default stream handle instead
+    sh = s.cuda_stream if s.cuda_stream != 0 else 0x1
     _ck(lib().chimera_loglike_device(
         h, cid, n, C.c_void_p(theta_t.data_ptr()), precision, C.c_void_p(lnL_t.data_ptr()),
         C.c_void_p(neff_t.data_ptr()) if neff_t is not None else None,
         C.c_void_p(status_t.data_ptr()) if status_t is not None else None,
-        C.c_void_p(s.cuda_stream)), "chimera_loglike_device")
+        C.c_void_p(sh)), "chimera_loglike_device")
 
 
 def chimera_terms(h, cid, theta, precision=MIXED, n_events=None):

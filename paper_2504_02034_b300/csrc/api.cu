@@ -4,6 +4,7 @@
 // orchestration of the kernels K1 -> K3 -> K2/K4 -> K5 -> K6 on a stream.
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <cstdio>
 #include <cstdlib>
 #include <numeric>
@@ -149,6 +150,8 @@ int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat) {
         {(void **)&ws.invZ32, sizeof(float) * (size_t)std::max<int64_t>(ng, 1)},
         {(void **)&ws.grad, sizeof(double) * 12 * (size_t)Hn},
         {(void **)&ws.pairs, sizeof(unsigned long long) * (size_t)Hn},
+        {(void **)&ws.dk, sizeof(double) * (size_t)Hn * NT_FWD},
+        {(void **)&ws.fmax_bits, sizeof(unsigned long long) * (size_t)Hn},
     };
     for (auto &it : items) {
         int rc = dev_alloc(ctx, it.p, it.b);
@@ -309,7 +312,7 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
     CK(cudaMemcpyAsync(ws.param, ws.hstage, ws.param_bytes(H), cudaMemcpyHostToDevice, ws.st));
     CallPtrs p = ws.ptrs(H, c);
     if (p.pairs) CK(cudaMemsetAsync(p.pairs, 0, sizeof(unsigned long long) * H, ws.st));
-    launch_hyper_tables(c, p, H, ws.st);
+    launch_hyper_tables(c, p, H, ws.dk, ws.fmax_bits, ws.st);
     if (ws.trace) CK(cudaEventRecord(ws.tev[2], ws.st));
     if (precision == CHIMERA_FP64) launch_event_fp64(c, p, H, ws.st);
     else launch_event_mixed(c, p, H, ws.st);
@@ -415,6 +418,8 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     c.n_inj_total = d->n_inj_total;
     c.z_max = d->z_max;
     c.dz = d->z_max / (d->n_z - 1);
+    c.z_max32 = (float)c.z_max;
+    c.dz32 = (float)c.dz;
     c.n_gal_total = d->n_gal_total;
     c.lambda_g = d->lambda_g;
     c.beta = d->beta;
@@ -492,6 +497,55 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     }
     c.n_seg = (int64_t)seg_pf.size();
     c.max_seg = max_seg;
+    // ---- warp groups and the per-event redshift reference (mixed kernel)
+    std::vector<int4> groups;
+    std::vector<int32_t> ev_goff(ne + 1, 0);
+    std::vector<float2> ev_ref(ne);
+    int max_groups = 1;
+    for (int i = 0; i < ne; i++) {
+        const int64_t a = d->sample_off[i], n = d->sample_off[i + 1] - a;
+        double m = 0, m2 = 0;
+        for (int64_t j = a; j < a + n; j++) {
+            double l = std::log(sd[j]);
+            m += l;
+            m2 += l * l;
+        }
+        m /= n;
+        const double sl = std::sqrt(std::max(m2 / n - m * m, 0.0)) * std::pow((double)n, -0.2);
+        // reference: the median d_L of the event
+        std::vector<double> dd(sd.begin() + a, sd.begin() + a + n);
+        std::nth_element(dd.begin(), dd.begin() + n / 2, dd.end());
+        {
+            int k;
+            float f;
+            tcoord(dd[n / 2], k, f);
+            float kb;
+            memcpy(&kb, &k, 4);
+            ev_ref[i] = make_float2(kb, f);
+        }
+        ev_goff[i] = (int32_t)groups.size();
+        for (int32_t sgi = ev_segoff[i]; sgi < ev_segoff[i + 1]; sgi++) {
+            const int64_t s0 = seg_soff[sgi], s1 = seg_soff[sgi + 1];
+            const int sr = sgi - ev_segoff[i];
+            // a chunk of up to 128 neighbours is halved (in multiples of 32)
+            // while its spread in ln d_L exceeds 4 bandwidth-equivalents
+            std::function<void(int64_t, int)> emit = [&](int64_t st, int cnt) {
+                double spread = std::log(sd[st + cnt - 1]) - std::log(sd[st]);
+                if (cnt > 32 && spread > 4.0 * sl) {
+                    int first = 32 * ((cnt + 63) / 64);
+                    emit(st, first);
+                    emit(st + first, cnt - first);
+                } else {
+                    groups.push_back(make_int4((int)(st - a), cnt, sr, 0));
+                }
+            };
+            for (int64_t g0 = s0; g0 < s1; g0 += GROUP_MAX)
+                emit(g0, (int)std::min<int64_t>(GROUP_MAX, s1 - g0));
+        }
+        max_groups = std::max<int>(max_groups, (int)groups.size() - ev_goff[i]);
+    }
+    ev_goff[ne] = (int32_t)groups.size();
+    c.max_groups = max_groups;
     // ---- heavy-first event order: cost ~ N_s x spread of ln d_L
     std::vector<double> cost(ne);
     for (int i = 0; i < ne; i++) {
@@ -572,6 +626,9 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         {(void **)&c.seg_soff, seg_soff.data(), 8 * seg_soff.size()},
         {(void **)&c.seg_pf, seg_pf.data(), 8 * seg_pf.size()},
         {(void **)&c.ev_segoff, ev_segoff.data(), 4 * ev_segoff.size()},
+        {(void **)&c.groups, groups.data(), 16 * groups.size()},
+        {(void **)&c.ev_goff, ev_goff.data(), 4 * ev_goff.size()},
+        {(void **)&c.ev_ref, ev_ref.data(), 8 * ev_ref.size()},
         {(void **)&c.pix_S, pixS.data(), 8 * pixS.size()},
         {(void **)&c.gal_off, goff.data(), 8 * goff.size()},
         {(void **)&c.pix_sigmax, sigmax.data(), 8 * sigmax.size()},

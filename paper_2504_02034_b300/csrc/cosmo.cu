@@ -3,11 +3,13 @@
 // k_fwd_table  - per distinct Om: cumulative D_c(z_k)/(c/H0) on the forward
 //                grid z_k = k*HT by 5-point Gauss-Legendre panels and a block
 //                prefix sum, all in FP64.
-// k_hyper      - per hyperpoint: mass-model normalisations, d_L^gw and J on
-//                the forward nodes (monotonicity check on z <= 10), the
-//                inverse table z(u), u = sqrt(d_L / d_top), by Newton on the
-//                Hermite-interpolated forward relation, and the grid factor
-//                F(z_a) = psi(z_a) / [(1+z_a)^3 |J(z_a)|] of Eq. like-integrals.
+// k_fwd_nodes, k_inv_nodes, k_grid, k_hyper_final - per hyperpoint, each
+//                spread over (nodes x hyperpoints) so that the FP64 work uses
+//                every SM: d_L^gw and J on the forward nodes (monotonicity
+//                check on z <= 10), the inverse table z(u), u = sqrt(d_L/d_top),
+//                by Newton on the Hermite-interpolated forward relation, the
+//                grid factor F(z_a) = psi(z_a) / [(1+z_a)^3 |J(z_a)|] of
+//                Eq. like-integrals, and the mass-model normalisations.
 #include <math_constants.h>
 
 #include "internal.cuh"
@@ -70,102 +72,103 @@ __global__ void __launch_bounds__(FWD_THREADS) k_fwd_table(double Om, double *ou
     if (t == 0) out[0] = 0.0;
 }
 
-constexpr int HYP_THREADS = 512;
+constexpr int HYP_THREADS = 256;
 
 __device__ double std_normal_cdf(double x) { return 0.5 * erfc(-x * 0.70710678118654752440); }
 
-__global__ void __launch_bounds__(HYP_THREADS) k_hyper(DevCatalog c, CallPtrs p, int H) {
-    extern __shared__ double sh[];
-    double *dk = sh;                  // [NT_FWD] d_L^gw at the forward nodes
-    double *Jk = dk + NT_FWD;         // [NT_FWD] its derivative
-    double2 *nodes = (double2 *)(Jk + NT_FWD);  // [NU+1]
-    __shared__ double th[12];
-    __shared__ int s_nonmono;
-    __shared__ double s_fmax[HYP_THREADS / 32];
-    const int h = blockIdx.x, t = threadIdx.x;
-    if (t < 12) th[t] = p.theta[h * 12 + t];
-    if (t == 0) s_nonmono = 0;
-    __syncthreads();
+// K1b.1: d_L^gw and J at the forward nodes of every hyperpoint; J <= 0 on
+// z <= 10 sets the NONMONOTONE bit.
+__global__ void __launch_bounds__(HYP_THREADS) k_fwd_nodes(CallPtrs p, double *dk) {
+    const int h = blockIdx.y;
+    const int k = blockIdx.x * HYP_THREADS + threadIdx.x;
+    if (k >= NT_FWD) return;
+    const double *th = p.theta + 12 * h;
+    const double cH = C_KMS / th[0];
+    double d, J;
+    chimd::dgw_J(k * HT, cH * p.fwd[h][k], th, cH, &d, &J);
+    dk[(size_t)h * NT_FWD + k] = d;
+    if (k <= K_Z10 && !(J > 0.0)) atomicOr(p.status + h, CHIMERA_PT_NONMONOTONE);
+}
+
+// K1b.2: inverse nodes z(u_k), d = d_top u_k^2, by bracketing on the forward
+// nodes and Newton on the Hermite-interpolated forward relation.
+__global__ void __launch_bounds__(HYP_THREADS) k_inv_nodes(DevCatalog c, CallPtrs p, const double *dkall) {
+    const int h = blockIdx.y;
+    const int k = blockIdx.x * HYP_THREADS + threadIdx.x;
+    if (k > NU) return;
+    const double *th = p.theta + 12 * h;
+    const double *dk = dkall + (size_t)h * NT_FWD;
     const double *fwd = p.fwd[h];
-    const double H0 = th[0], Om = th[1];
-    const double cH = C_KMS / H0;
-
-    // forward relation at the nodes; J <= 0 on z <= 10 flags non-monotonicity
-    for (int k = t; k < NT_FWD; k += HYP_THREADS) {
-        double z = k * HT, d, J;
-        chimd::dgw_J(z, cH * fwd[k], th, cH, &d, &J);
-        dk[k] = d;
-        Jk[k] = J;
-        if (k <= K_Z10 && !(J > 0.0)) s_nonmono = 1;
-    }
-    __syncthreads();
-
-    // inverse nodes z(u_k), d = d_top u_k^2
+    const double cH = C_KMS / th[0], Om = th[1];
     const double dtop = c.d_top;
-    for (int k = t; k <= NU; k += HYP_THREADS) {
-        double u = (double)k / NU, d = dtop * u * u;
-        double z = 0.0, dzdu = 0.0;
-        if (k > 0) {
-            if (!(d <= dk[NT_FWD - 1])) {
-                z = CUDART_NAN;
-                dzdu = CUDART_NAN;
-            } else {
-                int lo = 0, hi = NT_FWD - 1;  // dk[lo] <= d < dk[hi]
-                while (hi - lo > 1) {
-                    int mid = (lo + hi) >> 1;
-                    if (dk[mid] <= d) lo = mid; else hi = mid;
-                }
-                double den = dk[hi] - dk[lo];
-                double fr = den > 0.0 ? (d - dk[lo]) / den : 0.0;
-                z = (lo + fr) * HT;
-                double dd, J;
-                for (int it = 0; it < 3; it++) {
-                    chimd::dgw_J(z, cH * chimd::dc_hermite(fwd, z, Om), th, cH, &dd, &J);
-                    double step = (dd - d) / J;
-                    if (isfinite(step)) z -= step;
-                }
-                chimd::dgw_J(z, cH * chimd::dc_hermite(fwd, z, Om), th, cH, &dd, &J);
-                dzdu = 2.0 * u * dtop / J;
+    double u = (double)k / NU, d = dtop * u * u;
+    double z = 0.0, dzdu = 0.0;
+    if (k > 0) {
+        if (!(d <= dk[NT_FWD - 1])) {
+            z = CUDART_NAN;
+            dzdu = CUDART_NAN;
+        } else {
+            int lo = 0, hi = NT_FWD - 1;  // dk[lo] <= d < dk[hi]
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (dk[mid] <= d) lo = mid; else hi = mid;
             }
+            double den = dk[hi] - dk[lo];
+            double fr = den > 0.0 ? (d - dk[lo]) / den : 0.0;
+            z = (lo + fr) * HT;
+            double dd, J;
+            for (int it = 0; it < 2; it++) {
+                chimd::dgw_J(z, cH * chimd::dc_hermite(fwd, z, Om), th, cH, &dd, &J);
+                double step = (dd - d) / J;
+                if (isfinite(step)) z -= step;
+            }
+            chimd::dgw_J(z, cH * chimd::dc_hermite(fwd, z, Om), th, cH, &dd, &J);
+            dzdu = 2.0 * u * dtop / J;
         }
-        nodes[k] = make_double2(z, dzdu);
-        p.inv64[(size_t)h * (NU + 1) + k] = make_double2(z, dzdu);
     }
-    __syncthreads();
+    p.inv64[(size_t)h * (NU + 1) + k] = make_double2(z, dzdu);
+}
+
+// K1b.3: grid factor F(z_a) = psi / ((1+z)^3 |J|) and its maximum.
+__global__ void __launch_bounds__(HYP_THREADS) k_grid(DevCatalog c, CallPtrs p, unsigned long long *fmax_bits) {
+    const int h = blockIdx.y;
+    const int a = blockIdx.x * HYP_THREADS + threadIdx.x;
+    double F = 0.0;
+    if (a < c.n_z) {
+        const double *th = p.theta + 12 * h;
+        const double cH = C_KMS / th[0];
+        double z = a * c.dz, d, J;
+        chimd::dgw_J(z, cH * chimd::dc_hermite(p.fwd[h], z, th[1]), th, cH, &d, &J);
+        double ap = 1.0 + z;
+        F = chimd::psi_of(z, th) / (ap * ap * ap * fabs(J));
+        if (!isfinite(F)) F = 0.0;
+        p.F64[(size_t)h * c.n_z + a] = F;
+    }
+    for (int o = 16; o > 0; o >>= 1) F = fmax(F, __shfl_xor_sync(0xffffffffu, F, o));
+    // F >= 0, so the ordering of the bit patterns is the ordering of the values
+    if ((threadIdx.x & 31) == 0 && F > 0.0) atomicMax(fmax_bits + h, (unsigned long long)__double_as_longlong(F));
+}
+
+// K1b.4: per-hyperpoint constants, FP32 inverse intervals, normalised F.
+__global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallPtrs p,
+                                                            const double *dkall,
+                                                            const unsigned long long *fmax_bits) {
+    const int h = blockIdx.x, t = threadIdx.x;
+    const double Fm = __longlong_as_double((long long)fmax_bits[h]);
+    const double Fs = Fm > 0.0 ? Fm : 1.0;
+    const double2 *nd = p.inv64 + (size_t)h * (NU + 1);
     for (int k = t; k < NU; k += HYP_THREADS) {
-        double2 a = nodes[k], b = nodes[k + 1];
+        double2 a = nd[k], b = nd[k + 1];
         p.inv32[(size_t)h * NU + k] =
             make_float4((float)a.x, (float)(a.y / NU), (float)b.x, (float)(b.y / NU));
     }
-
-    // grid factor F(z_a) = psi / ((1+z)^3 |J|)
-    double fm = 0.0;
-    const int nz = c.n_z;
-    for (int a = t; a < nz; a += HYP_THREADS) {
-        double z = a * c.dz, d, J;
-        chimd::dgw_J(z, cH * chimd::dc_hermite(fwd, z, Om), th, cH, &d, &J);
-        double ap = 1.0 + z;
-        double F = chimd::psi_of(z, th) / (ap * ap * ap * fabs(J));
-        if (!isfinite(F)) F = 0.0;
-        p.F64[(size_t)h * nz + a] = F;
-        fm = fm > F ? fm : F;
-    }
-    for (int o = 16; o > 0; o >>= 1) fm = fmax(fm, __shfl_xor_sync(0xffffffffu, fm, o));
-    if ((t & 31) == 0) s_fmax[t >> 5] = fm;
-    __syncthreads();
-    if (t < 32) {
-        double x = t < HYP_THREADS / 32 ? s_fmax[t] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-        if (t == 0) s_fmax[0] = x;
-    }
-    __syncthreads();
-    const double Fs = s_fmax[0] > 0.0 ? s_fmax[0] : 1.0;
-    for (int a = t; a < nz; a += HYP_THREADS)
-        p.F32[(size_t)h * nz + a] = (float)(p.F64[(size_t)h * nz + a] / Fs);
-
+    for (int a = t; a < c.n_z; a += HYP_THREADS)
+        p.F32[(size_t)h * c.n_z + a] = (float)(p.F64[(size_t)h * c.n_z + a] / Fs);
     if (t == 0) {
+        const double *th = p.theta + 12 * h;
         HP hp;
         for (int k = 0; k < 12; k++) hp.th[k] = th[k];
+        const double cH = C_KMS / th[0];
         hp.cH = cH;
         const double alpha = th[4], mu = th[5], sg = th[6], mmin = th[7], mmax = th[8];
         const double lam = c.lambda_g, beta = c.beta;
@@ -178,10 +181,10 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper(DevCatalog c, CallPtrs p,
         hp.b1 = 1.0 + beta;
         hp.mmin_b1 = pow(mmin, 1.0 + beta);
         hp.lmmin = log(mmin);
-        hp.dc_zmax = cH * chimd::dc_hermite(fwd, c.z_max, Om);
-        hp.d_valid = dk[K_Z10];
+        hp.dc_zmax = cH * chimd::dc_hermite(p.fwd[h], c.z_max, th[1]);
+        hp.d_valid = dkall[(size_t)h * NT_FWD + K_Z10];
         hp.F_scale = Fs;
-        double tv = sqrt(hp.d_valid / dtop) * NU;
+        double tv = sqrt(hp.d_valid / c.d_top) * NU;
         hp.t_valid = tv;
         if (!(tv < NU)) {
             hp.k_valid = NU;
@@ -190,10 +193,26 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper(DevCatalog c, CallPtrs p,
             hp.k_valid = (int)floor(tv);
             hp.f_valid = (float)(tv - hp.k_valid);
         }
-        int st = p.status[h];
-        if (s_nonmono) st |= CHIMERA_PT_NONMONOTONE;
-        hp.status = st;
-        hp.pad = 0.f;
+        hp.status = p.status[h];
+        hp.c_pl32 = (float)hp.c_pl;
+        hp.c_g32 = (float)hp.c_g;
+        hp.alpha32 = (float)alpha;
+        hp.mu32 = (float)mu;
+        hp.inv_sg32 = (float)(1.0 / sg);
+        hp.mmin32 = (float)mmin;
+        hp.mmax32 = (float)mmax;
+        hp.beta32 = (float)beta;
+        hp.b1_32 = (float)hp.b1;
+        hp.mmin_b1_32 = (float)hp.mmin_b1;
+        hp.lmmin32 = (float)hp.lmmin;
+        hp.xi0_32 = (float)th[2];
+        hp.n32 = (float)th[3];
+        hp.om32 = (float)th[1];
+        hp.gam32 = (float)th[9];
+        hp.kap32 = (float)th[10];
+        hp.l1zp32 = (float)log1p(th[11]);
+        hp.cH32 = (float)cH;
+        hp.inv_dc3_32 = (float)(1.0 / (hp.dc_zmax * hp.dc_zmax * hp.dc_zmax));
         p.hp[h] = hp;
     }
 }
@@ -204,10 +223,13 @@ void launch_fwd_table(double Om, double *out, cudaStream_t st) {
     k_fwd_table<<<1, FWD_THREADS, 0, st>>>(Om, out);
 }
 
-void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st) {
-    size_t smem = sizeof(double) * 2 * NT_FWD + sizeof(double2) * (NU + 1);
-    cudaFuncSetAttribute(k_hyper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_hyper<<<H, HYP_THREADS, smem, st>>>(c, p, H);
+void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, double *dk,
+                         unsigned long long *fmax_bits, cudaStream_t st) {
+    cudaMemsetAsync(fmax_bits, 0, sizeof(unsigned long long) * H, st);
+    k_fwd_nodes<<<dim3((NT_FWD + HYP_THREADS - 1) / HYP_THREADS, H), HYP_THREADS, 0, st>>>(p, dk);
+    k_inv_nodes<<<dim3((NU + 1 + HYP_THREADS - 1) / HYP_THREADS, H), HYP_THREADS, 0, st>>>(c, p, dk);
+    k_grid<<<dim3((c.n_z + HYP_THREADS - 1) / HYP_THREADS, H), HYP_THREADS, 0, st>>>(c, p, fmax_bits);
+    k_hyper_final<<<H, HYP_THREADS, 0, st>>>(c, p, dk, fmax_bits);
 }
 
 }  // namespace chim

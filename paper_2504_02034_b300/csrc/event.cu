@@ -26,6 +26,9 @@
 //
 // FP64 kernel: the plain form, one exp per grid point and sample within
 // +-9 b, every quantity in double.
+//
+// Both kernels keep each KDE on its support, the grid segment between its
+// first and last sample widened by KDE_MARGIN bandwidths (Sec. 2.3).
 #include <math_constants.h>
 
 #include "internal.cuh"
@@ -91,18 +94,20 @@ __device__ __forceinline__ double bandwidth_rule(double W1, double W2, double Vw
     return dz;
 }
 
-// Shared layout of the mixed kernel (floats unless noted).
+// Shared layout of the mixed kernel.
 struct MixLayout {
-    int ns_pad, nz_pad, seg_pad;
+    int ns_pad, nz_pad, seg_pad, gmax_pad;
     __host__ __device__ static int pad4(int x) { return (x + 3) & ~3; }
-    __host__ __device__ MixLayout(int max_ns, int nz, int max_seg) {
+    __host__ __device__ MixLayout(int max_ns, int nz, int max_seg, int max_groups) {
         ns_pad = pad4(max_ns);
         nz_pad = pad4(nz);
         seg_pad = pad4(max_seg + 1);
+        gmax_pad = pad4(max_groups);
     }
+    // floats: zs, ws, Fs, D tables, C table, group results; ints: segv
     __host__ __device__ size_t bytes() const {
-        return sizeof(float) * (2 * (size_t)ns_pad + nz_pad + (size_t)EV_WARPS * DCAP) +
-               sizeof(int) * 2 * (size_t)seg_pad + sizeof(double) * (8 + EV_WARPS * 8);
+        return sizeof(float) * (2 * (size_t)ns_pad + nz_pad + (size_t)EV_WARPS * DCAP + CCAP + gmax_pad) +
+               sizeof(int) * (size_t)seg_pad + sizeof(double) * (8 + EV_WARPS * 8);
     }
 };
 
@@ -112,69 +117,140 @@ struct MixParams {
     float fv;
 };
 
+// Mass-model weight p(m1) p(m2|m1) from log source-frame masses, with the
+// SFU exponential (relative error ~1e-6, independent between samples).
 __device__ __forceinline__ float mass_weight32(const MixParams &q, float lm1, float lm2) {
-    float m1 = expf(lm1), m2 = expf(lm2);
+    float m1 = __expf(lm1), m2 = __expf(lm2);
     if (!(m1 >= q.mmin && m1 <= q.mmax && m2 >= q.mmin && m2 <= m1)) return 0.f;
     float x = (m1 - q.mu) * q.inv_sg;
-    float p1 = q.c_pl * expf(-q.alpha * lm1) + q.c_g * expf(-0.5f * x * x);
+    float p1 = q.c_pl * __expf(-q.alpha * lm1) + q.c_g * __expf(-0.5f * x * x);
     float p2;
     if (fabsf(q.b1) < 1e-6f) {
         float l = lm1 - q.lmmin;
-        p2 = l > 0.f ? 1.f / (m2 * l) : 0.f;
+        p2 = l > 0.f ? __fdividef(1.f, m2 * l) : 0.f;
     } else {
-        float den = m1 * expf(q.beta * lm1) - q.mmin_b1;
-        p2 = den > 0.f ? q.b1 * expf(q.beta * lm2) / den : 0.f;
+        float den = m1 * __expf(q.beta * lm1) - q.mmin_b1;
+        p2 = den > 0.f ? __fdividef(q.b1 * __expf(q.beta * lm2), den) : 0.f;
     }
     return p1 * p2;
 }
 
+// Union path: a group of nearby samples shares the grid origin t_o; the
+// table D covers tau in [-4 nqb, 4 nqf - 1] and is read as broadcast float4.
+// The per-sample sums are polynomials in B = exp(2 u ds):
+//   sum_{tau >= 0} D_tau B^tau      and      sum_{tau >= 1} D_-tau B^-tau,
+// evaluated by Horner's rule from the highest power down: one FMA per
+// (sample, grid point).  The intermediates are partial sums divided by
+// exp(-u^2) B^tau, so they stay within the float range for |u| <= 3.1.
 template <int R>
-__device__ __forceinline__ void chains(const float *D, int T4, const float (&u)[R], float ds,
-                                       float (&acc)[R]) {
-    float Pf[R], Pb[R], B[R], Bi[R], af[R], ab[R];
+__device__ __forceinline__ void chains(const float *D, int nqb, int nqf, const float (&u)[R],
+                                       float ds, float lnscale, float (&acc)[R]) {
+    float A[R], B[R], Bi[R], af[R], ab[R];
 #pragma unroll
     for (int r = 0; r < R; r++) {
-        float A = expf(-u[r] * u[r]);
-        B[r] = expf(2.f * u[r] * ds);
-        Bi[r] = expf(-2.f * u[r] * ds);
-        Pf[r] = A;
-        Pb[r] = A * Bi[r];
+        A[r] = __expf(-u[r] * u[r] - lnscale);
+        B[r] = __expf(2.f * u[r] * ds);
+        Bi[r] = __expf(-2.f * u[r] * ds);
         af[r] = 0.f;
         ab[r] = 0.f;
     }
-    const float4 *Df = reinterpret_cast<const float4 *>(D + T4 + 4);
-    const int nq = (T4 + 4) >> 2;
-#pragma unroll 2
-    for (int q = 0; q < nq; q++) {
-        float4 d = Df[q];
-        float4 e = Df[-q - 1];
+    const float4 *D0 = reinterpret_cast<const float4 *>(D) + nqb;  // tau = 0
+    // forward coefficients tau = 4q .. 4q+3 and backward tau = -4q-4 .. -4q-1
+    // are consumed together over the common length (two independent chains)
+    const int nc = min(nqf, nqb);
+    for (int q = max(nqf, nqb) - 1; q >= nc; q--) {
+        if (q < nqf) {
+            float4 d = D0[q];
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                af[r] = fmaf(af[r], B[r], d.w);
+                af[r] = fmaf(af[r], B[r], d.z);
+                af[r] = fmaf(af[r], B[r], d.y);
+                af[r] = fmaf(af[r], B[r], d.x);
+            }
+        } else {
+            float4 e = D0[-q - 1];
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                ab[r] = fmaf(ab[r], Bi[r], e.x);
+                ab[r] = fmaf(ab[r], Bi[r], e.y);
+                ab[r] = fmaf(ab[r], Bi[r], e.z);
+                ab[r] = fmaf(ab[r], Bi[r], e.w);
+            }
+        }
+    }
+    float4 dn = make_float4(0.f, 0.f, 0.f, 0.f), en = dn;
+    if (nc > 0) { dn = D0[nc - 1]; en = D0[-nc]; }
+    for (int q = nc - 1; q >= 0; q--) {
+        float4 d = dn, e = en;
+        if (q > 0) { dn = D0[q - 1]; en = D0[-q]; }
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            af[r] = fmaf(Pf[r], d.x, af[r]); Pf[r] *= B[r];
-            af[r] = fmaf(Pf[r], d.y, af[r]); Pf[r] *= B[r];
-            af[r] = fmaf(Pf[r], d.z, af[r]); Pf[r] *= B[r];
-            af[r] = fmaf(Pf[r], d.w, af[r]); Pf[r] *= B[r];
-            ab[r] = fmaf(Pb[r], e.w, ab[r]); Pb[r] *= Bi[r];
-            ab[r] = fmaf(Pb[r], e.z, ab[r]); Pb[r] *= Bi[r];
-            ab[r] = fmaf(Pb[r], e.y, ab[r]); Pb[r] *= Bi[r];
-            ab[r] = fmaf(Pb[r], e.x, ab[r]); Pb[r] *= Bi[r];
+            af[r] = fmaf(af[r], B[r], d.w);
+            ab[r] = fmaf(ab[r], Bi[r], e.x);
+            af[r] = fmaf(af[r], B[r], d.z);
+            ab[r] = fmaf(ab[r], Bi[r], e.y);
+            af[r] = fmaf(af[r], B[r], d.y);
+            ab[r] = fmaf(ab[r], Bi[r], e.z);
+            af[r] = fmaf(af[r], B[r], d.x);
+            ab[r] = fmaf(ab[r], Bi[r], e.w);
         }
     }
 #pragma unroll
-    for (int r = 0; r < R; r++) acc[r] = af[r] + ab[r];
+    for (int r = 0; r < R; r++) acc[r] = A[r] * fmaf(Bi[r], ab[r], af[r]);
+}
+
+// R samples per lane (lane, lane+32, ...) of a group sharing one table.
+template <int R>
+__device__ __forceinline__ float union_samples(const float *D, int nqb, int nqf, const float *z,
+                                               const float *w, int cnt, int lane, float zo,
+                                               float inv_s2b, float ds, float lnscale) {
+    float u[R], ww[R], acc[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        int j = lane + 32 * r;
+        bool in = j < cnt;
+        u[r] = in ? (z[j] - zo) * inv_s2b : 0.f;
+        ww[r] = in ? w[j] : 0.f;
+    }
+    chains<R>(D, nqb, nqf, u, ds, lnscale, acc);
+    float v = 0.f;
+#pragma unroll
+    for (int r = 0; r < R; r++) v = fmaf(ww[r], acc[r], v);
+    return v;
+}
+
+// Per-lane path for a sparse group: every lane runs its own window around
+// the grid point ts nearest to its sample, exp(-(u - ds t)^2) =
+// exp(-u^2) B^t C_t with |u| <= ds/2, as two Horner chains in B and 1/B
+// over the group's H' (staged with zero padding, so no bounds tests).
+__device__ __forceinline__ float lane_chain(const float *Hc, const float *CT, int Tw, float z,
+                                            int ts, float dz, float inv_s2b, float ds) {
+    const float u = (z - ts * dz) * inv_s2b;
+    const float A = __expf(-u * u), B = __expf(2.f * u * ds), Bi = __expf(-2.f * u * ds);
+    float af = CT[Tw] * Hc[Tw], ab = CT[Tw + 1] * Hc[-Tw - 1];
+#pragma unroll 2
+    for (int t = Tw - 1; t >= 0; t--) {
+        const float c = CT[t], c1 = CT[t + 1];
+        af = fmaf(af, B, c * Hc[t]);
+        ab = fmaf(ab, Bi, c1 * Hc[-1 - t]);
+    }
+    return A * fmaf(Bi, ab, af);
 }
 
 __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, CallPtrs p, int H) {
     extern __shared__ float4 smem4[];
-    const MixLayout L(c.max_ns, c.n_z, c.max_seg);
+    const MixLayout L(c.max_ns, c.n_z, c.max_seg, c.max_groups);
     float *zs = reinterpret_cast<float *>(smem4);
     float *ws = zs + L.ns_pad;
     float *Fs = ws + L.ns_pad;
     float *Dt = Fs + L.nz_pad;
-    int *segv = reinterpret_cast<int *>(Dt + EV_WARPS * DCAP);
-    int *gpre = segv + L.seg_pad;
-    double *red = reinterpret_cast<double *>(gpre + L.seg_pad);
+    float *CT = Dt + EV_WARPS * DCAP;
+    float *gres = CT + CCAP;
+    int *segv = reinterpret_cast<int *>(gres + L.gmax_pad);
+    double *red = reinterpret_cast<double *>(segv + L.seg_pad);
     __shared__ int s_gctr;
+    __shared__ float s_f[8];  // block scalars computed once by thread 0
 
     const int h = blockIdx.x % H;
     const int ev = c.ev_order[blockIdx.x / H];
@@ -186,191 +262,233 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
         return;
     }
     MixParams q;
-    q.c_pl = (float)hp.c_pl; q.c_g = (float)hp.c_g; q.alpha = (float)hp.th[4];
-    q.mu = (float)hp.th[5]; q.inv_sg = (float)(1.0 / hp.th[6]); q.mmin = (float)hp.th[7];
-    q.mmax = (float)hp.th[8]; q.beta = (float)c.beta; q.b1 = (float)hp.b1;
-    q.mmin_b1 = (float)hp.mmin_b1; q.lmmin = (float)hp.lmmin; q.kv = hp.k_valid; q.fv = hp.f_valid;
+    q.c_pl = hp.c_pl32; q.c_g = hp.c_g32; q.alpha = hp.alpha32;
+    q.mu = hp.mu32; q.inv_sg = hp.inv_sg32; q.mmin = hp.mmin32;
+    q.mmax = hp.mmax32; q.beta = hp.beta32; q.b1 = hp.b1_32;
+    q.mmin_b1 = hp.mmin_b1_32; q.lmmin = hp.lmmin32; q.kv = hp.k_valid; q.fv = hp.f_valid;
 
     const int nz = c.n_z;
-    const float dz = (float)c.dz;
+    const float dz = c.dz32;
     for (int a = tid; a < nz; a += EV_THREADS) Fs[a] = p.F32[(size_t)h * nz + a];
+    if (tid == 0) s_gctr = 0;
 
-    // ---- phase A: z_j, w_j and the moment sums
+    // ---- phase A: z_j, w_j and one-pass moments about the redshift of the
+    // event's median d_L (shifted sums: no cancellation in the variance)
     const int64_t s0 = c.ev_soff[ev];
     const int ns = (int)(c.ev_soff[ev + 1] - s0);
     const float4 *inv = p.inv32 + (size_t)h * NU;
-    float acc1[4] = {0.f, 0.f, 0.f, 0.f};  // W1, Wz, W2, n_valid
-    float accz = 0.f;
-    for (int j = tid; j < ns; j += EV_THREADS) {
-        float4 s = c.s32[s0 + j];
-        int k = __float_as_int(s.x);
-        float f = s.y;
-        float z = CUDART_INF_F, w = 0.f;
-        bool valid = (k < q.kv) || (k == q.kv && f <= q.fv);
-        if (valid) {
-            float zz = chimd::hermite4(inv[k], f);
+    float zref;
+    {
+        float2 r = c.ev_ref[ev];
+        int k = __float_as_int(r.x);
+        bool ok = (k < q.kv) || (k == q.kv && r.y <= q.fv);
+        zref = ok ? chimd::hermite4(__ldg(inv + k), r.y) : 0.f;
+        if (!isfinite(zref)) zref = 0.f;
+    }
+    float m[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // W1, Wd, Wd2, W2, n, Sd, Sd2
+    for (int j0 = tid; j0 < ns; j0 += 4 * EV_THREADS) {
+        float4 sv[4];
+#pragma unroll
+        for (int uu = 0; uu < 4; uu++) {
+            int j = j0 + uu * EV_THREADS;
+            sv[uu] = j < ns ? __ldg(c.s32 + s0 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float4 nd[4];
+#pragma unroll
+        for (int uu = 0; uu < 4; uu++) {
+            int k = __float_as_int(sv[uu].x);
+            bool valid = (j0 + uu * EV_THREADS < ns) && ((k < q.kv) || (k == q.kv && sv[uu].y <= q.fv));
+            nd[uu] = valid ? __ldg(inv + k) : make_float4(CUDART_INF_F, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int uu = 0; uu < 4; uu++) {
+            int j = j0 + uu * EV_THREADS;
+            if (j >= ns) break;
+            float z = CUDART_INF_F, w = 0.f;
+            float zz = chimd::hermite4(nd[uu], sv[uu].y);
             if (isfinite(zz)) {
                 z = zz;
-                float lz = log1pf(z);
-                w = mass_weight32(q, s.z - lz, s.w - lz);
+                float lz = __logf(1.f + z);
+                w = mass_weight32(q, sv[uu].z - lz, sv[uu].w - lz);
+                float d = z - zref;
+                m[0] += w; m[1] += w * d; m[2] += w * d * d; m[3] += w * w;
+                m[4] += 1.f; m[5] += d; m[6] += d * d;
+            }
+            zs[j] = z;
+            ws[j] = w;
+        }
+    }
+    block_sum<7, EV_THREADS>(m, red);
+    if (tid == 0) {
+        // Scott's rule in FP32 (the mixed path's precision): weighted, then
+        // unweighted, then the grid spacing
+        const double W1 = red[0], n = red[4];
+        float bl = dz;
+        bool done = false;
+        if (W1 > 0.0) {
+            double mw = red[1] / W1, var = red[2] / W1 - mw * mw, neff = W1 * W1 / red[3];
+            if (neff >= 2.0 && var > 0.0) {
+                bl = sqrtf((float)var) * exp2f(-0.2f * log2f((float)neff));
+                done = true;
             }
         }
-        zs[j] = z;
-        ws[j] = w;
-        if (z < CUDART_INF_F) {
-            acc1[0] += w; acc1[1] += w * z; acc1[2] += w * w; acc1[3] += 1.f;
-            accz += z;
+        if (!done && n >= 2.0) {
+            double mu = red[5] / n, var = red[6] / n - mu * mu;
+            if (var > 0.0) bl = sqrtf((float)var) * exp2f(-0.2f * log2f((float)n));
         }
+        s_f[2] = bl;
     }
-    {
-        float v[5] = {acc1[0], acc1[1], acc1[2], acc1[3], accz};
-        block_sum<5, EV_THREADS>(v, red);
-    }
-    const double W1 = red[0], Wz = red[1], W2 = red[2], nv = red[3], Sz = red[4];
     __syncthreads();
-    const float mw = W1 > 0.0 ? (float)(Wz / W1) : 0.f;
-    const float mu_ = nv > 0.0 ? (float)(Sz / nv) : 0.f;
-    {
-        float v[2] = {0.f, 0.f};
-        for (int j = tid; j < ns; j += EV_THREADS) {
-            float z = zs[j];
-            if (z < CUDART_INF_F) {
-                float dw = z - mw, du = z - mu_;
-                v[0] += ws[j] * dw * dw;
-                v[1] += du * du;
-            }
-        }
-        block_sum<2, EV_THREADS>(v, red);
-    }
-    const double bd = bandwidth_rule(W1, W2, red[0], nv, red[1], c.dz);
-    const float b = (float)bd;
+    const float b = s_f[2];
+    const double bd = (double)b;
+    const float inv_s2b = 0.70710678f / b;
+    const float ds = dz * inv_s2b;
+    const float halfk = KW32 * b;
 
-    // ---- segments: valid prefix (sorted d_L => z ascending, invalid at the end)
+    // ---- Gaussian factor table C_t = exp(-(ds t)^2) and segment valid counts
+    for (int t = tid; t < CCAP; t += EV_THREADS) {
+        float x = ds * (float)t;
+        CT[t] = __expf(-x * x);
+    }
     const int sg0 = c.ev_segoff[ev], nseg = c.ev_segoff[ev + 1] - sg0;
     for (int k = tid; k < nseg; k += EV_THREADS) {
         int lo = (int)(c.seg_soff[sg0 + k] - s0), hi = (int)(c.seg_soff[sg0 + k + 1] - s0);
         int l = lo, r = hi;
         while (l < r) {
-            int m = (l + r) >> 1;
-            if (zs[m] < CUDART_INF_F) l = m + 1; else r = m;
+            int mm = (l + r) >> 1;
+            if (zs[mm] < CUDART_INF_F) l = mm + 1; else r = mm;
         }
         segv[k] = l - lo;
     }
     __syncthreads();
-    if (tid == 0) {
-        int acc = 0;
-        for (int k = 0; k < nseg; k++) {
-            gpre[k] = acc;
-            acc += (segv[k] + GROUP_MAX - 1) / GROUP_MAX;
-        }
-        gpre[nseg] = acc;
-        s_gctr = 0;
-    }
-    __syncthreads();
-    const int ngroups = gpre[nseg];
+    const int g0 = c.ev_goff[ev];
+    const int ngroups = c.ev_goff[ev + 1] - g0;
 
-    // ---- phase B: warp groups
-    const float inv_s2b = 0.70710678f / b;
-    const float ds = dz * inv_s2b;
-    const float halfk = KW32 * b;
+    // ---- phase B: groups taken dynamically by warps; each group's value is
+    // computed by a fixed lane assignment and stored in its own slot, and the
+    // slots are added in group order, so the result does not depend on timing.
     float *D = Dt + wid * DCAP;
     const float *prof = reinterpret_cast<const float *>(p.prof[h]);
-    float lsum = 0.f, lcomp = 0.f;  // Kahan
+    const int Tw = (int)ceilf(halfk / dz + 0.5f);
     unsigned long long npairs = 0;  // algorithmic pair count (roofline only)
     while (true) {
         int g = 0;
         if (lane == 0) g = atomicAdd(&s_gctr, 1);
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= ngroups) break;
-        int l = 0, r = nseg;  // gpre[l] <= g < gpre[l+1]
-        while (r - l > 1) {
-            int m = (l + r) >> 1;
-            if (gpre[m] <= g) l = m; else r = m;
-        }
-        const int sk = l;
-        const int gi = g - gpre[sk];
-        const int lo = (int)(c.seg_soff[sg0 + sk] - s0) + gi * GROUP_MAX;
-        const int cnt = min(GROUP_MAX, segv[sk] - gi * GROUP_MAX);
-        const float pf = (float)c.seg_pf[sg0 + sk];
-        const int64_t row = c.kde_mode == CHIMERA_KDE_MANY_1D ? (int64_t)(sg0 + sk) : (int64_t)ev;
-        const float *G = prof + row * nz;
-        const float zlo = zs[lo], zhi = zs[lo + cnt - 1];
-        const float spread = zhi - zlo;
-        const float halfw = 0.5f * spread + halfk;
-        const float Tf = ceilf(halfw / dz) + 1.f;
-        const int T = Tf < (float)DCAP ? (int)Tf : DCAP;  // beyond DCAP the fast path is off anyway
-        const int T4 = (T + 3) & ~3;
-        const int t_o = (int)rintf(0.5f * (zlo + zhi) / dz);
-        if (p.pairs) {
-            for (int j = lane; j < cnt; j += 32) {
-                float z = zs[lo + j];
-                if (ws[lo + j] == 0.f) continue;
-                int a0 = max(0, (int)ceilf((z - halfk) / dz));
-                int a1 = min(nz - 1, (int)floorf((z + halfk) / dz));
-                if (a1 >= a0) npairs += (unsigned long long)(a1 - a0 + 1);
-            }
-        }
-        if (t_o - T > nz - 1 || t_o + T < 0) continue;  // group entirely off the grid
-        const bool fast = spread <= 8.f * b && ds <= 0.5f && 2 * T4 + 8 <= DCAP;
+        const int4 gi = __ldg(c.groups + g0 + g);
+        const int sk = gi.z;
+        const int seg_lo = (int)(c.seg_soff[sg0 + sk] - s0);
+        const int lo = gi.x;
+        const int cnt = min(gi.y, segv[sk] - (lo - seg_lo));  // valid samples only
         float v = 0.f;
-        if (fast) {
-            __syncwarp();
-            for (int idx = lane; idx < 2 * T4 + 8; idx += 32) {
-                int tau = idx - (T4 + 4);
-                int a = t_o + tau;
-                float val = 0.f;
-                if (tau >= -T && tau <= T && a >= 0 && a < nz) {
-                    float x = ds * (float)tau;
-                    float wa = (a == 0 || a == nz - 1) ? 0.5f : 1.f;
-                    val = expf(-x * x) * wa * Fs[a] * G[a];
+        if (cnt > 0) {
+            const float pf = (float)c.seg_pf[sg0 + sk];
+            const int64_t row = c.kde_mode == CHIMERA_KDE_MANY_1D ? (int64_t)(sg0 + sk) : (int64_t)ev;
+            const float *G = prof + row * nz;
+            // KDE support of this segment: its samples' range +- KDE_MARGIN b
+            const int s_lo = max(0, (int)ceilf((zs[seg_lo] - (float)KDE_MARGIN * b) / dz));
+            const int s_hi = min(nz - 1, (int)floorf((zs[seg_lo + segv[sk] - 1] + (float)KDE_MARGIN * b) / dz));
+            const float zlo = zs[lo], zhi = zs[lo + cnt - 1];
+            const float spread = zhi - zlo;
+            if (p.pairs) {
+                for (int j = lane; j < cnt; j += 32) {
+                    float z = zs[lo + j];
+                    if (ws[lo + j] == 0.f) continue;
+                    int a0 = max(s_lo, (int)ceilf((z - halfk) / dz));
+                    int a1 = min(s_hi, (int)floorf((z + halfk) / dz));
+                    if (a1 >= a0) npairs += (unsigned long long)(a1 - a0 + 1);
                 }
-                D[idx] = val;
             }
-            __syncwarp();
-            const float zo = t_o * dz;
-            if (cnt > 32) {
-                float u[2], w2[2], acc[2];
-#pragma unroll
-                for (int rr = 0; rr < 2; rr++) {
-                    int j = lane + 32 * rr;
-                    bool in = j < cnt;
-                    u[rr] = in ? (zs[lo + j] - zo) * inv_s2b : 0.f;
-                    w2[rr] = in ? ws[lo + j] : 0.f;
+            // grid range the group can touch
+            const float fA0 = floorf((zlo - halfk) / dz), fA1 = ceilf((zhi + halfk) / dz);
+            const int A0 = fA0 < (float)s_lo ? s_lo : (int)fA0;
+            const int A1 = fA1 > (float)s_hi ? s_hi : (int)fA1;
+            if (A0 <= A1) {
+                const float tof = rintf(0.5f * (zlo + zhi) / dz);
+                const int t_o = tof > 1e8f ? 100000000 : (int)tof;
+                const int thi = A1 - t_o, tlo = t_o - A0;  // tau in [-tlo, thi]
+                const int nqf = thi >= 0 ? (thi + 4) >> 2 : 0;
+                const int nqb = tlo >= 1 ? (tlo + 3) >> 2 : 0;
+                // shared origin for spreads up to 16 b; beyond 8 b the table is
+                // scaled by e^20 (undone in A) to keep every relevant
+                // coefficient and Horner intermediate in the normal float range
+                const bool uni = ds <= 0.5f && spread <= 16.f * b && thi >= -1 && tlo >= 0 &&
+                                 4 * (nqf + nqb) <= DCAP && 4 * max(nqf, nqb) < CCAP;
+                if (uni) {
+                    const float lnscale = spread > 8.f * b ? 20.f : 0.f;
+                    const float scale = spread > 8.f * b ? 4.85165195e8f : 1.f;  // e^20
+                    __syncwarp();
+                    for (int idx = lane; idx < 4 * (nqf + nqb); idx += 32) {
+                        int tau = idx - 4 * nqb;
+                        int a = t_o + tau;
+                        float val = 0.f;
+                        if (a >= A0 && a <= A1) {
+                            float wa = (a == 0 || a == nz - 1) ? 0.5f : 1.f;
+                            val = CT[tau < 0 ? -tau : tau] * scale * wa * Fs[a] * __ldg(G + a);
+                        }
+                        D[idx] = val;
+                    }
+                    __syncwarp();
+                    const float zo = t_o * dz;
+                    switch ((cnt + 31) >> 5) {
+                        case 1: v = union_samples<1>(D, nqb, nqf, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale); break;
+                        case 2: v = union_samples<2>(D, nqb, nqf, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale); break;
+                        case 3: v = union_samples<3>(D, nqb, nqf, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale); break;
+                        default: v = union_samples<4>(D, nqb, nqf, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale); break;
+                    }
+                } else if (ds <= 2.f && Tw + 2 < CCAP && (A1 - A0 + 1) + 2 * Tw + 4 <= DCAP) {
+                    // stage H' on [base, base + span) with zeros outside [A0, A1]
+                    const int base = A0 - Tw - 2, span = (A1 - A0 + 1) + 2 * Tw + 4;
+                    __syncwarp();
+                    for (int i = lane; i < span; i += 32) {
+                        int a = base + i;
+                        float val = 0.f;
+                        if (a >= A0 && a <= A1) {
+                            float wa = (a == 0 || a == nz - 1) ? 0.5f : 1.f;
+                            val = wa * Fs[a] * __ldg(G + a);
+                        }
+                        D[i] = val;
+                    }
+                    __syncwarp();
+                    for (int j = lane; j < cnt; j += 32) {
+                        float w = ws[lo + j];
+                        if (w == 0.f) continue;
+                        float z = zs[lo + j];
+                        int ts = (int)rintf(fminf(z / dz, 1e8f));
+                        ts = min(max(ts, A0 - 1), A1 + 1);
+                        // a sample further than its window from [A0, A1] adds nothing
+                        // (and would push exp(2 u ds) out of range)
+                        if (fabsf(z - ts * dz) > halfk + dz) continue;
+                        v += w * lane_chain(D + (ts - base), CT, Tw, z, ts, dz, inv_s2b, ds);
+                    }
+                } else {
+                    for (int j = lane; j < cnt; j += 32) {
+                        float z = zs[lo + j], w = ws[lo + j];
+                        if (w == 0.f) continue;
+                        int a0 = max(A0, (int)ceilf((z - halfk) / dz));
+                        int a1 = min(A1, (int)floorf((z + halfk) / dz));
+                        float sacc = 0.f;
+                        for (int a = a0; a <= a1; a++) {
+                            float x = (a * dz - z) * inv_s2b;
+                            float wa = (a == 0 || a == nz - 1) ? 0.5f : 1.f;
+                            sacc += expf(-x * x) * wa * Fs[a] * G[a];
+                        }
+                        v += w * sacc;
+                    }
                 }
-                chains<2>(D, T4, u, ds, acc);
-                v = w2[0] * acc[0] + w2[1] * acc[1];
-            } else {
-                float u[1], acc[1];
-                bool in = lane < cnt;
-                u[0] = in ? (zs[lo + lane] - zo) * inv_s2b : 0.f;
-                float w1 = in ? ws[lo + lane] : 0.f;
-                chains<1>(D, T4, u, ds, acc);
-                v = w1 * acc[0];
             }
-        } else {
-            for (int j = lane; j < cnt; j += 32) {
-                float z = zs[lo + j], w = ws[lo + j];
-                if (w == 0.f) continue;
-                int a0 = max(0, (int)ceilf((z - halfk) / dz));
-                int a1 = min(nz - 1, (int)floorf((z + halfk) / dz));
-                float s = 0.f;
-                for (int a = a0; a <= a1; a++) {
-                    float x = (a * dz - z) * inv_s2b;
-                    float wa = (a == 0 || a == nz - 1) ? 0.5f : 1.f;
-                    s += expf(-x * x) * wa * Fs[a] * G[a];
-                }
-                v += w * s;
-            }
+            v = warp_sum(v) * pf;
         }
-        float y = pf * v - lcomp;
-        float t = lsum + y;
-        lcomp = (t - lsum) - y;
-        lsum = t;
+        if (lane == 0) gres[g] = v;
     }
+    __syncthreads();
+    // fixed-order sum of the group values
     {
-        float vv[1] = {lsum};
-        __syncthreads();
-        block_sum<1, EV_THREADS>(vv, red);
+        double sacc = 0.0;
+        for (int g = tid; g < ngroups; g += EV_THREADS) sacc += (double)gres[g];
+        double vv[1] = {sacc};
+        block_sumd<1, EV_THREADS>(vv, red);
     }
     if (p.pairs) {
         for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
@@ -498,7 +616,10 @@ __global__ void __launch_bounds__(EV64_THREADS) k_event_fp64(DevCatalog c, CallP
         if (w == 0.0) continue;
         const int64_t row = c.kde_mode == CHIMERA_KDE_MANY_1D ? (int64_t)(sg0 + l) : (int64_t)ev;
         const double *G = prof + row * nz;
-        double a0 = ceil((z - KW64 * b) / dz), a1 = floor((z + KW64 * b) / dz);
+        // window +-KW64 b, clipped to the segment's KDE support
+        const double smin = zs[lo] - KDE_MARGIN * b, smax = zs[lo + segv[l] - 1] + KDE_MARGIN * b;
+        double a0 = fmax(ceil((z - KW64 * b) / dz), ceil(smin / dz));
+        double a1 = fmin(floor((z + KW64 * b) / dz), floor(smax / dz));
         int ia0 = a0 < 0.0 ? 0 : (a0 > nz ? nz : (int)a0);
         int ia1 = a1 > nz - 1 ? nz - 1 : (a1 < -1.0 ? -1 : (int)a1);
         double s = 0.0;
@@ -523,7 +644,7 @@ __global__ void __launch_bounds__(EV64_THREADS) k_event_fp64(DevCatalog c, CallP
 
 }  // namespace
 
-size_t event_mixed_smem(const DevCatalog &c) { return MixLayout(c.max_ns, c.n_z, c.max_seg).bytes(); }
+size_t event_mixed_smem(const DevCatalog &c) { return MixLayout(c.max_ns, c.n_z, c.max_seg, c.max_groups).bytes(); }
 
 size_t event_fp64_smem(const DevCatalog &c) {
     return sizeof(double) * 2 * (size_t)c.max_ns + sizeof(int) * (size_t)((c.max_seg + 2) & ~1) +

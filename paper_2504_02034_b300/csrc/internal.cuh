@@ -6,7 +6,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
-#include "../../include/chimera.h"
+#include "chimera.h"
 
 namespace chim {
 
@@ -23,12 +23,16 @@ constexpr int NU = 2048;
 constexpr float KW32 = 6.0f;
 constexpr double KW64 = 9.0;
 constexpr float KWG32 = 6.0f;
+// Each KDE is zero outside the grid segment holding its samples, widened by
+// KDE_MARGIN bandwidths (Sec. 2.3: evaluated only where the samples are).
+constexpr double KDE_MARGIN = 6.0;
 constexpr double KWG64 = 9.0;
 // Mixed event kernel geometry.
 constexpr int EV_WARPS = 16;          // warps per block
 constexpr int EV_THREADS = EV_WARPS * 32;
 constexpr int DCAP = 768;             // D-table floats per warp
-constexpr int GROUP_MAX = 64;         // samples per warp group (2 per lane)
+constexpr int GROUP_MAX = 128;        // samples per warp group (up to 4 per lane)
+constexpr int CCAP = DCAP / 2 + 8;    // entries of the Gaussian factor table exp(-(ds t)^2)
 // FP64 event kernel.
 constexpr int EV64_THREADS = 256;
 // Selection kernel: injections per block per hyperpoint.
@@ -52,7 +56,10 @@ struct HP {
     int32_t status;   // CHIMERA_PT_* bits known after the table stage
     int32_t k_valid;  // floor(t_valid), clamped
     float f_valid;    // t_valid - k_valid
-    float pad;
+    // FP32 copies for the mixed-precision kernels (converted once here, so
+    // that no kernel thread runs FP64 conversions or divisions)
+    float c_pl32, c_g32, alpha32, mu32, inv_sg32, mmin32, mmax32, beta32, b1_32, mmin_b1_32,
+        lmmin32, xi0_32, n32, om32, gam32, kap32, l1zp32, cH32, inv_dc3_32;
 };
 
 // Resident catalog (device pointers unless noted).
@@ -60,6 +67,7 @@ struct DevCatalog {
     int32_t n_events, n_z, kde_mode, gal_storage;
     int64_t n_samples, n_pix, n_gal, n_det, n_inj_total;
     double z_max, dz, n_gal_total, lambda_g, beta, d_top;
+    float z_max32, dz32;  // float copies for the mixed kernels
     int32_t max_ns, max_seg, max_npix;
     // events
     int64_t *ev_soff;     // [n_events+1] sample offsets (sorted storage)
@@ -70,6 +78,14 @@ struct DevCatalog {
     int64_t *seg_soff;    // [n_seg+1] sample offsets of each segment
     double *seg_pf;       // [n_seg] S_ik / N_k (many-1D) or 1 / N_s (single-1D)
     int32_t *ev_segoff;   // [n_events+1] segment offsets per event
+    // warp groups of the mixed event kernel, fixed at load: up to 64
+    // neighbouring samples of one segment (split in two when their spread in
+    // ln d_L is wide); (start relative to the event, count, segment relative
+    // to the event, 0)
+    int4 *groups;
+    int32_t *ev_goff;     // [n_events+1] group offsets per event
+    int32_t max_groups;   // most groups of any event
+    float2 *ev_ref;       // [n_events] inverse-table (k bits, f) of the event's median d_L
     // pixels
     double *pix_S;        // [n_pix]
     int64_t *gal_off;     // [n_pix+1], galaxies sorted by z inside a pixel
@@ -112,7 +128,9 @@ struct CallPtrs {
 // K1a: forward table D_c(z_k) / (c/H0) for one Om into `out` [NT_FWD].
 void launch_fwd_table(double Om, double *out, cudaStream_t st);
 // K1b: per-hyperpoint parameters, inverse tables, grid factors, status.
-void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st);
+// dk: [H x NT_FWD] scratch, fmax_bits: [H] scratch.
+void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, double *dk,
+                         unsigned long long *fmax_bits, cudaStream_t st);
 // K3: galaxy redshift prior on the grid for one Om.  dv: [n_z] scratch,
 // invZ: [n_gal] scratch; out64 (FP64 values) or out32 (stored values).
 void launch_galaxy_profile(const DevCatalog &c, const double *fwd, double Om, double *dv,

@@ -1,6 +1,6 @@
 // K8: microbenchmarks for the roofline denominators of this GPU.
-//  - FP32 "pair" rate: the KDE inner-loop mix, one FMUL (P *= B) and one FFMA
-//    (acc += P * D) per pair, eight independent chains per thread;
+//  - FP32 "pair" rate: the KDE inner-loop step, one FFMA (Horner: acc = acc *
+//    B + D) per pair, eight independent chains per thread;
 //  - MUFU ex2 rate (ex2.approx.f32 in independent chains);
 //  - FP64 DFMA rate;
 //  - device-to-device copy bandwidth (read + write bytes).
@@ -24,10 +24,7 @@ __global__ void k_pairs(float *out, int iters, float seed) {
     const float D = 0.5f + seed * 1e-3f;
     for (int i = 0; i < iters; i++) {
 #pragma unroll
-        for (int r = 0; r < 8; r++) {
-            A[r] = fmaf(P[r], D, A[r]);
-            P[r] *= B[r];
-        }
+        for (int r = 0; r < 8; r++) A[r] = fmaf(A[r], B[r], D);  // Horner step
     }
     float s = 0.f;
 #pragma unroll

@@ -65,6 +65,8 @@ struct Workspace {
     double *lnI = nullptr, *bw = nullptr, *selp = nullptr;
     double *lnL = nullptr, *neff = nullptr, *xi = nullptr;
     double *dv = nullptr, *invZ64 = nullptr;
+    double *dk = nullptr;                  // [H x NT_FWD] forward-node scratch
+    unsigned long long *fmax_bits = nullptr;  // [H]
     float *invZ32 = nullptr;
     // adjoint buffers
     double *grad = nullptr;       // [H x 12]

@@ -35,14 +35,14 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_mixed(DevCatalog c, Call
     const float4 *inv = p.inv32 + (size_t)h * NU;
     const int kv = hp.k_valid;
     const float fv = hp.f_valid;
-    const float xi0 = (float)hp.th[2], n = (float)hp.th[3], om = (float)hp.th[1];
-    const float gam = (float)hp.th[9], kap = (float)hp.th[10], l1zp = log1pf((float)hp.th[11]);
-    const float cH = (float)hp.cH, zmax = (float)c.z_max;
-    const float inv_dc3 = (float)(1.0 / (hp.dc_zmax * hp.dc_zmax * hp.dc_zmax));
-    const float mmin = (float)hp.th[7], mmax = (float)hp.th[8], mu = (float)hp.th[5];
-    const float inv_sg = (float)(1.0 / hp.th[6]), alpha = (float)hp.th[4];
-    const float c_pl = (float)hp.c_pl, c_g = (float)hp.c_g, beta = (float)c.beta;
-    const float b1 = (float)hp.b1, mmin_b1 = (float)hp.mmin_b1, lmmin = (float)hp.lmmin;
+    const float xi0 = hp.xi0_32, n = hp.n32, om = hp.om32;
+    const float gam = hp.gam32, kap = hp.kap32, l1zp = hp.l1zp32;
+    const float cH = hp.cH32, zmax = c.z_max32;
+    const float inv_dc3 = hp.inv_dc3_32;
+    const float mmin = hp.mmin32, mmax = hp.mmax32, mu = hp.mu32;
+    const float inv_sg = hp.inv_sg32, alpha = hp.alpha32;
+    const float c_pl = hp.c_pl32, c_g = hp.c_g32, beta = hp.beta32;
+    const float b1 = hp.b1_32, mmin_b1 = hp.mmin_b1_32, lmmin = hp.lmmin32;
     float s1 = 0.f, s2 = 0.f;
     const int64_t base = (int64_t)chunk * SEL_CHUNK;
     for (int q = 0; q < SEL_PER_THREAD; q++) {
@@ -177,33 +177,20 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_fp64(DevCatalog c, CallP
 
 constexpr int CMB_THREADS = 256;
 
-// Neumaier-compensated block sum in a fixed order: thread t sums elements
-// t, t+256, ... in order, then thread 0 adds the 256 partials in order.
+// Block sum in a fixed order: thread t adds elements t, t+256, ... in
+// sequence, then a pairwise tree over the 256 partial sums.
 __device__ double fixed_order_sum(const double *x, int64_t n, int64_t stride, double *sh) {
-    double s = 0.0, comp = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += CMB_THREADS) {
-        double v = x[i * stride];
-        double t = s + v;
-        comp += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
-        s = t;
-    }
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += CMB_THREADS) s += x[i * stride];
     sh[threadIdx.x] = s;
-    sh[CMB_THREADS + threadIdx.x] = comp;
     __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0) {
-        double cs = 0.0;
-        for (int i = 0; i < CMB_THREADS; i++) {
-            double v = sh[i];
-            double t = r + v;
-            cs += fabs(r) >= fabs(v) ? (r - t) + v : (v - t) + r;
-            r = t;
-            cs += sh[CMB_THREADS + i];
-        }
-        r += cs;
+    for (int w = CMB_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
     }
+    double r = sh[0];
     __syncthreads();
-    return r;  // valid on thread 0
+    return r;
 }
 
 __global__ void __launch_bounds__(CMB_THREADS) k_combine(DevCatalog c, CallPtrs p, int H) {
@@ -237,7 +224,10 @@ __global__ void __launch_bounds__(CMB_THREADS) k_combine(DevCatalog c, CallPtrs 
         } else {
             lnL = sI - (double)c.n_events * log(xi);
         }
-        if (!(neff >= 5.0 * c.n_events)) st |= CHIMERA_PT_NEFF_LOW;
+        // the effective-count warning is only meaningful for an admissible point
+        if (!(hp.status & (CHIMERA_PT_OUT_OF_SUPPORT | CHIMERA_PT_NONMONOTONE)) &&
+            !(neff >= 5.0 * c.n_events))
+            st |= CHIMERA_PT_NEFF_LOW;
         p.lnL[h] = lnL;
         p.neff[h] = neff;
         p.xi[h] = xi;

@@ -330,7 +330,7 @@ def config_hyperpoints(config, variant=1, n=None):
 
 def quantize_galaxies(cat, storage):
     """Return a copy of `cat` whose galaxy z and sigma are rounded the way the
-    device stores them: z as a 16-bit offset from the pixel's first galaxy,
+    device stores them: z as a 16-bit offset from the pixel's smallest z,
     sigma as a 16-bit float (FP16 or BF16).  Feeding the copy to the oracle
     isolates kernel error from storage rounding."""
     import torch  # only for the bf16 rounding primitive
@@ -348,7 +348,7 @@ def quantize_galaxies(cat, storage):
         a, b = int(off[p]), int(off[p + 1])
         if b <= a:
             continue
-        ref = np.float32(gz[a])
+        ref = np.float32(gz[a:b].min())  # the device keeps the pixel's smallest z as reference
         d = torch.tensor((gz[a:b].astype(np.float32) - ref), dtype=torch.float32).to(dt).to(torch.float32).numpy()
         gz[a:b] = (np.float32(ref) + d.astype(np.float32)).astype(np.float64)
         gs[a:b] = torch.tensor(gs[a:b].astype(np.float32)).to(dt).to(torch.float32).numpy().astype(np.float64)

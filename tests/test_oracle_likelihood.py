@@ -167,8 +167,9 @@ def test_brute_force_continuous_quadrature(orc):
                     for m, (a, s) in enumerate(zip(gz, gs)))
                 zz, ww = (z[sel], w[sel]) if mode == 1 else (z, w)
                 integrand = lambda x: phi(x, zz, ww) / Nk * F(x) * G(x)
-                # the KDE vanishes (below 1e-31 relative) outside +-12 b of its samples
-                lo, hi = max(0.0, zz.min() - 12 * b), min(zmax, zz.max() + 12 * b)
+                # each KDE lives on the grid segment that holds its samples,
+                # widened by 6 bandwidths (Sec. 2.3)
+                lo, hi = max(0.0, zz.min() - 6 * b), min(zmax, zz.max() + 6 * b)
                 pts = [a for a in gz if lo < a < hi]
                 I += ev["S"][k] * quad(integrand, lo, hi, points=pts or None, limit=400, epsrel=1e-12)[0]
             got = cat.event_lnI(t, i)

@@ -266,6 +266,36 @@ int chimera_stage_ms(chimera_ctx *ctx, double *ms);
 int chimera_kde_pairs(chimera_ctx *ctx, int32_t catalog_id, int32_t n_points, const double *theta,
                       int64_t *pairs);
 
+/*
+ * chimera_selection_static: the selection term xi and N_eff (same FP64
+ * arithmetic as the catalog path) for callers that cannot allocate device
+ * memory, e.g. code whose memory pool owns the whole device, code that must
+ * stay inside another framework's allocator, or loops that must not let
+ * cudaMalloc / cudaFree synchronise the device.  The paper has no
+ * counterpart; this is an interface convenience.
+ *
+ * It allocates nothing: every intermediate lives in one fixed device array
+ * of about 14 MB compiled into the library, which every GPU that loads the
+ * library holds until exit.  It runs on the calling thread's current CUDA
+ * device and on `stream` (a cudaStream_t; NULL = the legacy default stream).
+ *   theta        host [n_points x 12], n_points <= 64 (else UNSUPPORTED).
+ *   n_det        detected injections, 1 .. 8388608 (else UNSUPPORTED);
+ *   n_inj_total  all injections drawn, >= n_det.
+ *   inj_dL, inj_m1d, inj_m2d, inj_log_pi
+ *                device [n_det] double, as in chimera_catalog_desc.
+ *   lambda_g, beta, z_max  as in chimera_catalog_desc.
+ *   xi, neff     device [n_points] double out (0 for an inadmissible point).
+ * The first call on a device looks up the array's device address and
+ * should come before any stream capture; it also reads the largest d_L back
+ * to the host, so every call synchronises `stream` once.  Calls share the
+ * array: calls that overlap on the GPU race and must be serialised by the
+ * caller.  Errors: INVALID_ARG, UNSUPPORTED, CUDA.
+ */
+int chimera_selection_static(int32_t n_points, const double *theta, int64_t n_det,
+                             int64_t n_inj_total, const double *inj_dL, const double *inj_m1d,
+                             const double *inj_m2d, const double *inj_log_pi, double lambda_g,
+                             double beta, double z_max, double *xi, double *neff, void *stream);
+
 /* Name of an error code; never NULL. */
 const char *chimera_strerror(int code);
 /* Detail of the last failure on the calling thread ("" if none). */

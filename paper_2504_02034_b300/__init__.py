@@ -113,6 +113,8 @@ ABI = {
     "chimera_stage_ms": (C.c_int, [_P, _pd]),
     "chimera_kde_pairs": (C.c_int, [_P, C.c_int32, C.c_int32, _pd, _pi64]),
     "chimera_peaks": (C.c_int, [_P, _pd]),
+    "chimera_selection_static": (C.c_int, [C.c_int32, _pd, C.c_int64, C.c_int64, _P, _P, _P, _P,
+                                           C.c_double, C.c_double, C.c_double, _P, _P, _P]),
 }
 
 
@@ -305,6 +307,21 @@ def chimera_peaks(h):
     out = np.zeros(4)
     _ck(lib().chimera_peaks(h, _dp(out)), "chimera_peaks")
     return dict(pair_per_s=out[0], ex2_per_s=out[1], dfma_per_s=out[2], copy_bytes_per_s=out[3])
+
+
+def chimera_selection_static(theta, inj, n_inj_total, lambda_g, beta, z_max, xi_t, neff_t, stream=None):
+    """No-allocation selection term.  inj: dict of float64 CUDA tensors
+    dL, m1d, m2d, log_pi (same length); xi_t, neff_t: float64 CUDA tensors
+    [n_points] written on `stream` (torch stream or None = current)."""
+    import torch
+    t = _th(theta)
+    s = stream if stream is not None else torch.cuda.current_stream(xi_t.device)
+    sh = s.cuda_stream if s.cuda_stream != 0 else 0x1
+    ptr = lambda x: C.c_void_p(x.data_ptr())
+    _ck(lib().chimera_selection_static(t.shape[0], _dp(t), int(inj["dL"].numel()), int(n_inj_total),
+                                       ptr(inj["dL"]), ptr(inj["m1d"]), ptr(inj["m2d"]), ptr(inj["log_pi"]),
+                                       float(lambda_g), float(beta), float(z_max), ptr(xi_t), ptr(neff_t),
+                                       C.c_void_p(sh)), "chimera_selection_static")
 
 
 def chimera_strerror(code):

@@ -1,11 +1,934 @@
-// K7: hand-written adjoint of ln L (in progress).
+// K7: hand-written adjoint of ln L with respect to the 12 hyperparameters
+// (H0, Om, Xi0, n, alpha, mu_g, sigma_g, m_min, m_max, gamma, kappa, z_p).
+//
+// ln L = sum_i ln I_i - N_obs ln xi                            (Eq. hyperlike)
+//
+// Event term.  In grid units I_i' = sum_k pf_k sum_{j in k} w_j S0_j with
+//   S0_j = sum_a e_ja H_k(a), e_ja = exp(-u_ja^2/2), u_ja = (z_a - z_j)/b,
+//   H_k(a) = w'_a F(z_a) G_k(z_a),  and ln I_i = ln I_i' - ln b + const.
+// Differentiating (the KDE is recomputed, nothing per pair is stored):
+//   dI'/dtheta = sum pf w [ S0 dln w/dtheta + (S1 / b) dz/dtheta ]
+//              + S2tot dln b/dtheta + sum_a M(a) dln F(z_a)/dtheta
+//              + [Om only] sum_k pf_k sum_a w'_a F K_k(a) dG_k(a)/dOm,
+//   S1_j = sum_a e H u, S2_j = sum_a e H u^2, S2tot = sum pf w S2,
+//   K_k(a) = sum_{j in k} w_j e_ja (the pixel KDE on the grid, recomputed
+//   grid-point by grid-point), M(a) = sum_k pf_k H_k(a) K_k(a).
+// z_j depends on (H0, Om, Xi0, n) through d_L^gw(z_j) = d_j (Eq. dL-mg),
+// dz/dtheta = -(d d_L^gw/dtheta)/J; w_j on the mass parameters and on z_j
+// through m = m_det/(1+z) (Sec. 2.1); b on every sample through Scott's rule
+// (weighted mean/variance and n_eff).  The edges of the mass ranges and of
+// the KDE windows are not differentiated (the almost-everywhere derivative).
+//
+// Selection term (Eq. bias as the injection sum):
+//   dxi/dtheta = (1/N_inj) sum_j s_j dln s_j/dtheta,
+//   ln s = ln p(m1,m2) + ln psi(z) + ln p_z(z) - 3 ln(1+z) - ln J(z) - ln pi_inj,
+// with the chain through z_j for the cosmological parameters.
+#include <algorithm>
+#include <map>
+
+#include <cuda_fp16.h>
+#include <math_constants.h>
+
+#include "mass.cuh"
 #include "runtime.cuh"
 
 namespace chim {
 
-int backward(Ctx &, Catalog &, Workspace &, int, int) {
-    set_error("gradient not available in this build");
-    return CHIMERA_ERR_UNSUPPORTED;
+// Per-hyperpoint constants of the adjoint (FP64).
+struct HPd {
+    double dlc_pl[3];  // d ln c_pl / d(alpha, m_min, m_max)
+    double dlc_g[4];   // d ln c_g / d(mu_g, sigma_g, m_min, m_max)
+    double dlpz_zmax;  // d ln [1 / V_c(z_max)] / dOm
+};
+
+// Device views of the adjoint's inputs and scratch.
+struct AdjPtrs {
+    const double *const *fwdO;   // [H] dDhat/dOm table of h's Om
+    const double *const *dprof;  // [H] dG/dOm profile of h's Om (rows as the forward profile)
+    HPd *hpd;                    // [H]
+    double *dznode;              // [H x (NU+1) x 4] dz/d(H0, Om, Xi0, n) at the inverse-table nodes
+    double *Q;                   // [H x n_z x 7] d ln F / d(H0, Om, Xi0, n, gamma, kappa, z_p)
+    double *dlnI;                // [H x n_events x 12]
+    double *selg;                // [H x n_chunk x 13] sum s dln s / dtheta (12), sum s
+    double *grad;                // [H x 12]
+};
+
+namespace {
+
+constexpr int ADJ_THREADS = 256;
+constexpr int FWD_THREADS = 512;
+constexpr int FWD_PER_THREAD = 10;
+
+// ---- dDhat/dOm = -1/2 int_0^z ((1+z)^3 - 1) / E^3 dz, cumulative ----
+__global__ void __launch_bounds__(FWD_THREADS) k_fwd_table_dOm(double Om, double *out) {
+    __shared__ double warp_tot[FWD_THREADS / 32];
+    const int t = threadIdx.x;
+    const double x1 = sqrt(5.0 - 2.0 * sqrt(10.0 / 7.0)) / 3.0;
+    const double x2 = sqrt(5.0 + 2.0 * sqrt(10.0 / 7.0)) / 3.0;
+    const double w0 = 128.0 / 225.0;
+    const double w1 = (322.0 + 13.0 * sqrt(70.0)) / 900.0;
+    const double w2 = (322.0 - 13.0 * sqrt(70.0)) / 900.0;
+    auto g = [Om](double z) {
+        double a = 1.0 + z, E = chimd::E_of(z, Om);
+        return -0.5 * (a * a * a - 1.0) / (E * E * E);
+    };
+    double loc[FWD_PER_THREAD];
+    double run = 0.0;
+#pragma unroll
+    for (int cc = 0; cc < FWD_PER_THREAD; cc++) {
+        int k = t * FWD_PER_THREAD + cc;
+        if (k < NT_FWD - 1) {
+            double m = (k + 0.5) * HT, hh = 0.5 * HT;
+            double s = w0 * g(m) + w1 * (g(m - hh * x1) + g(m + hh * x1)) + w2 * (g(m - hh * x2) + g(m + hh * x2));
+            run += s * hh;
+        }
+        loc[cc] = run;
+    }
+    const int lane = t & 31, wid = t >> 5;
+    double v = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        double y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) warp_tot[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        double x = lane < FWD_THREADS / 32 ? warp_tot[lane] : 0.0;
+        for (int o = 1; o < 32; o <<= 1) {
+            double y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane < FWD_THREADS / 32) warp_tot[lane] = x;
+    }
+    __syncthreads();
+    double offset = (v - run) + (wid > 0 ? warp_tot[wid - 1] : 0.0);
+#pragma unroll
+    for (int cc = 0; cc < FWD_PER_THREAD; cc++) {
+        int k = t * FWD_PER_THREAD + cc;
+        if (k < NT_FWD - 1) out[k + 1] = offset + loc[cc];
+    }
+    if (t == 0) out[0] = 0.0;
+}
+
+// Hermite interpolation of dDhat/dOm (node derivatives known in closed form).
+__device__ __forceinline__ double dcO_hermite(const double *fwdO, double z, double Om) {
+    double t = z / HT;
+    int k = (int)floor(t);
+    if (k < 0) k = 0;
+    if (k > NT_FWD - 2) k = NT_FWD - 2;
+    double f = t - k;
+    auto g = [Om](double zz) {
+        double a = 1.0 + zz, E = chimd::E_of(zz, Om);
+        return -0.5 * (a * a * a - 1.0) / (E * E * E);
+    };
+    double m0 = HT * g(k * HT), m1 = HT * g((k + 1) * HT);
+    double f2 = f * f, f3 = f2 * f;
+    return (2 * f3 - 3 * f2 + 1) * fwdO[k] + (f3 - 2 * f2 + f) * m0 + (-2 * f3 + 3 * f2) * fwdO[k + 1] +
+           (f3 - f2) * m1;
+}
+
+// Derivatives of the distance relation at redshift z for one hyperpoint.
+struct ZDer {
+    double dz[4];     // dz/d(H0, Om, Xi0, n) at fixed d_L
+    double dlnJ[4];   // d ln J / d(H0, Om, Xi0, n) at fixed z
+    double dlnJ_dz;   // d ln J / dz
+    double dlnpz_dOm; // d ln p_z / dOm at fixed z (p_z = dV/dz / V(z_max))
+    double dlnpz_dz;
+};
+
+__device__ ZDer zder(double z, const double *th, const double *fwd, const double *fwdO, double dlpz_zmax) {
+    ZDer r;
+    const double H0 = th[0], Om = th[1], Xi0 = th[2], n = th[3];
+    const double cH = C_KMS / H0, a = 1.0 + z;
+    const double Dh = chimd::dc_hermite(fwd, z, Om), DhO = dcO_hermite(fwdO, z, Om);
+    const double E = chimd::E_of(z, Om), iE = 1.0 / E;
+    const double D = cH * Dh, DO = cH * DhO;
+    const double la = log(a), pw = exp(-n * la);
+    const double xi = Xi0 + (1.0 - Xi0) * pw, dxi = -n * (1.0 - Xi0) * pw / a;
+    const double P = D + a * cH * iE;  // d d_L^em / dz
+    const double J = P * xi + a * D * dxi;
+    const double d = a * D * xi;
+    const double dd[4] = {-d / H0, a * DO * xi, a * D * (1.0 - pw), -a * D * (1.0 - Xi0) * la * pw};
+    for (int k = 0; k < 4; k++) r.dz[k] = -dd[k] / J;
+    const double diE_dOm = -(a * a * a - 1.0) * 0.5 * iE * iE * iE;
+    const double dxi_dn = -(1.0 - Xi0) * la * pw, ddxi_dn = (1.0 - Xi0) * (pw / a) * (n * la - 1.0);
+    const double dJ[4] = {-J / H0, (DO + a * cH * diE_dOm) * xi + a * DO * dxi,
+                          P * (1.0 - pw) + a * D * n * pw / a, P * dxi_dn + a * D * ddxi_dn};
+    for (int k = 0; k < 4; k++) r.dlnJ[k] = dJ[k] / J;
+    const double Ep = 1.5 * Om * a * a * iE;  // dE/dz
+    const double d2xi = n * (n + 1.0) * (1.0 - Xi0) * pw / (a * a);
+    const double dJdz = (2.0 * cH * iE - a * cH * Ep * iE * iE) * xi + P * dxi + (D + a * cH * iE) * dxi + a * D * d2xi;
+    r.dlnJ_dz = dJdz / J;
+    r.dlnpz_dOm = 2.0 * DhO / Dh - (a * a * a - 1.0) * 0.5 * iE * iE + dlpz_zmax;
+    r.dlnpz_dz = 2.0 * iE / Dh - Ep * iE;
+    return r;
+}
+
+// d ln psi / d(gamma, kappa, z_p) and d ln psi / dz (Sec. 3.1)
+__device__ void dlnpsi(double z, const double *th, double *g3, double *dz) {
+    const double gam = th[9], kap = th[10], zp = th[11], a = 1.0 + z;
+    const double L = log(a / (1.0 + zp));
+    const double x = exp((gam + kap) * L);
+    const double r = x / (1.0 + x);
+    g3[0] = log(a) - r * L;
+    g3[1] = -r * L;
+    g3[2] = r * (gam + kap) / (1.0 + zp);
+    *dz = gam / a - r * (gam + kap) / a;
+}
+
+// Mass-model log-derivatives for source masses (m1, m2): direct derivatives
+// d ln p / d(alpha, mu, sigma, m_min, m_max) and d ln p / dz through
+// m = m_det / (1+z).  Zero when the weight is zero.
+__device__ void dlnpm(const HP &hp, const HPd &hd, double beta, double m1, double m2, double a,
+                      double *d5, double *ddz) {
+    for (int k = 0; k < 5; k++) d5[k] = 0.0;
+    *ddz = 0.0;
+    const double alpha = hp.th[4], mu = hp.th[5], sg = hp.th[6], mmin = hp.th[7], mmax = hp.th[8];
+    if (!(m1 >= mmin && m1 <= mmax && m2 >= mmin && m2 <= m1) || !(m1 > mmin)) return;
+    const double x = (m1 - mu) / sg;
+    const double PL = hp.c_pl * pow(m1, -alpha), GG = hp.c_g * exp(-0.5 * x * x);
+    const double p1 = PL + GG;
+    if (!(p1 > 0.0)) return;
+    const double ip1 = 1.0 / p1;
+    d5[0] = PL * (hd.dlc_pl[0] - log(m1)) * ip1;
+    d5[1] = GG * (hd.dlc_g[0] + x / sg) * ip1;
+    d5[2] = GG * (hd.dlc_g[1] + x * x / sg) * ip1;
+    d5[3] = (PL * hd.dlc_pl[1] + GG * hd.dlc_g[2]) * ip1;
+    d5[4] = (PL * hd.dlc_pl[2] + GG * hd.dlc_g[3]) * ip1;
+    const double dp1_dm1 = (-alpha * PL / m1 - GG * x / sg) * ip1;
+    double dp2_dm1, dp2_dm2, dp2_dmin;
+    if (fabs(hp.b1) < 1e-12) {
+        const double L = log(m1 / mmin);
+        dp2_dm1 = -1.0 / (m1 * L);
+        dp2_dm2 = -1.0 / m2;
+        dp2_dmin = 1.0 / (mmin * L);
+    } else {
+        const double q = pow(m1, hp.b1) - hp.mmin_b1;
+        dp2_dm1 = -hp.b1 * pow(m1, beta) / q;
+        dp2_dm2 = beta / m2;
+        dp2_dmin = hp.b1 * pow(mmin, beta) / q;
+    }
+    d5[3] += dp2_dmin;
+    *ddz = -(m1 * (dp1_dm1 + dp2_dm1) + m2 * dp2_dm2) / a;
+}
+
+__device__ double std_normal_pdf(double x) { return 0.39894228040143267794 * exp(-0.5 * x * x); }
+
+// ---- per-hyperpoint derivative tables ----
+__global__ void __launch_bounds__(ADJ_THREADS) k_adj_tables(DevCatalog c, CallPtrs p, AdjPtrs q) {
+    const int h = blockIdx.x, t = threadIdx.x;
+    const HP &hp = p.hp[h];
+    const double *th = hp.th;
+    const double *fwd = p.fwd[h], *fwdO = q.fwdO[h];
+    if (t == 0) {
+        HPd hd;
+        const double alpha = th[4], mu = th[5], sg = th[6], mmin = th[7], mmax = th[8];
+        const double s1 = 1.0 - alpha;
+        double PL, dPLds;
+        const double la = log(mmax), lb = log(mmin);
+        if (fabs(s1) < 1e-12) {
+            PL = la - lb;
+            dPLds = 0.5 * (la * la - lb * lb);
+        } else {
+            const double A = pow(mmax, s1), B = pow(mmin, s1);
+            PL = (A - B) / s1;
+            dPLds = ((la * A - lb * B) * s1 - (A - B)) / (s1 * s1);
+        }
+        hd.dlc_pl[0] = dPLds / PL;  // d ln c_pl / d alpha = -(dPL/dalpha)/PL, dPL/dalpha = -dPL/ds
+        hd.dlc_pl[1] = pow(mmin, -alpha) / PL;
+        hd.dlc_pl[2] = -pow(mmax, -alpha) / PL;
+        const double A = (mmin - mu) / sg, B = (mmax - mu) / sg;
+        const double den = 0.5 * erfc(-B * 0.70710678118654752440) - 0.5 * erfc(-A * 0.70710678118654752440);
+        const double pA = std_normal_pdf(A), pB = std_normal_pdf(B);
+        if (den > 0.0) {
+            hd.dlc_g[0] = -((pA - pB) / sg) / den;
+            hd.dlc_g[1] = -1.0 / sg - ((A * pA - B * pB) / sg) / den;
+            hd.dlc_g[2] = pA / (sg * den);
+            hd.dlc_g[3] = -pB / (sg * den);
+        } else {
+            hd.dlc_g[0] = hd.dlc_g[1] = hd.dlc_g[2] = hd.dlc_g[3] = 0.0;
+        }
+        const double zm = c.z_max;
+        hd.dlpz_zmax = -3.0 * dcO_hermite(fwdO, zm, th[1]) / chimd::dc_hermite(fwd, zm, th[1]);
+        q.hpd[h] = hd;
+    }
+    // dz/dtheta at the inverse-table nodes
+    const double2 *nd = p.inv64 + (size_t)h * (NU + 1);
+    for (int k = t; k <= NU; k += ADJ_THREADS) {
+        double z = nd[k].x;
+        double *o = q.dznode + ((size_t)h * (NU + 1) + k) * 4;
+        if (k == 0 || !isfinite(z)) {
+            for (int j = 0; j < 4; j++) o[j] = 0.0;
+            continue;
+        }
+        ZDer r = zder(z, th, fwd, fwdO, 0.0);
+        for (int j = 0; j < 4; j++) o[j] = r.dz[j];
+    }
+    // d ln F / dtheta on the grid, F = psi / ((1+z)^3 J)
+    for (int a = t; a < c.n_z; a += ADJ_THREADS) {
+        double z = a * c.dz;
+        ZDer r = zder(z, th, fwd, fwdO, 0.0);
+        double g3[3], dz;
+        dlnpsi(z, th, g3, &dz);
+        double *o = q.Q + ((size_t)h * c.n_z + a) * 7;
+        for (int j = 0; j < 4; j++) o[j] = -r.dlnJ[j];
+        o[4] = g3[0];
+        o[5] = g3[1];
+        o[6] = g3[2];
+    }
+}
+
+// dz/dtheta of a sample by linear interpolation between inverse-table nodes
+__device__ __forceinline__ void dz_interp(const AdjPtrs &q, int h, int k, double f, double *dz) {
+    const double *a = q.dznode + ((size_t)h * (NU + 1) + k) * 4;
+    for (int j = 0; j < 4; j++) dz[j] = a[j] + f * (a[4 + j] - a[j]);
+}
+
+template <int NV>
+__device__ void bsum(double (&v)[NV], double *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        double s = v[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[wid * NV + k] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int w = 0; w < ADJ_THREADS / 32; w++) s += red[w * NV + threadIdx.x];
+        red[(ADJ_THREADS / 32) * NV + threadIdx.x] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = red[(ADJ_THREADS / 32) * NV + k];
+    __syncthreads();
+}
+
+// Per (event, hyperpoint): d ln I_i / d theta (12).  FP64 follows the FP64
+// forward kernel (inversion with Newton polish, +-9 b windows); MIXED follows
+// the mixed forward kernel (FP32 inverse table and mass model, +-6 b windows,
+// FP32 bandwidth) so that the gradient is that of the computed ln L.
+template <bool F64>
+__global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtrs p, AdjPtrs q, int H) {
+    extern __shared__ double sh[];
+    double *zs = sh;
+    double *ws = zs + c.max_ns;
+    int *segv = reinterpret_cast<int *>(ws + c.max_ns);
+    double *red = reinterpret_cast<double *>(segv + ((c.max_seg + 2) & ~1));
+    const int h = blockIdx.x % H;
+    const int ev = c.ev_order[blockIdx.x / H];
+    const int tid = threadIdx.x;
+    const HP &hp = p.hp[h];
+    const HPd &hd = q.hpd[h];
+    double *out = q.dlnI + ((size_t)h * c.n_events + ev) * 12;
+    if (hp.status & (CHIMERA_PT_OUT_OF_SUPPORT | CHIMERA_PT_NONMONOTONE)) {
+        if (tid < 12) out[tid] = 0.0;
+        return;
+    }
+    const int64_t s0 = c.ev_soff[ev];
+    const int ns = (int)(c.ev_soff[ev + 1] - s0);
+    const double KW = F64 ? KW64 : (double)KW32;
+    MixParams mp;
+    mp.c_pl = hp.c_pl32; mp.c_g = hp.c_g32; mp.alpha = hp.alpha32; mp.mu = hp.mu32;
+    mp.inv_sg = hp.inv_sg32; mp.mmin = hp.mmin32; mp.mmax = hp.mmax32; mp.beta = hp.beta32;
+    mp.b1 = hp.b1_32; mp.mmin_b1 = hp.mmin_b1_32; mp.lmmin = hp.lmmin32; mp.kv = hp.k_valid; mp.fv = hp.f_valid;
+    const float4 *inv = p.inv32 + (size_t)h * NU;
+
+    // ---- z_j, w_j exactly as the forward kernel of this precision
+    for (int j = tid; j < ns; j += ADJ_THREADS) {
+        double z = CUDART_INF, w = 0.0;
+        if (F64) {
+            double zz;
+            if (invert64(c, p, h, hp, c.sd64[s0 + j], &zz)) {
+                z = zz;
+                w = mass_weight64(hp, c.beta, c.sm1_64[s0 + j] / (1.0 + zz), c.sm2_64[s0 + j] / (1.0 + zz));
+            }
+        } else {
+            float4 s = c.s32[s0 + j];
+            int k = __float_as_int(s.x);
+            if ((k < mp.kv) || (k == mp.kv && s.y <= mp.fv)) {
+                float zz = chimd::hermite4(inv[k], s.y);
+                if (isfinite(zz)) {
+                    z = zz;
+                    float lz = __logf(1.f + zz);
+                    w = mass_weight32(mp, s.z - lz, s.w - lz);
+                }
+            }
+        }
+        zs[j] = z;
+        ws[j] = w;
+    }
+    __syncthreads();
+    // moments (two-pass, FP64)
+    double m1v[4] = {0, 0, 0, 0};  // W1, Wz, W2, n_valid
+    double mz = 0.0;
+    for (int j = tid; j < ns; j += ADJ_THREADS)
+        if (zs[j] < CUDART_INF) {
+            m1v[0] += ws[j]; m1v[1] += ws[j] * zs[j]; m1v[2] += ws[j] * ws[j]; m1v[3] += 1.0; mz += zs[j];
+        }
+    double m5[5] = {m1v[0], m1v[1], m1v[2], m1v[3], mz};
+    bsum<5>(m5, red);
+    const double W1 = m5[0], W2 = m5[2], nv = m5[3];
+    const double Mw = W1 > 0.0 ? m5[1] / W1 : 0.0, Mu = nv > 0.0 ? m5[4] / nv : 0.0;
+    double m2v[2] = {0.0, 0.0};
+    for (int j = tid; j < ns; j += ADJ_THREADS)
+        if (zs[j] < CUDART_INF) {
+            m2v[0] += ws[j] * (zs[j] - Mw) * (zs[j] - Mw);
+            m2v[1] += (zs[j] - Mu) * (zs[j] - Mu);
+        }
+    bsum<2>(m2v, red);
+    const double varw = W1 > 0.0 ? m2v[0] / W1 : 0.0, neffw = W1 > 0.0 ? W1 * W1 / W2 : 0.0;
+    const double varu = nv > 0.0 ? m2v[1] / nv : 0.0;
+    int rule;  // 0 weighted, 1 unweighted, 2 grid spacing
+    double b;
+    if (W1 > 0.0 && neffw >= 2.0 && varw > 0.0) {
+        rule = 0;
+        b = sqrt(varw) * pow(neffw, -0.2);
+    } else if (nv >= 2.0 && varu > 0.0) {
+        rule = 1;
+        b = sqrt(varu) * pow(nv, -0.2);
+    } else {
+        rule = 2;
+        b = c.dz;
+    }
+    if (!F64) b = (double)p.bw[(size_t)h * c.n_events + ev];  // the forward kernel's FP32 bandwidth
+
+    // segment valid counts
+    const int sg0 = c.ev_segoff[ev], nseg = c.ev_segoff[ev + 1] - sg0;
+    for (int k = tid; k < nseg; k += ADJ_THREADS) {
+        int lo = (int)(c.seg_soff[sg0 + k] - s0), hi = (int)(c.seg_soff[sg0 + k + 1] - s0);
+        int l = lo, r = hi;
+        while (l < r) {
+            int m = (l + r) >> 1;
+            if (zs[m] < CUDART_INF) l = m + 1; else r = m;
+        }
+        segv[k] = l - lo;
+    }
+    __syncthreads();
+
+    // ---- per-sample derivatives: bandwidth gradient and the sample sums
+    const int nz = c.n_z;
+    const double dz = c.dz;
+    const double *Fg = p.F64 + (size_t)h * nz;
+    const double *Qg = q.Q + (size_t)h * nz * 7;
+    double A12[12], B4[4], S2t = 0.0, I0 = 0.0, db9[9];
+    for (int k = 0; k < 12; k++) A12[k] = 0.0;
+    for (int k = 0; k < 4; k++) B4[k] = 0.0;
+    for (int k = 0; k < 9; k++) db9[k] = 0.0;
+    for (int j = tid; j < ns; j += ADJ_THREADS) {
+        int l = 0, r = nseg;  // segment of j
+        while (r - l > 1) {
+            int m = (l + r) >> 1;
+            if ((int)(c.seg_soff[sg0 + m] - s0) <= j) l = m; else r = m;
+        }
+        const int lo = (int)(c.seg_soff[sg0 + l] - s0);
+        if (j - lo >= segv[l]) continue;
+        const double z = zs[j], w = ws[j], a1 = 1.0 + z;
+        // dz/dtheta and d ln w/dtheta
+        double dd[4];
+        {
+            double dL = c.sd64[s0 + j];
+            double t = sqrt(dL / c.d_top) * NU;
+            int kk = min((int)t, NU - 1);
+            dz_interp(q, h, kk, t - kk, dd);
+        }
+        double d5[5], dwz;
+        dlnpm(hp, hd, c.beta, c.sm1_64[s0 + j] / a1, c.sm2_64[s0 + j] / a1, a1, d5, &dwz);
+        double dlw[9];
+        for (int k = 0; k < 4; k++) dlw[k] = dwz * dd[k];
+        for (int k = 0; k < 5; k++) dlw[4 + k] = d5[k];
+        // Scott's rule: d ln b = sum_j (dlnb/dw_j) w_j dln w_j + (dlnb/dz_j) dz_j
+        if (rule == 0) {
+            const double cw = 0.5 * ((z - Mw) * (z - Mw) - varw) / (W1 * varw) - 0.2 * (2.0 / W1 - 2.0 * w / W2);
+            const double cz = w * (z - Mw) / (W1 * varw);
+            for (int k = 0; k < 9; k++) db9[k] += cw * w * dlw[k] + (k < 4 ? cz * dd[k] : 0.0);
+        } else if (rule == 1) {
+            const double cz = (z - Mu) / (nv * varu);
+            for (int k = 0; k < 4; k++) db9[k] += cz * dd[k];
+        }
+        if (w == 0.0) continue;
+        // window sums S0, S1, S2
+        const double pf = c.seg_pf[sg0 + l];
+        const int64_t row = c.kde_mode == CHIMERA_KDE_MANY_1D ? (int64_t)(sg0 + l) : (int64_t)ev;
+        const double smin = zs[lo] - KDE_MARGIN * b, smax = zs[lo + segv[l] - 1] + KDE_MARGIN * b;
+        double a0 = fmax(ceil((z - KW * b) / dz), ceil(smin / dz));
+        double aa1 = fmin(floor((z + KW * b) / dz), floor(smax / dz));
+        int ia0 = a0 < 0.0 ? 0 : (a0 > nz ? nz : (int)a0);
+        int ia1 = aa1 > nz - 1 ? nz - 1 : (aa1 < -1.0 ? -1 : (int)aa1);
+        double S0 = 0.0, S1 = 0.0, S2 = 0.0;
+        for (int a = ia0; a <= ia1; a++) {
+            double Ga = F64 ? reinterpret_cast<const double *>(p.prof[h])[row * nz + a]
+                            : (double)reinterpret_cast<const float *>(p.prof[h])[row * nz + a];
+            double Hh = ((a == 0 || a == nz - 1) ? 0.5 : 1.0) * Fg[a] * Ga;
+            double u = (a * dz - z) / b;
+            double e = exp(-0.5 * u * u) * Hh;
+            S0 += e;
+            S1 += e * u;
+            S2 += e * u * u;
+        }
+        const double pw = pf * w;
+        I0 += pw * S0;
+        S2t += pw * S2;
+        for (int k = 0; k < 9; k++) A12[k] += pw * S0 * dlw[k];
+        for (int k = 0; k < 4; k++) B4[k] += pw * S1 / b * dd[k];
+    }
+    // ---- grid term: per segment and grid point, the KDE K_k(a)
+    double C8[8];  // 7 d ln F terms + the galaxy Om term
+    for (int k = 0; k < 8; k++) C8[k] = 0.0;
+    for (int l = 0; l < nseg; l++) {
+        const int lo = (int)(c.seg_soff[sg0 + l] - s0), cnt = segv[l];
+        if (cnt <= 0) continue;
+        const double pf = c.seg_pf[sg0 + l];
+        const int64_t row = c.kde_mode == CHIMERA_KDE_MANY_1D ? (int64_t)(sg0 + l) : (int64_t)ev;
+        const double smin = zs[lo] - KDE_MARGIN * b, smax = zs[lo + cnt - 1] + KDE_MARGIN * b;
+        const int alo = max(0, (int)ceil(smin / dz)), ahi = min(nz - 1, (int)floor(smax / dz));
+        for (int a = alo + tid; a <= ahi; a += ADJ_THREADS) {
+            const double za = a * dz;
+            // samples whose window covers a: z in [za - KW b, za + KW b]
+            int jl = lo, jr = lo + cnt;
+            while (jl < jr) {
+                int m = (jl + jr) >> 1;
+                if (zs[m] < za - KW * b) jl = m + 1; else jr = m;
+            }
+            double K = 0.0;
+            for (int j = jl; j < lo + cnt && zs[j] <= za + KW * b; j++) {
+                // same per-sample window rule as the sums above
+                double z = zs[j];
+                double a0 = ceil((z - KW * b) / dz), aa1 = floor((z + KW * b) / dz);
+                if (a < a0 || a > aa1) continue;
+                double u = (za - z) / b;
+                K += ws[j] * exp(-0.5 * u * u);
+            }
+            if (K == 0.0) continue;
+            double Ga = F64 ? reinterpret_cast<const double *>(p.prof[h])[row * nz + a]
+                            : (double)reinterpret_cast<const float *>(p.prof[h])[row * nz + a];
+            double wa = (a == 0 || a == nz - 1) ? 0.5 : 1.0;
+            double M = pf * wa * Fg[a] * Ga * K;
+            for (int k = 0; k < 7; k++) C8[k] += M * Qg[(size_t)a * 7 + k];
+            double dGa = q.dprof[h][row * nz + a];
+            C8[7] += pf * wa * Fg[a] * dGa * K;
+        }
+    }
+    // ---- block sums and the 12 derivatives
+    double v[28];
+    for (int k = 0; k < 9; k++) v[k] = A12[k];
+    for (int k = 0; k < 4; k++) v[9 + k] = B4[k];
+    v[13] = S2t;
+    v[14] = I0;
+    for (int k = 0; k < 8; k++) v[15 + k] = C8[k];
+    for (int k = 0; k < 5; k++) v[23 + k] = 0.0;
+    double vb[9];
+    for (int k = 0; k < 9; k++) vb[k] = db9[k];
+    bsum<28>(v, red);
+    bsum<9>(vb, red);
+    if (tid == 0) {
+        const double I = v[14];
+        double g[12];
+        for (int k = 0; k < 12; k++) g[k] = 0.0;
+        if (I > 0.0) {
+            // cosmology (H0, Om, Xi0, n): w through z, z directly, b, grid factor
+            for (int k = 0; k < 4; k++)
+                g[k] = (v[k] + v[9 + k] + v[13] * vb[k] + v[15 + k]) / I - vb[k];
+            g[1] += v[22] / I;  // galaxy prior through dV_c/dz and the Z_g
+            // mass parameters: w directly and b
+            for (int k = 0; k < 5; k++) g[4 + k] = (v[4 + k] + v[13] * vb[4 + k]) / I - vb[4 + k];
+            // rate (gamma, kappa, z_p): grid factor only
+            for (int k = 0; k < 3; k++) g[9 + k] = v[19 + k] / I;
+        }
+        for (int k = 0; k < 12; k++) out[k] = g[k];
+    }
+}
+
+// Selection adjoint: per block, sum_j s_j dln s_j / dtheta (12) and sum_j s_j.
+template <bool F64>
+__global__ void __launch_bounds__(ADJ_THREADS) k_select_adj(DevCatalog c, CallPtrs p, AdjPtrs q, int H) {
+    __shared__ double red[(ADJ_THREADS / 32 + 1) * 13];
+    const int h = blockIdx.y, chunk = blockIdx.x;
+    const HP &hp = p.hp[h];
+    const HPd &hd = q.hpd[h];
+    const double *th = hp.th;
+    double acc[13];
+    for (int k = 0; k < 13; k++) acc[k] = 0.0;
+    MixParams mp;
+    mp.c_pl = hp.c_pl32; mp.c_g = hp.c_g32; mp.alpha = hp.alpha32; mp.mu = hp.mu32;
+    mp.inv_sg = hp.inv_sg32; mp.mmin = hp.mmin32; mp.mmax = hp.mmax32; mp.beta = hp.beta32;
+    mp.b1 = hp.b1_32; mp.mmin_b1 = hp.mmin_b1_32; mp.lmmin = hp.lmmin32; mp.kv = hp.k_valid; mp.fv = hp.f_valid;
+    const int64_t base = (int64_t)chunk * SEL_CHUNK;
+    const double inv_dc3 = 1.0 / (hp.dc_zmax * hp.dc_zmax * hp.dc_zmax);
+    for (int qq = 0; qq < SEL_PER_THREAD; qq++) {
+        int64_t j = base + qq * ADJ_THREADS + threadIdx.x;
+        if (j >= c.n_det) break;
+        double d = c.id64[j], z;
+        if (F64) {
+            if (!invert64(c, p, h, hp, d, &z)) continue;
+        } else {
+            float4 a4 = c.i32a[j];
+            int k = __float_as_int(a4.x);
+            if (!((k < mp.kv) || (k == mp.kv && a4.y <= mp.fv))) continue;
+            float zz = chimd::hermite4(p.inv32[(size_t)h * NU + k], a4.y);
+            if (!isfinite(zz)) continue;
+            z = zz;
+        }
+        if (!(z <= c.z_max)) continue;
+        const double a1 = 1.0 + z;
+        const double m1 = c.im1_64[j] / a1, m2 = c.im2_64[j] / a1;
+        const double mmin = th[7], mmax = th[8];
+        if (!(m1 >= mmin && m1 <= mmax && m2 >= mmin && m2 <= m1) || !(m1 > mmin)) continue;
+        // s_j (FP64 arithmetic on this path's z)
+        double x = (m1 - th[5]) / th[6];
+        double p1 = hp.c_pl * pow(m1, -th[4]) + hp.c_g * exp(-0.5 * x * x);
+        double p2 = fabs(hp.b1) < 1e-12 ? 1.0 / (m2 * log(m1 / mmin))
+                                         : hp.b1 * pow(m2, c.beta) / (pow(m1, hp.b1) - hp.mmin_b1);
+        double Dc = hp.cH * chimd::dc_hermite(p.fwd[h], z, th[1]), dd, J;
+        chimd::dgw_J(z, Dc, th, hp.cH, &dd, &J);
+        double E = chimd::E_of(z, th[1]);
+        double pz = 3.0 * hp.cH * Dc * Dc / E * inv_dc3;
+        double s = p1 * p2 * chimd::psi_of(z, th) * pz / (a1 * a1 * a1 * fabs(J) * exp(c.ilp64[j]));
+        // log-derivatives
+        ZDer r = zder(z, th, p.fwd[h], q.fwdO[h], hd.dlpz_zmax);
+        double d5[5], dwz, g3[3], dpsiz;
+        dlnpm(hp, hd, c.beta, m1, m2, a1, d5, &dwz);
+        dlnpsi(z, th, g3, &dpsiz);
+        const double dls_dz = dwz + dpsiz + r.dlnpz_dz - 3.0 / a1 - r.dlnJ_dz;
+        double g[12];
+        g[0] = -r.dlnJ[0];
+        g[1] = r.dlnpz_dOm - r.dlnJ[1];
+        g[2] = -r.dlnJ[2];
+        g[3] = -r.dlnJ[3];
+        for (int k = 0; k < 4; k++) g[k] += dls_dz * r.dz[k];
+        for (int k = 0; k < 5; k++) g[4 + k] = d5[k];
+        for (int k = 0; k < 3; k++) g[9 + k] = g3[k];
+        for (int k = 0; k < 12; k++) acc[k] += s * g[k];
+        acc[12] += s;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < 13; k++) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[wid * 13 + k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 13) {
+        double v = 0.0;
+        for (int w = 0; w < ADJ_THREADS / 32; w++) v += red[w * 13 + threadIdx.x];
+        q.selg[((size_t)h * p.n_chunk + chunk) * 13 + threadIdx.x] = v;
+    }
+}
+
+// grad[h] = sum_i d ln I_i - N_obs (sum_j s_j dln s_j) / (sum_j s_j); zero
+// for a point whose ln L is -inf.  Fixed-order sums (deterministic).
+__global__ void __launch_bounds__(ADJ_THREADS) k_combine_adj(DevCatalog c, CallPtrs p, AdjPtrs q, int H) {
+    __shared__ double red[(ADJ_THREADS / 32 + 1) * 25];
+    const int h = blockIdx.x;
+    double v[25];
+    for (int k = 0; k < 25; k++) v[k] = 0.0;
+    for (int i = threadIdx.x; i < c.n_events; i += ADJ_THREADS) {
+        const double *d = q.dlnI + ((size_t)h * c.n_events + i) * 12;
+        for (int k = 0; k < 12; k++) v[k] += d[k];
+    }
+    for (int ch = threadIdx.x; ch < p.n_chunk; ch += ADJ_THREADS) {
+        const double *d = q.selg + ((size_t)h * p.n_chunk + ch) * 13;
+        for (int k = 0; k < 13; k++) v[12 + k] += d[k];
+    }
+    bsum<25>(v, red);
+    if (threadIdx.x < 12) {
+        const int k = threadIdx.x;
+        const double S = v[24];
+        const bool bad = !isfinite(p.lnL[h]) || !(S > 0.0);
+        q.grad[(size_t)h * 12 + k] = bad ? 0.0 : v[k] - (double)c.n_events * v[12 + k] / S;
+    }
+}
+
+// dV_c/dz (as D^2/E) and its Om derivative on the grid, for one Om.
+__global__ void k_dv_pair(const double *fwd, const double *fwdO, double Om, double dz, int nz, double *dv,
+                          double *dvO) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nz) return;
+    double z = a * dz, ap = 1.0 + z;
+    double D = chimd::dc_hermite(fwd, z, Om), DO = dcO_hermite(fwdO, z, Om), E = chimd::E_of(z, Om);
+    dv[a] = D * D / E;
+    dvO[a] = 2.0 * D * DO / E - D * D * (ap * ap * ap - 1.0) * 0.5 / (E * E * E);
+}
+
+// Galaxy (z, sigma): FP64 values, or the stored values of the mixed path.
+__device__ __forceinline__ void gal_value(const DevCatalog &c, int64_t p, int64_t g, bool f64, double &z,
+                                          double &s) {
+    if (f64 || c.gal_storage == CHIMERA_GAL_F32) {
+        z = f64 ? c.gz64[g] : (double)c.gz32[g];
+        s = f64 ? c.gs64[g] : (double)c.gs32[g];
+    } else if (c.gal_storage == CHIMERA_GAL_F16) {
+        z = (double)(c.pix_zref[p] + __half2float(__ushort_as_half(c.gzq[g])));
+        s = (double)__half2float(__ushort_as_half(c.gsq[g]));
+    } else {
+        z = (double)(c.pix_zref[p] + __uint_as_float(((uint32_t)c.gzq[g]) << 16));
+        s = (double)__uint_as_float(((uint32_t)c.gsq[g]) << 16);
+    }
+}
+
+// dG_k/dOm on the grid (FP64), with the galaxy windows of the forward profile
+// of the same precision:
+//   G = dv sum_g N_g / Z_g,  G' = dv' sum_g N_g / Z_g - dv sum_g N_g Z_g' / Z_g^2,
+//   Z_g' = sum_a w_a N_g(z_a) dv'(z_a).
+template <bool F64>
+__global__ void __launch_bounds__(ADJ_THREADS) k_profile_dOm(DevCatalog c, const double *dv, const double *dvO,
+                                                            double *invZ, double *ZO, double *out) {
+    const int64_t p = blockIdx.x;
+    const int64_t g0 = c.gal_off[p], g1 = c.gal_off[p + 1];
+    const int nz = c.n_z;
+    const double dz = c.dz, norm = 0.39894228040143267794;
+    const double KWG = F64 ? KWG64 : (double)KWG32;
+    for (int64_t g = g0 + threadIdx.x; g < g1; g += ADJ_THREADS) {
+        double zg, sg;
+        gal_value(c, p, g, F64, zg, sg);
+        double a0 = ceil((zg - KWG * sg) / dz), a1 = floor((zg + KWG * sg) / dz);
+        int lo = a0 < 0.0 ? 0 : (a0 > nz ? nz : (int)a0);
+        int hi = a1 > nz - 1 ? nz - 1 : (a1 < -1.0 ? -1 : (int)a1);
+        double Z = 0.0, Zp = 0.0;
+        for (int a = lo; a <= hi; a++) {
+            double u = (a * dz - zg) / sg, wa = (a == 0 || a == nz - 1) ? 0.5 * dz : dz;
+            double Nv = wa * norm / sg * exp(-0.5 * u * u);
+            Z += Nv * dv[a];
+            Zp += Nv * dvO[a];
+        }
+        invZ[g] = Z > 0.0 ? 1.0 / Z : 0.0;
+        ZO[g] = Zp;
+    }
+    __syncthreads();
+    const double smax = F64 ? c.pix_sigmax[p] * KWG64 : (double)(c.pix_sigmax32[p] * KWG32);
+    for (int a = threadIdx.x; a < nz; a += ADJ_THREADS) {
+        double za = a * dz, s1 = 0.0, s2 = 0.0;
+        int64_t l = g0, r = g1;
+        while (l < r) {
+            int64_t m = (l + r) >> 1;
+            double zm, sm;
+            gal_value(c, p, m, F64, zm, sm);
+            if (zm < za - smax) l = m + 1; else r = m;
+        }
+        for (int64_t g = l; g < g1; g++) {
+            double zg, sg;
+            gal_value(c, p, g, F64, zg, sg);
+            if (zg > za + smax) break;
+            double a0 = ceil((zg - KWG * sg) / dz), a1 = floor((zg + KWG * sg) / dz);
+            if (a < a0 || a > a1 || invZ[g] == 0.0) continue;
+            double u = (za - zg) / sg;
+            double Nv = norm / sg * exp(-0.5 * u * u);
+            s1 += Nv * invZ[g];
+            s2 += Nv * ZO[g] * invZ[g] * invZ[g];
+        }
+        out[p * nz + a] = dvO[a] * s1 - dv[a] * s2;
+    }
+}
+
+// Single-1D: sum_k S_k dG_k/dOm per event.
+__global__ void k_dprofile_sum(DevCatalog c, const double *G, double *outh) {
+    const int ev = blockIdx.x, nz = c.n_z;
+    const int64_t p0 = c.ev_poff[ev], p1 = c.ev_poff[ev + 1];
+    for (int a = threadIdx.x; a < nz; a += blockDim.x) {
+        double s = 0.0;
+        for (int64_t p = p0; p < p1; p++) s += c.pix_S[p] * G[p * nz + a];
+        outh[(int64_t)ev * nz + a] = s;
+    }
+}
+
+}  // namespace
+
+size_t adjoint_event_smem(const DevCatalog &c) {
+    return sizeof(double) * 2 * (size_t)c.max_ns + sizeof(int) * (size_t)((c.max_seg + 2) & ~1) +
+           sizeof(double) * (ADJ_THREADS / 32 + 1) * 28;
+}
+
+void launch_adjoint(const DevCatalog &c, const CallPtrs &p, const AdjPtrs &q, int H, bool fp64, cudaStream_t st) {
+    k_adj_tables<<<H, ADJ_THREADS, 0, st>>>(c, p, q);
+    const size_t smem = adjoint_event_smem(c);
+    const unsigned nb = (unsigned)((int64_t)c.n_events * H);
+    if (fp64) {
+        cudaFuncSetAttribute(k_event_adj<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (nb) k_event_adj<true><<<nb, ADJ_THREADS, smem, st>>>(c, p, q, H);
+        if (p.n_chunk) k_select_adj<true><<<dim3(p.n_chunk, H), ADJ_THREADS, 0, st>>>(c, p, q, H);
+    } else {
+        cudaFuncSetAttribute(k_event_adj<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (nb) k_event_adj<false><<<nb, ADJ_THREADS, smem, st>>>(c, p, q, H);
+        if (p.n_chunk) k_select_adj<false><<<dim3(p.n_chunk, H), ADJ_THREADS, 0, st>>>(c, p, q, H);
+    }
+    k_combine_adj<<<H, ADJ_THREADS, 0, st>>>(c, p, q, H);
+}
+
+#define CK(call)                                               \
+    do {                                                       \
+        int rc_ = cuda_check((call), #call);                   \
+        if (rc_) return rc_;                                   \
+    } while (0)
+#define RC(call)                                               \
+    do {                                                       \
+        int rc_ = (call);                                      \
+        if (rc_) return rc_;                                   \
+    } while (0)
+
+namespace {
+
+size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Layout of the adjoint scratch for H points of catalog c.
+struct AdjLayout {
+    size_t o_ptrs, o_hpd, o_dzn, o_Q, o_dlnI, o_selg, o_dv, o_dvO, o_invZ, o_ZO, total;
+    AdjLayout(const DevCatalog &c, int H, int nchunk) {
+        size_t o = 0;
+        auto take = [&](size_t b) { size_t r = o; o += al256(b); return r; };
+        o_ptrs = take(2 * sizeof(void *) * (size_t)H);
+        o_hpd = take(sizeof(HPd) * (size_t)H);
+        o_dzn = take(sizeof(double) * 4 * (size_t)H * (NU + 1));
+        o_Q = take(sizeof(double) * 7 * (size_t)H * c.n_z);
+        o_dlnI = take(sizeof(double) * 12 * (size_t)H * c.n_events);
+        o_selg = take(sizeof(double) * 13 * (size_t)H * std::max(nchunk, 1));
+        o_dv = take(sizeof(double) * c.n_z);
+        o_dvO = take(sizeof(double) * c.n_z);
+        o_invZ = take(sizeof(double) * (size_t)std::max<int64_t>(c.n_gal, 1));
+        o_ZO = take(sizeof(double) * (size_t)std::max<int64_t>(c.n_gal, 1));
+        total = o;
+    }
+};
+
+int fwdO_table(Ctx &ctx, double Om, cudaStream_t st, const double **out) {
+    uint64_t key = bits_of(Om);
+    auto it = ctx.fwdO.find(key);
+    if (it == ctx.fwdO.end()) {
+        FwdEntry e;
+        RC(dev_alloc(ctx, (void **)&e.table, sizeof(double) * NT_FWD));
+        if (cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming) != cudaSuccess) {
+            dev_free(ctx, e.table, sizeof(double) * NT_FWD);
+            return cuda_check(cudaGetLastError(), "cudaEventCreate");
+        }
+        k_fwd_table_dOm<<<1, FWD_THREADS, 0, st>>>(Om, e.table);
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(e.ready, st));
+        it = ctx.fwdO.emplace(key, e).first;
+    } else {
+        CK(cudaStreamWaitEvent(st, it->second.ready, 0));
+    }
+    *out = it->second.table;
+    return CHIMERA_OK;
+}
+
+// dG/dOm profile for (Om, precision), cached with the forward profiles.
+int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double Om, bool f64, const double *fwd,
+             const double *fwdO, const double **out) {
+    const int kind = f64 ? 2 : 3;
+    auto key = std::make_pair(bits_of(Om), kind);
+    auto it = cat.prof.find(key);
+    const DevCatalog &c = cat.d;
+    if (it == cat.prof.end()) {
+        ProfEntry e;
+        e.bytes = sizeof(double) * (size_t)c.n_pix * c.n_z;
+        const size_t hb = c.kde_mode == CHIMERA_KDE_SINGLE_1D ? sizeof(double) * (size_t)c.n_events * c.n_z : 0;
+        evict_profiles(ctx, cat, e.bytes + hb);
+        RC(dev_alloc(ctx, &e.G, e.bytes));
+        if (hb) {
+            int rc = dev_alloc(ctx, &e.Gh, hb);
+            if (rc) { dev_free(ctx, e.G, e.bytes); return rc; }
+            e.hbytes = hb;
+        }
+        if (cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming) != cudaSuccess) {
+            free_prof_entry(ctx, e);
+            return cuda_check(cudaGetLastError(), "cudaEventCreate");
+        }
+        double *dv = reinterpret_cast<double *>(ws.gscr + L.o_dv);
+        double *dvO = reinterpret_cast<double *>(ws.gscr + L.o_dvO);
+        double *invZ = reinterpret_cast<double *>(ws.gscr + L.o_invZ);
+        double *ZO = reinterpret_cast<double *>(ws.gscr + L.o_ZO);
+        k_dv_pair<<<(c.n_z + 255) / 256, 256, 0, ws.st>>>(fwd, fwdO, Om, c.dz, c.n_z, dv, dvO);
+        if (c.n_pix > 0) {
+            if (f64) k_profile_dOm<true><<<(unsigned)c.n_pix, ADJ_THREADS, 0, ws.st>>>(c, dv, dvO, invZ, ZO, (double *)e.G);
+            else k_profile_dOm<false><<<(unsigned)c.n_pix, ADJ_THREADS, 0, ws.st>>>(c, dv, dvO, invZ, ZO, (double *)e.G);
+        }
+        if (hb) k_dprofile_sum<<<c.n_events, 256, 0, ws.st>>>(c, (const double *)e.G, (double *)e.Gh);
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(e.ready, ws.st));
+        it = cat.prof.emplace(key, e).first;
+    } else {
+        CK(cudaStreamWaitEvent(ws.st, it->second.ready, 0));
+    }
+    it->second.last_use = ctx.tick;
+    *out = reinterpret_cast<const double *>(c.kde_mode == CHIMERA_KDE_SINGLE_1D ? it->second.Gh : it->second.G);
+    return CHIMERA_OK;
+}
+
+}  // namespace
+
+void adjoint_release(Ctx &ctx, Workspace &ws) {
+    if (ws.gscr) dev_free(ctx, ws.gscr, ws.gscr_bytes);
+    ws.gscr = nullptr;
+    ws.gscr_bytes = 0;
+    if (ws.ahstage) cudaFreeHost(ws.ahstage);
+    ws.ahstage = nullptr;
+    ws.ahstage_bytes = 0;
+}
+
+int backward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, int precision) {
+    const DevCatalog &c = cat.d;
+    const bool f64 = precision == CHIMERA_FP64;
+    const int nchunk = selection_chunks(c);
+    AdjLayout L(c, H, nchunk);
+    if (ws.gscr_bytes < L.total) {
+        if (ws.st) CK(cudaStreamSynchronize(ws.st));
+        if (ws.gscr) dev_free(ctx, ws.gscr, ws.gscr_bytes);
+        ws.gscr = nullptr;
+        ws.gscr_bytes = 0;
+        RC(dev_alloc(ctx, (void **)&ws.gscr, L.total));
+        ws.gscr_bytes = L.total;
+    }
+    const size_t hb = 2 * sizeof(void *) * (size_t)H;
+    if (ws.ahstage_bytes < hb) {
+        if (ws.st) CK(cudaStreamSynchronize(ws.st));
+        if (ws.ahstage) cudaFreeHost(ws.ahstage);
+        ws.ahstage = nullptr;
+        ws.ahstage_bytes = 0;
+        if (cudaMallocHost(&ws.ahstage, hb) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMallocHost failed for the adjoint staging buffer");
+            return CHIMERA_ERR_CUDA;
+        }
+        ws.ahstage_bytes = hb;
+    }
+    if (ws.trace) CK(cudaEventRecord(ws.tev[6], ws.st));
+    // the sanitised theta and the forward-table pointers forward() staged
+    const double *th = reinterpret_cast<const double *>(ws.hstage);
+    const double *const *fw =
+        reinterpret_cast<const double *const *>(ws.hstage + sizeof(double) * 12 * H + 8 * (size_t)H);
+    const double **hO = reinterpret_cast<const double **>(ws.ahstage);
+    const double **hP = hO + H;
+    std::map<uint64_t, std::pair<const double *, const double *>> byOm;
+    for (int h = 0; h < H; h++) {
+        const double Om = th[12 * h + 1];
+        const uint64_t key = bits_of(Om);
+        auto it = byOm.find(key);
+        if (it == byOm.end()) {
+            const double *fO = nullptr, *dG = nullptr;
+            RC(fwdO_table(ctx, Om, ws.st, &fO));
+            RC(dprofile(ctx, cat, ws, L, Om, f64, fw[h], fO, &dG));
+            it = byOm.emplace(key, std::make_pair(fO, dG)).first;
+        }
+        hO[h] = it->second.first;
+        hP[h] = it->second.second;
+    }
+    CK(cudaMemcpyAsync(ws.gscr + L.o_ptrs, ws.ahstage, hb, cudaMemcpyHostToDevice, ws.st));
+    AdjPtrs q;
+    q.fwdO = reinterpret_cast<const double *const *>(ws.gscr + L.o_ptrs);
+    q.dprof = q.fwdO + H;
+    q.hpd = reinterpret_cast<HPd *>(ws.gscr + L.o_hpd);
+    q.dznode = reinterpret_cast<double *>(ws.gscr + L.o_dzn);
+    q.Q = reinterpret_cast<double *>(ws.gscr + L.o_Q);
+    q.dlnI = reinterpret_cast<double *>(ws.gscr + L.o_dlnI);
+    q.selg = reinterpret_cast<double *>(ws.gscr + L.o_selg);
+    q.grad = ws.grad;
+    CallPtrs p = ws.ptrs(H, c);
+    launch_adjoint(c, p, q, H, f64, ws.st);
+    CK(cudaGetLastError());
+    if (ws.trace) {
+        CK(cudaEventRecord(ws.tev[7], ws.st));
+        ws.traced_adjoint = true;
+    }
+    return CHIMERA_OK;
 }
 
 }  // namespace chim

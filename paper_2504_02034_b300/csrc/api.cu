@@ -103,6 +103,7 @@ CallPtrs Workspace::ptrs(int H, const DevCatalog &c) const {
 }
 
 void ws_release(Ctx &ctx, Workspace &ws) {
+    adjoint_release(ctx, ws);
     for (void *a : ws.allocs) cudaFree(a);
     ws.allocs.clear();
     ctx.used -= ws.bytes;
@@ -182,13 +183,13 @@ int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat) {
 }
 
 // ------------------------------------------------------------ caches ----
-static uint64_t bits_of(double x) {
+uint64_t bits_of(double x) {
     uint64_t b;
     memcpy(&b, &x, 8);
     return b;
 }
 
-static int fwd_table(Ctx &ctx, double Om, cudaStream_t st, const double **out) {
+int fwd_table(Ctx &ctx, double Om, cudaStream_t st, const double **out) {
     uint64_t key = bits_of(Om);
     auto it = ctx.fwd.find(key);
     if (it == ctx.fwd.end()) {
@@ -206,7 +207,15 @@ static int fwd_table(Ctx &ctx, double Om, cudaStream_t st, const double **out) {
     return CHIMERA_OK;
 }
 
-static void evict_profiles(Ctx &ctx, Catalog &cat, size_t need) {
+void free_prof_entry(Ctx &ctx, ProfEntry &e) {
+    dev_free(ctx, e.G, e.bytes);
+    if (e.Gh) dev_free(ctx, e.Gh, e.hbytes);
+    if (e.ready) cudaEventDestroy(e.ready);
+    e.G = e.Gh = nullptr;
+    e.ready = nullptr;
+}
+
+void evict_profiles(Ctx &ctx, Catalog &cat, size_t need) {
     // least recently used first, never the ones touched by the current call
     while (ctx.used.load() + need > ctx.budget && !cat.prof.empty()) {
         auto victim = cat.prof.end();
@@ -216,9 +225,7 @@ static void evict_profiles(Ctx &ctx, Catalog &cat, size_t need) {
                 victim = it;
         if (victim == cat.prof.end()) return;
         cudaDeviceSynchronize();
-        dev_free(ctx, victim->second.G, victim->second.bytes);
-        if (victim->second.Gh) dev_free(ctx, victim->second.Gh, 0);
-        cudaEventDestroy(victim->second.ready);
+        free_prof_entry(ctx, victim->second);
         cat.prof.erase(victim);
     }
 }
@@ -238,6 +245,7 @@ static int profile(Ctx &ctx, Catalog &cat, Workspace &ws, double Om, int kind, c
         if (hb) {
             int rc = dev_alloc(ctx, &e.Gh, hb);
             if (rc) { dev_free(ctx, e.G, e.bytes); return rc; }
+            e.hbytes = hb;
         }
         CK(cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming));
         if (kind == 0)
@@ -707,11 +715,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
 }
 
 static void free_catalog(Ctx &ctx, Catalog &cat) {
-    for (auto &kv : cat.prof) {
-        dev_free(ctx, kv.second.G, kv.second.bytes);
-        if (kv.second.Gh) dev_free(ctx, kv.second.Gh, 0);
-        if (kv.second.ready) cudaEventDestroy(kv.second.ready);
-    }
+    for (auto &kv : cat.prof) free_prof_entry(ctx, kv.second);
     cat.prof.clear();
     for (void *a : cat.allocs) cudaFree(a);
     cat.allocs.clear();
@@ -786,6 +790,11 @@ void chimera_destroy(chimera_ctx *h) {
         cudaEventDestroy(kv.second.ready);
     }
     ctx.fwd.clear();
+    for (auto &kv : ctx.fwdO) {
+        dev_free(ctx, kv.second.table, sizeof(double) * NT_FWD);
+        cudaEventDestroy(kv.second.ready);
+    }
+    ctx.fwdO.clear();
     ws_release(ctx, ctx.ws);
     cudaStreamDestroy(ctx.stream);
     delete h;

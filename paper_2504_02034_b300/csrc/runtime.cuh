@@ -28,11 +28,14 @@ struct FwdEntry {
     cudaEvent_t ready = nullptr;
 };
 
-// Galaxy profile cache entry for one (Om, kind) of one catalog.
+// Galaxy profile cache entry for one (Om, kind) of one catalog.  Kinds:
+// 0 FP64 profile, 1 FP32 profile of the stored galaxy values, 2 FP64 dG/dOm,
+// 3 FP64 dG/dOm of the stored galaxy values.
 struct ProfEntry {
     void *G = nullptr;   // [n_pix x n_z] double (kind 0) or float (kind 1)
     void *Gh = nullptr;  // single-1D: [n_events x n_z]
-    size_t bytes = 0;
+    size_t bytes = 0;    // bytes of G
+    size_t hbytes = 0;   // bytes of Gh
     cudaEvent_t ready = nullptr;
     uint64_t last_use = 0;
 };
@@ -70,8 +73,10 @@ struct Workspace {
     float *invZ32 = nullptr;
     // adjoint buffers
     double *grad = nullptr;       // [H x 12]
-    double *gscr = nullptr;       // adjoint scratch
+    char *gscr = nullptr;         // adjoint scratch (allocated on the first gradient call)
     size_t gscr_bytes = 0;
+    char *ahstage = nullptr;      // pinned staging of the adjoint's pointer arrays
+    size_t ahstage_bytes = 0;
     // windowed-pair counters (roofline accounting), used when count_pairs
     unsigned long long *pairs = nullptr;
     bool count_pairs = false;
@@ -98,6 +103,7 @@ struct Ctx {
     std::map<int32_t, std::shared_ptr<Catalog>> cats;
     int32_t next_id = 0;
     std::unordered_map<uint64_t, FwdEntry> fwd;
+    std::unordered_map<uint64_t, FwdEntry> fwdO;  // dDhat/dOm tables (adjoint)
     Workspace ws;
     uint64_t tick = 0;
     Server *server = nullptr;
@@ -114,11 +120,17 @@ void ws_release(Ctx &ctx, Workspace &ws);
 // theta: host [H x 12].  Leaves lnL / neff / xi / status / lnI / bw on the
 // device in `ws`.  Returns a CHIMERA_ERR_* code.
 int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, int precision);
-// Adjoint after forward() on the same workspace; leaves grad [H x 12].
+// Adjoint after forward() on the same workspace (reads the sanitised theta
+// and the forward tables forward() left there); leaves grad [H x 12].
 int backward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, int precision);
-void launch_adjoint(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, double *grad,
-                    double *scratch, cudaStream_t st);
-size_t adjoint_scratch_bytes(const DevCatalog &c, int H);
+// Releases the adjoint's scratch of a workspace.
+void adjoint_release(Ctx &ctx, Workspace &ws);
+
+// Cache helpers shared by the forward and adjoint orchestration.
+uint64_t bits_of(double x);
+int fwd_table(Ctx &ctx, double Om, cudaStream_t st, const double **out);
+void evict_profiles(Ctx &ctx, Catalog &cat, size_t need);
+void free_prof_entry(Ctx &ctx, ProfEntry &e);
 
 std::shared_ptr<Catalog> find_catalog(Ctx &ctx, int32_t id);
 

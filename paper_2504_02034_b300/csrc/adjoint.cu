@@ -329,10 +329,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
     const int64_t s0 = c.ev_soff[ev];
     const int ns = (int)(c.ev_soff[ev + 1] - s0);
     const double KW = F64 ? KW64 : (double)KW32;
-    MixParams mp;
-    mp.c_pl = hp.c_pl32; mp.c_g = hp.c_g32; mp.alpha = hp.alpha32; mp.mu = hp.mu32;
-    mp.inv_sg = hp.inv_sg32; mp.mmin = hp.mmin32; mp.mmax = hp.mmax32; mp.beta = hp.beta32;
-    mp.b1 = hp.b1_32; mp.mmin_b1 = hp.mmin_b1_32; mp.lmmin = hp.lmmin32; mp.kv = hp.k_valid; mp.fv = hp.f_valid;
+    const MixParams mp = mix_params(hp);
     const float4 *inv = p.inv32 + (size_t)h * NU;
 
     // ---- z_j, w_j exactly as the forward kernel of this precision
@@ -349,9 +346,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
             int k = __float_as_int(s.x);
             if ((k < mp.kv) || (k == mp.kv && s.y <= mp.fv)) {
                 float zz = chimd::hermite4(inv[k], s.y);
-                if (isfinite(zz)) {
+                if (zz < CUDART_INF_F) {
                     z = zz;
-                    float lz = __logf(1.f + zz);
+                    float lz = __log2f(1.f + zz);
                     w = mass_weight32(mp, s.z - lz, s.w - lz);
                 }
             }
@@ -550,10 +547,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_select_adj(DevCatalog c, CallPt
     const double *th = hp.th;
     double acc[13];
     for (int k = 0; k < 13; k++) acc[k] = 0.0;
-    MixParams mp;
-    mp.c_pl = hp.c_pl32; mp.c_g = hp.c_g32; mp.alpha = hp.alpha32; mp.mu = hp.mu32;
-    mp.inv_sg = hp.inv_sg32; mp.mmin = hp.mmin32; mp.mmax = hp.mmax32; mp.beta = hp.beta32;
-    mp.b1 = hp.b1_32; mp.mmin_b1 = hp.mmin_b1_32; mp.lmmin = hp.lmmin32; mp.kv = hp.k_valid; mp.fv = hp.f_valid;
+    const MixParams mp = mix_params(hp);
     const int64_t base = (int64_t)chunk * SEL_CHUNK;
     const double inv_dc3 = 1.0 / (hp.dc_zmax * hp.dc_zmax * hp.dc_zmax);
     for (int qq = 0; qq < SEL_PER_THREAD; qq++) {

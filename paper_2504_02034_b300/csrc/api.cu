@@ -465,7 +465,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         tcoord(d->dL_Mpc[o], k, f);
         float kb;
         memcpy(&kb, &k, 4);
-        s32[j] = make_float4(kb, f, (float)std::log(d->m1_det[o]), (float)std::log(d->m2_det[o]));
+        s32[j] = make_float4(kb, f, (float)std::log2(d->m1_det[o]), (float)std::log2(d->m2_det[o]));
         sd[j] = d->dL_Mpc[o];
         sm1[j] = d->m1_det[o];
         sm2[j] = d->m2_det[o];
@@ -509,6 +509,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     std::vector<int4> groups;
     std::vector<int32_t> ev_goff(ne + 1, 0);
     std::vector<float2> ev_ref(ne);
+    std::vector<int2> ev_krange(ne);
     int max_groups = 1;
     for (int i = 0; i < ne; i++) {
         const int64_t a = d->sample_off[i], n = d->sample_off[i + 1] - a;
@@ -520,6 +521,17 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         }
         m /= n;
         const double sl = std::sqrt(std::max(m2 / n - m * m, 0.0)) * std::pow((double)n, -0.2);
+        {
+            int kmin = NU, kmax = 0;
+            for (int64_t j = a; j < a + n; j++) {
+                int k;
+                float f;
+                tcoord(sd[j], k, f);
+                kmin = std::min(kmin, k);
+                kmax = std::max(kmax, k);
+            }
+            ev_krange[i] = make_int2(kmin, kmax);
+        }
         // reference: the median d_L of the event
         std::vector<double> dd(sd.begin() + a, sd.begin() + a + n);
         std::nth_element(dd.begin(), dd.begin() + n / 2, dd.end());
@@ -637,6 +649,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         {(void **)&c.groups, groups.data(), 16 * groups.size()},
         {(void **)&c.ev_goff, ev_goff.data(), 4 * ev_goff.size()},
         {(void **)&c.ev_ref, ev_ref.data(), 8 * ev_ref.size()},
+        {(void **)&c.ev_krange, ev_krange.data(), 8 * ev_krange.size()},
         {(void **)&c.pix_S, pixS.data(), 8 * pixS.size()},
         {(void **)&c.gal_off, goff.data(), 8 * goff.size()},
         {(void **)&c.pix_sigmax, sigmax.data(), 8 * sigmax.size()},

@@ -213,6 +213,8 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
         hp.l1zp32 = (float)log1p(th[11]);
         hp.cH32 = (float)cH;
         hp.inv_dc3_32 = (float)(1.0 / (hp.dc_zmax * hp.dc_zmax * hp.dc_zmax));
+        hp.l2min32 = (float)log2(mmin);
+        hp.l2max32 = (float)log2(mmax);
         p.hp[h] = hp;
     }
 }

@@ -11,18 +11,19 @@
 //   I = sum_k pf_k sum_{j in k} w_j sum_a w_a phi_b(z_a - z_j) F(z_a) G_k(z_a)
 // with pf_k = S_k / N_k (many-1D) or 1 / N_s (single-1D, G summed over
 // pixels).  Samples are stored sorted by d_L inside each segment, hence by z
-// for every hyperpoint, and processed in warp groups of up to 64 neighbours.
+// for every hyperpoint, and processed in warp groups of up to 128 neighbours
+// (fixed at load time).
 //
-// Mixed kernel, fast path: for a group with origin grid index t_o the
-// Gaussian factorises on the uniform grid,
-//   exp(-(u - ds tau)^2) = exp(-u^2) * exp(2 u ds)^tau * exp(-ds^2 tau^2),
-// u = (z_j - z_o)/(sqrt2 b), ds = dz/(sqrt2 b), tau = a - t_o, so with the
-// per-group table D_tau = exp(-ds^2 tau^2) w'_a F(z_a) G(z_a) in shared
-// memory the inner loop is one multiply (P *= B) and one FMA (acc += P D)
-// per grid point and sample, with D read as a broadcast float4.  Two chains
-// per sample run outwards from the group centre.  Groups whose spread
-// exceeds 8 b, whose kernel is narrower than 1.4 grid steps, or whose table
-// would not fit, use a direct per-sample window with one exp per point.
+// Mixed kernel: for a group with origin grid index t_o the Gaussian
+// factorises on the uniform grid,
+//   exp(-(u - ds tau)^2) = exp(-u^2) * B^tau * C_tau,  B = exp(2 u ds),
+//   C_tau = exp(-ds^2 tau^2), u = (z_j - z_o)/(sqrt2 b), ds = dz/(sqrt2 b),
+// tau = a - t_o, so with the per-group table D_tau = C_tau w_a F(z_a) G(z_a)
+// in shared memory the sum over the grid is a polynomial in B (and one in
+// 1/B for tau < 0), evaluated by Horner's rule: one FFMA per (sample, grid
+// point), with D read as a broadcast float4 and up to four samples per lane.
+// Groups wider than 16 b use a per-lane Horner chain on their own windows;
+// kernels narrower than ~0.7 grid steps (ds > 2) use direct exponentials.
 //
 // FP64 kernel: the plain form, one exp per grid point and sample within
 // +-9 b, every quantity in double.
@@ -105,10 +106,12 @@ struct MixLayout {
         seg_pad = pad4(max_seg + 1);
         gmax_pad = pad4(max_groups);
     }
-    // floats: zs, ws, Fs, D tables, C table, group results; ints: segv
+    // int4: group metadata; floats: zs, ws, Fs, D tables, C table, group
+    // results, segment prefactors; ints: segment valid counts and starts
     __host__ __device__ size_t bytes() const {
-        return sizeof(float) * (2 * (size_t)ns_pad + nz_pad + (size_t)EV_WARPS * DCAP + CCAP + gmax_pad) +
-               sizeof(int) * (size_t)seg_pad + sizeof(double) * (8 + EV_WARPS * 8);
+        return sizeof(int4) * (size_t)gmax_pad +
+               sizeof(float) * (2 * (size_t)ns_pad + nz_pad + (size_t)EV_WARPS * DCAP + CCAP + gmax_pad + seg_pad) +
+               sizeof(int) * 2 * (size_t)seg_pad + sizeof(double) * (8 + EV_WARPS * 8);
     }
 };
 
@@ -118,8 +121,8 @@ struct MixLayout {
 // (sample, grid point).  The intermediates are partial sums divided by
 // exp(-u^2) B^tau, so they stay within the float range for |u| <= 3.1.
 template <int R>
-__device__ __forceinline__ void chains(const float *D, int nqb, int nqf, const float (&u)[R],
-                                       float ds, float lnscale, float (&acc)[R]) {
+__device__ __forceinline__ void chains(const float *D, int nq, const float (&u)[R], float ds, float lnscale,
+                                       float (&acc)[R]) {
     float A[R], B[R], Bi[R], af[R], ab[R];
 #pragma unroll
     for (int r = 0; r < R; r++) {
@@ -129,36 +132,14 @@ __device__ __forceinline__ void chains(const float *D, int nqb, int nqf, const f
         af[r] = 0.f;
         ab[r] = 0.f;
     }
-    const float4 *D0 = reinterpret_cast<const float4 *>(D) + nqb;  // tau = 0
-    // forward coefficients tau = 4q .. 4q+3 and backward tau = -4q-4 .. -4q-1
-    // are consumed together over the common length (two independent chains)
-    const int nc = min(nqf, nqb);
-    for (int q = max(nqf, nqb) - 1; q >= nc; q--) {
-        if (q < nqf) {
-            float4 d = D0[q];
-#pragma unroll
-            for (int r = 0; r < R; r++) {
-                af[r] = fmaf(af[r], B[r], d.w);
-                af[r] = fmaf(af[r], B[r], d.z);
-                af[r] = fmaf(af[r], B[r], d.y);
-                af[r] = fmaf(af[r], B[r], d.x);
-            }
-        } else {
-            float4 e = D0[-q - 1];
-#pragma unroll
-            for (int r = 0; r < R; r++) {
-                ab[r] = fmaf(ab[r], Bi[r], e.x);
-                ab[r] = fmaf(ab[r], Bi[r], e.y);
-                ab[r] = fmaf(ab[r], Bi[r], e.z);
-                ab[r] = fmaf(ab[r], Bi[r], e.w);
-            }
-        }
-    }
-    float4 dn = make_float4(0.f, 0.f, 0.f, 0.f), en = dn;
-    if (nc > 0) { dn = D0[nc - 1]; en = D0[-nc]; }
-    for (int q = nc - 1; q >= 0; q--) {
-        float4 d = dn, e = en;
-        if (q > 0) { dn = D0[q - 1]; en = D0[-q]; }
+    // the table holds tau in [-4 nq, 4 nq): forward coefficients
+    // tau = 4q .. 4q+3 from q = nq-1 down, backward tau = -4q-4 .. -4q-1
+    // from q = nq-1 down, consumed together (two independent chains)
+    const float4 *pf = reinterpret_cast<const float4 *>(D) + 2 * nq - 1;
+    const float4 *pb = reinterpret_cast<const float4 *>(D);
+#pragma unroll 2
+    for (int it = 0; it < nq; it++) {
+        const float4 d = pf[-it], e = pb[it];
 #pragma unroll
         for (int r = 0; r < R; r++) {
             af[r] = fmaf(af[r], B[r], d.w);
@@ -177,9 +158,8 @@ __device__ __forceinline__ void chains(const float *D, int nqb, int nqf, const f
 
 // R samples per lane (lane, lane+32, ...) of a group sharing one table.
 template <int R>
-__device__ __forceinline__ float union_samples(const float *D, int nqb, int nqf, const float *z,
-                                               const float *w, int cnt, int lane, float zo,
-                                               float inv_s2b, float ds, float lnscale) {
+__device__ __forceinline__ float union_samples(const float *D, int nq, const float *z, const float *w, int cnt,
+                                               int lane, float zo, float inv_s2b, float ds, float lnscale) {
     float u[R], ww[R], acc[R];
 #pragma unroll
     for (int r = 0; r < R; r++) {
@@ -188,11 +168,63 @@ __device__ __forceinline__ float union_samples(const float *D, int nqb, int nqf,
         u[r] = in ? (z[j] - zo) * inv_s2b : 0.f;
         ww[r] = in ? w[j] : 0.f;
     }
-    chains<R>(D, nqb, nqf, u, ds, lnscale, acc);
+    chains<R>(D, nq, u, ds, lnscale, acc);
     float v = 0.f;
 #pragma unroll
     for (int r = 0; r < R; r++) v = fmaf(ww[r], acc[r], v);
     return v;
+}
+
+// Asynchronous 16-byte global -> shared copies (cp.async, completion per
+// thread by commit groups).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Phase A staging inside the D-table region: a ring of RING chunks of
+// EV_THREADS samples and up to NODE_CAP inverse-table nodes.
+constexpr int RING = 4;
+constexpr int NODE_CAP = EV_WARPS * DCAP / 4 - RING * EV_THREADS;
+static_assert(NODE_CAP >= 256, "phase A staging does not fit the D-table region");
+
+// Warp-cooperative staging of a coefficient table: for idx < len and grid
+// point a = a_first + idx, D[idx] = C_|idx - tau0| * scale * F'(z_a) G(z_a)
+// (with the Gaussian factor when WITH_C, F' carrying the trapezoid weight),
+// zero outside [A0, A1].  The profile loads of up to eight entries per lane
+// are issued before any of them is used, so a table costs about one memory
+// latency per 256 entries instead of one per 32.
+template <bool WITH_C>
+__device__ __forceinline__ void stage_table(float *D, int len, int a_first, int A0, int A1, const float *G,
+                                            const float *Fs, const float *CT, int tau0, float scale, int lane) {
+    for (int i0 = 0; i0 < len; i0 += 8 * 32) {
+        float gv[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int idx = i0 + u * 32 + lane;
+            const int a = a_first + idx;
+            gv[u] = (idx < len && a >= A0 && a <= A1) ? __ldg(G + a) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int idx = i0 + u * 32 + lane;
+            if (idx < len) {
+                const int a = a_first + idx;
+                const float f = (a >= A0 && a <= A1) ? Fs[a] : 0.f;
+                float val = f * gv[u];
+                if (WITH_C) {
+                    const int tau = idx - tau0;
+                    val *= CT[tau < 0 ? -tau : tau] * scale;
+                }
+                D[idx] = val;
+            }
+        }
+    }
 }
 
 // Per-lane path for a sparse group: every lane runs its own window around
@@ -216,16 +248,18 @@ __device__ __forceinline__ float lane_chain(const float *Hc, const float *CT, in
 __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, CallPtrs p, int H) {
     extern __shared__ float4 smem4[];
     const MixLayout L(c.max_ns, c.n_z, c.max_seg, c.max_groups);
-    float *zs = reinterpret_cast<float *>(smem4);
+    int4 *grp = reinterpret_cast<int4 *>(smem4);
+    float *zs = reinterpret_cast<float *>(grp + L.gmax_pad);
     float *ws = zs + L.ns_pad;
     float *Fs = ws + L.ns_pad;
     float *Dt = Fs + L.nz_pad;
     float *CT = Dt + EV_WARPS * DCAP;
     float *gres = CT + CCAP;
-    int *segv = reinterpret_cast<int *>(gres + L.gmax_pad);
-    double *red = reinterpret_cast<double *>(segv + L.seg_pad);
+    float *segpf = gres + L.gmax_pad;
+    int *segv = reinterpret_cast<int *>(segpf + L.seg_pad);
+    int *seglo = segv + L.seg_pad;
+    double *red = reinterpret_cast<double *>(seglo + L.seg_pad);
     __shared__ int s_gctr;
-    __shared__ float s_f[8];  // block scalars computed once by thread 0
 
     const int h = blockIdx.x % H;
     const int ev = c.ev_order[blockIdx.x / H];
@@ -236,16 +270,25 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
         if (tid == 0) { p.lnI[out] = 0.0; p.bw[out] = 0.0; }
         return;
     }
-    MixParams q;
-    q.c_pl = hp.c_pl32; q.c_g = hp.c_g32; q.alpha = hp.alpha32;
-    q.mu = hp.mu32; q.inv_sg = hp.inv_sg32; q.mmin = hp.mmin32;
-    q.mmax = hp.mmax32; q.beta = hp.beta32; q.b1 = hp.b1_32;
-    q.mmin_b1 = hp.mmin_b1_32; q.lmmin = hp.lmmin32; q.kv = hp.k_valid; q.fv = hp.f_valid;
+    const MixParams q = mix_params(hp);
 
     const int nz = c.n_z;
     const float dz = c.dz32;
-    for (int a = tid; a < nz; a += EV_THREADS) Fs[a] = p.F32[(size_t)h * nz + a];
+    const float inv_dz = 1.f / dz;
+    // F(z_a) with the trapezoid weight folded in
+    for (int a = tid; a < nz; a += EV_THREADS)
+        Fs[a] = p.F32[(size_t)h * nz + a] * ((a == 0 || a == nz - 1) ? 0.5f : 1.f);
     if (tid == 0) s_gctr = 0;
+    // group and segment metadata of this event, staged once (the loads
+    // overlap phase A)
+    const int g0 = c.ev_goff[ev];
+    const int ngroups = c.ev_goff[ev + 1] - g0;
+    const int sg0 = c.ev_segoff[ev], nseg = c.ev_segoff[ev + 1] - sg0;
+    for (int g = tid; g < ngroups; g += EV_THREADS) grp[g] = __ldg(c.groups + g0 + g);
+    for (int k = tid; k <= nseg; k += EV_THREADS) {
+        seglo[k] = (int)(c.seg_soff[sg0 + k] - c.ev_soff[ev]);
+        if (k < nseg) segpf[k] = (float)c.seg_pf[sg0 + k];
+    }
 
     // ---- phase A: z_j, w_j and one-pass moments about the redshift of the
     // event's median d_L (shifted sums: no cancellation in the variance)
@@ -261,60 +304,79 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
         if (!isfinite(zref)) zref = 0.f;
     }
     float m[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // W1, Wd, Wd2, W2, n, Sd, Sd2
-    for (int j0 = tid; j0 < ns; j0 += 4 * EV_THREADS) {
-        float4 sv[4];
+    const float4 *sp = c.s32 + s0;
+    // one sample: table coordinate -> z (Hermite on the node pair), log2
+    // source masses, weight, moments; invalid samples (beyond d_L^gw(10))
+    // get z = inf and w = 0 and stay out of the moments
+    auto sample = [&](const float4 &sv, const float4 &nd, int j) {
+        const float z = chimd::hermite4(nd, sv.y);
+        const bool ok = z < CUDART_INF_F;  // false for inf and NaN
+        const float lz = __log2f(1.f + z);
+        float w = mass_weight32(q, sv.z - lz, sv.w - lz);
+        w = ok ? w : 0.f;
+        const float d = ok ? z - zref : 0.f;
+        const float wd = w * d;
+        m[0] += w; m[1] += wd; m[2] = fmaf(wd, d, m[2]); m[3] = fmaf(w, w, m[3]);
+        m[4] += ok ? 1.f : 0.f; m[5] += d; m[6] = fmaf(d, d, m[6]);
+        zs[j] = ok ? z : CUDART_INF_F;
+        ws[j] = w;
+    };
+    // The samples stream through a ring of RING chunks of EV_THREADS float4
+    // in shared memory (cp.async, RING-1 chunks ahead; each thread copies and
+    // reads only its own slot), and the inverse-table nodes of the event's
+    // d_L range are staged once, so the per-sample node gather is a shared
+    // load.  Both live in the D-table region, which phase B reuses.
+    float4 *ring = reinterpret_cast<float4 *>(Dt);
+    float4 *snode = ring + RING * EV_THREADS;
+    const int2 kr = c.ev_krange[ev];
+    const bool staged = kr.y - kr.x < NODE_CAP;  // block-uniform
+    if (staged)
+        for (int i = tid; i <= kr.y - kr.x; i += EV_THREADS) cp_async16(snode + i, inv + kr.x + i);
 #pragma unroll
-        for (int uu = 0; uu < 4; uu++) {
-            int j = j0 + uu * EV_THREADS;
-            sv[uu] = j < ns ? __ldg(c.s32 + s0 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        float4 nd[4];
-#pragma unroll
-        for (int uu = 0; uu < 4; uu++) {
-            int k = __float_as_int(sv[uu].x);
-            bool valid = (j0 + uu * EV_THREADS < ns) && ((k < q.kv) || (k == q.kv && sv[uu].y <= q.fv));
-            nd[uu] = valid ? __ldg(inv + k) : make_float4(CUDART_INF_F, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int uu = 0; uu < 4; uu++) {
-            int j = j0 + uu * EV_THREADS;
-            if (j >= ns) break;
-            float z = CUDART_INF_F, w = 0.f;
-            float zz = chimd::hermite4(nd[uu], sv[uu].y);
-            if (isfinite(zz)) {
-                z = zz;
-                float lz = __logf(1.f + z);
-                w = mass_weight32(q, sv[uu].z - lz, sv[uu].w - lz);
-                float d = z - zref;
-                m[0] += w; m[1] += w * d; m[2] += w * d * d; m[3] += w * w;
-                m[4] += 1.f; m[5] += d; m[6] += d * d;
-            }
-            zs[j] = z;
-            ws[j] = w;
+    for (int cc = 0; cc < RING - 1; cc++) {
+        const int jj = cc * EV_THREADS + tid;
+        if (jj < ns) cp_async16(ring + cc * EV_THREADS + tid, sp + jj);
+        cp_async_commit();
+    }
+    cp_async_wait<RING - 2>();  // the nodes and chunk 0 of this thread
+    __syncthreads();            // every thread's node copies
+    const int nch = (ns + EV_THREADS - 1) / EV_THREADS;
+    for (int cc = 0; cc < nch; cc++) {
+        const int jn = (cc + RING - 1) * EV_THREADS + tid;
+        if (jn < ns) cp_async16(ring + ((cc + RING - 1) % RING) * EV_THREADS + tid, sp + jn);
+        cp_async_commit();
+        cp_async_wait<RING - 1>();  // chunk cc of this thread
+        const int j = cc * EV_THREADS + tid;
+        if (j < ns) {
+            const float4 sv = ring[(cc % RING) * EV_THREADS + tid];
+            const int k = __float_as_int(sv.x);
+            const bool valid = (k < q.kv) || (k == q.kv && sv.y <= q.fv);
+            const float4 nd = !valid ? make_float4(CUDART_INF_F, 0.f, 0.f, 0.f)
+                                     : (staged ? snode[k - kr.x] : __ldg(inv + k));
+            sample(sv, nd, j);
         }
     }
     block_sum<7, EV_THREADS>(m, red);
-    if (tid == 0) {
-        // Scott's rule in FP32 (the mixed path's precision): weighted, then
-        // unweighted, then the grid spacing
-        const double W1 = red[0], n = red[4];
-        float bl = dz;
+    // Scott's rule in FP32 (the mixed path's precision), every thread from
+    // the same block sums: weighted, then unweighted, then the grid spacing
+    float bl = dz;
+    {
+        const float W1 = (float)red[0], n = (float)red[4];
         bool done = false;
-        if (W1 > 0.0) {
-            double mw = red[1] / W1, var = red[2] / W1 - mw * mw, neff = W1 * W1 / red[3];
-            if (neff >= 2.0 && var > 0.0) {
-                bl = sqrtf((float)var) * exp2f(-0.2f * log2f((float)neff));
+        if (W1 > 0.f) {
+            const float mw = (float)red[1] / W1, var = (float)red[2] / W1 - mw * mw;
+            const float neff = W1 * W1 / (float)red[3];
+            if (neff >= 2.f && var > 0.f) {
+                bl = sqrtf(var) * exp2f(-0.2f * log2f(neff));
                 done = true;
             }
         }
-        if (!done && n >= 2.0) {
-            double mu = red[5] / n, var = red[6] / n - mu * mu;
-            if (var > 0.0) bl = sqrtf((float)var) * exp2f(-0.2f * log2f((float)n));
+        if (!done && n >= 2.f) {
+            const float mu = (float)red[5] / n, var = (float)red[6] / n - mu * mu;
+            if (var > 0.f) bl = sqrtf(var) * exp2f(-0.2f * log2f(n));
         }
-        s_f[2] = bl;
     }
-    __syncthreads();
-    const float b = s_f[2];
+    const float b = bl;
     const double bd = (double)b;
     const float inv_s2b = 0.70710678f / b;
     const float ds = dz * inv_s2b;
@@ -325,9 +387,8 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
         float x = ds * (float)t;
         CT[t] = __expf(-x * x);
     }
-    const int sg0 = c.ev_segoff[ev], nseg = c.ev_segoff[ev + 1] - sg0;
     for (int k = tid; k < nseg; k += EV_THREADS) {
-        int lo = (int)(c.seg_soff[sg0 + k] - s0), hi = (int)(c.seg_soff[sg0 + k + 1] - s0);
+        int lo = seglo[k], hi = seglo[k + 1];
         int l = lo, r = hi;
         while (l < r) {
             int mm = (l + r) >> 1;
@@ -336,101 +397,83 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
         segv[k] = l - lo;
     }
     __syncthreads();
-    const int g0 = c.ev_goff[ev];
-    const int ngroups = c.ev_goff[ev + 1] - g0;
 
     // ---- phase B: groups taken dynamically by warps; each group's value is
     // computed by a fixed lane assignment and stored in its own slot, and the
     // slots are added in group order, so the result does not depend on timing.
     float *D = Dt + wid * DCAP;
     const float *prof = reinterpret_cast<const float *>(p.prof[h]);
-    const int Tw = (int)ceilf(halfk / dz + 0.5f);
+    const int Tw = (int)ceilf(halfk * inv_dz + 0.5f);
     unsigned long long npairs = 0;  // algorithmic pair count (roofline only)
     while (true) {
         int g = 0;
         if (lane == 0) g = atomicAdd(&s_gctr, 1);
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= ngroups) break;
-        const int4 gi = __ldg(c.groups + g0 + g);
+        const int4 gi = grp[g];
         const int sk = gi.z;
-        const int seg_lo = (int)(c.seg_soff[sg0 + sk] - s0);
+        const int seg_lo = seglo[sk];
         const int lo = gi.x;
         const int cnt = min(gi.y, segv[sk] - (lo - seg_lo));  // valid samples only
         float v = 0.f;
         if (cnt > 0) {
-            const float pf = (float)c.seg_pf[sg0 + sk];
+            const float pf = segpf[sk];
             const int64_t row = c.kde_mode == CHIMERA_KDE_MANY_1D ? (int64_t)(sg0 + sk) : (int64_t)ev;
             const float *G = prof + row * nz;
             // KDE support of this segment: its samples' range +- KDE_MARGIN b
-            const int s_lo = max(0, (int)ceilf((zs[seg_lo] - (float)KDE_MARGIN * b) / dz));
-            const int s_hi = min(nz - 1, (int)floorf((zs[seg_lo + segv[sk] - 1] + (float)KDE_MARGIN * b) / dz));
+            const int s_lo = max(0, (int)ceilf((zs[seg_lo] - (float)KDE_MARGIN * b) * inv_dz));
+            const int s_hi = min(nz - 1, (int)floorf((zs[seg_lo + segv[sk] - 1] + (float)KDE_MARGIN * b) * inv_dz));
             const float zlo = zs[lo], zhi = zs[lo + cnt - 1];
             const float spread = zhi - zlo;
             if (p.pairs) {
                 for (int j = lane; j < cnt; j += 32) {
                     float z = zs[lo + j];
                     if (ws[lo + j] == 0.f) continue;
-                    int a0 = max(s_lo, (int)ceilf((z - halfk) / dz));
-                    int a1 = min(s_hi, (int)floorf((z + halfk) / dz));
+                    int a0 = max(s_lo, (int)ceilf((z - halfk) * inv_dz));
+                    int a1 = min(s_hi, (int)floorf((z + halfk) * inv_dz));
                     if (a1 >= a0) npairs += (unsigned long long)(a1 - a0 + 1);
                 }
             }
             // grid range the group can touch
-            const float fA0 = floorf((zlo - halfk) / dz), fA1 = ceilf((zhi + halfk) / dz);
+            const float fA0 = floorf((zlo - halfk) * inv_dz), fA1 = ceilf((zhi + halfk) * inv_dz);
             const int A0 = fA0 < (float)s_lo ? s_lo : (int)fA0;
             const int A1 = fA1 > (float)s_hi ? s_hi : (int)fA1;
             if (A0 <= A1) {
-                const float tof = rintf(0.5f * (zlo + zhi) / dz);
+                const float tof = rintf(0.5f * (zlo + zhi) * inv_dz);
                 const int t_o = tof > 1e8f ? 100000000 : (int)tof;
                 const int thi = A1 - t_o, tlo = t_o - A0;  // tau in [-tlo, thi]
                 const int nqf = thi >= 0 ? (thi + 4) >> 2 : 0;
                 const int nqb = tlo >= 1 ? (tlo + 3) >> 2 : 0;
+                const int nq = max(nqf, nqb);  // symmetric table, zero-padded
                 // shared origin for spreads up to 16 b; beyond 8 b the table is
                 // scaled by e^20 (undone in A) to keep every relevant
                 // coefficient and Horner intermediate in the normal float range
                 const bool uni = ds <= 0.5f && spread <= 16.f * b && thi >= -1 && tlo >= 0 &&
-                                 4 * (nqf + nqb) <= DCAP && 4 * max(nqf, nqb) < CCAP;
+                                 8 * nq <= DCAP && 4 * nq < CCAP;
                 if (uni) {
                     const float lnscale = spread > 8.f * b ? 20.f : 0.f;
                     const float scale = spread > 8.f * b ? 4.85165195e8f : 1.f;  // e^20
                     __syncwarp();
-                    for (int idx = lane; idx < 4 * (nqf + nqb); idx += 32) {
-                        int tau = idx - 4 * nqb;
-                        int a = t_o + tau;
-                        float val = 0.f;
-                        if (a >= A0 && a <= A1) {
-                            float wa = (a == 0 || a == nz - 1) ? 0.5f : 1.f;
-                            val = CT[tau < 0 ? -tau : tau] * scale * wa * Fs[a] * __ldg(G + a);
-                        }
-                        D[idx] = val;
-                    }
+                    stage_table<true>(D, 8 * nq, t_o - 4 * nq, A0, A1, G, Fs, CT, 4 * nq, scale, lane);
                     __syncwarp();
                     const float zo = t_o * dz;
                     switch ((cnt + 31) >> 5) {
-                        case 1: v = union_samples<1>(D, nqb, nqf, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale); break;
-                        case 2: v = union_samples<2>(D, nqb, nqf, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale); break;
-                        case 3: v = union_samples<3>(D, nqb, nqf, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale); break;
-                        default: v = union_samples<4>(D, nqb, nqf, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale); break;
+                        case 1: v = union_samples<1>(D, nq, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale); break;
+                        case 2: v = union_samples<2>(D, nq, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale); break;
+                        case 3: v = union_samples<3>(D, nq, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale); break;
+                        default: v = union_samples<4>(D, nq, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale); break;
                     }
                 } else if (ds <= 2.f && Tw + 2 < CCAP && (A1 - A0 + 1) + 2 * Tw + 4 <= DCAP) {
                     // stage H' on [base, base + span) with zeros outside [A0, A1]
                     const int base = A0 - Tw - 2, span = (A1 - A0 + 1) + 2 * Tw + 4;
                     __syncwarp();
-                    for (int i = lane; i < span; i += 32) {
-                        int a = base + i;
-                        float val = 0.f;
-                        if (a >= A0 && a <= A1) {
-                            float wa = (a == 0 || a == nz - 1) ? 0.5f : 1.f;
-                            val = wa * Fs[a] * __ldg(G + a);
-                        }
-                        D[i] = val;
-                    }
+                    stage_table<false>(D, span, base, A0, A1, G, Fs, CT, 0, 1.f, lane);
                     __syncwarp();
                     for (int j = lane; j < cnt; j += 32) {
                         float w = ws[lo + j];
                         if (w == 0.f) continue;
                         float z = zs[lo + j];
-                        int ts = (int)rintf(fminf(z / dz, 1e8f));
+                        int ts = (int)rintf(fminf(z * inv_dz, 1e8f));
                         ts = min(max(ts, A0 - 1), A1 + 1);
                         // a sample further than its window from [A0, A1] adds nothing
                         // (and would push exp(2 u ds) out of range)
@@ -441,13 +484,12 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
                     for (int j = lane; j < cnt; j += 32) {
                         float z = zs[lo + j], w = ws[lo + j];
                         if (w == 0.f) continue;
-                        int a0 = max(A0, (int)ceilf((z - halfk) / dz));
-                        int a1 = min(A1, (int)floorf((z + halfk) / dz));
+                        int a0 = max(A0, (int)ceilf((z - halfk) * inv_dz));
+                        int a1 = min(A1, (int)floorf((z + halfk) * inv_dz));
                         float sacc = 0.f;
                         for (int a = a0; a <= a1; a++) {
                             float x = (a * dz - z) * inv_s2b;
-                            float wa = (a == 0 || a == nz - 1) ? 0.5f : 1.f;
-                            sacc += expf(-x * x) * wa * Fs[a] * G[a];
+                            sacc += expf(-x * x) * Fs[a] * G[a];
                         }
                         v += w * sacc;
                     }

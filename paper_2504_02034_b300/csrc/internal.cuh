@@ -60,6 +60,7 @@ struct HP {
     // that no kernel thread runs FP64 conversions or divisions)
     float c_pl32, c_g32, alpha32, mu32, inv_sg32, mmin32, mmax32, beta32, b1_32, mmin_b1_32,
         lmmin32, xi0_32, n32, om32, gam32, kap32, l1zp32, cH32, inv_dc3_32;
+    float l2min32, l2max32;  // log2 m_min, log2 m_max
 };
 
 // Resident catalog (device pointers unless noted).
@@ -86,6 +87,7 @@ struct DevCatalog {
     int32_t *ev_goff;     // [n_events+1] group offsets per event
     int32_t max_groups;   // most groups of any event
     float2 *ev_ref;       // [n_events] inverse-table (k bits, f) of the event's median d_L
+    int2 *ev_krange;      // [n_events] smallest and largest inverse-table interval of its samples
     // pixels
     double *pix_S;        // [n_pix]
     int64_t *gal_off;     // [n_pix+1], galaxies sorted by z inside a pixel
@@ -97,7 +99,7 @@ struct DevCatalog {
     float *gz32, *gs32;   // F32 storage
     uint16_t *gzq, *gsq;  // F16/BF16 storage (z as offset from pix_zref)
     // PE samples
-    float4 *s32;          // (inverse-table interval k as int bits, fraction f, ln m1_det, ln m2_det)
+    float4 *s32;          // (inverse-table interval k as int bits, fraction f, log2 m1_det, log2 m2_det)
     double *sd64, *sm1_64, *sm2_64;
     // detected injections
     float4 *i32a;         // (k bits, f, ln m1_det, ln m2_det)

@@ -9,28 +9,67 @@
 
 namespace chim {
 
+// 2^x by the SFU (PTX ex2.approx.ftz: relative error ~2^-22, 0 for very
+// negative x).
+inline __device__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// FP32 mass-model constants of one hyperpoint, in the log2 domain: the
+// weight is built from exp2 / log2 of the SFU (relative error ~1e-6 per
+// sample, independent between samples).
 struct MixParams {
-    float c_pl, c_g, alpha, mu, inv_sg, mmin, mmax, beta, b1, mmin_b1, lmmin;
+    float c_pl, c_g, mu, inv_sg, mmin_b1, b1;
+    float na2;     // -alpha             (m1^-alpha   = 2^(na2 l1))
+    float gk;      // -log2(e)/2 / sg^2 folded with (m1 - mu): 2^(gk x^2), x = m1 - mu
+    float beta;    //                     (m2^beta    = 2^(beta l2))
+    float l2min, l2max;
+    float inv_lmin_ln2;  // beta = -1 form: 1 / ln 2
+    bool logp2;    // beta == -1: p(m2|m1) = 1 / (m2 ln(m1 / m_min))
     int kv;
     float fv;
 };
 
-// Mass-model weight p(m1) p(m2|m1) from log source-frame masses, with the
-// SFU exponential (relative error ~1e-6, independent between samples).
-inline __device__ float mass_weight32(const MixParams &q, float lm1, float lm2) {
-    float m1 = __expf(lm1), m2 = __expf(lm2);
-    if (!(m1 >= q.mmin && m1 <= q.mmax && m2 >= q.mmin && m2 <= m1)) return 0.f;
-    float x = (m1 - q.mu) * q.inv_sg;
-    float p1 = q.c_pl * __expf(-q.alpha * lm1) + q.c_g * __expf(-0.5f * x * x);
+inline __device__ MixParams mix_params(const HP &hp) {
+    MixParams q;
+    q.c_pl = hp.c_pl32;
+    q.c_g = hp.c_g32;
+    q.mu = hp.mu32;
+    q.inv_sg = hp.inv_sg32;
+    q.mmin_b1 = hp.mmin_b1_32;
+    q.b1 = hp.b1_32;
+    q.na2 = -hp.alpha32;
+    q.gk = -0.72134752044448170368f * hp.inv_sg32 * hp.inv_sg32;
+    q.beta = hp.beta32;
+    q.l2min = hp.l2min32;
+    q.l2max = hp.l2max32;
+    q.inv_lmin_ln2 = 1.44269504088896340736f;
+    q.logp2 = fabsf(hp.b1_32) < 1e-6f;
+    q.kv = hp.k_valid;
+    q.fv = hp.f_valid;
+    return q;
+}
+
+// Mass-model weight p(m1) p(m2|m1) (Sec. 3.1) from log2 source-frame masses
+// l1 = log2 m1, l2 = log2 m2; zero outside m_min <= m2 <= m1 <= m_max.
+// Branch-free apart from the hyperpoint-uniform beta = -1 form.
+inline __device__ float mass_weight32(const MixParams &q, float l1, float l2) {
+    const float m1 = ex2(l1);
+    const float x = m1 - q.mu;
+    const float p1 = q.c_pl * ex2(q.na2 * l1) + q.c_g * ex2(q.gk * x * x);
     float p2;
-    if (fabsf(q.b1) < 1e-6f) {
-        float l = lm1 - q.lmmin;
-        p2 = l > 0.f ? __fdividef(1.f, m2 * l) : 0.f;
+    if (q.logp2) {
+        const float m2 = ex2(l2);
+        const float l = l1 - q.l2min;
+        p2 = l > 0.f ? __fdividef(q.inv_lmin_ln2, m2 * l) : 0.f;
     } else {
-        float den = m1 * __expf(q.beta * lm1) - q.mmin_b1;
-        p2 = den > 0.f ? __fdividef(q.b1 * __expf(q.beta * lm2), den) : 0.f;
+        const float den = ex2(q.b1 * l1) - q.mmin_b1;
+        p2 = den > 0.f ? __fdividef(q.b1 * ex2(q.beta * l2), den) : 0.f;
     }
-    return p1 * p2;
+    const bool in = (l2 >= q.l2min) & (l2 <= l1) & (l1 <= q.l2max);
+    return in ? p1 * p2 : 0.f;
 }
 
 inline __device__ double mass_weight64(const HP &hp, double beta, double m1, double m2) {

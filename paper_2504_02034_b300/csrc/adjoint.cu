@@ -24,6 +24,7 @@
 //   ln s = ln p(m1,m2) + ln psi(z) + ln p_z(z) - 3 ln(1+z) - ln J(z) - ln pi_inj,
 // with the chain through z_j for the cosmological parameters.
 #include <algorithm>
+#include <type_traits>
 #include <map>
 
 #include <cuda_fp16.h>
@@ -39,6 +40,7 @@ struct HPd {
     double dlc_pl[3];  // d ln c_pl / d(alpha, m_min, m_max)
     double dlc_g[4];   // d ln c_g / d(mu_g, sigma_g, m_min, m_max)
     double dlpz_zmax;  // d ln [1 / V_c(z_max)] / dOm
+    float dlc_pl32[3], dlc_g32[4], dlpz_zmax32;  // FP32 copies (mixed adjoint)
 };
 
 // Device views of the adjoint's inputs and scratch.
@@ -47,7 +49,9 @@ struct AdjPtrs {
     const double *const *dprof;  // [H] dG/dOm profile of h's Om (rows as the forward profile)
     HPd *hpd;                    // [H]
     double *dznode;              // [H x (NU+1) x 4] dz/d(H0, Om, Xi0, n) at the inverse-table nodes
+    float4 *dznode32;            // [H x (NU+1)] FP32 copy
     double *Q;                   // [H x n_z x 7] d ln F / d(H0, Om, Xi0, n, gamma, kappa, z_p)
+    float *Q32;                  // [H x n_z x 8] FP32 copy, padded to 8
     double *dlnI;                // [H x n_events x 12]
     double *selg;                // [H x n_chunk x 13] sum s dln s / dtheta (12), sum s
     double *grad;                // [H x 12]
@@ -127,89 +131,125 @@ __device__ __forceinline__ double dcO_hermite(const double *fwdO, double z, doub
            (f3 - f2) * m1;
 }
 
-// Derivatives of the distance relation at redshift z for one hyperpoint.
-struct ZDer {
-    double dz[4];     // dz/d(H0, Om, Xi0, n) at fixed d_L
-    double dlnJ[4];   // d ln J / d(H0, Om, Xi0, n) at fixed z
-    double dlnJ_dz;   // d ln J / dz
-    double dlnpz_dOm; // d ln p_z / dOm at fixed z (p_z = dV/dz / V(z_max))
-    double dlnpz_dz;
+// Derivatives of the distance relation at redshift z for one hyperpoint
+// (Eq. dL-mg and its z-derivative J), given Dh = D_c / (c/H0) and
+// DhO = dDh/dOm at z.
+template <typename T>
+struct ZDerT {
+    T dz[4];      // dz/d(H0, Om, Xi0, n) at fixed d_L
+    T dlnJ[4];    // d ln J / d(H0, Om, Xi0, n) at fixed z
+    T dlnJ_dz;    // d ln J / dz
+    T dlnpz_dOm;  // d ln p_z / dOm at fixed z (p_z = dV/dz / V(z_max))
+    T dlnpz_dz;
 };
+using ZDer = ZDerT<double>;
 
-__device__ ZDer zder(double z, const double *th, const double *fwd, const double *fwdO, double dlpz_zmax) {
-    ZDer r;
-    const double H0 = th[0], Om = th[1], Xi0 = th[2], n = th[3];
-    const double cH = C_KMS / H0, a = 1.0 + z;
-    const double Dh = chimd::dc_hermite(fwd, z, Om), DhO = dcO_hermite(fwdO, z, Om);
-    const double E = chimd::E_of(z, Om), iE = 1.0 / E;
-    const double D = cH * Dh, DO = cH * DhO;
-    const double la = log(a), pw = exp(-n * la);
-    const double xi = Xi0 + (1.0 - Xi0) * pw, dxi = -n * (1.0 - Xi0) * pw / a;
-    const double P = D + a * cH * iE;  // d d_L^em / dz
-    const double J = P * xi + a * D * dxi;
-    const double d = a * D * xi;
-    const double dd[4] = {-d / H0, a * DO * xi, a * D * (1.0 - pw), -a * D * (1.0 - Xi0) * la * pw};
+template <typename T>
+__device__ ZDerT<T> zder_t(T z, T H0, T Om, T Xi0, T n, T Dh, T DhO, T dlpz_zmax) {
+    ZDerT<T> r;
+    const T one = T(1), cH = T(C_KMS) / H0, a = one + z;
+    const T E = sqrt(Om * a * a * a + one - Om), iE = one / E;
+    const T D = cH * Dh, DO = cH * DhO;
+    const T la = log(a), pw = exp(-n * la);
+    const T xi = Xi0 + (one - Xi0) * pw, dxi = -n * (one - Xi0) * pw / a;
+    const T P = D + a * cH * iE;  // d d_L^em / dz
+    const T J = P * xi + a * D * dxi;
+    const T d = a * D * xi;
+    const T dd[4] = {-d / H0, a * DO * xi, a * D * (one - pw), -a * D * (one - Xi0) * la * pw};
     for (int k = 0; k < 4; k++) r.dz[k] = -dd[k] / J;
-    const double diE_dOm = -(a * a * a - 1.0) * 0.5 * iE * iE * iE;
-    const double dxi_dn = -(1.0 - Xi0) * la * pw, ddxi_dn = (1.0 - Xi0) * (pw / a) * (n * la - 1.0);
-    const double dJ[4] = {-J / H0, (DO + a * cH * diE_dOm) * xi + a * DO * dxi,
-                          P * (1.0 - pw) + a * D * n * pw / a, P * dxi_dn + a * D * ddxi_dn};
+    const T diE_dOm = -(a * a * a - one) * T(0.5) * iE * iE * iE;
+    const T dxi_dn = -(one - Xi0) * la * pw, ddxi_dn = (one - Xi0) * (pw / a) * (n * la - one);
+    const T dJ[4] = {-J / H0, (DO + a * cH * diE_dOm) * xi + a * DO * dxi, P * (one - pw) + D * n * pw,
+                     P * dxi_dn + a * D * ddxi_dn};
     for (int k = 0; k < 4; k++) r.dlnJ[k] = dJ[k] / J;
-    const double Ep = 1.5 * Om * a * a * iE;  // dE/dz
-    const double d2xi = n * (n + 1.0) * (1.0 - Xi0) * pw / (a * a);
-    const double dJdz = (2.0 * cH * iE - a * cH * Ep * iE * iE) * xi + P * dxi + (D + a * cH * iE) * dxi + a * D * d2xi;
+    const T Ep = T(1.5) * Om * a * a * iE;  // dE/dz
+    const T d2xi = n * (n + one) * (one - Xi0) * pw / (a * a);
+    const T dJdz = (T(2) * cH * iE - a * cH * Ep * iE * iE) * xi + T(2) * P * dxi + a * D * d2xi;
     r.dlnJ_dz = dJdz / J;
-    r.dlnpz_dOm = 2.0 * DhO / Dh - (a * a * a - 1.0) * 0.5 * iE * iE + dlpz_zmax;
-    r.dlnpz_dz = 2.0 * iE / Dh - Ep * iE;
+    r.dlnpz_dOm = T(2) * DhO / Dh - (a * a * a - one) * T(0.5) * iE * iE + dlpz_zmax;
+    r.dlnpz_dz = T(2) * iE / Dh - Ep * iE;
     return r;
 }
 
+__device__ ZDer zder(double z, const double *th, const double *fwd, const double *fwdO, double dlpz_zmax) {
+    return zder_t<double>(z, th[0], th[1], th[2], th[3], chimd::dc_hermite(fwd, z, th[1]),
+                          dcO_hermite(fwdO, z, th[1]), dlpz_zmax);
+}
+
 // d ln psi / d(gamma, kappa, z_p) and d ln psi / dz (Sec. 3.1)
-__device__ void dlnpsi(double z, const double *th, double *g3, double *dz) {
-    const double gam = th[9], kap = th[10], zp = th[11], a = 1.0 + z;
-    const double L = log(a / (1.0 + zp));
-    const double x = exp((gam + kap) * L);
-    const double r = x / (1.0 + x);
+template <typename T>
+__device__ void dlnpsi_t(T z, T gam, T kap, T zp, T *g3, T *dz) {
+    const T one = T(1), a = one + z;
+    const T L = log(a / (one + zp));
+    const T x = exp((gam + kap) * L);
+    const T r = x / (one + x);
     g3[0] = log(a) - r * L;
     g3[1] = -r * L;
-    g3[2] = r * (gam + kap) / (1.0 + zp);
+    g3[2] = r * (gam + kap) / (one + zp);
     *dz = gam / a - r * (gam + kap) / a;
+}
+__device__ void dlnpsi(double z, const double *th, double *g3, double *dz) {
+    dlnpsi_t<double>(z, th[9], th[10], th[11], g3, dz);
 }
 
 // Mass-model log-derivatives for source masses (m1, m2): direct derivatives
 // d ln p / d(alpha, mu, sigma, m_min, m_max) and d ln p / dz through
 // m = m_det / (1+z).  Zero when the weight is zero.
-__device__ void dlnpm(const HP &hp, const HPd &hd, double beta, double m1, double m2, double a,
-                      double *d5, double *ddz) {
-    for (int k = 0; k < 5; k++) d5[k] = 0.0;
-    *ddz = 0.0;
-    const double alpha = hp.th[4], mu = hp.th[5], sg = hp.th[6], mmin = hp.th[7], mmax = hp.th[8];
-    if (!(m1 >= mmin && m1 <= mmax && m2 >= mmin && m2 <= m1) || !(m1 > mmin)) return;
-    const double x = (m1 - mu) / sg;
-    const double PL = hp.c_pl * pow(m1, -alpha), GG = hp.c_g * exp(-0.5 * x * x);
-    const double p1 = PL + GG;
-    if (!(p1 > 0.0)) return;
-    const double ip1 = 1.0 / p1;
-    d5[0] = PL * (hd.dlc_pl[0] - log(m1)) * ip1;
-    d5[1] = GG * (hd.dlc_g[0] + x / sg) * ip1;
-    d5[2] = GG * (hd.dlc_g[1] + x * x / sg) * ip1;
-    d5[3] = (PL * hd.dlc_pl[1] + GG * hd.dlc_g[2]) * ip1;
-    d5[4] = (PL * hd.dlc_pl[2] + GG * hd.dlc_g[3]) * ip1;
-    const double dp1_dm1 = (-alpha * PL / m1 - GG * x / sg) * ip1;
-    double dp2_dm1, dp2_dm2, dp2_dmin;
-    if (fabs(hp.b1) < 1e-12) {
-        const double L = log(m1 / mmin);
-        dp2_dm1 = -1.0 / (m1 * L);
-        dp2_dm2 = -1.0 / m2;
-        dp2_dmin = 1.0 / (mmin * L);
+template <typename T>
+struct MassDer {
+    T alpha, mu, sg, mmin, mmax, c_pl, c_g, b1, mmin_b1, beta;
+    T dlc_pl[3], dlc_g[4];
+};
+
+template <typename T>
+__device__ void dlnpm_t(const MassDer<T> &md, T m1, T m2, T a, T *d5, T *ddz) {
+    for (int k = 0; k < 5; k++) d5[k] = T(0);
+    *ddz = T(0);
+    const T one = T(1);
+    if (!(m1 >= md.mmin && m1 <= md.mmax && m2 >= md.mmin && m2 <= m1) || !(m1 > md.mmin)) return;
+    const T isg = one / md.sg, x = (m1 - md.mu) * isg;
+    const T PL = md.c_pl * pow(m1, -md.alpha), GG = md.c_g * exp(T(-0.5) * x * x);
+    const T p1 = PL + GG;
+    if (!(p1 > T(0))) return;
+    const T ip1 = one / p1;
+    d5[0] = PL * (md.dlc_pl[0] - log(m1)) * ip1;
+    d5[1] = GG * (md.dlc_g[0] + x * isg) * ip1;
+    d5[2] = GG * (md.dlc_g[1] + x * x * isg) * ip1;
+    d5[3] = (PL * md.dlc_pl[1] + GG * md.dlc_g[2]) * ip1;
+    d5[4] = (PL * md.dlc_pl[2] + GG * md.dlc_g[3]) * ip1;
+    const T dp1_dm1 = (-md.alpha * PL / m1 - GG * x * isg) * ip1;
+    T dp2_dm1, dp2_dm2, dp2_dmin;
+    if (fabs(md.b1) < T(1e-6)) {
+        const T L = log(m1 / md.mmin);
+        dp2_dm1 = -one / (m1 * L);
+        dp2_dm2 = -one / m2;
+        dp2_dmin = one / (md.mmin * L);
     } else {
-        const double q = pow(m1, hp.b1) - hp.mmin_b1;
-        dp2_dm1 = -hp.b1 * pow(m1, beta) / q;
-        dp2_dm2 = beta / m2;
-        dp2_dmin = hp.b1 * pow(mmin, beta) / q;
+        const T q = pow(m1, md.b1) - md.mmin_b1;
+        dp2_dm1 = -md.b1 * pow(m1, md.beta) / q;
+        dp2_dm2 = md.beta / m2;
+        dp2_dmin = md.b1 * pow(md.mmin, md.beta) / q;
     }
     d5[3] += dp2_dmin;
     *ddz = -(m1 * (dp1_dm1 + dp2_dm1) + m2 * dp2_dm2) / a;
+}
+
+__device__ MassDer<double> mass_der64(const HP &hp, const HPd &hd, double beta) {
+    MassDer<double> md;
+    md.alpha = hp.th[4]; md.mu = hp.th[5]; md.sg = hp.th[6]; md.mmin = hp.th[7]; md.mmax = hp.th[8];
+    md.c_pl = hp.c_pl; md.c_g = hp.c_g; md.b1 = hp.b1; md.mmin_b1 = hp.mmin_b1; md.beta = beta;
+    for (int k = 0; k < 3; k++) md.dlc_pl[k] = hd.dlc_pl[k];
+    for (int k = 0; k < 4; k++) md.dlc_g[k] = hd.dlc_g[k];
+    return md;
+}
+
+__device__ MassDer<float> mass_der32(const HP &hp, const HPd &hd) {
+    MassDer<float> md;
+    md.alpha = hp.alpha32; md.mu = hp.mu32; md.sg = (float)hp.th[6]; md.mmin = hp.mmin32; md.mmax = hp.mmax32;
+    md.c_pl = hp.c_pl32; md.c_g = hp.c_g32; md.b1 = hp.b1_32; md.mmin_b1 = hp.mmin_b1_32; md.beta = hp.beta32;
+    for (int k = 0; k < 3; k++) md.dlc_pl[k] = hd.dlc_pl32[k];
+    for (int k = 0; k < 4; k++) md.dlc_g[k] = hd.dlc_g32[k];
+    return md;
 }
 
 __device__ double std_normal_pdf(double x) { return 0.39894228040143267794 * exp(-0.5 * x * x); }
@@ -250,6 +290,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_tables(DevCatalog c, CallPt
         }
         const double zm = c.z_max;
         hd.dlpz_zmax = -3.0 * dcO_hermite(fwdO, zm, th[1]) / chimd::dc_hermite(fwd, zm, th[1]);
+        for (int k = 0; k < 3; k++) hd.dlc_pl32[k] = (float)hd.dlc_pl[k];
+        for (int k = 0; k < 4; k++) hd.dlc_g32[k] = (float)hd.dlc_g[k];
+        hd.dlpz_zmax32 = (float)hd.dlpz_zmax;
         q.hpd[h] = hd;
     }
     // dz/dtheta at the inverse-table nodes
@@ -259,10 +302,12 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_tables(DevCatalog c, CallPt
         double *o = q.dznode + ((size_t)h * (NU + 1) + k) * 4;
         if (k == 0 || !isfinite(z)) {
             for (int j = 0; j < 4; j++) o[j] = 0.0;
+            q.dznode32[(size_t)h * (NU + 1) + k] = make_float4(0.f, 0.f, 0.f, 0.f);
             continue;
         }
         ZDer r = zder(z, th, fwd, fwdO, 0.0);
         for (int j = 0; j < 4; j++) o[j] = r.dz[j];
+        q.dznode32[(size_t)h * (NU + 1) + k] = make_float4((float)r.dz[0], (float)r.dz[1], (float)r.dz[2], (float)r.dz[3]);
     }
     // d ln F / dtheta on the grid, F = psi / ((1+z)^3 J)
     for (int a = t; a < c.n_z; a += ADJ_THREADS) {
@@ -275,6 +320,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_tables(DevCatalog c, CallPt
         o[4] = g3[0];
         o[5] = g3[1];
         o[6] = g3[2];
+        float *o32 = q.Q32 + ((size_t)h * c.n_z + a) * 8;
+        for (int j = 0; j < 7; j++) o32[j] = (float)o[j];
+        o32[7] = 0.f;
     }
 }
 
@@ -306,14 +354,17 @@ __device__ void bsum(double (&v)[NV], double *red) {
 }
 
 // Per (event, hyperpoint): d ln I_i / d theta (12).  FP64 follows the FP64
-// forward kernel (inversion with Newton polish, +-9 b windows); MIXED follows
-// the mixed forward kernel (FP32 inverse table and mass model, +-6 b windows,
-// FP32 bandwidth) so that the gradient is that of the computed ln L.
+// forward kernel (inversion with Newton polish, +-9 b windows, FP64 profile)
+// in double; MIXED follows the mixed forward kernel (FP32 inverse table and
+// mass model, +-6 b windows, its FP32 bandwidth, FP32 profile and grid
+// factor) in float, with the per-thread sums carried to double for the
+// block reduction, so that the gradient is that of the computed ln L.
 template <bool F64>
 __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtrs p, AdjPtrs q, int H) {
+    using T = typename std::conditional<F64, double, float>::type;
     extern __shared__ double sh[];
-    double *zs = sh;
-    double *ws = zs + c.max_ns;
+    T *zs = reinterpret_cast<T *>(sh);
+    T *ws = zs + c.max_ns;
     int *segv = reinterpret_cast<int *>(ws + c.max_ns);
     double *red = reinterpret_cast<double *>(segv + ((c.max_seg + 2) & ~1));
     const int h = blockIdx.x % H;
@@ -328,28 +379,29 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
     }
     const int64_t s0 = c.ev_soff[ev];
     const int ns = (int)(c.ev_soff[ev + 1] - s0);
-    const double KW = F64 ? KW64 : (double)KW32;
+    const T KW = F64 ? T(KW64) : T(KW32);
+    const T TINF = F64 ? T(CUDART_INF) : T(CUDART_INF_F);
     const MixParams mp = mix_params(hp);
     const float4 *inv = p.inv32 + (size_t)h * NU;
 
     // ---- z_j, w_j exactly as the forward kernel of this precision
     for (int j = tid; j < ns; j += ADJ_THREADS) {
-        double z = CUDART_INF, w = 0.0;
+        T z = TINF, w = T(0);
         if (F64) {
             double zz;
             if (invert64(c, p, h, hp, c.sd64[s0 + j], &zz)) {
-                z = zz;
-                w = mass_weight64(hp, c.beta, c.sm1_64[s0 + j] / (1.0 + zz), c.sm2_64[s0 + j] / (1.0 + zz));
+                z = T(zz);
+                w = T(mass_weight64(hp, c.beta, c.sm1_64[s0 + j] / (1.0 + zz), c.sm2_64[s0 + j] / (1.0 + zz)));
             }
         } else {
-            float4 s = c.s32[s0 + j];
-            int k = __float_as_int(s.x);
-            if ((k < mp.kv) || (k == mp.kv && s.y <= mp.fv)) {
-                float zz = chimd::hermite4(inv[k], s.y);
+            float4 sv = c.s32[s0 + j];
+            int k = __float_as_int(sv.x);
+            if ((k < mp.kv) || (k == mp.kv && sv.y <= mp.fv)) {
+                float zz = chimd::hermite4(inv[k], sv.y);
                 if (zz < CUDART_INF_F) {
-                    z = zz;
+                    z = T(zz);
                     float lz = __log2f(1.f + zz);
-                    w = mass_weight32(mp, s.z - lz, s.w - lz);
+                    w = T(mass_weight32(mp, sv.z - lz, sv.w - lz));
                 }
             }
         }
@@ -358,21 +410,21 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
     }
     __syncthreads();
     // moments (two-pass, FP64)
-    double m1v[4] = {0, 0, 0, 0};  // W1, Wz, W2, n_valid
-    double mz = 0.0;
+    double m5[5] = {0, 0, 0, 0, 0};  // W1, Wz, W2, n_valid, Sz
     for (int j = tid; j < ns; j += ADJ_THREADS)
-        if (zs[j] < CUDART_INF) {
-            m1v[0] += ws[j]; m1v[1] += ws[j] * zs[j]; m1v[2] += ws[j] * ws[j]; m1v[3] += 1.0; mz += zs[j];
+        if (zs[j] < TINF) {
+            const double z = zs[j], w = ws[j];
+            m5[0] += w; m5[1] += w * z; m5[2] += w * w; m5[3] += 1.0; m5[4] += z;
         }
-    double m5[5] = {m1v[0], m1v[1], m1v[2], m1v[3], mz};
     bsum<5>(m5, red);
     const double W1 = m5[0], W2 = m5[2], nv = m5[3];
     const double Mw = W1 > 0.0 ? m5[1] / W1 : 0.0, Mu = nv > 0.0 ? m5[4] / nv : 0.0;
     double m2v[2] = {0.0, 0.0};
     for (int j = tid; j < ns; j += ADJ_THREADS)
-        if (zs[j] < CUDART_INF) {
-            m2v[0] += ws[j] * (zs[j] - Mw) * (zs[j] - Mw);
-            m2v[1] += (zs[j] - Mu) * (zs[j] - Mu);
+        if (zs[j] < TINF) {
+            const double z = zs[j], w = ws[j];
+            m2v[0] += w * (z - Mw) * (z - Mw);
+            m2v[1] += (z - Mu) * (z - Mu);
         }
     bsum<2>(m2v, red);
     const double varw = W1 > 0.0 ? m2v[0] / W1 : 0.0, neffw = W1 > 0.0 ? W1 * W1 / W2 : 0.0;
@@ -389,7 +441,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
         rule = 2;
         b = c.dz;
     }
-    if (!F64) b = (double)p.bw[(size_t)h * c.n_events + ev];  // the forward kernel's FP32 bandwidth
+    if (!F64) b = p.bw[(size_t)h * c.n_events + ev];  // the forward kernel's FP32 bandwidth
 
     // segment valid counts
     const int sg0 = c.ev_segoff[ev], nseg = c.ev_segoff[ev + 1] - sg0;
@@ -398,7 +450,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
         int l = lo, r = hi;
         while (l < r) {
             int m = (l + r) >> 1;
-            if (zs[m] < CUDART_INF) l = m + 1; else r = m;
+            if (zs[m] < TINF) l = m + 1; else r = m;
         }
         segv[k] = l - lo;
     }
@@ -406,13 +458,23 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
 
     // ---- per-sample derivatives: bandwidth gradient and the sample sums
     const int nz = c.n_z;
-    const double dz = c.dz;
-    const double *Fg = p.F64 + (size_t)h * nz;
-    const double *Qg = q.Q + (size_t)h * nz * 7;
-    double A12[12], B4[4], S2t = 0.0, I0 = 0.0, db9[9];
-    for (int k = 0; k < 12; k++) A12[k] = 0.0;
-    for (int k = 0; k < 4; k++) B4[k] = 0.0;
-    for (int k = 0; k < 9; k++) db9[k] = 0.0;
+    const T dz = T(c.dz), bt = T(b), ib = T(1) / bt;
+    const T cw0 = T(W1 > 0.0 ? 1.0 / (W1 * varw) : 0.0), cw1 = T(W1 > 0.0 ? 2.0 / W1 : 0.0);
+    const T cw2 = T(W2 > 0.0 ? 2.0 / W2 : 0.0), cu = T(nv > 0.0 && varu > 0.0 ? 1.0 / (nv * varu) : 0.0);
+    const T Mwt = T(Mw), Mut = T(Mu), varwt = T(varw);
+    // grid factor (FP32 path: F / F_scale; every term carries the same scale)
+    const double *F64g = p.F64 + (size_t)h * nz;
+    const float *F32g = p.F32 + (size_t)h * nz;
+    auto Fg = [&](int a) -> T { return F64 ? T(F64g[a]) : T(F32g[a]); };
+    auto Gv = [&](int64_t row, int a) -> T {
+        return F64 ? T(reinterpret_cast<const double *>(p.prof[h])[row * nz + a])
+                   : T(reinterpret_cast<const float *>(p.prof[h])[row * nz + a]);
+    };
+    const MassDer<double> md64 = mass_der64(hp, hd, c.beta);
+    const MassDer<float> md32 = mass_der32(hp, hd);
+    T A9[9], B4[4], db9[9], S2t = T(0), I0 = T(0);
+    for (int k = 0; k < 9; k++) { A9[k] = T(0); db9[k] = T(0); }
+    for (int k = 0; k < 4; k++) B4[k] = T(0);
     for (int j = tid; j < ns; j += ADJ_THREADS) {
         int l = 0, r = nseg;  // segment of j
         while (r - l > 1) {
@@ -421,95 +483,120 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
         }
         const int lo = (int)(c.seg_soff[sg0 + l] - s0);
         if (j - lo >= segv[l]) continue;
-        const double z = zs[j], w = ws[j], a1 = 1.0 + z;
-        // dz/dtheta and d ln w/dtheta
-        double dd[4];
+        const T z = zs[j], w = ws[j], a1 = T(1) + z;
+        // dz/dtheta (linear between inverse-table nodes) and d ln w/dtheta
+        T dd[4], d5[5], dwz;
         {
-            double dL = c.sd64[s0 + j];
-            double t = sqrt(dL / c.d_top) * NU;
-            int kk = min((int)t, NU - 1);
-            dz_interp(q, h, kk, t - kk, dd);
+            const double t = sqrt(c.sd64[s0 + j] / c.d_top) * NU;
+            const int kk = min((int)t, NU - 1);
+            const T f = T(t - kk);
+            if (F64) {
+                double ddd[4];
+                dz_interp(q, h, kk, t - kk, ddd);
+                for (int k = 0; k < 4; k++) dd[k] = T(ddd[k]);
+            } else {
+                const float4 n0 = q.dznode32[(size_t)h * (NU + 1) + kk], n1 = q.dznode32[(size_t)h * (NU + 1) + kk + 1];
+                dd[0] = n0.x + f * (n1.x - n0.x);
+                dd[1] = n0.y + f * (n1.y - n0.y);
+                dd[2] = n0.z + f * (n1.z - n0.z);
+                dd[3] = n0.w + f * (n1.w - n0.w);
+            }
         }
-        double d5[5], dwz;
-        dlnpm(hp, hd, c.beta, c.sm1_64[s0 + j] / a1, c.sm2_64[s0 + j] / a1, a1, d5, &dwz);
-        double dlw[9];
+        if (F64) {
+            double e5[5], ez;
+            dlnpm_t<double>(md64, c.sm1_64[s0 + j] / double(a1), c.sm2_64[s0 + j] / double(a1), double(a1), e5, &ez);
+            for (int k = 0; k < 5; k++) d5[k] = T(e5[k]);
+            dwz = T(ez);
+        } else {
+            const float4 sv = c.s32[s0 + j];
+            const float lz = __log2f(float(a1));
+            float e5[5], ez;
+            dlnpm_t<float>(md32, ex2(sv.z - lz), ex2(sv.w - lz), float(a1), e5, &ez);
+            for (int k = 0; k < 5; k++) d5[k] = T(e5[k]);
+            dwz = T(ez);
+        }
+        T dlw[9];
         for (int k = 0; k < 4; k++) dlw[k] = dwz * dd[k];
         for (int k = 0; k < 5; k++) dlw[4 + k] = d5[k];
         // Scott's rule: d ln b = sum_j (dlnb/dw_j) w_j dln w_j + (dlnb/dz_j) dz_j
         if (rule == 0) {
-            const double cw = 0.5 * ((z - Mw) * (z - Mw) - varw) / (W1 * varw) - 0.2 * (2.0 / W1 - 2.0 * w / W2);
-            const double cz = w * (z - Mw) / (W1 * varw);
-            for (int k = 0; k < 9; k++) db9[k] += cw * w * dlw[k] + (k < 4 ? cz * dd[k] : 0.0);
+            const T cw = T(0.5) * ((z - Mwt) * (z - Mwt) - varwt) * cw0 - T(0.2) * (cw1 - w * cw2);
+            const T cz = w * (z - Mwt) * cw0;
+            for (int k = 0; k < 9; k++) db9[k] += cw * w * dlw[k] + (k < 4 ? cz * dd[k] : T(0));
         } else if (rule == 1) {
-            const double cz = (z - Mu) / (nv * varu);
+            const T cz = (z - Mut) * cu;
             for (int k = 0; k < 4; k++) db9[k] += cz * dd[k];
         }
-        if (w == 0.0) continue;
-        // window sums S0, S1, S2
-        const double pf = c.seg_pf[sg0 + l];
+        if (w == T(0)) continue;
+        // window sums S0, S1, S2 of e = exp(-u^2/2) H, u = (z_a - z)/b
+        const T pf = T(c.seg_pf[sg0 + l]);
         const int64_t row = c.kde_mode == CHIMERA_KDE_MANY_1D ? (int64_t)(sg0 + l) : (int64_t)ev;
-        const double smin = zs[lo] - KDE_MARGIN * b, smax = zs[lo + segv[l] - 1] + KDE_MARGIN * b;
-        double a0 = fmax(ceil((z - KW * b) / dz), ceil(smin / dz));
-        double aa1 = fmin(floor((z + KW * b) / dz), floor(smax / dz));
-        int ia0 = a0 < 0.0 ? 0 : (a0 > nz ? nz : (int)a0);
-        int ia1 = aa1 > nz - 1 ? nz - 1 : (aa1 < -1.0 ? -1 : (int)aa1);
-        double S0 = 0.0, S1 = 0.0, S2 = 0.0;
+        const T smin = zs[lo] - T(KDE_MARGIN) * bt, smax = zs[lo + segv[l] - 1] + T(KDE_MARGIN) * bt;
+        const T a0 = fmax(ceil((z - KW * bt) / dz), ceil(smin / dz));
+        const T aa1 = fmin(floor((z + KW * bt) / dz), floor(smax / dz));
+        const int ia0 = a0 < T(0) ? 0 : (a0 > T(nz) ? nz : (int)a0);
+        const int ia1 = aa1 > T(nz - 1) ? nz - 1 : (aa1 < T(-1) ? -1 : (int)aa1);
+        T S0 = T(0), S1 = T(0), S2 = T(0);
         for (int a = ia0; a <= ia1; a++) {
-            double Ga = F64 ? reinterpret_cast<const double *>(p.prof[h])[row * nz + a]
-                            : (double)reinterpret_cast<const float *>(p.prof[h])[row * nz + a];
-            double Hh = ((a == 0 || a == nz - 1) ? 0.5 : 1.0) * Fg[a] * Ga;
-            double u = (a * dz - z) / b;
-            double e = exp(-0.5 * u * u) * Hh;
+            const T Hh = ((a == 0 || a == nz - 1) ? T(0.5) : T(1)) * Fg(a) * Gv(row, a);
+            const T u = (T(a) * dz - z) * ib;
+            const T e = (F64 ? T(exp(-0.5 * double(u * u))) : T(__expf(-0.5f * float(u * u)))) * Hh;
             S0 += e;
             S1 += e * u;
             S2 += e * u * u;
         }
-        const double pw = pf * w;
+        const T pw = pf * w;
         I0 += pw * S0;
         S2t += pw * S2;
-        for (int k = 0; k < 9; k++) A12[k] += pw * S0 * dlw[k];
-        for (int k = 0; k < 4; k++) B4[k] += pw * S1 / b * dd[k];
+        for (int k = 0; k < 9; k++) A9[k] += pw * S0 * dlw[k];
+        for (int k = 0; k < 4; k++) B4[k] += pw * S1 * ib * dd[k];
     }
     // ---- grid term: per segment and grid point, the KDE K_k(a)
-    double C8[8];  // 7 d ln F terms + the galaxy Om term
-    for (int k = 0; k < 8; k++) C8[k] = 0.0;
+    T C8[8];  // 7 d ln F terms + the galaxy Om term
+    for (int k = 0; k < 8; k++) C8[k] = T(0);
     for (int l = 0; l < nseg; l++) {
         const int lo = (int)(c.seg_soff[sg0 + l] - s0), cnt = segv[l];
         if (cnt <= 0) continue;
-        const double pf = c.seg_pf[sg0 + l];
+        const T pf = T(c.seg_pf[sg0 + l]);
         const int64_t row = c.kde_mode == CHIMERA_KDE_MANY_1D ? (int64_t)(sg0 + l) : (int64_t)ev;
-        const double smin = zs[lo] - KDE_MARGIN * b, smax = zs[lo + cnt - 1] + KDE_MARGIN * b;
+        const T smin = zs[lo] - T(KDE_MARGIN) * bt, smax = zs[lo + cnt - 1] + T(KDE_MARGIN) * bt;
         const int alo = max(0, (int)ceil(smin / dz)), ahi = min(nz - 1, (int)floor(smax / dz));
         for (int a = alo + tid; a <= ahi; a += ADJ_THREADS) {
-            const double za = a * dz;
+            const T za = T(a) * dz;
             // samples whose window covers a: z in [za - KW b, za + KW b]
             int jl = lo, jr = lo + cnt;
             while (jl < jr) {
                 int m = (jl + jr) >> 1;
-                if (zs[m] < za - KW * b) jl = m + 1; else jr = m;
+                if (zs[m] < za - KW * bt) jl = m + 1; else jr = m;
             }
-            double K = 0.0;
-            for (int j = jl; j < lo + cnt && zs[j] <= za + KW * b; j++) {
+            T K = T(0);
+            for (int j = jl; j < lo + cnt && zs[j] <= za + KW * bt; j++) {
                 // same per-sample window rule as the sums above
-                double z = zs[j];
-                double a0 = ceil((z - KW * b) / dz), aa1 = floor((z + KW * b) / dz);
-                if (a < a0 || a > aa1) continue;
-                double u = (za - z) / b;
-                K += ws[j] * exp(-0.5 * u * u);
+                const T z = zs[j];
+                const T a0 = ceil((z - KW * bt) / dz), aa1 = floor((z + KW * bt) / dz);
+                if (T(a) < a0 || T(a) > aa1) continue;
+                const T u = (za - z) * ib;
+                K += ws[j] * (F64 ? T(exp(-0.5 * double(u * u))) : T(__expf(-0.5f * float(u * u))));
             }
-            if (K == 0.0) continue;
-            double Ga = F64 ? reinterpret_cast<const double *>(p.prof[h])[row * nz + a]
-                            : (double)reinterpret_cast<const float *>(p.prof[h])[row * nz + a];
-            double wa = (a == 0 || a == nz - 1) ? 0.5 : 1.0;
-            double M = pf * wa * Fg[a] * Ga * K;
-            for (int k = 0; k < 7; k++) C8[k] += M * Qg[(size_t)a * 7 + k];
-            double dGa = q.dprof[h][row * nz + a];
-            C8[7] += pf * wa * Fg[a] * dGa * K;
+            if (K == T(0)) continue;
+            const T wa = (a == 0 || a == nz - 1) ? T(0.5) : T(1);
+            const T FK = pf * wa * Fg(a) * K;
+            const T M = FK * Gv(row, a);
+            if (F64) {
+                const double *Qa = q.Q + ((size_t)h * nz + a) * 7;
+                for (int k = 0; k < 7; k++) C8[k] += M * T(Qa[k]);
+            } else {
+                const float4 *Qa = reinterpret_cast<const float4 *>(q.Q32 + ((size_t)h * nz + a) * 8);
+                const float4 qa = Qa[0], qb = Qa[1];
+                C8[0] += M * qa.x; C8[1] += M * qa.y; C8[2] += M * qa.z; C8[3] += M * qa.w;
+                C8[4] += M * qb.x; C8[5] += M * qb.y; C8[6] += M * qb.z;
+            }
+            C8[7] += FK * T(q.dprof[h][row * nz + a]);
         }
     }
-    // ---- block sums and the 12 derivatives
+    // ---- block sums (double) and the 12 derivatives
     double v[28];
-    for (int k = 0; k < 9; k++) v[k] = A12[k];
+    for (int k = 0; k < 9; k++) v[k] = A9[k];
     for (int k = 0; k < 4; k++) v[9 + k] = B4[k];
     v[13] = S2t;
     v[14] = I0;
@@ -537,55 +624,112 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
     }
 }
 
-// Selection adjoint: per block, sum_j s_j dln s_j / dtheta (12) and sum_j s_j.
+// Hermite interpolation of dDhat/dOm in FP32 (table values rounded).
+__device__ __forceinline__ float dcO_hermite32(const double *fwdO, float z, float Om) {
+    const float t = z * float(1.0 / HT);
+    int k = (int)floorf(t);
+    k = max(0, min(k, NT_FWD - 2));
+    const float f = t - k;
+    auto g = [Om](float zz) {
+        const float a = 1.f + zz, E = sqrtf(Om * a * a * a + 1.f - Om);
+        return -0.5f * (a * a * a - 1.f) / (E * E * E);
+    };
+    const float ht = float(HT);
+    const float m0 = ht * g(k * ht), m1 = ht * g((k + 1) * ht);
+    const float f2 = f * f, f3 = f2 * f;
+    return (2.f * f3 - 3.f * f2 + 1.f) * float(fwdO[k]) + (f3 - 2.f * f2 + f) * m0 +
+           (-2.f * f3 + 3.f * f2) * float(fwdO[k + 1]) + (f3 - f2) * m1;
+}
+
+// Selection adjoint: per block, sum_j s_j dln s_j / dtheta (12) and sum_j s_j,
+// with dln s/dz chained through z_j for the cosmological parameters.  FP64
+// recomputes s_j as the FP64 selection kernel does; MIXED in float from the
+// mixed kernel's z_j (D_c from the measured distance, D_c = d_L/((1+z) Xi)).
 template <bool F64>
 __global__ void __launch_bounds__(ADJ_THREADS) k_select_adj(DevCatalog c, CallPtrs p, AdjPtrs q, int H) {
+    using T = typename std::conditional<F64, double, float>::type;
     __shared__ double red[(ADJ_THREADS / 32 + 1) * 13];
     const int h = blockIdx.y, chunk = blockIdx.x;
     const HP &hp = p.hp[h];
     const HPd &hd = q.hpd[h];
     const double *th = hp.th;
-    double acc[13];
-    for (int k = 0; k < 13; k++) acc[k] = 0.0;
+    T acc[13];
+    for (int k = 0; k < 13; k++) acc[k] = T(0);
     const MixParams mp = mix_params(hp);
+    const MassDer<double> md64 = mass_der64(hp, hd, c.beta);
+    const MassDer<float> md32 = mass_der32(hp, hd);
     const int64_t base = (int64_t)chunk * SEL_CHUNK;
     const double inv_dc3 = 1.0 / (hp.dc_zmax * hp.dc_zmax * hp.dc_zmax);
+    const T H0 = T(th[0]), Om = T(th[1]), Xi0 = T(th[2]), nn = T(th[3]);
+    const T cH = T(hp.cH), one = T(1);
     for (int qq = 0; qq < SEL_PER_THREAD; qq++) {
         int64_t j = base + qq * ADJ_THREADS + threadIdx.x;
         if (j >= c.n_det) break;
-        double d = c.id64[j], z;
-        if (F64) {
-            if (!invert64(c, p, h, hp, d, &z)) continue;
+        T z, m1, m2, s;
+        ZDerT<T> r;
+        T d5[5], dwz;
+        if constexpr (F64) {
+            double zz;
+            if (!invert64(c, p, h, hp, c.id64[j], &zz)) continue;
+            if (!(zz <= c.z_max)) continue;
+            const double a1 = 1.0 + zz;
+            const double dm1 = c.im1_64[j] / a1, dm2 = c.im2_64[j] / a1;
+            const double mmin = th[7], mmax = th[8];
+            if (!(dm1 >= mmin && dm1 <= mmax && dm2 >= mmin && dm2 <= dm1) || !(dm1 > mmin)) continue;
+            const double x = (dm1 - th[5]) / th[6];
+            const double p1 = hp.c_pl * pow(dm1, -th[4]) + hp.c_g * exp(-0.5 * x * x);
+            const double p2 = fabs(hp.b1) < 1e-12 ? 1.0 / (dm2 * log(dm1 / mmin))
+                                                  : hp.b1 * pow(dm2, c.beta) / (pow(dm1, hp.b1) - hp.mmin_b1);
+            const double Dc = hp.cH * chimd::dc_hermite(p.fwd[h], zz, th[1]);
+            double dd, J;
+            chimd::dgw_J(zz, Dc, th, hp.cH, &dd, &J);
+            const double E = chimd::E_of(zz, th[1]);
+            const double pz = 3.0 * hp.cH * Dc * Dc / E * inv_dc3;
+            s = T(p1 * p2 * chimd::psi_of(zz, th) * pz / (a1 * a1 * a1 * fabs(J) * exp(c.ilp64[j])));
+            const ZDer r64 = zder(zz, th, p.fwd[h], q.fwdO[h], hd.dlpz_zmax);
+            r = r64;
+            double e5[5], ez;
+            dlnpm_t<double>(md64, dm1, dm2, a1, e5, &ez);
+            for (int k = 0; k < 5; k++) d5[k] = T(e5[k]);
+            dwz = T(ez);
+            z = T(zz); m1 = T(dm1); m2 = T(dm2);
         } else {
-            float4 a4 = c.i32a[j];
-            int k = __float_as_int(a4.x);
+            const float4 a4 = c.i32a[j];
+            const int k = __float_as_int(a4.x);
             if (!((k < mp.kv) || (k == mp.kv && a4.y <= mp.fv))) continue;
-            float zz = chimd::hermite4(p.inv32[(size_t)h * NU + k], a4.y);
-            if (!isfinite(zz)) continue;
-            z = zz;
+            const float zz = chimd::hermite4(p.inv32[(size_t)h * NU + k], a4.y);
+            if (!(zz <= c.z_max32)) continue;
+            const float a1 = 1.f + zz, lz = log1pf(zz);
+            const float fm1 = expf(a4.z - lz), fm2 = expf(a4.w - lz);
+            const float mmin = hp.mmin32, mmax = hp.mmax32;
+            if (!(fm1 >= mmin && fm1 <= mmax && fm2 >= mmin && fm2 <= fm1) || !(fm1 > mmin)) continue;
+            const float x = (fm1 - hp.mu32) * hp.inv_sg32;
+            const float p1 = hp.c_pl32 * powf(fm1, -hp.alpha32) + hp.c_g32 * expf(-0.5f * x * x);
+            const float p2 = fabsf(hp.b1_32) < 1e-6f ? 1.f / (fm2 * logf(fm1 / mmin))
+                                                    : hp.b1_32 * powf(fm2, hp.beta32) / (powf(fm1, hp.b1_32) - hp.mmin_b1_32);
+            const float fn = float(nn), fxi0 = float(Xi0), pwz = expf(-fn * lz);
+            const float xi = fxi0 + (1.f - fxi0) * pwz, dxi = -fn * (1.f - fxi0) * pwz / a1;
+            const float Dc = c.i32b[j].x / (a1 * xi);
+            const float fom = float(Om), E = sqrtf(fom * a1 * a1 * a1 + 1.f - fom);
+            const float fcH = float(cH);
+            const float J = (Dc + a1 * fcH / E) * xi + a1 * Dc * dxi;
+            const float pz = 3.f * fcH * Dc * Dc / E * float(inv_dc3);
+            const float psi = expf(hp.gam32 * lz) / (1.f + expf((hp.gam32 + hp.kap32) * (lz - hp.l1zp32)));
+            s = T(p1 * p2 * psi * pz / (a1 * a1 * a1 * fabsf(J) * expf(c.i32b[j].y)));
+            const float DhO = dcO_hermite32(q.fwdO[h], zz, fom);
+            const ZDerT<float> r32 = zder_t<float>(zz, float(H0), fom, fxi0, fn, Dc / fcH, DhO, hd.dlpz_zmax32);
+            r = r32;
+            float e5[5], ez;
+            dlnpm_t<float>(md32, fm1, fm2, a1, e5, &ez);
+            for (int kk = 0; kk < 5; kk++) d5[kk] = T(e5[kk]);
+            dwz = T(ez);
+            z = T(zz); m1 = T(fm1); m2 = T(fm2);
         }
-        if (!(z <= c.z_max)) continue;
-        const double a1 = 1.0 + z;
-        const double m1 = c.im1_64[j] / a1, m2 = c.im2_64[j] / a1;
-        const double mmin = th[7], mmax = th[8];
-        if (!(m1 >= mmin && m1 <= mmax && m2 >= mmin && m2 <= m1) || !(m1 > mmin)) continue;
-        // s_j (FP64 arithmetic on this path's z)
-        double x = (m1 - th[5]) / th[6];
-        double p1 = hp.c_pl * pow(m1, -th[4]) + hp.c_g * exp(-0.5 * x * x);
-        double p2 = fabs(hp.b1) < 1e-12 ? 1.0 / (m2 * log(m1 / mmin))
-                                         : hp.b1 * pow(m2, c.beta) / (pow(m1, hp.b1) - hp.mmin_b1);
-        double Dc = hp.cH * chimd::dc_hermite(p.fwd[h], z, th[1]), dd, J;
-        chimd::dgw_J(z, Dc, th, hp.cH, &dd, &J);
-        double E = chimd::E_of(z, th[1]);
-        double pz = 3.0 * hp.cH * Dc * Dc / E * inv_dc3;
-        double s = p1 * p2 * chimd::psi_of(z, th) * pz / (a1 * a1 * a1 * fabs(J) * exp(c.ilp64[j]));
-        // log-derivatives
-        ZDer r = zder(z, th, p.fwd[h], q.fwdO[h], hd.dlpz_zmax);
-        double d5[5], dwz, g3[3], dpsiz;
-        dlnpm(hp, hd, c.beta, m1, m2, a1, d5, &dwz);
-        dlnpsi(z, th, g3, &dpsiz);
-        const double dls_dz = dwz + dpsiz + r.dlnpz_dz - 3.0 / a1 - r.dlnJ_dz;
-        double g[12];
+        (void)m1; (void)m2;
+        T g3[3], dpsiz;
+        dlnpsi_t<T>(z, T(th[9]), T(th[10]), T(th[11]), g3, &dpsiz);
+        const T dls_dz = dwz + dpsiz + r.dlnpz_dz - T(3) / (one + z) - r.dlnJ_dz;
+        T g[12];
         g[0] = -r.dlnJ[0];
         g[1] = r.dlnpz_dOm - r.dlnJ[1];
         g[2] = -r.dlnJ[2];
@@ -598,7 +742,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_select_adj(DevCatalog c, CallPt
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int k = 0; k < 13; k++) {
-        double v = acc[k];
+        double v = double(acc[k]);
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red[wid * 13 + k] = v;
     }
@@ -765,14 +909,16 @@ size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Layout of the adjoint scratch for H points of catalog c.
 struct AdjLayout {
-    size_t o_ptrs, o_hpd, o_dzn, o_Q, o_dlnI, o_selg, o_dv, o_dvO, o_invZ, o_ZO, total;
+    size_t o_ptrs, o_hpd, o_dzn, o_dzn32, o_Q, o_Q32, o_dlnI, o_selg, o_dv, o_dvO, o_invZ, o_ZO, total;
     AdjLayout(const DevCatalog &c, int H, int nchunk) {
         size_t o = 0;
         auto take = [&](size_t b) { size_t r = o; o += al256(b); return r; };
         o_ptrs = take(2 * sizeof(void *) * (size_t)H);
         o_hpd = take(sizeof(HPd) * (size_t)H);
         o_dzn = take(sizeof(double) * 4 * (size_t)H * (NU + 1));
+        o_dzn32 = take(sizeof(float4) * (size_t)H * (NU + 1));
         o_Q = take(sizeof(double) * 7 * (size_t)H * c.n_z);
+        o_Q32 = take(sizeof(float) * 8 * (size_t)H * c.n_z);
         o_dlnI = take(sizeof(double) * 12 * (size_t)H * c.n_events);
         o_selg = take(sizeof(double) * 13 * (size_t)H * std::max(nchunk, 1));
         o_dv = take(sizeof(double) * c.n_z);
@@ -911,7 +1057,9 @@ int backward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, int precision) {
     q.dprof = q.fwdO + H;
     q.hpd = reinterpret_cast<HPd *>(ws.gscr + L.o_hpd);
     q.dznode = reinterpret_cast<double *>(ws.gscr + L.o_dzn);
+    q.dznode32 = reinterpret_cast<float4 *>(ws.gscr + L.o_dzn32);
     q.Q = reinterpret_cast<double *>(ws.gscr + L.o_Q);
+    q.Q32 = reinterpret_cast<float *>(ws.gscr + L.o_Q32);
     q.dlnI = reinterpret_cast<double *>(ws.gscr + L.o_dlnI);
     q.selg = reinterpret_cast<double *>(ws.gscr + L.o_selg);
     q.grad = ws.grad;

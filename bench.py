@@ -11,6 +11,11 @@ events, `e2e` times the host-pointer entry point (hyperpoints copied in,
 ln L copied out) end to end.  L2 is flushed (a 256 MiB write) between timed
 steps because the catalog (~100 MB) would otherwise stay L2-resident.
 
+Beside the headline: the plain FP64 one-point-per-call path, ln L with its
+gradient (chimera_grad, mixed and FP64), and a serving stream (Poisson
+arrivals over four resident catalogs of 100 to 5000 events, 1-512 points per
+request, a quarter with gradients) with its p50/p99 latency.
+
 Run: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Multi-GPU (torchrun): every rank evaluates its own walkers on its own GPU
 (independent replicas, weak scaling); only a barrier and a max of the times
@@ -142,27 +147,32 @@ def traffic_from_profiles():
         return None
 
 
-def cpu_baseline(cat, theta, budget_s=20.0):
-    """The FP64 oracle, as it stands, on the host cores: one hyperpoint over
-    the first E events, with the matching share of injections."""
+def cpu_baseline(cat, thetas, budget_s=20.0):
+    """The FP64 oracle, as it stands, on the host cores: hyperpoints of the
+    benchmark batch over the first E events (with the matching share of
+    injections), E and then the number of hyperpoints grown until the sample
+    takes about budget_s / 2 of wall time."""
     import oracle
-    from synth import catalog as sc  # noqa: F401
     cores = os.cpu_count() or 1
-    # bounded sample: size E so the run takes ~budget_s of wall time
-    E = 8
     ne = cat["n_events"]
+    E, P = 8, 1
     while True:
         sub = _sub_catalog(cat, E)
         oc = oracle.Catalog(sub)
         t0 = time.perf_counter()
-        oc.loglike(theta, nthreads=cores)
+        for k in range(P):
+            oc.loglike(thetas[k % len(thetas)], nthreads=cores)
         dt = time.perf_counter() - t0
-        if dt * 2 > budget_s or E >= ne:
+        if dt * 2 > budget_s or (E >= ne and P >= len(thetas)):
             break
-        E = min(ne, int(E * max(2.0, min(8.0, budget_s / max(dt, 1e-3) / 2))))
-    return {"value": E / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "1 hyperpoint x first %d of %d events with %d of %d detected injections, FP64, %d threads, %.1f s"
-                      % (E, ne, sub["inj_dL"].size, cat["inj_dL"].size, cores, dt)}
+        grow = max(2.0, min(8.0, budget_s / max(dt, 1e-3) / 2))
+        if E < ne:
+            E = min(ne, int(E * grow))
+        else:
+            P = min(len(thetas), int(P * grow))
+    return {"value": P * E / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d hyperpoint(s) x first %d of %d events with %d of %d detected injections, FP64, %d threads, %.1f s"
+                      % (P, E, ne, sub["inj_dL"].size, cat["inj_dL"].size, cores, dt)}
 
 
 def _sub_catalog(cat, E):
@@ -179,6 +189,74 @@ def _sub_catalog(cat, E):
                inj_dL=cat["inj_dL"][:nd], inj_m1d=cat["inj_m1d"][:nd], inj_m2d=cat["inj_m2d"][:nd],
                inj_log_pi=cat["inj_log_pi"][:nd])
     return sub
+
+
+def grad_stats(pkg, ctx, cid, theta, NE, reps=3):
+    """ln L and its 12-component gradient through chimera_grad (host buffers),
+    mixed and FP64, on the benchmark batch; adjoint stage time from the trace."""
+    out = {}
+    for name, prec, pts in (("mixed", pkg.MIXED, theta), ("fp64_single_point", pkg.FP64, theta[:1])):
+        pkg.chimera_grad(ctx.h, cid, pts, prec)
+        t, adj = [], []
+        for _ in range(reps if prec == pkg.MIXED else 1):
+            t0 = time.perf_counter()
+            pkg.chimera_grad(ctx.h, cid, pts, prec)
+            t.append(time.perf_counter() - t0)
+            adj.append(pkg.chimera_stage_ms(ctx.h)["adjoint"])
+        out[name] = {"value": pts.shape[0] * NE * len(t) / sum(t), "unit": "evals/s (ln L + 12 derivatives)",
+                     "ms_per_call": 1e3 * sum(t) / len(t), "adjoint_ms": sum(adj) / len(adj),
+                     "hyperpoints": int(pts.shape[0])}
+    return out
+
+
+def serving_stream(pkg, ctx, bench_cid, bench_cat, n_req, seed=2504020345):
+    """Request stream over four resident catalogs (spectroscopic 100 / 300 /
+    1000 events at Xi0 = 0.6 / 1 / 1.8, photometric 5000 events x 4000 PE with
+    x3 galaxies in BF16): Poisson arrivals with mean 2 ms, 1-512 hyperpoints
+    (log-uniform), gradient flag with probability 0.25, mixed precision."""
+    from synth import catalog as sc
+    t_gen = time.perf_counter()
+    cats = [(sc.config_catalog(2, variant=0, n_events=100), 0.6),
+            (bench_cat, 1.0),
+            (sc.config_catalog(2, variant=2, n_events=1000), 1.8),
+            (sc.config_catalog(3, n_events=5000, n_pe=4000), 1.0)]
+    cids = [ctx.load(c) if c is not bench_cat else bench_cid for c, _ in cats]
+    nev = [c["n_events"] for c, _ in cats]
+    t_gen = time.perf_counter() - t_gen
+    rng = np.random.default_rng(seed)
+    arrive = np.cumsum(rng.exponential(2e-3, n_req))
+    which = rng.integers(0, len(cats), n_req)
+    npts = np.clip(np.floor(np.exp(rng.uniform(0.0, np.log(513.0), n_req))), 1, 512).astype(int)
+    want_grad = rng.random(n_req) < 0.25
+    thetas = [sc.make_hyperpoints(int(n), seed=seed + 7 * i, Xi0=cats[w][1]) for i, (n, w) in enumerate(zip(npts, which))]
+    # warm the per-catalog caches (galaxy profiles and their Om derivatives)
+    for cid, (c, xi0) in zip(cids, cats):
+        for flags in (pkg.SERVE_MIXED, pkg.SERVE_MIXED | pkg.SERVE_GRAD):
+            tk = pkg.chimera_serve_submit(ctx.h, cid, sc.make_hyperpoints(1, seed=seed, Xi0=xi0), flags)
+            pkg.chimera_serve_poll(ctx.h, tk, 1, grad=bool(flags & pkg.SERVE_GRAD))
+    pkg.chimera_serve_reset_stats(ctx.h)
+    t0 = time.perf_counter()
+    tickets = []
+    for i in range(n_req):
+        dt = t0 + arrive[i] - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        flags = pkg.SERVE_MIXED | (pkg.SERVE_GRAD if want_grad[i] else 0)
+        tickets.append(pkg.chimera_serve_submit(ctx.h, cids[which[i]], thetas[i], flags))
+    for i, tk in enumerate(tickets):
+        pkg.chimera_serve_poll(ctx.h, tk, int(npts[i]), grad=bool(want_grad[i]))
+    wall = time.perf_counter() - t0
+    st = pkg.chimera_serve_stats(ctx.h)
+    evals = int(sum(int(n) * nev[w] for n, w in zip(npts, which)))
+    for cid, (c, _) in zip(cids, cats):
+        if c is not bench_cat:
+            ctx.unload(cid)
+    return {"requests": n_req, "catalog_events": nev, "gradient_requests": int(want_grad.sum()),
+            "hyperpoints": int(npts.sum()), "offered_req_per_s": n_req / float(arrive[-1]),
+            "achieved_req_per_s": n_req / wall, "evals_per_s": evals / wall, "unit": "evals/s",
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "batches": st["batches"], "wall_s": wall, "catalog_setup_s": t_gen,
+            "precision": "mixed"}
 
 
 def run_reference(args, ws, rank):
@@ -222,6 +300,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--serve-requests", type=int, default=120,
+                    help="length of the serving stream (0 skips it)")
     ap.add_argument("--profile", action="store_true",
                     help="run W warm-up launches and one more launch of the timed step, then exit (for ncu)")
     args = ap.parse_args()
@@ -313,6 +393,9 @@ def main():
             fp.append(time.perf_counter() - t0)
     fp64_val = NE * len(fp) / sum(fp)
 
+    grads = grad_stats(pkg, ctx, cid, theta, NE)
+    serving = serving_stream(pkg, ctx, cid, cat, args.serve_requests) if args.serve_requests > 0 and rank == 0 else None
+
     kern = sum(kern_ms) / len(kern_ms)
     clock_mhz = (clk or {}).get("sm_max_mhz") or 2032.0
     peak_pairs = SM_COUNT * FP32_LANES * clock_mhz * 1e6 / OPS_PER_PAIR
@@ -336,6 +419,8 @@ def main():
         "fp64_single_point": {"value": fp64_val, "unit": UNIT, "ms_per_call": 1e3 * sum(fp) / len(fp)},
         "mixed_over_fp64": value / ws / fp64_val,
         "stage_ms": mean_stage,
+        "gradient": grads,
+        "serving": serving,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(theta.nbytes),
                 "d2h_bytes_per_step": int(H * (8 + 8 + 4))},
         # per step: k_fwd_nodes, k_inv_nodes, k_grid, k_hyper_final, k_event_mixed,
@@ -346,7 +431,7 @@ def main():
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cat, theta[0])
+        line["cpu_baseline"] = cpu_baseline(cat, theta)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -245,6 +245,10 @@ typedef struct {
     int64_t admitted_bytes_peak;
 } chimera_serve_stats_t;
 int chimera_serve_stats(chimera_ctx *ctx, chimera_serve_stats_t *out);
+/* chimera_serve_reset_stats: forget the latencies and counters gathered so
+ * far (e.g. after warm-up requests); requests in flight are still counted
+ * when they complete.  Errors: INVALID_ARG for a NULL ctx. */
+int chimera_serve_reset_stats(chimera_ctx *ctx);
 
 /*
  * Tracing.  chimera_set_trace(ctx, 1) makes the synchronous likelihood

@@ -107,6 +107,7 @@ ABI = {
     "chimera_serve_poll": (C.c_int, [_P, C.c_uint64, C.c_int64, _pd, _pd, _pi32]),
     "chimera_serve_cancel": (C.c_int, [_P, C.c_uint64]),
     "chimera_serve_stats": (C.c_int, [_P, C.POINTER(ServeStats)]),
+    "chimera_serve_reset_stats": (C.c_int, [_P]),
     "chimera_strerror": (C.c_char_p, [C.c_int]),
     "chimera_last_error": (C.c_char_p, []),
     "chimera_set_trace": (C.c_int, [_P, C.c_int]),
@@ -283,6 +284,10 @@ def chimera_serve_stats(h):
     s = ServeStats()
     _ck(lib().chimera_serve_stats(h, C.byref(s)), "chimera_serve_stats")
     return {k: getattr(s, k) for k, _ in ServeStats._fields_}
+
+
+def chimera_serve_reset_stats(h):
+    _ck(lib().chimera_serve_reset_stats(h), "chimera_serve_reset_stats")
 
 
 def chimera_set_trace(h, enable=True):

@@ -953,6 +953,11 @@ int chimera_serve_cancel(chimera_ctx *h, uint64_t ticket) {
     return serve_cancel(h->c, ticket);
 }
 
+int chimera_serve_reset_stats(chimera_ctx *h) {
+    if (!h) { set_error("bad argument"); return CHIMERA_ERR_INVALID_ARG; }
+    return serve_reset_stats(h->c);
+}
+
 int chimera_serve_stats(chimera_ctx *h, chimera_serve_stats_t *out) {
     if (!h || !out) { set_error("bad argument"); return CHIMERA_ERR_INVALID_ARG; }
     return serve_stats(h->c, out);

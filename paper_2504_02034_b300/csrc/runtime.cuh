@@ -143,6 +143,7 @@ int serve_poll(Ctx &ctx, uint64_t ticket, int64_t timeout_us, double *lnL, doubl
                int32_t *status);
 int serve_cancel(Ctx &ctx, uint64_t ticket);
 int serve_stats(Ctx &ctx, chimera_serve_stats_t *out);
+int serve_reset_stats(Ctx &ctx);
 void serve_shutdown(Ctx &ctx);
 
 }  // namespace chim

@@ -367,6 +367,16 @@ int serve_stats(Ctx &ctx, chimera_serve_stats_t *out) {
     return CHIMERA_OK;
 }
 
+int serve_reset_stats(Ctx &ctx) {
+    Server *s = get_server(ctx);
+    std::lock_guard<std::mutex> lk(s->m);
+    s->lat_ms.clear();
+    s->batches = 0;
+    s->points = 0;
+    s->admitted_peak = 0;
+    return CHIMERA_OK;
+}
+
 void serve_shutdown(Ctx &ctx) {
     Server *s = ctx.server;
     if (!s) return;

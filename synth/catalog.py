@@ -299,7 +299,7 @@ _CONFIGS = {
             gal_fixed=200, n_points=1),
     2: dict(n_events=300, n_pe=5000, n_inj=2_000_000, n_z=1000, Xi0=1.0, n_points=16),
     3: dict(n_events=300, n_pe=5000, n_inj=2_000_000, n_z=1000, Xi0=1.0, photo=True,
-            gal_factor=3.0, gal_storage=GAL_F16, n_points=512),
+            gal_factor=3.0, gal_storage=GAL_BF16, n_points=512),
     4: dict(n_events=5000, n_pe=4000, n_inj=5_000_000, n_z=1000, Xi0=1.0, n_points=64,
             vary_Om=True),
 }

@@ -79,6 +79,7 @@ def test_null_arguments_rejected(chim):
     assert L.chimera_create(None, 0, 0) == chim.CHIMERA_ERR_INVALID_ARG
     assert L.chimera_loglike(None, 0, 1, None, 0, None, None, None) == chim.CHIMERA_ERR_INVALID_ARG
     assert L.chimera_serve_stats(None, None) == chim.CHIMERA_ERR_INVALID_ARG
+    assert L.chimera_serve_reset_stats(None) == chim.CHIMERA_ERR_INVALID_ARG
     L.chimera_destroy(None)
 
 

@@ -700,7 +700,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_select_adj(DevCatalog c, CallPt
             const float zz = chimd::hermite4(p.inv32[(size_t)h * NU + k], a4.y);
             if (!(zz <= c.z_max32)) continue;
             const float a1 = 1.f + zz, lz = log1pf(zz);
-            const float fm1 = expf(a4.z - lz), fm2 = expf(a4.w - lz);
+            const float lz2 = lz * 1.44269504088896340736f;
+            const float fm1 = exp2f(a4.z - lz2), fm2 = exp2f(a4.w - lz2);
             const float mmin = hp.mmin32, mmax = hp.mmax32;
             if (!(fm1 >= mmin && fm1 <= mmax && fm2 >= mmin && fm2 <= fm1) || !(fm1 > mmin)) continue;
             const float x = (fm1 - hp.mu32) * hp.inv_sg32;

@@ -151,7 +151,7 @@ int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat) {
         {(void **)&ws.invZ32, sizeof(float) * (size_t)std::max<int64_t>(ng, 1)},
         {(void **)&ws.grad, sizeof(double) * 12 * (size_t)Hn},
         {(void **)&ws.pairs, sizeof(unsigned long long) * (size_t)Hn},
-        {(void **)&ws.dk, sizeof(double) * (size_t)Hn * NT_FWD},
+        {(void **)&ws.dk, sizeof(double) * 2 * (size_t)Hn * NT_FWD},
         {(void **)&ws.fmax_bits, sizeof(unsigned long long) * (size_t)Hn},
     };
     for (auto &it : items) {
@@ -629,7 +629,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         tcoord(d->inj_dL[j], k, f);
         float kb;
         memcpy(&kb, &k, 4);
-        i32a[j] = make_float4(kb, f, (float)std::log(d->inj_m1d[j]), (float)std::log(d->inj_m2d[j]));
+        i32a[j] = make_float4(kb, f, (float)std::log2(d->inj_m1d[j]), (float)std::log2(d->inj_m2d[j]));
         i32b[j] = make_float2((float)d->inj_dL[j], (float)d->inj_log_pi[j]);
     }
     std::vector<int64_t> ev_soff(d->sample_off, d->sample_off + ne + 1);

@@ -78,7 +78,7 @@ __device__ double std_normal_cdf(double x) { return 0.5 * erfc(-x * 0.7071067811
 
 // K1b.1: d_L^gw and J at the forward nodes of every hyperpoint; J <= 0 on
 // z <= 10 sets the NONMONOTONE bit.
-__global__ void __launch_bounds__(HYP_THREADS) k_fwd_nodes(CallPtrs p, double *dk) {
+__global__ void __launch_bounds__(HYP_THREADS) k_fwd_nodes(CallPtrs p, double *dk, double *jk) {
     const int h = blockIdx.y;
     const int k = blockIdx.x * HYP_THREADS + threadIdx.x;
     if (k >= NT_FWD) return;
@@ -87,42 +87,49 @@ __global__ void __launch_bounds__(HYP_THREADS) k_fwd_nodes(CallPtrs p, double *d
     double d, J;
     chimd::dgw_J(k * HT, cH * p.fwd[h][k], th, cH, &d, &J);
     dk[(size_t)h * NT_FWD + k] = d;
+    jk[(size_t)h * NT_FWD + k] = J;
     if (k <= K_Z10 && !(J > 0.0)) atomicOr(p.status + h, CHIMERA_PT_NONMONOTONE);
 }
 
-// K1b.2: inverse nodes z(u_k), d = d_top u_k^2, by bracketing on the forward
-// nodes and Newton on the Hermite-interpolated forward relation.
-__global__ void __launch_bounds__(HYP_THREADS) k_inv_nodes(DevCatalog c, CallPtrs p, const double *dkall) {
+// K1b.2: inverse nodes z(u_k), d = d_top u_k^2: bracketing on the forward
+// nodes (staged in shared memory), cubic Hermite of z(d) between the two
+// bracketing nodes (slopes 1/J), then one Newton step on the
+// Hermite-interpolated forward relation.
+__global__ void __launch_bounds__(HYP_THREADS) k_inv_nodes(DevCatalog c, CallPtrs p, const double *dkall,
+                                                          const double *jkall) {
+    __shared__ double sdk[NT_FWD];
     const int h = blockIdx.y;
     const int k = blockIdx.x * HYP_THREADS + threadIdx.x;
+    const double *dk = dkall + (size_t)h * NT_FWD;
+    const double *jk = jkall + (size_t)h * NT_FWD;
+    for (int i = threadIdx.x; i < NT_FWD; i += HYP_THREADS) sdk[i] = dk[i];
+    __syncthreads();
     if (k > NU) return;
     const double *th = p.theta + 12 * h;
-    const double *dk = dkall + (size_t)h * NT_FWD;
     const double *fwd = p.fwd[h];
     const double cH = C_KMS / th[0], Om = th[1];
     const double dtop = c.d_top;
     double u = (double)k / NU, d = dtop * u * u;
     double z = 0.0, dzdu = 0.0;
     if (k > 0) {
-        if (!(d <= dk[NT_FWD - 1])) {
+        if (!(d <= sdk[NT_FWD - 1])) {
             z = CUDART_NAN;
             dzdu = CUDART_NAN;
         } else {
-            int lo = 0, hi = NT_FWD - 1;  // dk[lo] <= d < dk[hi]
+            int lo = 0, hi = NT_FWD - 1;  // sdk[lo] <= d < sdk[hi]
             while (hi - lo > 1) {
                 int mid = (lo + hi) >> 1;
-                if (dk[mid] <= d) lo = mid; else hi = mid;
+                if (sdk[mid] <= d) lo = mid; else hi = mid;
             }
-            double den = dk[hi] - dk[lo];
-            double fr = den > 0.0 ? (d - dk[lo]) / den : 0.0;
-            z = (lo + fr) * HT;
+            const double dl = sdk[lo], dh = sdk[hi], den = dh - dl;
+            const double t = den > 0.0 ? (d - dl) / den : 0.0;
+            const double t2 = t * t, t3 = t2 * t;
+            z = (2 * t3 - 3 * t2 + 1) * (lo * HT) + (t3 - 2 * t2 + t) * den / jk[lo] +
+                (-2 * t3 + 3 * t2) * (hi * HT) + (t3 - t2) * den / jk[hi];
             double dd, J;
-            for (int it = 0; it < 2; it++) {
-                chimd::dgw_J(z, cH * chimd::dc_hermite(fwd, z, Om), th, cH, &dd, &J);
-                double step = (dd - d) / J;
-                if (isfinite(step)) z -= step;
-            }
             chimd::dgw_J(z, cH * chimd::dc_hermite(fwd, z, Om), th, cH, &dd, &J);
+            const double step = (dd - d) / J;
+            if (isfinite(step)) z -= step;
             dzdu = 2.0 * u * dtop / J;
         }
     }
@@ -157,31 +164,46 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
     const double Fm = __longlong_as_double((long long)fmax_bits[h]);
     const double Fs = Fm > 0.0 ? Fm : 1.0;
     const double2 *nd = p.inv64 + (size_t)h * (NU + 1);
+    __shared__ double sc[8];
+    const double inv_nu = 1.0 / NU;  // exact: NU is a power of two
     for (int k = t; k < NU; k += HYP_THREADS) {
         double2 a = nd[k], b = nd[k + 1];
         p.inv32[(size_t)h * NU + k] =
-            make_float4((float)a.x, (float)(a.y / NU), (float)b.x, (float)(b.y / NU));
+            make_float4((float)a.x, (float)(a.y * inv_nu), (float)b.x, (float)(b.y * inv_nu));
     }
+    const double iFs = 1.0 / Fs;
     for (int a = t; a < c.n_z; a += HYP_THREADS)
-        p.F32[(size_t)h * c.n_z + a] = (float)(p.F64[(size_t)h * c.n_z + a] / Fs);
+        p.F32[(size_t)h * c.n_z + a] = (float)(p.F64[(size_t)h * c.n_z + a] * iFs);
+    const double *th = p.theta + 12 * h;
+    const double alpha = th[4], mu = th[5], sg = th[6], mmin = th[7], mmax = th[8];
+    const double lam = c.lambda_g, beta = c.beta;
+    // the independent FP64 scalars, one per lane of warp 0
+    if (t < 4) {
+        double v = 0.0;
+        if (t == 0)
+            v = fabs(1.0 - alpha) < 1e-12 ? log(mmax / mmin)
+                                          : (pow(mmax, 1.0 - alpha) - pow(mmin, 1.0 - alpha)) / (1.0 - alpha);
+        else if (t == 1)
+            v = std_normal_cdf((mmax - mu) / sg) - std_normal_cdf((mmin - mu) / sg);
+        else if (t == 2)
+            v = pow(mmin, 1.0 + beta);
+        else
+            v = chimd::dc_hermite(p.fwd[h], c.z_max, th[1]);
+        sc[t] = v;
+    }
+    __syncthreads();
     if (t == 0) {
-        const double *th = p.theta + 12 * h;
         HP hp;
         for (int k = 0; k < 12; k++) hp.th[k] = th[k];
         const double cH = C_KMS / th[0];
         hp.cH = cH;
-        const double alpha = th[4], mu = th[5], sg = th[6], mmin = th[7], mmax = th[8];
-        const double lam = c.lambda_g, beta = c.beta;
-        double plint = fabs(1.0 - alpha) < 1e-12
-                           ? log(mmax / mmin)
-                           : (pow(mmax, 1.0 - alpha) - pow(mmin, 1.0 - alpha)) / (1.0 - alpha);
-        double den = std_normal_cdf((mmax - mu) / sg) - std_normal_cdf((mmin - mu) / sg);
+        const double plint = sc[0], den = sc[1];
         hp.c_pl = (1.0 - lam) / plint;
         hp.c_g = den > 0.0 ? lam / (sg * 2.50662827463100050242 * den) : 0.0;
         hp.b1 = 1.0 + beta;
-        hp.mmin_b1 = pow(mmin, 1.0 + beta);
+        hp.mmin_b1 = sc[2];
         hp.lmmin = log(mmin);
-        hp.dc_zmax = cH * chimd::dc_hermite(p.fwd[h], c.z_max, th[1]);
+        hp.dc_zmax = cH * sc[3];
         hp.d_valid = dkall[(size_t)h * NT_FWD + K_Z10];
         hp.F_scale = Fs;
         double tv = sqrt(hp.d_valid / c.d_top) * NU;
@@ -228,8 +250,9 @@ void launch_fwd_table(double Om, double *out, cudaStream_t st) {
 void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, double *dk,
                          unsigned long long *fmax_bits, cudaStream_t st) {
     cudaMemsetAsync(fmax_bits, 0, sizeof(unsigned long long) * H, st);
-    k_fwd_nodes<<<dim3((NT_FWD + HYP_THREADS - 1) / HYP_THREADS, H), HYP_THREADS, 0, st>>>(p, dk);
-    k_inv_nodes<<<dim3((NU + 1 + HYP_THREADS - 1) / HYP_THREADS, H), HYP_THREADS, 0, st>>>(c, p, dk);
+    double *jk = dk + (size_t)H * NT_FWD;  // J at the forward nodes
+    k_fwd_nodes<<<dim3((NT_FWD + HYP_THREADS - 1) / HYP_THREADS, H), HYP_THREADS, 0, st>>>(p, dk, jk);
+    k_inv_nodes<<<dim3((NU + 1 + HYP_THREADS - 1) / HYP_THREADS, H), HYP_THREADS, 0, st>>>(c, p, dk, jk);
     k_grid<<<dim3((c.n_z + HYP_THREADS - 1) / HYP_THREADS, H), HYP_THREADS, 0, st>>>(c, p, fmax_bits);
     k_hyper_final<<<H, HYP_THREADS, 0, st>>>(c, p, dk, fmax_bits);
 }

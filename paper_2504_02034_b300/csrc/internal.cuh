@@ -102,7 +102,7 @@ struct DevCatalog {
     float4 *s32;          // (inverse-table interval k as int bits, fraction f, log2 m1_det, log2 m2_det)
     double *sd64, *sm1_64, *sm2_64;
     // detected injections
-    float4 *i32a;         // (k bits, f, ln m1_det, ln m2_det)
+    float4 *i32a;         // (k bits, f, log2 m1_det, log2 m2_det)
     float2 *i32b;         // (d_L, ln pi_inj)
     double *id64, *im1_64, *im2_64, *ilp64;
 };
@@ -130,7 +130,8 @@ struct CallPtrs {
 // K1a: forward table D_c(z_k) / (c/H0) for one Om into `out` [NT_FWD].
 void launch_fwd_table(double Om, double *out, cudaStream_t st);
 // K1b: per-hyperpoint parameters, inverse tables, grid factors, status.
-// dk: [H x NT_FWD] scratch, fmax_bits: [H] scratch.
+// dk: [2 x H x NT_FWD] scratch (d_L^gw, then J, at the forward nodes),
+// fmax_bits: [H] scratch.
 void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, double *dk,
                          unsigned long long *fmax_bits, cudaStream_t st);
 // K3: galaxy redshift prior on the grid for one Om.  dv: [n_z] scratch,
@@ -188,7 +189,7 @@ __device__ __forceinline__ double xi_of(double z, double xi0, double n) {
 __device__ __forceinline__ void dgw_J(double z, double Dc, const double *th, double cH, double *d,
                                       double *J) {
     double a = 1.0 + z;
-    double p = pow(a, -th[3]);
+    double p = exp(-th[3] * log(a));  // (1+z)^-n
     double xi = th[2] + (1.0 - th[2]) * p;
     double dxi = -th[3] * (1.0 - th[2]) * p / a;
     double E = E_of(z, th[1]);
@@ -198,8 +199,8 @@ __device__ __forceinline__ void dgw_J(double z, double Dc, const double *th, dou
 
 // Madau-Dickinson shape (Sec. 3.1), unnormalised.
 __device__ __forceinline__ double psi_of(double z, const double *th) {
-    double a = 1.0 + z;
-    return pow(a, th[9]) / (1.0 + pow(a / (1.0 + th[11]), th[9] + th[10]));
+    const double la = log(1.0 + z);
+    return exp(th[9] * la) / (1.0 + exp((th[9] + th[10]) * (la - log1p(th[11]))));
 }
 
 __device__ __forceinline__ float hermite4(float4 nd, float f) {

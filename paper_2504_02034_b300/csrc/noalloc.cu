@@ -41,7 +41,7 @@ constexpr size_t OFF_INV32 = al(OFF_INV64 + sizeof(double2) * ST_HMAX * (NU + 1)
 constexpr size_t OFF_F64 = al(OFF_INV32 + sizeof(float4) * ST_HMAX * NU);
 constexpr size_t OFF_F32 = al(OFF_F64 + sizeof(double) * ST_HMAX * ST_NZ);
 constexpr size_t OFF_DK = al(OFF_F32 + sizeof(float) * ST_HMAX * ST_NZ);
-constexpr size_t OFF_FMAX = al(OFF_DK + sizeof(double) * ST_HMAX * NT_FWD);
+constexpr size_t OFF_FMAX = al(OFF_DK + sizeof(double) * 2 * ST_HMAX * NT_FWD);  // d and J per node
 constexpr size_t OFF_FWD = al(OFF_FMAX + sizeof(unsigned long long) * ST_HMAX);
 constexpr size_t OFF_SELP = al(OFF_FWD + sizeof(double) * ST_HMAX * NT_FWD);
 constexpr size_t OFF_DTOP = al(OFF_SELP + sizeof(double) * 2 * ST_HMAX * ST_CHUNK_MAX);

@@ -68,7 +68,7 @@ struct Workspace {
     double *lnI = nullptr, *bw = nullptr, *selp = nullptr;
     double *lnL = nullptr, *neff = nullptr, *xi = nullptr;
     double *dv = nullptr, *invZ64 = nullptr;
-    double *dk = nullptr;                  // [H x NT_FWD] forward-node scratch
+    double *dk = nullptr;                  // [2 x H x NT_FWD] forward-node scratch (d, J)
     unsigned long long *fmax_bits = nullptr;  // [H]
     float *invZ32 = nullptr;
     // adjoint buffers

@@ -12,6 +12,7 @@
 #include <math_constants.h>
 
 #include "internal.cuh"
+#include "mass.cuh"
 
 namespace chim {
 
@@ -27,77 +28,85 @@ __device__ __forceinline__ float warp_sumf(float v) {
     return v;
 }
 
-// mixed: FP32 per term with full-accuracy libm, FP64 across warps
+// mixed: FP32 per term in the log2 domain with SFU exp2 / log2 / reciprocal
+// (relative error ~1e-6 per term, independent between injections), FP64
+// across warps.  The mass model is the event kernel's (mass_weight32).  A
+// block takes one chunk of injections for SEL_HB hyperpoints: every
+// injection is read once and evaluated for all of them.
+constexpr int SEL_HB = 2;
+
+struct SelConst {
+    MixParams q;
+    const float4 *inv;
+    float xi0, n, om, gam, gk, l2zp, cH, k3;
+};
+
 __global__ void __launch_bounds__(SEL_THREADS) k_select_mixed(DevCatalog c, CallPtrs p, int H) {
-    __shared__ double red[2 * (SEL_THREADS / 32)];
-    const int h = blockIdx.y, chunk = blockIdx.x;
-    const HP &hp = p.hp[h];
-    const float4 *inv = p.inv32 + (size_t)h * NU;
-    const int kv = hp.k_valid;
-    const float fv = hp.f_valid;
-    const float xi0 = hp.xi0_32, n = hp.n32, om = hp.om32;
-    const float gam = hp.gam32, kap = hp.kap32, l1zp = hp.l1zp32;
-    const float cH = hp.cH32, zmax = c.z_max32;
-    const float inv_dc3 = hp.inv_dc3_32;
-    const float mmin = hp.mmin32, mmax = hp.mmax32, mu = hp.mu32;
-    const float inv_sg = hp.inv_sg32, alpha = hp.alpha32;
-    const float c_pl = hp.c_pl32, c_g = hp.c_g32, beta = hp.beta32;
-    const float b1 = hp.b1_32, mmin_b1 = hp.mmin_b1_32, lmmin = hp.lmmin32;
-    float s1 = 0.f, s2 = 0.f;
-    const int64_t base = (int64_t)chunk * SEL_CHUNK;
-    for (int q = 0; q < SEL_PER_THREAD; q++) {
-        int64_t j = base + q * SEL_THREADS + threadIdx.x;
-        if (j >= c.n_det) break;
-        float4 a = c.i32a[j];
-        float2 bq = c.i32b[j];
-        int k = __float_as_int(a.x);
-        float f = a.y;
-        if (!((k < kv) || (k == kv && f <= fv))) continue;
-        float z = chimd::hermite4(inv[k], f);
-        if (!(z <= zmax)) continue;
-        float lz = log1pf(z), ap = 1.f + z;
-        float lm1 = a.z - lz, lm2 = a.w - lz;
-        float m1 = expf(lm1), m2 = expf(lm2);
-        if (!(m1 >= mmin && m1 <= mmax && m2 >= mmin && m2 <= m1)) continue;
-        float x = (m1 - mu) * inv_sg;
-        float p1 = c_pl * expf(-alpha * lm1) + c_g * expf(-0.5f * x * x);
-        float p2;
-        if (fabsf(b1) < 1e-6f) {
-            float l = lm1 - lmmin;
-            p2 = l > 0.f ? 1.f / (m2 * l) : 0.f;
-        } else {
-            float den = m1 * expf(beta * lm1) - mmin_b1;
-            p2 = den > 0.f ? b1 * expf(beta * lm2) / den : 0.f;
-        }
-        float pw = expf(-n * lz);
-        float xi = xi0 + (1.f - xi0) * pw;
-        float dxi = -n * (1.f - xi0) * pw / ap;
-        float Dc = bq.x / (ap * xi);
-        float E = sqrtf(om * ap * ap * ap + 1.f - om);
-        float J = (Dc + ap * cH / E) * xi + ap * Dc * dxi;
-        float psi = expf(gam * lz) / (1.f + expf((gam + kap) * (lz - l1zp)));
-        float pz = 3.f * cH * Dc * Dc / E * inv_dc3;
-        float s = p1 * p2 * psi * pz / (ap * ap * ap * fabsf(J)) * expf(-bq.y);
-        s1 += s;
-        s2 += s * s;
-    }
-    s1 = warp_sumf(s1);
-    s2 = warp_sumf(s2);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        red[2 * wid] = s1;
-        red[2 * wid + 1] = s2;
+    __shared__ double red[2 * SEL_HB * (SEL_THREADS / 32)];
+    __shared__ SelConst scs[SEL_HB];
+    const int chunk = blockIdx.x, h0 = blockIdx.y * SEL_HB;
+    const int nh = min(SEL_HB, H - h0);
+    if (threadIdx.x < nh) {
+        const HP &hp = p.hp[h0 + threadIdx.x];
+        SelConst k;
+        k.q = mix_params(hp);
+        k.inv = p.inv32 + (size_t)(h0 + threadIdx.x) * NU;
+        k.xi0 = hp.xi0_32; k.n = hp.n32; k.om = hp.om32;
+        k.gam = hp.gam32; k.gk = hp.gam32 + hp.kap32;
+        k.l2zp = hp.l1zp32 * 1.44269504088896340736f;
+        k.cH = hp.cH32; k.k3 = 3.f * hp.cH32 * hp.inv_dc3_32;
+        scs[threadIdx.x] = k;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double a1 = 0.0, a2 = 0.0;
-        for (int w = 0; w < SEL_THREADS / 32; w++) {
-            a1 += red[2 * w];
-            a2 += red[2 * w + 1];
+    const float zmax = c.z_max32;
+    float s1[SEL_HB], s2[SEL_HB];
+#pragma unroll
+    for (int hb = 0; hb < SEL_HB; hb++) s1[hb] = s2[hb] = 0.f;
+    const int64_t base = (int64_t)chunk * SEL_CHUNK;
+    for (int qq = 0; qq < SEL_PER_THREAD; qq++) {
+        const int64_t j = base + qq * SEL_THREADS + threadIdx.x;
+        if (j >= c.n_det) break;
+        const float4 a = __ldg(c.i32a + j);
+        const float2 bq = __ldg(c.i32b + j);
+        const int k = __float_as_int(a.x);
+        const float ipi = ex2(-bq.y * 1.44269504088896340736f);  // 1 / pi_inj
+#pragma unroll
+        for (int hb = 0; hb < SEL_HB; hb++) {
+            if (hb >= nh) break;
+            const SelConst &K = scs[hb];
+            if (!((k < K.q.kv) || (k == K.q.kv && a.y <= K.q.fv))) continue;
+            const float z = chimd::hermite4(__ldg(K.inv + k), a.y);
+            if (!(z <= zmax)) continue;
+            const float ap = 1.f + z, lz2 = __log2f(ap), rap = __fdividef(1.f, ap);
+            const float w = mass_weight32(K.q, a.z - lz2, a.w - lz2);
+            const float pw = ex2(-K.n * lz2);  // (1+z)^-n
+            const float xi = K.xi0 + (1.f - K.xi0) * pw;
+            const float dxi = -K.n * (1.f - K.xi0) * pw * rap;
+            const float Dc = __fdividef(bq.x * rap, xi);  // D_c = d_L / ((1+z) Xi)
+            const float rE = rsqrtf(K.om * ap * ap * ap + 1.f - K.om);
+            const float J = (Dc + ap * K.cH * rE) * xi + ap * Dc * dxi;
+            const float psi = __fdividef(ex2(K.gam * lz2), 1.f + ex2(K.gk * (lz2 - K.l2zp)));
+            const float pz = K.k3 * Dc * Dc * rE;
+            const float sv = __fdividef(w * psi * pz * rap * rap * rap, fabsf(J)) * ipi;
+            s1[hb] += sv;
+            s2[hb] = fmaf(sv, sv, s2[hb]);
         }
-        double *o = p.selp + ((size_t)h * p.n_chunk + chunk) * 2;
-        o[0] = a1;
-        o[1] = a2;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int hb = 0; hb < SEL_HB; hb++) {
+        const float a1 = warp_sumf(s1[hb]), a2 = warp_sumf(s2[hb]);
+        if (lane == 0) {
+            red[(2 * hb) * (SEL_THREADS / 32) + wid] = a1;
+            red[(2 * hb + 1) * (SEL_THREADS / 32) + wid] = a2;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * nh) {
+        double acc = 0.0;
+        for (int w = 0; w < SEL_THREADS / 32; w++) acc += red[threadIdx.x * (SEL_THREADS / 32) + w];
+        const int hb = threadIdx.x >> 1;
+        p.selp[((size_t)(h0 + hb) * p.n_chunk + chunk) * 2 + (threadIdx.x & 1)] = acc;
     }
 }
 
@@ -243,9 +252,8 @@ int selection_chunks(const DevCatalog &c) {
 }
 
 void launch_selection(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, cudaStream_t st) {
-    dim3 grid(p.n_chunk, H);
-    if (fp64) k_select_fp64<<<grid, SEL_THREADS, 0, st>>>(c, p, H);
-    else k_select_mixed<<<grid, SEL_THREADS, 0, st>>>(c, p, H);
+    if (fp64) k_select_fp64<<<dim3(p.n_chunk, H), SEL_THREADS, 0, st>>>(c, p, H);
+    else k_select_mixed<<<dim3(p.n_chunk, (H + SEL_HB - 1) / SEL_HB), SEL_THREADS, 0, st>>>(c, p, H);
 }
 
 void launch_combine(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st) {

@@ -562,6 +562,17 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
             for (int64_t g0 = s0; g0 < s1; g0 += GROUP_MAX)
                 emit(g0, (int)std::min<int64_t>(GROUP_MAX, s1 - g0));
         }
+        // costliest groups first (samples x (ln d_L spread + window)), so that
+        // the warps of a block finish their last groups close together
+        {
+            auto cost_of = [&](const int4 &g) {
+                const int64_t st = a + g.x;
+                const double spread = std::log(sd[st + g.y - 1]) - std::log(sd[st]);
+                return (double)((g.y + 31) / 32) * (spread + 12.0 * sl);
+            };
+            std::stable_sort(groups.begin() + ev_goff[i], groups.end(),
+                             [&](const int4 &x, const int4 &y) { return cost_of(x) > cost_of(y); });
+        }
         max_groups = std::max<int>(max_groups, (int)groups.size() - ev_goff[i]);
     }
     ev_goff[ne] = (int32_t)groups.size();

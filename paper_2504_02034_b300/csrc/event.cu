@@ -106,12 +106,14 @@ struct MixLayout {
         seg_pad = pad4(max_seg + 1);
         gmax_pad = pad4(max_groups);
     }
-    // int4: group metadata; floats: zs, ws, Fs, D tables, C table, group
-    // results, segment prefactors; ints: segment valid counts and starts
+    // int4: group metadata; floats: zs, ws, Fs, D tables, C table (both
+    // signs of tau), group results, segment prefactors; ints: segment valid
+    // counts, starts and KDE support ranges
     __host__ __device__ size_t bytes() const {
         return sizeof(int4) * (size_t)gmax_pad +
-               sizeof(float) * (2 * (size_t)ns_pad + nz_pad + (size_t)EV_WARPS * DCAP + CCAP + gmax_pad + seg_pad) +
-               sizeof(int) * 2 * (size_t)seg_pad + sizeof(double) * (8 + EV_WARPS * 8);
+               sizeof(float) * (2 * (size_t)ns_pad + nz_pad + (size_t)EV_WARPS * DCAP + 2 * CCAP + gmax_pad + seg_pad) +
+               sizeof(int) * 4 * (size_t)seg_pad + sizeof(double) * 2 * (size_t)seg_pad +
+               sizeof(double) * (8 + EV_WARPS * 8);
     }
 };
 
@@ -156,6 +158,59 @@ __device__ __forceinline__ void chains(const float *D, int nq, const float (&u)[
     for (int r = 0; r < R; r++) acc[r] = A[r] * fmaf(Bi[r], ab[r], af[r]);
 }
 
+// As stage_table<true>, as float4: a_first and the C-table pointer Cq
+// (C at tau = -4 nq) are multiples of 4, G and Fs are 16-byte aligned, so
+// each lane builds four entries from one 128-bit load of each operand.
+__device__ __forceinline__ void stage_table4(float *D, int nq, int a_first, int A0, int A1, const float *G,
+                                             const float *Fs, const float *Cq, float scale, int lane) {
+    float4 *D4 = reinterpret_cast<float4 *>(D);
+    const float4 *C4 = reinterpret_cast<const float4 *>(Cq);
+#pragma unroll 2
+    for (int i = lane; i < 2 * nq; i += 32) {
+        const int a4 = a_first + 4 * i;
+        float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (a4 + 3 >= A0 && a4 <= A1) {
+            // a4 >= A0 - 3 >= -3 and a4 is a multiple of 4, so a4 >= 0; a4 <= A1 < nz
+            float4 g = __ldg(reinterpret_cast<const float4 *>(G + a4));
+            const float4 f = *reinterpret_cast<const float4 *>(Fs + a4);
+            const float4 cc = C4[i];
+            val = make_float4(cc.x * scale * f.x * g.x, cc.y * scale * f.y * g.y, cc.z * scale * f.z * g.z,
+                              cc.w * scale * f.w * g.w);
+            if (a4 < A0 || a4 + 3 > A1) {
+                if (a4 < A0 || a4 > A1) val.x = 0.f;
+                if (a4 + 1 < A0 || a4 + 1 > A1) val.y = 0.f;
+                if (a4 + 2 < A0 || a4 + 2 > A1) val.z = 0.f;
+                if (a4 + 3 < A0 || a4 + 3 > A1) val.w = 0.f;
+            }
+        }
+        D4[i] = val;
+    }
+}
+
+// A group of at most SMALL_CNT samples: lanes take the grid points of the
+// group's range, each sums the samples whose window holds it (one SFU
+// exponential per pair); cheaper than a table for so few samples.
+constexpr int SMALL_CNT = 6;
+__device__ __forceinline__ float small_group(const float *z, const float *w, int cnt, int A0, int A1,
+                                             const float *G, const float *Fs, float dz, float inv_s2b,
+                                             float halfk, int lane) {
+    float acc = 0.f;
+#pragma unroll 2
+    for (int a = A0 + lane; a <= A1; a += 32) {
+        const float za = a * dz;
+        const float h = Fs[a] * __ldg(G + a);
+        float k = 0.f;
+        for (int j = 0; j < cnt; j++) {
+            const float d = za - z[j];
+            const float x = d * inv_s2b;
+            const float e = ex2(-1.44269504088896340736f * x * x);
+            k = fabsf(d) <= halfk ? fmaf(w[j], e, k) : k;
+        }
+        acc = fmaf(k, h, acc);
+    }
+    return acc;
+}
+
 // R samples per lane (lane, lane+32, ...) of a group sharing one table.
 template <int R>
 __device__ __forceinline__ float union_samples(const float *D, int nq, const float *z, const float *w, int cnt,
@@ -180,6 +235,14 @@ __device__ __forceinline__ float union_samples(const float *D, int nq, const flo
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -253,12 +316,17 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
     float *ws = zs + L.ns_pad;
     float *Fs = ws + L.ns_pad;
     float *Dt = Fs + L.nz_pad;
-    float *CT = Dt + EV_WARPS * DCAP;
-    float *gres = CT + CCAP;
+    float *CT2 = Dt + EV_WARPS * DCAP;  // C at tau = t - CCAP, t in [0, 2 CCAP)
+    float *CT = CT2 + CCAP;             // C at tau, tau in [-CCAP, CCAP)
+    float *gres = CT2 + 2 * CCAP;
     float *segpf = gres + L.gmax_pad;
     int *segv = reinterpret_cast<int *>(segpf + L.seg_pad);
     int *seglo = segv + L.seg_pad;
-    double *red = reinterpret_cast<double *>(seglo + L.seg_pad);
+    int *segA0 = seglo + L.seg_pad;  // KDE support of each segment on the grid
+    int *segA1 = segA0 + L.seg_pad;
+    long long *seg64 = reinterpret_cast<long long *>(segA1 + L.seg_pad);  // staged segment offsets
+    double *spf64 = reinterpret_cast<double *>(seg64 + L.seg_pad);        // staged prefactors
+    double *red = spf64 + L.seg_pad;
     __shared__ int s_gctr;
 
     const int h = blockIdx.x % H;
@@ -275,36 +343,63 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
     const int nz = c.n_z;
     const float dz = c.dz32;
     const float inv_dz = 1.f / dz;
-    // F(z_a) with the trapezoid weight folded in
-    for (int a = tid; a < nz; a += EV_THREADS)
-        Fs[a] = p.F32[(size_t)h * nz + a] * ((a == 0 || a == nz - 1) ? 0.5f : 1.f);
     if (tid == 0) s_gctr = 0;
-    // group and segment metadata of this event, staged once (the loads
-    // overlap phase A)
+    // ---- prologue: every per-event and per-point input the block needs is
+    // requested at once with cp.async (no register staging, no stall per
+    // load); the copies complete while the ring prologue is in flight.
+    const int64_t s0 = c.ev_soff[ev];
+    const int ns = (int)(c.ev_soff[ev + 1] - s0);
     const int g0 = c.ev_goff[ev];
     const int ngroups = c.ev_goff[ev + 1] - g0;
     const int sg0 = c.ev_segoff[ev], nseg = c.ev_segoff[ev + 1] - sg0;
-    for (int g = tid; g < ngroups; g += EV_THREADS) grp[g] = __ldg(c.groups + g0 + g);
+    const int2 kr = c.ev_krange[ev];
+    const float2 zr = c.ev_ref[ev];
+    const float4 *inv = p.inv32 + (size_t)h * NU;
+    const float4 *sp = c.s32 + s0;
+    // The samples stream through a ring of RING chunks of EV_THREADS float4
+    // in shared memory (cp.async, RING-1 chunks ahead; each thread copies and
+    // reads only its own slot), and the inverse-table nodes of the event's
+    // d_L range are staged once, so the per-sample node gather is a shared
+    // load.  Both live in the D-table region, which phase B reuses.
+    float4 *ring = reinterpret_cast<float4 *>(Dt);
+    float4 *snode = ring + RING * EV_THREADS;
+    const bool staged = kr.y - kr.x < NODE_CAP;  // block-uniform
+    if (staged)
+        for (int i = tid; i <= kr.y - kr.x; i += EV_THREADS) cp_async16(snode + i, inv + kr.x + i);
+    for (int g = tid; g < ngroups; g += EV_THREADS) cp_async16(grp + g, c.groups + g0 + g);
     for (int k = tid; k <= nseg; k += EV_THREADS) {
-        seglo[k] = (int)(c.seg_soff[sg0 + k] - c.ev_soff[ev]);
-        if (k < nseg) segpf[k] = (float)c.seg_pf[sg0 + k];
+        cp_async8(seg64 + k, c.seg_soff + sg0 + k);
+        if (k < nseg) cp_async8(spf64 + k, c.seg_pf + sg0 + k);
+    }
+    // F(z_a) (the trapezoid weight of the two end points is applied below)
+    for (int a = tid; a < nz; a += EV_THREADS) cp_async4(Fs + a, p.F32 + (size_t)h * nz + a);
+#pragma unroll
+    for (int cc = 0; cc < RING - 1; cc++) {
+        const int jj = cc * EV_THREADS + tid;
+        if (jj < ns) cp_async16(ring + cc * EV_THREADS + tid, sp + jj);
+        cp_async_commit();
+    }
+    cp_async_wait<RING - 2>();  // everything above except ring chunks 1 .. RING-2
+    __syncthreads();            // every thread's copies
+    if (tid == 0) Fs[0] *= 0.5f;
+    if (tid == 1 && nz > 1) Fs[nz - 1] *= 0.5f;
+    for (int k = tid; k <= nseg; k += EV_THREADS) {
+        seglo[k] = (int)(seg64[k] - s0);
+        if (k < nseg) segpf[k] = (float)spf64[k];
     }
 
     // ---- phase A: z_j, w_j and one-pass moments about the redshift of the
     // event's median d_L (shifted sums: no cancellation in the variance)
-    const int64_t s0 = c.ev_soff[ev];
-    const int ns = (int)(c.ev_soff[ev + 1] - s0);
-    const float4 *inv = p.inv32 + (size_t)h * NU;
     float zref;
     {
-        float2 r = c.ev_ref[ev];
-        int k = __float_as_int(r.x);
-        bool ok = (k < q.kv) || (k == q.kv && r.y <= q.fv);
-        zref = ok ? chimd::hermite4(__ldg(inv + k), r.y) : 0.f;
+        const int k = __float_as_int(zr.x);
+        const bool ok = (k < q.kv) || (k == q.kv && zr.y <= q.fv);
+        const float4 nd = !ok ? make_float4(0.f, 0.f, 0.f, 0.f)
+                              : (staged ? snode[k - kr.x] : __ldg(inv + k));
+        zref = chimd::hermite4(nd, zr.y);
         if (!isfinite(zref)) zref = 0.f;
     }
     float m[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // W1, Wd, Wd2, W2, n, Sd, Sd2
-    const float4 *sp = c.s32 + s0;
     // one sample: table coordinate -> z (Hermite on the node pair), log2
     // source masses, weight, moments; invalid samples (beyond d_L^gw(10))
     // get z = inf and w = 0 and stay out of the moments
@@ -321,25 +416,6 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
         zs[j] = ok ? z : CUDART_INF_F;
         ws[j] = w;
     };
-    // The samples stream through a ring of RING chunks of EV_THREADS float4
-    // in shared memory (cp.async, RING-1 chunks ahead; each thread copies and
-    // reads only its own slot), and the inverse-table nodes of the event's
-    // d_L range are staged once, so the per-sample node gather is a shared
-    // load.  Both live in the D-table region, which phase B reuses.
-    float4 *ring = reinterpret_cast<float4 *>(Dt);
-    float4 *snode = ring + RING * EV_THREADS;
-    const int2 kr = c.ev_krange[ev];
-    const bool staged = kr.y - kr.x < NODE_CAP;  // block-uniform
-    if (staged)
-        for (int i = tid; i <= kr.y - kr.x; i += EV_THREADS) cp_async16(snode + i, inv + kr.x + i);
-#pragma unroll
-    for (int cc = 0; cc < RING - 1; cc++) {
-        const int jj = cc * EV_THREADS + tid;
-        if (jj < ns) cp_async16(ring + cc * EV_THREADS + tid, sp + jj);
-        cp_async_commit();
-    }
-    cp_async_wait<RING - 2>();  // the nodes and chunk 0 of this thread
-    __syncthreads();            // every thread's node copies
     const int nch = (ns + EV_THREADS - 1) / EV_THREADS;
     for (int cc = 0; cc < nch; cc++) {
         const int jn = (cc + RING - 1) * EV_THREADS + tid;
@@ -383,9 +459,9 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
     const float halfk = KW32 * b;
 
     // ---- Gaussian factor table C_t = exp(-(ds t)^2) and segment valid counts
-    for (int t = tid; t < CCAP; t += EV_THREADS) {
-        float x = ds * (float)t;
-        CT[t] = __expf(-x * x);
+    for (int t = tid; t < 2 * CCAP; t += EV_THREADS) {
+        float x = ds * (float)(t - CCAP);
+        CT2[t] = __expf(-x * x);
     }
     for (int k = tid; k < nseg; k += EV_THREADS) {
         int lo = seglo[k], hi = seglo[k + 1];
@@ -395,6 +471,14 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
             if (zs[mm] < CUDART_INF_F) l = mm + 1; else r = mm;
         }
         segv[k] = l - lo;
+        // KDE support: the segment's samples' range +- KDE_MARGIN b
+        if (l > lo) {
+            segA0[k] = max(0, (int)ceilf((zs[lo] - (float)KDE_MARGIN * b) * inv_dz));
+            segA1[k] = min(nz - 1, (int)floorf((zs[l - 1] + (float)KDE_MARGIN * b) * inv_dz));
+        } else {
+            segA0[k] = 0;
+            segA1[k] = -1;
+        }
     }
     __syncthreads();
 
@@ -404,6 +488,7 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
     float *D = Dt + wid * DCAP;
     const float *prof = reinterpret_cast<const float *>(p.prof[h]);
     const int Tw = (int)ceilf(halfk * inv_dz + 0.5f);
+    const bool vec4 = (nz & 3) == 0;  // profile rows 16-byte aligned
     unsigned long long npairs = 0;  // algorithmic pair count (roofline only)
     while (true) {
         int g = 0;
@@ -420,9 +505,7 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
             const float pf = segpf[sk];
             const int64_t row = c.kde_mode == CHIMERA_KDE_MANY_1D ? (int64_t)(sg0 + sk) : (int64_t)ev;
             const float *G = prof + row * nz;
-            // KDE support of this segment: its samples' range +- KDE_MARGIN b
-            const int s_lo = max(0, (int)ceilf((zs[seg_lo] - (float)KDE_MARGIN * b) * inv_dz));
-            const int s_hi = min(nz - 1, (int)floorf((zs[seg_lo + segv[sk] - 1] + (float)KDE_MARGIN * b) * inv_dz));
+            const int s_lo = segA0[sk], s_hi = segA1[sk];  // KDE support of the segment
             const float zlo = zs[lo], zhi = zs[lo + cnt - 1];
             const float spread = zhi - zlo;
             if (p.pairs) {
@@ -438,8 +521,13 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
             const float fA0 = floorf((zlo - halfk) * inv_dz), fA1 = ceilf((zhi + halfk) * inv_dz);
             const int A0 = fA0 < (float)s_lo ? s_lo : (int)fA0;
             const int A1 = fA1 > (float)s_hi ? s_hi : (int)fA1;
-            if (A0 <= A1) {
-                const float tof = rintf(0.5f * (zlo + zhi) * inv_dz);
+            if (A0 <= A1 && cnt <= SMALL_CNT) {
+                // a few samples: lanes over the grid points, direct exponentials
+                v = small_group(zs + lo, ws + lo, cnt, A0, A1, G, Fs, dz, inv_s2b, halfk, lane);
+            } else if (A0 <= A1) {
+                // group origin; a multiple of 4 when the profile rows are
+                // 16-byte aligned, so that the table is staged as float4
+                const float tof = vec4 ? 4.f * rintf(0.125f * (zlo + zhi) * inv_dz) : rintf(0.5f * (zlo + zhi) * inv_dz);
                 const int t_o = tof > 1e8f ? 100000000 : (int)tof;
                 const int thi = A1 - t_o, tlo = t_o - A0;  // tau in [-tlo, thi]
                 const int nqf = thi >= 0 ? (thi + 4) >> 2 : 0;
@@ -454,7 +542,8 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
                     const float lnscale = spread > 8.f * b ? 20.f : 0.f;
                     const float scale = spread > 8.f * b ? 4.85165195e8f : 1.f;  // e^20
                     __syncwarp();
-                    stage_table<true>(D, 8 * nq, t_o - 4 * nq, A0, A1, G, Fs, CT, 4 * nq, scale, lane);
+                    if (vec4) stage_table4(D, nq, t_o - 4 * nq, A0, A1, G, Fs, CT - 4 * nq, scale, lane);
+                    else stage_table<true>(D, 8 * nq, t_o - 4 * nq, A0, A1, G, Fs, CT, 4 * nq, scale, lane);
                     __syncwarp();
                     const float zo = t_o * dz;
                     switch ((cnt + 31) >> 5) {

@@ -377,6 +377,18 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
         if (tid < 12) out[tid] = 0.0;
         return;
     }
+    // grid factor x trapezoid weight, staged in shared memory on the FP32
+    // path (F / F_scale: every term carries the same scale); read from the
+    // FP64 table on the FP64 path, whose block already holds double samples
+    float *Fw32 = reinterpret_cast<float *>(red + (ADJ_THREADS / 32 + 1) * 28);
+    auto Fw = [&](int a) -> T {
+        if constexpr (F64) {
+            return ((a == 0 || a == c.n_z - 1) ? 0.5 : 1.0) * p.F64[(size_t)h * c.n_z + a];
+        } else {
+            return Fw32[a];
+        }
+    };
+
     const int64_t s0 = c.ev_soff[ev];
     const int ns = (int)(c.ev_soff[ev + 1] - s0);
     const T KW = F64 ? T(KW64) : T(KW32);
@@ -384,6 +396,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
     const MixParams mp = mix_params(hp);
     const float4 *inv = p.inv32 + (size_t)h * NU;
 
+    if (!F64)
+        for (int a = tid; a < c.n_z; a += ADJ_THREADS)
+            Fw32[a] = ((a == 0 || a == c.n_z - 1) ? 0.5f : 1.f) * p.F32[(size_t)h * c.n_z + a];
     // ---- z_j, w_j exactly as the forward kernel of this precision
     for (int j = tid; j < ns; j += ADJ_THREADS) {
         T z = TINF, w = T(0);
@@ -462,10 +477,6 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
     const T cw0 = T(W1 > 0.0 ? 1.0 / (W1 * varw) : 0.0), cw1 = T(W1 > 0.0 ? 2.0 / W1 : 0.0);
     const T cw2 = T(W2 > 0.0 ? 2.0 / W2 : 0.0), cu = T(nv > 0.0 && varu > 0.0 ? 1.0 / (nv * varu) : 0.0);
     const T Mwt = T(Mw), Mut = T(Mu), varwt = T(varw);
-    // grid factor (FP32 path: F / F_scale; every term carries the same scale)
-    const double *F64g = p.F64 + (size_t)h * nz;
-    const float *F32g = p.F32 + (size_t)h * nz;
-    auto Fg = [&](int a) -> T { return F64 ? T(F64g[a]) : T(F32g[a]); };
     auto Gv = [&](int64_t row, int a) -> T {
         return F64 ? T(reinterpret_cast<const double *>(p.prof[h])[row * nz + a])
                    : T(reinterpret_cast<const float *>(p.prof[h])[row * nz + a]);
@@ -538,7 +549,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
         const int ia1 = aa1 > T(nz - 1) ? nz - 1 : (aa1 < T(-1) ? -1 : (int)aa1);
         T S0 = T(0), S1 = T(0), S2 = T(0);
         for (int a = ia0; a <= ia1; a++) {
-            const T Hh = ((a == 0 || a == nz - 1) ? T(0.5) : T(1)) * Fg(a) * Gv(row, a);
+            const T Hh = Fw(a) * Gv(row, a);
             const T u = (T(a) * dz - z) * ib;
             const T e = (F64 ? T(exp(-0.5 * double(u * u))) : T(__expf(-0.5f * float(u * u)))) * Hh;
             S0 += e;
@@ -569,18 +580,14 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
                 int m = (jl + jr) >> 1;
                 if (zs[m] < za - KW * bt) jl = m + 1; else jr = m;
             }
+            // the samples whose window holds a: |z - za| <= KW b
             T K = T(0);
             for (int j = jl; j < lo + cnt && zs[j] <= za + KW * bt; j++) {
-                // same per-sample window rule as the sums above
-                const T z = zs[j];
-                const T a0 = ceil((z - KW * bt) / dz), aa1 = floor((z + KW * bt) / dz);
-                if (T(a) < a0 || T(a) > aa1) continue;
-                const T u = (za - z) * ib;
+                const T u = (za - zs[j]) * ib;
                 K += ws[j] * (F64 ? T(exp(-0.5 * double(u * u))) : T(__expf(-0.5f * float(u * u))));
             }
             if (K == T(0)) continue;
-            const T wa = (a == 0 || a == nz - 1) ? T(0.5) : T(1);
-            const T FK = pf * wa * Fg(a) * K;
+            const T FK = pf * Fw(a) * K;
             const T M = FK * Gv(row, a);
             if (F64) {
                 const double *Qa = q.Q + ((size_t)h * nz + a) * 7;
@@ -872,14 +879,15 @@ __global__ void k_dprofile_sum(DevCatalog c, const double *G, double *outh) {
 
 }  // namespace
 
-size_t adjoint_event_smem(const DevCatalog &c) {
-    return sizeof(double) * 2 * (size_t)c.max_ns + sizeof(int) * (size_t)((c.max_seg + 2) & ~1) +
-           sizeof(double) * (ADJ_THREADS / 32 + 1) * 28;
+size_t adjoint_event_smem(const DevCatalog &c, bool fp64) {
+    return (fp64 ? sizeof(double) : sizeof(float)) * 2 * (size_t)c.max_ns +
+           sizeof(int) * (size_t)((c.max_seg + 2) & ~1) + sizeof(double) * (ADJ_THREADS / 32 + 1) * 28 +
+           (fp64 ? 0 : sizeof(float) * (size_t)c.n_z);
 }
 
 void launch_adjoint(const DevCatalog &c, const CallPtrs &p, const AdjPtrs &q, int H, bool fp64, cudaStream_t st) {
     k_adj_tables<<<H, ADJ_THREADS, 0, st>>>(c, p, q);
-    const size_t smem = adjoint_event_smem(c);
+    const size_t smem = adjoint_event_smem(c, fp64);
     const unsigned nb = (unsigned)((int64_t)c.n_events * H);
     if (fp64) {
         cudaFuncSetAttribute(k_event_adj<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -406,6 +406,16 @@ def main():
             "peak_basis": "148 SMs x 128 FP32 lanes x %.0f MHz x 1 FFMA per pair (derived)" % clock_mhz,
             "measured_pair_peak": peaks["pair_per_s"] / 1e9,
             "frac_of_measured": achieved / peaks["pair_per_s"]}
+    # The bound of the direct method (one exponential and three FP32 ops per
+    # windowed evaluation, E of them; the profile and sample bytes B at the
+    # copy bandwidth), with the rates K8 measured on this GPU.  The kernel
+    # evaluates the Gaussians by Horner's rule instead, so it can run faster
+    # than this bound; "frac" above is against its own one-FFMA-per-pair bound.
+    bw = (measured_peaks().get("hbm_gbs") or peaks["copy_bytes_per_s"] / 1e9) * 1e9
+    t_direct = max(pairs / peaks["ex2_per_s"], 3 * pairs / peaks["pair_per_s"],
+                   (roof["traffic"] or 0.0) / bw)
+    roof["direct_method_bound"] = {"t_bound_ms": 1e3 * t_direct, "frac": 1e3 * t_direct / kern,
+                                   "basis": "max(E / ex2 rate, 3 E / FFMA rate, bytes / copy bandwidth), K8-measured rates"}
     mean_stage = {k: sum(s[k] for s in stage) / len(stage) for k in stage[0]}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -254,9 +254,11 @@ int chimera_serve_reset_stats(chimera_ctx *ctx);
  * Tracing.  chimera_set_trace(ctx, 1) makes the synchronous likelihood
  * calls record CUDA events around each stage on the context's stream;
  * chimera_stage_ms then returns the last call's stage times in
- * milliseconds: ms[0] cosmology tables (K1), ms[1] galaxy profile (K3,
- * 0 when cached), ms[2] event integrals (K2+K4), ms[3] selection (K5),
- * ms[4] combine (K6), ms[5] adjoint (K7, gradient calls only).
+ * milliseconds (ms holds 7 doubles): ms[0] cosmology tables (K1), ms[1]
+ * galaxy profile (K3, 0 when cached), ms[2] event integrals (K4; with the
+ * reweighting for FP64, where K2 is fused into it), ms[3] selection (K5),
+ * ms[4] combine (K6), ms[5] adjoint (K7, gradient calls only), ms[6]
+ * reweighting (K2, mixed path).
  */
 int chimera_set_trace(chimera_ctx *ctx, int enable);
 int chimera_stage_ms(chimera_ctx *ctx, double *ms);

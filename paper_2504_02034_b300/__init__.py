@@ -295,9 +295,10 @@ def chimera_set_trace(h, enable=True):
 
 
 def chimera_stage_ms(h):
-    ms = np.zeros(6)
+    ms = np.zeros(7)
     _ck(lib().chimera_stage_ms(h, _dp(ms)), "chimera_stage_ms")
-    return dict(tables=ms[0], galaxy=ms[1], event=ms[2], selection=ms[3], combine=ms[4], adjoint=ms[5])
+    return dict(tables=ms[0], galaxy=ms[1], event=ms[2], selection=ms[3], combine=ms[4], adjoint=ms[5],
+                reweight=ms[6])
 
 
 def chimera_kde_pairs(h, cid, theta):

@@ -94,6 +94,7 @@ CallPtrs Workspace::ptrs(int H, const DevCatalog &c) const {
     p.lnI = lnI;
     p.bw = bw;
     p.selp = selp;
+    p.zw = zw;
     p.n_chunk = selection_chunks(c);
     p.lnL = lnL;
     p.neff = neff;
@@ -116,13 +117,24 @@ void ws_release(Ctx &ctx, Workspace &ws) {
     ws.nz_cap = 0;
     ws.nchunk_cap = 0;
     ws.ngal_cap = 0;
+    ws.zw_tile = 0;
+    ws.zpad_cap = 0;
+}
+
+// Hyperpoints per reweighting tile: the tile buffer holds z and w of every
+// sample for that many points, at most 1 GiB.
+static int zw_tile_for(int H, int64_t n_zpad) {
+    const int64_t cap = (int64_t)1 << 30;
+    const int64_t t = cap / (8 * std::max<int64_t>(n_zpad, 1));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(H, t));
 }
 
 int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat) {
     const DevCatalog &c = cat.d;
     int nch = selection_chunks(c);
+    const int tile = zw_tile_for(H, c.n_zpad);
     if (H <= ws.Hcap && c.n_events <= ws.nev_cap && c.n_z <= ws.nz_cap && nch <= ws.nchunk_cap &&
-        c.n_gal <= ws.ngal_cap)
+        c.n_gal <= ws.ngal_cap && tile <= ws.zw_tile && c.n_zpad <= ws.zpad_cap)
         return CHIMERA_OK;
     // grow (with some headroom) and re-allocate everything
     int Hn = std::max(H, ws.Hcap);
@@ -130,6 +142,8 @@ int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat) {
     int nz = std::max(c.n_z, ws.nz_cap);
     int nc = std::max(nch, ws.nchunk_cap);
     int64_t ng = std::max<int64_t>(c.n_gal, ws.ngal_cap);
+    const int ztile = std::max(tile, ws.zw_tile);
+    const int64_t zpad = std::max<int64_t>(c.n_zpad, ws.zpad_cap);
     if (ws.st) cudaStreamSynchronize(ws.st);
     ws_release(ctx, ws);
     struct Item { void **p; size_t b; };
@@ -153,6 +167,7 @@ int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat) {
         {(void **)&ws.pairs, sizeof(unsigned long long) * (size_t)Hn},
         {(void **)&ws.dk, sizeof(double) * 2 * (size_t)Hn * NT_FWD},
         {(void **)&ws.fmax_bits, sizeof(unsigned long long) * (size_t)Hn},
+        {(void **)&ws.zw, sizeof(float) * 2 * (size_t)zpad * ztile},
     };
     for (auto &it : items) {
         int rc = dev_alloc(ctx, it.p, it.b);
@@ -179,6 +194,8 @@ int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat) {
     ws.nz_cap = nz;
     ws.nchunk_cap = nc;
     ws.ngal_cap = ng;
+    ws.zw_tile = ztile;
+    ws.zpad_cap = zpad;
     return CHIMERA_OK;
 }
 
@@ -292,6 +309,7 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
         for (auto &e : ws.tev)
             if (!e) CK(cudaEventCreate(&e));
         ws.traced_adjoint = false;
+        ws.traced_tiles = 0;
         CK(cudaEventRecord(ws.tev[0], ws.st));
     }
     memset(st, 0, 8 * (size_t)H);
@@ -323,7 +341,26 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
     launch_hyper_tables(c, p, H, ws.dk, ws.fmax_bits, ws.st);
     if (ws.trace) CK(cudaEventRecord(ws.tev[2], ws.st));
     if (precision == CHIMERA_FP64) launch_event_fp64(c, p, H, ws.st);
-    else launch_event_mixed(c, p, H, ws.st);
+    else {
+        // reweighting and event integrals by tiles of hyperpoints
+        const int tile = std::max(1, std::min(H, ws.zw_tile));
+        const int ntiles = (H + tile - 1) / tile;
+        if (ws.trace) {
+            while ((int)ws.tile_ev.size() < 2 * ntiles) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                ws.tile_ev.push_back(e);
+            }
+            ws.traced_tiles = ntiles;
+        }
+        for (int t = 0; t < ntiles; t++) {
+            const int h0 = t * tile, nh = std::min(tile, H - h0);
+            launch_reweight(c, p, h0, nh, ws.st);
+            if (ws.trace) CK(cudaEventRecord(ws.tile_ev[2 * t], ws.st));
+            launch_event_mixed(c, p, h0, nh, ws.st);
+            if (ws.trace) CK(cudaEventRecord(ws.tile_ev[2 * t + 1], ws.st));
+        }
+    }
     if (ws.trace) CK(cudaEventRecord(ws.tev[3], ws.st));
     launch_selection(c, p, H, precision == CHIMERA_FP64, ws.st);
     if (ws.trace) CK(cudaEventRecord(ws.tev[4], ws.st));
@@ -509,7 +546,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     std::vector<int4> groups;
     std::vector<int32_t> ev_goff(ne + 1, 0);
     std::vector<float2> ev_ref(ne);
-    std::vector<int2> ev_krange(ne);
+    std::vector<int64_t> ev_zoff(ne + 1, 0);
     int max_groups = 1;
     for (int i = 0; i < ne; i++) {
         const int64_t a = d->sample_off[i], n = d->sample_off[i + 1] - a;
@@ -521,17 +558,6 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         }
         m /= n;
         const double sl = std::sqrt(std::max(m2 / n - m * m, 0.0)) * std::pow((double)n, -0.2);
-        {
-            int kmin = NU, kmax = 0;
-            for (int64_t j = a; j < a + n; j++) {
-                int k;
-                float f;
-                tcoord(sd[j], k, f);
-                kmin = std::min(kmin, k);
-                kmax = std::max(kmax, k);
-            }
-            ev_krange[i] = make_int2(kmin, kmax);
-        }
         // reference: the median d_L of the event
         std::vector<double> dd(sd.begin() + a, sd.begin() + a + n);
         std::nth_element(dd.begin(), dd.begin() + n / 2, dd.end());
@@ -548,10 +574,12 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
             const int64_t s0 = seg_soff[sgi], s1 = seg_soff[sgi + 1];
             const int sr = sgi - ev_segoff[i];
             // a chunk of up to 128 neighbours is halved (in multiples of 32)
-            // while its spread in ln d_L exceeds 4 bandwidth-equivalents
+            // while its spread in ln d_L exceeds 16 bandwidth-equivalents (wider groups are
+            // still evaluated, by the per-lane path; the threshold was tuned on the
+            // 300-event catalog)
             std::function<void(int64_t, int)> emit = [&](int64_t st, int cnt) {
                 double spread = std::log(sd[st + cnt - 1]) - std::log(sd[st]);
-                if (cnt > 32 && spread > 4.0 * sl) {
+                if (cnt > 32 && spread > 16.0 * sl) {
                     int first = 32 * ((cnt + 63) / 64);
                     emit(st, first);
                     emit(st + first, cnt - first);
@@ -576,6 +604,9 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         max_groups = std::max<int>(max_groups, (int)groups.size() - ev_goff[i]);
     }
     ev_goff[ne] = (int32_t)groups.size();
+    for (int i = 0; i < ne; i++)
+        ev_zoff[i + 1] = ev_zoff[i] + ((d->sample_off[i + 1] - d->sample_off[i] + 3) & ~(int64_t)3);
+    c.n_zpad = std::max<int64_t>(ev_zoff[ne], 4);
     c.max_groups = max_groups;
     // ---- heavy-first event order: cost ~ N_s x spread of ln d_L
     std::vector<double> cost(ne);
@@ -660,7 +691,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         {(void **)&c.groups, groups.data(), 16 * groups.size()},
         {(void **)&c.ev_goff, ev_goff.data(), 4 * ev_goff.size()},
         {(void **)&c.ev_ref, ev_ref.data(), 8 * ev_ref.size()},
-        {(void **)&c.ev_krange, ev_krange.data(), 8 * ev_krange.size()},
+        {(void **)&c.ev_zoff, ev_zoff.data(), 8 * ev_zoff.size()},
         {(void **)&c.pix_S, pixS.data(), 8 * pixS.size()},
         {(void **)&c.gal_off, goff.data(), 8 * goff.size()},
         {(void **)&c.pix_sigmax, sigmax.data(), 8 * sigmax.size()},
@@ -820,6 +851,10 @@ void chimera_destroy(chimera_ctx *h) {
     }
     ctx.fwdO.clear();
     ws_release(ctx, ctx.ws);
+    for (auto &e : ctx.ws.tev)
+        if (e) cudaEventDestroy(e);
+    for (auto &e : ctx.ws.tile_ev) cudaEventDestroy(e);
+    ctx.ws.tile_ev.clear();
     cudaStreamDestroy(ctx.stream);
     delete h;
 }
@@ -985,7 +1020,7 @@ int chimera_stage_ms(chimera_ctx *h, double *ms) {
     if (!h || !ms) { set_error("null argument"); return CHIMERA_ERR_INVALID_ARG; }
     std::lock_guard<std::recursive_mutex> lk(h->c.mu);
     Workspace &ws = h->c.ws;
-    for (int i = 0; i < 6; i++) ms[i] = 0.0;
+    for (int i = 0; i < 7; i++) ms[i] = 0.0;
     if (!ws.trace || !ws.tev[5]) { set_error("tracing is off or no traced call yet"); return CHIMERA_ERR_INVALID_ARG; }
     CK(cudaEventSynchronize(ws.tev[5]));
     float t;
@@ -993,6 +1028,17 @@ int chimera_stage_ms(chimera_ctx *h, double *ms) {
     CK(cudaEventElapsedTime(&t, ws.tev[1], ws.tev[2])); ms[0] = t;
     CK(cudaEventElapsedTime(&t, ws.tev[0], ws.tev[1])); ms[1] = t;
     CK(cudaEventElapsedTime(&t, ws.tev[2], ws.tev[3])); ms[2] = t;
+    if (ws.traced_tiles > 0) {  // mixed: split K2 and K4 per tile
+        double rw = 0.0, ev = 0.0;
+        for (int i = 0; i < ws.traced_tiles; i++) {
+            CK(cudaEventElapsedTime(&t, i == 0 ? ws.tev[2] : ws.tile_ev[2 * i - 1], ws.tile_ev[2 * i]));
+            rw += t;
+            CK(cudaEventElapsedTime(&t, ws.tile_ev[2 * i], ws.tile_ev[2 * i + 1]));
+            ev += t;
+        }
+        ms[2] = ev;
+        ms[6] = rw;
+    }
     CK(cudaEventElapsedTime(&t, ws.tev[3], ws.tev[4])); ms[3] = t;
     CK(cudaEventElapsedTime(&t, ws.tev[4], ws.tev[5])); ms[4] = t;
     if (ws.traced_adjoint && ws.tev[6] && ws.tev[7]) {

@@ -122,15 +122,21 @@ struct MixLayout {
 // evaluated by Horner's rule from the highest power down: one FMA per
 // (sample, grid point).  The intermediates are partial sums divided by
 // exp(-u^2) B^tau, so they stay within the float range for |u| <= 3.1.
+// R samples per lane (lane, lane+32, ...) of a group share one table; each
+// sample's weight and its factor exp(-u^2) are folded into one coefficient
+// before the chains, so a sample holds five registers through the loop.
 template <int R>
-__device__ __forceinline__ void chains(const float *D, int nq, const float (&u)[R], float ds, float lnscale,
-                                       float (&acc)[R]) {
-    float A[R], B[R], Bi[R], af[R], ab[R];
+__device__ __forceinline__ float union_samples(const float *D, int nq, const float *z, const float *w, int cnt,
+                                               int lane, float zo, float inv_s2b, float ds, float lnscale) {
+    float cw[R], B[R], Bi[R], af[R], ab[R];
 #pragma unroll
     for (int r = 0; r < R; r++) {
-        A[r] = __expf(-u[r] * u[r] - lnscale);
-        B[r] = __expf(2.f * u[r] * ds);
-        Bi[r] = __expf(-2.f * u[r] * ds);
+        const int j = lane + 32 * r;
+        const bool in = j < cnt;
+        const float u = in ? (z[j] - zo) * inv_s2b : 0.f;
+        cw[r] = in ? w[j] * __expf(-u * u - lnscale) : 0.f;
+        B[r] = __expf(2.f * u * ds);
+        Bi[r] = __expf(-2.f * u * ds);
         af[r] = 0.f;
         ab[r] = 0.f;
     }
@@ -154,8 +160,10 @@ __device__ __forceinline__ void chains(const float *D, int nq, const float (&u)[
             ab[r] = fmaf(ab[r], Bi[r], e.w);
         }
     }
+    float v = 0.f;
 #pragma unroll
-    for (int r = 0; r < R; r++) acc[r] = A[r] * fmaf(Bi[r], ab[r], af[r]);
+    for (int r = 0; r < R; r++) v = fmaf(cw[r], fmaf(Bi[r], ab[r], af[r]), v);
+    return v;
 }
 
 // As stage_table<true>, as float4: a_first and the C-table pointer Cq
@@ -211,25 +219,6 @@ __device__ __forceinline__ float small_group(const float *z, const float *w, int
     return acc;
 }
 
-// R samples per lane (lane, lane+32, ...) of a group sharing one table.
-template <int R>
-__device__ __forceinline__ float union_samples(const float *D, int nq, const float *z, const float *w, int cnt,
-                                               int lane, float zo, float inv_s2b, float ds, float lnscale) {
-    float u[R], ww[R], acc[R];
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-        int j = lane + 32 * r;
-        bool in = j < cnt;
-        u[r] = in ? (z[j] - zo) * inv_s2b : 0.f;
-        ww[r] = in ? w[j] : 0.f;
-    }
-    chains<R>(D, nq, u, ds, lnscale, acc);
-    float v = 0.f;
-#pragma unroll
-    for (int r = 0; r < R; r++) v = fmaf(ww[r], acc[r], v);
-    return v;
-}
-
 // Asynchronous 16-byte global -> shared copies (cp.async, completion per
 // thread by commit groups).
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -250,11 +239,6 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Phase A staging inside the D-table region: a ring of RING chunks of
-// EV_THREADS samples and up to NODE_CAP inverse-table nodes.
-constexpr int RING = 4;
-constexpr int NODE_CAP = EV_WARPS * DCAP / 4 - RING * EV_THREADS;
-static_assert(NODE_CAP >= 256, "phase A staging does not fit the D-table region");
 
 // Warp-cooperative staging of a coefficient table: for idx < len and grid
 // point a = a_first + idx, D[idx] = C_|idx - tau0| * scale * F'(z_a) G(z_a)
@@ -308,7 +292,97 @@ __device__ __forceinline__ float lane_chain(const float *Hc, const float *CT, in
     return A * fmaf(Bi, ab, af);
 }
 
-__global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, CallPtrs p, int H) {
+// K2 (mixed): reweighting of every PE sample for hyperpoints h0 .. h0+nh-1,
+// one block per (event, point): z_j and w_j go to the tile buffer (FP32,
+// 16-byte aligned per event), the one-pass moments about the redshift of
+// the event's median d_L give the FP32 Scott bandwidth.  Many small blocks
+// keep the SMs full while the loads of the inverse-table nodes are in flight.
+constexpr int RW_THREADS = 256;
+__global__ void __launch_bounds__(RW_THREADS) k_reweight(DevCatalog c, CallPtrs p, int h0, int nh) {
+    __shared__ double red[8 + (RW_THREADS / 32) * 8];
+    const int hl = blockIdx.x % nh, h = h0 + hl;
+    const int ev = blockIdx.x / nh;
+    const int tid = threadIdx.x;
+    const HP &hp = p.hp[h];
+    if (hp.status & (CHIMERA_PT_OUT_OF_SUPPORT | CHIMERA_PT_NONMONOTONE)) return;
+    const MixParams q = mix_params(hp);
+    const int64_t s0 = c.ev_soff[ev];
+    const int ns = (int)(c.ev_soff[ev + 1] - s0);
+    float *zd = p.zw + (size_t)hl * 2 * c.n_zpad + c.ev_zoff[ev];
+    float *wd = zd + c.n_zpad;
+    const float4 *inv = p.inv32 + (size_t)h * NU;
+    const float4 *sp = c.s32 + s0;
+    float zref;
+    {
+        const float2 zr = c.ev_ref[ev];
+        const int k = __float_as_int(zr.x);
+        const bool ok = (k < q.kv) || (k == q.kv && zr.y <= q.fv);
+        zref = ok ? chimd::hermite4(__ldg(inv + k), zr.y) : 0.f;
+        if (!isfinite(zref)) zref = 0.f;
+    }
+    float m[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // W1, Wd, Wd2, W2, n, Sd, Sd2
+    // one sample: table coordinate -> z (Hermite on the node pair), log2
+    // source masses, weight, moments; invalid samples (beyond d_L^gw(10))
+    // get z = inf and w = 0 and stay out of the moments
+    auto sample = [&](const float4 &sv, const float4 &nd, int j) {
+        const float z = chimd::hermite4(nd, sv.y);
+        const bool ok = z < CUDART_INF_F;  // false for inf and NaN
+        const float lz = __log2f(1.f + z);
+        float w = mass_weight32(q, sv.z - lz, sv.w - lz);
+        w = ok ? w : 0.f;
+        const float d = ok ? z - zref : 0.f;
+        const float wd_ = w * d;
+        m[0] += w; m[1] += wd_; m[2] = fmaf(wd_, d, m[2]); m[3] = fmaf(w, w, m[3]);
+        m[4] += ok ? 1.f : 0.f; m[5] += d; m[6] = fmaf(d, d, m[6]);
+        zd[j] = ok ? z : CUDART_INF_F;
+        wd[j] = w;
+    };
+    auto node = [&](const float4 &sv) {
+        const int k = __float_as_int(sv.x);
+        const bool valid = (k < q.kv) || (k == q.kv && sv.y <= q.fv);
+        return valid ? __ldg(inv + k) : make_float4(CUDART_INF_F, 0.f, 0.f, 0.f);
+    };
+    int j = tid;
+    // four samples per thread in flight: loads first, then the arithmetic
+    for (; j + 3 * RW_THREADS < ns; j += 4 * RW_THREADS) {
+        float4 sv[4], nd[4];
+#pragma unroll
+        for (int uu = 0; uu < 4; uu++) sv[uu] = __ldg(sp + j + uu * RW_THREADS);
+#pragma unroll
+        for (int uu = 0; uu < 4; uu++) nd[uu] = node(sv[uu]);
+#pragma unroll
+        for (int uu = 0; uu < 4; uu++) sample(sv[uu], nd[uu], j + uu * RW_THREADS);
+    }
+    for (; j < ns; j += RW_THREADS) {
+        const float4 sv = __ldg(sp + j);
+        sample(sv, node(sv), j);
+    }
+    block_sum<7, RW_THREADS>(m, red);
+    if (tid == 0) {
+        // Scott's rule in FP32 (the mixed path's precision) from the block
+        // sums: weighted, then unweighted, then the grid spacing
+        float bl = c.dz32;
+        const float W1 = (float)red[0], n = (float)red[4];
+        bool done = false;
+        if (W1 > 0.f) {
+            const float mw = (float)red[1] / W1, var = (float)red[2] / W1 - mw * mw;
+            const float neff = W1 * W1 / (float)red[3];
+            if (neff >= 2.f && var > 0.f) {
+                bl = sqrtf(var) * exp2f(-0.2f * log2f(neff));
+                done = true;
+            }
+        }
+        if (!done && n >= 2.f) {
+            const float mu = (float)red[5] / n, var = (float)red[6] / n - mu * mu;
+            if (var > 0.f) bl = sqrtf(var) * exp2f(-0.2f * log2f(n));
+        }
+        p.bw[(size_t)h * c.n_events + ev] = (double)bl;
+    }
+}
+
+// K4 (mixed): the event integral for hyperpoints h0 .. h0+nh-1 from the
+// reweighted samples of the tile buffer, one block per (event, point).
+__global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, CallPtrs p, int h0, int nh) {
     extern __shared__ float4 smem4[];
     const MixLayout L(c.max_ns, c.n_z, c.max_seg, c.max_groups);
     int4 *grp = reinterpret_cast<int4 *>(smem4);
@@ -329,8 +403,8 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
     double *red = spf64 + L.seg_pad;
     __shared__ int s_gctr;
 
-    const int h = blockIdx.x % H;
-    const int ev = c.ev_order[blockIdx.x / H];
+    const int hl = blockIdx.x % nh, h = h0 + hl;
+    const int ev = c.ev_order[blockIdx.x / nh];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const size_t out = (size_t)h * c.n_events + ev;
     const HP &hp = p.hp[h];
@@ -338,34 +412,25 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
         if (tid == 0) { p.lnI[out] = 0.0; p.bw[out] = 0.0; }
         return;
     }
-    const MixParams q = mix_params(hp);
-
     const int nz = c.n_z;
     const float dz = c.dz32;
     const float inv_dz = 1.f / dz;
     if (tid == 0) s_gctr = 0;
-    // ---- prologue: every per-event and per-point input the block needs is
-    // requested at once with cp.async (no register staging, no stall per
-    // load); the copies complete while the ring prologue is in flight.
+    // ---- prologue: the event's reweighted samples, its group and segment
+    // metadata and F, all requested at once with cp.async
     const int64_t s0 = c.ev_soff[ev];
     const int ns = (int)(c.ev_soff[ev + 1] - s0);
     const int g0 = c.ev_goff[ev];
     const int ngroups = c.ev_goff[ev + 1] - g0;
     const int sg0 = c.ev_segoff[ev], nseg = c.ev_segoff[ev + 1] - sg0;
-    const int2 kr = c.ev_krange[ev];
-    const float2 zr = c.ev_ref[ev];
-    const float4 *inv = p.inv32 + (size_t)h * NU;
-    const float4 *sp = c.s32 + s0;
-    // The samples stream through a ring of RING chunks of EV_THREADS float4
-    // in shared memory (cp.async, RING-1 chunks ahead; each thread copies and
-    // reads only its own slot), and the inverse-table nodes of the event's
-    // d_L range are staged once, so the per-sample node gather is a shared
-    // load.  Both live in the D-table region, which phase B reuses.
-    float4 *ring = reinterpret_cast<float4 *>(Dt);
-    float4 *snode = ring + RING * EV_THREADS;
-    const bool staged = kr.y - kr.x < NODE_CAP;  // block-uniform
-    if (staged)
-        for (int i = tid; i <= kr.y - kr.x; i += EV_THREADS) cp_async16(snode + i, inv + kr.x + i);
+    {
+        const float *zsrc = p.zw + (size_t)hl * 2 * c.n_zpad + c.ev_zoff[ev];
+        const float *wsrc = zsrc + c.n_zpad;
+        for (int i = tid; i < (ns + 3) >> 2; i += EV_THREADS) {
+            cp_async16(zs + 4 * i, zsrc + 4 * i);
+            cp_async16(ws + 4 * i, wsrc + 4 * i);
+        }
+    }
     for (int g = tid; g < ngroups; g += EV_THREADS) cp_async16(grp + g, c.groups + g0 + g);
     for (int k = tid; k <= nseg; k += EV_THREADS) {
         cp_async8(seg64 + k, c.seg_soff + sg0 + k);
@@ -373,87 +438,18 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
     }
     // F(z_a) (the trapezoid weight of the two end points is applied below)
     for (int a = tid; a < nz; a += EV_THREADS) cp_async4(Fs + a, p.F32 + (size_t)h * nz + a);
-#pragma unroll
-    for (int cc = 0; cc < RING - 1; cc++) {
-        const int jj = cc * EV_THREADS + tid;
-        if (jj < ns) cp_async16(ring + cc * EV_THREADS + tid, sp + jj);
-        cp_async_commit();
-    }
-    cp_async_wait<RING - 2>();  // everything above except ring chunks 1 .. RING-2
-    __syncthreads();            // every thread's copies
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
     if (tid == 0) Fs[0] *= 0.5f;
     if (tid == 1 && nz > 1) Fs[nz - 1] *= 0.5f;
     for (int k = tid; k <= nseg; k += EV_THREADS) {
         seglo[k] = (int)(seg64[k] - s0);
         if (k < nseg) segpf[k] = (float)spf64[k];
     }
-
-    // ---- phase A: z_j, w_j and one-pass moments about the redshift of the
-    // event's median d_L (shifted sums: no cancellation in the variance)
-    float zref;
-    {
-        const int k = __float_as_int(zr.x);
-        const bool ok = (k < q.kv) || (k == q.kv && zr.y <= q.fv);
-        const float4 nd = !ok ? make_float4(0.f, 0.f, 0.f, 0.f)
-                              : (staged ? snode[k - kr.x] : __ldg(inv + k));
-        zref = chimd::hermite4(nd, zr.y);
-        if (!isfinite(zref)) zref = 0.f;
-    }
-    float m[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // W1, Wd, Wd2, W2, n, Sd, Sd2
-    // one sample: table coordinate -> z (Hermite on the node pair), log2
-    // source masses, weight, moments; invalid samples (beyond d_L^gw(10))
-    // get z = inf and w = 0 and stay out of the moments
-    auto sample = [&](const float4 &sv, const float4 &nd, int j) {
-        const float z = chimd::hermite4(nd, sv.y);
-        const bool ok = z < CUDART_INF_F;  // false for inf and NaN
-        const float lz = __log2f(1.f + z);
-        float w = mass_weight32(q, sv.z - lz, sv.w - lz);
-        w = ok ? w : 0.f;
-        const float d = ok ? z - zref : 0.f;
-        const float wd = w * d;
-        m[0] += w; m[1] += wd; m[2] = fmaf(wd, d, m[2]); m[3] = fmaf(w, w, m[3]);
-        m[4] += ok ? 1.f : 0.f; m[5] += d; m[6] = fmaf(d, d, m[6]);
-        zs[j] = ok ? z : CUDART_INF_F;
-        ws[j] = w;
-    };
-    const int nch = (ns + EV_THREADS - 1) / EV_THREADS;
-    for (int cc = 0; cc < nch; cc++) {
-        const int jn = (cc + RING - 1) * EV_THREADS + tid;
-        if (jn < ns) cp_async16(ring + ((cc + RING - 1) % RING) * EV_THREADS + tid, sp + jn);
-        cp_async_commit();
-        cp_async_wait<RING - 1>();  // chunk cc of this thread
-        const int j = cc * EV_THREADS + tid;
-        if (j < ns) {
-            const float4 sv = ring[(cc % RING) * EV_THREADS + tid];
-            const int k = __float_as_int(sv.x);
-            const bool valid = (k < q.kv) || (k == q.kv && sv.y <= q.fv);
-            const float4 nd = !valid ? make_float4(CUDART_INF_F, 0.f, 0.f, 0.f)
-                                     : (staged ? snode[k - kr.x] : __ldg(inv + k));
-            sample(sv, nd, j);
-        }
-    }
-    block_sum<7, EV_THREADS>(m, red);
-    // Scott's rule in FP32 (the mixed path's precision), every thread from
-    // the same block sums: weighted, then unweighted, then the grid spacing
-    float bl = dz;
-    {
-        const float W1 = (float)red[0], n = (float)red[4];
-        bool done = false;
-        if (W1 > 0.f) {
-            const float mw = (float)red[1] / W1, var = (float)red[2] / W1 - mw * mw;
-            const float neff = W1 * W1 / (float)red[3];
-            if (neff >= 2.f && var > 0.f) {
-                bl = sqrtf(var) * exp2f(-0.2f * log2f(neff));
-                done = true;
-            }
-        }
-        if (!done && n >= 2.f) {
-            const float mu = (float)red[5] / n, var = (float)red[6] / n - mu * mu;
-            if (var > 0.f) bl = sqrtf(var) * exp2f(-0.2f * log2f(n));
-        }
-    }
-    const float b = bl;
-    const double bd = (double)b;
+    __syncthreads();
+    const double bd = p.bw[out];  // the reweighting kernel's FP32 bandwidth
+    const float b = (float)bd;
     const float inv_s2b = 0.70710678f / b;
     const float ds = dz * inv_s2b;
     const float halfk = KW32 * b;
@@ -546,12 +542,14 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
                     else stage_table<true>(D, 8 * nq, t_o - 4 * nq, A0, A1, G, Fs, CT, 4 * nq, scale, lane);
                     __syncwarp();
                     const float zo = t_o * dz;
+#define CHIM_UNION(R) v = union_samples<R>(D, nq, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale)
                     switch ((cnt + 31) >> 5) {
-                        case 1: v = union_samples<1>(D, nq, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale); break;
-                        case 2: v = union_samples<2>(D, nq, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale); break;
-                        case 3: v = union_samples<3>(D, nq, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale); break;
-                        default: v = union_samples<4>(D, nq, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale); break;
+                        case 1: CHIM_UNION(1); break;
+                        case 2: CHIM_UNION(2); break;
+                        case 3: CHIM_UNION(3); break;
+                        default: CHIM_UNION(4); break;
                     }
+#undef CHIM_UNION
                 } else if (ds <= 2.f && Tw + 2 < CCAP && (A1 - A0 + 1) + 2 * Tw + 4 <= DCAP) {
                     // stage H' on [base, base + span) with zeros outside [A0, A1]
                     const int base = A0 - Tw - 2, span = (A1 - A0 + 1) + 2 * Tw + 4;
@@ -720,10 +718,16 @@ size_t event_fp64_smem(const DevCatalog &c) {
            sizeof(double) * (8 + (EV64_THREADS / 32) * 8);
 }
 
-void launch_event_mixed(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st) {
+void launch_reweight(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cudaStream_t st) {
+    const unsigned nb = (unsigned)((int64_t)c.n_events * nh);
+    if (nb) k_reweight<<<nb, RW_THREADS, 0, st>>>(c, p, h0, nh);
+}
+
+void launch_event_mixed(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cudaStream_t st) {
     size_t smem = event_mixed_smem(c);
     cudaFuncSetAttribute(k_event_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_event_mixed<<<(unsigned)(c.n_events * H), EV_THREADS, smem, st>>>(c, p, H);
+    const unsigned nb = (unsigned)((int64_t)c.n_events * nh);
+    if (nb) k_event_mixed<<<nb, EV_THREADS, smem, st>>>(c, p, h0, nh);
 }
 
 void launch_event_fp64(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st) {

@@ -87,7 +87,9 @@ struct DevCatalog {
     int32_t *ev_goff;     // [n_events+1] group offsets per event
     int32_t max_groups;   // most groups of any event
     float2 *ev_ref;       // [n_events] inverse-table (k bits, f) of the event's median d_L
-    int2 *ev_krange;      // [n_events] smallest and largest inverse-table interval of its samples
+    int64_t *ev_zoff;     // [n_events+1] offsets of the events in a reweighted-sample row
+                          // (each a multiple of 4 floats)
+    int64_t n_zpad;       // length of a reweighted-sample row
     // pixels
     double *pix_S;        // [n_pix]
     int64_t *gal_off;     // [n_pix+1], galaxies sorted by z inside a pixel
@@ -120,6 +122,8 @@ struct CallPtrs {
     double *lnI;              // [H x n_events]
     double *bw;               // [H x n_events]
     double *selp;             // [H x n_chunk x 2] selection partial sums (scratch)
+    float *zw;                // [tile x 2 x n_zpad] reweighted samples (z row, then w row) of a
+                              // tile of hyperpoints (mixed path)
     int32_t n_chunk;
     double *lnL, *neff, *xi;  // [H]
     int32_t *status;          // [H]
@@ -143,7 +147,10 @@ void launch_galaxy_profile(const DevCatalog &c, const double *fwd, double Om, do
 void launch_profile_sum(const DevCatalog &c, const double *G64, const float *G32, double *outh64,
                         float *outh32, cudaStream_t st);
 // K2+K4: per-event ln I for every (event, h).
-void launch_event_mixed(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st);
+// Mixed: reweighting (K2) into p.zw, then the event integral (K4) from it,
+// for the hyperpoints h0 .. h0+nh-1 (nh at most the tile the buffer holds).
+void launch_reweight(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cudaStream_t st);
+void launch_event_mixed(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cudaStream_t st);
 void launch_event_fp64(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st);
 size_t event_mixed_smem(const DevCatalog &c);
 size_t event_fp64_smem(const DevCatalog &c);

@@ -69,6 +69,9 @@ struct Workspace {
     double *lnL = nullptr, *neff = nullptr, *xi = nullptr;
     double *dv = nullptr, *invZ64 = nullptr;
     double *dk = nullptr;                  // [2 x H x NT_FWD] forward-node scratch (d, J)
+    float *zw = nullptr;                   // [zw_tile x 2 x zpad_cap] reweighted samples (mixed)
+    int zw_tile = 0;                       // hyperpoints per reweighting tile
+    int64_t zpad_cap = 0;
     unsigned long long *fmax_bits = nullptr;  // [H]
     float *invZ32 = nullptr;
     // adjoint buffers
@@ -84,6 +87,8 @@ struct Workspace {
     bool trace = false;
     cudaEvent_t tev[8] = {};
     bool traced_adjoint = false;
+    std::vector<cudaEvent_t> tile_ev;  // mixed: after the reweighting and after K4 of each tile
+    int traced_tiles = 0;
     // host pinned staging
     char *hstage = nullptr;
     size_t hstage_bytes = 0;

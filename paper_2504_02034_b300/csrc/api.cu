@@ -364,7 +364,7 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
     if (ws.trace) CK(cudaEventRecord(ws.tev[3], ws.st));
     launch_selection(c, p, H, precision == CHIMERA_FP64, ws.st);
     if (ws.trace) CK(cudaEventRecord(ws.tev[4], ws.st));
-    launch_combine(c, p, H, ws.st);
+    launch_combine(c, p, H, precision != CHIMERA_FP64, ws.st);
     if (ws.trace) CK(cudaEventRecord(ws.tev[5], ws.st));
     CK(cudaGetLastError());
     return CHIMERA_OK;

@@ -587,22 +587,26 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
         if (lane == 0) gres[g] = v;
     }
     __syncthreads();
-    // fixed-order sum of the group values
+    // fixed-order FP32 tree sum of the group values (relative error ~1e-7;
+    // B300's FP64 rate would make a double reduction the block's longest
+    // step); the combine kernel takes the FP64 log
     {
-        double sacc = 0.0;
-        for (int g = tid; g < ngroups; g += EV_THREADS) sacc += (double)gres[g];
-        double vv[1] = {sacc};
-        block_sumd<1, EV_THREADS>(vv, red);
+        float sacc = 0.f;
+        for (int g = tid; g < ngroups; g += EV_THREADS) sacc += gres[g];
+        sacc = warp_sum(sacc);
+        float *redf = reinterpret_cast<float *>(red);
+        if (lane == 0) redf[wid] = sacc;
+        __syncthreads();
+        if (tid == 0) {
+            float I = 0.f;
+            for (int w = 0; w < EV_WARPS; w++) I += redf[w];
+            p.lnI[out] = (double)I;  // the raw integral: F / F_scale units, without 1/b
+            p.bw[out] = bd;
+        }
     }
     if (p.pairs) {
         for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
         if (lane == 0 && npairs) atomicAdd(p.pairs + h, npairs);
-    }
-    if (tid == 0) {
-        double I = red[0];
-        double pref = c.dz * hp.F_scale / (c.n_gal_total * 2.50662827463100050242 * bd);
-        p.lnI[out] = I > 0.0 ? log(I) + log(pref) : -CUDART_INF;
-        p.bw[out] = bd;
     }
 }
 

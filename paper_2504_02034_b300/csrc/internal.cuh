@@ -156,7 +156,8 @@ size_t event_mixed_smem(const DevCatalog &c);
 size_t event_fp64_smem(const DevCatalog &c);
 // K5: selection partial sums; K6: combine into ln L.
 void launch_selection(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, cudaStream_t st);
-void launch_combine(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st);
+// raw: the mixed event kernel left raw integrals in lnI (K6 takes the log).
+void launch_combine(const DevCatalog &c, const CallPtrs &p, int H, bool raw, cudaStream_t st);
 int selection_chunks(const DevCatalog &c);
 // K8 microbenchmarks.
 int run_peaks(double *out, cudaStream_t st);

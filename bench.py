@@ -69,34 +69,101 @@ def allmax(ws, x):
     return float(t.item())
 
 
-class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+class _Nvml:
+    """Read-only NVML queries through the driver's libnvidia-ml (ctypes)."""
+    SW_POWER_CAP, HW_SLOWDOWN, SW_THERMAL, HW_THERMAL = 0x4, 0x8, 0x20, 0x40
+    CLOCK_SM = 1
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    def __init__(self, gpu):
+        import ctypes as C
+        self.C = C
+        self.lib = C.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = C.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(gpu), C.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self.reasons_fn = fn if fn is not None else self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def clock(self, maximum=False):
+        v = self.C.c_uint()
+        f = self.lib.nvmlDeviceGetMaxClockInfo if maximum else self.lib.nvmlDeviceGetClockInfo
+        if f(self.h, self.C.c_int(self.CLOCK_SM), self.C.byref(v)) != 0:
+            raise OSError("clock query failed")
+        return float(v.value)
+
+    def reasons(self):
+        v = self.C.c_ulonglong()
+        if self.reasons_fn(self.h, self.C.byref(v)) != 0:
+            raise OSError("reason query failed")
+        return v.value
+
+
+class Clocks:
+    """SM clock and throttle-reason samples taken while the timed region runs:
+    NVML (read-only) polled from a background thread every ~1 ms, with the
+    nvidia-smi sampler as the fallback when NVML is unavailable."""
 
     def __init__(self, gpu):
         self.gpu = gpu
-        self.proc = None
-        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.samples = []
+        self.stop_flag = False
+        self.th = None
+        self.smi = None
+        try:
+            self.nv = _Nvml(gpu)
+            self.max_mhz = self.nv.clock(maximum=True)
+        except Exception:
+            self.nv = None
+
+    def _poll(self):
+        nv = self.nv
+        names = [("hw_slowdown", nv.HW_SLOWDOWN), ("hw_thermal_slowdown", nv.HW_THERMAL),
+                 ("sw_thermal_slowdown", nv.SW_THERMAL), ("sw_power_cap", nv.SW_POWER_CAP)]
+        while not self.stop_flag:
+            try:
+                mhz = nv.clock()
+                bits = nv.reasons()
+                self.samples.append((mhz, [n for n, b in names if bits & b]))
+            except Exception:
+                pass
+            time.sleep(0.001)
 
     def start(self):
+        if self.nv is not None:
+            import threading
+            self.th = threading.Thread(target=self._poll, daemon=True)
+            self.th.start()
+            return
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        fields = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+            self.smi = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + fields,
                  "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
         except (FileNotFoundError, OSError):
-            self.proc = None
+            self.smi = None
 
     def stop(self):
-        if self.proc is None:
+        if self.th is not None:
+            self.stop_flag = True
+            self.th.join()
+            if not self.samples:
+                return None
+            sm = [m for m, _ in self.samples]
+            reasons = sorted({r for _, rs in self.samples for r in rs})
+            return {"sm_mhz": statistics.median(sm), "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                    "samples": len(sm), "source": "nvml"}
+        if self.smi is None:
             return None
-        self.proc.terminate()
+        self.smi.terminate()
         try:
-            self.proc.wait(timeout=5)
+            self.smi.wait(timeout=5)
         except subprocess.TimeoutExpired:
-            self.proc.kill()
+            self.smi.kill()
         self.f.flush()
         self.f.seek(0)
         rows = [l.strip().split(", ") for l in self.f.read().splitlines() if l.strip()]
@@ -114,7 +181,7 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi"}
 
 
 def measured_peaks():

@@ -428,6 +428,11 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         max_np = std::max<int>(max_np, (int)b);
     }
     const int64_t ns = d->sample_off[ne], np = d->pix_off[ne];
+    // sample offsets (padded to 4 per event) are 32-bit on the device
+    if (ns + 3 * (int64_t)ne >= ((int64_t)1 << 31)) {
+        set_error("more than 2^31 PE samples in one catalog");
+        return CHIMERA_ERR_UNSUPPORTED;
+    }
     if (d->gal_off[0] != 0) return bad("gal_off must start at 0");
     for (int64_t p = 0; p < np; p++) {
         if (d->gal_off[p + 1] < d->gal_off[p]) return bad("gal_off not monotone");
@@ -624,6 +629,14 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     std::vector<int32_t> ev_order(ne);
     std::iota(ev_order.begin(), ev_order.end(), 0);
     std::stable_sort(ev_order.begin(), ev_order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<int4> ev_info(2 * (size_t)ne);
+    for (int pos = 0; pos < ne; pos++) {
+        const int e = ev_order[pos];
+        ev_info[2 * pos] = make_int4(e, (int)d->sample_off[e], (int)(d->sample_off[e + 1] - d->sample_off[e]),
+                                     (int)ev_zoff[e]);
+        ev_info[2 * pos + 1] = make_int4(ev_goff[e], ev_goff[e + 1] - ev_goff[e], ev_segoff[e],
+                                         ev_segoff[e + 1] - ev_segoff[e]);
+    }
     // ---- galaxies: sorted by z inside each pixel
     std::vector<int64_t> gorder(ng);
     std::iota(gorder.begin(), gorder.end(), 0);
@@ -685,6 +698,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         {(void **)&c.ev_soff, ev_soff.data(), 8 * ev_soff.size()},
         {(void **)&c.ev_poff, ev_poff.data(), 8 * ev_poff.size()},
         {(void **)&c.ev_order, ev_order.data(), 4 * ev_order.size()},
+        {(void **)&c.ev_info, ev_info.data(), 16 * ev_info.size()},
         {(void **)&c.seg_soff, seg_soff.data(), 8 * seg_soff.size()},
         {(void **)&c.seg_pf, seg_pf.data(), 8 * seg_pf.size()},
         {(void **)&c.ev_segoff, ev_segoff.data(), 4 * ev_segoff.size()},

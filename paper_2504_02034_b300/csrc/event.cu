@@ -301,7 +301,7 @@ constexpr int RW_THREADS = 256;
 __global__ void __launch_bounds__(RW_THREADS) k_reweight(DevCatalog c, CallPtrs p, int h0, int nh) {
     __shared__ double red[8 + (RW_THREADS / 32) * 8];
     const int hl = blockIdx.x % nh, h = h0 + hl;
-    const int ev = blockIdx.x / nh;
+    const int ev = blockIdx.x / nh;  // natural order: consecutive blocks stream neighbouring samples
     const int tid = threadIdx.x;
     const HP &hp = p.hp[h];
     if (hp.status & (CHIMERA_PT_OUT_OF_SUPPORT | CHIMERA_PT_NONMONOTONE)) return;
@@ -404,7 +404,9 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
     __shared__ int s_gctr;
 
     const int hl = blockIdx.x % nh, h = h0 + hl;
-    const int ev = c.ev_order[blockIdx.x / nh];
+    const int4 ei = __ldg(c.ev_info + 2 * (blockIdx.x / nh));      // (ev, s0, ns, zoff)
+    const int4 ej = __ldg(c.ev_info + 2 * (blockIdx.x / nh) + 1);  // (g0, ngroups, sg0, nseg)
+    const int ev = ei.x;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const size_t out = (size_t)h * c.n_events + ev;
     const HP &hp = p.hp[h];
@@ -418,13 +420,12 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
     if (tid == 0) s_gctr = 0;
     // ---- prologue: the event's reweighted samples, its group and segment
     // metadata and F, all requested at once with cp.async
-    const int64_t s0 = c.ev_soff[ev];
-    const int ns = (int)(c.ev_soff[ev + 1] - s0);
-    const int g0 = c.ev_goff[ev];
-    const int ngroups = c.ev_goff[ev + 1] - g0;
-    const int sg0 = c.ev_segoff[ev], nseg = c.ev_segoff[ev + 1] - sg0;
+    const int64_t s0 = ei.y;
+    const int ns = ei.z;
+    const int g0 = ej.x, ngroups = ej.y;
+    const int sg0 = ej.z, nseg = ej.w;
     {
-        const float *zsrc = p.zw + (size_t)hl * 2 * c.n_zpad + c.ev_zoff[ev];
+        const float *zsrc = p.zw + (size_t)hl * 2 * c.n_zpad + ei.w;
         const float *wsrc = zsrc + c.n_zpad;
         for (int i = tid; i < (ns + 3) >> 2; i += EV_THREADS) {
             cp_async16(zs + 4 * i, zsrc + 4 * i);

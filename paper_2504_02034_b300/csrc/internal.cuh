@@ -74,6 +74,9 @@ struct DevCatalog {
     int64_t *ev_soff;     // [n_events+1] sample offsets (sorted storage)
     int64_t *ev_poff;     // [n_events+1] flat pixel offsets
     int32_t *ev_order;    // [n_events] heavy-first launch order
+    // per launch position (heavy-first order): the event's index and offsets,
+    // read by one 32-byte load: (ev, s0, ns, zoff) and (g0, ngroups, sg0, nseg)
+    int4 *ev_info;
     // KDE segments: many-1D = pixels, single-1D = events
     int64_t n_seg;
     int64_t *seg_soff;    // [n_seg+1] sample offsets of each segment

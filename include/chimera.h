@@ -256,7 +256,8 @@ int chimera_serve_reset_stats(chimera_ctx *ctx);
  * chimera_stage_ms then returns the last call's stage times in
  * milliseconds (ms holds 7 doubles): ms[0] cosmology tables (K1), ms[1]
  * galaxy profile (K3, 0 when cached), ms[2] event integrals (K4; with the
- * reweighting for FP64, where K2 is fused into it), ms[3] selection (K5),
+ * reweighting for FP64, where K2 is fused into it), ms[3] selection (K5,
+ * which runs on a second stream beside K2/K4, so the stages overlap),
  * ms[4] combine (K6), ms[5] adjoint (K7, gradient calls only), ms[6]
  * reweighting (K2, mixed path).
  */

@@ -103,6 +103,15 @@ CallPtrs Workspace::ptrs(int H, const DevCatalog &c) const {
     return p;
 }
 
+void ws_destroy_streams(Workspace &ws) {
+    if (ws.st2) cudaStreamSynchronize(ws.st2);
+    if (ws.ev_fork) cudaEventDestroy(ws.ev_fork);
+    if (ws.ev_join) cudaEventDestroy(ws.ev_join);
+    if (ws.st2) cudaStreamDestroy(ws.st2);
+    ws.st2 = nullptr;
+    ws.ev_fork = ws.ev_join = nullptr;
+}
+
 void ws_release(Ctx &ctx, Workspace &ws) {
     adjoint_release(ctx, ws);
     for (void *a : ws.allocs) cudaFree(a);
@@ -340,6 +349,22 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
     if (p.pairs) CK(cudaMemsetAsync(p.pairs, 0, sizeof(unsigned long long) * H, ws.st));
     launch_hyper_tables(c, p, H, ws.dk, ws.fmax_bits, ws.st);
     if (ws.trace) CK(cudaEventRecord(ws.tev[2], ws.st));
+    // the selection term needs only the per-point tables: it runs on a side
+    // stream of the lowest priority beside the event kernels, whose blocks
+    // are dispatched first (the library streams have the highest priority)
+    if (!ws.st2) {
+        int lo = 0, hi = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CK(cudaStreamCreateWithPriority(&ws.st2, cudaStreamNonBlocking, lo));
+        CK(cudaEventCreateWithFlags(&ws.ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ws.ev_join, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(ws.ev_fork, ws.st));
+    CK(cudaStreamWaitEvent(ws.st2, ws.ev_fork, 0));
+    if (ws.trace) CK(cudaEventRecord(ws.tev[8], ws.st2));
+    launch_selection(c, p, H, precision == CHIMERA_FP64, ws.st2);
+    if (ws.trace) CK(cudaEventRecord(ws.tev[9], ws.st2));
+    CK(cudaEventRecord(ws.ev_join, ws.st2));
     if (precision == CHIMERA_FP64) launch_event_fp64(c, p, H, ws.st);
     else {
         // reweighting and event integrals by tiles of hyperpoints
@@ -362,7 +387,7 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
         }
     }
     if (ws.trace) CK(cudaEventRecord(ws.tev[3], ws.st));
-    launch_selection(c, p, H, precision == CHIMERA_FP64, ws.st);
+    CK(cudaStreamWaitEvent(ws.st, ws.ev_join, 0));
     if (ws.trace) CK(cudaEventRecord(ws.tev[4], ws.st));
     launch_combine(c, p, H, precision != CHIMERA_FP64, ws.st);
     if (ws.trace) CK(cudaEventRecord(ws.tev[5], ws.st));
@@ -833,7 +858,9 @@ int chimera_create(chimera_ctx **out, int device, size_t budget) {
     CK(cudaSetDevice(device));
     auto *h = new chimera_ctx();
     h->c.device = device;
-    if (cudaStreamCreateWithFlags(&h->c.stream, cudaStreamNonBlocking) != cudaSuccess) {
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (cudaStreamCreateWithPriority(&h->c.stream, cudaStreamNonBlocking, prio_hi) != cudaSuccess) {
         delete h;
         set_error("cudaStreamCreate failed");
         return CHIMERA_ERR_CUDA;
@@ -865,6 +892,7 @@ void chimera_destroy(chimera_ctx *h) {
     }
     ctx.fwdO.clear();
     ws_release(ctx, ctx.ws);
+    ws_destroy_streams(ctx.ws);
     for (auto &e : ctx.ws.tev)
         if (e) cudaEventDestroy(e);
     for (auto &e : ctx.ws.tile_ev) cudaEventDestroy(e);
@@ -1053,7 +1081,7 @@ int chimera_stage_ms(chimera_ctx *h, double *ms) {
         ms[2] = ev;
         ms[6] = rw;
     }
-    CK(cudaEventElapsedTime(&t, ws.tev[3], ws.tev[4])); ms[3] = t;
+    CK(cudaEventElapsedTime(&t, ws.tev[8], ws.tev[9])); ms[3] = t;  // side stream
     CK(cudaEventElapsedTime(&t, ws.tev[4], ws.tev[5])); ms[4] = t;
     if (ws.traced_adjoint && ws.tev[6] && ws.tev[7]) {
         CK(cudaEventSynchronize(ws.tev[7]));

@@ -83,9 +83,13 @@ struct Workspace {
     // windowed-pair counters (roofline accounting), used when count_pairs
     unsigned long long *pairs = nullptr;
     bool count_pairs = false;
+    // second stream for the selection term, which runs beside the event
+    // kernels (fork after the per-point tables, join before the combine)
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // stage tracing (CUDA events around K1, K3, K4, K5, K6, K7)
     bool trace = false;
-    cudaEvent_t tev[8] = {};
+    cudaEvent_t tev[10] = {};
     bool traced_adjoint = false;
     std::vector<cudaEvent_t> tile_ev;  // mixed: after the reweighting and after K4 of each tile
     int traced_tiles = 0;
@@ -120,6 +124,8 @@ void dev_free(Ctx &ctx, void *p, size_t bytes);
 
 int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat);
 void ws_release(Ctx &ctx, Workspace &ws);
+// Destroys the workspace's side stream and fork/join events.
+void ws_destroy_streams(Workspace &ws);
 
 // Forward pass for H points on workspace `ws` (enqueued on ws.st).
 // theta: host [H x 12].  Leaves lnL / neff / xi / status / lnI / bw on the

@@ -116,7 +116,9 @@ int Server::launch(Lane &L, std::vector<std::shared_ptr<Request>> &b) {
     int rc = lane_buffers(L, H);
     if (rc) return rc;
     if (!L.ws.st) {
-        if (cudaStreamCreateWithFlags(&L.ws.st, cudaStreamNonBlocking) != cudaSuccess) {
+        int prio_lo = 0, prio_hi = 0;
+        cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+        if (cudaStreamCreateWithPriority(&L.ws.st, cudaStreamNonBlocking, prio_hi) != cudaSuccess) {
             cudaGetLastError();
             set_error("cudaStreamCreate failed");
             return CHIMERA_ERR_CUDA;
@@ -390,6 +392,7 @@ void serve_shutdown(Ctx &ctx) {
     for (auto &L : s->lanes) {
         if (L.ws.st) cudaStreamSynchronize(L.ws.st);
         ws_release(ctx, L.ws);
+        ws_destroy_streams(L.ws);
         if (L.ws.st) cudaStreamDestroy(L.ws.st);
         if (L.done) cudaEventDestroy(L.done);
         if (L.h_lnL) cudaFreeHost(L.h_lnL);

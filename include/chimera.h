@@ -282,7 +282,7 @@ int chimera_kde_pairs(chimera_ctx *ctx, int32_t catalog_id, int32_t n_points, co
  * counterpart; this is an interface convenience.
  *
  * It allocates nothing: every intermediate lives in one fixed device array
- * of about 17 MB compiled into the library, which every GPU that loads the
+ * of about 14 MB compiled into the library, which every GPU that loads the
  * library holds until exit.  It runs on the calling thread's current CUDA
  * device and on `stream` (a cudaStream_t; NULL = the legacy default stream).
  *   theta        host [n_points x 12], n_points <= 64 (else UNSUPPORTED).

@@ -174,7 +174,7 @@ int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat) {
         {(void **)&ws.invZ32, sizeof(float) * (size_t)std::max<int64_t>(ng, 1)},
         {(void **)&ws.grad, sizeof(double) * 12 * (size_t)Hn},
         {(void **)&ws.pairs, sizeof(unsigned long long) * (size_t)Hn},
-        {(void **)&ws.dk, sizeof(double) * 2 * (size_t)Hn * NT_FWD},
+        {(void **)&ws.dk, sizeof(float) * 2 * (size_t)Hn * NT_FWD},
         {(void **)&ws.fmax_bits, sizeof(unsigned long long) * (size_t)Hn},
         {(void **)&ws.zw, sizeof(float) * 2 * (size_t)zpad * ztile},
     };
@@ -347,7 +347,7 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
     CK(cudaMemcpyAsync(ws.param, ws.hstage, ws.param_bytes(H), cudaMemcpyHostToDevice, ws.st));
     CallPtrs p = ws.ptrs(H, c);
     if (p.pairs) CK(cudaMemsetAsync(p.pairs, 0, sizeof(unsigned long long) * H, ws.st));
-    launch_hyper_tables(c, p, H, ws.dk, ws.fmax_bits, ws.st);
+    launch_hyper_tables(c, p, H, precision == CHIMERA_FP64, ws.dk, ws.fmax_bits, ws.st);
     if (ws.trace) CK(cudaEventRecord(ws.tev[2], ws.st));
     // the selection term needs only the per-point tables: it runs on a side
     // stream of the lowest priority beside the event kernels, whose blocks

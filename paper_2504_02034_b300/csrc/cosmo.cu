@@ -76,109 +76,156 @@ constexpr int HYP_THREADS = 256;
 
 __device__ double std_normal_cdf(double x) { return 0.5 * erfc(-x * 0.70710678118654752440); }
 
-// K1b.1: d_L^gw and J at the forward nodes of every hyperpoint; J <= 0 on
-// z <= 10 sets the NONMONOTONE bit.
-__global__ void __launch_bounds__(HYP_THREADS) k_fwd_nodes(CallPtrs p, double *dk, double *jk) {
+// FP32 forward relation at z from D = D_c [Mpc]: d_L^gw and its z-derivative J.
+__device__ __forceinline__ void dgw_J32(float z, float D, float cH, float om, float xi0, float n, float &d,
+                                       float &J) {
+    const float a = 1.f + z;
+    const float pw = exp2f(-n * log2f(a));  // (1+z)^-n
+    const float xi = xi0 + (1.f - xi0) * pw;
+    const float dxi = -n * (1.f - xi0) * pw / a;
+    const float E = sqrtf(om * a * a * a + 1.f - om);
+    d = a * D * xi;
+    J = (D + a * cH / E) * xi + a * D * dxi;
+}
+
+// K1b.1, one launch for two independent parts per hyperpoint (blockIdx.y):
+//  * blocks x < nbn: d_L^gw and J at the forward nodes, in FP32 (they seed
+//    the FP64 inversion and carry the monotonicity check: J <= 0 on z <= 10
+//    sets the NONMONOTONE bit);
+//  * blocks x >= nbn: the grid factor F(z_a) = psi / ((1+z)^3 |J|) and its
+//    maximum, in FP64 for FP64 calls (F64), in FP32 for mixed ones (F32, not
+//    yet normalised).
+__global__ void __launch_bounds__(HYP_THREADS) k_nodes_grid(DevCatalog c, CallPtrs p, float2 *djall,
+                                                           unsigned long long *fmax_bits, int nbn, bool f64) {
     const int h = blockIdx.y;
-    const int k = blockIdx.x * HYP_THREADS + threadIdx.x;
-    if (k >= NT_FWD) return;
     const double *th = p.theta + 12 * h;
     const double cH = C_KMS / th[0];
-    double d, J;
-    chimd::dgw_J(k * HT, cH * p.fwd[h][k], th, cH, &d, &J);
-    dk[(size_t)h * NT_FWD + k] = d;
-    jk[(size_t)h * NT_FWD + k] = J;
-    if (k <= K_Z10 && !(J > 0.0)) atomicOr(p.status + h, CHIMERA_PT_NONMONOTONE);
+    const double *fwd = p.fwd[h];
+    if ((int)blockIdx.x < nbn) {
+        const int k = blockIdx.x * HYP_THREADS + threadIdx.x;
+        if (k >= NT_FWD) return;
+        float d, J;
+        dgw_J32(k * (float)HT, (float)(cH * fwd[k]), (float)cH, (float)th[1], (float)th[2], (float)th[3], d, J);
+        djall[(size_t)h * NT_FWD + k] = make_float2(d, J);
+        if (k <= K_Z10 && !(J > 0.f)) atomicOr(p.status + h, CHIMERA_PT_NONMONOTONE);
+        return;
+    }
+    const int a = (blockIdx.x - nbn) * HYP_THREADS + threadIdx.x;
+    unsigned long long bits = 0;
+    if (a < c.n_z) {
+        if (f64) {
+            double z = a * c.dz, d, J;
+            chimd::dgw_J(z, cH * chimd::dc_hermite(fwd, z, th[1]), th, cH, &d, &J);
+            const double ap = 1.0 + z;
+            double F = chimd::psi_of(z, th) / (ap * ap * ap * fabs(J));
+            if (!isfinite(F)) F = 0.0;
+            p.F64[(size_t)h * c.n_z + a] = F;
+            bits = (unsigned long long)__double_as_longlong(F);
+        } else {
+            // D_c by cubic Hermite on the forward table, in FP32
+            const float z = a * c.dz32, om = (float)th[1], ht = (float)HT;
+            const float t = z / ht;
+            const int k = min(max((int)floorf(t), 0), NT_FWD - 2);
+            const float f = t - k, f2 = f * f, f3 = f2 * f;
+            auto slope = [om, ht](float zz) {
+                const float aa = 1.f + zz;
+                return ht / sqrtf(om * aa * aa * aa + 1.f - om);
+            };
+            const float Dh = (2.f * f3 - 3.f * f2 + 1.f) * (float)fwd[k] + (f3 - 2.f * f2 + f) * slope(k * ht) +
+                             (-2.f * f3 + 3.f * f2) * (float)fwd[k + 1] + (f3 - f2) * slope((k + 1) * ht);
+            float d, J;
+            dgw_J32(z, (float)cH * Dh, (float)cH, om, (float)th[2], (float)th[3], d, J);
+            const float ap = 1.f + z, l2a = log2f(ap);
+            const float gam = (float)th[9], gk = (float)(th[9] + th[10]);
+            const float psi = exp2f(gam * l2a) / (1.f + exp2f(gk * (l2a - (float)log2(1.0 + th[11]))));
+            float F = psi / (ap * ap * ap * fabsf(J));
+            if (!isfinite(F)) F = 0.f;
+            p.F32[(size_t)h * c.n_z + a] = F;
+            bits = (unsigned long long)__float_as_uint(F);
+        }
+    }
+    // F >= 0, so the ordering of the bit patterns is the ordering of the values
+    for (int o = 16; o > 0; o >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, o));
+    if ((threadIdx.x & 31) == 0 && bits > 0) atomicMax(fmax_bits + h, bits);
 }
 
 // K1b.2: inverse nodes z(u_k), d = d_top u_k^2: bracketing on the forward
 // nodes (staged in shared memory), cubic Hermite of z(d) between the two
-// bracketing nodes (slopes 1/J), then one Newton step on the
-// Hermite-interpolated forward relation.
-__global__ void __launch_bounds__(HYP_THREADS) k_inv_nodes(DevCatalog c, CallPtrs p, const double *dkall,
-                                                          const double *jkall) {
-    __shared__ double sdk[NT_FWD];
+// bracketing nodes (slopes 1/J), then one FP64 Newton step on the
+// Hermite-interpolated forward relation.  A block computes the nodes
+// base .. base+256 (one more than it owns) so that it also writes the FP32
+// node pairs of its intervals.
+__global__ void __launch_bounds__(HYP_THREADS) k_inv_nodes(DevCatalog c, CallPtrs p, const float2 *djall) {
+    __shared__ float sdk[NT_FWD];
+    __shared__ double2 snd[HYP_THREADS + 1];
     const int h = blockIdx.y;
-    const int k = blockIdx.x * HYP_THREADS + threadIdx.x;
-    const double *dk = dkall + (size_t)h * NT_FWD;
-    const double *jk = jkall + (size_t)h * NT_FWD;
-    for (int i = threadIdx.x; i < NT_FWD; i += HYP_THREADS) sdk[i] = dk[i];
+    const int base = blockIdx.x * HYP_THREADS;
+    const float2 *dj = djall + (size_t)h * NT_FWD;
+    for (int i = threadIdx.x; i < NT_FWD; i += HYP_THREADS) sdk[i] = dj[i].x;
     __syncthreads();
-    if (k > NU) return;
     const double *th = p.theta + 12 * h;
     const double *fwd = p.fwd[h];
     const double cH = C_KMS / th[0], Om = th[1];
     const double dtop = c.d_top;
-    double u = (double)k / NU, d = dtop * u * u;
-    double z = 0.0, dzdu = 0.0;
-    if (k > 0) {
-        if (!(d <= sdk[NT_FWD - 1])) {
-            z = CUDART_NAN;
-            dzdu = CUDART_NAN;
-        } else {
-            int lo = 0, hi = NT_FWD - 1;  // sdk[lo] <= d < sdk[hi]
-            while (hi - lo > 1) {
-                int mid = (lo + hi) >> 1;
-                if (sdk[mid] <= d) lo = mid; else hi = mid;
+    for (int t = threadIdx.x; t <= HYP_THREADS; t += HYP_THREADS) {
+        const int k = base + t;
+        if (k > NU) break;
+        const double u = (double)k / NU, d = dtop * u * u;
+        double z = 0.0, dzdu = 0.0;
+        if (k > 0) {
+            if (!(d <= (double)sdk[NT_FWD - 1])) {
+                z = CUDART_NAN;
+                dzdu = CUDART_NAN;
+            } else {
+                int lo = 0, hi = NT_FWD - 1;  // sdk[lo] <= d < sdk[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if ((double)sdk[mid] <= d) lo = mid; else hi = mid;
+                }
+                const double dl = sdk[lo], dh = sdk[hi], den = dh - dl;
+                const double tt = den > 0.0 ? (d - dl) / den : 0.0;
+                const double t2 = tt * tt, t3 = t2 * tt;
+                z = (2 * t3 - 3 * t2 + 1) * (lo * HT) + (t3 - 2 * t2 + tt) * den / (double)dj[lo].y +
+                    (-2 * t3 + 3 * t2) * (hi * HT) + (t3 - t2) * den / (double)dj[hi].y;
+                double dd, J;
+                chimd::dgw_J(z, cH * chimd::dc_hermite(fwd, z, Om), th, cH, &dd, &J);
+                const double step = (dd - d) / J;
+                if (isfinite(step)) z -= step;
+                dzdu = 2.0 * u * dtop / J;
             }
-            const double dl = sdk[lo], dh = sdk[hi], den = dh - dl;
-            const double t = den > 0.0 ? (d - dl) / den : 0.0;
-            const double t2 = t * t, t3 = t2 * t;
-            z = (2 * t3 - 3 * t2 + 1) * (lo * HT) + (t3 - 2 * t2 + t) * den / jk[lo] +
-                (-2 * t3 + 3 * t2) * (hi * HT) + (t3 - t2) * den / jk[hi];
-            double dd, J;
-            chimd::dgw_J(z, cH * chimd::dc_hermite(fwd, z, Om), th, cH, &dd, &J);
-            const double step = (dd - d) / J;
-            if (isfinite(step)) z -= step;
-            dzdu = 2.0 * u * dtop / J;
         }
+        snd[t] = make_double2(z, dzdu);
+        if (t < HYP_THREADS || k == NU) p.inv64[(size_t)h * (NU + 1) + k] = snd[t];
     }
-    p.inv64[(size_t)h * (NU + 1) + k] = make_double2(z, dzdu);
+    __syncthreads();
+    const int k = base + threadIdx.x;
+    if (k < NU) {
+        const double inv_nu = 1.0 / NU;  // exact: NU is a power of two
+        const double2 a = snd[threadIdx.x], b = snd[threadIdx.x + 1];
+        p.inv32[(size_t)h * NU + k] = make_float4((float)a.x, (float)(a.y * inv_nu), (float)b.x, (float)(b.y * inv_nu));
+    }
 }
 
-// K1b.3: grid factor F(z_a) = psi / ((1+z)^3 |J|) and its maximum.
-__global__ void __launch_bounds__(HYP_THREADS) k_grid(DevCatalog c, CallPtrs p, unsigned long long *fmax_bits) {
-    const int h = blockIdx.y;
-    const int a = blockIdx.x * HYP_THREADS + threadIdx.x;
-    double F = 0.0;
-    if (a < c.n_z) {
-        const double *th = p.theta + 12 * h;
-        const double cH = C_KMS / th[0];
-        double z = a * c.dz, d, J;
-        chimd::dgw_J(z, cH * chimd::dc_hermite(p.fwd[h], z, th[1]), th, cH, &d, &J);
-        double ap = 1.0 + z;
-        F = chimd::psi_of(z, th) / (ap * ap * ap * fabs(J));
-        if (!isfinite(F)) F = 0.0;
-        p.F64[(size_t)h * c.n_z + a] = F;
-    }
-    for (int o = 16; o > 0; o >>= 1) F = fmax(F, __shfl_xor_sync(0xffffffffu, F, o));
-    // F >= 0, so the ordering of the bit patterns is the ordering of the values
-    if ((threadIdx.x & 31) == 0 && F > 0.0) atomicMax(fmax_bits + h, (unsigned long long)__double_as_longlong(F));
-}
-
-// K1b.4: per-hyperpoint constants, FP32 inverse intervals, normalised F.
+// K1b.3: per-hyperpoint constants (block x = 0, the independent FP64 scalars
+// one per lane) and, for mixed calls, F normalised by its maximum.
 __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallPtrs p,
-                                                            const double *dkall,
-                                                            const unsigned long long *fmax_bits) {
-    const int h = blockIdx.x, t = threadIdx.x;
-    const double Fm = __longlong_as_double((long long)fmax_bits[h]);
+                                                            const unsigned long long *fmax_bits, bool f64) {
+    const int h = blockIdx.y, t = threadIdx.x;
+    const double Fm = f64 ? __longlong_as_double((long long)fmax_bits[h])
+                          : (double)__uint_as_float((unsigned)fmax_bits[h]);
     const double Fs = Fm > 0.0 ? Fm : 1.0;
-    const double2 *nd = p.inv64 + (size_t)h * (NU + 1);
-    __shared__ double sc[8];
-    const double inv_nu = 1.0 / NU;  // exact: NU is a power of two
-    for (int k = t; k < NU; k += HYP_THREADS) {
-        double2 a = nd[k], b = nd[k + 1];
-        p.inv32[(size_t)h * NU + k] =
-            make_float4((float)a.x, (float)(a.y * inv_nu), (float)b.x, (float)(b.y * inv_nu));
+    if (!f64) {
+        const float iFs = (float)(1.0 / Fs);
+        const int a = blockIdx.x * HYP_THREADS + t;
+        if (a < c.n_z) p.F32[(size_t)h * c.n_z + a] *= iFs;
     }
-    const double iFs = 1.0 / Fs;
-    for (int a = t; a < c.n_z; a += HYP_THREADS)
-        p.F32[(size_t)h * c.n_z + a] = (float)(p.F64[(size_t)h * c.n_z + a] * iFs);
+    if (blockIdx.x != 0) return;
+    __shared__ double sc[8];
     const double *th = p.theta + 12 * h;
     const double alpha = th[4], mu = th[5], sg = th[6], mmin = th[7], mmax = th[8];
     const double lam = c.lambda_g, beta = c.beta;
-    // the independent FP64 scalars, one per lane of warp 0
-    if (t < 4) {
+    const double cH = C_KMS / th[0];
+    if (t < 5) {
         double v = 0.0;
         if (t == 0)
             v = fabs(1.0 - alpha) < 1e-12 ? log(mmax / mmin)
@@ -187,15 +234,18 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
             v = std_normal_cdf((mmax - mu) / sg) - std_normal_cdf((mmin - mu) / sg);
         else if (t == 2)
             v = pow(mmin, 1.0 + beta);
-        else
+        else if (t == 3)
             v = chimd::dc_hermite(p.fwd[h], c.z_max, th[1]);
+        else {  // d_L^gw at the end of the redshift range, z = 10, in FP64
+            double J;
+            chimd::dgw_J(K_Z10 * HT, cH * p.fwd[h][K_Z10], th, cH, &v, &J);
+        }
         sc[t] = v;
     }
     __syncthreads();
     if (t == 0) {
         HP hp;
         for (int k = 0; k < 12; k++) hp.th[k] = th[k];
-        const double cH = C_KMS / th[0];
         hp.cH = cH;
         const double plint = sc[0], den = sc[1];
         hp.c_pl = (1.0 - lam) / plint;
@@ -204,7 +254,7 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
         hp.mmin_b1 = sc[2];
         hp.lmmin = log(mmin);
         hp.dc_zmax = cH * sc[3];
-        hp.d_valid = dkall[(size_t)h * NT_FWD + K_Z10];
+        hp.d_valid = sc[4];
         hp.F_scale = Fs;
         double tv = sqrt(hp.d_valid / c.d_top) * NU;
         hp.t_valid = tv;
@@ -247,14 +297,15 @@ void launch_fwd_table(double Om, double *out, cudaStream_t st) {
     k_fwd_table<<<1, FWD_THREADS, 0, st>>>(Om, out);
 }
 
-void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, double *dk,
+void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, double *dk,
                          unsigned long long *fmax_bits, cudaStream_t st) {
+    float2 *dj = reinterpret_cast<float2 *>(dk);  // (d, J) of the forward nodes, FP32
     cudaMemsetAsync(fmax_bits, 0, sizeof(unsigned long long) * H, st);
-    double *jk = dk + (size_t)H * NT_FWD;  // J at the forward nodes
-    k_fwd_nodes<<<dim3((NT_FWD + HYP_THREADS - 1) / HYP_THREADS, H), HYP_THREADS, 0, st>>>(p, dk, jk);
-    k_inv_nodes<<<dim3((NU + 1 + HYP_THREADS - 1) / HYP_THREADS, H), HYP_THREADS, 0, st>>>(c, p, dk, jk);
-    k_grid<<<dim3((c.n_z + HYP_THREADS - 1) / HYP_THREADS, H), HYP_THREADS, 0, st>>>(c, p, fmax_bits);
-    k_hyper_final<<<H, HYP_THREADS, 0, st>>>(c, p, dk, fmax_bits);
+    const int nbn = (NT_FWD + HYP_THREADS - 1) / HYP_THREADS;
+    const int nbg = (c.n_z + HYP_THREADS - 1) / HYP_THREADS;
+    k_nodes_grid<<<dim3(nbn + nbg, H), HYP_THREADS, 0, st>>>(c, p, dj, fmax_bits, nbn, fp64);
+    k_inv_nodes<<<dim3((NU + HYP_THREADS - 1) / HYP_THREADS, H), HYP_THREADS, 0, st>>>(c, p, dj);
+    k_hyper_final<<<dim3(fp64 ? 1 : nbg, H), HYP_THREADS, 0, st>>>(c, p, fmax_bits, fp64);
 }
 
 }  // namespace chim

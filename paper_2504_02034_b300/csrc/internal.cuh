@@ -136,10 +136,11 @@ struct CallPtrs {
 // ---- launch wrappers (host) ----
 // K1a: forward table D_c(z_k) / (c/H0) for one Om into `out` [NT_FWD].
 void launch_fwd_table(double Om, double *out, cudaStream_t st);
-// K1b: per-hyperpoint parameters, inverse tables, grid factors, status.
-// dk: [2 x H x NT_FWD] scratch (d_L^gw, then J, at the forward nodes),
+// K1b: per-hyperpoint parameters, inverse tables, grid factors (F64 for
+// fp64, normalised F32 otherwise), status.  dk: scratch of at least
+// H x NT_FWD x 8 bytes (FP32 d_L^gw and J at the forward nodes),
 // fmax_bits: [H] scratch.
-void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, double *dk,
+void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, double *dk,
                          unsigned long long *fmax_bits, cudaStream_t st);
 // K3: galaxy redshift prior on the grid for one Om.  dv: [n_z] scratch,
 // invZ: [n_gal] scratch; out64 (FP64 values) or out32 (stored values).

@@ -41,7 +41,7 @@ constexpr size_t OFF_INV32 = al(OFF_INV64 + sizeof(double2) * ST_HMAX * (NU + 1)
 constexpr size_t OFF_F64 = al(OFF_INV32 + sizeof(float4) * ST_HMAX * NU);
 constexpr size_t OFF_F32 = al(OFF_F64 + sizeof(double) * ST_HMAX * ST_NZ);
 constexpr size_t OFF_DK = al(OFF_F32 + sizeof(float) * ST_HMAX * ST_NZ);
-constexpr size_t OFF_FMAX = al(OFF_DK + sizeof(double) * 2 * ST_HMAX * NT_FWD);  // d and J per node
+constexpr size_t OFF_FMAX = al(OFF_DK + sizeof(float) * 2 * ST_HMAX * NT_FWD);  // FP32 d and J per node
 constexpr size_t OFF_FWD = al(OFF_FMAX + sizeof(unsigned long long) * ST_HMAX);
 constexpr size_t OFF_SELP = al(OFF_FWD + sizeof(double) * ST_HMAX * NT_FWD);
 constexpr size_t OFF_DTOP = al(OFF_SELP + sizeof(double) * 2 * ST_HMAX * ST_CHUNK_MAX);
@@ -225,7 +225,7 @@ extern "C" int chimera_selection_static(int32_t n_points, const double *theta, i
     p.F32 = reinterpret_cast<float *>(S + OFF_F32);
     p.selp = reinterpret_cast<double *>(S + OFF_SELP);
     p.n_chunk = selection_chunks(c);
-    launch_hyper_tables(c, p, H, reinterpret_cast<double *>(S + OFF_DK),
+    launch_hyper_tables(c, p, H, true, reinterpret_cast<double *>(S + OFF_DK),
                         reinterpret_cast<unsigned long long *>(S + OFF_FMAX), st);
     launch_selection(c, p, H, true, st);
     k_static_reduce<<<H, 256, 0, st>>>(p.selp, p.n_chunk, (double)n_inj_total, p.hp, xi, neff);

@@ -68,7 +68,7 @@ struct Workspace {
     double *lnI = nullptr, *bw = nullptr, *selp = nullptr;
     double *lnL = nullptr, *neff = nullptr, *xi = nullptr;
     double *dv = nullptr, *invZ64 = nullptr;
-    double *dk = nullptr;                  // [2 x H x NT_FWD] forward-node scratch (d, J)
+    double *dk = nullptr;                  // [H x NT_FWD] forward-node scratch (FP32 d, J)
     float *zw = nullptr;                   // [zw_tile x 2 x zpad_cap] reweighted samples (mixed)
     int zw_tile = 0;                       // hyperpoints per reweighting tile
     int64_t zpad_cap = 0;

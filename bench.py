@@ -500,10 +500,10 @@ def main():
         "serving": serving,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(theta.nbytes),
                 "d2h_bytes_per_step": int(H * (8 + 8 + 4))},
-        # per step: k_fwd_nodes, k_inv_nodes, k_grid, k_hyper_final, k_reweight,
+        # per step: k_nodes_grid, k_inv_nodes, k_hyper_final, k_reweight,
         # k_event_mixed, k_select_mixed, k_combine (the forward table and galaxy
         # profile are cached)
-        "gpu_launches": 8 * args.steps,
+        "gpu_launches": 7 * args.steps,
         "roofline": roof,
         "peaks_measured": {k: v for k, v in peaks.items()},
         "clocks": clk,

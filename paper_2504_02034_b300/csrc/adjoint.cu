@@ -46,7 +46,7 @@ struct HPd {
 // Device views of the adjoint's inputs and scratch.
 struct AdjPtrs {
     const double *const *fwdO;   // [H] dDhat/dOm table of h's Om
-    const double *const *dprof;  // [H] dG/dOm profile of h's Om (rows as the forward profile)
+    const double *const *dprof;  // [H] dG/dOm profile of h's Om (rows as the forward profile; FP32 values on the mixed path)
     HPd *hpd;                    // [H]
     double *dznode;              // [H x (NU+1) x 4] dz/d(H0, Om, Xi0, n) at the inverse-table nodes
     float4 *dznode32;            // [H x (NU+1)] FP32 copy
@@ -360,13 +360,16 @@ __device__ void bsum(double (&v)[NV], double *red) {
 // factor) in float, with the per-thread sums carried to double for the
 // block reduction, so that the gradient is that of the computed ln L.
 template <bool F64>
-__global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtrs p, AdjPtrs q, int H) {
+__global__ void __launch_bounds__(ADJ_THREADS, F64 ? 1 : 3) k_event_adj(DevCatalog c, CallPtrs p, AdjPtrs q, int H) {
     using T = typename std::conditional<F64, double, float>::type;
     extern __shared__ double sh[];
     T *zs = reinterpret_cast<T *>(sh);
     T *ws = zs + c.max_ns;
+    const int segn = (c.max_seg + 2) & ~1;
     int *segv = reinterpret_cast<int *>(ws + c.max_ns);
-    double *red = reinterpret_cast<double *>(segv + ((c.max_seg + 2) & ~1));
+    int *sA0 = segv + segn;   // first grid point of each segment's KDE support
+    int *scum = sA0 + segn;   // exclusive prefix of the support lengths
+    double *red = reinterpret_cast<double *>(scum + segn);
     const int h = blockIdx.x % H;
     const int ev = c.ev_order[blockIdx.x / H];
     const int tid = threadIdx.x;
@@ -424,23 +427,34 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
         ws[j] = w;
     }
     __syncthreads();
-    // moments (two-pass, FP64)
-    double m5[5] = {0, 0, 0, 0, 0};  // W1, Wz, W2, n_valid, Sz
-    for (int j = tid; j < ns; j += ADJ_THREADS)
-        if (zs[j] < TINF) {
-            const double z = zs[j], w = ws[j];
-            m5[0] += w; m5[1] += w * z; m5[2] += w * w; m5[3] += 1.0; m5[4] += z;
-        }
+    // moments (two-pass): per-thread sums in the path's precision, block
+    // sums in double
+    double m5[5];  // W1, Wz, W2, n_valid, Sz
+    {
+        T t5[5] = {T(0), T(0), T(0), T(0), T(0)};
+        for (int j = tid; j < ns; j += ADJ_THREADS)
+            if (zs[j] < TINF) {
+                const T z = zs[j], w = ws[j];
+                t5[0] += w; t5[1] += w * z; t5[2] += w * w; t5[3] += T(1); t5[4] += z;
+            }
+        for (int k = 0; k < 5; k++) m5[k] = t5[k];
+    }
     bsum<5>(m5, red);
     const double W1 = m5[0], W2 = m5[2], nv = m5[3];
     const double Mw = W1 > 0.0 ? m5[1] / W1 : 0.0, Mu = nv > 0.0 ? m5[4] / nv : 0.0;
-    double m2v[2] = {0.0, 0.0};
-    for (int j = tid; j < ns; j += ADJ_THREADS)
-        if (zs[j] < TINF) {
-            const double z = zs[j], w = ws[j];
-            m2v[0] += w * (z - Mw) * (z - Mw);
-            m2v[1] += (z - Mu) * (z - Mu);
-        }
+    double m2v[2];
+    {
+        const T Mwv = T(Mw), Muv = T(Mu);
+        T t2[2] = {T(0), T(0)};
+        for (int j = tid; j < ns; j += ADJ_THREADS)
+            if (zs[j] < TINF) {
+                const T z = zs[j], w = ws[j];
+                t2[0] += w * (z - Mwv) * (z - Mwv);
+                t2[1] += (z - Muv) * (z - Muv);
+            }
+        m2v[0] = t2[0];
+        m2v[1] = t2[1];
+    }
     bsum<2>(m2v, red);
     const double varw = W1 > 0.0 ? m2v[0] / W1 : 0.0, neffw = W1 > 0.0 ? W1 * W1 / W2 : 0.0;
     const double varu = nv > 0.0 ? m2v[1] / nv : 0.0;
@@ -497,15 +511,17 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
         const T z = zs[j], w = ws[j], a1 = T(1) + z;
         // dz/dtheta (linear between inverse-table nodes) and d ln w/dtheta
         T dd[4], d5[5], dwz;
-        {
+        if (F64) {
             const double t = sqrt(c.sd64[s0 + j] / c.d_top) * NU;
             const int kk = min((int)t, NU - 1);
-            const T f = T(t - kk);
-            if (F64) {
-                double ddd[4];
-                dz_interp(q, h, kk, t - kk, ddd);
-                for (int k = 0; k < 4; k++) dd[k] = T(ddd[k]);
-            } else {
+            double ddd[4];
+            dz_interp(q, h, kk, t - kk, ddd);
+            for (int k = 0; k < 4; k++) dd[k] = T(ddd[k]);
+        } else {
+            {  // the sample's inverse-table cell and offset, as packed at load
+                const float4 sv = c.s32[s0 + j];
+                const int kk = __float_as_int(sv.x);
+                const float f = sv.y;
                 const float4 n0 = q.dznode32[(size_t)h * (NU + 1) + kk], n1 = q.dznode32[(size_t)h * (NU + 1) + kk + 1];
                 dd[0] = n0.x + f * (n1.x - n0.x);
                 dd[1] = n0.y + f * (n1.y - n0.y);
@@ -562,44 +578,73 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
         for (int k = 0; k < 9; k++) A9[k] += pw * S0 * dlw[k];
         for (int k = 0; k < 4; k++) B4[k] += pw * S1 * ib * dd[k];
     }
-    // ---- grid term: per segment and grid point, the KDE K_k(a)
+    // ---- grid term: the KDE K_k(a) at every grid point of every segment's
+    // support; the (segment, grid point) items are spread over all threads
+    for (int l = tid; l < nseg; l += ADJ_THREADS) {
+        const int lo = (int)(c.seg_soff[sg0 + l] - s0), cnt = segv[l];
+        int alo = 0, len = 0;
+        if (cnt > 0) {
+            const T smin = zs[lo] - T(KDE_MARGIN) * bt, smax = zs[lo + cnt - 1] + T(KDE_MARGIN) * bt;
+            alo = max(0, (int)ceil(smin / dz));
+            len = max(0, min(nz - 1, (int)floor(smax / dz)) - alo + 1);
+        }
+        sA0[l] = alo;
+        scum[l + 1] = len;
+    }
+    __syncthreads();
+    if (tid < 32) {  // in-place inclusive scan of scum[1 .. nseg] by warp 0
+        int carry = 0;
+        for (int b0 = 1; b0 <= nseg; b0 += 32) {
+            const int i = b0 + tid;
+            int v = i <= nseg ? scum[i] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, v, o);
+                if (tid >= o) v += y;
+            }
+            if (i <= nseg) scum[i] = v + carry;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+        if (tid == 0) scum[0] = 0;
+    }
+    __syncthreads();
     T C8[8];  // 7 d ln F terms + the galaxy Om term
     for (int k = 0; k < 8; k++) C8[k] = T(0);
-    for (int l = 0; l < nseg; l++) {
+    const int nitems = scum[nseg];
+    for (int it = tid; it < nitems; it += ADJ_THREADS) {
+        int l = 0, r = nseg;  // the segment: last l with scum[l] <= it
+        while (r - l > 1) {
+            const int m = (l + r) >> 1;
+            if (scum[m] <= it) l = m; else r = m;
+        }
         const int lo = (int)(c.seg_soff[sg0 + l] - s0), cnt = segv[l];
-        if (cnt <= 0) continue;
+        const int a = sA0[l] + (it - scum[l]);
         const T pf = T(c.seg_pf[sg0 + l]);
         const int64_t row = c.kde_mode == CHIMERA_KDE_MANY_1D ? (int64_t)(sg0 + l) : (int64_t)ev;
-        const T smin = zs[lo] - T(KDE_MARGIN) * bt, smax = zs[lo + cnt - 1] + T(KDE_MARGIN) * bt;
-        const int alo = max(0, (int)ceil(smin / dz)), ahi = min(nz - 1, (int)floor(smax / dz));
-        for (int a = alo + tid; a <= ahi; a += ADJ_THREADS) {
-            const T za = T(a) * dz;
-            // samples whose window covers a: z in [za - KW b, za + KW b]
-            int jl = lo, jr = lo + cnt;
-            while (jl < jr) {
-                int m = (jl + jr) >> 1;
-                if (zs[m] < za - KW * bt) jl = m + 1; else jr = m;
-            }
-            // the samples whose window holds a: |z - za| <= KW b
-            T K = T(0);
-            for (int j = jl; j < lo + cnt && zs[j] <= za + KW * bt; j++) {
-                const T u = (za - zs[j]) * ib;
-                K += ws[j] * (F64 ? T(exp(-0.5 * double(u * u))) : T(__expf(-0.5f * float(u * u))));
-            }
-            if (K == T(0)) continue;
-            const T FK = pf * Fw(a) * K;
-            const T M = FK * Gv(row, a);
-            if (F64) {
-                const double *Qa = q.Q + ((size_t)h * nz + a) * 7;
-                for (int k = 0; k < 7; k++) C8[k] += M * T(Qa[k]);
-            } else {
-                const float4 *Qa = reinterpret_cast<const float4 *>(q.Q32 + ((size_t)h * nz + a) * 8);
-                const float4 qa = Qa[0], qb = Qa[1];
-                C8[0] += M * qa.x; C8[1] += M * qa.y; C8[2] += M * qa.z; C8[3] += M * qa.w;
-                C8[4] += M * qb.x; C8[5] += M * qb.y; C8[6] += M * qb.z;
-            }
-            C8[7] += FK * T(q.dprof[h][row * nz + a]);
+        const T za = T(a) * dz;
+        // samples whose window covers a: |z - za| <= KW b
+        int jl = lo, jr = lo + cnt;
+        while (jl < jr) {
+            const int m = (jl + jr) >> 1;
+            if (zs[m] < za - KW * bt) jl = m + 1; else jr = m;
         }
+        T K = T(0);
+        for (int j = jl; j < lo + cnt && zs[j] <= za + KW * bt; j++) {
+            const T u = (za - zs[j]) * ib;
+            K += ws[j] * (F64 ? T(exp(-0.5 * double(u * u))) : T(__expf(-0.5f * float(u * u))));
+        }
+        if (K == T(0)) continue;
+        const T FK = pf * Fw(a) * K;
+        const T M = FK * Gv(row, a);
+        if (F64) {
+            const double *Qa = q.Q + ((size_t)h * nz + a) * 7;
+            for (int k = 0; k < 7; k++) C8[k] += M * T(Qa[k]);
+        } else {
+            const float4 *Qa = reinterpret_cast<const float4 *>(q.Q32 + ((size_t)h * nz + a) * 8);
+            const float4 qa = Qa[0], qb = Qa[1];
+            C8[0] += M * qa.x; C8[1] += M * qa.y; C8[2] += M * qa.z; C8[3] += M * qa.w;
+            C8[4] += M * qb.x; C8[5] += M * qb.y; C8[6] += M * qb.z;
+        }
+        C8[7] += FK * T(q.dprof[h][row * nz + a]);
     }
     // ---- block sums (double) and the 12 derivatives
     double v[28];
@@ -628,6 +673,411 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
             for (int k = 0; k < 3; k++) g[9 + k] = v[19 + k] / I;
         }
         for (int k = 0; k < 12; k++) out[k] = g[k];
+    }
+}
+
+// ---- MIXED event adjoint on the factorised Gaussian ----
+//
+// The per-sample sums of the adjoint are sums over grid offsets of the same
+// Gaussian as the forward kernel's: with an origin t_o per run of samples,
+// u = (z_j - z_o)/(sqrt2 b), ds = dz/(sqrt2 b), B = exp(2 u ds),
+//   e_ja = exp(-u^2) B^tau C_tau,  tau = a - t_o,  C_tau = exp(-(ds tau)^2),
+//   u_ja = (z_a - z_j)/b = sqrt2 (ds tau - u),
+// so that with P_X(B) = sum_tau X_tau C_tau H(a) B^tau
+//   S0 = e^{-u^2} P_1,  S1 = sqrt2 e^{-u^2} (ds P_tau - u P_1),
+//   S2 = 2 e^{-u^2} (ds^2 P_tau2 - 2 ds u P_tau + u^2 P_1),
+// and the grid term, sum_a M(a) Q_k(a) = sum_j pf w_j sum_a e_ja H(a) Q_k(a),
+// is the per-sample sum with X = Q_k (likewise for w'_a F dG/dOm).  The
+// eleven polynomials are evaluated together by Horner's rule (one FMA per
+// polynomial, sample and grid point) from a table of 12 floats per offset,
+// staged by the warp in chunks of AM_CH offsets per side.  Runs hold up to
+// 64 neighbouring samples of one group (two per lane) whose spread is at
+// most 16 b; beyond 8 b the table is scaled by e^20 (undone in e^{-u^2}),
+// which keeps every coefficient and intermediate in the normal float range.
+// Kernels narrower than ~0.7 grid steps (ds > 0.5) use direct exponentials.
+// The sample's own derivative terms (dz/dtheta, d ln w/dtheta and Scott's
+// rule) are taken by the lane that holds it, right after its sums.
+constexpr int AM_THREADS = ADJ_THREADS, AM_WARPS = AM_THREADS / 32;
+constexpr int AM_CH = 64;
+constexpr int AM_ROWS = 2 * AM_CH + 1;  // per warp: +tau rows, -tau rows, tau = 0
+constexpr int AM_RED = 32;              // floats per warp in the block sums
+
+// Fixed-order FP32 block sum of NV values (NV <= AM_RED); every thread gets
+// the totals.  FP32 keeps the reduction off B300's narrow FP64 pipe.
+template <int NV>
+__device__ void bsumf(float (&v)[NV], float *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        float s = v[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[wid * NV + k] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        float s = 0.f;
+        for (int w = 0; w < AM_WARPS; w++) s += red[w * NV + threadIdx.x];
+        red[AM_WARPS * NV + threadIdx.x] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = red[AM_WARPS * NV + k];
+    __syncthreads();
+}
+
+// Per-block constants of the sample terms, kept in shared memory (the
+// Horner chains need the registers).
+struct AdjMixConst {
+    MassDer<float> md;
+    float cw0, cw1, cw2, cu, Mw, Mu, varw, ib;
+    int rule;
+};
+
+struct AdjMixLayout {
+    int ns_pad, nz_pad, seg_pad;
+    __host__ __device__ AdjMixLayout(int max_ns, int nz, int max_seg)
+        : ns_pad((max_ns + 3) & ~3), nz_pad((nz + 3) & ~3), seg_pad((max_seg + 4) & ~3) {}
+    // float4: table rows; float: block sums, zs, ws, F', segment
+    // prefactors; int: segment valid counts, starts and KDE supports
+    __host__ __device__ size_t bytes() const {
+        return sizeof(float4) * 3 * (size_t)AM_WARPS * AM_ROWS +
+               sizeof(float) * ((AM_WARPS + 1) * AM_RED + 2 * (size_t)ns_pad + nz_pad + seg_pad) +
+               sizeof(int) * 4 * (size_t)seg_pad;
+    }
+};
+
+__global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c, CallPtrs p, AdjPtrs q, int H) {
+    extern __shared__ float4 am4[];
+    __shared__ AdjMixConst kc;
+    const AdjMixLayout L(c.max_ns, c.n_z, c.max_seg);
+    float4 *rows = am4;
+    float *red = reinterpret_cast<float *>(rows + 3 * AM_WARPS * AM_ROWS);
+    float *zs = red + (AM_WARPS + 1) * AM_RED;
+    float *ws = zs + L.ns_pad;
+    float *Fs = ws + L.ns_pad;  // F' = trapezoid weight x F / F_scale
+    float *segpf = Fs + L.nz_pad;
+    int *segv = reinterpret_cast<int *>(segpf + L.seg_pad);
+    int *seglo = segv + L.seg_pad;
+    int *segA0 = seglo + L.seg_pad;
+    int *segA1 = segA0 + L.seg_pad;
+
+    const int h = blockIdx.x % H;
+    const int4 ei = __ldg(c.ev_info + 2 * (blockIdx.x / H));      // (ev, s0, ns, zoff)
+    const int4 ej = __ldg(c.ev_info + 2 * (blockIdx.x / H) + 1);  // (g0, ngroups, sg0, nseg)
+    const int ev = ei.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const HP &hp = p.hp[h];
+    const HPd &hd = q.hpd[h];
+    double *out = q.dlnI + ((size_t)h * c.n_events + ev) * 12;
+    if (hp.status & (CHIMERA_PT_OUT_OF_SUPPORT | CHIMERA_PT_NONMONOTONE)) {
+        if (tid < 12) out[tid] = 0.0;
+        return;
+    }
+    const int64_t s0 = ei.y;
+    const int ns = ei.z;
+    const int g0 = ej.x, ngroups = ej.y, sg0 = ej.z, nseg = ej.w;
+    const int nz = c.n_z;
+    const MixParams mp = mix_params(hp);
+    const float4 *inv = p.inv32 + (size_t)h * NU;
+    for (int a = tid; a < nz; a += AM_THREADS)
+        Fs[a] = ((a == 0 || a == nz - 1) ? 0.5f : 1.f) * p.F32[(size_t)h * nz + a];
+    for (int k = tid; k <= nseg; k += AM_THREADS) {
+        seglo[k] = (int)(c.seg_soff[sg0 + k] - s0);
+        if (k < nseg) segpf[k] = (float)c.seg_pf[sg0 + k];
+    }
+    // ---- z_j, w_j exactly as the mixed reweighting kernel
+    for (int j = tid; j < ns; j += AM_THREADS) {
+        float z = CUDART_INF_F, w = 0.f;
+        const float4 sv = __ldg(c.s32 + s0 + j);
+        const int k = __float_as_int(sv.x);
+        if ((k < mp.kv) || (k == mp.kv && sv.y <= mp.fv)) {
+            const float zz = chimd::hermite4(__ldg(inv + k), sv.y);
+            if (zz < CUDART_INF_F) {
+                z = zz;
+                const float lz = __log2f(1.f + zz);
+                w = mass_weight32(mp, sv.z - lz, sv.w - lz);
+            }
+        }
+        zs[j] = z;
+        ws[j] = w;
+    }
+    __syncthreads();
+    // ---- moments (two-pass) for the derivative of Scott's rule
+    float m5[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // W1, Wz, W2, n_valid, Sz
+    for (int j = tid; j < ns; j += AM_THREADS)
+        if (zs[j] < CUDART_INF_F) {
+            const float z = zs[j], w = ws[j];
+            m5[0] += w; m5[1] += w * z; m5[2] += w * w; m5[3] += 1.f; m5[4] += z;
+        }
+    bsumf<5>(m5, red);
+    const float W1 = m5[0], W2 = m5[2], nv = m5[3];
+    const float Mw = W1 > 0.f ? m5[1] / W1 : 0.f, Mu = nv > 0.f ? m5[4] / nv : 0.f;
+    float m2v[2] = {0.f, 0.f};
+    for (int j = tid; j < ns; j += AM_THREADS)
+        if (zs[j] < CUDART_INF_F) {
+            const float z = zs[j], w = ws[j];
+            m2v[0] += w * (z - Mw) * (z - Mw);
+            m2v[1] += (z - Mu) * (z - Mu);
+        }
+    bsumf<2>(m2v, red);
+    const float varw = W1 > 0.f ? m2v[0] / W1 : 0.f, neffw = W1 > 0.f ? W1 * W1 / W2 : 0.f;
+    const float varu = nv > 0.f ? m2v[1] / nv : 0.f;
+    // 0 weighted, 1 unweighted, 2 grid spacing; the bandwidth itself is the
+    // reweighting kernel's FP32 one
+    const int rule = (W1 > 0.f && neffw >= 2.f && varw > 0.f) ? 0 : ((nv >= 2.f && varu > 0.f) ? 1 : 2);
+    const float b = (float)p.bw[(size_t)h * c.n_events + ev];
+    const float dz = c.dz32, inv_dz = 1.f / dz, ib = 1.f / b;
+    const float inv_s2b = 0.70710678f / b, ds = dz * inv_s2b, halfk = KW32 * b;
+    // ---- segment valid counts and KDE supports (as the forward kernel)
+    for (int k = tid; k < nseg; k += AM_THREADS) {
+        const int lo = seglo[k], hi = seglo[k + 1];
+        int l = lo, r = hi;
+        while (l < r) {
+            const int m = (l + r) >> 1;
+            if (zs[m] < CUDART_INF_F) l = m + 1; else r = m;
+        }
+        segv[k] = l - lo;
+        if (l > lo) {
+            segA0[k] = max(0, (int)ceilf((zs[lo] - (float)KDE_MARGIN * b) * inv_dz));
+            segA1[k] = min(nz - 1, (int)floorf((zs[l - 1] + (float)KDE_MARGIN * b) * inv_dz));
+        } else {
+            segA0[k] = 0;
+            segA1[k] = -1;
+        }
+    }
+    __syncthreads();
+
+    if (tid == 0) {
+        kc.md = mass_der32(hp, hd);
+        kc.cw0 = rule == 0 ? 1.f / (W1 * varw) : 0.f;
+        kc.cw1 = W1 > 0.f ? 2.f / W1 : 0.f;
+        kc.cw2 = W2 > 0.f ? 2.f / W2 : 0.f;
+        kc.cu = nv > 0.f && varu > 0.f ? 1.f / (nv * varu) : 0.f;
+        kc.Mw = Mw;
+        kc.Mu = Mu;
+        kc.varw = varw;
+        kc.ib = ib;
+        kc.rule = rule;
+    }
+    __syncthreads();
+    const float4 *dzn = q.dznode32 + (size_t)h * (NU + 1);
+    float A9[9], B4[4], C8[8], db9[9], S2t = 0.f, I0 = 0.f;
+    for (int k = 0; k < 9; k++) { A9[k] = 0.f; db9[k] = 0.f; }
+    for (int k = 0; k < 4; k++) B4[k] = 0.f;
+    for (int k = 0; k < 8; k++) C8[k] = 0.f;
+    // one valid sample with its sums (S0, S1, S2 and the grid-term sums X[7]
+    // over Q_k, X[7] over dG/dOm), H without the segment prefactor
+    auto sample_terms = [&](int j, float pf, float S0, float S1, float S2, const float (&X)[8]) {
+        const float z = zs[j], w = ws[j], a1 = 1.f + z;
+        const float4 sv = __ldg(c.s32 + s0 + j);
+        float dd[4];
+        {
+            const int kk = __float_as_int(sv.x);
+            const float f = sv.y;
+            const float4 n0 = __ldg(dzn + kk), n1 = __ldg(dzn + kk + 1);
+            dd[0] = n0.x + f * (n1.x - n0.x);
+            dd[1] = n0.y + f * (n1.y - n0.y);
+            dd[2] = n0.z + f * (n1.z - n0.z);
+            dd[3] = n0.w + f * (n1.w - n0.w);
+        }
+        float dlw[9];
+        {
+            const float lz = __log2f(a1);
+            float e5[5], ez;
+            dlnpm_t<float>(kc.md, ex2(sv.z - lz), ex2(sv.w - lz), a1, e5, &ez);
+            for (int k = 0; k < 4; k++) dlw[k] = ez * dd[k];
+            for (int k = 0; k < 5; k++) dlw[4 + k] = e5[k];
+        }
+        if (kc.rule == 0) {
+            const float zm = z - kc.Mw;
+            const float cw = 0.5f * (zm * zm - kc.varw) * kc.cw0 - 0.2f * (kc.cw1 - w * kc.cw2);
+            const float cz = w * zm * kc.cw0;
+            for (int k = 0; k < 9; k++) db9[k] += cw * w * dlw[k] + (k < 4 ? cz * dd[k] : 0.f);
+        } else if (kc.rule == 1) {
+            const float cz = (z - kc.Mu) * kc.cu;
+            for (int k = 0; k < 4; k++) db9[k] += cz * dd[k];
+        }
+        if (w == 0.f) return;
+        const float pw = pf * w, pwb = pw * S1 * kc.ib;
+        I0 += pw * S0;
+        S2t += pw * S2;
+        for (int k = 0; k < 9; k++) A9[k] += pw * S0 * dlw[k];
+        for (int k = 0; k < 4; k++) B4[k] += pwb * dd[k];
+        for (int k = 0; k < 8; k++) C8[k] += pw * X[k];
+    };
+
+    float4 *tw = rows + 3 * wid * AM_ROWS;  // this warp's table
+    const float *prof = reinterpret_cast<const float *>(p.prof[h]);
+    const float *dprof = reinterpret_cast<const float *>(q.dprof[h]);  // FP32 on this path
+    const float4 *Q4 = reinterpret_cast<const float4 *>(q.Q32 + (size_t)h * nz * 8);
+    // groups in a fixed warp assignment (the sums do not depend on timing)
+    for (int g = wid; g < ngroups; g += AM_WARPS) {
+        const int4 gi = __ldg(c.groups + g0 + g);
+        const int sk = gi.z, lo = gi.x;
+        const int cnt = min(gi.y, segv[sk] - (lo - seglo[sk]));  // valid samples only
+        if (cnt <= 0) continue;
+        const float pf = segpf[sk];
+        const int64_t row = c.kde_mode == CHIMERA_KDE_MANY_1D ? (int64_t)(sg0 + sk) : (int64_t)ev;
+        const float *G = prof + row * nz;
+        const float *dG = dprof + row * nz;
+        const int s_lo = segA0[sk], s_hi = segA1[sk];
+        if (ds > 0.5f) {
+            // narrow kernel: direct exponentials on each sample's window
+            for (int jj = lane; jj < cnt; jj += 32) {
+                const int j = lo + jj;
+                const float z = zs[j];
+                float S0 = 0.f, S1 = 0.f, S2 = 0.f, X[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (ws[j] != 0.f) {
+                    const int a0 = max(s_lo, (int)ceilf((z - halfk) * inv_dz));
+                    const int a1 = min(s_hi, (int)floorf((z + halfk) * inv_dz));
+                    for (int a = a0; a <= a1; a++) {
+                        const float x = (a * dz - z) * inv_s2b;
+                        const float e = __expf(-x * x) * Fs[a];
+                        const float eh = e * __ldg(G + a), U = 1.41421356f * x;
+                        const float4 qa = __ldg(Q4 + 2 * a), qb = __ldg(Q4 + 2 * a + 1);
+                        S0 += eh;
+                        S1 += eh * U;
+                        S2 += eh * U * U;
+                        X[0] += eh * qa.x; X[1] += eh * qa.y; X[2] += eh * qa.z; X[3] += eh * qa.w;
+                        X[4] += eh * qb.x; X[5] += eh * qb.y; X[6] += eh * qb.z;
+                        X[7] += e * __ldg(dG + a);
+                    }
+                }
+                sample_terms(j, pf, S0, S1, S2, X);
+            }
+            continue;
+        }
+        // one run of n samples from st on, R per lane (n <= 32 R)
+        auto run = [&](auto Rc, int st, int n) {
+            constexpr int R = decltype(Rc)::value;
+            const float zlo = zs[lo + st], zhi = zs[lo + st + n - 1];
+            const float fA0 = floorf((zlo - halfk) * inv_dz), fA1 = ceilf((zhi + halfk) * inv_dz);
+            const int A0 = fA0 < (float)s_lo ? s_lo : (int)fA0;
+            const int A1 = fA1 > (float)s_hi ? s_hi : (int)fA1;
+            const int t_o = (int)rintf(0.5f * (zlo + zhi) * inv_dz);
+            const int T = max(0, max(A1 - t_o, t_o - A0));
+            const float lnscale = zhi - zlo > 8.f * b ? 20.f : 0.f;
+            const float zo = t_o * dz;
+            float u[R], Bf[R], Bb[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int idx = lane + 32 * r;
+                u[r] = idx < n ? (zs[lo + st + idx] - zo) * inv_s2b : 0.f;
+                Bf[r] = __expf(2.f * u[r] * ds);
+                Bb[r] = __expf(-2.f * u[r] * ds);
+            }
+            float af[R][11], ab[R][11];
+#pragma unroll
+            for (int r = 0; r < R; r++)
+#pragma unroll
+                for (int k = 0; k < 11; k++) { af[r][k] = 0.f; ab[r][k] = 0.f; }
+            // Horner from the outermost offsets in: chunks of AM_CH offsets per
+            // side (+m rows at [0, AM_CH), -m rows at [AM_CH, 2 AM_CH)); the
+            // last chunk also stages tau = 0 (row 2 AM_CH), which closes the
+            // forward chain
+            for (int mhi = T;; mhi -= AM_CH) {
+                const int mlo = max(1, mhi - AM_CH + 1), nr = max(0, mhi - mlo + 1);
+                const bool last = mlo <= 1;
+                const int nst = 2 * nr + (last ? 1 : 0);
+                __syncwarp();
+                for (int i = lane; i < nst; i += 32) {
+                    int tau, slot;
+                    if (i < nr) { tau = mhi - i; slot = i; }
+                    else if (i < 2 * nr) { tau = -(mhi - (i - nr)); slot = AM_CH + (i - nr); }
+                    else { tau = 0; slot = 2 * AM_CH; }
+                    const int a = t_o + tau;
+                    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+                    if (a >= A0 && a <= A1) {
+                        const float x = ds * (float)tau;
+                        const float cf = __expf(lnscale - x * x) * Fs[a];
+                        const float hh = cf * __ldg(G + a);
+                        const float4 qa = __ldg(Q4 + 2 * a), qb = __ldg(Q4 + 2 * a + 1);
+                        const float tt = (float)tau;
+                        r0 = make_float4(hh, tt * hh, tt * tt * hh, hh * qa.x);
+                        r1 = make_float4(hh * qa.y, hh * qa.z, hh * qa.w, hh * qb.x);
+                        r2 = make_float4(hh * qb.y, hh * qb.z, cf * __ldg(dG + a), 0.f);
+                    }
+                    tw[3 * slot] = r0;
+                    tw[3 * slot + 1] = r1;
+                    tw[3 * slot + 2] = r2;
+                }
+                __syncwarp();
+#pragma unroll 2
+                for (int i = 0; i < nr; i++) {
+                    const float4 f0 = tw[3 * i], f1 = tw[3 * i + 1], f2 = tw[3 * i + 2];
+                    const float4 e0 = tw[3 * (AM_CH + i)], e1 = tw[3 * (AM_CH + i) + 1], e2 = tw[3 * (AM_CH + i) + 2];
+                    const float cf_[11] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w, f2.x, f2.y, f2.z};
+                    const float cb_[11] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w, e2.x, e2.y, e2.z};
+#pragma unroll
+                    for (int r = 0; r < R; r++)
+#pragma unroll
+                        for (int k = 0; k < 11; k++) {
+                            af[r][k] = fmaf(af[r][k], Bf[r], cf_[k]);
+                            ab[r][k] = fmaf(ab[r][k], Bb[r], cb_[k]);
+                        }
+                }
+                if (last) {
+                    const float4 f0 = tw[6 * AM_CH], f1 = tw[6 * AM_CH + 1], f2 = tw[6 * AM_CH + 2];
+                    const float c0_[11] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w, f2.x, f2.y, f2.z};
+#pragma unroll
+                    for (int r = 0; r < R; r++)
+#pragma unroll
+                        for (int k = 0; k < 11; k++) af[r][k] = fmaf(af[r][k], Bf[r], c0_[k]);
+                    break;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int idx = lane + 32 * r;
+                if (idx >= n) continue;
+                const float uu = u[r], E = __expf(-uu * uu - lnscale);
+                float P[11];
+#pragma unroll
+                for (int k = 0; k < 11; k++) P[k] = E * fmaf(Bb[r], ab[r][k], af[r][k]);
+                const float S1 = 1.41421356f * (ds * P[1] - uu * P[0]);
+                const float S2 = 2.f * (ds * ds * P[2] - 2.f * ds * uu * P[1] + uu * uu * P[0]);
+                const float X[8] = {P[3], P[4], P[5], P[6], P[7], P[8], P[9], P[10]};
+                sample_terms(lo + st + idx, pf, P[0], S1, S2, X);
+            }
+        };
+        for (int st = 0; st < cnt;) {
+            // a run: the longest prefix of up to 64 samples spanning <= 16 b
+            int n;
+            {
+                const float zf = zs[lo + st], lim = 16.f * b;
+                const bool p0 = st + lane < cnt && zs[lo + st + lane] - zf <= lim;
+                const bool p1 = st + 32 + lane < cnt && zs[lo + st + 32 + lane] - zf <= lim;
+                const unsigned b0 = __ballot_sync(0xffffffffu, p0), b1 = __ballot_sync(0xffffffffu, p1);
+                n = b0 != 0xffffffffu ? __ffs(~b0) - 1 : 32 + (b1 != 0xffffffffu ? __ffs(~b1) - 1 : 32);
+            }
+            if (n <= 32) run(std::integral_constant<int, 1>{}, st, n);
+            else run(std::integral_constant<int, 2>{}, st, n);
+            st += n;
+        }
+    }
+    // ---- block sums (FP32, fixed order) and the 12 derivatives
+    float v[32];
+    for (int k = 0; k < 9; k++) v[k] = A9[k];
+    for (int k = 0; k < 4; k++) v[9 + k] = B4[k];
+    v[13] = S2t;
+    v[14] = I0;
+    for (int k = 0; k < 8; k++) v[15 + k] = C8[k];
+    for (int k = 0; k < 9; k++) v[23 + k] = db9[k];  // d ln b / dtheta
+    bsumf<32>(v, red);
+    if (tid == 0) {
+        const double I = v[14];
+        const float *vb = v + 23;
+        double gr[12];
+        for (int k = 0; k < 12; k++) gr[k] = 0.0;
+        if (I > 0.0) {
+            const double iI = 1.0 / I;
+            for (int k = 0; k < 4; k++)
+                gr[k] = ((double)v[k] + v[9 + k] + (double)v[13] * vb[k] + v[15 + k]) * iI - vb[k];
+            gr[1] += v[22] * iI;
+            for (int k = 0; k < 5; k++) gr[4 + k] = ((double)v[4 + k] + (double)v[13] * vb[4 + k]) * iI - vb[4 + k];
+            for (int k = 0; k < 3; k++) gr[9 + k] = v[19 + k] * iI;
+        }
+        for (int k = 0; k < 12; k++) out[k] = gr[k];
     }
 }
 
@@ -880,9 +1330,9 @@ __global__ void k_dprofile_sum(DevCatalog c, const double *G, double *outh) {
 }  // namespace
 
 size_t adjoint_event_smem(const DevCatalog &c, bool fp64) {
-    return (fp64 ? sizeof(double) : sizeof(float)) * 2 * (size_t)c.max_ns +
-           sizeof(int) * (size_t)((c.max_seg + 2) & ~1) + sizeof(double) * (ADJ_THREADS / 32 + 1) * 28 +
-           (fp64 ? 0 : sizeof(float) * (size_t)c.n_z);
+    if (!fp64) return AdjMixLayout(c.max_ns, c.n_z, c.max_seg).bytes();
+    return sizeof(double) * 2 * (size_t)c.max_ns + sizeof(int) * 3 * (size_t)((c.max_seg + 2) & ~1) +
+           sizeof(double) * (ADJ_THREADS / 32 + 1) * 28;
 }
 
 void launch_adjoint(const DevCatalog &c, const CallPtrs &p, const AdjPtrs &q, int H, bool fp64, cudaStream_t st) {
@@ -894,8 +1344,8 @@ void launch_adjoint(const DevCatalog &c, const CallPtrs &p, const AdjPtrs &q, in
         if (nb) k_event_adj<true><<<nb, ADJ_THREADS, smem, st>>>(c, p, q, H);
         if (p.n_chunk) k_select_adj<true><<<dim3(p.n_chunk, H), ADJ_THREADS, 0, st>>>(c, p, q, H);
     } else {
-        cudaFuncSetAttribute(k_event_adj<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (nb) k_event_adj<false><<<nb, ADJ_THREADS, smem, st>>>(c, p, q, H);
+        cudaFuncSetAttribute(k_event_adj_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (nb) k_event_adj_mixed<<<nb, AM_THREADS, smem, st>>>(c, p, q, H);
         if (p.n_chunk) k_select_adj<false><<<dim3(p.n_chunk, H), ADJ_THREADS, 0, st>>>(c, p, q, H);
     }
     k_combine_adj<<<H, ADJ_THREADS, 0, st>>>(c, p, q, H);
@@ -959,7 +1409,15 @@ int fwdO_table(Ctx &ctx, double Om, cudaStream_t st, const double **out) {
     return CHIMERA_OK;
 }
 
-// dG/dOm profile for (Om, precision), cached with the forward profiles.
+// FP32 copy of a profile (the mixed adjoint's tables read FP32).
+__global__ void k_to_f32(const double *src, float *dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
+// dG/dOm profile for (Om, precision), cached with the forward profiles.  The
+// mixed entry holds the FP64 rows followed by their FP32 copy, and hands out
+// the copy.
 int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double Om, bool f64, const double *fwd,
              const double *fwdO, const double **out) {
     const int kind = f64 ? 2 : 3;
@@ -968,8 +1426,9 @@ int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double O
     const DevCatalog &c = cat.d;
     if (it == cat.prof.end()) {
         ProfEntry e;
-        e.bytes = sizeof(double) * (size_t)c.n_pix * c.n_z;
-        const size_t hb = c.kde_mode == CHIMERA_KDE_SINGLE_1D ? sizeof(double) * (size_t)c.n_events * c.n_z : 0;
+        const size_t per = f64 ? sizeof(double) : sizeof(double) + sizeof(float);
+        e.bytes = per * (size_t)c.n_pix * c.n_z;
+        const size_t hb = c.kde_mode == CHIMERA_KDE_SINGLE_1D ? per * (size_t)c.n_events * c.n_z : 0;
         evict_profiles(ctx, cat, e.bytes + hb);
         RC(dev_alloc(ctx, &e.G, e.bytes));
         if (hb) {
@@ -991,6 +1450,12 @@ int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double O
             else k_profile_dOm<false><<<(unsigned)c.n_pix, ADJ_THREADS, 0, ws.st>>>(c, dv, dvO, invZ, ZO, (double *)e.G);
         }
         if (hb) k_dprofile_sum<<<c.n_events, 256, 0, ws.st>>>(c, (const double *)e.G, (double *)e.Gh);
+        if (!f64) {
+            const int64_t n = (int64_t)(hb ? c.n_events : c.n_pix) * c.n_z;
+            double *src = reinterpret_cast<double *>(hb ? e.Gh : e.G);
+            if (n > 0) k_to_f32<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, ws.st>>>(
+                src, reinterpret_cast<float *>(src + n), n);
+        }
         CK(cudaGetLastError());
         CK(cudaEventRecord(e.ready, ws.st));
         it = cat.prof.emplace(key, e).first;
@@ -998,7 +1463,10 @@ int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double O
         CK(cudaStreamWaitEvent(ws.st, it->second.ready, 0));
     }
     it->second.last_use = ctx.tick;
-    *out = reinterpret_cast<const double *>(c.kde_mode == CHIMERA_KDE_SINGLE_1D ? it->second.Gh : it->second.G);
+    const bool single = c.kde_mode == CHIMERA_KDE_SINGLE_1D;
+    const double *g = reinterpret_cast<const double *>(single ? it->second.Gh : it->second.G);
+    if (!f64) g += (int64_t)(single ? c.n_events : c.n_pix) * c.n_z;  // the FP32 copy (pointer kept as double*)
+    *out = g;
     return CHIMERA_OK;
 }
 

@@ -254,9 +254,11 @@ __device__ MassDer<float> mass_der32(const HP &hp, const HPd &hd) {
 
 __device__ double std_normal_pdf(double x) { return 0.39894228040143267794 * exp(-0.5 * x * x); }
 
-// ---- per-hyperpoint derivative tables ----
+// ---- per-hyperpoint derivative tables (blockIdx.y splits the nodes and
+// grid points of one hyperpoint over several blocks) ----
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_tables(DevCatalog c, CallPtrs p, AdjPtrs q) {
-    const int h = blockIdx.x, t = threadIdx.x;
+    const int h = blockIdx.x;
+    const int t = blockIdx.y * ADJ_THREADS + threadIdx.x, nt = gridDim.y * ADJ_THREADS;
     const HP &hp = p.hp[h];
     const double *th = hp.th;
     const double *fwd = p.fwd[h], *fwdO = q.fwdO[h];
@@ -297,7 +299,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_tables(DevCatalog c, CallPt
     }
     // dz/dtheta at the inverse-table nodes
     const double2 *nd = p.inv64 + (size_t)h * (NU + 1);
-    for (int k = t; k <= NU; k += ADJ_THREADS) {
+    for (int k = t; k <= NU; k += nt) {
         double z = nd[k].x;
         double *o = q.dznode + ((size_t)h * (NU + 1) + k) * 4;
         if (k == 0 || !isfinite(z)) {
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_tables(DevCatalog c, CallPt
         q.dznode32[(size_t)h * (NU + 1) + k] = make_float4((float)r.dz[0], (float)r.dz[1], (float)r.dz[2], (float)r.dz[3]);
     }
     // d ln F / dtheta on the grid, F = psi / ((1+z)^3 J)
-    for (int a = t; a < c.n_z; a += ADJ_THREADS) {
+    for (int a = t; a < c.n_z; a += nt) {
         double z = a * c.dz;
         ZDer r = zder(z, th, fwd, fwdO, 0.0);
         double g3[3], dz;
@@ -687,19 +689,25 @@ __global__ void __launch_bounds__(ADJ_THREADS, F64 ? 1 : 3) k_event_adj(DevCatal
 //   S0 = e^{-u^2} P_1,  S1 = sqrt2 e^{-u^2} (ds P_tau - u P_1),
 //   S2 = 2 e^{-u^2} (ds^2 P_tau2 - 2 ds u P_tau + u^2 P_1),
 // and the grid term, sum_a M(a) Q_k(a) = sum_j pf w_j sum_a e_ja H(a) Q_k(a),
-// is the per-sample sum with X = Q_k (likewise for w'_a F dG/dOm).  The
-// eleven polynomials are evaluated together by Horner's rule (one FMA per
-// polynomial, sample and grid point) from a table of 12 floats per offset,
-// staged by the warp in chunks of AM_CH offsets per side.  Runs hold up to
-// 64 neighbouring samples of one group (two per lane) whose spread is at
-// most 16 b; beyond 8 b the table is scaled by e^20 (undone in e^{-u^2}),
-// which keeps every coefficient and intermediate in the normal float range.
-// Kernels narrower than ~0.7 grid steps (ds > 0.5) use direct exponentials.
-// The sample's own derivative terms (dz/dtheta, d ln w/dtheta and Scott's
-// rule) are taken by the lane that holds it, right after its sums.
+// is the per-sample sum with X = Q_k (likewise for w'_a F dG/dOm).  Q for
+// H0 is 1/H0 at every z (J is proportional to c/H0), so its sum is S0/H0;
+// the other ten polynomials are evaluated together by Horner's rule (one FMA
+// per polynomial, sample and grid point) from a table of 10 floats per
+// offset, staged by the warp in chunks of AM_CH offsets per side, the +m and
+// -m rows side by side.  Runs hold up to 64 neighbouring samples of one
+// group (one or two per lane) whose spread is at most 16 b; beyond 8 b the
+// table is scaled by e^20 (undone in e^{-u^2}), which keeps every
+// coefficient and intermediate in the normal float range.  Kernels narrower
+// than ~0.7 grid steps (ds > 0.5) use direct exponentials.  Each lane then
+// takes its samples' own derivative terms (dz/dtheta, d ln w/dtheta and
+// Scott's rule) from the run's sums, left in the warp's table space.
 constexpr int AM_THREADS = ADJ_THREADS, AM_WARPS = AM_THREADS / 32;
 constexpr int AM_CH = 64;
-constexpr int AM_ROWS = 2 * AM_CH + 1;  // per warp: +tau rows, -tau rows, tau = 0
+constexpr int AM_NP = 10;              // polynomials (table floats per offset)
+constexpr int AM_SLOT = 2 * AM_NP / 4;  // float4 per slot: the +m and -m rows
+constexpr int AM_SLOTS = AM_CH + 1;     // per warp; slot AM_CH holds tau = 0
+constexpr int AM_RUN = 64;              // samples per run
+static_assert(AM_NP * AM_RUN <= 4 * AM_SLOT * AM_SLOTS, "run sums fit in the table space");
 constexpr int AM_RED = 32;              // floats per warp in the block sums
 
 // Fixed-order FP32 block sum of NV values (NV <= AM_RED); every thread gets
@@ -740,7 +748,7 @@ struct AdjMixLayout {
     // float4: table rows; float: block sums, zs, ws, F', segment
     // prefactors; int: segment valid counts, starts and KDE supports
     __host__ __device__ size_t bytes() const {
-        return sizeof(float4) * 3 * (size_t)AM_WARPS * AM_ROWS +
+        return sizeof(float4) * AM_SLOT * (size_t)AM_WARPS * AM_SLOTS +
                sizeof(float) * ((AM_WARPS + 1) * AM_RED + 2 * (size_t)ns_pad + nz_pad + seg_pad) +
                sizeof(int) * 4 * (size_t)seg_pad;
     }
@@ -751,7 +759,7 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
     __shared__ AdjMixConst kc;
     const AdjMixLayout L(c.max_ns, c.n_z, c.max_seg);
     float4 *rows = am4;
-    float *red = reinterpret_cast<float *>(rows + 3 * AM_WARPS * AM_ROWS);
+    float *red = reinterpret_cast<float *>(rows + AM_SLOT * AM_WARPS * AM_SLOTS);
     float *zs = red + (AM_WARPS + 1) * AM_RED;
     float *ws = zs + L.ns_pad;
     float *Fs = ws + L.ns_pad;  // F' = trapezoid weight x F / F_scale
@@ -865,9 +873,11 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
     for (int k = 0; k < 9; k++) { A9[k] = 0.f; db9[k] = 0.f; }
     for (int k = 0; k < 4; k++) B4[k] = 0.f;
     for (int k = 0; k < 8; k++) C8[k] = 0.f;
-    // one valid sample with its sums (S0, S1, S2 and the grid-term sums X[7]
-    // over Q_k, X[7] over dG/dOm), H without the segment prefactor
-    auto sample_terms = [&](int j, float pf, float S0, float S1, float S2, const float (&X)[8]) {
+    // one valid sample with its sums Sv = (S0, S1, S2, sums over Q_1 .. Q_6,
+    // sum over dG/dOm), H without the segment prefactor
+    const float iH0 = 1.f / hp.h0_32;
+    auto sample_terms = [&](int j, float pf, const float (&Sv)[AM_NP]) {
+        const float S0 = Sv[0], S1 = Sv[1], S2 = Sv[2];
         const float z = zs[j], w = ws[j], a1 = 1.f + z;
         const float4 sv = __ldg(c.s32 + s0 + j);
         float dd[4];
@@ -903,10 +913,13 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
         S2t += pw * S2;
         for (int k = 0; k < 9; k++) A9[k] += pw * S0 * dlw[k];
         for (int k = 0; k < 4; k++) B4[k] += pwb * dd[k];
-        for (int k = 0; k < 8; k++) C8[k] += pw * X[k];
+        C8[0] += pw * S0 * iH0;
+        for (int k = 1; k < 8; k++) C8[k] += pw * Sv[2 + k];
     };
 
-    float4 *tw = rows + 3 * wid * AM_ROWS;  // this warp's table
+    float4 *tw = rows + AM_SLOT * wid * AM_SLOTS;  // this warp's table
+    float *twf = reinterpret_cast<float *>(tw);
+    float *buf = twf;  // a run's per-sample sums [k][idx], after its chains
     const float *prof = reinterpret_cast<const float *>(p.prof[h]);
     const float *dprof = reinterpret_cast<const float *>(q.dprof[h]);  // FP32 on this path
     const float4 *Q4 = reinterpret_cast<const float4 *>(q.Q32 + (size_t)h * nz * 8);
@@ -921,12 +934,13 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
         const float *G = prof + row * nz;
         const float *dG = dprof + row * nz;
         const int s_lo = segA0[sk], s_hi = segA1[sk];
-        if (ds > 0.5f) {
-            // narrow kernel: direct exponentials on each sample's window
-            for (int jj = lane; jj < cnt; jj += 32) {
-                const int j = lo + jj;
+        // narrow kernel: direct exponentials on each sample's window
+        auto direct = [&](int st, int n) {
+            for (int idx = lane; idx < n; idx += 32) {
+                const int j = lo + st + idx;
                 const float z = zs[j];
-                float S0 = 0.f, S1 = 0.f, S2 = 0.f, X[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float Sv[AM_NP];
+                for (int k = 0; k < AM_NP; k++) Sv[k] = 0.f;
                 if (ws[j] != 0.f) {
                     const int a0 = max(s_lo, (int)ceilf((z - halfk) * inv_dz));
                     const int a1 = min(s_hi, (int)floorf((z + halfk) * inv_dz));
@@ -935,18 +949,17 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
                         const float e = __expf(-x * x) * Fs[a];
                         const float eh = e * __ldg(G + a), U = 1.41421356f * x;
                         const float4 qa = __ldg(Q4 + 2 * a), qb = __ldg(Q4 + 2 * a + 1);
-                        S0 += eh;
-                        S1 += eh * U;
-                        S2 += eh * U * U;
-                        X[0] += eh * qa.x; X[1] += eh * qa.y; X[2] += eh * qa.z; X[3] += eh * qa.w;
-                        X[4] += eh * qb.x; X[5] += eh * qb.y; X[6] += eh * qb.z;
-                        X[7] += e * __ldg(dG + a);
+                        Sv[0] += eh;
+                        Sv[1] += eh * U;
+                        Sv[2] += eh * U * U;
+                        Sv[3] += eh * qa.y; Sv[4] += eh * qa.z; Sv[5] += eh * qa.w;
+                        Sv[6] += eh * qb.x; Sv[7] += eh * qb.y; Sv[8] += eh * qb.z;
+                        Sv[9] += e * __ldg(dG + a);
                     }
                 }
-                sample_terms(j, pf, S0, S1, S2, X);
+                for (int k = 0; k < AM_NP; k++) buf[k * AM_RUN + idx] = Sv[k];
             }
-            continue;
-        }
+        };
         // one run of n samples from st on, R per lane (n <= 32 R)
         auto run = [&](auto Rc, int st, int n) {
             constexpr int R = decltype(Rc)::value;
@@ -966,92 +979,107 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
                 Bf[r] = __expf(2.f * u[r] * ds);
                 Bb[r] = __expf(-2.f * u[r] * ds);
             }
-            float af[R][11], ab[R][11];
+            float af[R][AM_NP], ab[R][AM_NP];
 #pragma unroll
             for (int r = 0; r < R; r++)
 #pragma unroll
-                for (int k = 0; k < 11; k++) { af[r][k] = 0.f; ab[r][k] = 0.f; }
-            // Horner from the outermost offsets in: chunks of AM_CH offsets per
-            // side (+m rows at [0, AM_CH), -m rows at [AM_CH, 2 AM_CH)); the
-            // last chunk also stages tau = 0 (row 2 AM_CH), which closes the
-            // forward chain
+                for (int k = 0; k < AM_NP; k++) { af[r][k] = 0.f; ab[r][k] = 0.f; }
+            // Horner from the outermost offsets in, AM_CH offsets per side at
+            // a time (slot i: the rows of +m and -m, m = mhi - i); the last
+            // chunk also stages tau = 0, which closes the forward chain
             for (int mhi = T;; mhi -= AM_CH) {
                 const int mlo = max(1, mhi - AM_CH + 1), nr = max(0, mhi - mlo + 1);
                 const bool last = mlo <= 1;
                 const int nst = 2 * nr + (last ? 1 : 0);
                 __syncwarp();
                 for (int i = lane; i < nst; i += 32) {
-                    int tau, slot;
-                    if (i < nr) { tau = mhi - i; slot = i; }
-                    else if (i < 2 * nr) { tau = -(mhi - (i - nr)); slot = AM_CH + (i - nr); }
-                    else { tau = 0; slot = 2 * AM_CH; }
+                    int tau;
+                    float *dst;
+                    if (i < nr) { tau = mhi - i; dst = twf + 4 * AM_SLOT * i; }
+                    else if (i < 2 * nr) { tau = -(mhi - (i - nr)); dst = twf + 4 * AM_SLOT * (i - nr) + AM_NP; }
+                    else { tau = 0; dst = twf + 4 * AM_SLOT * AM_CH; }
                     const int a = t_o + tau;
-                    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+                    float2 r0 = make_float2(0.f, 0.f), r1 = r0, r2 = r0, r3 = r0, r4 = r0;
                     if (a >= A0 && a <= A1) {
                         const float x = ds * (float)tau;
                         const float cf = __expf(lnscale - x * x) * Fs[a];
                         const float hh = cf * __ldg(G + a);
                         const float4 qa = __ldg(Q4 + 2 * a), qb = __ldg(Q4 + 2 * a + 1);
                         const float tt = (float)tau;
-                        r0 = make_float4(hh, tt * hh, tt * tt * hh, hh * qa.x);
-                        r1 = make_float4(hh * qa.y, hh * qa.z, hh * qa.w, hh * qb.x);
-                        r2 = make_float4(hh * qb.y, hh * qb.z, cf * __ldg(dG + a), 0.f);
+                        r0 = make_float2(hh, tt * hh);
+                        r1 = make_float2(tt * tt * hh, hh * qa.y);
+                        r2 = make_float2(hh * qa.z, hh * qa.w);
+                        r3 = make_float2(hh * qb.x, hh * qb.y);
+                        r4 = make_float2(hh * qb.z, cf * __ldg(dG + a));
                     }
-                    tw[3 * slot] = r0;
-                    tw[3 * slot + 1] = r1;
-                    tw[3 * slot + 2] = r2;
+                    float2 *d2 = reinterpret_cast<float2 *>(dst);
+                    d2[0] = r0; d2[1] = r1; d2[2] = r2; d2[3] = r3; d2[4] = r4;
                 }
                 __syncwarp();
 #pragma unroll 2
                 for (int i = 0; i < nr; i++) {
-                    const float4 f0 = tw[3 * i], f1 = tw[3 * i + 1], f2 = tw[3 * i + 2];
-                    const float4 e0 = tw[3 * (AM_CH + i)], e1 = tw[3 * (AM_CH + i) + 1], e2 = tw[3 * (AM_CH + i) + 2];
-                    const float cf_[11] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w, f2.x, f2.y, f2.z};
-                    const float cb_[11] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w, e2.x, e2.y, e2.z};
+                    const float4 *sl = tw + AM_SLOT * i;
+                    const float4 v0 = sl[0], v1 = sl[1], v2 = sl[2], v3 = sl[3], v4 = sl[4];
+                    const float cf_[AM_NP] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y};
+                    const float cb_[AM_NP] = {v2.z, v2.w, v3.x, v3.y, v3.z, v3.w, v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
                     for (int r = 0; r < R; r++)
 #pragma unroll
-                        for (int k = 0; k < 11; k++) {
+                        for (int k = 0; k < AM_NP; k++) {
                             af[r][k] = fmaf(af[r][k], Bf[r], cf_[k]);
                             ab[r][k] = fmaf(ab[r][k], Bb[r], cb_[k]);
                         }
                 }
                 if (last) {
-                    const float4 f0 = tw[6 * AM_CH], f1 = tw[6 * AM_CH + 1], f2 = tw[6 * AM_CH + 2];
-                    const float c0_[11] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w, f2.x, f2.y, f2.z};
+                    const float4 *sl = tw + AM_SLOT * AM_CH;
+                    const float4 v0 = sl[0], v1 = sl[1], v2 = sl[2];
+                    const float c0_[AM_NP] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y};
 #pragma unroll
                     for (int r = 0; r < R; r++)
 #pragma unroll
-                        for (int k = 0; k < 11; k++) af[r][k] = fmaf(af[r][k], Bf[r], c0_[k]);
+                        for (int k = 0; k < AM_NP; k++) af[r][k] = fmaf(af[r][k], Bf[r], c0_[k]);
                     break;
                 }
             }
+            __syncwarp();  // the table space now takes the run's sums
 #pragma unroll
             for (int r = 0; r < R; r++) {
                 const int idx = lane + 32 * r;
                 if (idx >= n) continue;
                 const float uu = u[r], E = __expf(-uu * uu - lnscale);
-                float P[11];
+                float P[AM_NP];
 #pragma unroll
-                for (int k = 0; k < 11; k++) P[k] = E * fmaf(Bb[r], ab[r][k], af[r][k]);
-                const float S1 = 1.41421356f * (ds * P[1] - uu * P[0]);
-                const float S2 = 2.f * (ds * ds * P[2] - 2.f * ds * uu * P[1] + uu * uu * P[0]);
-                const float X[8] = {P[3], P[4], P[5], P[6], P[7], P[8], P[9], P[10]};
-                sample_terms(lo + st + idx, pf, P[0], S1, S2, X);
+                for (int k = 0; k < AM_NP; k++) P[k] = E * fmaf(Bb[r], ab[r][k], af[r][k]);
+                buf[idx] = P[0];
+                buf[AM_RUN + idx] = 1.41421356f * (ds * P[1] - uu * P[0]);
+                buf[2 * AM_RUN + idx] = 2.f * (ds * ds * P[2] - 2.f * ds * uu * P[1] + uu * uu * P[0]);
+#pragma unroll
+                for (int k = 3; k < AM_NP; k++) buf[k * AM_RUN + idx] = P[k];
             }
         };
         for (int st = 0; st < cnt;) {
-            // a run: the longest prefix of up to 64 samples spanning <= 16 b
             int n;
-            {
+            if (ds > 0.5f) {
+                n = min(AM_RUN, cnt - st);
+                direct(st, n);
+            } else {
+                // a run: the longest prefix of up to 64 samples spanning <= 16 b
                 const float zf = zs[lo + st], lim = 16.f * b;
                 const bool p0 = st + lane < cnt && zs[lo + st + lane] - zf <= lim;
                 const bool p1 = st + 32 + lane < cnt && zs[lo + st + 32 + lane] - zf <= lim;
                 const unsigned b0 = __ballot_sync(0xffffffffu, p0), b1 = __ballot_sync(0xffffffffu, p1);
                 n = b0 != 0xffffffffu ? __ffs(~b0) - 1 : 32 + (b1 != 0xffffffffu ? __ffs(~b1) - 1 : 32);
+                if (n <= 32) run(std::integral_constant<int, 1>{}, st, n);
+                else run(std::integral_constant<int, 2>{}, st, n);
             }
-            if (n <= 32) run(std::integral_constant<int, 1>{}, st, n);
-            else run(std::integral_constant<int, 2>{}, st, n);
+            // each lane reads back the sums it wrote
+            for (int idx = lane; idx < n; idx += 32) {
+                float Sv[AM_NP];
+#pragma unroll
+                for (int k = 0; k < AM_NP; k++) Sv[k] = buf[k * AM_RUN + idx];
+                sample_terms(lo + st + idx, pf, Sv);
+            }
+            __syncwarp();
             st += n;
         }
     }
@@ -1116,9 +1144,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_select_adj(DevCatalog c, CallPt
     const MassDer<double> md64 = mass_der64(hp, hd, c.beta);
     const MassDer<float> md32 = mass_der32(hp, hd);
     const int64_t base = (int64_t)chunk * SEL_CHUNK;
-    const double inv_dc3 = 1.0 / (hp.dc_zmax * hp.dc_zmax * hp.dc_zmax);
-    const T H0 = T(th[0]), Om = T(th[1]), Xi0 = T(th[2]), nn = T(th[3]);
-    const T cH = T(hp.cH), one = T(1);
+    const T one = T(1);
     for (int qq = 0; qq < SEL_PER_THREAD; qq++) {
         int64_t j = base + qq * ADJ_THREADS + threadIdx.x;
         if (j >= c.n_det) break;
@@ -1141,7 +1167,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_select_adj(DevCatalog c, CallPt
             double dd, J;
             chimd::dgw_J(zz, Dc, th, hp.cH, &dd, &J);
             const double E = chimd::E_of(zz, th[1]);
-            const double pz = 3.0 * hp.cH * Dc * Dc / E * inv_dc3;
+            const double pz = 3.0 * hp.cH * Dc * Dc / E / (hp.dc_zmax * hp.dc_zmax * hp.dc_zmax);
             s = T(p1 * p2 * chimd::psi_of(zz, th) * pz / (a1 * a1 * a1 * fabs(J) * exp(c.ilp64[j])));
             const ZDer r64 = zder(zz, th, p.fwd[h], q.fwdO[h], hd.dlpz_zmax);
             r = r64;
@@ -1165,17 +1191,17 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_select_adj(DevCatalog c, CallPt
             const float p1 = hp.c_pl32 * powf(fm1, -hp.alpha32) + hp.c_g32 * expf(-0.5f * x * x);
             const float p2 = fabsf(hp.b1_32) < 1e-6f ? 1.f / (fm2 * logf(fm1 / mmin))
                                                     : hp.b1_32 * powf(fm2, hp.beta32) / (powf(fm1, hp.b1_32) - hp.mmin_b1_32);
-            const float fn = float(nn), fxi0 = float(Xi0), pwz = expf(-fn * lz);
+            const float fn = hp.n32, fxi0 = hp.xi0_32, pwz = expf(-fn * lz);
             const float xi = fxi0 + (1.f - fxi0) * pwz, dxi = -fn * (1.f - fxi0) * pwz / a1;
             const float Dc = c.i32b[j].x / (a1 * xi);
-            const float fom = float(Om), E = sqrtf(fom * a1 * a1 * a1 + 1.f - fom);
-            const float fcH = float(cH);
+            const float fom = hp.om32, E = sqrtf(fom * a1 * a1 * a1 + 1.f - fom);
+            const float fcH = hp.cH32;
             const float J = (Dc + a1 * fcH / E) * xi + a1 * Dc * dxi;
-            const float pz = 3.f * fcH * Dc * Dc / E * float(inv_dc3);
+            const float pz = 3.f * fcH * Dc * Dc / E * hp.inv_dc3_32;
             const float psi = expf(hp.gam32 * lz) / (1.f + expf((hp.gam32 + hp.kap32) * (lz - hp.l1zp32)));
             s = T(p1 * p2 * psi * pz / (a1 * a1 * a1 * fabsf(J) * expf(c.i32b[j].y)));
             const float DhO = dcO_hermite32(q.fwdO[h], zz, fom);
-            const ZDerT<float> r32 = zder_t<float>(zz, float(H0), fom, fxi0, fn, Dc / fcH, DhO, hd.dlpz_zmax32);
+            const ZDerT<float> r32 = zder_t<float>(zz, hp.h0_32, fom, fxi0, fn, Dc / fcH, DhO, hd.dlpz_zmax32);
             r = r32;
             float e5[5], ez;
             dlnpm_t<float>(md32, fm1, fm2, a1, e5, &ez);
@@ -1185,7 +1211,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_select_adj(DevCatalog c, CallPt
         }
         (void)m1; (void)m2;
         T g3[3], dpsiz;
-        dlnpsi_t<T>(z, T(th[9]), T(th[10]), T(th[11]), g3, &dpsiz);
+        if constexpr (F64) dlnpsi_t<T>(z, th[9], th[10], th[11], g3, &dpsiz);
+        else dlnpsi_t<T>(z, hp.gam32, hp.kap32, hp.zp32, g3, &dpsiz);
         const T dls_dz = dwz + dpsiz + r.dlnpz_dz - T(3) / (one + z) - r.dlnJ_dz;
         T g[12];
         g[0] = -r.dlnJ[0];
@@ -1198,17 +1225,21 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_select_adj(DevCatalog c, CallPt
         for (int k = 0; k < 12; k++) acc[k] += s * g[k];
         acc[12] += s;
     }
+    // block partial sums: FP64 on the FP64 path, a fixed-order FP32 tree on
+    // the mixed path (off the narrow FP64 pipe); the chunks are added in
+    // FP64 by the combine kernel
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T *redT = reinterpret_cast<T *>(red);
     for (int k = 0; k < 13; k++) {
-        double v = double(acc[k]);
+        T v = acc[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[wid * 13 + k] = v;
+        if (lane == 0) redT[wid * 13 + k] = v;
     }
     __syncthreads();
     if (threadIdx.x < 13) {
-        double v = 0.0;
-        for (int w = 0; w < ADJ_THREADS / 32; w++) v += red[w * 13 + threadIdx.x];
-        q.selg[((size_t)h * p.n_chunk + chunk) * 13 + threadIdx.x] = v;
+        T v = T(0);
+        for (int w = 0; w < ADJ_THREADS / 32; w++) v += redT[w * 13 + threadIdx.x];
+        q.selg[((size_t)h * p.n_chunk + chunk) * 13 + threadIdx.x] = double(v);
     }
 }
 
@@ -1336,7 +1367,7 @@ size_t adjoint_event_smem(const DevCatalog &c, bool fp64) {
 }
 
 void launch_adjoint(const DevCatalog &c, const CallPtrs &p, const AdjPtrs &q, int H, bool fp64, cudaStream_t st) {
-    k_adj_tables<<<H, ADJ_THREADS, 0, st>>>(c, p, q);
+    k_adj_tables<<<dim3(H, 8), ADJ_THREADS, 0, st>>>(c, p, q);
     const size_t smem = adjoint_event_smem(c, fp64);
     const unsigned nb = (unsigned)((int64_t)c.n_events * H);
     if (fp64) {

@@ -287,6 +287,8 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
         hp.inv_dc3_32 = (float)(1.0 / (hp.dc_zmax * hp.dc_zmax * hp.dc_zmax));
         hp.l2min32 = (float)log2(mmin);
         hp.l2max32 = (float)log2(mmax);
+        hp.h0_32 = (float)th[0];
+        hp.zp32 = (float)th[11];
         p.hp[h] = hp;
     }
 }

@@ -61,6 +61,7 @@ struct HP {
     float c_pl32, c_g32, alpha32, mu32, inv_sg32, mmin32, mmax32, beta32, b1_32, mmin_b1_32,
         lmmin32, xi0_32, n32, om32, gam32, kap32, l1zp32, cH32, inv_dc3_32;
     float l2min32, l2max32;  // log2 m_min, log2 m_max
+    float h0_32, zp32;
 };
 
 // Resident catalog (device pointers unless noted).

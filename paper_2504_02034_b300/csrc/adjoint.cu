@@ -1269,81 +1269,25 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_combine_adj(DevCatalog c, CallP
 
 // dV_c/dz (as D^2/E) and its Om derivative on the grid, for one Om.
 __global__ void k_dv_pair(const double *fwd, const double *fwdO, double Om, double dz, int nz, double *dv,
-                          double *dvO) {
+                          double *dvO, float *dv32, float *dvO32) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= nz) return;
     double z = a * dz, ap = 1.0 + z;
     double D = chimd::dc_hermite(fwd, z, Om), DO = dcO_hermite(fwdO, z, Om), E = chimd::E_of(z, Om);
     dv[a] = D * D / E;
     dvO[a] = 2.0 * D * DO / E - D * D * (ap * ap * ap - 1.0) * 0.5 / (E * E * E);
+    dv32[a] = (float)dv[a];
+    dvO32[a] = (float)dvO[a];
 }
 
-// Galaxy (z, sigma): FP64 values, or the stored values of the mixed path.
-__device__ __forceinline__ void gal_value(const DevCatalog &c, int64_t p, int64_t g, bool f64, double &z,
-                                          double &s) {
-    if (f64 || c.gal_storage == CHIMERA_GAL_F32) {
-        z = f64 ? c.gz64[g] : (double)c.gz32[g];
-        s = f64 ? c.gs64[g] : (double)c.gs32[g];
-    } else if (c.gal_storage == CHIMERA_GAL_F16) {
-        z = (double)(c.pix_zref[p] + __half2float(__ushort_as_half(c.gzq[g])));
-        s = (double)__half2float(__ushort_as_half(c.gsq[g]));
-    } else {
-        z = (double)(c.pix_zref[p] + __uint_as_float(((uint32_t)c.gzq[g]) << 16));
-        s = (double)__uint_as_float(((uint32_t)c.gsq[g]) << 16);
-    }
-}
-
-// dG_k/dOm on the grid (FP64), with the galaxy windows of the forward profile
-// of the same precision:
-//   G = dv sum_g N_g / Z_g,  G' = dv' sum_g N_g / Z_g - dv sum_g N_g Z_g' / Z_g^2,
-//   Z_g' = sum_a w_a N_g(z_a) dv'(z_a).
-template <bool F64>
-__global__ void __launch_bounds__(ADJ_THREADS) k_profile_dOm(DevCatalog c, const double *dv, const double *dvO,
-                                                            double *invZ, double *ZO, double *out) {
-    const int64_t p = blockIdx.x;
-    const int64_t g0 = c.gal_off[p], g1 = c.gal_off[p + 1];
-    const int nz = c.n_z;
-    const double dz = c.dz, norm = 0.39894228040143267794;
-    const double KWG = F64 ? KWG64 : (double)KWG32;
-    for (int64_t g = g0 + threadIdx.x; g < g1; g += ADJ_THREADS) {
-        double zg, sg;
-        gal_value(c, p, g, F64, zg, sg);
-        double a0 = ceil((zg - KWG * sg) / dz), a1 = floor((zg + KWG * sg) / dz);
-        int lo = a0 < 0.0 ? 0 : (a0 > nz ? nz : (int)a0);
-        int hi = a1 > nz - 1 ? nz - 1 : (a1 < -1.0 ? -1 : (int)a1);
-        double Z = 0.0, Zp = 0.0;
-        for (int a = lo; a <= hi; a++) {
-            double u = (a * dz - zg) / sg, wa = (a == 0 || a == nz - 1) ? 0.5 * dz : dz;
-            double Nv = wa * norm / sg * exp(-0.5 * u * u);
-            Z += Nv * dv[a];
-            Zp += Nv * dvO[a];
-        }
-        invZ[g] = Z > 0.0 ? 1.0 / Z : 0.0;
-        ZO[g] = Zp;
-    }
-    __syncthreads();
-    const double smax = F64 ? c.pix_sigmax[p] * KWG64 : (double)(c.pix_sigmax32[p] * KWG32);
-    for (int a = threadIdx.x; a < nz; a += ADJ_THREADS) {
-        double za = a * dz, s1 = 0.0, s2 = 0.0;
-        int64_t l = g0, r = g1;
-        while (l < r) {
-            int64_t m = (l + r) >> 1;
-            double zm, sm;
-            gal_value(c, p, m, F64, zm, sm);
-            if (zm < za - smax) l = m + 1; else r = m;
-        }
-        for (int64_t g = l; g < g1; g++) {
-            double zg, sg;
-            gal_value(c, p, g, F64, zg, sg);
-            if (zg > za + smax) break;
-            double a0 = ceil((zg - KWG * sg) / dz), a1 = floor((zg + KWG * sg) / dz);
-            if (a < a0 || a > a1 || invZ[g] == 0.0) continue;
-            double u = (za - zg) / sg;
-            double Nv = norm / sg * exp(-0.5 * u * u);
-            s1 += Nv * invZ[g];
-            s2 += Nv * ZO[g] * invZ[g] * invZ[g];
-        }
-        out[p * nz + a] = dvO[a] * s1 - dv[a] * s2;
+// Single-1D, mixed: sum_k S_k dG_k/dOm per event in FP32.
+__global__ void k_dprofile_sum32(DevCatalog c, const float *G, float *outh) {
+    const int ev = blockIdx.x, nz = c.n_z;
+    const int64_t p0 = c.ev_poff[ev], p1 = c.ev_poff[ev + 1];
+    for (int a = threadIdx.x; a < nz; a += blockDim.x) {
+        float s = 0.f;
+        for (int64_t p = p0; p < p1; p++) s += (float)c.pix_S[p] * G[p * nz + a];
+        outh[(int64_t)ev * nz + a] = s;
     }
 }
 
@@ -1411,8 +1355,8 @@ struct AdjLayout {
         o_Q32 = take(sizeof(float) * 8 * (size_t)H * c.n_z);
         o_dlnI = take(sizeof(double) * 12 * (size_t)H * c.n_events);
         o_selg = take(sizeof(double) * 13 * (size_t)H * std::max(nchunk, 1));
-        o_dv = take(sizeof(double) * c.n_z);
-        o_dvO = take(sizeof(double) * c.n_z);
+        o_dv = take((sizeof(double) + sizeof(float)) * c.n_z);  // FP64 values, then their FP32 copy
+        o_dvO = take((sizeof(double) + sizeof(float)) * c.n_z);
         o_invZ = take(sizeof(double) * (size_t)std::max<int64_t>(c.n_gal, 1));
         o_ZO = take(sizeof(double) * (size_t)std::max<int64_t>(c.n_gal, 1));
         total = o;
@@ -1440,15 +1384,8 @@ int fwdO_table(Ctx &ctx, double Om, cudaStream_t st, const double **out) {
     return CHIMERA_OK;
 }
 
-// FP32 copy of a profile (the mixed adjoint's tables read FP32).
-__global__ void k_to_f32(const double *src, float *dst, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = (float)src[i];
-}
-
-// dG/dOm profile for (Om, precision), cached with the forward profiles.  The
-// mixed entry holds the FP64 rows followed by their FP32 copy, and hands out
-// the copy.
+// dG/dOm profile for (Om, precision), cached with the forward profiles
+// (FP64 rows for FP64 calls, FP32 rows for mixed ones).
 int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double Om, bool f64, const double *fwd,
              const double *fwdO, const double **out) {
     const int kind = f64 ? 2 : 3;
@@ -1457,7 +1394,7 @@ int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double O
     const DevCatalog &c = cat.d;
     if (it == cat.prof.end()) {
         ProfEntry e;
-        const size_t per = f64 ? sizeof(double) : sizeof(double) + sizeof(float);
+        const size_t per = f64 ? sizeof(double) : sizeof(float);
         e.bytes = per * (size_t)c.n_pix * c.n_z;
         const size_t hb = c.kde_mode == CHIMERA_KDE_SINGLE_1D ? per * (size_t)c.n_events * c.n_z : 0;
         evict_profiles(ctx, cat, e.bytes + hb);
@@ -1475,17 +1412,12 @@ int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double O
         double *dvO = reinterpret_cast<double *>(ws.gscr + L.o_dvO);
         double *invZ = reinterpret_cast<double *>(ws.gscr + L.o_invZ);
         double *ZO = reinterpret_cast<double *>(ws.gscr + L.o_ZO);
-        k_dv_pair<<<(c.n_z + 255) / 256, 256, 0, ws.st>>>(fwd, fwdO, Om, c.dz, c.n_z, dv, dvO);
-        if (c.n_pix > 0) {
-            if (f64) k_profile_dOm<true><<<(unsigned)c.n_pix, ADJ_THREADS, 0, ws.st>>>(c, dv, dvO, invZ, ZO, (double *)e.G);
-            else k_profile_dOm<false><<<(unsigned)c.n_pix, ADJ_THREADS, 0, ws.st>>>(c, dv, dvO, invZ, ZO, (double *)e.G);
-        }
-        if (hb) k_dprofile_sum<<<c.n_events, 256, 0, ws.st>>>(c, (const double *)e.G, (double *)e.Gh);
-        if (!f64) {
-            const int64_t n = (int64_t)(hb ? c.n_events : c.n_pix) * c.n_z;
-            double *src = reinterpret_cast<double *>(hb ? e.Gh : e.G);
-            if (n > 0) k_to_f32<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, ws.st>>>(
-                src, reinterpret_cast<float *>(src + n), n);
+        float *dv32 = reinterpret_cast<float *>(dv + c.n_z), *dvO32 = reinterpret_cast<float *>(dvO + c.n_z);
+        k_dv_pair<<<(c.n_z + 255) / 256, 256, 0, ws.st>>>(fwd, fwdO, Om, c.dz, c.n_z, dv, dvO, dv32, dvO32);
+        launch_galaxy_dOm(c, dv, dvO, dv32, dvO32, f64, invZ, ZO, e.G, ws.st);
+        if (hb) {
+            if (f64) k_dprofile_sum<<<c.n_events, 256, 0, ws.st>>>(c, (const double *)e.G, (double *)e.Gh);
+            else k_dprofile_sum32<<<c.n_events, 256, 0, ws.st>>>(c, (const float *)e.G, (float *)e.Gh);
         }
         CK(cudaGetLastError());
         CK(cudaEventRecord(e.ready, ws.st));
@@ -1494,10 +1426,8 @@ int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double O
         CK(cudaStreamWaitEvent(ws.st, it->second.ready, 0));
     }
     it->second.last_use = ctx.tick;
-    const bool single = c.kde_mode == CHIMERA_KDE_SINGLE_1D;
-    const double *g = reinterpret_cast<const double *>(single ? it->second.Gh : it->second.G);
-    if (!f64) g += (int64_t)(single ? c.n_events : c.n_pix) * c.n_z;  // the FP32 copy (pointer kept as double*)
-    *out = g;
+    // FP32 rows on the mixed path (the pointer table is typed double*)
+    *out = reinterpret_cast<const double *>(c.kde_mode == CHIMERA_KDE_SINGLE_1D ? it->second.Gh : it->second.G);
     return CHIMERA_OK;
 }
 

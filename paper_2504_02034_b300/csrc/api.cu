@@ -169,7 +169,7 @@ int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat) {
         {(void **)&ws.lnL, sizeof(double) * Hn},
         {(void **)&ws.neff, sizeof(double) * Hn},
         {(void **)&ws.xi, sizeof(double) * Hn},
-        {(void **)&ws.dv, sizeof(double) * nz},
+        {(void **)&ws.dv, (sizeof(double) + sizeof(float)) * nz},
         {(void **)&ws.invZ64, sizeof(double) * (size_t)std::max<int64_t>(ng, 1)},
         {(void **)&ws.invZ32, sizeof(float) * (size_t)std::max<int64_t>(ng, 1)},
         {(void **)&ws.grad, sizeof(double) * 12 * (size_t)Hn},
@@ -716,6 +716,18 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     std::vector<int64_t> ev_poff(d->pix_off, d->pix_off + ne + 1);
     std::vector<int64_t> goff(d->gal_off, d->gal_off + np + 1);
     std::vector<double> pixS(d->sky_S, d->sky_S + np);
+    // galaxy-profile work lists
+    std::vector<int32_t> gw_pix, dense_pix;
+    std::vector<int64_t> gw_g0;
+    for (int64_t p = 0; p < np; p++) {
+        for (int64_t g = goff[p]; g < goff[p + 1]; g += GAL_CHUNK) {
+            gw_pix.push_back((int32_t)p);
+            gw_g0.push_back(g);
+        }
+        if (goff[p + 1] - goff[p] > GAL_DENSE) dense_pix.push_back((int32_t)p);
+    }
+    c.n_gw = (int64_t)gw_pix.size();
+    c.n_dense = (int32_t)dense_pix.size();
 
     // ---- upload
     struct Up { void **dst; const void *src; size_t bytes; };
@@ -736,6 +748,9 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         {(void **)&c.pix_sigmax, sigmax.data(), 8 * sigmax.size()},
         {(void **)&c.pix_sigmax32, sigmax32.data(), 4 * sigmax32.size()},
         {(void **)&c.pix_zref, zref.data(), 4 * zref.size()},
+        {(void **)&c.gw_pix, gw_pix.data(), 4 * gw_pix.size()},
+        {(void **)&c.gw_g0, gw_g0.data(), 8 * gw_g0.size()},
+        {(void **)&c.dense_pix, dense_pix.data(), 4 * dense_pix.size()},
         {(void **)&c.gz64, gz.data(), 8 * gz.size()},
         {(void **)&c.gs64, gs.data(), 8 * gs.size()},
         {(void **)&c.s32, s32.data(), 16 * s32.size()},

@@ -10,10 +10,21 @@
 // galaxy contributes on the grid points within KWG sigma of its redshift,
 // in both Z_g and G, so every galaxy keeps unit weight on the grid.
 //
-// One block per pixel: phase 1 computes 1/Z_g for the pixel's galaxies,
-// phase 2 gathers, for each grid point, the galaxies whose window covers it
-// (galaxies are sorted by z inside a pixel at load time), so the sums are
-// formed in a fixed order without atomics.
+// The Om derivative used by the adjoint has the same structure:
+//   dG/dOm = dv' sum_g N_g / Z_g - dv sum_g N_g Z_g' / Z_g^2,
+//   Z_g'   = sum_a w_a N_g(z_a) dv'(z_a),   dv = dV_c/dz, dv' = d dv / dOm.
+//
+// Three launches per profile, balanced whatever the pixel occupancy (a
+// pixel can hold tens of thousands of galaxies while most hold a few
+// hundred):
+//   norm:   1 / Z_g (and Z_g') for every galaxy, over load-time chunks of
+//           GAL_CHUNK galaxies of one pixel, one galaxy per thread;
+//   gather: one block per pixel of at most GAL_DENSE galaxies, one grid
+//           point per thread, the galaxies whose window covers it (sorted by
+//           z inside the pixel at load time, found by binary search);
+//   dense:  one block per (dense pixel, grid point), the covering galaxies
+//           spread over the block and added by a fixed-order tree.
+// Every sum has a fixed order, so a profile is reproducible bit for bit.
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
@@ -25,30 +36,14 @@ namespace {
 
 constexpr int GAL_THREADS = 256;
 
-__global__ void k_dvdz(const double *fwd, double Om, double dz, int nz, double *dv) {
+// dV_c/dz (up to constants) on the grid, FP64 and its FP32 copy.
+__global__ void k_dvdz(const double *fwd, double Om, double dz, int nz, double *dv, float *dv32) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a < nz) {
         double z = a * dz;
         double D = chimd::dc_hermite(fwd, z, Om);
         dv[a] = D * D / chimd::E_of(z, Om);
-    }
-}
-
-__device__ __forceinline__ float bf16_bits_to_float(uint16_t b) {
-    return __uint_as_float(((uint32_t)b) << 16);
-}
-
-// Galaxy (z, sigma) as the device stores it for the mixed path.
-__device__ __forceinline__ void gal32(const DevCatalog &c, int64_t p, int64_t g, float &z, float &s) {
-    if (c.gal_storage == CHIMERA_GAL_F32) {
-        z = c.gz32[g];
-        s = c.gs32[g];
-    } else if (c.gal_storage == CHIMERA_GAL_F16) {
-        z = c.pix_zref[p] + __half2float(__ushort_as_half(c.gzq[g]));
-        s = __half2float(__ushort_as_half(c.gsq[g]));
-    } else {
-        z = c.pix_zref[p] + bf16_bits_to_float(c.gzq[g]);
-        s = bf16_bits_to_float(c.gsq[g]);
+        dv32[a] = (float)dv[a];
     }
 }
 
@@ -58,92 +53,193 @@ __device__ __forceinline__ void window(double zg, double kw, double dz, int nz, 
     hi = a1 > nz - 1 ? nz - 1 : (a1 < -1.0 ? -1 : (int)a1);
 }
 
-// FP64 profile from the double galaxy values.
-__global__ void __launch_bounds__(GAL_THREADS) k_profile64(DevCatalog c, const double *dv,
-                                                          double *invZ, double *G) {
-    const int64_t p = blockIdx.x;
-    const int64_t g0 = c.gal_off[p], g1 = c.gal_off[p + 1];
-    const int nz = c.n_z;
-    const double dz = c.dz, norm = 0.39894228040143267794;
-    for (int64_t g = g0 + threadIdx.x; g < g1; g += GAL_THREADS) {
-        double zg = c.gz64[g], sg = c.gs64[g];
-        int lo, hi;
-        window(zg, KWG64 * sg, dz, nz, lo, hi);
-        double Z = 0.0;
-        for (int a = lo; a <= hi; a++) {
-            double u = (a * dz - zg) / sg;
-            double wa = (a == 0 || a == nz - 1) ? 0.5 * dz : dz;
-            Z += wa * norm / sg * exp(-0.5 * u * u) * dv[a];
-        }
-        invZ[g] = Z > 0.0 ? 1.0 / Z : 0.0;
+// Galaxy access by precision: FP64 values and windows of KWG64 sigma, or the
+// stored values of the mixed path and its windows of KWG32 sigma.
+template <bool F64>
+struct Gal;
+template <>
+struct Gal<true> {
+    using T = double;
+    __device__ static void read(const DevCatalog &c, int64_t, int64_t g, double &z, double &s) {
+        z = c.gz64[g];
+        s = c.gs64[g];
     }
-    __syncthreads();
-    const double smax = c.pix_sigmax[p] * KWG64;
-    for (int a = threadIdx.x; a < nz; a += GAL_THREADS) {
-        double za = a * dz, acc = 0.0;
-        // first galaxy with z >= za - smax, first with z > za + smax
-        int64_t l = g0, r = g1;
-        while (l < r) {
-            int64_t m = (l + r) >> 1;
-            if (c.gz64[m] < za - smax) l = m + 1; else r = m;
-        }
-        for (int64_t g = l; g < g1; g++) {
-            double zg = c.gz64[g];
-            if (zg > za + smax) break;
-            double sg = c.gs64[g];
-            int lo, hi;
-            window(zg, KWG64 * sg, dz, nz, lo, hi);
-            if (a < lo || a > hi) continue;
-            double u = (za - zg) / sg;
-            acc += norm / sg * exp(-0.5 * u * u) * invZ[g];
-        }
-        G[p * nz + a] = acc * dv[a];
+    __device__ static void win(const DevCatalog &c, double zg, double sg, int &lo, int &hi) {
+        window(zg, KWG64 * sg, c.dz, c.n_z, lo, hi);
+    }
+    __device__ static double reach(const DevCatalog &c, int64_t p) { return c.pix_sigmax[p] * KWG64; }
+    __device__ static double step(const DevCatalog &c) { return c.dz; }
+    __device__ static double gauss(double u) { return exp(-0.5 * u * u); }
+};
+template <>
+struct Gal<false> {
+    using T = float;
+    __device__ static void read(const DevCatalog &c, int64_t p, int64_t g, float &z, float &s) {
+        chimd::gal32(c, p, g, z, s);
+    }
+    __device__ static void win(const DevCatalog &c, float zg, float sg, int &lo, int &hi) {
+        chimd::gal_window32(zg, sg, 1.f / c.dz32, c.n_z, lo, hi);
+    }
+    __device__ static float reach(const DevCatalog &c, int64_t p) { return c.pix_sigmax32[p] * KWG32; }
+    __device__ static float step(const DevCatalog &c) { return c.dz32; }
+    __device__ static float gauss(float u) { return __expf(-0.5f * u * u); }
+};
+
+// 1 / Z_g (and Z_g' with WITH_O) for the galaxies of one load-time chunk.
+template <bool F64, bool WITH_O>
+__global__ void __launch_bounds__(GAL_CHUNK) k_gal_norm(DevCatalog c, const typename Gal<F64>::T *dv,
+                                                       const typename Gal<F64>::T *dvO,
+                                                       typename Gal<F64>::T *invZ, typename Gal<F64>::T *ZO) {
+    using G = Gal<F64>;
+    using T = typename G::T;
+    const int p = c.gw_pix[blockIdx.x];
+    const int64_t g = c.gw_g0[blockIdx.x] + threadIdx.x;
+    if (g >= c.gal_off[p + 1]) return;
+    const int nz = c.n_z;
+    const T dz = G::step(c), norm = T(0.39894228040143267794);
+    T zg, sg;
+    G::read(c, p, g, zg, sg);
+    int lo, hi;
+    G::win(c, zg, sg, lo, hi);
+    const T isg = T(1) / sg;
+    T Z = T(0), Zp = T(0);
+    for (int a = lo; a <= hi; a++) {
+        const T u = (a * dz - zg) * isg;
+        const T Nv = ((a == 0 || a == nz - 1) ? T(0.5) * dz : dz) * G::gauss(u);
+        Z += Nv * dv[a];
+        if (WITH_O) Zp += Nv * dvO[a];
+    }
+    Z *= norm * isg;
+    invZ[g] = Z > T(0) ? T(1) / Z : T(0);
+    if (WITH_O) ZO[g] = Zp * norm * isg;
+}
+
+// The sums of one grid point over galaxies [l, r) of pixel p, strided by
+// `step` from `first`: s1 = sum N/Z, s2 = sum N Z'/Z^2 (WITH_O).
+template <bool F64, bool WITH_O>
+__device__ __forceinline__ void gather_range(const DevCatalog &c, int64_t p, int a, int64_t first, int64_t r,
+                                             int stride, const typename Gal<F64>::T *invZ,
+                                             const typename Gal<F64>::T *ZO, typename Gal<F64>::T &s1,
+                                             typename Gal<F64>::T &s2) {
+    using G = Gal<F64>;
+    using T = typename G::T;
+    const T za = a * G::step(c);
+    for (int64_t g = first; g < r; g += stride) {
+        T zg, sg;
+        G::read(c, p, g, zg, sg);
+        int lo, hi;
+        G::win(c, zg, sg, lo, hi);
+        const T iz = invZ[g];
+        if (a < lo || a > hi || iz == T(0)) continue;
+        const T isg = T(1) / sg, u = (za - zg) * isg;
+        const T Nv = isg * G::gauss(u);
+        s1 += Nv * iz;
+        if (WITH_O) s2 += Nv * ZO[g] * iz * iz;
     }
 }
 
-// Mixed-path profile (FP32 arithmetic) from the stored galaxy values.
-__global__ void __launch_bounds__(GAL_THREADS) k_profile32(DevCatalog c, const double *dv,
-                                                          float *invZ, float *G) {
+// First galaxy of pixel p (galaxies [g0, g1), sorted by z) with z >= x, or
+// with z > x when `after`.
+template <bool F64>
+__device__ __forceinline__ int64_t gal_bound(const DevCatalog &c, int64_t p, int64_t g0, int64_t g1,
+                                             typename Gal<F64>::T x, bool after) {
+    using G = Gal<F64>;
+    using T = typename G::T;
+    int64_t l = g0, r = g1;
+    while (l < r) {
+        const int64_t m = (l + r) >> 1;
+        T zm, sm;
+        G::read(c, p, m, zm, sm);
+        if (after ? zm <= x : zm < x) l = m + 1; else r = m;
+    }
+    return l;
+}
+
+template <bool F64, bool WITH_O>
+__device__ __forceinline__ typename Gal<F64>::T gather_out(const typename Gal<F64>::T *dv,
+                                                           const typename Gal<F64>::T *dvO, int a,
+                                                           typename Gal<F64>::T s1, typename Gal<F64>::T s2) {
+    using T = typename Gal<F64>::T;
+    const T norm = T(0.39894228040143267794);
+    return WITH_O ? norm * (dvO[a] * s1 - dv[a] * s2) : norm * s1 * dv[a];
+}
+
+// One block per pixel of at most GAL_DENSE galaxies, one grid point per thread.
+template <bool F64, bool WITH_O>
+__global__ void __launch_bounds__(GAL_THREADS) k_gal_gather(DevCatalog c, const typename Gal<F64>::T *dv,
+                                                           const typename Gal<F64>::T *dvO,
+                                                           const typename Gal<F64>::T *invZ,
+                                                           const typename Gal<F64>::T *ZO,
+                                                           typename Gal<F64>::T *out) {
+    using G = Gal<F64>;
+    using T = typename G::T;
     const int64_t p = blockIdx.x;
     const int64_t g0 = c.gal_off[p], g1 = c.gal_off[p + 1];
+    if (g1 - g0 > GAL_DENSE) return;  // the dense kernel's pixel
     const int nz = c.n_z;
-    const float dz = (float)c.dz, norm = 0.3989422804f;
-    for (int64_t g = g0 + threadIdx.x; g < g1; g += GAL_THREADS) {
-        float zg, sg;
-        gal32(c, p, g, zg, sg);
-        int lo, hi;
-        window(zg, (double)(KWG32 * sg), c.dz, nz, lo, hi);
-        float Z = 0.f;
-        for (int a = lo; a <= hi; a++) {
-            float u = (a * dz - zg) / sg;
-            float wa = (a == 0 || a == nz - 1) ? 0.5f * dz : dz;
-            Z += wa * norm / sg * expf(-0.5f * u * u) * (float)dv[a];
-        }
-        invZ[g] = Z > 0.f ? 1.f / Z : 0.f;
+    const T dz = G::step(c), reach = G::reach(c, p);
+    for (int a = threadIdx.x; a < nz; a += GAL_THREADS) {
+        const T za = a * dz;
+        T s1 = T(0), s2 = T(0);
+        const int64_t l = gal_bound<F64>(c, p, g0, g1, za - reach, false);
+        const int64_t r = gal_bound<F64>(c, p, l, g1, za + reach, true);
+        gather_range<F64, WITH_O>(c, p, a, l, r, 1, invZ, ZO, s1, s2);
+        out[p * nz + a] = gather_out<F64, WITH_O>(dv, dvO, a, s1, s2);
+    }
+}
+
+// One block per (dense pixel, grid point).
+template <bool F64, bool WITH_O>
+__global__ void __launch_bounds__(GAL_THREADS) k_gal_gather_dense(DevCatalog c, const typename Gal<F64>::T *dv,
+                                                                 const typename Gal<F64>::T *dvO,
+                                                                 const typename Gal<F64>::T *invZ,
+                                                                 const typename Gal<F64>::T *ZO,
+                                                                 typename Gal<F64>::T *out) {
+    using G = Gal<F64>;
+    using T = typename G::T;
+    __shared__ int64_t lr[2];
+    __shared__ T red[2][GAL_THREADS / 32];
+    const int64_t p = c.dense_pix[blockIdx.x];
+    const int a = blockIdx.y;
+    const int64_t g0 = c.gal_off[p], g1 = c.gal_off[p + 1];
+    const T za = a * G::step(c), reach = G::reach(c, p);
+    if (threadIdx.x == 0) {
+        lr[0] = gal_bound<F64>(c, p, g0, g1, za - reach, false);
+        lr[1] = gal_bound<F64>(c, p, lr[0], g1, za + reach, true);
     }
     __syncthreads();
-    const float smax = c.pix_sigmax32[p] * KWG32;
-    for (int a = threadIdx.x; a < nz; a += GAL_THREADS) {
-        float za = a * dz, acc = 0.f;
-        int64_t l = g0, r = g1;
-        while (l < r) {
-            int64_t m = (l + r) >> 1;
-            float zm, sm;
-            gal32(c, p, m, zm, sm);
-            if (zm < za - smax) l = m + 1; else r = m;
-        }
-        for (int64_t g = l; g < g1; g++) {
-            float zg, sg;
-            gal32(c, p, g, zg, sg);
-            if (zg > za + smax) break;
-            int lo, hi;
-            window(zg, (double)(KWG32 * sg), c.dz, nz, lo, hi);
-            if (a < lo || a > hi) continue;
-            float u = (za - zg) / sg;
-            acc += norm / sg * expf(-0.5f * u * u) * invZ[g];
-        }
-        G[p * nz + a] = acc * (float)dv[a];
+    T s1 = T(0), s2 = T(0);
+    gather_range<F64, WITH_O>(c, p, a, lr[0] + threadIdx.x, lr[1], GAL_THREADS, invZ, ZO, s1, s2);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        if (WITH_O) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     }
+    if (lane == 0) {
+        red[0][wid] = s1;
+        red[1][wid] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T t1 = T(0), t2 = T(0);
+        for (int w = 0; w < GAL_THREADS / 32; w++) {
+            t1 += red[0][w];
+            t2 += red[1][w];
+        }
+        out[p * c.n_z + a] = gather_out<F64, WITH_O>(dv, dvO, a, t1, t2);
+    }
+}
+
+template <bool F64, bool WITH_O>
+void launch_profile_t(const DevCatalog &c, const typename Gal<F64>::T *dv, const typename Gal<F64>::T *dvO,
+                      typename Gal<F64>::T *invZ, typename Gal<F64>::T *ZO, typename Gal<F64>::T *out,
+                      cudaStream_t st) {
+    if (c.n_pix == 0) return;
+    if (c.n_gw > 0) k_gal_norm<F64, WITH_O><<<(unsigned)c.n_gw, GAL_CHUNK, 0, st>>>(c, dv, dvO, invZ, ZO);
+    k_gal_gather<F64, WITH_O><<<(unsigned)c.n_pix, GAL_THREADS, 0, st>>>(c, dv, dvO, invZ, ZO, out);
+    if (c.n_dense > 0)
+        k_gal_gather_dense<F64, WITH_O><<<dim3((unsigned)c.n_dense, (unsigned)c.n_z), GAL_THREADS, 0, st>>>(
+            c, dv, dvO, invZ, ZO, out);
 }
 
 // Single-1D: sum_k S_k G_k(z_a) per event.
@@ -170,10 +266,18 @@ __global__ void k_profile_sum(DevCatalog c, const double *G64, const float *G32,
 void launch_galaxy_profile(const DevCatalog &c, const double *fwd, double Om, double *dv,
                            double *invZ64, float *invZ32, double *out64, float *out32,
                            cudaStream_t st) {
-    k_dvdz<<<(c.n_z + 255) / 256, 256, 0, st>>>(fwd, Om, c.dz, c.n_z, dv);
-    if (c.n_pix == 0) return;
-    if (out64) k_profile64<<<(unsigned)c.n_pix, GAL_THREADS, 0, st>>>(c, dv, invZ64, out64);
-    if (out32) k_profile32<<<(unsigned)c.n_pix, GAL_THREADS, 0, st>>>(c, dv, invZ32, out32);
+    float *dv32 = reinterpret_cast<float *>(dv + c.n_z);
+    k_dvdz<<<(c.n_z + 255) / 256, 256, 0, st>>>(fwd, Om, c.dz, c.n_z, dv, dv32);
+    if (out64) launch_profile_t<true, false>(c, dv, nullptr, invZ64, nullptr, out64, st);
+    if (out32) launch_profile_t<false, false>(c, dv32, nullptr, invZ32, nullptr, out32, st);
+}
+
+void launch_galaxy_dOm(const DevCatalog &c, const double *dv, const double *dvO, const float *dv32,
+                       const float *dvO32, bool f64, void *invZ, void *ZO, void *out, cudaStream_t st) {
+    if (f64)
+        launch_profile_t<true, true>(c, dv, dvO, (double *)invZ, (double *)ZO, (double *)out, st);
+    else
+        launch_profile_t<false, true>(c, dv32, dvO32, (float *)invZ, (float *)ZO, (float *)out, st);
 }
 
 void launch_profile_sum(const DevCatalog &c, const double *G64, const float *G32, double *outh64,

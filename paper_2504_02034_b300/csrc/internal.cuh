@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 
 #include "chimera.h"
@@ -23,6 +24,8 @@ constexpr int NU = 2048;
 constexpr float KW32 = 6.0f;
 constexpr double KW64 = 9.0;
 constexpr float KWG32 = 6.0f;
+constexpr int GAL_CHUNK = 256;   // galaxies per normalisation block
+constexpr int GAL_DENSE = 1024;  // pixels above this gather per grid point by blocks
 // Each KDE is zero outside the grid segment holding its samples, widened by
 // KDE_MARGIN bandwidths (Sec. 2.3: evaluated only where the samples are).
 constexpr double KDE_MARGIN = 6.0;
@@ -100,6 +103,14 @@ struct DevCatalog {
     double *pix_sigmax;   // [n_pix] widest galaxy of the pixel (FP64 values)
     float *pix_sigmax32;  // [n_pix] widest galaxy (stored values)
     float *pix_zref;      // [n_pix] F16/BF16 offset reference
+    // galaxy-profile work lists, fixed at load: every chunk of up to
+    // GAL_CHUNK galaxies of one pixel (pixel, first galaxy), and the pixels
+    // with more than GAL_DENSE galaxies
+    int64_t n_gw;
+    int32_t *gw_pix;
+    int64_t *gw_g0;
+    int32_t n_dense;
+    int32_t *dense_pix;
     // galaxies
     double *gz64, *gs64;  // FP64 values
     float *gz32, *gs32;   // F32 storage
@@ -143,11 +154,16 @@ void launch_fwd_table(double Om, double *out, cudaStream_t st);
 // fmax_bits: [H] scratch.
 void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, double *dk,
                          unsigned long long *fmax_bits, cudaStream_t st);
-// K3: galaxy redshift prior on the grid for one Om.  dv: [n_z] scratch,
-// invZ: [n_gal] scratch; out64 (FP64 values) or out32 (stored values).
+// K3: galaxy redshift prior on the grid for one Om.  dv: scratch of n_z
+// doubles followed by n_z floats, invZ: [n_gal] scratch; out64 (FP64
+// values) or out32 (stored values).
 void launch_galaxy_profile(const DevCatalog &c, const double *fwd, double Om, double *dv,
                            double *invZ64, float *invZ32, double *out64, float *out32,
                            cudaStream_t st);
+// dG/dOm of the galaxy profile (FP64 from dv, dvO, or FP32 from their FP32
+// copies); invZ, ZO: [n_gal] scratch of the precision's type; out [n_pix x n_z].
+void launch_galaxy_dOm(const DevCatalog &c, const double *dv, const double *dvO, const float *dv32,
+                       const float *dvO32, bool f64, void *invZ, void *ZO, void *out, cudaStream_t st);
 // Single-1D sky-summed profile: outh[event][a] = sum_k S_k G[k][a].
 void launch_profile_sum(const DevCatalog &c, const double *G64, const float *G32, double *outh64,
                         float *outh32, cudaStream_t st);
@@ -214,6 +230,32 @@ __device__ __forceinline__ void dgw_J(double z, double Dc, const double *th, dou
 __device__ __forceinline__ double psi_of(double z, const double *th) {
     const double la = log(1.0 + z);
     return exp(th[9] * la) / (1.0 + exp((th[9] + th[10]) * (la - log1p(th[11]))));
+}
+
+// Galaxy (z, sigma) as the device stores it for the mixed path: F32, or
+// F16/BF16 with z as an offset from the pixel's reference redshift.
+__device__ __forceinline__ void gal32(const chim::DevCatalog &c, int64_t p, int64_t g, float &z, float &s) {
+    if (c.gal_storage == CHIMERA_GAL_F32) {
+        z = c.gz32[g];
+        s = c.gs32[g];
+    } else if (c.gal_storage == CHIMERA_GAL_F16) {
+        z = c.pix_zref[p] + __half2float(__ushort_as_half(c.gzq[g]));
+        s = __half2float(__ushort_as_half(c.gsq[g]));
+    } else {
+        z = c.pix_zref[p] + __uint_as_float(((uint32_t)c.gzq[g]) << 16);
+        s = __uint_as_float(((uint32_t)c.gsq[g]) << 16);
+    }
+}
+
+// Grid window of a galaxy on the mixed path: the points within KWG32 sigma
+// of its redshift, [lo, hi] (empty when hi < lo).  The forward profile and
+// its Om derivative take their windows from here, so that every galaxy
+// keeps unit weight on the same grid points in both.
+__device__ __forceinline__ void gal_window32(float zg, float sg, float inv_dz, int nz, int &lo, int &hi) {
+    const float kw = chim::KWG32 * sg;
+    const float a0 = ceilf((zg - kw) * inv_dz), a1 = floorf((zg + kw) * inv_dz);
+    lo = a0 < 0.f ? 0 : (a0 > (float)nz ? nz : (int)a0);
+    hi = a1 > (float)(nz - 1) ? nz - 1 : (a1 < -1.f ? -1 : (int)a1);
 }
 
 __device__ __forceinline__ float hermite4(float4 nd, float f) {

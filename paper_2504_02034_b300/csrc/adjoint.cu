@@ -60,59 +60,6 @@ struct AdjPtrs {
 namespace {
 
 constexpr int ADJ_THREADS = 256;
-constexpr int FWD_THREADS = 512;
-constexpr int FWD_PER_THREAD = 10;
-
-// ---- dDhat/dOm = -1/2 int_0^z ((1+z)^3 - 1) / E^3 dz, cumulative ----
-__global__ void __launch_bounds__(FWD_THREADS) k_fwd_table_dOm(double Om, double *out) {
-    __shared__ double warp_tot[FWD_THREADS / 32];
-    const int t = threadIdx.x;
-    const double x1 = sqrt(5.0 - 2.0 * sqrt(10.0 / 7.0)) / 3.0;
-    const double x2 = sqrt(5.0 + 2.0 * sqrt(10.0 / 7.0)) / 3.0;
-    const double w0 = 128.0 / 225.0;
-    const double w1 = (322.0 + 13.0 * sqrt(70.0)) / 900.0;
-    const double w2 = (322.0 - 13.0 * sqrt(70.0)) / 900.0;
-    auto g = [Om](double z) {
-        double a = 1.0 + z, E = chimd::E_of(z, Om);
-        return -0.5 * (a * a * a - 1.0) / (E * E * E);
-    };
-    double loc[FWD_PER_THREAD];
-    double run = 0.0;
-#pragma unroll
-    for (int cc = 0; cc < FWD_PER_THREAD; cc++) {
-        int k = t * FWD_PER_THREAD + cc;
-        if (k < NT_FWD - 1) {
-            double m = (k + 0.5) * HT, hh = 0.5 * HT;
-            double s = w0 * g(m) + w1 * (g(m - hh * x1) + g(m + hh * x1)) + w2 * (g(m - hh * x2) + g(m + hh * x2));
-            run += s * hh;
-        }
-        loc[cc] = run;
-    }
-    const int lane = t & 31, wid = t >> 5;
-    double v = run;
-    for (int o = 1; o < 32; o <<= 1) {
-        double y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += y;
-    }
-    if (lane == 31) warp_tot[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        double x = lane < FWD_THREADS / 32 ? warp_tot[lane] : 0.0;
-        for (int o = 1; o < 32; o <<= 1) {
-            double y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane < FWD_THREADS / 32) warp_tot[lane] = x;
-    }
-    __syncthreads();
-    double offset = (v - run) + (wid > 0 ? warp_tot[wid - 1] : 0.0);
-#pragma unroll
-    for (int cc = 0; cc < FWD_PER_THREAD; cc++) {
-        int k = t * FWD_PER_THREAD + cc;
-        if (k < NT_FWD - 1) out[k + 1] = offset + loc[cc];
-    }
-    if (t == 0) out[0] = 0.0;
-}
 
 // Hermite interpolation of dDhat/dOm (node derivatives known in closed form).
 __device__ __forceinline__ double dcO_hermite(const double *fwdO, double z, double Om) {
@@ -1373,7 +1320,7 @@ int fwdO_table(Ctx &ctx, double Om, cudaStream_t st, const double **out) {
             dev_free(ctx, e.table, sizeof(double) * NT_FWD);
             return cuda_check(cudaGetLastError(), "cudaEventCreate");
         }
-        k_fwd_table_dOm<<<1, FWD_THREADS, 0, st>>>(Om, e.table);
+        launch_fwd_table_dOm(Om, e.table, st);
         CK(cudaGetLastError());
         CK(cudaEventRecord(e.ready, st));
         it = ctx.fwdO.emplace(key, e).first;

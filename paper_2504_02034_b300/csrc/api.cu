@@ -775,6 +775,12 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         ups.push_back({(void **)&c.gzq, gzq.data(), 2 * gzq.size()});
         ups.push_back({(void **)&c.gsq, gsq.data(), 2 * gsq.size()});
     }
+    // the dense pixels' candidate ranges: allocated here, filled on the device
+    if (c.n_dense > 0) {
+        const size_t lb = sizeof(int2) * (size_t)c.n_dense * c.n_z;
+        ups.push_back({(void **)&c.dense_lr64, nullptr, lb});
+        ups.push_back({(void **)&c.dense_lr32, nullptr, lb});
+    }
     size_t total = 0;
     for (auto &u : ups) total += (std::max<size_t>(u.bytes, 16) + 255) & ~(size_t)255;
     if (ctx.used.load() + total > ctx.budget) {
@@ -790,13 +796,23 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         }
         cat->allocs.push_back(*u.dst);
         cat->bytes += (std::max<size_t>(u.bytes, 16) + 255) & ~(size_t)255;
-        if (u.bytes) {
+        if (u.bytes && u.src) {
             cudaError_t e = cudaMemcpy(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
             if (e != cudaSuccess) {
                 for (void *a : cat->allocs) cudaFree(a);
                 ctx.used -= cat->bytes;
                 return cuda_check(e, "cudaMemcpy catalog upload");
             }
+        }
+    }
+    if (c.n_dense > 0) {
+        launch_dense_ranges(c, 0);
+        cudaError_t e = cudaStreamSynchronize(0);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            for (void *a : cat->allocs) cudaFree(a);
+            ctx.used -= cat->bytes;
+            return cuda_check(e, "dense galaxy ranges");
         }
     }
     // event kernels need their shared memory

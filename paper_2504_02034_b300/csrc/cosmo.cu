@@ -1,15 +1,19 @@
 // K1: cosmology tables (Eqs. dL-em, dL-mg, jacobian; Sec. 2.1).
 //
-// k_fwd_table  - per distinct Om: cumulative D_c(z_k)/(c/H0) on the forward
-//                grid z_k = k*HT by 5-point Gauss-Legendre panels and a block
-//                prefix sum, all in FP64.
-// k_fwd_nodes, k_inv_nodes, k_grid, k_hyper_final - per hyperpoint, each
-//                spread over (nodes x hyperpoints) so that the FP64 work uses
-//                every SM: d_L^gw and J on the forward nodes (monotonicity
-//                check on z <= 10), the inverse table z(u), u = sqrt(d_L/d_top),
-//                by Newton on the Hermite-interpolated forward relation, the
-//                grid factor F(z_a) = psi(z_a) / [(1+z_a)^3 |J(z_a)|] of
-//                Eq. like-integrals, and the mass-model normalisations.
+// k_fwd_panels + k_fwd_offsets - per distinct Om: cumulative D_c(z_k)/(c/H0)
+//                on the forward grid z_k = k*HT by 5-point Gauss-Legendre
+//                panels, one panel per thread over FWD_BLOCKS blocks (the FP64
+//                evaluations spread over that many SMs), block prefix sums and
+//                a one-block pass that adds the preceding blocks' totals, all
+//                in FP64.  The same pair gives the Om derivative of the table
+//                for the adjoint.
+// k_nodes_grid, k_inv_nodes, k_hyper_final - per hyperpoint, each spread over
+//                (nodes x hyperpoints) so that the work uses every SM: d_L^gw
+//                and J on the forward nodes (monotonicity check on z <= 10),
+//                the inverse table z(u), u = sqrt(d_L/d_top), by Newton on the
+//                Hermite-interpolated forward relation, the grid factor
+//                F(z_a) = psi(z_a) / [(1+z_a)^3 |J(z_a)|] of Eq. like-integrals,
+//                and the mass-model normalisations.
 #include <math_constants.h>
 
 #include "internal.cuh"
@@ -18,58 +22,63 @@ namespace chim {
 
 namespace {
 
-constexpr int FWD_THREADS = 512;
-constexpr int FWD_PER_THREAD = 10;
-static_assert(FWD_THREADS * FWD_PER_THREAD >= NT_FWD - 1, "forward table coverage");
+constexpr int FWD_THREADS = 128;
+constexpr int FWD_BLOCKS = (NT_FWD - 1 + FWD_THREADS - 1) / FWD_THREADS;
 
-__global__ void __launch_bounds__(FWD_THREADS) k_fwd_table(double Om, double *out) {
+// Integrand of the table: 1/E (KIND 0) or d(1/E)/dOm = -((1+z)^3 - 1)/(2 E^3)
+// (KIND 1, the Om derivative used by the adjoint).
+template <int KIND>
+__device__ __forceinline__ double fwd_integrand(double z, double Om) {
+    const double E = chimd::E_of(z, Om);
+    if (KIND == 0) return 1.0 / E;
+    const double a = 1.0 + z;
+    return -0.5 * (a * a * a - 1.0) / (E * E * E);
+}
+
+// One panel [z_k, z_k+1] per thread, 5-point Gauss-Legendre (nodes and
+// weights in closed form); out[k+1] = the block's inclusive prefix.
+template <int KIND>
+__global__ void __launch_bounds__(FWD_THREADS) k_fwd_panels(double Om, double *out) {
     __shared__ double warp_tot[FWD_THREADS / 32];
-    const int t = threadIdx.x;
-    // 5-point Gauss-Legendre nodes and weights in closed form.
+    const int t = threadIdx.x, k = blockIdx.x * FWD_THREADS + t;
     const double x1 = sqrt(5.0 - 2.0 * sqrt(10.0 / 7.0)) / 3.0;
     const double x2 = sqrt(5.0 + 2.0 * sqrt(10.0 / 7.0)) / 3.0;
     const double w0 = 128.0 / 225.0;
     const double w1 = (322.0 + 13.0 * sqrt(70.0)) / 900.0;
     const double w2 = (322.0 - 13.0 * sqrt(70.0)) / 900.0;
-    double loc[FWD_PER_THREAD];
-    double run = 0.0;
-#pragma unroll
-    for (int c = 0; c < FWD_PER_THREAD; c++) {
-        int k = t * FWD_PER_THREAD + c;
-        if (k < NT_FWD - 1) {
-            double m = (k + 0.5) * HT, hh = 0.5 * HT;
-            double s = w0 / chimd::E_of(m, Om) +
-                       w1 * (1.0 / chimd::E_of(m - hh * x1, Om) + 1.0 / chimd::E_of(m + hh * x1, Om)) +
-                       w2 * (1.0 / chimd::E_of(m - hh * x2, Om) + 1.0 / chimd::E_of(m + hh * x2, Om));
-            run += s * hh;
-        }
-        loc[c] = run;
+    double s = 0.0;
+    if (k < NT_FWD - 1) {
+        const double m = (k + 0.5) * HT, hh = 0.5 * HT;
+        s = hh * (w0 * fwd_integrand<KIND>(m, Om) +
+                  w1 * (fwd_integrand<KIND>(m - hh * x1, Om) + fwd_integrand<KIND>(m + hh * x1, Om)) +
+                  w2 * (fwd_integrand<KIND>(m - hh * x2, Om) + fwd_integrand<KIND>(m + hh * x2, Om)));
     }
-    // block exclusive scan of the per-thread totals
     const int lane = t & 31, wid = t >> 5;
-    double v = run;
+    double v = s;
     for (int o = 1; o < 32; o <<= 1) {
-        double y = __shfl_up_sync(0xffffffffu, v, o);
+        const double y = __shfl_up_sync(0xffffffffu, v, o);
         if (lane >= o) v += y;
     }
     if (lane == 31) warp_tot[wid] = v;
     __syncthreads();
-    if (wid == 0) {
-        double x = lane < FWD_THREADS / 32 ? warp_tot[lane] : 0.0;
-        for (int o = 1; o < 32; o <<= 1) {
-            double y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+    double off = 0.0;
+    for (int w = 0; w < wid; w++) off += warp_tot[w];
+    if (k < NT_FWD - 1) out[k + 1] = off + v;
+    if (k == 0) out[0] = 0.0;
+}
+
+// Adds to every block's entries the totals of the blocks before it.
+__global__ void __launch_bounds__(1024) k_fwd_offsets(double *out) {
+    __shared__ double off[FWD_BLOCKS];
+    if (threadIdx.x == 0) {
+        double run = 0.0;
+        for (int b = 0; b < FWD_BLOCKS; b++) {
+            off[b] = run;
+            if (b + 1 < FWD_BLOCKS) run += out[(b + 1) * FWD_THREADS];  // block b's total
         }
-        if (lane < FWD_THREADS / 32) warp_tot[lane] = x;
     }
     __syncthreads();
-    double offset = (v - run) + (wid > 0 ? warp_tot[wid - 1] : 0.0);
-#pragma unroll
-    for (int c = 0; c < FWD_PER_THREAD; c++) {
-        int k = t * FWD_PER_THREAD + c;
-        if (k < NT_FWD - 1) out[k + 1] = offset + loc[c];
-    }
-    if (t == 0) out[0] = 0.0;
+    for (int k = FWD_THREADS + threadIdx.x; k < NT_FWD - 1; k += 1024) out[k + 1] += off[k / FWD_THREADS];
 }
 
 constexpr int HYP_THREADS = 256;
@@ -296,7 +305,13 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
 }  // namespace
 
 void launch_fwd_table(double Om, double *out, cudaStream_t st) {
-    k_fwd_table<<<1, FWD_THREADS, 0, st>>>(Om, out);
+    k_fwd_panels<0><<<FWD_BLOCKS, FWD_THREADS, 0, st>>>(Om, out);
+    k_fwd_offsets<<<1, 1024, 0, st>>>(out);
+}
+
+void launch_fwd_table_dOm(double Om, double *out, cudaStream_t st) {
+    k_fwd_panels<1><<<FWD_BLOCKS, FWD_THREADS, 0, st>>>(Om, out);
+    k_fwd_offsets<<<1, 1024, 0, st>>>(out);
 }
 
 void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, double *dk,

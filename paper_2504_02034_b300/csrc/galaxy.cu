@@ -188,28 +188,38 @@ __global__ void __launch_bounds__(GAL_THREADS) k_gal_gather(DevCatalog c, const 
     }
 }
 
-// One block per (dense pixel, grid point).
+// Candidate ranges of the dense pixels: one thread per (dense pixel, grid
+// point), the same bounds as the gather kernel's.
+template <bool F64>
+__global__ void k_dense_ranges(DevCatalog c, int2 *lr) {
+    using G = Gal<F64>;
+    using T = typename G::T;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)c.n_dense * c.n_z) return;
+    const int64_t p = c.dense_pix[i / c.n_z];
+    const int a = (int)(i % c.n_z);
+    const int64_t g0 = c.gal_off[p], g1 = c.gal_off[p + 1];
+    const T za = a * G::step(c), reach = G::reach(c, p);
+    const int64_t l = gal_bound<F64>(c, p, g0, g1, za - reach, false);
+    const int64_t r = gal_bound<F64>(c, p, l, g1, za + reach, true);
+    lr[i] = make_int2((int)(l - g0), (int)(r - g0));
+}
+
+// One block per (dense pixel, grid point), over the load-time candidate range.
 template <bool F64, bool WITH_O>
 __global__ void __launch_bounds__(GAL_THREADS) k_gal_gather_dense(DevCatalog c, const typename Gal<F64>::T *dv,
                                                                  const typename Gal<F64>::T *dvO,
                                                                  const typename Gal<F64>::T *invZ,
                                                                  const typename Gal<F64>::T *ZO,
                                                                  typename Gal<F64>::T *out) {
-    using G = Gal<F64>;
-    using T = typename G::T;
-    __shared__ int64_t lr[2];
+    using T = typename Gal<F64>::T;
     __shared__ T red[2][GAL_THREADS / 32];
     const int64_t p = c.dense_pix[blockIdx.x];
     const int a = blockIdx.y;
-    const int64_t g0 = c.gal_off[p], g1 = c.gal_off[p + 1];
-    const T za = a * G::step(c), reach = G::reach(c, p);
-    if (threadIdx.x == 0) {
-        lr[0] = gal_bound<F64>(c, p, g0, g1, za - reach, false);
-        lr[1] = gal_bound<F64>(c, p, lr[0], g1, za + reach, true);
-    }
-    __syncthreads();
+    const int64_t g0 = c.gal_off[p];
+    const int2 lr = (F64 ? c.dense_lr64 : c.dense_lr32)[(int64_t)blockIdx.x * c.n_z + a];
     T s1 = T(0), s2 = T(0);
-    gather_range<F64, WITH_O>(c, p, a, lr[0] + threadIdx.x, lr[1], GAL_THREADS, invZ, ZO, s1, s2);
+    gather_range<F64, WITH_O>(c, p, a, g0 + lr.x + threadIdx.x, g0 + lr.y, GAL_THREADS, invZ, ZO, s1, s2);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int o = 16; o > 0; o >>= 1) {
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
@@ -270,6 +280,14 @@ void launch_galaxy_profile(const DevCatalog &c, const double *fwd, double Om, do
     k_dvdz<<<(c.n_z + 255) / 256, 256, 0, st>>>(fwd, Om, c.dz, c.n_z, dv, dv32);
     if (out64) launch_profile_t<true, false>(c, dv, nullptr, invZ64, nullptr, out64, st);
     if (out32) launch_profile_t<false, false>(c, dv32, nullptr, invZ32, nullptr, out32, st);
+}
+
+void launch_dense_ranges(const DevCatalog &c, cudaStream_t st) {
+    const int64_t n = (int64_t)c.n_dense * c.n_z;
+    if (n == 0) return;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    k_dense_ranges<true><<<nb, 256, 0, st>>>(c, c.dense_lr64);
+    k_dense_ranges<false><<<nb, 256, 0, st>>>(c, c.dense_lr32);
 }
 
 void launch_galaxy_dOm(const DevCatalog &c, const double *dv, const double *dvO, const float *dv32,

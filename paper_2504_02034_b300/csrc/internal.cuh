@@ -111,6 +111,11 @@ struct DevCatalog {
     int64_t *gw_g0;
     int32_t n_dense;
     int32_t *dense_pix;
+    // [n_dense x n_z] per dense pixel and grid point, the galaxies whose
+    // window can cover the point, [x, y) relative to the pixel's first
+    // galaxy (FP64 values and reach; stored values and the mixed reach);
+    // filled on the device at load
+    int2 *dense_lr64, *dense_lr32;
     // galaxies
     double *gz64, *gs64;  // FP64 values
     float *gz32, *gs32;   // F32 storage
@@ -148,6 +153,8 @@ struct CallPtrs {
 // ---- launch wrappers (host) ----
 // K1a: forward table D_c(z_k) / (c/H0) for one Om into `out` [NT_FWD].
 void launch_fwd_table(double Om, double *out, cudaStream_t st);
+// Its Om derivative, d/dOm of D_c(z_k)/(c/H0), into `out` [NT_FWD] (adjoint).
+void launch_fwd_table_dOm(double Om, double *out, cudaStream_t st);
 // K1b: per-hyperpoint parameters, inverse tables, grid factors (F64 for
 // fp64, normalised F32 otherwise), status.  dk: scratch of at least
 // H x NT_FWD x 8 bytes (FP32 d_L^gw and J at the forward nodes),
@@ -164,6 +171,9 @@ void launch_galaxy_profile(const DevCatalog &c, const double *fwd, double Om, do
 // copies); invZ, ZO: [n_gal] scratch of the precision's type; out [n_pix x n_z].
 void launch_galaxy_dOm(const DevCatalog &c, const double *dv, const double *dvO, const float *dv32,
                        const float *dvO32, bool f64, void *invZ, void *ZO, void *out, cudaStream_t st);
+// Candidate galaxy ranges of the dense pixels (Om-independent), into
+// c.dense_lr64 / c.dense_lr32.
+void launch_dense_ranges(const DevCatalog &c, cudaStream_t st);
 // Single-1D sky-summed profile: outh[event][a] = sum_k S_k G[k][a].
 void launch_profile_sum(const DevCatalog &c, const double *G64, const float *G32, double *outh64,
                         float *outh32, cudaStream_t st);

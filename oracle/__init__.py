@@ -85,6 +85,12 @@ def lib():
         L.orc_event_lnI.argtypes = [pc, pd, C.c_int64, ph, pd]
         L.orc_selection.argtypes = [pc, pd, ph, C.c_int, pd, pd, pd]
         L.orc_loglike.argtypes = [pc, pd, ph, C.c_int, pd, pd, pd, pd, pi32]
+        L.orc_loglike_binned.argtypes = [pc, pd, ph, C.c_int, pd, pd, pd, pd, pi32]
+        L.orc_event_kde_binned.argtypes = [pc, pd, C.c_int64, C.c_int32, pd]
+        L.orc_event_lnI_binned.argtypes = [pc, pd, C.c_int64, ph, pd]
+        L.orc_linear_bins.argtypes = [C.c_int64, pd, pd, d, C.c_int64, C.c_int64, pd]
+        L.orc_linear_bins.restype = C.c_int64
+        L.orc_kde_arrays.argtypes = [C.c_int64, pd, pd, d, C.c_int64, d, C.c_int32, pd]
         _lib = L
     return _lib
 
@@ -156,9 +162,10 @@ class Catalog:
         lib().orc_event_bandwidth(self.ref, _p(_th(theta)), ev, C.byref(b))
         return b.value
 
-    def kde(self, theta, ev, pixel=-1):
+    def kde(self, theta, ev, pixel=-1, binned=False):
         K = np.zeros(self.n_z)
-        lib().orc_event_kde(self.ref, _p(_th(theta)), ev, pixel, _p(K))
+        f = lib().orc_event_kde_binned if binned else lib().orc_event_kde
+        f(self.ref, _p(_th(theta)), ev, pixel, _p(K))
         return K
 
     def galaxy_profile(self, theta, ev, pixel, hk=None):
@@ -171,9 +178,10 @@ class Catalog:
         lib().orc_grid_factor(self.ref, _p(_th(theta)), C.byref(hk or hooks()), _p(F))
         return F
 
-    def event_lnI(self, theta, ev, hk=None):
+    def event_lnI(self, theta, ev, hk=None, binned=False):
         v = C.c_double()
-        lib().orc_event_lnI(self.ref, _p(_th(theta)), ev, C.byref(hk or hooks()), C.byref(v))
+        f = lib().orc_event_lnI_binned if binned else lib().orc_event_lnI
+        f(self.ref, _p(_th(theta)), ev, C.byref(hk or hooks()), C.byref(v))
         return v.value
 
     def selection(self, theta, hk=None, nthreads=0, want_s=False):
@@ -184,12 +192,13 @@ class Catalog:
                             C.byref(xi), C.byref(ne), _p(s) if want_s else None)
         return (xi.value, ne.value, s[:n]) if want_s else (xi.value, ne.value)
 
-    def loglike(self, theta, hk=None, nthreads=0):
+    def loglike(self, theta, hk=None, nthreads=0, binned=False):
         """Returns dict(lnL, lnI[n_events], xi, neff, status)."""
         lnL, xi, ne = C.c_double(), C.c_double(), C.c_double()
         st = C.c_int32()
         lnI = np.zeros(max(self.n_events, 1))
-        lib().orc_loglike(self.ref, _p(_th(theta)), C.byref(hk or hooks()), nthreads,
+        f = lib().orc_loglike_binned if binned else lib().orc_loglike
+        f(self.ref, _p(_th(theta)), C.byref(hk or hooks()), nthreads,
                           C.byref(lnL), _p(lnI), C.byref(xi), C.byref(ne), C.byref(st))
         return dict(lnL=lnL.value, lnI=lnI[: self.n_events], xi=xi.value, neff=ne.value,
                     status=st.value)
@@ -265,3 +274,23 @@ def check_theta(theta):
 
 def monotone(theta):
     return lib().orc_monotone(_p(_th(theta)))
+
+
+def linear_bins(z, w, dz, b0, nb):
+    """Linear binning of weighted samples onto nodes b0 .. b0+nb-1 of the
+    lattice b dz; returns (node weights, parts that fell outside)."""
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    cb = np.zeros(int(nb))
+    lost = lib().orc_linear_bins(z.size, _p(z), _p(w), float(dz), int(b0), int(nb), _p(cb))
+    return cb, int(lost)
+
+
+def kde_arrays(z, w, b, n_z, z_max, binned=False):
+    """Weighted Gaussian KDE (1/N normalisation, support: sample range +- 6 b)
+    of the samples (z, w) on the grid of n_z points on [0, z_max]."""
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    K = np.zeros(int(n_z))
+    lib().orc_kde_arrays(z.size, _p(z), _p(w), float(b), int(n_z), float(z_max), int(binned), _p(K))
+    return K

@@ -287,53 +287,131 @@ int orc_event_bandwidth(const orc_catalog *c, const double *th, int64_t ev, doub
     return 0;
 }
 
-/* Weighted Gaussian KDE on the grid (Eqs. gw-kernel-many1d/single1d):
- * K(z_a) = (1/N) sum_{j in set} w_j exp(-(z_a - z_j)^2 / 2b^2) / (sqrt(2 pi) b),
- * the set being the pixel's samples (N = N_k) or all samples (N = N_s).
- * The KDE is evaluated only on the part of the grid that holds the set's
- * samples and is zero elsewhere (Sec. 2.3): z_a in
- * [min z_j - ORC_KDE_MARGIN b, max z_j + ORC_KDE_MARGIN b] over the set's
- * samples with a redshift; every sample term inside is kept in full.       */
-static void kde_grid(const orc_catalog *c, int64_t ev, int32_t pixel,
-                     const double *z, const double *w, const int32_t *valid,
-                     double b, double *K) {
-    int64_t j0 = c->sample_off[ev], n = c->sample_off[ev + 1] - j0;
-    int64_t cnt = 0;
-    double zlo = INFINITY, zhi = -INFINITY;
+/* Linear binning of weighted samples onto the lattice z_b = b dz (the
+ * binned-KDE option: the paper bins the weighted samples of each pixel or
+ * event, Sec. 2.3; reading: each sample is split between the two lattice
+ * nodes that bracket it, in proportion to its distance from the other one).
+ * A sample at z with t = z / dz, b = floor(t), f = t - b adds w (1 - f) to
+ * node b and w f to node b + 1.  Nodes [b0, b0 + nb) are kept in cb; the
+ * return value counts sample parts that fell outside that range.          */
+int64_t orc_linear_bins(int64_t n, const double *z, const double *w, double dz,
+                        int64_t b0, int64_t nb, double *cb) {
+    int64_t lost = 0;
+    for (int64_t b = 0; b < nb; b++) cb[b] = 0.0;
     for (int64_t j = 0; j < n; j++) {
-        if (pixel >= 0 && c->pix_of_sample[j0 + j] != pixel) continue;
-        cnt++;
+        if (w[j] == 0.0 || !isfinite(z[j])) continue;
+        double t = z[j] / dz, fb = floor(t), f = t - fb;
+        int64_t b = (int64_t)fb - b0;
+        if (b >= 0 && b < nb) cb[b] += w[j] * (1.0 - f); else lost++;
+        if (b + 1 >= 0 && b + 1 < nb) cb[b + 1] += w[j] * f; else lost++;
+    }
+    return lost;
+}
+
+/* Weighted Gaussian KDE of one sample set on the grid (Eqs.
+ * gw-kernel-many1d/single1d):
+ * K(z_a) = (1/N) sum_{j in set} w_j exp(-(z_a - z_j)^2 / 2b^2) / (sqrt(2 pi) b),
+ * N the set's size (all its samples, valid or not).  The KDE is evaluated
+ * only on the part of the grid that holds the set's samples and is zero
+ * elsewhere (Sec. 2.3): z_a in [min z_j - ORC_KDE_MARGIN b,
+ * max z_j + ORC_KDE_MARGIN b] over the samples with a redshift; every sample
+ * term inside is kept in full.  binned != 0: the samples are replaced by
+ * their linear bins (orc_linear_bins) before the same sum; the support stays
+ * that of the samples.                                                    */
+static void kde_set(int64_t n, const double *z, const double *w, const int32_t *valid,
+                    int64_t N, double b, int64_t nz, double z_max, int binned, double *K) {
+    const double dz = z_max / (double)(nz - 1);
+    double zlo = INFINITY, zhi = -INFINITY;
+    for (int64_t j = 0; j < n; j++)
         if (valid[j]) {
             if (z[j] < zlo) zlo = z[j];
             if (z[j] > zhi) zhi = z[j];
         }
+    double norm = 1.0 / (sqrt(2.0 * M_PI) * b);
+    double *zb = NULL, *cb = NULL, *wv = NULL;
+    int64_t m = 0;
+    if (binned && zlo <= zhi) {
+        int64_t b0 = (int64_t)floor(zlo / dz), nb = (int64_t)floor(zhi / dz) - b0 + 2;
+        cb = malloc(sizeof(double) * nb);
+        zb = malloc(sizeof(double) * nb);
+        wv = malloc(sizeof(double) * (n + 1));
+        for (int64_t j = 0; j < n; j++) wv[j] = valid[j] ? w[j] : 0.0;
+        orc_linear_bins(n, z, wv, dz, b0, nb, cb);
+        for (int64_t k = 0; k < nb; k++) zb[k] = z_max * (double)(b0 + k) / (double)(nz - 1);
+        m = nb;
     }
     zlo -= ORC_KDE_MARGIN * b;
     zhi += ORC_KDE_MARGIN * b;
-    double norm = 1.0 / (sqrt(2.0 * M_PI) * b);
-    for (int64_t a = 0; a < c->n_z; a++) {
-        double za = grid_z(c, a), s = 0.0;
+    for (int64_t a = 0; a < nz; a++) {
+        double za = z_max * (double)a / (double)(nz - 1), s = 0.0;
         if (!(za >= zlo && za <= zhi)) { K[a] = 0.0; continue; }
-        for (int64_t j = 0; j < n; j++) {
-            if (!valid[j] || w[j] == 0.0) continue;
-            if (pixel >= 0 && c->pix_of_sample[j0 + j] != pixel) continue;
-            double u = (za - z[j]) / b;
-            s += w[j] * exp(-0.5 * u * u);
+        if (binned) {
+            for (int64_t k = 0; k < m; k++) {
+                if (cb[k] == 0.0) continue;
+                double u = (za - zb[k]) / b;
+                s += cb[k] * exp(-0.5 * u * u);
+            }
+        } else {
+            for (int64_t j = 0; j < n; j++) {
+                if (!valid[j] || w[j] == 0.0) continue;
+                double u = (za - z[j]) / b;
+                s += w[j] * exp(-0.5 * u * u);
+            }
         }
-        K[a] = cnt > 0 ? s * norm / (double)cnt : 0.0;
+        K[a] = N > 0 ? s * norm / (double)N : 0.0;
     }
+    free(zb); free(cb); free(wv);
 }
 
-int orc_event_kde(const orc_catalog *c, const double *th, int64_t ev,
-                  int32_t pixel, double *K) {
+int orc_kde_arrays(int64_t n, const double *z, const double *w, double b, int64_t nz,
+                   double z_max, int32_t binned, double *K) {
+    int32_t *v = malloc(sizeof(int32_t) * (n + 1));
+    for (int64_t j = 0; j < n; j++) v[j] = isfinite(z[j]) ? 1 : 0;
+    kde_set(n, z, w, v, n, b, nz, z_max, binned, K);
+    free(v);
+    return 0;
+}
+
+/* The KDE of one pixel's samples (pixel >= 0) or of all the event's samples
+ * (pixel = -1) on the grid. */
+static void kde_grid(const orc_catalog *c, int64_t ev, int32_t pixel,
+                     const double *z, const double *w, const int32_t *valid,
+                     double b, int binned, double *K) {
+    int64_t j0 = c->sample_off[ev], n = c->sample_off[ev + 1] - j0;
+    double *zs = malloc(sizeof(double) * (n + 1)), *ws = malloc(sizeof(double) * (n + 1));
+    int32_t *vs = malloc(sizeof(int32_t) * (n + 1));
+    int64_t cnt = 0;
+    for (int64_t j = 0; j < n; j++) {
+        if (pixel >= 0 && c->pix_of_sample[j0 + j] != pixel) continue;
+        zs[cnt] = z[j];
+        ws[cnt] = w[j];
+        vs[cnt] = valid[j];
+        cnt++;
+    }
+    kde_set(cnt, zs, ws, vs, cnt, b, c->n_z, c->z_max, binned, K);
+    free(zs); free(ws); free(vs);
+}
+
+static int event_kde_impl(const orc_catalog *c, const double *th, int64_t ev,
+                          int32_t pixel, int binned, double *K) {
     int64_t n = c->sample_off[ev + 1] - c->sample_off[ev];
     double *z = malloc(sizeof(double) * (n + 1)), *w = malloc(sizeof(double) * (n + 1));
     int32_t *v = malloc(sizeof(int32_t) * (n + 1));
     samples_h(c, th, ev, &default_hooks, z, w, v);
     double b = bandwidth_of(n, z, w, v, grid_dz(c));
-    kde_grid(c, ev, pixel, z, w, v, b, K);
+    kde_grid(c, ev, pixel, z, w, v, b, binned, K);
     free(z); free(w); free(v);
     return 0;
+}
+
+int orc_event_kde(const orc_catalog *c, const double *th, int64_t ev,
+                  int32_t pixel, double *K) {
+    return event_kde_impl(c, th, ev, pixel, 0, K);
+}
+
+int orc_event_kde_binned(const orc_catalog *c, const double *th, int64_t ev,
+                         int32_t pixel, double *K) {
+    return event_kde_impl(c, th, ev, pixel, 1, K);
 }
 
 /* Galaxy prior of one pixel on the grid (Eq. p-cat, complete catalog):
@@ -393,7 +471,7 @@ int orc_grid_factor(const orc_catalog *c, const double *th,
  * many-1D : I = sum_k S_k sum_a w_a K_k(z_a) F(z_a) G_k(z_a)
  * single-1D: I = sum_a w_a K(z_a) F(z_a) sum_k S_k G_k(z_a)              */
 static double event_lnI_impl(const orc_catalog *c, const double *th, int64_t ev,
-                             const orc_hooks *hk, const double *F, const double *dv) {
+                             const orc_hooks *hk, const double *F, const double *dv, int binned) {
     int64_t n = c->sample_off[ev + 1] - c->sample_off[ev];
     int64_t nz = c->n_z;
     int32_t npix = (int32_t)(c->pix_off[ev + 1] - c->pix_off[ev]);
@@ -407,14 +485,14 @@ static double event_lnI_impl(const orc_catalog *c, const double *th, int64_t ev,
     if (c->kde_mode == ORC_KDE_MANY_1D) {
         for (int32_t k = 0; k < npix; k++) {
             double S = c->sky_S[c->pix_off[ev] + k];
-            kde_grid(c, ev, k, z, w, v, b, K);
+            kde_grid(c, ev, k, z, w, v, b, binned, K);
             galaxy_profile_dv(c, ev, k, dv, G);
             double s = 0.0;
             for (int64_t a = 0; a < nz; a++) s += grid_w(c, a) * K[a] * F[a] * G[a];
             I += S * s;
         }
     } else {
-        kde_grid(c, ev, -1, z, w, v, b, K);
+        kde_grid(c, ev, -1, z, w, v, b, binned, K);
         for (int32_t k = 0; k < npix; k++) {
             double S = c->sky_S[c->pix_off[ev] + k];
             galaxy_profile_dv(c, ev, k, dv, G);
@@ -426,15 +504,25 @@ static double event_lnI_impl(const orc_catalog *c, const double *th, int64_t ev,
     return (I > 0.0 && isfinite(I)) ? log(I) : -INFINITY;
 }
 
-int orc_event_lnI(const orc_catalog *c, const double *th, int64_t ev,
-                  const orc_hooks *hk, double *lnI) {
+static int event_lnI_entry(const orc_catalog *c, const double *th, int64_t ev,
+                           const orc_hooks *hk, int binned, double *lnI) {
     if (!hk) hk = &default_hooks;
     double *F = malloc(sizeof(double) * c->n_z), *dv = malloc(sizeof(double) * c->n_z);
     orc_grid_factor(c, th, hk, F);
     grid_dvdz(c, th, hk, dv);
-    *lnI = event_lnI_impl(c, th, ev, hk, F, dv);
+    *lnI = event_lnI_impl(c, th, ev, hk, F, dv, binned);
     free(F); free(dv);
     return isfinite(*lnI) ? 0 : 1;
+}
+
+int orc_event_lnI(const orc_catalog *c, const double *th, int64_t ev,
+                  const orc_hooks *hk, double *lnI) {
+    return event_lnI_entry(c, th, ev, hk, 0, lnI);
+}
+
+int orc_event_lnI_binned(const orc_catalog *c, const double *th, int64_t ev,
+                         const orc_hooks *hk, double *lnI) {
+    return event_lnI_entry(c, th, ev, hk, 1, lnI);
 }
 
 /* Neumaier compensated sum                                                */
@@ -488,9 +576,9 @@ int orc_selection(const orc_catalog *c, const double *th, const orc_hooks *hk,
 }
 
 /* ln L = sum_i ln I_i - N_obs ln xi                          (Eq. hyperlike) */
-int orc_loglike(const orc_catalog *c, const double *th, const orc_hooks *hk,
-                int nthreads, double *lnL, double *lnI_out, double *xi_out,
-                double *neff_out, int32_t *status) {
+static int loglike_impl(const orc_catalog *c, const double *th, const orc_hooks *hk,
+                        int nthreads, int binned, double *lnL, double *lnI_out, double *xi_out,
+                        double *neff_out, int32_t *status) {
     if (!hk) hk = &default_hooks;
     int64_t ne = c->n_events;
     *status = ORC_OK;
@@ -506,7 +594,7 @@ int orc_loglike(const orc_catalog *c, const double *th, const orc_hooks *hk,
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
-    for (int64_t i = 0; i < ne; i++) lnI[i] = event_lnI_impl(c, th, i, hk, F, dv);
+    for (int64_t i = 0; i < ne; i++) lnI[i] = event_lnI_impl(c, th, i, hk, F, dv, binned);
     double xi, neff;
     orc_selection(c, th, hk, nthreads, &xi, &neff, NULL);
     int bad = !(xi > 0.0);
@@ -519,4 +607,16 @@ int orc_loglike(const orc_catalog *c, const double *th, const orc_hooks *hk,
     if (neff_out) *neff_out = neff;
     free(lnI); free(F); free(dv);
     return 0;
+}
+
+int orc_loglike(const orc_catalog *c, const double *th, const orc_hooks *hk,
+                int nthreads, double *lnL, double *lnI_out, double *xi_out,
+                double *neff_out, int32_t *status) {
+    return loglike_impl(c, th, hk, nthreads, 0, lnL, lnI_out, xi_out, neff_out, status);
+}
+
+int orc_loglike_binned(const orc_catalog *c, const double *th, const orc_hooks *hk,
+                       int nthreads, double *lnL, double *lnI_out, double *xi_out,
+                       double *neff_out, int32_t *status) {
+    return loglike_impl(c, th, hk, nthreads, 1, lnL, lnI_out, xi_out, neff_out, status);
 }

@@ -95,6 +95,19 @@ int orc_grid_factor(const orc_catalog *c, const double *th,
 int orc_event_lnI(const orc_catalog *c, const double *th, int64_t ev,
                   const orc_hooks *hk, double *lnI);
 
+/* ---- binned KDE option (Sec. 2.3: the weighted samples are binned) ----
+ * Reading: linear binning onto the grid lattice z_b = b dz; the KDE of the
+ * bins keeps the bandwidth, normalisation and support of the samples' KDE.
+ * orc_linear_bins returns the number of sample parts outside [b0, b0+nb). */
+int64_t orc_linear_bins(int64_t n, const double *z, const double *w, double dz,
+                        int64_t b0, int64_t nb, double *cb);
+int orc_kde_arrays(int64_t n, const double *z, const double *w, double b, int64_t nz,
+                   double z_max, int32_t binned, double *K);
+int orc_event_kde_binned(const orc_catalog *c, const double *th, int64_t ev,
+                         int32_t pixel, double *K);
+int orc_event_lnI_binned(const orc_catalog *c, const double *th, int64_t ev,
+                         const orc_hooks *hk, double *lnI);
+
 /* ---- selection (Eq. bias, injection sum and N_eff) ---- */
 int orc_selection(const orc_catalog *c, const double *th, const orc_hooks *hk,
                   int nthreads, double *xi, double *neff, double *s_out);
@@ -103,6 +116,9 @@ int orc_selection(const orc_catalog *c, const double *th, const orc_hooks *hk,
 int orc_loglike(const orc_catalog *c, const double *th, const orc_hooks *hk,
                 int nthreads, double *lnL, double *lnI, double *xi,
                 double *neff, int32_t *status);
+int orc_loglike_binned(const orc_catalog *c, const double *th, const orc_hooks *hk,
+                       int nthreads, double *lnL, double *lnI, double *xi,
+                       double *neff, int32_t *status);
 
 #ifdef __cplusplus
 }

@@ -302,18 +302,14 @@ __device__ void bsum(double (&v)[NV], double *red) {
     __syncthreads();
 }
 
-// Per (event, hyperpoint): d ln I_i / d theta (12).  FP64 follows the FP64
-// forward kernel (inversion with Newton polish, +-9 b windows, FP64 profile)
-// in double; MIXED follows the mixed forward kernel (FP32 inverse table and
-// mass model, +-6 b windows, its FP32 bandwidth, FP32 profile and grid
-// factor) in float, with the per-thread sums carried to double for the
-// block reduction, so that the gradient is that of the computed ln L.
-template <bool F64>
-__global__ void __launch_bounds__(ADJ_THREADS, F64 ? 1 : 3) k_event_adj(DevCatalog c, CallPtrs p, AdjPtrs q, int H) {
-    using T = typename std::conditional<F64, double, float>::type;
+// Per (event, hyperpoint) on the FP64 path: d ln I_i / d theta (12),
+// following the FP64 forward kernel (inversion with Newton polish, +-9 b
+// windows, FP64 profile) in double, so that the gradient is that of the
+// computed ln L.
+__global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtrs p, AdjPtrs q, int H) {
     extern __shared__ double sh[];
-    T *zs = reinterpret_cast<T *>(sh);
-    T *ws = zs + c.max_ns;
+    double *zs = sh;
+    double *ws = zs + c.max_ns;
     const int segn = (c.max_seg + 2) & ~1;
     int *segv = reinterpret_cast<int *>(ws + c.max_ns);
     int *sA0 = segv + segn;   // first grid point of each segment's KDE support
@@ -329,81 +325,41 @@ __global__ void __launch_bounds__(ADJ_THREADS, F64 ? 1 : 3) k_event_adj(DevCatal
         if (tid < 12) out[tid] = 0.0;
         return;
     }
-    // grid factor x trapezoid weight, staged in shared memory on the FP32
-    // path (F / F_scale: every term carries the same scale); read from the
-    // FP64 table on the FP64 path, whose block already holds double samples
-    float *Fw32 = reinterpret_cast<float *>(red + (ADJ_THREADS / 32 + 1) * 28);
-    auto Fw = [&](int a) -> T {
-        if constexpr (F64) {
-            return ((a == 0 || a == c.n_z - 1) ? 0.5 : 1.0) * p.F64[(size_t)h * c.n_z + a];
-        } else {
-            return Fw32[a];
-        }
+    // grid factor x trapezoid weight
+    auto Fw = [&](int a) -> double {
+        return ((a == 0 || a == c.n_z - 1) ? 0.5 : 1.0) * p.F64[(size_t)h * c.n_z + a];
     };
-
     const int64_t s0 = c.ev_soff[ev];
     const int ns = (int)(c.ev_soff[ev + 1] - s0);
-    const T KW = F64 ? T(KW64) : T(KW32);
-    const T TINF = F64 ? T(CUDART_INF) : T(CUDART_INF_F);
-    const MixParams mp = mix_params(hp);
-    const float4 *inv = p.inv32 + (size_t)h * NU;
-
-    if (!F64)
-        for (int a = tid; a < c.n_z; a += ADJ_THREADS)
-            Fw32[a] = ((a == 0 || a == c.n_z - 1) ? 0.5f : 1.f) * p.F32[(size_t)h * c.n_z + a];
-    // ---- z_j, w_j exactly as the forward kernel of this precision
+    const double KW = KW64;
+    // ---- z_j, w_j exactly as the FP64 forward kernel
     for (int j = tid; j < ns; j += ADJ_THREADS) {
-        T z = TINF, w = T(0);
-        if (F64) {
-            double zz;
-            if (invert64(c, p, h, hp, c.sd64[s0 + j], &zz)) {
-                z = T(zz);
-                w = T(mass_weight64(hp, c.beta, c.sm1_64[s0 + j] / (1.0 + zz), c.sm2_64[s0 + j] / (1.0 + zz)));
-            }
-        } else {
-            float4 sv = c.s32[s0 + j];
-            int k = __float_as_int(sv.x);
-            if ((k < mp.kv) || (k == mp.kv && sv.y <= mp.fv)) {
-                float zz = chimd::hermite4(inv[k], sv.y);
-                if (zz < CUDART_INF_F) {
-                    z = T(zz);
-                    float lz = __log2f(1.f + zz);
-                    w = T(mass_weight32(mp, sv.z - lz, sv.w - lz));
-                }
-            }
+        double z = CUDART_INF, w = 0.0, zz;
+        if (invert64(c, p, h, hp, c.sd64[s0 + j], &zz)) {
+            z = zz;
+            w = mass_weight64(hp, c.beta, c.sm1_64[s0 + j] / (1.0 + zz), c.sm2_64[s0 + j] / (1.0 + zz));
         }
         zs[j] = z;
         ws[j] = w;
     }
     __syncthreads();
-    // moments (two-pass): per-thread sums in the path's precision, block
-    // sums in double
-    double m5[5];  // W1, Wz, W2, n_valid, Sz
-    {
-        T t5[5] = {T(0), T(0), T(0), T(0), T(0)};
-        for (int j = tid; j < ns; j += ADJ_THREADS)
-            if (zs[j] < TINF) {
-                const T z = zs[j], w = ws[j];
-                t5[0] += w; t5[1] += w * z; t5[2] += w * w; t5[3] += T(1); t5[4] += z;
-            }
-        for (int k = 0; k < 5; k++) m5[k] = t5[k];
-    }
+    // ---- moments (two-pass) and Scott's rule
+    double m5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // W1, Wz, W2, n_valid, Sz
+    for (int j = tid; j < ns; j += ADJ_THREADS)
+        if (zs[j] < CUDART_INF) {
+            const double z = zs[j], w = ws[j];
+            m5[0] += w; m5[1] += w * z; m5[2] += w * w; m5[3] += 1.0; m5[4] += z;
+        }
     bsum<5>(m5, red);
     const double W1 = m5[0], W2 = m5[2], nv = m5[3];
     const double Mw = W1 > 0.0 ? m5[1] / W1 : 0.0, Mu = nv > 0.0 ? m5[4] / nv : 0.0;
-    double m2v[2];
-    {
-        const T Mwv = T(Mw), Muv = T(Mu);
-        T t2[2] = {T(0), T(0)};
-        for (int j = tid; j < ns; j += ADJ_THREADS)
-            if (zs[j] < TINF) {
-                const T z = zs[j], w = ws[j];
-                t2[0] += w * (z - Mwv) * (z - Mwv);
-                t2[1] += (z - Muv) * (z - Muv);
-            }
-        m2v[0] = t2[0];
-        m2v[1] = t2[1];
-    }
+    double m2v[2] = {0.0, 0.0};
+    for (int j = tid; j < ns; j += ADJ_THREADS)
+        if (zs[j] < CUDART_INF) {
+            const double z = zs[j], w = ws[j];
+            m2v[0] += w * (z - Mw) * (z - Mw);
+            m2v[1] += (z - Mu) * (z - Mu);
+        }
     bsum<2>(m2v, red);
     const double varw = W1 > 0.0 ? m2v[0] / W1 : 0.0, neffw = W1 > 0.0 ? W1 * W1 / W2 : 0.0;
     const double varu = nv > 0.0 ? m2v[1] / nv : 0.0;
@@ -419,7 +375,6 @@ __global__ void __launch_bounds__(ADJ_THREADS, F64 ? 1 : 3) k_event_adj(DevCatal
         rule = 2;
         b = c.dz;
     }
-    if (!F64) b = p.bw[(size_t)h * c.n_events + ev];  // the forward kernel's FP32 bandwidth
 
     // segment valid counts
     const int sg0 = c.ev_segoff[ev], nseg = c.ev_segoff[ev + 1] - sg0;
@@ -428,7 +383,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, F64 ? 1 : 3) k_event_adj(DevCatal
         int l = lo, r = hi;
         while (l < r) {
             int m = (l + r) >> 1;
-            if (zs[m] < TINF) l = m + 1; else r = m;
+            if (zs[m] < CUDART_INF) l = m + 1; else r = m;
         }
         segv[k] = l - lo;
     }
@@ -436,19 +391,15 @@ __global__ void __launch_bounds__(ADJ_THREADS, F64 ? 1 : 3) k_event_adj(DevCatal
 
     // ---- per-sample derivatives: bandwidth gradient and the sample sums
     const int nz = c.n_z;
-    const T dz = T(c.dz), bt = T(b), ib = T(1) / bt;
-    const T cw0 = T(W1 > 0.0 ? 1.0 / (W1 * varw) : 0.0), cw1 = T(W1 > 0.0 ? 2.0 / W1 : 0.0);
-    const T cw2 = T(W2 > 0.0 ? 2.0 / W2 : 0.0), cu = T(nv > 0.0 && varu > 0.0 ? 1.0 / (nv * varu) : 0.0);
-    const T Mwt = T(Mw), Mut = T(Mu), varwt = T(varw);
-    auto Gv = [&](int64_t row, int a) -> T {
-        return F64 ? T(reinterpret_cast<const double *>(p.prof[h])[row * nz + a])
-                   : T(reinterpret_cast<const float *>(p.prof[h])[row * nz + a]);
-    };
+    const double dz = c.dz, ib = 1.0 / b;
+    const double cw0 = W1 > 0.0 ? 1.0 / (W1 * varw) : 0.0, cw1 = W1 > 0.0 ? 2.0 / W1 : 0.0;
+    const double cw2 = W2 > 0.0 ? 2.0 / W2 : 0.0, cu = nv > 0.0 && varu > 0.0 ? 1.0 / (nv * varu) : 0.0;
+    const double *prof = reinterpret_cast<const double *>(p.prof[h]);
+    auto Gv = [&](int64_t row, int a) -> double { return prof[row * nz + a]; };
     const MassDer<double> md64 = mass_der64(hp, hd, c.beta);
-    const MassDer<float> md32 = mass_der32(hp, hd);
-    T A9[9], B4[4], db9[9], S2t = T(0), I0 = T(0);
-    for (int k = 0; k < 9; k++) { A9[k] = T(0); db9[k] = T(0); }
-    for (int k = 0; k < 4; k++) B4[k] = T(0);
+    double A9[9], B4[4], db9[9], S2t = 0.0, I0 = 0.0;
+    for (int k = 0; k < 9; k++) { A9[k] = 0.0; db9[k] = 0.0; }
+    for (int k = 0; k < 4; k++) B4[k] = 0.0;
     for (int j = tid; j < ns; j += ADJ_THREADS) {
         int l = 0, r = nseg;  // segment of j
         while (r - l > 1) {
@@ -457,71 +408,46 @@ __global__ void __launch_bounds__(ADJ_THREADS, F64 ? 1 : 3) k_event_adj(DevCatal
         }
         const int lo = (int)(c.seg_soff[sg0 + l] - s0);
         if (j - lo >= segv[l]) continue;
-        const T z = zs[j], w = ws[j], a1 = T(1) + z;
+        const double z = zs[j], w = ws[j], a1 = 1.0 + z;
         // dz/dtheta (linear between inverse-table nodes) and d ln w/dtheta
-        T dd[4], d5[5], dwz;
-        if (F64) {
+        double dd[4], d5[5], dwz;
+        {
             const double t = sqrt(c.sd64[s0 + j] / c.d_top) * NU;
             const int kk = min((int)t, NU - 1);
-            double ddd[4];
-            dz_interp(q, h, kk, t - kk, ddd);
-            for (int k = 0; k < 4; k++) dd[k] = T(ddd[k]);
-        } else {
-            {  // the sample's inverse-table cell and offset, as packed at load
-                const float4 sv = c.s32[s0 + j];
-                const int kk = __float_as_int(sv.x);
-                const float f = sv.y;
-                const float4 n0 = q.dznode32[(size_t)h * (NU + 1) + kk], n1 = q.dznode32[(size_t)h * (NU + 1) + kk + 1];
-                dd[0] = n0.x + f * (n1.x - n0.x);
-                dd[1] = n0.y + f * (n1.y - n0.y);
-                dd[2] = n0.z + f * (n1.z - n0.z);
-                dd[3] = n0.w + f * (n1.w - n0.w);
-            }
+            dz_interp(q, h, kk, t - kk, dd);
         }
-        if (F64) {
-            double e5[5], ez;
-            dlnpm_t<double>(md64, c.sm1_64[s0 + j] / double(a1), c.sm2_64[s0 + j] / double(a1), double(a1), e5, &ez);
-            for (int k = 0; k < 5; k++) d5[k] = T(e5[k]);
-            dwz = T(ez);
-        } else {
-            const float4 sv = c.s32[s0 + j];
-            const float lz = __log2f(float(a1));
-            float e5[5], ez;
-            dlnpm_t<float>(md32, ex2(sv.z - lz), ex2(sv.w - lz), float(a1), e5, &ez);
-            for (int k = 0; k < 5; k++) d5[k] = T(e5[k]);
-            dwz = T(ez);
-        }
-        T dlw[9];
+        dlnpm_t<double>(md64, c.sm1_64[s0 + j] / a1, c.sm2_64[s0 + j] / a1, a1, d5, &dwz);
+        double dlw[9];
         for (int k = 0; k < 4; k++) dlw[k] = dwz * dd[k];
         for (int k = 0; k < 5; k++) dlw[4 + k] = d5[k];
         // Scott's rule: d ln b = sum_j (dlnb/dw_j) w_j dln w_j + (dlnb/dz_j) dz_j
         if (rule == 0) {
-            const T cw = T(0.5) * ((z - Mwt) * (z - Mwt) - varwt) * cw0 - T(0.2) * (cw1 - w * cw2);
-            const T cz = w * (z - Mwt) * cw0;
-            for (int k = 0; k < 9; k++) db9[k] += cw * w * dlw[k] + (k < 4 ? cz * dd[k] : T(0));
+            const double cw = 0.5 * ((z - Mw) * (z - Mw) - varw) * cw0 - 0.2 * (cw1 - w * cw2);
+            const double cz = w * (z - Mw) * cw0;
+            for (int k = 0; k < 9; k++) db9[k] += cw * w * dlw[k] + (k < 4 ? cz * dd[k] : 0.0);
         } else if (rule == 1) {
-            const T cz = (z - Mut) * cu;
+            const double cz = (z - Mu) * cu;
             for (int k = 0; k < 4; k++) db9[k] += cz * dd[k];
         }
-        if (w == T(0)) continue;
+        if (w == 0.0) continue;
         // window sums S0, S1, S2 of e = exp(-u^2/2) H, u = (z_a - z)/b
-        const T pf = T(c.seg_pf[sg0 + l]);
+        const double pf = c.seg_pf[sg0 + l];
         const int64_t row = c.kde_mode == CHIMERA_KDE_MANY_1D ? (int64_t)(sg0 + l) : (int64_t)ev;
-        const T smin = zs[lo] - T(KDE_MARGIN) * bt, smax = zs[lo + segv[l] - 1] + T(KDE_MARGIN) * bt;
-        const T a0 = fmax(ceil((z - KW * bt) / dz), ceil(smin / dz));
-        const T aa1 = fmin(floor((z + KW * bt) / dz), floor(smax / dz));
-        const int ia0 = a0 < T(0) ? 0 : (a0 > T(nz) ? nz : (int)a0);
-        const int ia1 = aa1 > T(nz - 1) ? nz - 1 : (aa1 < T(-1) ? -1 : (int)aa1);
-        T S0 = T(0), S1 = T(0), S2 = T(0);
+        const double smin = zs[lo] - KDE_MARGIN * b, smax = zs[lo + segv[l] - 1] + KDE_MARGIN * b;
+        const double a0 = fmax(ceil((z - KW * b) / dz), ceil(smin / dz));
+        const double aa1 = fmin(floor((z + KW * b) / dz), floor(smax / dz));
+        const int ia0 = a0 < 0.0 ? 0 : (a0 > nz ? nz : (int)a0);
+        const int ia1 = aa1 > nz - 1 ? nz - 1 : (aa1 < -1.0 ? -1 : (int)aa1);
+        double S0 = 0.0, S1 = 0.0, S2 = 0.0;
         for (int a = ia0; a <= ia1; a++) {
-            const T Hh = Fw(a) * Gv(row, a);
-            const T u = (T(a) * dz - z) * ib;
-            const T e = (F64 ? T(exp(-0.5 * double(u * u))) : T(__expf(-0.5f * float(u * u)))) * Hh;
+            const double Hh = Fw(a) * Gv(row, a);
+            const double u = (a * dz - z) * ib;
+            const double e = exp(-0.5 * u * u) * Hh;
             S0 += e;
             S1 += e * u;
             S2 += e * u * u;
         }
-        const T pw = pf * w;
+        const double pw = pf * w;
         I0 += pw * S0;
         S2t += pw * S2;
         for (int k = 0; k < 9; k++) A9[k] += pw * S0 * dlw[k];
@@ -533,7 +459,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, F64 ? 1 : 3) k_event_adj(DevCatal
         const int lo = (int)(c.seg_soff[sg0 + l] - s0), cnt = segv[l];
         int alo = 0, len = 0;
         if (cnt > 0) {
-            const T smin = zs[lo] - T(KDE_MARGIN) * bt, smax = zs[lo + cnt - 1] + T(KDE_MARGIN) * bt;
+            const double smin = zs[lo] - KDE_MARGIN * b, smax = zs[lo + cnt - 1] + KDE_MARGIN * b;
             alo = max(0, (int)ceil(smin / dz));
             len = max(0, min(nz - 1, (int)floor(smax / dz)) - alo + 1);
         }
@@ -556,8 +482,8 @@ __global__ void __launch_bounds__(ADJ_THREADS, F64 ? 1 : 3) k_event_adj(DevCatal
         if (tid == 0) scum[0] = 0;
     }
     __syncthreads();
-    T C8[8];  // 7 d ln F terms + the galaxy Om term
-    for (int k = 0; k < 8; k++) C8[k] = T(0);
+    double C8[8];  // 7 d ln F terms + the galaxy Om term
+    for (int k = 0; k < 8; k++) C8[k] = 0.0;
     const int nitems = scum[nseg];
     for (int it = tid; it < nitems; it += ADJ_THREADS) {
         int l = 0, r = nseg;  // the segment: last l with scum[l] <= it
@@ -567,33 +493,26 @@ __global__ void __launch_bounds__(ADJ_THREADS, F64 ? 1 : 3) k_event_adj(DevCatal
         }
         const int lo = (int)(c.seg_soff[sg0 + l] - s0), cnt = segv[l];
         const int a = sA0[l] + (it - scum[l]);
-        const T pf = T(c.seg_pf[sg0 + l]);
+        const double pf = c.seg_pf[sg0 + l];
         const int64_t row = c.kde_mode == CHIMERA_KDE_MANY_1D ? (int64_t)(sg0 + l) : (int64_t)ev;
-        const T za = T(a) * dz;
+        const double za = a * dz;
         // samples whose window covers a: |z - za| <= KW b
         int jl = lo, jr = lo + cnt;
         while (jl < jr) {
             const int m = (jl + jr) >> 1;
-            if (zs[m] < za - KW * bt) jl = m + 1; else jr = m;
+            if (zs[m] < za - KW * b) jl = m + 1; else jr = m;
         }
-        T K = T(0);
-        for (int j = jl; j < lo + cnt && zs[j] <= za + KW * bt; j++) {
-            const T u = (za - zs[j]) * ib;
-            K += ws[j] * (F64 ? T(exp(-0.5 * double(u * u))) : T(__expf(-0.5f * float(u * u))));
+        double K = 0.0;
+        for (int j = jl; j < lo + cnt && zs[j] <= za + KW * b; j++) {
+            const double u = (za - zs[j]) * ib;
+            K += ws[j] * exp(-0.5 * u * u);
         }
-        if (K == T(0)) continue;
-        const T FK = pf * Fw(a) * K;
-        const T M = FK * Gv(row, a);
-        if (F64) {
-            const double *Qa = q.Q + ((size_t)h * nz + a) * 7;
-            for (int k = 0; k < 7; k++) C8[k] += M * T(Qa[k]);
-        } else {
-            const float4 *Qa = reinterpret_cast<const float4 *>(q.Q32 + ((size_t)h * nz + a) * 8);
-            const float4 qa = Qa[0], qb = Qa[1];
-            C8[0] += M * qa.x; C8[1] += M * qa.y; C8[2] += M * qa.z; C8[3] += M * qa.w;
-            C8[4] += M * qb.x; C8[5] += M * qb.y; C8[6] += M * qb.z;
-        }
-        C8[7] += FK * T(q.dprof[h][row * nz + a]);
+        if (K == 0.0) continue;
+        const double FK = pf * Fw(a) * K;
+        const double M = FK * Gv(row, a);
+        const double *Qa = q.Q + ((size_t)h * nz + a) * 7;
+        for (int k = 0; k < 7; k++) C8[k] += M * Qa[k];
+        C8[7] += FK * q.dprof[h][row * nz + a];
     }
     // ---- block sums (double) and the 12 derivatives
     double v[28];
@@ -1262,8 +1181,8 @@ void launch_adjoint(const DevCatalog &c, const CallPtrs &p, const AdjPtrs &q, in
     const size_t smem = adjoint_event_smem(c, fp64);
     const unsigned nb = (unsigned)((int64_t)c.n_events * H);
     if (fp64) {
-        cudaFuncSetAttribute(k_event_adj<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (nb) k_event_adj<true><<<nb, ADJ_THREADS, smem, st>>>(c, p, q, H);
+        cudaFuncSetAttribute(k_event_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (nb) k_event_adj<<<nb, ADJ_THREADS, smem, st>>>(c, p, q, H);
         if (p.n_chunk) k_select_adj<true><<<dim3(p.n_chunk, H), ADJ_THREADS, 0, st>>>(c, p, q, H);
     } else {
         cudaFuncSetAttribute(k_event_adj_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

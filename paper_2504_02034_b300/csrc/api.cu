@@ -382,7 +382,8 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
             const int h0 = t * tile, nh = std::min(tile, H - h0);
             launch_reweight(c, p, h0, nh, ws.st);
             if (ws.trace) CK(cudaEventRecord(ws.tile_ev[2 * t], ws.st));
-            launch_event_mixed(c, p, h0, nh, ws.st);
+            if (precision == CHIMERA_MIXED_BINNED) launch_event_binned(c, p, h0, nh, ws.st);
+            else launch_event_mixed(c, p, h0, nh, ws.st);
             if (ws.trace) CK(cudaEventRecord(ws.tile_ev[2 * t + 1], ws.st));
         }
     }
@@ -818,7 +819,8 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     // event kernels need their shared memory
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx.device);
-    if ((int)event_mixed_smem(c) > maxsm || (int)event_fp64_smem(c) > maxsm) {
+    if ((int)event_mixed_smem(c) > maxsm || (int)event_fp64_smem(c) > maxsm ||
+        (int)event_binned_smem(c) > maxsm) {
         for (void *a : cat->allocs) cudaFree(a);
         ctx.used -= cat->bytes;
         set_error("catalog needs more shared memory per block than the device offers");
@@ -963,7 +965,10 @@ int chimera_catalog_info(chimera_ctx *h, int32_t id, chimera_catalog_info_t *inf
 static int check_call(chimera_ctx *h, int32_t n, const void *theta, int32_t prec, const void *out) {
     if (!h || !theta || !out) { set_error("null argument"); return CHIMERA_ERR_INVALID_ARG; }
     if (n <= 0) { set_error("n_points must be positive"); return CHIMERA_ERR_INVALID_ARG; }
-    if (prec != CHIMERA_FP64 && prec != CHIMERA_MIXED) { set_error("bad precision"); return CHIMERA_ERR_INVALID_ARG; }
+    if (prec != CHIMERA_FP64 && prec != CHIMERA_MIXED && prec != CHIMERA_MIXED_BINNED) {
+        set_error("bad precision");
+        return CHIMERA_ERR_INVALID_ARG;
+    }
     return CHIMERA_OK;
 }
 
@@ -1036,6 +1041,10 @@ int chimera_terms(chimera_ctx *h, int32_t id, int32_t n, const double *theta, in
 int chimera_grad(chimera_ctx *h, int32_t id, int32_t n, const double *theta, int32_t prec,
                  double *lnL, double *dlnL, int32_t *status) {
     RC(check_call(h, n, theta, prec, lnL));
+    if (prec == CHIMERA_MIXED_BINNED) {
+        set_error("the adjoint follows the unbinned KDE: use CHIMERA_FP64 or CHIMERA_MIXED");
+        return CHIMERA_ERR_INVALID_ARG;
+    }
     if (!dlnL) { set_error("dlnL is NULL"); return CHIMERA_ERR_INVALID_ARG; }
     Ctx &ctx = h->c;
     std::lock_guard<std::recursive_mutex> lk(ctx.mu);

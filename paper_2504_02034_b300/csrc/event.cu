@@ -611,6 +611,153 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
     }
 }
 
+// ------------------------------------------------------------ binned ---
+// K4 (mixed, binned-KDE option; Sec. 2.3: the weighted samples of each
+// pixel, or of the whole event in single-1D, are binned).  Reading: linear
+// binning onto the grid lattice z_n = n dz, then the Gaussian KDE of the
+// nodes with the samples' bandwidth, windows (+-KW32 b) and support:
+//   I = sum_k pf_k sum_n c_kn sum_a C_{|a-n|} F'(z_a) G_k(z_a),
+//   c_kn = sum_{j in k} w_j max(0, 1 - |z_j / dz - n|),  C_m = exp(-(m dz)^2 / 2b^2),
+// in the mixed kernel's units (raw I).  The work per segment is
+// (nodes) x (window) instead of (samples) x (window), which pays where a
+// segment holds many more samples than grid points under its samples
+// (single-1D).  One thread per node gathers the node's weight from the
+// segment's samples in sample order (sorted by z), so the sums are
+// deterministic, then runs the node's window over the segment's staged
+// H = F' G (consecutive nodes across a warp read consecutive H entries;
+// the C entry is a broadcast).
+constexpr int BN_THREADS = 256;
+constexpr int BN_HPAD = 4;  // zero entries staged on each side of a segment's support
+
+struct BinLayout {
+    int ns_pad, nz_pad, seg_pad;
+    __host__ __device__ BinLayout(int max_ns, int nz, int max_seg)
+        : ns_pad((max_ns + 3) & ~3), nz_pad((nz + 2 * BN_HPAD + 3) & ~3), seg_pad((max_seg + 4) & ~3) {}
+    // floats: zs, ws, F', H (padded), C table (2 n_z entries), segment
+    // prefactors, block sums; ints: segment starts, valid counts
+    __host__ __device__ size_t bytes() const {
+        return sizeof(float) * (2 * (size_t)ns_pad + 4 * (size_t)nz_pad + seg_pad + BN_THREADS / 32) +
+               sizeof(int) * 2 * (size_t)seg_pad;
+    }
+};
+
+__global__ void __launch_bounds__(BN_THREADS) k_event_binned(DevCatalog c, CallPtrs p, int h0, int nh) {
+    extern __shared__ float4 bsm4[];
+    const BinLayout L(c.max_ns, c.n_z, c.max_seg);
+    float *zs = reinterpret_cast<float *>(bsm4);
+    float *ws = zs + L.ns_pad;
+    float *Fs = ws + L.ns_pad;
+    float *Hs = Fs + L.nz_pad;      // H[a] at Hs[a + BN_HPAD]
+    float *Ct = Hs + L.nz_pad;      // C_m, m < 2 nz_pad
+    float *segpf = Ct + 2 * L.nz_pad;
+    float *redf = segpf + L.seg_pad;
+    int *seglo = reinterpret_cast<int *>(redf + BN_THREADS / 32);
+    int *segv = seglo + L.seg_pad;
+
+    const int hl = blockIdx.x % nh, h = h0 + hl;
+    const int4 ei = __ldg(c.ev_info + 2 * (blockIdx.x / nh));      // (ev, s0, ns, zoff)
+    const int4 ej = __ldg(c.ev_info + 2 * (blockIdx.x / nh) + 1);  // (g0, ngroups, sg0, nseg)
+    const int ev = ei.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const size_t out = (size_t)h * c.n_events + ev;
+    const HP &hp = p.hp[h];
+    if (hp.status & (CHIMERA_PT_OUT_OF_SUPPORT | CHIMERA_PT_NONMONOTONE)) {
+        if (tid == 0) { p.lnI[out] = 0.0; p.bw[out] = 0.0; }
+        return;
+    }
+    const int nz = c.n_z;
+    const float dz = c.dz32, inv_dz = 1.f / dz;
+    const int ns = ei.z, sg0 = ej.z, nseg = ej.w;
+    const int64_t s0 = ei.y;
+    {
+        const float *zsrc = p.zw + (size_t)hl * 2 * c.n_zpad + ei.w;
+        const float *wsrc = zsrc + c.n_zpad;
+        for (int i = tid; i < ns; i += BN_THREADS) {
+            zs[i] = __ldg(zsrc + i);
+            ws[i] = __ldg(wsrc + i);
+        }
+    }
+    for (int a = tid; a < nz; a += BN_THREADS)
+        Fs[a] = ((a == 0 || a == nz - 1) ? 0.5f : 1.f) * p.F32[(size_t)h * nz + a];
+    for (int k = tid; k <= nseg; k += BN_THREADS) {
+        seglo[k] = (int)(c.seg_soff[sg0 + k] - s0);
+        if (k < nseg) segpf[k] = (float)c.seg_pf[sg0 + k];
+    }
+    const double bd = p.bw[out];  // the reweighting kernel's FP32 bandwidth
+    const float b = (float)bd;
+    const float inv_s2b = 0.70710678f / b;
+    const int W = (int)fminf(KW32 * b * inv_dz, 1e8f);  // window half-width in nodes
+    const int nct = min(W + 1, 2 * L.nz_pad);
+    for (int m = tid; m < nct; m += BN_THREADS) {
+        const float x = m * dz * inv_s2b;
+        Ct[m] = __expf(-x * x);
+    }
+    __syncthreads();
+    for (int k = tid; k < nseg; k += BN_THREADS) {
+        int l = seglo[k], r = seglo[k + 1];
+        const int lo = l;
+        while (l < r) {
+            const int m = (l + r) >> 1;
+            if (zs[m] < CUDART_INF_F) l = m + 1; else r = m;
+        }
+        segv[k] = l - lo;
+    }
+    __syncthreads();
+    const float *prof = reinterpret_cast<const float *>(p.prof[h]);
+    float acc = 0.f;
+    for (int k = 0; k < nseg; k++) {
+        const int lo = seglo[k], cnt = segv[k];
+        if (cnt == 0) continue;
+        // the segment's KDE support (as the unbinned kernel) and its nodes
+        const int A0 = max(0, (int)ceilf((zs[lo] - (float)KDE_MARGIN * b) * inv_dz));
+        const int A1 = min(nz - 1, (int)floorf((zs[lo + cnt - 1] + (float)KDE_MARGIN * b) * inv_dz));
+        if (A0 > A1) continue;
+        const int N0 = (int)floorf(zs[lo] * inv_dz);
+        const int N1 = (int)fminf(floorf(zs[lo + cnt - 1] * inv_dz) + 1.f, (float)A1 + (float)W);
+        const int64_t row = c.kde_mode == CHIMERA_KDE_MANY_1D ? (int64_t)(sg0 + k) : (int64_t)ev;
+        const float *G = prof + row * nz;
+        for (int a = A0 - BN_HPAD + tid; a <= A1 + BN_HPAD; a += BN_THREADS)
+            Hs[a + BN_HPAD] = (a >= A0 && a <= A1) ? Fs[a] * __ldg(G + a) : 0.f;
+        __syncthreads();
+        const float pf = segpf[k];
+        for (int n = N0 + tid; n <= N1; n += BN_THREADS) {
+            // the node's weight: samples with floor(z / dz) in {n - 1, n}
+            int l = lo, r = lo + cnt;
+            while (l < r) {
+                const int m = (l + r) >> 1;
+                if (floorf(zs[m] * inv_dz) < (float)(n - 1)) l = m + 1; else r = m;
+            }
+            float cw = 0.f;
+            for (int j = l; j < lo + cnt; j++) {
+                const float t = zs[j] * inv_dz, fb = floorf(t);
+                if (fb > (float)n) break;
+                const float f = t - fb;
+                cw += fb == (float)n ? ws[j] * (1.f - f) : ws[j] * f;
+            }
+            if (cw == 0.f) continue;
+            const int a0 = max(A0, n - W), a1 = min(A1, n + W);
+            float sacc = 0.f;
+            for (int a = a0; a <= a1; a++) {
+                const int m = abs(a - n);
+                const float cm = m < nct ? Ct[m] : __expf(-(m * dz * inv_s2b) * (m * dz * inv_s2b));
+                sacc = fmaf(cm, Hs[a + BN_HPAD], sacc);
+            }
+            acc = fmaf(pf * cw, sacc, acc);
+        }
+        __syncthreads();  // Hs is restaged for the next segment
+    }
+    // fixed-order FP32 tree sum; the combine kernel takes the FP64 log
+    acc = warp_sum(acc);
+    if (lane == 0) redf[wid] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        float I = 0.f;
+        for (int w = 0; w < BN_THREADS / 32; w++) I += redf[w];
+        p.lnI[out] = (double)I;
+        p.bw[out] = bd;
+    }
+}
+
 // ---------------------------------------------------------------- FP64 ---
 __global__ void __launch_bounds__(EV64_THREADS) k_event_fp64(DevCatalog c, CallPtrs p, int H) {
     extern __shared__ double sd[];
@@ -733,6 +880,15 @@ void launch_event_mixed(const DevCatalog &c, const CallPtrs &p, int h0, int nh, 
     cudaFuncSetAttribute(k_event_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const unsigned nb = (unsigned)((int64_t)c.n_events * nh);
     if (nb) k_event_mixed<<<nb, EV_THREADS, smem, st>>>(c, p, h0, nh);
+}
+
+size_t event_binned_smem(const DevCatalog &c) { return BinLayout(c.max_ns, c.n_z, c.max_seg).bytes(); }
+
+void launch_event_binned(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cudaStream_t st) {
+    size_t smem = event_binned_smem(c);
+    cudaFuncSetAttribute(k_event_binned, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const unsigned nb = (unsigned)((int64_t)c.n_events * nh);
+    if (nb) k_event_binned<<<nb, BN_THREADS, smem, st>>>(c, p, h0, nh);
 }
 
 void launch_event_fp64(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st) {

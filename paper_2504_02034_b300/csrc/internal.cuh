@@ -183,6 +183,10 @@ void launch_profile_sum(const DevCatalog &c, const double *G64, const float *G32
 void launch_reweight(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cudaStream_t st);
 void launch_event_mixed(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cudaStream_t st);
 void launch_event_fp64(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st);
+// K4 with the binned KDE (CHIMERA_MIXED_BINNED), from the same tile buffer
+// as launch_event_mixed.
+void launch_event_binned(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cudaStream_t st);
+size_t event_binned_smem(const DevCatalog &c);
 size_t event_mixed_smem(const DevCatalog &c);
 size_t event_fp64_smem(const DevCatalog &c);
 // K5: selection partial sums; K6: combine into ln L.

@@ -276,6 +276,47 @@ def grad_stats(pkg, ctx, cid, theta, NE, reps=3):
     return out
 
 
+def binned_stats(pkg, ctx, torch, dev, theta, steps):
+    """The binned-KDE option (CHIMERA_MIXED_BINNED) against the unbinned mixed
+    path on the benchmark catalog in its single-1D form (300 events x 5000
+    PE, one KDE per event), 16 hyperpoints per launch, device-timed as the
+    main step (CUDA events, L2 flushed between steps)."""
+    from synth import catalog as sc
+    cat = sc.config_catalog(2, kde_mode=sc.KDE_SINGLE_1D)
+    cid = ctx.load(cat)
+    H, NE = theta.shape[0], cat["n_events"]
+    th_dev = torch.tensor(theta, device=dev, dtype=torch.float64)
+    out = torch.empty(H, device=dev, dtype=torch.float64)
+    neff = torch.empty_like(out)
+    st = torch.empty(H, device=dev, dtype=torch.int32)
+    flush = torch.empty(256 << 20, device=dev, dtype=torch.uint8)
+    stream = torch.cuda.current_stream(dev)
+    res = {"catalog": "300 events x 5000 PE, single-1D KDE, 16 hyperpoints per launch"}
+    for name, prec in (("mixed", pkg.MIXED), ("binned", pkg.MIXED_BINNED)):
+        for _ in range(3):
+            pkg.chimera_loglike_device(ctx.h, cid, th_dev, prec, out, neff, st, stream)
+        torch.cuda.synchronize()
+        ms, ev_ms = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pkg.chimera_loglike_device(ctx.h, cid, th_dev, prec, out, neff, st, stream)
+            e1.record(stream)
+            ev_ms.append(pkg.chimera_stage_ms(ctx.h)["event"])
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = sum(ms) / len(ms)
+        res[name] = {"value": H * NE / (t * 1e-3), "unit": UNIT, "ms_per_step": t,
+                     "event_kernel_ms": sum(ev_ms) / len(ev_ms)}
+    lnL_b, _, _ = pkg.chimera_loglike(ctx.h, cid, theta, pkg.MIXED_BINNED)
+    lnL_m, _, _ = pkg.chimera_loglike(ctx.h, cid, theta, pkg.MIXED)
+    res["binned_over_mixed"] = res["binned"]["value"] / res["mixed"]["value"]
+    res["max_abs_delta_lnL"] = float(np.max(np.abs(lnL_b - lnL_m)))
+    ctx.unload(cid)
+    return res
+
+
 def serving_stream(pkg, ctx, bench_cid, bench_cat, n_req, seed=2504020345):
     """Request stream over four resident catalogs (spectroscopic 100 / 300 /
     1000 events at Xi0 = 0.6 / 1 / 1.8, photometric 5000 events x 4000 PE with
@@ -461,6 +502,7 @@ def main():
     fp64_val = NE * len(fp) / sum(fp)
 
     grads = grad_stats(pkg, ctx, cid, theta, NE)
+    binned = binned_stats(pkg, ctx, torch, dev, theta, max(3, args.steps // 2)) if rank == 0 else None
     serving = serving_stream(pkg, ctx, cid, cat, args.serve_requests) if args.serve_requests > 0 and rank == 0 else None
 
     kern = sum(kern_ms) / len(kern_ms)
@@ -497,6 +539,7 @@ def main():
         "mixed_over_fp64": value / ws / fp64_val,
         "stage_ms": mean_stage,
         "gradient": grads,
+        "binned_kde": binned,
         "serving": serving,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(theta.nbytes),
                 "d2h_bytes_per_step": int(H * (8 + 8 + 4))},

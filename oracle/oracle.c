@@ -20,6 +20,9 @@
  *  - selection: s_j carries the injection draw density and the homogeneous
  *    redshift prior dV_c/dz / V_c(z_max)                 (Eqs. bias, p-miss)
  *  - samples whose d_L lies beyond d_L^gw(z = 10) get weight 0.
+ *  - binned-KDE option (Sec. 2.3 bins the weighted samples): linear binning
+ *    onto the grid lattice z_n = n dz, then the KDE of the nodes with the
+ *    samples' bandwidth, normalisation and support
  */
 #include "oracle.h"
 

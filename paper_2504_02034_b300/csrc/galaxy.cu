@@ -164,7 +164,10 @@ __device__ __forceinline__ typename Gal<F64>::T gather_out(const typename Gal<F6
     return WITH_O ? norm * (dvO[a] * s1 - dv[a] * s2) : norm * s1 * dv[a];
 }
 
-// One block per pixel of at most GAL_DENSE galaxies, one grid point per thread.
+// One block per pixel of at most GAL_DENSE galaxies, one grid point per
+// thread; the pixel's galaxies (z, sigma, 1/Z, Z') are staged in shared
+// memory first, so the two binary searches and the gather of every grid
+// point read shared memory.
 template <bool F64, bool WITH_O>
 __global__ void __launch_bounds__(GAL_THREADS) k_gal_gather(DevCatalog c, const typename Gal<F64>::T *dv,
                                                            const typename Gal<F64>::T *dvO,
@@ -173,17 +176,37 @@ __global__ void __launch_bounds__(GAL_THREADS) k_gal_gather(DevCatalog c, const 
                                                            typename Gal<F64>::T *out) {
     using G = Gal<F64>;
     using T = typename G::T;
+    __shared__ T sz[GAL_DENSE], ss[GAL_DENSE], siz[GAL_DENSE], szo[WITH_O ? GAL_DENSE : 1];
     const int64_t p = blockIdx.x;
     const int64_t g0 = c.gal_off[p], g1 = c.gal_off[p + 1];
-    if (g1 - g0 > GAL_DENSE) return;  // the dense kernel's pixel
+    const int ng = (int)(g1 - g0);
+    if (ng > GAL_DENSE) return;  // the dense kernel's pixel
+    for (int i = threadIdx.x; i < ng; i += GAL_THREADS) {
+        G::read(c, p, g0 + i, sz[i], ss[i]);
+        siz[i] = invZ[g0 + i];
+        if (WITH_O) szo[i] = ZO[g0 + i];
+    }
+    __syncthreads();
     const int nz = c.n_z;
     const T dz = G::step(c), reach = G::reach(c, p);
     for (int a = threadIdx.x; a < nz; a += GAL_THREADS) {
         const T za = a * dz;
+        int l = 0, r = ng;  // first galaxy with z >= za - reach
+        while (l < r) {
+            const int m = (l + r) >> 1;
+            if (sz[m] < za - reach) l = m + 1; else r = m;
+        }
         T s1 = T(0), s2 = T(0);
-        const int64_t l = gal_bound<F64>(c, p, g0, g1, za - reach, false);
-        const int64_t r = gal_bound<F64>(c, p, l, g1, za + reach, true);
-        gather_range<F64, WITH_O>(c, p, a, l, r, 1, invZ, ZO, s1, s2);
+        for (int i = l; i < ng && sz[i] <= za + reach; i++) {
+            int lo, hi;
+            G::win(c, sz[i], ss[i], lo, hi);
+            const T iz = siz[i];
+            if (a < lo || a > hi || iz == T(0)) continue;
+            const T isg = T(1) / ss[i], u = (za - sz[i]) * isg;
+            const T Nv = isg * G::gauss(u);
+            s1 += Nv * iz;
+            if (WITH_O) s2 += Nv * szo[i] * iz * iz;
+        }
         out[p * nz + a] = gather_out<F64, WITH_O>(dv, dvO, a, s1, s2);
     }
 }

@@ -303,7 +303,8 @@ static bool admissible(const double *t) {
            t[8] > t[7] && t[11] > -1.0;
 }
 
-int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, int precision) {
+int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, int precision,
+            double *out_lnL, double *out_neff, int32_t *out_status) {
     RC(ws_ensure(ctx, ws, H, cat));
     ctx.tick++;
     const DevCatalog &c = cat.d;
@@ -390,6 +391,9 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
     if (ws.trace) CK(cudaEventRecord(ws.tev[3], ws.st));
     CK(cudaStreamWaitEvent(ws.st, ws.ev_join, 0));
     if (ws.trace) CK(cudaEventRecord(ws.tev[4], ws.st));
+    p.out_lnL = out_lnL;
+    p.out_neff = out_neff;
+    p.out_status = out_status;
     launch_combine(c, p, H, precision != CHIMERA_FP64, ws.st);
     if (ws.trace) CK(cudaEventRecord(ws.tev[5], ws.st));
     CK(cudaGetLastError());
@@ -930,6 +934,7 @@ void chimera_destroy(chimera_ctx *h) {
         if (e) cudaEventDestroy(e);
     for (auto &e : ctx.ws.tile_ev) cudaEventDestroy(e);
     ctx.ws.tile_ev.clear();
+    if (ctx.dev_done) cudaEventDestroy(ctx.dev_done);
     cudaStreamDestroy(ctx.stream);
     delete h;
 }
@@ -1005,17 +1010,11 @@ int chimera_loglike_device(chimera_ctx *h, int32_t id, int32_t n, const double *
     std::vector<double> th(12 * (size_t)n);
     CK(cudaMemcpyAsync(th.data(), theta_dev, sizeof(double) * 12 * n, cudaMemcpyDeviceToHost, us));
     CK(cudaStreamSynchronize(us));
-    RC(forward(ctx, *cat, ctx.ws, n, th.data(), prec));
-    cudaEvent_t ev;
-    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    cudaStream_t st = ctx.ws.st;
-    CallPtrs p = ctx.ws.ptrs(n, cat->d);
-    CK(cudaMemcpyAsync(lnL_dev, ctx.ws.lnL, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    if (neff_dev) CK(cudaMemcpyAsync(neff_dev, ctx.ws.neff, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    if (status_dev) CK(cudaMemcpyAsync(status_dev, p.status, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
-    CK(cudaEventRecord(ev, st));
-    CK(cudaStreamWaitEvent(us, ev, 0));
-    cudaEventDestroy(ev);
+    // the combine kernel writes the caller's buffers directly
+    RC(forward(ctx, *cat, ctx.ws, n, th.data(), prec, lnL_dev, neff_dev, status_dev));
+    if (!ctx.dev_done) CK(cudaEventCreateWithFlags(&ctx.dev_done, cudaEventDisableTiming));
+    CK(cudaEventRecord(ctx.dev_done, ctx.ws.st));
+    CK(cudaStreamWaitEvent(us, ctx.dev_done, 0));
     return CHIMERA_OK;
 }
 

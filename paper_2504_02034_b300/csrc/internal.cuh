@@ -148,6 +148,10 @@ struct CallPtrs {
     double *lnL, *neff, *xi;  // [H]
     int32_t *status;          // [H]
     unsigned long long *pairs;  // [H] windowed-pair counter, or nullptr
+    // caller buffers [H] that the combine kernel also fills (device entry
+    // point), or nullptr
+    double *out_lnL, *out_neff;
+    int32_t *out_status;
 };
 
 // ---- launch wrappers (host) ----

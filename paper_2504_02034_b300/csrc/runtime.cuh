@@ -30,7 +30,7 @@ struct FwdEntry {
 
 // Galaxy profile cache entry for one (Om, kind) of one catalog.  Kinds:
 // 0 FP64 profile, 1 FP32 profile of the stored galaxy values, 2 FP64 dG/dOm,
-// 3 FP64 dG/dOm of the stored galaxy values.
+// 3 FP32 dG/dOm of the stored galaxy values.
 struct ProfEntry {
     void *G = nullptr;   // [n_pix x n_z] double (kind 0) or float (kind 1)
     void *Gh = nullptr;  // single-1D: [n_events x n_z]
@@ -106,6 +106,7 @@ struct Server;
 struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaEvent_t dev_done = nullptr;  // device entry point: the caller's stream waits on it
     size_t budget = 0;
     std::atomic<size_t> used{0};
     std::recursive_mutex mu;
@@ -130,7 +131,10 @@ void ws_destroy_streams(Workspace &ws);
 // Forward pass for H points on workspace `ws` (enqueued on ws.st).
 // theta: host [H x 12].  Leaves lnL / neff / xi / status / lnI / bw on the
 // device in `ws`.  Returns a CHIMERA_ERR_* code.
-int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, int precision);
+// The forward pass; out_* (device, may be nullptr) also receive ln L, N_eff
+// and the status words from the combine kernel.
+int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, int precision,
+            double *out_lnL = nullptr, double *out_neff = nullptr, int32_t *out_status = nullptr);
 // Adjoint after forward() on the same workspace (reads the sanitised theta
 // and the forward tables forward() left there); leaves grad [H x 12].
 int backward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, int precision);

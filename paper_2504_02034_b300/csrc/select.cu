@@ -254,6 +254,9 @@ __global__ void __launch_bounds__(CMB_THREADS) k_combine(DevCatalog c, CallPtrs 
         p.neff[h] = neff;
         p.xi[h] = xi;
         p.status[h] = st;
+        if (p.out_lnL) p.out_lnL[h] = lnL;
+        if (p.out_neff) p.out_neff[h] = neff;
+        if (p.out_status) p.out_status[h] = st;
     }
 }
 

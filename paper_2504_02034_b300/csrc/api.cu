@@ -394,7 +394,7 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
     p.out_lnL = out_lnL;
     p.out_neff = out_neff;
     p.out_status = out_status;
-    launch_combine(c, p, H, precision != CHIMERA_FP64, ws.st);
+    launch_combine(c, p, H, ws.st);
     if (ws.trace) CK(cudaEventRecord(ws.tev[5], ws.st));
     CK(cudaGetLastError());
     return CHIMERA_OK;

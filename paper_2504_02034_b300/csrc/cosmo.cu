@@ -229,27 +229,46 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
         if (a < c.n_z) p.F32[(size_t)h * c.n_z + a] *= iFs;
     }
     if (blockIdx.x != 0) return;
-    __shared__ double sc[8];
+    // the FP64 scalars, one warp each (lane 0), so that their transcendental
+    // chains run side by side instead of serialised by divergence
+    __shared__ double sc[12];
     const double *th = p.theta + 12 * h;
     const double alpha = th[4], mu = th[5], sg = th[6], mmin = th[7], mmax = th[8];
     const double lam = c.lambda_g, beta = c.beta;
     const double cH = C_KMS / th[0];
-    if (t < 5) {
+    const int w = t >> 5;
+    if ((t & 31) == 0) {
         double v = 0.0;
-        if (t == 0)
-            v = fabs(1.0 - alpha) < 1e-12 ? log(mmax / mmin)
-                                          : (pow(mmax, 1.0 - alpha) - pow(mmin, 1.0 - alpha)) / (1.0 - alpha);
-        else if (t == 1)
-            v = std_normal_cdf((mmax - mu) / sg) - std_normal_cdf((mmin - mu) / sg);
-        else if (t == 2)
-            v = pow(mmin, 1.0 + beta);
-        else if (t == 3)
-            v = chimd::dc_hermite(p.fwd[h], c.z_max, th[1]);
-        else {  // d_L^gw at the end of the redshift range, z = 10, in FP64
-            double J;
-            chimd::dgw_J(K_Z10 * HT, cH * p.fwd[h][K_Z10], th, cH, &v, &J);
+        switch (w) {
+            case 0:
+                v = fabs(1.0 - alpha) < 1e-12 ? log(mmax / mmin)
+                                              : (pow(mmax, 1.0 - alpha) - pow(mmin, 1.0 - alpha)) / (1.0 - alpha);
+                break;
+            case 1: v = std_normal_cdf((mmax - mu) / sg) - std_normal_cdf((mmin - mu) / sg); break;
+            case 2: v = pow(mmin, 1.0 + beta); break;
+            case 3: v = chimd::dc_hermite(p.fwd[h], c.z_max, th[1]); break;
+            case 4: {  // d_L^gw at the end of the redshift range, z = 10, in FP64
+                double J;
+                chimd::dgw_J(K_Z10 * HT, cH * p.fwd[h][K_Z10], th, cH, &v, &J);
+                sc[8] = sqrt(v / c.d_top) * NU;  // its inverse-table coordinate
+                break;
+            }
+            case 5:
+                v = log(mmin);
+                sc[9] = log1p(th[11]);
+                break;
+            case 6:
+                v = log2(mmin);
+                sc[10] = 1.0 / sg;
+                break;
+            default:
+                v = log2(mmax);
+                // ln of the constant factor of the mixed path's raw event
+                // integral: dz F_scale / (N_gal,tot sqrt(2 pi)), times 1/b per event
+                sc[11] = log(c.dz * Fs / (c.n_gal_total * 2.50662827463100050242));
+                break;
         }
-        sc[t] = v;
+        sc[w] = v;
     }
     __syncthreads();
     if (t == 0) {
@@ -261,11 +280,11 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
         hp.c_g = den > 0.0 ? lam / (sg * 2.50662827463100050242 * den) : 0.0;
         hp.b1 = 1.0 + beta;
         hp.mmin_b1 = sc[2];
-        hp.lmmin = log(mmin);
+        hp.lmmin = sc[5];
         hp.dc_zmax = cH * sc[3];
         hp.d_valid = sc[4];
         hp.F_scale = Fs;
-        double tv = sqrt(hp.d_valid / c.d_top) * NU;
+        const double tv = sc[8];
         hp.t_valid = tv;
         if (!(tv < NU)) {
             hp.k_valid = NU;
@@ -274,12 +293,13 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
             hp.k_valid = (int)floor(tv);
             hp.f_valid = (float)(tv - hp.k_valid);
         }
+        hp.ln_k0 = sc[11];
         hp.status = p.status[h];
         hp.c_pl32 = (float)hp.c_pl;
         hp.c_g32 = (float)hp.c_g;
         hp.alpha32 = (float)alpha;
         hp.mu32 = (float)mu;
-        hp.inv_sg32 = (float)(1.0 / sg);
+        hp.inv_sg32 = (float)sc[10];
         hp.mmin32 = (float)mmin;
         hp.mmax32 = (float)mmax;
         hp.beta32 = (float)beta;
@@ -291,11 +311,11 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
         hp.om32 = (float)th[1];
         hp.gam32 = (float)th[9];
         hp.kap32 = (float)th[10];
-        hp.l1zp32 = (float)log1p(th[11]);
+        hp.l1zp32 = (float)sc[9];
         hp.cH32 = (float)cH;
         hp.inv_dc3_32 = (float)(1.0 / (hp.dc_zmax * hp.dc_zmax * hp.dc_zmax));
-        hp.l2min32 = (float)log2(mmin);
-        hp.l2max32 = (float)log2(mmax);
+        hp.l2min32 = (float)sc[6];
+        hp.l2max32 = (float)sc[7];
         hp.h0_32 = (float)th[0];
         hp.zp32 = (float)th[11];
         p.hp[h] = hp;

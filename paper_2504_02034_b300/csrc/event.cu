@@ -84,6 +84,19 @@ __device__ void block_sumd(double (&v)[NV], double *red) {
     __syncthreads();
 }
 
+// ln I of a mixed event kernel from its raw FP32 integral I' (grid factor in
+// units of F_scale, without the 1/b and catalog constants):
+//   ln I = ln I' - ln b + ln(dz F_scale / (N_gal,tot sqrt(2 pi))),
+// the last term per point in FP64 (hp.ln_k0); ln I' and ln b are split as
+// m 2^e so that the FP32 logs only see m in [0.5, 1) (absolute error
+// ~1e-7, the order of the FP32 sums themselves).
+__device__ __forceinline__ double ln_mixed(float I, float b, double ln_k0) {
+    if (!(I > 0.f)) return -CUDART_INF;
+    int eI, eb;
+    const float mI = frexpf(I, &eI), mb = frexpf(b, &eb);
+    return ln_k0 + (double)(logf(mI) - logf(mb)) + (double)(eI - eb) * 0.69314718055994530942;
+}
+
 // Scott bandwidth from the moment sums (same rule as the paper reading:
 // weighted, then unweighted, then the grid spacing).
 __device__ __forceinline__ double bandwidth_rule(double W1, double W2, double Vw, double nv,
@@ -590,7 +603,7 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
     __syncthreads();
     // fixed-order FP32 tree sum of the group values (relative error ~1e-7;
     // B300's FP64 rate would make a double reduction the block's longest
-    // step); the combine kernel takes the FP64 log
+    // step), then ln I (ln_mixed)
     {
         float sacc = 0.f;
         for (int g = tid; g < ngroups; g += EV_THREADS) sacc += gres[g];
@@ -601,7 +614,7 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
         if (tid == 0) {
             float I = 0.f;
             for (int w = 0; w < EV_WARPS; w++) I += redf[w];
-            p.lnI[out] = (double)I;  // the raw integral: F / F_scale units, without 1/b
+            p.lnI[out] = ln_mixed(I, (float)bd, p.hp[h].ln_k0);
             p.bw[out] = bd;
         }
     }
@@ -618,7 +631,7 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
 // nodes with the samples' bandwidth, windows (+-KW32 b) and support:
 //   I = sum_k pf_k sum_n c_kn sum_a C_{|a-n|} F'(z_a) G_k(z_a),
 //   c_kn = sum_{j in k} w_j max(0, 1 - |z_j / dz - n|),  C_m = exp(-(m dz)^2 / 2b^2),
-// in the mixed kernel's units (raw I).  The work per segment is
+// in the mixed kernel's units (ln_mixed gives ln I).  The work per segment is
 // (nodes) x (window) instead of (samples) x (window), which pays where a
 // segment holds many more samples than grid points under its samples
 // (single-1D).  One thread per node gathers the node's weight from the
@@ -746,14 +759,14 @@ __global__ void __launch_bounds__(BN_THREADS) k_event_binned(DevCatalog c, CallP
         }
         __syncthreads();  // Hs is restaged for the next segment
     }
-    // fixed-order FP32 tree sum; the combine kernel takes the FP64 log
+    // fixed-order FP32 tree sum, then ln I (ln_mixed)
     acc = warp_sum(acc);
     if (lane == 0) redf[wid] = acc;
     __syncthreads();
     if (tid == 0) {
         float I = 0.f;
         for (int w = 0; w < BN_THREADS / 32; w++) I += redf[w];
-        p.lnI[out] = (double)I;
+        p.lnI[out] = ln_mixed(I, b, hp.ln_k0);
         p.bw[out] = bd;
     }
 }

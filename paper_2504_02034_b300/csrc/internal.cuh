@@ -56,6 +56,7 @@ struct HP {
     double d_valid;   // d_L^gw(z = 10) [Mpc]
     double F_scale;   // max over the grid of F(z_a)
     double t_valid;   // inverse-table coordinate of d_valid
+    double ln_k0;     // ln(dz F_scale / (N_gal,tot sqrt(2 pi))): the mixed event kernels' log offset
     int32_t status;   // CHIMERA_PT_* bits known after the table stage
     int32_t k_valid;  // floor(t_valid), clamped
     float f_valid;    // t_valid - k_valid
@@ -196,7 +197,7 @@ size_t event_fp64_smem(const DevCatalog &c);
 // K5: selection partial sums; K6: combine into ln L.
 void launch_selection(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, cudaStream_t st);
 // raw: the mixed event kernel left raw integrals in lnI (K6 takes the log).
-void launch_combine(const DevCatalog &c, const CallPtrs &p, int H, bool raw, cudaStream_t st);
+void launch_combine(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st);
 int selection_chunks(const DevCatalog &c);
 // K8 microbenchmarks.
 int run_peaks(double *out, cudaStream_t st);

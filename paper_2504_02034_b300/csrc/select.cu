@@ -202,25 +202,12 @@ __device__ double fixed_order_sum(const double *x, int64_t n, int64_t stride, do
     return r;
 }
 
-// raw: the mixed event kernel left the raw integral I' (grid factor in units
-// of F_scale, without the 1/b and catalog constants); its FP64 log is taken
-// here, one event per thread: ln I = ln I' + ln(dz F_scale / (N_gal,tot
-// sqrt(2 pi) b)).
-__global__ void __launch_bounds__(CMB_THREADS) k_combine(DevCatalog c, CallPtrs p, int H, bool raw) {
+__global__ void __launch_bounds__(CMB_THREADS) k_combine(DevCatalog c, CallPtrs p, int H) {
     __shared__ double sh[2 * CMB_THREADS];
     __shared__ int s_bad;
     const int h = blockIdx.x;
     const HP &hp = p.hp[h];
     if (threadIdx.x == 0) s_bad = 0;
-    if (raw && !(hp.status & (CHIMERA_PT_OUT_OF_SUPPORT | CHIMERA_PT_NONMONOTONE))) {
-        double *lr = p.lnI + (size_t)h * c.n_events;
-        const double *bw = p.bw + (size_t)h * c.n_events;
-        const double k0 = c.dz * hp.F_scale / (c.n_gal_total * 2.50662827463100050242);
-        for (int i = threadIdx.x; i < c.n_events; i += CMB_THREADS) {
-            const double I = lr[i];
-            lr[i] = I > 0.0 ? log(I) + log(k0 / bw[i]) : -CUDART_INF;
-        }
-    }
     __syncthreads();
     const double *lnI = p.lnI + (size_t)h * c.n_events;
     for (int i = threadIdx.x; i < c.n_events; i += CMB_THREADS)
@@ -272,8 +259,8 @@ void launch_selection(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, 
     else k_select_mixed<<<dim3(p.n_chunk, (H + SEL_HB - 1) / SEL_HB), SEL_THREADS, 0, st>>>(c, p, H);
 }
 
-void launch_combine(const DevCatalog &c, const CallPtrs &p, int H, bool raw, cudaStream_t st) {
-    k_combine<<<H, CMB_THREADS, 0, st>>>(c, p, H, raw);
+void launch_combine(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st) {
+    k_combine<<<H, CMB_THREADS, 0, st>>>(c, p, H);
 }
 
 }  // namespace chim

@@ -1234,9 +1234,9 @@ int fwdO_table(Ctx &ctx, double Om, cudaStream_t st, const double **out) {
     auto it = ctx.fwdO.find(key);
     if (it == ctx.fwdO.end()) {
         FwdEntry e;
-        RC(dev_alloc(ctx, (void **)&e.table, sizeof(double) * NT_FWD));
+        RC(cache_alloc(ctx, (void **)&e.table, sizeof(double) * NT_FWD, st));
         if (cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming) != cudaSuccess) {
-            dev_free(ctx, e.table, sizeof(double) * NT_FWD);
+            cache_free(ctx, e.table, sizeof(double) * NT_FWD);
             return cuda_check(cudaGetLastError(), "cudaEventCreate");
         }
         launch_fwd_table_dOm(Om, e.table, st);
@@ -1264,10 +1264,10 @@ int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double O
         e.bytes = per * (size_t)c.n_pix * c.n_z;
         const size_t hb = c.kde_mode == CHIMERA_KDE_SINGLE_1D ? per * (size_t)c.n_events * c.n_z : 0;
         evict_profiles(ctx, cat, e.bytes + hb);
-        RC(dev_alloc(ctx, &e.G, e.bytes));
+        RC(cache_alloc(ctx, &e.G, e.bytes, ws.st));
         if (hb) {
-            int rc = dev_alloc(ctx, &e.Gh, hb);
-            if (rc) { dev_free(ctx, e.G, e.bytes); return rc; }
+            int rc = cache_alloc(ctx, &e.Gh, hb, ws.st);
+            if (rc) { cache_free(ctx, e.G, e.bytes); return rc; }
             e.hbytes = hb;
         }
         if (cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming) != cudaSuccess) {
@@ -1279,7 +1279,7 @@ int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double O
         double *invZ = reinterpret_cast<double *>(ws.gscr + L.o_invZ);
         double *ZO = reinterpret_cast<double *>(ws.gscr + L.o_ZO);
         float *dv32 = reinterpret_cast<float *>(dv + c.n_z), *dvO32 = reinterpret_cast<float *>(dvO + c.n_z);
-        k_dv_pair<<<(c.n_z + 255) / 256, 256, 0, ws.st>>>(fwd, fwdO, Om, c.dz, c.n_z, dv, dvO, dv32, dvO32);
+        k_dv_pair<<<(c.n_z + 63) / 64, 64, 0, ws.st>>>(fwd, fwdO, Om, c.dz, c.n_z, dv, dvO, dv32, dvO32);
         launch_galaxy_dOm(c, dv, dvO, dv32, dvO32, f64, invZ, ZO, e.G, ws.st);
         if (hb) {
             if (f64) k_dprofile_sum<<<c.n_events, 256, 0, ws.st>>>(c, (const double *)e.G, (double *)e.Gh);

@@ -75,6 +75,61 @@ void dev_free(Ctx &ctx, void *p, size_t bytes) {
     ctx.used -= bytes;
 }
 
+int cache_alloc(Ctx &ctx, void **p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    long n = ++g_alloc_count;
+    if (const char *f = getenv("CHIMERA_FAULT_ALLOC")) {
+        if (atol(f) == n) {
+            set_error("injected allocation failure (CHIMERA_FAULT_ALLOC)");
+            return CHIMERA_ERR_CUDA;
+        }
+    }
+    if (ctx.used.load() + bytes > ctx.budget) {
+        set_error("allocation of " + std::to_string(bytes) + " bytes exceeds the HBM budget");
+        return CHIMERA_ERR_ADMISSION;
+    }
+    if (!ctx.pool) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = ctx.device;
+        cudaError_t e = cudaMemPoolCreate(&ctx.pool, &props);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx.pool = nullptr;
+            return cuda_check(e, "cudaMemPoolCreate");
+        }
+        uint64_t keep = UINT64_MAX;  // freed memory stays in the pool
+        cudaMemPoolSetAttribute(ctx.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx.pool, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return cuda_check(e, "cudaMallocFromPoolAsync");
+    }
+    ctx.used += bytes;
+    return CHIMERA_OK;
+}
+
+void cache_free(Ctx &ctx, void *p, size_t bytes) {
+    if (!p) return;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    cudaFreeAsync(p, ctx.stream);
+    ctx.used -= bytes;
+}
+
+// Returns the pool's unused memory to the device (after evictions and
+// unloads), so that the budget accounting stays a bound on what is held.
+void trim_cache_pool(Ctx &ctx) {
+    if (!ctx.pool) return;
+    cudaStreamSynchronize(ctx.stream);
+    cudaMemPoolTrimTo(ctx.pool, 0);
+}
+
 // ------------------------------------------------------- workspace ----
 CallPtrs Workspace::ptrs(int H, const DevCatalog &c) const {
     CallPtrs p{};
@@ -220,7 +275,7 @@ int fwd_table(Ctx &ctx, double Om, cudaStream_t st, const double **out) {
     auto it = ctx.fwd.find(key);
     if (it == ctx.fwd.end()) {
         FwdEntry e;
-        RC(dev_alloc(ctx, (void **)&e.table, sizeof(double) * NT_FWD));
+        RC(cache_alloc(ctx, (void **)&e.table, sizeof(double) * NT_FWD, st));
         CK(cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming));
         launch_fwd_table(Om, e.table, st);
         CK(cudaGetLastError());
@@ -234,8 +289,8 @@ int fwd_table(Ctx &ctx, double Om, cudaStream_t st, const double **out) {
 }
 
 void free_prof_entry(Ctx &ctx, ProfEntry &e) {
-    dev_free(ctx, e.G, e.bytes);
-    if (e.Gh) dev_free(ctx, e.Gh, e.hbytes);
+    cache_free(ctx, e.G, e.bytes);
+    if (e.Gh) cache_free(ctx, e.Gh, e.hbytes);
     if (e.ready) cudaEventDestroy(e.ready);
     e.G = e.Gh = nullptr;
     e.ready = nullptr;
@@ -253,6 +308,7 @@ void evict_profiles(Ctx &ctx, Catalog &cat, size_t need) {
         cudaDeviceSynchronize();
         free_prof_entry(ctx, victim->second);
         cat.prof.erase(victim);
+        trim_cache_pool(ctx);
     }
 }
 
@@ -267,10 +323,10 @@ static int profile(Ctx &ctx, Catalog &cat, Workspace &ws, double Om, int kind, c
         e.bytes = esz * (size_t)c.n_pix * c.n_z;
         size_t hb = c.kde_mode == CHIMERA_KDE_SINGLE_1D ? esz * (size_t)c.n_events * c.n_z : 0;
         evict_profiles(ctx, cat, e.bytes + hb);
-        RC(dev_alloc(ctx, &e.G, e.bytes));
+        RC(cache_alloc(ctx, &e.G, e.bytes, ws.st));
         if (hb) {
-            int rc = dev_alloc(ctx, &e.Gh, hb);
-            if (rc) { dev_free(ctx, e.G, e.bytes); return rc; }
+            int rc = cache_alloc(ctx, &e.Gh, hb, ws.st);
+            if (rc) { cache_free(ctx, e.G, e.bytes); return rc; }
             e.hbytes = hb;
         }
         CK(cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming));
@@ -814,7 +870,31 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         launch_dense_ranges(c, 0);
         cudaError_t e = cudaStreamSynchronize(0);
         if (e == cudaSuccess) e = cudaGetLastError();
+        // the work lists of the dense gather: points with galaxies in reach
+        const size_t nl = (size_t)c.n_dense * c.n_z;
+        std::vector<int2> lr(nl), items;
+        for (int prec = 0; prec < 2 && e == cudaSuccess; prec++) {
+            e = cudaMemcpy(lr.data(), prec ? c.dense_lr32 : c.dense_lr64, sizeof(int2) * nl, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) break;
+            items.clear();
+            for (size_t i = 0; i < nl; i++)
+                if (lr[i].y > lr[i].x) items.push_back(make_int2((int)(i / c.n_z), (int)(i % c.n_z)));
+            int2 **dst = prec ? &c.dense_items32 : &c.dense_items64;
+            (prec ? c.n_ditems32 : c.n_ditems64) = (int64_t)items.size();
+            const size_t ib = sizeof(int2) * std::max<size_t>(items.size(), 1);
+            int rc = dev_alloc(ctx, (void **)dst, ib);
+            if (rc) {
+                for (void *a : cat->allocs) cudaFree(a);
+                ctx.used -= cat->bytes;
+                return rc;
+            }
+            cat->allocs.push_back(*dst);
+            cat->bytes += (ib + 255) & ~(size_t)255;
+            if (!items.empty())
+                e = cudaMemcpy(*dst, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+        }
         if (e != cudaSuccess) {
+            cudaGetLastError();
             for (void *a : cat->allocs) cudaFree(a);
             ctx.used -= cat->bytes;
             return cuda_check(e, "dense galaxy ranges");
@@ -848,6 +928,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
 static void free_catalog(Ctx &ctx, Catalog &cat) {
     for (auto &kv : cat.prof) free_prof_entry(ctx, kv.second);
     cat.prof.clear();
+    trim_cache_pool(ctx);
     for (void *a : cat.allocs) cudaFree(a);
     cat.allocs.clear();
     ctx.used -= cat.bytes;
@@ -919,12 +1000,12 @@ void chimera_destroy(chimera_ctx *h) {
     for (auto &kv : ctx.cats) free_catalog(ctx, *kv.second);
     ctx.cats.clear();
     for (auto &kv : ctx.fwd) {
-        dev_free(ctx, kv.second.table, sizeof(double) * NT_FWD);
+        cache_free(ctx, kv.second.table, sizeof(double) * NT_FWD);
         cudaEventDestroy(kv.second.ready);
     }
     ctx.fwd.clear();
     for (auto &kv : ctx.fwdO) {
-        dev_free(ctx, kv.second.table, sizeof(double) * NT_FWD);
+        cache_free(ctx, kv.second.table, sizeof(double) * NT_FWD);
         cudaEventDestroy(kv.second.ready);
     }
     ctx.fwdO.clear();
@@ -935,6 +1016,8 @@ void chimera_destroy(chimera_ctx *h) {
     for (auto &e : ctx.ws.tile_ev) cudaEventDestroy(e);
     ctx.ws.tile_ev.clear();
     if (ctx.dev_done) cudaEventDestroy(ctx.dev_done);
+    cudaStreamSynchronize(ctx.stream);  // the pool's frees are ordered on it
+    if (ctx.pool) cudaMemPoolDestroy(ctx.pool);
     cudaStreamDestroy(ctx.stream);
     delete h;
 }

@@ -67,14 +67,17 @@ __global__ void __launch_bounds__(FWD_THREADS) k_fwd_panels(double Om, double *o
     if (k == 0) out[0] = 0.0;
 }
 
-// Adds to every block's entries the totals of the blocks before it.
+// Adds to every block's entries the totals of the blocks before it (the
+// totals are read in parallel, then added in block order).
 __global__ void __launch_bounds__(1024) k_fwd_offsets(double *out) {
-    __shared__ double off[FWD_BLOCKS];
+    __shared__ double tot[FWD_BLOCKS], off[FWD_BLOCKS];
+    if (threadIdx.x + 1 < FWD_BLOCKS) tot[threadIdx.x] = out[(threadIdx.x + 1) * FWD_THREADS];  // block's total
+    __syncthreads();
     if (threadIdx.x == 0) {
         double run = 0.0;
         for (int b = 0; b < FWD_BLOCKS; b++) {
             off[b] = run;
-            if (b + 1 < FWD_BLOCKS) run += out[(b + 1) * FWD_THREADS];  // block b's total
+            if (b + 1 < FWD_BLOCKS) run += tot[b];
         }
     }
     __syncthreads();

@@ -22,8 +22,9 @@
 //   gather: one block per pixel of at most GAL_DENSE galaxies, one grid
 //           point per thread, the galaxies whose window covers it (sorted by
 //           z inside the pixel at load time, found by binary search);
-//   dense:  one block per (dense pixel, grid point), the covering galaxies
-//           spread over the block and added by a fixed-order tree.
+//   dense:  one block per (dense pixel, grid point) with galaxies in reach
+//           (load-time lists), the covering galaxies spread over the block
+//           and added by a fixed-order tree.
 // Every sum has a fixed order, so a profile is reproducible bit for bit.
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -180,7 +181,10 @@ __global__ void __launch_bounds__(GAL_THREADS) k_gal_gather(DevCatalog c, const 
     const int64_t p = blockIdx.x;
     const int64_t g0 = c.gal_off[p], g1 = c.gal_off[p + 1];
     const int ng = (int)(g1 - g0);
-    if (ng > GAL_DENSE) return;  // the dense kernel's pixel
+    if (ng > GAL_DENSE) {  // the dense kernel's pixel: zero its row, the dense kernel fills it
+        for (int a = threadIdx.x; a < c.n_z; a += GAL_THREADS) out[p * c.n_z + a] = T(0);
+        return;
+    }
     for (int i = threadIdx.x; i < ng; i += GAL_THREADS) {
         G::read(c, p, g0 + i, sz[i], ss[i]);
         siz[i] = invZ[g0 + i];
@@ -228,7 +232,9 @@ __global__ void k_dense_ranges(DevCatalog c, int2 *lr) {
     lr[i] = make_int2((int)(l - g0), (int)(r - g0));
 }
 
-// One block per (dense pixel, grid point), over the load-time candidate range.
+// One block per (dense pixel, grid point) whose load-time candidate range
+// is not empty (the other points of a dense row are zeroed by the gather
+// kernel); the range is spread over the block and added by a fixed tree.
 template <bool F64, bool WITH_O>
 __global__ void __launch_bounds__(GAL_THREADS) k_gal_gather_dense(DevCatalog c, const typename Gal<F64>::T *dv,
                                                                  const typename Gal<F64>::T *dvO,
@@ -237,10 +243,11 @@ __global__ void __launch_bounds__(GAL_THREADS) k_gal_gather_dense(DevCatalog c, 
                                                                  typename Gal<F64>::T *out) {
     using T = typename Gal<F64>::T;
     __shared__ T red[2][GAL_THREADS / 32];
-    const int64_t p = c.dense_pix[blockIdx.x];
-    const int a = blockIdx.y;
+    const int2 item = (F64 ? c.dense_items64 : c.dense_items32)[blockIdx.x];  // (dense index, grid point)
+    const int64_t p = c.dense_pix[item.x];
+    const int a = item.y;
     const int64_t g0 = c.gal_off[p];
-    const int2 lr = (F64 ? c.dense_lr64 : c.dense_lr32)[(int64_t)blockIdx.x * c.n_z + a];
+    const int2 lr = (F64 ? c.dense_lr64 : c.dense_lr32)[(int64_t)item.x * c.n_z + a];
     T s1 = T(0), s2 = T(0);
     gather_range<F64, WITH_O>(c, p, a, g0 + lr.x + threadIdx.x, g0 + lr.y, GAL_THREADS, invZ, ZO, s1, s2);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -270,9 +277,11 @@ void launch_profile_t(const DevCatalog &c, const typename Gal<F64>::T *dv, const
     if (c.n_pix == 0) return;
     if (c.n_gw > 0) k_gal_norm<F64, WITH_O><<<(unsigned)c.n_gw, GAL_CHUNK, 0, st>>>(c, dv, dvO, invZ, ZO);
     k_gal_gather<F64, WITH_O><<<(unsigned)c.n_pix, GAL_THREADS, 0, st>>>(c, dv, dvO, invZ, ZO, out);
-    if (c.n_dense > 0)
-        k_gal_gather_dense<F64, WITH_O><<<dim3((unsigned)c.n_dense, (unsigned)c.n_z), GAL_THREADS, 0, st>>>(
-            c, dv, dvO, invZ, ZO, out);
+    {
+        const int64_t ni = F64 ? c.n_ditems64 : c.n_ditems32;
+        if (ni > 0)
+            k_gal_gather_dense<F64, WITH_O><<<(unsigned)ni, GAL_THREADS, 0, st>>>(c, dv, dvO, invZ, ZO, out);
+    }
 }
 
 // Single-1D: sum_k S_k G_k(z_a) per event.
@@ -300,7 +309,7 @@ void launch_galaxy_profile(const DevCatalog &c, const double *fwd, double Om, do
                            double *invZ64, float *invZ32, double *out64, float *out32,
                            cudaStream_t st) {
     float *dv32 = reinterpret_cast<float *>(dv + c.n_z);
-    k_dvdz<<<(c.n_z + 255) / 256, 256, 0, st>>>(fwd, Om, c.dz, c.n_z, dv, dv32);
+    k_dvdz<<<(c.n_z + 63) / 64, 64, 0, st>>>(fwd, Om, c.dz, c.n_z, dv, dv32);  // FP64: spread over SMs
     if (out64) launch_profile_t<true, false>(c, dv, nullptr, invZ64, nullptr, out64, st);
     if (out32) launch_profile_t<false, false>(c, dv32, nullptr, invZ32, nullptr, out32, st);
 }

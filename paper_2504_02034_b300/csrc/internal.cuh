@@ -117,6 +117,10 @@ struct DevCatalog {
     // galaxy (FP64 values and reach; stored values and the mixed reach);
     // filled on the device at load
     int2 *dense_lr64, *dense_lr32;
+    // the (dense pixel index, grid point) pairs whose range is not empty,
+    // per precision (built at load from the ranges)
+    int64_t n_ditems64, n_ditems32;
+    int2 *dense_items64, *dense_items32;
     // galaxies
     double *gz64, *gs64;  // FP64 values
     float *gz32, *gs32;   // F32 storage

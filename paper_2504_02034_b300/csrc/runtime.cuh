@@ -107,6 +107,7 @@ struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t dev_done = nullptr;  // device entry point: the caller's stream waits on it
+    cudaMemPool_t pool = nullptr;    // cache entries (cache_alloc)
     size_t budget = 0;
     std::atomic<size_t> used{0};
     std::recursive_mutex mu;
@@ -122,6 +123,15 @@ struct Ctx {
 // Budgeted allocation; returns a CHIMERA_ERR_* code.
 int dev_alloc(Ctx &ctx, void **p, size_t bytes);
 void dev_free(Ctx &ctx, void *p, size_t bytes);
+// Cache entries (distance tables, galaxy profiles and their Om derivatives)
+// come from the context's stream-ordered memory pool, which keeps freed
+// memory for reuse: a call with many new Om values allocates without a
+// cudaMalloc each.  The allocation is ordered on `st`; other streams use the
+// entry after waiting on its ready event.  cache_free is called only with
+// the device idle (eviction, unload, destroy).
+int cache_alloc(Ctx &ctx, void **p, size_t bytes, cudaStream_t st);
+void cache_free(Ctx &ctx, void *p, size_t bytes);
+void trim_cache_pool(Ctx &ctx);
 
 int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat);
 void ws_release(Ctx &ctx, Workspace &ws);

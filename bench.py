@@ -317,6 +317,29 @@ def binned_stats(pkg, ctx, torch, dev, theta, steps):
     return res
 
 
+def om_varying_stats(pkg, ctx, cid, theta, NE, calls=3):
+    """Walkers whose Om is new at every point (the differentiation workload's
+    pattern): every call brings 16 Om values never seen before, so each pays
+    its distance tables and galaxy profiles (and, with the gradient, their Om
+    derivatives).  ln L and ln L + gradient through the host entry points,
+    mixed precision, on the benchmark catalog; wall time per call."""
+    out = {}
+    for name, fn in (("loglike", lambda t: pkg.chimera_loglike(ctx.h, cid, t, pkg.MIXED)),
+                     ("gradient", lambda t: pkg.chimera_grad(ctx.h, cid, t, pkg.MIXED))):
+        ts = []
+        for k in range(calls + 1):
+            t = theta.copy()
+            t[:, 1] = 0.28 + 0.04 * np.random.default_rng(1000 * k + len(name)).random(theta.shape[0])
+            t0 = time.perf_counter()
+            fn(t)
+            if k > 0:  # the first call warms the code paths
+                ts.append(time.perf_counter() - t0)
+        ms = 1e3 * sum(ts) / len(ts)
+        out[name] = {"ms_per_call": ms, "value": theta.shape[0] * NE / (ms * 1e-3), "unit": UNIT,
+                     "new_om_per_call": int(theta.shape[0])}
+    return out
+
+
 def serving_stream(pkg, ctx, bench_cid, bench_cat, n_req, seed=2504020345):
     """Request stream over four resident catalogs (spectroscopic 100 / 300 /
     1000 events at Xi0 = 0.6 / 1 / 1.8, photometric 5000 events x 4000 PE with
@@ -503,6 +526,7 @@ def main():
 
     grads = grad_stats(pkg, ctx, cid, theta, NE)
     binned = binned_stats(pkg, ctx, torch, dev, theta, max(3, args.steps // 2)) if rank == 0 else None
+    om_var = om_varying_stats(pkg, ctx, cid, theta, NE) if rank == 0 else None
     serving = serving_stream(pkg, ctx, cid, cat, args.serve_requests) if args.serve_requests > 0 and rank == 0 else None
 
     kern = sum(kern_ms) / len(kern_ms)
@@ -540,6 +564,7 @@ def main():
         "stage_ms": mean_stage,
         "gradient": grads,
         "binned_kde": binned,
+        "om_varying": om_var,
         "serving": serving,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(theta.nbytes),
                 "d2h_bytes_per_step": int(H * (8 + 8 + 4))},

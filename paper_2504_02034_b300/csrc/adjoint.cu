@@ -997,7 +997,7 @@ __device__ __forceinline__ float dcO_hermite32(const double *fwdO, float z, floa
 // recomputes s_j as the FP64 selection kernel does; MIXED in float from the
 // mixed kernel's z_j (D_c from the measured distance, D_c = d_L/((1+z) Xi)).
 template <bool F64>
-__global__ void __launch_bounds__(ADJ_THREADS) k_select_adj(DevCatalog c, CallPtrs p, AdjPtrs q, int H) {
+__global__ void __launch_bounds__(ADJ_THREADS, F64 ? 1 : 4) k_select_adj(DevCatalog c, CallPtrs p, AdjPtrs q, int H) {
     using T = typename std::conditional<F64, double, float>::type;
     __shared__ double red[(ADJ_THREADS / 32 + 1) * 13];
     const int h = blockIdx.y, chunk = blockIdx.x;

@@ -68,6 +68,15 @@ extern "C" {
  * points under them (single-1D).  ln L and chimera_terms only: chimera_grad
  * and serving reject it (INVALID_ARG). */
 #define CHIMERA_MIXED_BINNED 2
+/* Kernel-shape flag, OR'ed into the precision of chimera_loglike,
+ * chimera_loglike_device and chimera_terms (Sec. 2.3: the 1-D KDEs take a
+ * Gaussian or an Epanechnikov kernel).  Reading: the Epanechnikov kernel
+ * (3/4)(1 - u^2) on |u| <= 1, u = (z - z_j)/h, h = sqrt(5) b, the width whose
+ * variance equals the Gaussian's b^2 (b by the same Scott rule); windows
+ * are the kernel's own support |z - z_j| <= h.  Works with CHIMERA_FP64,
+ * CHIMERA_MIXED (one evaluation per sample and grid point in FP32) and
+ * CHIMERA_MIXED_BINNED; chimera_grad and serving reject it (INVALID_ARG). */
+#define CHIMERA_KERNEL_EPANECHNIKOV 0x10
 
 /* ---- KDE variant, fixed per catalog (Sec. 2.3) ---- */
 #define CHIMERA_KDE_SINGLE_1D 0 /* one redshift KDE per event, Eq. gw-kernel-single1d */

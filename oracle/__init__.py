@@ -15,6 +15,7 @@ _SO = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.c")
 
 OK, OUT_OF_SUPPORT, NONMONOTONE, NEFF_LOW = 0, 1, 2, 4
+GAUSSIAN, EPANECHNIKOV = 0, 1  # KDE kernel shapes
 
 
 def build(force=False):
@@ -49,6 +50,7 @@ class _Cat(C.Structure):
         ("inj_m2d", C.POINTER(C.c_double)), ("inj_log_pi", C.POINTER(C.c_double)),
         ("lambda_g", C.c_double), ("beta", C.c_double),
         ("kde_mode", C.c_int32),
+        ("kernel", C.c_int32),
     ]
 
 
@@ -90,7 +92,7 @@ def lib():
         L.orc_event_lnI_binned.argtypes = [pc, pd, C.c_int64, ph, pd]
         L.orc_linear_bins.argtypes = [C.c_int64, pd, pd, d, C.c_int64, C.c_int64, pd]
         L.orc_linear_bins.restype = C.c_int64
-        L.orc_kde_arrays.argtypes = [C.c_int64, pd, pd, d, C.c_int64, d, C.c_int32, pd]
+        L.orc_kde_arrays.argtypes = [C.c_int64, pd, pd, d, C.c_int64, d, C.c_int32, C.c_int32, pd]
         _lib = L
     return _lib
 
@@ -112,7 +114,7 @@ def hooks(psi_scale=1.0, mass_scale=1.0, flags=0):
 class Catalog:
     """Oracle view of a catalog dict (see synth.catalog.make_catalog)."""
 
-    def __init__(self, cat, kde_mode=None):
+    def __init__(self, cat, kde_mode=None, kernel=0):
         self.keep = {}
 
         def arr(key, dt):
@@ -139,6 +141,7 @@ class Catalog:
             _p(arr("inj_log_pi", np.float64)),
             float(cat["lambda_g"]), float(cat["beta"]),
             int(cat["kde_mode"] if kde_mode is None else kde_mode),
+            int(kernel),
         )
 
     @property
@@ -286,11 +289,12 @@ def linear_bins(z, w, dz, b0, nb):
     return cb, int(lost)
 
 
-def kde_arrays(z, w, b, n_z, z_max, binned=False):
-    """Weighted Gaussian KDE (1/N normalisation, support: sample range +- 6 b)
-    of the samples (z, w) on the grid of n_z points on [0, z_max]."""
+def kde_arrays(z, w, b, n_z, z_max, binned=False, kernel=GAUSSIAN):
+    """Weighted KDE (Gaussian of width b or Epanechnikov of width sqrt(5) b;
+    1/N normalisation, support: sample range +- 6 b) of the samples (z, w) on
+    the grid of n_z points on [0, z_max]."""
     z = np.ascontiguousarray(z, dtype=np.float64)
     w = np.ascontiguousarray(w, dtype=np.float64)
     K = np.zeros(int(n_z))
-    lib().orc_kde_arrays(z.size, _p(z), _p(w), float(b), int(n_z), float(z_max), int(binned), _p(K))
+    lib().orc_kde_arrays(z.size, _p(z), _p(w), float(b), int(n_z), float(z_max), int(binned), int(kernel), _p(K))
     return K

@@ -23,6 +23,8 @@
  *  - binned-KDE option (Sec. 2.3 bins the weighted samples): linear binning
  *    onto the grid lattice z_n = n dz, then the KDE of the nodes with the
  *    samples' bandwidth, normalisation and support
+ *  - Epanechnikov kernel option (Sec. 2.3): (3/4)(1 - u^2) on |u| <= 1 with
+ *    width h = sqrt(5) b (the Gaussian's variance b^2)
  */
 #include "oracle.h"
 
@@ -311,26 +313,29 @@ int64_t orc_linear_bins(int64_t n, const double *z, const double *w, double dz,
     return lost;
 }
 
-/* Weighted Gaussian KDE of one sample set on the grid (Eqs.
- * gw-kernel-many1d/single1d):
+/* Weighted KDE of one sample set on the grid (Eqs.
+ * gw-kernel-many1d/single1d), Gaussian:
  * K(z_a) = (1/N) sum_{j in set} w_j exp(-(z_a - z_j)^2 / 2b^2) / (sqrt(2 pi) b),
- * N the set's size (all its samples, valid or not).  The KDE is evaluated
- * only on the part of the grid that holds the set's samples and is zero
- * elsewhere (Sec. 2.3): z_a in [min z_j - ORC_KDE_MARGIN b,
+ * or Epanechnikov: (1/N) sum w_j (3/4h) max(0, 1 - ((z_a - z_j)/h)^2),
+ * h = sqrt(5) b; N the set's size (all its samples, valid or not).  The KDE
+ * is evaluated only on the part of the grid that holds the set's samples and
+ * is zero elsewhere (Sec. 2.3): z_a in [min z_j - ORC_KDE_MARGIN b,
  * max z_j + ORC_KDE_MARGIN b] over the samples with a redshift; every sample
  * term inside is kept in full.  binned != 0: the samples are replaced by
  * their linear bins (orc_linear_bins) before the same sum; the support stays
  * that of the samples.                                                    */
 static void kde_set(int64_t n, const double *z, const double *w, const int32_t *valid,
-                    int64_t N, double b, int64_t nz, double z_max, int binned, double *K) {
+                    int64_t N, double b, int64_t nz, double z_max, int binned, int kernel, double *K) {
     const double dz = z_max / (double)(nz - 1);
+    const int epan = kernel == ORC_KERNEL_EPANECHNIKOV;
+    const double hw = epan ? sqrt(5.0) * b : b;  /* the kernel's width */
     double zlo = INFINITY, zhi = -INFINITY;
     for (int64_t j = 0; j < n; j++)
         if (valid[j]) {
             if (z[j] < zlo) zlo = z[j];
             if (z[j] > zhi) zhi = z[j];
         }
-    double norm = 1.0 / (sqrt(2.0 * M_PI) * b);
+    double norm = epan ? 0.75 / hw : 1.0 / (sqrt(2.0 * M_PI) * b);
     double *zb = NULL, *cb = NULL, *wv = NULL;
     int64_t m = 0;
     if (binned && zlo <= zhi) {
@@ -351,14 +356,14 @@ static void kde_set(int64_t n, const double *z, const double *w, const int32_t *
         if (binned) {
             for (int64_t k = 0; k < m; k++) {
                 if (cb[k] == 0.0) continue;
-                double u = (za - zb[k]) / b;
-                s += cb[k] * exp(-0.5 * u * u);
+                double u = (za - zb[k]) / hw;
+                s += cb[k] * (epan ? (fabs(u) <= 1.0 ? 1.0 - u * u : 0.0) : exp(-0.5 * u * u));
             }
         } else {
             for (int64_t j = 0; j < n; j++) {
                 if (!valid[j] || w[j] == 0.0) continue;
-                double u = (za - z[j]) / b;
-                s += w[j] * exp(-0.5 * u * u);
+                double u = (za - z[j]) / hw;
+                s += w[j] * (epan ? (fabs(u) <= 1.0 ? 1.0 - u * u : 0.0) : exp(-0.5 * u * u));
             }
         }
         K[a] = N > 0 ? s * norm / (double)N : 0.0;
@@ -367,10 +372,10 @@ static void kde_set(int64_t n, const double *z, const double *w, const int32_t *
 }
 
 int orc_kde_arrays(int64_t n, const double *z, const double *w, double b, int64_t nz,
-                   double z_max, int32_t binned, double *K) {
+                   double z_max, int32_t binned, int32_t kernel, double *K) {
     int32_t *v = malloc(sizeof(int32_t) * (n + 1));
     for (int64_t j = 0; j < n; j++) v[j] = isfinite(z[j]) ? 1 : 0;
-    kde_set(n, z, w, v, n, b, nz, z_max, binned, K);
+    kde_set(n, z, w, v, n, b, nz, z_max, binned, kernel, K);
     free(v);
     return 0;
 }
@@ -391,7 +396,7 @@ static void kde_grid(const orc_catalog *c, int64_t ev, int32_t pixel,
         vs[cnt] = valid[j];
         cnt++;
     }
-    kde_set(cnt, zs, ws, vs, cnt, b, c->n_z, c->z_max, binned, K);
+    kde_set(cnt, zs, ws, vs, cnt, b, c->n_z, c->z_max, binned, c->kernel, K);
     free(zs); free(ws); free(vs);
 }
 

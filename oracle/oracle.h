@@ -32,6 +32,10 @@ extern "C" {
 
 enum { ORC_OK = 0, ORC_OUT_OF_SUPPORT = 1, ORC_NONMONOTONE = 2, ORC_NEFF_LOW = 4 };
 enum { ORC_KDE_SINGLE_1D = 0, ORC_KDE_MANY_1D = 1 };
+/* KDE kernel shape (Sec. 2.3 offers Gaussian and Epanechnikov).  Reading:
+ * the Epanechnikov kernel (3/4)(1 - u^2) on |u| <= 1, u = (z - z_j)/h, with
+ * h = sqrt(5) b, the width whose variance equals the Gaussian's b^2. */
+enum { ORC_KERNEL_GAUSSIAN = 0, ORC_KERNEL_EPANECHNIKOV = 1 };
 
 /* Test hooks.  Defaults (psi_scale = mass_scale = 1, flags = 0) give the
  * paper's likelihood; the others exist so that tests can check invariants and
@@ -60,6 +64,7 @@ typedef struct {
     const double *inj_dL, *inj_m1d, *inj_m2d, *inj_log_pi;
     double lambda_g, beta;
     int32_t kde_mode;
+    int32_t kernel;                 /* ORC_KERNEL_GAUSSIAN or ORC_KERNEL_EPANECHNIKOV */
 } orc_catalog;
 
 /* ---- cosmology (Eqs. dL-em, dL-mg, jacobian) ---- */
@@ -102,7 +107,7 @@ int orc_event_lnI(const orc_catalog *c, const double *th, int64_t ev,
 int64_t orc_linear_bins(int64_t n, const double *z, const double *w, double dz,
                         int64_t b0, int64_t nb, double *cb);
 int orc_kde_arrays(int64_t n, const double *z, const double *w, double b, int64_t nz,
-                   double z_max, int32_t binned, double *K);
+                   double z_max, int32_t binned, int32_t kernel, double *K);
 int orc_event_kde_binned(const orc_catalog *c, const double *th, int64_t ev,
                          int32_t pixel, double *K);
 int orc_event_lnI_binned(const orc_catalog *c, const double *th, int64_t ev,

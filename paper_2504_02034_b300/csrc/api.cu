@@ -361,6 +361,8 @@ static bool admissible(const double *t) {
 
 int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, int precision,
             double *out_lnL, double *out_neff, int32_t *out_status) {
+    const bool epan = (precision & CHIMERA_KERNEL_EPANECHNIKOV) != 0;
+    precision &= ~CHIMERA_KERNEL_EPANECHNIKOV;  // the base precision below
     RC(ws_ensure(ctx, ws, H, cat));
     ctx.tick++;
     const DevCatalog &c = cat.d;
@@ -403,6 +405,7 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
     if (ws.trace) CK(cudaEventRecord(ws.tev[1], ws.st));
     CK(cudaMemcpyAsync(ws.param, ws.hstage, ws.param_bytes(H), cudaMemcpyHostToDevice, ws.st));
     CallPtrs p = ws.ptrs(H, c);
+    p.kshape = epan ? 1 : 0;
     if (p.pairs) CK(cudaMemsetAsync(p.pairs, 0, sizeof(unsigned long long) * H, ws.st));
     launch_hyper_tables(c, p, H, precision == CHIMERA_FP64, ws.dk, ws.fmax_bits, ws.st);
     if (ws.trace) CK(cudaEventRecord(ws.tev[2], ws.st));
@@ -439,7 +442,8 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
             const int h0 = t * tile, nh = std::min(tile, H - h0);
             launch_reweight(c, p, h0, nh, ws.st);
             if (ws.trace) CK(cudaEventRecord(ws.tile_ev[2 * t], ws.st));
-            if (precision == CHIMERA_MIXED_BINNED) launch_event_binned(c, p, h0, nh, ws.st);
+            if (precision == CHIMERA_MIXED_BINNED || epan)
+                launch_event_binned(c, p, h0, nh, precision == CHIMERA_MIXED_BINNED, ws.st);
             else launch_event_mixed(c, p, h0, nh, ws.st);
             if (ws.trace) CK(cudaEventRecord(ws.tile_ev[2 * t + 1], ws.st));
         }
@@ -1053,7 +1057,8 @@ int chimera_catalog_info(chimera_ctx *h, int32_t id, chimera_catalog_info_t *inf
 static int check_call(chimera_ctx *h, int32_t n, const void *theta, int32_t prec, const void *out) {
     if (!h || !theta || !out) { set_error("null argument"); return CHIMERA_ERR_INVALID_ARG; }
     if (n <= 0) { set_error("n_points must be positive"); return CHIMERA_ERR_INVALID_ARG; }
-    if (prec != CHIMERA_FP64 && prec != CHIMERA_MIXED && prec != CHIMERA_MIXED_BINNED) {
+    const int base = prec & ~CHIMERA_KERNEL_EPANECHNIKOV;
+    if (base != CHIMERA_FP64 && base != CHIMERA_MIXED && base != CHIMERA_MIXED_BINNED) {
         set_error("bad precision");
         return CHIMERA_ERR_INVALID_ARG;
     }
@@ -1123,8 +1128,8 @@ int chimera_terms(chimera_ctx *h, int32_t id, int32_t n, const double *theta, in
 int chimera_grad(chimera_ctx *h, int32_t id, int32_t n, const double *theta, int32_t prec,
                  double *lnL, double *dlnL, int32_t *status) {
     RC(check_call(h, n, theta, prec, lnL));
-    if (prec == CHIMERA_MIXED_BINNED) {
-        set_error("the adjoint follows the unbinned KDE: use CHIMERA_FP64 or CHIMERA_MIXED");
+    if (prec != CHIMERA_FP64 && prec != CHIMERA_MIXED) {
+        set_error("the adjoint follows the unbinned Gaussian KDE: use CHIMERA_FP64 or CHIMERA_MIXED");
         return CHIMERA_ERR_INVALID_ARG;
     }
     if (!dlnL) { set_error("dlnL is NULL"); return CHIMERA_ERR_INVALID_ARG; }

@@ -90,11 +90,14 @@ __device__ void block_sumd(double (&v)[NV], double *red) {
 // the last term per point in FP64 (hp.ln_k0); ln I' and ln b are split as
 // m 2^e so that the FP32 logs only see m in [0.5, 1) (absolute error
 // ~1e-7, the order of the FP32 sums themselves).
-__device__ __forceinline__ double ln_mixed(float I, float b, double ln_k0) {
+// ln_k0 carries the Gaussian's 1/sqrt(2 pi); the Epanechnikov kernel's
+// normalisation 3/(4 sqrt5 b) adds ln(3 sqrt(2 pi) / (4 sqrt5)).
+__device__ __forceinline__ double ln_mixed(float I, float b, double ln_k0, bool epan = false) {
     if (!(I > 0.f)) return -CUDART_INF;
     int eI, eb;
     const float mI = frexpf(I, &eI), mb = frexpf(b, &eb);
-    return ln_k0 + (double)(logf(mI) - logf(mb)) + (double)(eI - eb) * 0.69314718055994530942;
+    return ln_k0 + (epan ? -0.17346249546415843 : 0.0) + (double)(logf(mI) - logf(mb)) +
+           (double)(eI - eb) * 0.69314718055994530942;
 }
 
 // Scott bandwidth from the moment sums (same rule as the paper reading:
@@ -654,6 +657,12 @@ struct BinLayout {
     }
 };
 
+// BINNED = false: the same block structure with one thread per sample and a
+// direct evaluation of the kernel per (sample, grid point); the mixed path's
+// Epanechnikov form (the Horner factorisation of the main kernel is specific
+// to the Gaussian).  The kernel shape (p.kshape) sets the weight table and
+// window: exp(-x^2/2), |x| <= KW32, or 1 - x^2/5, |x| <= sqrt5, x = dz m / b.
+template <bool BINNED>
 __global__ void __launch_bounds__(BN_THREADS) k_event_binned(DevCatalog c, CallPtrs p, int h0, int nh) {
     extern __shared__ float4 bsm4[];
     const BinLayout L(c.max_ns, c.n_z, c.max_seg);
@@ -698,13 +707,16 @@ __global__ void __launch_bounds__(BN_THREADS) k_event_binned(DevCatalog c, CallP
     }
     const double bd = p.bw[out];  // the reweighting kernel's FP32 bandwidth
     const float b = (float)bd;
-    const float inv_s2b = 0.70710678f / b;
-    const int W = (int)fminf(KW32 * b * inv_dz, 1e8f);  // window half-width in nodes
+    const bool epan = p.kshape == 1;
+    const float ib = 1.f / b;
+    const float half = epan ? 2.23606798f * b : KW32 * b;  // the kernel's window
+    auto kern = [&](float x) {  // x = (z_a - z) / b
+        return epan ? fmaxf(0.f, fmaf(-0.2f * x, x, 1.f)) : __expf(-0.5f * x * x);
+    };
+    const int W = (int)fminf(half * inv_dz, 1e8f);  // window half-width in nodes
     const int nct = min(W + 1, 2 * L.nz_pad);
-    for (int m = tid; m < nct; m += BN_THREADS) {
-        const float x = m * dz * inv_s2b;
-        Ct[m] = __expf(-x * x);
-    }
+    if (BINNED)
+        for (int m = tid; m < nct; m += BN_THREADS) Ct[m] = kern(m * dz * ib);
     __syncthreads();
     for (int k = tid; k < nseg; k += BN_THREADS) {
         int l = seglo[k], r = seglo[k + 1];
@@ -733,29 +745,41 @@ __global__ void __launch_bounds__(BN_THREADS) k_event_binned(DevCatalog c, CallP
             Hs[a + BN_HPAD] = (a >= A0 && a <= A1) ? Fs[a] * __ldg(G + a) : 0.f;
         __syncthreads();
         const float pf = segpf[k];
-        for (int n = N0 + tid; n <= N1; n += BN_THREADS) {
-            // the node's weight: samples with floor(z / dz) in {n - 1, n}
-            int l = lo, r = lo + cnt;
-            while (l < r) {
-                const int m = (l + r) >> 1;
-                if (floorf(zs[m] * inv_dz) < (float)(n - 1)) l = m + 1; else r = m;
+        if (BINNED) {
+            for (int n = N0 + tid; n <= N1; n += BN_THREADS) {
+                // the node's weight: samples with floor(z / dz) in {n - 1, n}
+                int l = lo, r = lo + cnt;
+                while (l < r) {
+                    const int m = (l + r) >> 1;
+                    if (floorf(zs[m] * inv_dz) < (float)(n - 1)) l = m + 1; else r = m;
+                }
+                float cw = 0.f;
+                for (int j = l; j < lo + cnt; j++) {
+                    const float t = zs[j] * inv_dz, fb = floorf(t);
+                    if (fb > (float)n) break;
+                    const float f = t - fb;
+                    cw += fb == (float)n ? ws[j] * (1.f - f) : ws[j] * f;
+                }
+                if (cw == 0.f) continue;
+                const int a0 = max(A0, n - W), a1 = min(A1, n + W);
+                float sacc = 0.f;
+                for (int a = a0; a <= a1; a++) {
+                    const int m = abs(a - n);
+                    const float cm = m < nct ? Ct[m] : kern(m * dz * ib);
+                    sacc = fmaf(cm, Hs[a + BN_HPAD], sacc);
+                }
+                acc = fmaf(pf * cw, sacc, acc);
             }
-            float cw = 0.f;
-            for (int j = l; j < lo + cnt; j++) {
-                const float t = zs[j] * inv_dz, fb = floorf(t);
-                if (fb > (float)n) break;
-                const float f = t - fb;
-                cw += fb == (float)n ? ws[j] * (1.f - f) : ws[j] * f;
+        } else {
+            for (int j = lo + tid; j < lo + cnt; j += BN_THREADS) {
+                const float z = zs[j], w = ws[j];
+                if (w == 0.f) continue;
+                const int a0 = max(A0, (int)ceilf((z - half) * inv_dz));
+                const int a1 = min(A1, (int)floorf((z + half) * inv_dz));
+                float sacc = 0.f;
+                for (int a = a0; a <= a1; a++) sacc = fmaf(kern((a * dz - z) * ib), Hs[a + BN_HPAD], sacc);
+                acc = fmaf(pf * w, sacc, acc);
             }
-            if (cw == 0.f) continue;
-            const int a0 = max(A0, n - W), a1 = min(A1, n + W);
-            float sacc = 0.f;
-            for (int a = a0; a <= a1; a++) {
-                const int m = abs(a - n);
-                const float cm = m < nct ? Ct[m] : __expf(-(m * dz * inv_s2b) * (m * dz * inv_s2b));
-                sacc = fmaf(cm, Hs[a + BN_HPAD], sacc);
-            }
-            acc = fmaf(pf * cw, sacc, acc);
         }
         __syncthreads();  // Hs is restaged for the next segment
     }
@@ -766,7 +790,7 @@ __global__ void __launch_bounds__(BN_THREADS) k_event_binned(DevCatalog c, CallP
     if (tid == 0) {
         float I = 0.f;
         for (int w = 0; w < BN_THREADS / 32; w++) I += redf[w];
-        p.lnI[out] = ln_mixed(I, b, hp.ln_k0);
+        p.lnI[out] = ln_mixed(I, b, hp.ln_k0, epan);
         p.bw[out] = bd;
     }
 }
@@ -832,6 +856,7 @@ __global__ void __launch_bounds__(EV64_THREADS) k_event_fp64(DevCatalog c, CallP
     __syncthreads();
     const int nz = c.n_z;
     const double dz = c.dz;
+    const bool epan = p.kshape == 1;
     const double *F = p.F64 + (size_t)h * nz;
     const double *prof = reinterpret_cast<const double *>(p.prof[h]);
     double tsum = 0.0;
@@ -848,17 +873,20 @@ __global__ void __launch_bounds__(EV64_THREADS) k_event_fp64(DevCatalog c, CallP
         if (w == 0.0) continue;
         const int64_t row = c.kde_mode == CHIMERA_KDE_MANY_1D ? (int64_t)(sg0 + l) : (int64_t)ev;
         const double *G = prof + row * nz;
-        // window +-KW64 b, clipped to the segment's KDE support
+        // window +-KW64 b (Gaussian) or +-h = sqrt(5) b (Epanechnikov),
+        // clipped to the segment's KDE support
         const double smin = zs[lo] - KDE_MARGIN * b, smax = zs[lo + segv[l] - 1] + KDE_MARGIN * b;
-        double a0 = fmax(ceil((z - KW64 * b) / dz), ceil(smin / dz));
-        double a1 = fmin(floor((z + KW64 * b) / dz), floor(smax / dz));
+        const double half = epan ? 2.23606797749978969641 * b : KW64 * b;
+        double a0 = fmax(ceil((z - half) / dz), ceil(smin / dz));
+        double a1 = fmin(floor((z + half) / dz), floor(smax / dz));
         int ia0 = a0 < 0.0 ? 0 : (a0 > nz ? nz : (int)a0);
         int ia1 = a1 > nz - 1 ? nz - 1 : (a1 < -1.0 ? -1 : (int)a1);
         double s = 0.0;
         for (int a = ia0; a <= ia1; a++) {
             double x = (a * dz - z) / b;
             double wa = (a == 0 || a == nz - 1) ? 0.5 : 1.0;
-            s += exp(-0.5 * x * x) * wa * F[a] * G[a];
+            const double kx = epan ? fmax(0.0, 1.0 - 0.2 * x * x) : exp(-0.5 * x * x);
+            s += kx * wa * F[a] * G[a];
         }
         tsum += c.seg_pf[sg0 + l] * w * s;
     }
@@ -868,7 +896,9 @@ __global__ void __launch_bounds__(EV64_THREADS) k_event_fp64(DevCatalog c, CallP
         block_sumd<1, EV64_THREADS>(v, red);
     }
     if (tid == 0) {
-        double I = red[0] * dz / (c.n_gal_total * 2.50662827463100050242 * b);
+        // kernel normalisation: 1/(sqrt(2 pi) b), or 3/(4 h) = 3/(4 sqrt5 b)
+        const double kn = epan ? 0.33541019662496845446 : 0.39894228040143267794;
+        double I = red[0] * dz * kn / (c.n_gal_total * b);
         p.lnI[out] = I > 0.0 ? log(I) : -CUDART_INF;
         p.bw[out] = b;
     }
@@ -897,11 +927,17 @@ void launch_event_mixed(const DevCatalog &c, const CallPtrs &p, int h0, int nh, 
 
 size_t event_binned_smem(const DevCatalog &c) { return BinLayout(c.max_ns, c.n_z, c.max_seg).bytes(); }
 
-void launch_event_binned(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cudaStream_t st) {
+void launch_event_binned(const DevCatalog &c, const CallPtrs &p, int h0, int nh, bool binned,
+                         cudaStream_t st) {
     size_t smem = event_binned_smem(c);
-    cudaFuncSetAttribute(k_event_binned, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const unsigned nb = (unsigned)((int64_t)c.n_events * nh);
-    if (nb) k_event_binned<<<nb, BN_THREADS, smem, st>>>(c, p, h0, nh);
+    if (binned) {
+        cudaFuncSetAttribute(k_event_binned<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (nb) k_event_binned<true><<<nb, BN_THREADS, smem, st>>>(c, p, h0, nh);
+    } else {
+        cudaFuncSetAttribute(k_event_binned<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (nb) k_event_binned<false><<<nb, BN_THREADS, smem, st>>>(c, p, h0, nh);
+    }
 }
 
 void launch_event_fp64(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st) {

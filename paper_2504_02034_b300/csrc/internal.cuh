@@ -150,6 +150,7 @@ struct CallPtrs {
     float *zw;                // [tile x 2 x n_zpad] reweighted samples (z row, then w row) of a
                               // tile of hyperpoints (mixed path)
     int32_t n_chunk;
+    int32_t kshape;           // KDE kernel: 0 Gaussian, 1 Epanechnikov
     double *lnL, *neff, *xi;  // [H]
     int32_t *status;          // [H]
     unsigned long long *pairs;  // [H] windowed-pair counter, or nullptr
@@ -192,9 +193,11 @@ void launch_profile_sum(const DevCatalog &c, const double *G64, const float *G32
 void launch_reweight(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cudaStream_t st);
 void launch_event_mixed(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cudaStream_t st);
 void launch_event_fp64(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st);
-// K4 with the binned KDE (CHIMERA_MIXED_BINNED), from the same tile buffer
-// as launch_event_mixed.
-void launch_event_binned(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cudaStream_t st);
+// K4 with the binned KDE (CHIMERA_MIXED_BINNED), or (binned = false) the
+// direct one-evaluation-per-pair form used for the Epanechnikov kernel, from
+// the same tile buffer as launch_event_mixed.
+void launch_event_binned(const DevCatalog &c, const CallPtrs &p, int h0, int nh, bool binned,
+                         cudaStream_t st);
 size_t event_binned_smem(const DevCatalog &c);
 size_t event_mixed_smem(const DevCatalog &c);
 size_t event_fp64_smem(const DevCatalog &c);

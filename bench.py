@@ -317,6 +317,36 @@ def binned_stats(pkg, ctx, torch, dev, theta, steps):
     return res
 
 
+def kernel_option_stats(pkg, ctx, torch, dev, cid, theta, NE, steps):
+    """The Epanechnikov kernel option (CHIMERA_KERNEL_EPANECHNIKOV, mixed) on
+    the benchmark catalog and batch, device-timed as the main step."""
+    H = theta.shape[0]
+    th_dev = torch.tensor(theta, device=dev, dtype=torch.float64)
+    out = torch.empty(H, device=dev, dtype=torch.float64)
+    neff = torch.empty_like(out)
+    st = torch.empty(H, device=dev, dtype=torch.int32)
+    flush = torch.empty(256 << 20, device=dev, dtype=torch.uint8)
+    stream = torch.cuda.current_stream(dev)
+    prec = pkg.MIXED | pkg.KERNEL_EPANECHNIKOV
+    for _ in range(3):
+        pkg.chimera_loglike_device(ctx.h, cid, th_dev, prec, out, neff, st, stream)
+    torch.cuda.synchronize()
+    ms, ev_ms = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pkg.chimera_loglike_device(ctx.h, cid, th_dev, prec, out, neff, st, stream)
+        e1.record(stream)
+        ev_ms.append(pkg.chimera_stage_ms(ctx.h)["event"])
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = sum(ms) / len(ms)
+    return {"epanechnikov_mixed": {"value": H * NE / (t * 1e-3), "unit": UNIT, "ms_per_step": t,
+                                   "event_kernel_ms": sum(ev_ms) / len(ev_ms),
+                                   "window": "|z - z_j| <= sqrt(5) b, one evaluation per pair"}}
+
+
 def om_varying_stats(pkg, ctx, cid, theta, NE, calls=3):
     """Walkers whose Om is new at every point (the differentiation workload's
     pattern): every call brings 16 Om values never seen before, so each pays
@@ -527,6 +557,7 @@ def main():
     grads = grad_stats(pkg, ctx, cid, theta, NE)
     binned = binned_stats(pkg, ctx, torch, dev, theta, max(3, args.steps // 2)) if rank == 0 else None
     om_var = om_varying_stats(pkg, ctx, cid, theta, NE) if rank == 0 else None
+    kern_opt = kernel_option_stats(pkg, ctx, torch, dev, cid, theta, NE, max(3, args.steps // 2)) if rank == 0 else None
     serving = serving_stream(pkg, ctx, cid, cat, args.serve_requests) if args.serve_requests > 0 and rank == 0 else None
 
     kern = sum(kern_ms) / len(kern_ms)
@@ -565,6 +596,7 @@ def main():
         "gradient": grads,
         "binned_kde": binned,
         "om_varying": om_var,
+        "kernel_options": kern_opt,
         "serving": serving,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(theta.nbytes),
                 "d2h_bytes_per_step": int(H * (8 + 8 + 4))},

@@ -465,6 +465,8 @@ def main():
                     help="length of the serving stream (0 skips it)")
     ap.add_argument("--profile", action="store_true",
                     help="run W warm-up launches and one more launch of the timed step, then exit (for ncu)")
+    ap.add_argument("--profile-grad", action="store_true",
+                    help="run W warm-up gradient calls (mixed, the benchmark batch) and one more, then exit (for ncu)")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -485,7 +487,7 @@ def main():
     H, NE = theta.shape[0], cat["n_events"]
     ctx = pkg.Context(local)
     cid = ctx.load(cat)
-    peaks = None if args.profile else pkg.chimera_peaks(ctx.h)
+    peaks = None if (args.profile or args.profile_grad) else pkg.chimera_peaks(ctx.h)
 
     th_dev = torch.tensor(theta, device=dev, dtype=torch.float64)
     out = torch.empty(H, device=dev, dtype=torch.float64)
@@ -501,6 +503,11 @@ def main():
         for _ in range(args.warmup + 1):
             step()
         torch.cuda.synchronize()
+        ctx.close()
+        return
+    if args.profile_grad:
+        for _ in range(args.warmup + 1):
+            pkg.chimera_grad(ctx.h, cid, theta, pkg.MIXED)
         ctx.close()
         return
     pkg.chimera_set_trace(ctx.h, True)

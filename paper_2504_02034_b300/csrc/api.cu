@@ -881,8 +881,13 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
             e = cudaMemcpy(lr.data(), prec ? c.dense_lr32 : c.dense_lr64, sizeof(int2) * nl, cudaMemcpyDeviceToHost);
             if (e != cudaSuccess) break;
             items.clear();
-            for (size_t i = 0; i < nl; i++)
-                if (lr[i].y > lr[i].x) items.push_back(make_int2((int)(i / c.n_z), (int)(i % c.n_z)));
+            for (int pass = 0; pass < 2; pass++)  // heavy ranges first, then light ones
+                for (size_t i = 0; i < nl; i++) {
+                    const int len = lr[i].y - lr[i].x;
+                    if (len > 0 && (len > GAL_HEAVY) == (pass == 0))
+                        items.push_back(make_int2((int)(i / c.n_z), (int)(i % c.n_z)));
+                    if (pass == 0 && i + 1 == nl) (prec ? c.n_dheavy32 : c.n_dheavy64) = (int64_t)items.size();
+                }
             int2 **dst = prec ? &c.dense_items32 : &c.dense_items64;
             (prec ? c.n_ditems32 : c.n_ditems64) = (int64_t)items.size();
             const size_t ib = sizeof(int2) * std::max<size_t>(items.size(), 1);

@@ -22,9 +22,9 @@
 //   gather: one block per pixel of at most GAL_DENSE galaxies, one grid
 //           point per thread, the galaxies whose window covers it (sorted by
 //           z inside the pixel at load time, found by binary search);
-//   dense:  one block per (dense pixel, grid point) with galaxies in reach
-//           (load-time lists), the covering galaxies spread over the block
-//           and added by a fixed-order tree.
+//   dense:  per (dense pixel, grid point) with galaxies in reach (load-time
+//           lists), a block (more than GAL_HEAVY candidates) or a warp, the
+//           candidates spread over its threads and added by a fixed tree.
 // Every sum has a fixed order, so a profile is reproducible bit for bit.
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -232,10 +232,12 @@ __global__ void k_dense_ranges(DevCatalog c, int2 *lr) {
     lr[i] = make_int2((int)(l - g0), (int)(r - g0));
 }
 
-// One block per (dense pixel, grid point) whose load-time candidate range
-// is not empty (the other points of a dense row are zeroed by the gather
-// kernel); the range is spread over the block and added by a fixed tree.
-template <bool F64, bool WITH_O>
+// Dense pixels, over the load-time lists of (dense pixel, grid point) pairs
+// whose candidate range is not empty (the other points of a dense row are
+// zeroed by the gather kernel).  HEAVY: one block per pair (ranges above
+// GAL_HEAVY galaxies), the range spread over the block and added by a fixed
+// tree; otherwise one warp per pair, added by a fixed xor tree.
+template <bool F64, bool WITH_O, bool HEAVY>
 __global__ void __launch_bounds__(GAL_THREADS) k_gal_gather_dense(DevCatalog c, const typename Gal<F64>::T *dv,
                                                                  const typename Gal<F64>::T *dvO,
                                                                  const typename Gal<F64>::T *invZ,
@@ -243,17 +245,27 @@ __global__ void __launch_bounds__(GAL_THREADS) k_gal_gather_dense(DevCatalog c, 
                                                                  typename Gal<F64>::T *out) {
     using T = typename Gal<F64>::T;
     __shared__ T red[2][GAL_THREADS / 32];
-    const int2 item = (F64 ? c.dense_items64 : c.dense_items32)[blockIdx.x];  // (dense index, grid point)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t n_heavy = F64 ? c.n_dheavy64 : c.n_dheavy32;
+    const int64_t n_all = F64 ? c.n_ditems64 : c.n_ditems32;
+    const int64_t idx = HEAVY ? (int64_t)blockIdx.x
+                              : n_heavy + (int64_t)blockIdx.x * (GAL_THREADS / 32) + wid;
+    if (!HEAVY && idx >= n_all) return;  // whole warps leave together
+    const int2 item = (F64 ? c.dense_items64 : c.dense_items32)[idx];  // (dense index, grid point)
     const int64_t p = c.dense_pix[item.x];
     const int a = item.y;
     const int64_t g0 = c.gal_off[p];
     const int2 lr = (F64 ? c.dense_lr64 : c.dense_lr32)[(int64_t)item.x * c.n_z + a];
     T s1 = T(0), s2 = T(0);
-    gather_range<F64, WITH_O>(c, p, a, g0 + lr.x + threadIdx.x, g0 + lr.y, GAL_THREADS, invZ, ZO, s1, s2);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (HEAVY) gather_range<F64, WITH_O>(c, p, a, g0 + lr.x + threadIdx.x, g0 + lr.y, GAL_THREADS, invZ, ZO, s1, s2);
+    else gather_range<F64, WITH_O>(c, p, a, g0 + lr.x + lane, g0 + lr.y, 32, invZ, ZO, s1, s2);
     for (int o = 16; o > 0; o >>= 1) {
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
         if (WITH_O) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (!HEAVY) {
+        if (lane == 0) out[p * c.n_z + a] = gather_out<F64, WITH_O>(dv, dvO, a, s1, s2);
+        return;
     }
     if (lane == 0) {
         red[0][wid] = s1;
@@ -278,9 +290,14 @@ void launch_profile_t(const DevCatalog &c, const typename Gal<F64>::T *dv, const
     if (c.n_gw > 0) k_gal_norm<F64, WITH_O><<<(unsigned)c.n_gw, GAL_CHUNK, 0, st>>>(c, dv, dvO, invZ, ZO);
     k_gal_gather<F64, WITH_O><<<(unsigned)c.n_pix, GAL_THREADS, 0, st>>>(c, dv, dvO, invZ, ZO, out);
     {
-        const int64_t ni = F64 ? c.n_ditems64 : c.n_ditems32;
-        if (ni > 0)
-            k_gal_gather_dense<F64, WITH_O><<<(unsigned)ni, GAL_THREADS, 0, st>>>(c, dv, dvO, invZ, ZO, out);
+        const int64_t nh = F64 ? c.n_dheavy64 : c.n_dheavy32;
+        const int64_t nl = (F64 ? c.n_ditems64 : c.n_ditems32) - nh;
+        const int wpb = GAL_THREADS / 32;
+        if (nh > 0)
+            k_gal_gather_dense<F64, WITH_O, true><<<(unsigned)nh, GAL_THREADS, 0, st>>>(c, dv, dvO, invZ, ZO, out);
+        if (nl > 0)
+            k_gal_gather_dense<F64, WITH_O, false>
+                <<<(unsigned)((nl + wpb - 1) / wpb), GAL_THREADS, 0, st>>>(c, dv, dvO, invZ, ZO, out);
     }
 }
 

@@ -26,6 +26,7 @@ constexpr double KW64 = 9.0;
 constexpr float KWG32 = 6.0f;
 constexpr int GAL_CHUNK = 256;   // galaxies per normalisation block
 constexpr int GAL_DENSE = 1024;  // pixels above this gather per grid point by blocks
+constexpr int GAL_HEAVY = 256;   // dense-pixel points with more candidates: a block each
 // Each KDE is zero outside the grid segment holding its samples, widened by
 // KDE_MARGIN bandwidths (Sec. 2.3: evaluated only where the samples are).
 constexpr double KDE_MARGIN = 6.0;
@@ -118,8 +119,9 @@ struct DevCatalog {
     // filled on the device at load
     int2 *dense_lr64, *dense_lr32;
     // the (dense pixel index, grid point) pairs whose range is not empty,
-    // per precision (built at load from the ranges)
-    int64_t n_ditems64, n_ditems32;
+    // per precision (built at load from the ranges): the first n_dheavy hold
+    // more than GAL_THREADS galaxies (a block each), the rest a warp each
+    int64_t n_ditems64, n_ditems32, n_dheavy64, n_dheavy32;
     int2 *dense_items64, *dense_items32;
     // galaxies
     double *gz64, *gs64;  // FP64 values

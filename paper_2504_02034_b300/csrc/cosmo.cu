@@ -167,19 +167,20 @@ __global__ void __launch_bounds__(HYP_THREADS) k_nodes_grid(DevCatalog c, CallPt
 // Hermite-interpolated forward relation.  A block computes the nodes
 // base .. base+256 (one more than it owns) so that it also writes the FP32
 // node pairs of its intervals.
-__global__ void __launch_bounds__(HYP_THREADS) k_inv_nodes(DevCatalog c, CallPtrs p, const float2 *djall) {
+constexpr int INV_THREADS = 128;  // FP64-bound: 2049 nodes x H spread over every SM
+__global__ void __launch_bounds__(INV_THREADS) k_inv_nodes(DevCatalog c, CallPtrs p, const float2 *djall) {
     __shared__ float sdk[NT_FWD];
-    __shared__ double2 snd[HYP_THREADS + 1];
+    __shared__ double2 snd[INV_THREADS + 1];
     const int h = blockIdx.y;
-    const int base = blockIdx.x * HYP_THREADS;
+    const int base = blockIdx.x * INV_THREADS;
     const float2 *dj = djall + (size_t)h * NT_FWD;
-    for (int i = threadIdx.x; i < NT_FWD; i += HYP_THREADS) sdk[i] = dj[i].x;
+    for (int i = threadIdx.x; i < NT_FWD; i += INV_THREADS) sdk[i] = dj[i].x;
     __syncthreads();
     const double *th = p.theta + 12 * h;
     const double *fwd = p.fwd[h];
     const double cH = C_KMS / th[0], Om = th[1];
     const double dtop = c.d_top;
-    for (int t = threadIdx.x; t <= HYP_THREADS; t += HYP_THREADS) {
+    for (int t = threadIdx.x; t <= INV_THREADS; t += INV_THREADS) {
         const int k = base + t;
         if (k > NU) break;
         const double u = (double)k / NU, d = dtop * u * u;
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(HYP_THREADS) k_inv_nodes(DevCatalog c, CallPtr
             }
         }
         snd[t] = make_double2(z, dzdu);
-        if (t < HYP_THREADS || k == NU) p.inv64[(size_t)h * (NU + 1) + k] = snd[t];
+        if (t < INV_THREADS || k == NU) p.inv64[(size_t)h * (NU + 1) + k] = snd[t];
     }
     __syncthreads();
     const int k = base + threadIdx.x;
@@ -344,7 +345,7 @@ void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp6
     const int nbn = (NT_FWD + HYP_THREADS - 1) / HYP_THREADS;
     const int nbg = (c.n_z + HYP_THREADS - 1) / HYP_THREADS;
     k_nodes_grid<<<dim3(nbn + nbg, H), HYP_THREADS, 0, st>>>(c, p, dj, fmax_bits, nbn, fp64);
-    k_inv_nodes<<<dim3((NU + HYP_THREADS - 1) / HYP_THREADS, H), HYP_THREADS, 0, st>>>(c, p, dj);
+    k_inv_nodes<<<dim3((NU + INV_THREADS - 1) / INV_THREADS, H), INV_THREADS, 0, st>>>(c, p, dj);
     k_hyper_final<<<dim3(fp64 ? 1 : nbg, H), HYP_THREADS, 0, st>>>(c, p, fmax_bits, fp64);
 }
 

@@ -51,7 +51,7 @@ struct AdjPtrs {
     double *dznode;              // [H x (NU+1) x 4] dz/d(H0, Om, Xi0, n) at the inverse-table nodes
     float4 *dznode32;            // [H x (NU+1)] FP32 copy
     double *Q;                   // [H x n_z x 7] d ln F / d(H0, Om, Xi0, n, gamma, kappa, z_p)
-    float *Q32;                  // [H x n_z x 8] FP32 copy, padded to 8
+    float *QT;                   // [H x n_z x AM_QT] FP32 (Q_k, dQ_k/dz, d2Q_k/dz2 / 2), k = Om .. z_p
     double *dlnI;                // [H x n_events x 12]
     double *selg;                // [H x n_chunk x 13] sum s dln s / dtheta (12), sum s
     double *grad;                // [H x 12]
@@ -269,10 +269,43 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_tables(DevCatalog c, CallPt
         o[4] = g3[0];
         o[5] = g3[1];
         o[6] = g3[2];
-        float *o32 = q.Q32 + ((size_t)h * c.n_z + a) * 8;
-        for (int j = 0; j < 7; j++) o32[j] = (float)o[j];
-        o32[7] = 0.f;
     }
+}
+
+// The FP32 second-order Taylor table of d ln F / dtheta on the grid for the
+// mixed adjoint: per grid point and k = Om, Xi0, n, gamma, kappa, z_p the
+// value, first derivative and half the second derivative in z, by central
+// differences of the FP64 table (one-sided at the grid ends).
+constexpr int AM_QT = 20;  // 18 used, padded to five float4
+__global__ void k_q_taylor(DevCatalog c, AdjPtrs q, int H) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int nz = c.n_z;
+    if (i >= (int64_t)H * nz) return;
+    const int h = (int)(i / nz), a = (int)(i % nz);
+    float *o = q.QT + (size_t)i * AM_QT;
+    if (nz < 3) {  // no stencil: the value alone
+        const double *Qa = q.Q + ((size_t)h * nz + a) * 7;
+        for (int k = 1; k < 7; k++) {
+            o[3 * (k - 1)] = (float)Qa[k];
+            o[3 * (k - 1) + 1] = 0.f;
+            o[3 * (k - 1) + 2] = 0.f;
+        }
+        o[18] = o[19] = 0.f;
+        return;
+    }
+    const int am = a == 0 ? 0 : (a == nz - 1 ? nz - 3 : a - 1);  // three consecutive points
+    const double *Q = q.Q + ((size_t)h * nz + am) * 7;
+    const double idz = 1.0 / c.dz, t = (double)(a - am - 1);  // a relative to the middle point
+    for (int k = 1; k < 7; k++) {
+        const double q0 = Q[k], q1 = Q[7 + k], q2 = Q[14 + k];
+        const double d1 = 0.5 * (q2 - q0) * idz, d2 = (q2 - 2.0 * q1 + q0) * idz * idz;
+        // value and slope at a from the parabola through the three points
+        o[3 * (k - 1)] = (float)(q1 + d1 * t * c.dz + 0.5 * d2 * t * t * c.dz * c.dz);
+        o[3 * (k - 1) + 1] = (float)(d1 + d2 * t * c.dz);
+        o[3 * (k - 1) + 2] = (float)(0.5 * d2);
+    }
+    o[18] = 0.f;
+    o[19] = 0.f;
 }
 
 // dz/dtheta of a sample by linear interpolation between inverse-table nodes
@@ -554,22 +587,33 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
 // so that with P_X(B) = sum_tau X_tau C_tau H(a) B^tau
 //   S0 = e^{-u^2} P_1,  S1 = sqrt2 e^{-u^2} (ds P_tau - u P_1),
 //   S2 = 2 e^{-u^2} (ds^2 P_tau2 - 2 ds u P_tau + u^2 P_1),
-// and the grid term, sum_a M(a) Q_k(a) = sum_j pf w_j sum_a e_ja H(a) Q_k(a),
-// is the per-sample sum with X = Q_k (likewise for w'_a F dG/dOm).  Q for
-// H0 is 1/H0 at every z (J is proportional to c/H0), so its sum is S0/H0;
-// the other ten polynomials are evaluated together by Horner's rule (one FMA
-// per polynomial, sample and grid point) from a table of 10 floats per
-// offset, staged by the warp in chunks of AM_CH offsets per side, the +m and
-// -m rows side by side.  Runs hold up to 64 neighbouring samples of one
-// group (one or two per lane) whose spread is at most 16 b; beyond 8 b the
-// table is scaled by e^20 (undone in e^{-u^2}), which keeps every
-// coefficient and intermediate in the normal float range.  Kernels narrower
-// than ~0.7 grid steps (ds > 0.5) use direct exponentials.  Each lane then
-// takes its samples' own derivative terms (dz/dtheta, d ln w/dtheta and
-// Scott's rule) from the run's sums, left in the warp's table space.
+// and the galaxy term sum_a e_ja w'_a F dG/dOm is a fourth polynomial.  The
+// four are evaluated together by Horner's rule (one FMA per polynomial,
+// sample and grid point) from a table of 4 floats per offset, staged by the
+// warp in chunks of AM_CH offsets per side, the +m and -m rows side by side.
+//
+// The grid term, sum_a M(a) Q_k(a) = sum_j pf w_j sum_a e_ja H(a) Q_k(a),
+// needs per sample sum_a e_ja H(a) Q_k(a).  Q_k = d ln F / dtheta_k is a
+// smooth function of z (Q for H0 is exactly 1/H0); over a window of +-6 b
+// it is replaced by its second-order Taylor polynomial about the sample's
+// grid point a_j, so that
+//   sum_a e H Q_k = Q_k S0 + Q_k' m1 + (Q_k''/2) m2,
+//   m1 = b S1 + d S0,  m2 = b^2 S2 + 2 d b S1 + d^2 S0,  d = z_j - z_aj,
+// with (Q, Q', Q''/2) from a per-grid-point FP32 table (central differences
+// of the FP64 table).  The truncation is third order in the window, ~1e-5
+// of the term at the benchmark's bandwidths, below the mixed path's FP32
+// error budget for the gradient.
+//
+// Runs hold up to 64 neighbouring samples of one group (one or two per lane)
+// whose spread is at most 16 b; beyond 8 b the table is scaled by e^20
+// (undone in e^{-u^2}), which keeps every coefficient and intermediate in the
+// normal float range.  Kernels narrower than ~0.7 grid steps (ds > 0.5) use
+// direct exponentials.  Each lane then takes its samples' own derivative
+// terms (dz/dtheta, d ln w/dtheta and Scott's rule) from the run's sums, left
+// in the warp's table space.
 constexpr int AM_THREADS = ADJ_THREADS, AM_WARPS = AM_THREADS / 32;
 constexpr int AM_CH = 64;
-constexpr int AM_NP = 10;              // polynomials (table floats per offset)
+constexpr int AM_NP = 4;               // polynomials (table floats per offset)
 constexpr int AM_SLOT = 2 * AM_NP / 4;  // float4 per slot: the +m and -m rows
 constexpr int AM_SLOTS = AM_CH + 1;     // per warp; slot AM_CH holds tau = 0
 constexpr int AM_RUN = 64;              // samples per run
@@ -739,9 +783,11 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
     for (int k = 0; k < 9; k++) { A9[k] = 0.f; db9[k] = 0.f; }
     for (int k = 0; k < 4; k++) B4[k] = 0.f;
     for (int k = 0; k < 8; k++) C8[k] = 0.f;
-    // one valid sample with its sums Sv = (S0, S1, S2, sums over Q_1 .. Q_6,
-    // sum over dG/dOm), H without the segment prefactor
+    // one valid sample with its sums Sv = (S0, S1, S2, sum over dG/dOm), H
+    // without the segment prefactor; the grid-term sums over Q_k come from
+    // S0, S1, S2 and the sample's Taylor row (see the kernel's comment)
     const float iH0 = 1.f / hp.h0_32;
+    const float4 *QT4 = reinterpret_cast<const float4 *>(q.QT + (size_t)h * nz * AM_QT);
     auto sample_terms = [&](int j, float pf, const float (&Sv)[AM_NP]) {
         const float S0 = Sv[0], S1 = Sv[1], S2 = Sv[2];
         const float z = zs[j], w = ws[j], a1 = 1.f + z;
@@ -780,7 +826,21 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
         for (int k = 0; k < 9; k++) A9[k] += pw * S0 * dlw[k];
         for (int k = 0; k < 4; k++) B4[k] += pwb * dd[k];
         C8[0] += pw * S0 * iH0;
-        for (int k = 1; k < 8; k++) C8[k] += pw * Sv[2 + k];
+        {
+            // moments of e H about the sample's grid point a_j:
+            // m1 = sum e H (z_a - z_aj), m2 = sum e H (z_a - z_aj)^2
+            const int aj = min(nz - 1, max(0, (int)rintf(z * inv_dz)));
+            const float dl = z - aj * dz, bS1 = b * S1;
+            const float m1 = fmaf(dl, S0, bS1), m2 = fmaf(b * b, S2, dl * fmaf(dl, S0, 2.f * bS1));
+            const float4 *row = QT4 + (size_t)aj * (AM_QT / 4);
+            const float4 r0 = __ldg(row), r1 = __ldg(row + 1), r2 = __ldg(row + 2), r3 = __ldg(row + 3),
+                         r4 = __ldg(row + 4);
+            const float t[18] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x,
+                                 r2.y, r2.z, r2.w, r3.x, r3.y, r3.z, r3.w, r4.x, r4.y};
+#pragma unroll
+            for (int k = 0; k < 6; k++) C8[1 + k] += pw * fmaf(t[3 * k + 2], m2, fmaf(t[3 * k + 1], m1, t[3 * k] * S0));
+        }
+        C8[7] += pw * Sv[3];
     };
 
     float4 *tw = rows + AM_SLOT * wid * AM_SLOTS;  // this warp's table
@@ -788,7 +848,6 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
     float *buf = twf;  // a run's per-sample sums [k][idx], after its chains
     const float *prof = reinterpret_cast<const float *>(p.prof[h]);
     const float *dprof = reinterpret_cast<const float *>(q.dprof[h]);  // FP32 on this path
-    const float4 *Q4 = reinterpret_cast<const float4 *>(q.Q32 + (size_t)h * nz * 8);
     // groups in a fixed warp assignment (the sums do not depend on timing)
     for (int g = wid; g < ngroups; g += AM_WARPS) {
         const int4 gi = __ldg(c.groups + g0 + g);
@@ -814,13 +873,10 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
                         const float x = (a * dz - z) * inv_s2b;
                         const float e = __expf(-x * x) * Fs[a];
                         const float eh = e * __ldg(G + a), U = 1.41421356f * x;
-                        const float4 qa = __ldg(Q4 + 2 * a), qb = __ldg(Q4 + 2 * a + 1);
                         Sv[0] += eh;
                         Sv[1] += eh * U;
                         Sv[2] += eh * U * U;
-                        Sv[3] += eh * qa.y; Sv[4] += eh * qa.z; Sv[5] += eh * qa.w;
-                        Sv[6] += eh * qb.x; Sv[7] += eh * qb.y; Sv[8] += eh * qb.z;
-                        Sv[9] += e * __ldg(dG + a);
+                        Sv[3] += e * __ldg(dG + a);
                     }
                 }
                 for (int k = 0; k < AM_NP; k++) buf[k * AM_RUN + idx] = Sv[k];
@@ -865,29 +921,26 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
                     else if (i < 2 * nr) { tau = -(mhi - (i - nr)); dst = twf + 4 * AM_SLOT * (i - nr) + AM_NP; }
                     else { tau = 0; dst = twf + 4 * AM_SLOT * AM_CH; }
                     const int a = t_o + tau;
-                    float2 r0 = make_float2(0.f, 0.f), r1 = r0, r2 = r0, r3 = r0, r4 = r0;
+                    float2 r0 = make_float2(0.f, 0.f), r1 = r0;
                     if (a >= A0 && a <= A1) {
                         const float x = ds * (float)tau;
                         const float cf = __expf(lnscale - x * x) * Fs[a];
                         const float hh = cf * __ldg(G + a);
-                        const float4 qa = __ldg(Q4 + 2 * a), qb = __ldg(Q4 + 2 * a + 1);
                         const float tt = (float)tau;
                         r0 = make_float2(hh, tt * hh);
-                        r1 = make_float2(tt * tt * hh, hh * qa.y);
-                        r2 = make_float2(hh * qa.z, hh * qa.w);
-                        r3 = make_float2(hh * qb.x, hh * qb.y);
-                        r4 = make_float2(hh * qb.z, cf * __ldg(dG + a));
+                        r1 = make_float2(tt * tt * hh, cf * __ldg(dG + a));
                     }
                     float2 *d2 = reinterpret_cast<float2 *>(dst);
-                    d2[0] = r0; d2[1] = r1; d2[2] = r2; d2[3] = r3; d2[4] = r4;
+                    d2[0] = r0;
+                    d2[1] = r1;
                 }
                 __syncwarp();
 #pragma unroll 2
                 for (int i = 0; i < nr; i++) {
                     const float4 *sl = tw + AM_SLOT * i;
-                    const float4 v0 = sl[0], v1 = sl[1], v2 = sl[2], v3 = sl[3], v4 = sl[4];
-                    const float cf_[AM_NP] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y};
-                    const float cb_[AM_NP] = {v2.z, v2.w, v3.x, v3.y, v3.z, v3.w, v4.x, v4.y, v4.z, v4.w};
+                    const float4 v0 = sl[0], v1 = sl[1];
+                    const float cf_[AM_NP] = {v0.x, v0.y, v0.z, v0.w};
+                    const float cb_[AM_NP] = {v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
                     for (int r = 0; r < R; r++)
 #pragma unroll
@@ -897,9 +950,8 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
                         }
                 }
                 if (last) {
-                    const float4 *sl = tw + AM_SLOT * AM_CH;
-                    const float4 v0 = sl[0], v1 = sl[1], v2 = sl[2];
-                    const float c0_[AM_NP] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y};
+                    const float4 v0 = tw[AM_SLOT * AM_CH];
+                    const float c0_[AM_NP] = {v0.x, v0.y, v0.z, v0.w};
 #pragma unroll
                     for (int r = 0; r < R; r++)
 #pragma unroll
@@ -919,8 +971,7 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
                 buf[idx] = P[0];
                 buf[AM_RUN + idx] = 1.41421356f * (ds * P[1] - uu * P[0]);
                 buf[2 * AM_RUN + idx] = 2.f * (ds * ds * P[2] - 2.f * ds * uu * P[1] + uu * uu * P[0]);
-#pragma unroll
-                for (int k = 3; k < AM_NP; k++) buf[k * AM_RUN + idx] = P[k];
+                buf[3 * AM_RUN + idx] = P[3];
             }
         };
         for (int st = 0; st < cnt;) {
@@ -1178,6 +1229,10 @@ size_t adjoint_event_smem(const DevCatalog &c, bool fp64) {
 
 void launch_adjoint(const DevCatalog &c, const CallPtrs &p, const AdjPtrs &q, int H, bool fp64, cudaStream_t st) {
     k_adj_tables<<<dim3(H, 8), ADJ_THREADS, 0, st>>>(c, p, q);
+    if (!fp64) {
+        const int64_t n = (int64_t)H * c.n_z;
+        k_q_taylor<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c, q, H);
+    }
     const size_t smem = adjoint_event_smem(c, fp64);
     const unsigned nb = (unsigned)((int64_t)c.n_events * H);
     if (fp64) {
@@ -1209,7 +1264,7 @@ size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Layout of the adjoint scratch for H points of catalog c.
 struct AdjLayout {
-    size_t o_ptrs, o_hpd, o_dzn, o_dzn32, o_Q, o_Q32, o_dlnI, o_selg, o_dv, o_dvO, o_invZ, o_ZO, total;
+    size_t o_ptrs, o_hpd, o_dzn, o_dzn32, o_Q, o_QT, o_dlnI, o_selg, o_dv, o_dvO, o_invZ, o_ZO, total;
     AdjLayout(const DevCatalog &c, int H, int nchunk) {
         size_t o = 0;
         auto take = [&](size_t b) { size_t r = o; o += al256(b); return r; };
@@ -1218,7 +1273,7 @@ struct AdjLayout {
         o_dzn = take(sizeof(double) * 4 * (size_t)H * (NU + 1));
         o_dzn32 = take(sizeof(float4) * (size_t)H * (NU + 1));
         o_Q = take(sizeof(double) * 7 * (size_t)H * c.n_z);
-        o_Q32 = take(sizeof(float) * 8 * (size_t)H * c.n_z);
+        o_QT = take(sizeof(float) * AM_QT * (size_t)H * c.n_z);
         o_dlnI = take(sizeof(double) * 12 * (size_t)H * c.n_events);
         o_selg = take(sizeof(double) * 13 * (size_t)H * std::max(nchunk, 1));
         o_dv = take((sizeof(double) + sizeof(float)) * c.n_z);  // FP64 values, then their FP32 copy
@@ -1363,7 +1418,7 @@ int backward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, int precision) {
     q.dznode = reinterpret_cast<double *>(ws.gscr + L.o_dzn);
     q.dznode32 = reinterpret_cast<float4 *>(ws.gscr + L.o_dzn32);
     q.Q = reinterpret_cast<double *>(ws.gscr + L.o_Q);
-    q.Q32 = reinterpret_cast<float *>(ws.gscr + L.o_Q32);
+    q.QT = reinterpret_cast<float *>(ws.gscr + L.o_QT);
     q.dlnI = reinterpret_cast<double *>(ws.gscr + L.o_dlnI);
     q.selg = reinterpret_cast<double *>(ws.gscr + L.o_selg);
     q.grad = ws.grad;

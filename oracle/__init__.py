@@ -51,6 +51,9 @@ class _Cat(C.Structure):
         ("lambda_g", C.c_double), ("beta", C.c_double),
         ("kde_mode", C.c_int32),
         ("kernel", C.c_int32),
+        ("f_R", C.c_double),
+        ("pix_area", C.POINTER(C.c_double)),
+        ("completeness", C.POINTER(C.c_double)),
     ]
 
 
@@ -142,6 +145,9 @@ class Catalog:
             float(cat["lambda_g"]), float(cat["beta"]),
             int(cat["kde_mode"] if kde_mode is None else kde_mode),
             int(kernel),
+            float(cat.get("f_R", 1.0)),
+            _p(arr("pix_area", np.float64)) if cat.get("completeness") is not None else None,
+            _p(arr("completeness", np.float64)) if cat.get("completeness") is not None else None,
         )
 
     @property

@@ -14,6 +14,11 @@
  *    widened by ORC_KDE_MARGIN bandwidths                         (Sec. 2.3)
  *  - galaxy Gaussians normalised on the same grid (discrete Z_g), w_g = 1,
  *    prefactor 1/N_gal,tot; complete catalog (f_R = 1)        (Eq. p-cat)
+ *  - incomplete catalog (Eqs. p-gal, p-miss, f-R) when a completeness is
+ *    given: the completeness P_compl of each pixel on the grid, the pixel's
+ *    solid angle and f_R are inputs (the paper leaves the completeness model
+ *    to the analysis; f_R is a full-sky integral); the pixel's galaxy mass is
+ *    f_R G_cat + (dOmega/4 pi)(1 - P_compl) dV_c/dz / V_c(z_max)
  *  - sky factor S_ik is an input density per steradian  (Eq. gw-kernel-many1d)
  *  - PE priors uniform: pi_PE = 1                                (Sec. 3.2)
  *  - mass model without low-edge smoothing; lambda_g, beta fixed (Sec. 3.1)
@@ -427,7 +432,7 @@ int orc_event_kde_binned(const orc_catalog *c, const double *th, int64_t ev,
  * Z_g = sum_a w_a N(z_a; z_g, s_g) dV_c/dz(z_a); galaxies with Z_g = 0
  * are dropped.                                                            */
 static void galaxy_profile_dv(const orc_catalog *c, int64_t ev, int32_t pixel,
-                              const double *dv, double *G) {
+                              const double *dv, double vmax, double *G) {
     int64_t p = c->pix_off[ev] + pixel;
     for (int64_t a = 0; a < c->n_z; a++) G[a] = 0.0;
     for (int64_t g = c->gal_off[p]; g < c->gal_off[p + 1]; g++) {
@@ -445,6 +450,15 @@ static void galaxy_profile_dv(const orc_catalog *c, int64_t ev, int32_t pixel,
         }
     }
     for (int64_t a = 0; a < c->n_z; a++) G[a] *= dv[a] / c->n_gal_total;
+    if (c->completeness) {
+        /* incomplete catalog: the pixel's mass of p_gal = f_R p_cat +
+         * (1 - f_R) p_miss, the missing galaxies homogeneous in comoving
+         * volume (Eq. p-miss): (dOmega_k / 4 pi) (1 - P_compl) dV_c/dz / V_c(z_max) */
+        const double area = c->pix_area[p] / (4.0 * M_PI);
+        const double *P = c->completeness + p * c->n_z;
+        for (int64_t a = 0; a < c->n_z; a++)
+            G[a] = c->f_R * G[a] + area * (1.0 - P[a]) * dv[a] / vmax;
+    }
 }
 
 static void grid_dvdz(const orc_catalog *c, const double *th, const orc_hooks *hk, double *dv) {
@@ -452,12 +466,18 @@ static void grid_dvdz(const orc_catalog *c, const double *th, const orc_hooks *h
         dv[a] = (hk->flags & 2) ? 1.0 : orc_dVc_dz(grid_z(c, a), th[0], th[1]);
 }
 
+/* V_c(z_max), the normalisation of the homogeneous missing-galaxy prior
+ * (Eq. p-miss); z_max under the dV_c/dz := 1 test hook. */
+static double grid_vmax(const orc_catalog *c, const double *th, const orc_hooks *hk) {
+    return (hk->flags & 2) ? c->z_max : orc_Vc(c->z_max, th[0], th[1]);
+}
+
 int orc_galaxy_profile(const orc_catalog *c, const double *th, int64_t ev,
                        int32_t pixel, const orc_hooks *hk, double *G) {
     if (!hk) hk = &default_hooks;
     double *dv = malloc(sizeof(double) * c->n_z);
     grid_dvdz(c, th, hk, dv);
-    galaxy_profile_dv(c, ev, pixel, dv, G);
+    galaxy_profile_dv(c, ev, pixel, dv, grid_vmax(c, th, hk), G);
     free(dv);
     return 0;
 }
@@ -480,6 +500,7 @@ int orc_grid_factor(const orc_catalog *c, const double *th,
  * single-1D: I = sum_a w_a K(z_a) F(z_a) sum_k S_k G_k(z_a)              */
 static double event_lnI_impl(const orc_catalog *c, const double *th, int64_t ev,
                              const orc_hooks *hk, const double *F, const double *dv, int binned) {
+    const double vmax = c->completeness ? grid_vmax(c, th, hk) : 1.0;
     int64_t n = c->sample_off[ev + 1] - c->sample_off[ev];
     int64_t nz = c->n_z;
     int32_t npix = (int32_t)(c->pix_off[ev + 1] - c->pix_off[ev]);
@@ -494,7 +515,7 @@ static double event_lnI_impl(const orc_catalog *c, const double *th, int64_t ev,
         for (int32_t k = 0; k < npix; k++) {
             double S = c->sky_S[c->pix_off[ev] + k];
             kde_grid(c, ev, k, z, w, v, b, binned, K);
-            galaxy_profile_dv(c, ev, k, dv, G);
+            galaxy_profile_dv(c, ev, k, dv, vmax, G);
             double s = 0.0;
             for (int64_t a = 0; a < nz; a++) s += grid_w(c, a) * K[a] * F[a] * G[a];
             I += S * s;
@@ -503,7 +524,7 @@ static double event_lnI_impl(const orc_catalog *c, const double *th, int64_t ev,
         kde_grid(c, ev, -1, z, w, v, b, binned, K);
         for (int32_t k = 0; k < npix; k++) {
             double S = c->sky_S[c->pix_off[ev] + k];
-            galaxy_profile_dv(c, ev, k, dv, G);
+            galaxy_profile_dv(c, ev, k, dv, vmax, G);
             for (int64_t a = 0; a < nz; a++) Gs[a] += S * G[a];
         }
         for (int64_t a = 0; a < nz; a++) I += grid_w(c, a) * K[a] * F[a] * Gs[a];

@@ -65,6 +65,12 @@ typedef struct {
     double lambda_g, beta;
     int32_t kde_mode;
     int32_t kernel;                 /* ORC_KERNEL_GAUSSIAN or ORC_KERNEL_EPANECHNIKOV */
+    /* incomplete catalog (Eqs. p-gal, p-miss, f-R), or completeness = NULL
+     * for a complete one: f_R, the solid angle of each flat pixel [sr] and
+     * the completeness P_compl of each pixel on the grid [n_pix_total x n_z] */
+    double f_R;
+    const double *pix_area;
+    const double *completeness;
 } orc_catalog;
 
 /* ---- cosmology (Eqs. dL-em, dL-mg, jacobian) ---- */

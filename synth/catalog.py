@@ -276,6 +276,29 @@ def make_catalog(*, n_events, n_pe, n_inj, n_z, Xi0, photo=False,
     )
 
 
+def add_completeness(cat, *, seed, f_R=0.75, width=0.05, zc_range=(0.3, 1.0)):
+    """An incomplete-catalog version of `cat` (Eqs. p-gal, p-miss, f-R): each
+    pixel gets its solid angle (side^2 of the tangent-plane square, recovered
+    from its sample count and sky factor: S_k = (N_k / N_s) / Delta Omega_k)
+    and a completeness that falls from 1 to 0 around a pixel redshift z_c
+    (logistic of width `width`, z_c uniform in zc_range) on the grid; f_R is
+    the catalog's full-sky completeness fraction, an input."""
+    rng = np.random.default_rng(seed)
+    out = dict(cat)
+    so, po = cat["sample_off"], cat["pix_off"]
+    area = np.empty(cat["sky_S"].size)
+    for e in range(cat["n_events"]):
+        ns = int(so[e + 1] - so[e])
+        cnt = np.bincount(cat["pix_of_sample"][so[e]:so[e + 1]], minlength=int(po[e + 1] - po[e]))
+        area[po[e]:po[e + 1]] = cnt / (ns * cat["sky_S"][po[e]:po[e + 1]])
+    za = cat["z_max"] * np.arange(cat["n_z"]) / (cat["n_z"] - 1)
+    zc = rng.uniform(zc_range[0], zc_range[1], area.size)
+    out["pix_area"] = area
+    out["completeness"] = np.ascontiguousarray(1.0 / (1.0 + np.exp((za[None, :] - zc[:, None]) / width)))
+    out["f_R"] = float(f_R)
+    return out
+
+
 def make_hyperpoints(n, *, seed, Xi0=1.0, vary_Om=False, width=0.01):
     """Walker hyperpoints: a Gaussian ball (width x prior range) about the
     fiducial, clipped to the walker box; Om held at 0.3 unless vary_Om."""

@@ -124,6 +124,18 @@ typedef struct chimera_ctx chimera_ctx;
  *  kde_mode        CHIMERA_KDE_SINGLE_1D or CHIMERA_KDE_MANY_1D.
  *  gal_storage     CHIMERA_GAL_F32 / F16 / BF16 (mixed path only; the FP64
  *                  path always uses the double values).
+ *  f_R, pix_area, completeness
+ *                  incomplete catalog (Eqs. p-gal, p-miss, f-R), or
+ *                  completeness = NULL for a complete one.  completeness
+ *                  [pix_off[n_events] x n_z] is P_compl of each pixel on the
+ *                  grid, in [0, 1]; pix_area [pix_off[n_events]] each pixel's
+ *                  solid angle [sr], > 0; f_R in [0, 1] the catalog's
+ *                  full-sky completeness fraction (Eq. f-R is an integral over
+ *                  the whole sky, which the events' pixels do not cover).
+ *                  Reading: p_gal = f_R p_cat + (1 - f_R) p_miss with the
+ *                  missing galaxies homogeneous in comoving volume (Eq.
+ *                  p-miss), so a pixel's galaxy term is
+ *                  f_R G_cat(z) + (pix_area/4 pi)(1 - P_compl(z)) dV_c/dz / V_c(z_max).
  */
 typedef struct {
     int32_t n_events;
@@ -143,6 +155,9 @@ typedef struct {
     double lambda_g, beta;
     int32_t kde_mode;
     int32_t gal_storage;
+    double f_R;
+    const double *pix_area;
+    const double *completeness;
 } chimera_catalog_desc;
 
 /* Footprint and sizes of a resident catalog (chimera_catalog_info_t). */

@@ -71,6 +71,9 @@ class CatalogDesc(C.Structure):
         ("lambda_g", C.c_double), ("beta", C.c_double),
         ("kde_mode", C.c_int32),
         ("gal_storage", C.c_int32),
+        ("f_R", C.c_double),
+        ("pix_area", C.POINTER(C.c_double)),
+        ("completeness", C.POINTER(C.c_double)),
     ]
 
 
@@ -185,7 +188,10 @@ def make_desc(cat):
         arr("inj_dL", np.float64), arr("inj_m1d", np.float64), arr("inj_m2d", np.float64),
         arr("inj_log_pi", np.float64),
         float(cat["lambda_g"]), float(cat["beta"]),
-        int(cat.get("kde_mode", KDE_MANY_1D)), int(cat.get("gal_storage", GAL_F32)))
+        int(cat.get("kde_mode", KDE_MANY_1D)), int(cat.get("gal_storage", GAL_F32)),
+        float(cat.get("f_R", 1.0)),
+        arr("pix_area", np.float64) if cat.get("completeness") is not None else None,
+        arr("completeness", np.float64) if cat.get("completeness") is not None else None)
     return d, keep
 
 

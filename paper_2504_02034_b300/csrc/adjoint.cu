@@ -59,24 +59,8 @@ struct AdjPtrs {
 
 namespace {
 
+using chimd::dcO_hermite;
 constexpr int ADJ_THREADS = 256;
-
-// Hermite interpolation of dDhat/dOm (node derivatives known in closed form).
-__device__ __forceinline__ double dcO_hermite(const double *fwdO, double z, double Om) {
-    double t = z / HT;
-    int k = (int)floor(t);
-    if (k < 0) k = 0;
-    if (k > NT_FWD - 2) k = NT_FWD - 2;
-    double f = t - k;
-    auto g = [Om](double zz) {
-        double a = 1.0 + zz, E = chimd::E_of(zz, Om);
-        return -0.5 * (a * a * a - 1.0) / (E * E * E);
-    };
-    double m0 = HT * g(k * HT), m1 = HT * g((k + 1) * HT);
-    double f2 = f * f, f3 = f2 * f;
-    return (2 * f3 - 3 * f2 + 1) * fwdO[k] + (f3 - 2 * f2 + f) * m0 + (-2 * f3 + 3 * f2) * fwdO[k + 1] +
-           (f3 - f2) * m1;
-}
 
 // Derivatives of the distance relation at redshift z for one hyperpoint
 // (Eq. dL-mg and its z-derivative J), given Dh = D_c / (c/H0) and
@@ -1335,7 +1319,7 @@ int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double O
         double *ZO = reinterpret_cast<double *>(ws.gscr + L.o_ZO);
         float *dv32 = reinterpret_cast<float *>(dv + c.n_z), *dvO32 = reinterpret_cast<float *>(dvO + c.n_z);
         k_dv_pair<<<(c.n_z + 63) / 64, 64, 0, ws.st>>>(fwd, fwdO, Om, c.dz, c.n_z, dv, dvO, dv32, dvO32);
-        launch_galaxy_dOm(c, dv, dvO, dv32, dvO32, f64, invZ, ZO, e.G, ws.st);
+        launch_galaxy_dOm(c, fwd, fwdO, Om, dv, dvO, dv32, dvO32, f64, invZ, ZO, e.G, ws.st);
         if (hb) {
             if (f64) k_dprofile_sum<<<c.n_events, 256, 0, ws.st>>>(c, (const double *)e.G, (double *)e.Gh);
             else k_dprofile_sum32<<<c.n_events, 256, 0, ws.st>>>(c, (const float *)e.G, (float *)e.Gh);

@@ -504,6 +504,10 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         return bad("lambda_g must lie in [0, 1] and beta be finite");
     if (d->kde_mode != CHIMERA_KDE_SINGLE_1D && d->kde_mode != CHIMERA_KDE_MANY_1D) return bad("bad kde_mode");
     if (d->gal_storage < 0 || d->gal_storage > 2) return bad("bad gal_storage");
+    if (d->completeness) {
+        if (!d->pix_area) return bad("an incomplete catalog needs pix_area");
+        if (!(d->f_R >= 0.0 && d->f_R <= 1.0)) return bad("f_R must lie in [0, 1]");
+    }
     if (d->sample_off[0] != 0 || d->pix_off[0] != 0) return bad("CSR offsets must start at 0");
     int max_ns = 0, max_np = 0;
     for (int i = 0; i < ne; i++) {
@@ -781,6 +785,26 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     std::vector<int64_t> ev_poff(d->pix_off, d->pix_off + ne + 1);
     std::vector<int64_t> goff(d->gal_off, d->gal_off + np + 1);
     std::vector<double> pixS(d->sky_S, d->sky_S + np);
+    // incomplete catalog: the missing-galaxy weight (1 - P_compl) pix_area / 4 pi
+    std::vector<double> miss64;
+    std::vector<float> miss32;
+    c.incomplete = d->completeness != nullptr;
+    c.f_R = d->completeness ? d->f_R : 1.0;
+    if (c.incomplete) {
+        const size_t nm = (size_t)np * (size_t)d->n_z;
+        miss64.resize(nm);
+        miss32.resize(nm);
+        for (int64_t p = 0; p < np; p++) {
+            const double ar = d->pix_area[p];
+            if (!(ar > 0.0) || !std::isfinite(ar)) return bad("pix_area must be positive");
+            for (int a = 0; a < d->n_z; a++) {
+                const double P = d->completeness[p * d->n_z + a];
+                if (!(P >= 0.0 && P <= 1.0)) return bad("completeness must lie in [0, 1]");
+                miss64[p * d->n_z + a] = (1.0 - P) * ar / (4.0 * M_PI);
+                miss32[p * d->n_z + a] = (float)miss64[p * d->n_z + a];
+            }
+        }
+    }
     // galaxy-profile work lists
     std::vector<int32_t> gw_pix, dense_pix;
     std::vector<int64_t> gw_g0;
@@ -814,6 +838,8 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         {(void **)&c.pix_sigmax32, sigmax32.data(), 4 * sigmax32.size()},
         {(void **)&c.pix_zref, zref.data(), 4 * zref.size()},
         {(void **)&c.gw_pix, gw_pix.data(), 4 * gw_pix.size()},
+        {(void **)&c.miss64, miss64.data(), 8 * miss64.size()},
+        {(void **)&c.miss32, miss32.data(), 4 * miss32.size()},
         {(void **)&c.gw_g0, gw_g0.data(), 8 * gw_g0.size()},
         {(void **)&c.dense_pix, dense_pix.data(), 4 * dense_pix.size()},
         {(void **)&c.gz64, gz.data(), 8 * gz.size()},

@@ -26,6 +26,12 @@
 //           lists), a block (more than GAL_HEAVY candidates) or a warp, the
 //           candidates spread over its threads and added by a fixed tree.
 // Every sum has a fixed order, so a profile is reproducible bit for bit.
+//
+// Incomplete catalogs (Eqs. p-gal, p-miss, f-R) add, after the gathers, the
+// missing galaxies, homogeneous in comoving volume: in the same N_gal,tot
+// units, G_k <- f_R G_k + N_gal,tot m_k(z_a) dV_c/dz(z_a) / V_c(z_max), with
+// m_k = (1 - P_compl) dOmega_k / 4 pi from the load and
+// dV_c/dz / V_c(z_max) = 3 dv / D_max^3 (dv = D^2/E, D in units of c/H0).
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
@@ -301,6 +307,45 @@ void launch_profile_t(const DevCatalog &c, const typename Gal<F64>::T *dv, const
     }
 }
 
+// The missing-galaxy term of an incomplete catalog, over the whole profile
+// (grid-stride); WITH_O writes its Om derivative, f_R dG + 3 N m (dv' -
+// 3 dv D_max'/D_max) / D_max^3, into the dG/dOm rows.  Thread 0 of each
+// block evaluates D_max (and D_max') once.
+template <bool F64, bool WITH_O>
+__global__ void __launch_bounds__(GAL_THREADS) k_gal_missing(DevCatalog c, const double *fwd, const double *fwdO,
+                                                            double Om, const typename Gal<F64>::T *dv,
+                                                            const typename Gal<F64>::T *dvO,
+                                                            typename Gal<F64>::T *out) {
+    using T = typename Gal<F64>::T;
+    __shared__ T s_c[2];
+    if (threadIdx.x == 0) {
+        const double D = chimd::dc_hermite(fwd, c.z_max, Om), D3 = D * D * D;
+        const double c1 = 3.0 * c.n_gal_total / D3;
+        s_c[0] = T(c1);
+        s_c[1] = WITH_O ? T(-3.0 * c1 * chimd::dcO_hermite(fwdO, c.z_max, Om) / D) : T(0);
+    }
+    __syncthreads();
+    const T c1 = s_c[0], c2 = s_c[1], fR = T(c.f_R);
+    const T *m = F64 ? (const T *)c.miss64 : (const T *)c.miss32;
+    const int nz = c.n_z;
+    const int64_t n = c.n_pix * nz;
+    for (int64_t i = blockIdx.x * (int64_t)GAL_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * GAL_THREADS) {
+        const int a = (int)(i % nz);
+        const T add = WITH_O ? m[i] * (c1 * dvO[a] + c2 * dv[a]) : m[i] * c1 * dv[a];
+        out[i] = fR * out[i] + add;
+    }
+}
+
+template <bool F64, bool WITH_O>
+void launch_missing_t(const DevCatalog &c, const double *fwd, const double *fwdO, double Om,
+                      const typename Gal<F64>::T *dv, const typename Gal<F64>::T *dvO,
+                      typename Gal<F64>::T *out, cudaStream_t st) {
+    if (!c.incomplete || c.n_pix == 0) return;
+    const int64_t n = c.n_pix * c.n_z;
+    const int64_t nb = std::min<int64_t>((n + GAL_THREADS - 1) / GAL_THREADS, 148 * 8);
+    k_gal_missing<F64, WITH_O><<<(unsigned)nb, GAL_THREADS, 0, st>>>(c, fwd, fwdO, Om, dv, dvO, out);
+}
+
 // Single-1D: sum_k S_k G_k(z_a) per event.
 __global__ void k_profile_sum(DevCatalog c, const double *G64, const float *G32, double *out64,
                               float *out32) {
@@ -327,8 +372,14 @@ void launch_galaxy_profile(const DevCatalog &c, const double *fwd, double Om, do
                            cudaStream_t st) {
     float *dv32 = reinterpret_cast<float *>(dv + c.n_z);
     k_dvdz<<<(c.n_z + 63) / 64, 64, 0, st>>>(fwd, Om, c.dz, c.n_z, dv, dv32);  // FP64: spread over SMs
-    if (out64) launch_profile_t<true, false>(c, dv, nullptr, invZ64, nullptr, out64, st);
-    if (out32) launch_profile_t<false, false>(c, dv32, nullptr, invZ32, nullptr, out32, st);
+    if (out64) {
+        launch_profile_t<true, false>(c, dv, nullptr, invZ64, nullptr, out64, st);
+        launch_missing_t<true, false>(c, fwd, nullptr, Om, dv, nullptr, out64, st);
+    }
+    if (out32) {
+        launch_profile_t<false, false>(c, dv32, nullptr, invZ32, nullptr, out32, st);
+        launch_missing_t<false, false>(c, fwd, nullptr, Om, dv32, nullptr, out32, st);
+    }
 }
 
 void launch_dense_ranges(const DevCatalog &c, cudaStream_t st) {
@@ -339,12 +390,16 @@ void launch_dense_ranges(const DevCatalog &c, cudaStream_t st) {
     k_dense_ranges<false><<<nb, 256, 0, st>>>(c, c.dense_lr32);
 }
 
-void launch_galaxy_dOm(const DevCatalog &c, const double *dv, const double *dvO, const float *dv32,
-                       const float *dvO32, bool f64, void *invZ, void *ZO, void *out, cudaStream_t st) {
-    if (f64)
+void launch_galaxy_dOm(const DevCatalog &c, const double *fwd, const double *fwdO, double Om, const double *dv,
+                       const double *dvO, const float *dv32, const float *dvO32, bool f64, void *invZ, void *ZO,
+                       void *out, cudaStream_t st) {
+    if (f64) {
         launch_profile_t<true, true>(c, dv, dvO, (double *)invZ, (double *)ZO, (double *)out, st);
-    else
+        launch_missing_t<true, true>(c, fwd, fwdO, Om, dv, dvO, (double *)out, st);
+    } else {
         launch_profile_t<false, true>(c, dv32, dvO32, (float *)invZ, (float *)ZO, (float *)out, st);
+        launch_missing_t<false, true>(c, fwd, fwdO, Om, dv32, dvO32, (float *)out, st);
+    }
 }
 
 void launch_profile_sum(const DevCatalog &c, const double *G64, const float *G32, double *outh64,

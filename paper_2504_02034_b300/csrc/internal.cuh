@@ -123,6 +123,12 @@ struct DevCatalog {
     // more than GAL_THREADS galaxies (a block each), the rest a warp each
     int64_t n_ditems64, n_ditems32, n_dheavy64, n_dheavy32;
     int2 *dense_items64, *dense_items32;
+    // incomplete catalog: f_R and, per pixel and grid point, the missing-
+    // galaxy weight (1 - P_compl) pix_area / 4 pi (nullptr when complete)
+    int32_t incomplete;
+    double f_R;
+    double *miss64;
+    float *miss32;
     // galaxies
     double *gz64, *gs64;  // FP64 values
     float *gz32, *gs32;   // F32 storage
@@ -181,8 +187,11 @@ void launch_galaxy_profile(const DevCatalog &c, const double *fwd, double Om, do
                            cudaStream_t st);
 // dG/dOm of the galaxy profile (FP64 from dv, dvO, or FP32 from their FP32
 // copies); invZ, ZO: [n_gal] scratch of the precision's type; out [n_pix x n_z].
-void launch_galaxy_dOm(const DevCatalog &c, const double *dv, const double *dvO, const float *dv32,
-                       const float *dvO32, bool f64, void *invZ, void *ZO, void *out, cudaStream_t st);
+// fwd, fwdO: the D_c table and its Om derivative (the missing-galaxy term of
+// an incomplete catalog needs D_c(z_max) and its derivative).
+void launch_galaxy_dOm(const DevCatalog &c, const double *fwd, const double *fwdO, double Om, const double *dv,
+                       const double *dvO, const float *dv32, const float *dvO32, bool f64, void *invZ, void *ZO,
+                       void *out, cudaStream_t st);
 // Candidate galaxy ranges of the dense pixels (Om-independent), into
 // c.dense_lr64 / c.dense_lr32.
 void launch_dense_ranges(const DevCatalog &c, cudaStream_t st);
@@ -234,6 +243,23 @@ __device__ __forceinline__ double dc_hermite(const double *fwd, double z, double
     double m0 = chim::HT / E_of(z0, Om), m1 = chim::HT / E_of(z1, Om);
     double f2 = f * f, f3 = f2 * f;
     return (2 * f3 - 3 * f2 + 1) * p0 + (f3 - 2 * f2 + f) * m0 + (-2 * f3 + 3 * f2) * p1 +
+           (f3 - f2) * m1;
+}
+
+// Hermite interpolation of dDhat/dOm (node derivatives known in closed form).
+__device__ __forceinline__ double dcO_hermite(const double *fwdO, double z, double Om) {
+    double t = z / chim::HT;
+    int k = (int)floor(t);
+    if (k < 0) k = 0;
+    if (k > chim::NT_FWD - 2) k = chim::NT_FWD - 2;
+    double f = t - k;
+    auto g = [Om](double zz) {
+        double a = 1.0 + zz, E = chimd::E_of(zz, Om);
+        return -0.5 * (a * a * a - 1.0) / (E * E * E);
+    };
+    double m0 = chim::HT * g(k * chim::HT), m1 = chim::HT * g((k + 1) * chim::HT);
+    double f2 = f * f, f3 = f2 * f;
+    return (2 * f3 - 3 * f2 + 1) * fwdO[k] + (f3 - 2 * f2 + f) * m0 + (-2 * f3 + 3 * f2) * fwdO[k + 1] +
            (f3 - f2) * m1;
 }
 

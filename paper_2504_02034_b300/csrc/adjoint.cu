@@ -1173,10 +1173,7 @@ __global__ void k_dv_pair(const double *fwd, const double *fwdO, double Om, doub
                           double *dvO, float *dv32, float *dvO32) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= nz) return;
-    double z = a * dz, ap = 1.0 + z;
-    double D = chimd::dc_hermite(fwd, z, Om), DO = dcO_hermite(fwdO, z, Om), E = chimd::E_of(z, Om);
-    dv[a] = D * D / E;
-    dvO[a] = 2.0 * D * DO / E - D * D * (ap * ap * ap - 1.0) * 0.5 / (E * E * E);
+    chimd::dv_pair(fwd, fwdO, a * dz, Om, dv[a], dvO[a]);
     dv32[a] = (float)dv[a];
     dvO32[a] = (float)dvO[a];
 }
@@ -1268,31 +1265,42 @@ struct AdjLayout {
     }
 };
 
-int fwdO_table(Ctx &ctx, double Om, cudaStream_t st, const double **out) {
-    uint64_t key = bits_of(Om);
-    auto it = ctx.fwdO.find(key);
-    if (it == ctx.fwdO.end()) {
-        FwdEntry e;
-        RC(cache_alloc(ctx, (void **)&e.table, sizeof(double) * NT_FWD, st));
-        if (cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming) != cudaSuccess) {
-            cache_free(ctx, e.table, sizeof(double) * NT_FWD);
-            return cuda_check(cudaGetLastError(), "cudaEventCreate");
-        }
-        launch_fwd_table_dOm(Om, e.table, st);
-        CK(cudaGetLastError());
-        CK(cudaEventRecord(e.ready, st));
-        it = ctx.fwdO.emplace(key, e).first;
-    } else {
-        CK(cudaStreamWaitEvent(st, it->second.ready, 0));
+// A mixed dG/dOm profile allocated but still to be computed (batched).
+struct PendingDprof {
+    double Om;
+    const double *fwd, *fwdO;
+    std::pair<uint64_t, int> key;
+};
+
+// The one-Om dG/dOm kernels into entry e.
+int dprofile_one(Workspace &ws, const AdjLayout &L, const DevCatalog &c, double Om, bool f64, const double *fwd,
+                 const double *fwdO, ProfEntry &e) {
+    double *dv = reinterpret_cast<double *>(ws.gscr + L.o_dv);
+    double *dvO = reinterpret_cast<double *>(ws.gscr + L.o_dvO);
+    double *invZ = reinterpret_cast<double *>(ws.gscr + L.o_invZ);
+    double *ZO = reinterpret_cast<double *>(ws.gscr + L.o_ZO);
+    float *dv32 = reinterpret_cast<float *>(dv + c.n_z), *dvO32 = reinterpret_cast<float *>(dvO + c.n_z);
+    k_dv_pair<<<(c.n_z + 63) / 64, 64, 0, ws.st>>>(fwd, fwdO, Om, c.dz, c.n_z, dv, dvO, dv32, dvO32);
+    launch_galaxy_dOm(c, fwd, fwdO, Om, dv, dvO, dv32, dvO32, f64, invZ, ZO, e.G, ws.st);
+    return CHIMERA_OK;
+}
+
+// Sky sums (single-1D) and the ready event of a computed entry.
+int dprofile_finish(Workspace &ws, const DevCatalog &c, bool f64, ProfEntry &e) {
+    if (e.Gh) {
+        if (f64) k_dprofile_sum<<<c.n_events, 256, 0, ws.st>>>(c, (const double *)e.G, (double *)e.Gh);
+        else k_dprofile_sum32<<<c.n_events, 256, 0, ws.st>>>(c, (const float *)e.G, (float *)e.Gh);
     }
-    *out = it->second.table;
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(e.ready, ws.st));
     return CHIMERA_OK;
 }
 
 // dG/dOm profile for (Om, precision), cached with the forward profiles
-// (FP64 rows for FP64 calls, FP32 rows for mixed ones).
+// (FP64 rows for FP64 calls, FP32 rows for mixed ones).  With `defer`, a new
+// mixed profile is only allocated and queued for flush_dprofiles.
 int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double Om, bool f64, const double *fwd,
-             const double *fwdO, const double **out) {
+             const double *fwdO, const double **out, std::vector<PendingDprof> *defer) {
     const int kind = f64 ? 2 : 3;
     auto key = std::make_pair(bits_of(Om), kind);
     auto it = cat.prof.find(key);
@@ -1313,20 +1321,14 @@ int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double O
             free_prof_entry(ctx, e);
             return cuda_check(cudaGetLastError(), "cudaEventCreate");
         }
-        double *dv = reinterpret_cast<double *>(ws.gscr + L.o_dv);
-        double *dvO = reinterpret_cast<double *>(ws.gscr + L.o_dvO);
-        double *invZ = reinterpret_cast<double *>(ws.gscr + L.o_invZ);
-        double *ZO = reinterpret_cast<double *>(ws.gscr + L.o_ZO);
-        float *dv32 = reinterpret_cast<float *>(dv + c.n_z), *dvO32 = reinterpret_cast<float *>(dvO + c.n_z);
-        k_dv_pair<<<(c.n_z + 63) / 64, 64, 0, ws.st>>>(fwd, fwdO, Om, c.dz, c.n_z, dv, dvO, dv32, dvO32);
-        launch_galaxy_dOm(c, fwd, fwdO, Om, dv, dvO, dv32, dvO32, f64, invZ, ZO, e.G, ws.st);
-        if (hb) {
-            if (f64) k_dprofile_sum<<<c.n_events, 256, 0, ws.st>>>(c, (const double *)e.G, (double *)e.Gh);
-            else k_dprofile_sum32<<<c.n_events, 256, 0, ws.st>>>(c, (const float *)e.G, (float *)e.Gh);
+        if (defer && !f64) {
+            it = cat.prof.emplace(key, e).first;
+            defer->push_back({Om, fwd, fwdO, key});
+        } else {
+            RC(dprofile_one(ws, L, c, Om, f64, fwd, fwdO, e));
+            RC(dprofile_finish(ws, c, f64, e));
+            it = cat.prof.emplace(key, e).first;
         }
-        CK(cudaGetLastError());
-        CK(cudaEventRecord(e.ready, ws.st));
-        it = cat.prof.emplace(key, e).first;
     } else {
         CK(cudaStreamWaitEvent(ws.st, it->second.ready, 0));
     }
@@ -1334,6 +1336,44 @@ int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double O
     // FP32 rows on the mixed path (the pointer table is typed double*)
     *out = reinterpret_cast<const double *>(c.kde_mode == CHIMERA_KDE_SINGLE_1D ? it->second.Gh : it->second.G);
     return CHIMERA_OK;
+}
+
+// Launch the pending mixed dG/dOm profiles, PROF_MB Om values per batched
+// pass (one alone takes the one-Om kernels; both give the same values).
+int flush_dprofiles(Catalog &cat, Workspace &ws, const AdjLayout &L, std::vector<PendingDprof> &pend) {
+    const DevCatalog &c = cat.d;
+    for (size_t b = 0; b < pend.size(); b += PROF_MB) {
+        const int n = (int)std::min<size_t>(PROF_MB, pend.size() - b);
+        if (n == 1) {
+            const PendingDprof &q = pend[b];
+            RC(dprofile_one(ws, L, c, q.Om, false, q.fwd, q.fwdO, cat.prof.at(q.key)));
+        } else {
+            MultiOm m{};
+            m.n = n;
+            for (int j = 0; j < PROF_MB; j++) {
+                const PendingDprof &q = pend[b + (j < n ? j : 0)];
+                m.fwd[j] = q.fwd;
+                m.fwdO[j] = q.fwdO;
+                m.Om[j] = q.Om;
+                m.out[j] = j < n ? (float *)cat.prof.at(q.key).G : nullptr;
+            }
+            launch_galaxy_profile_multi(c, m, true, ws.dvm, ws.invZm, ws.st);
+        }
+        for (int j = 0; j < n; j++) RC(dprofile_finish(ws, c, false, cat.prof.at(pend[b + j].key)));
+    }
+    pend.clear();
+    return CHIMERA_OK;
+}
+
+void drop_dpending(Ctx &ctx, Catalog &cat, Workspace &ws, std::vector<PendingDprof> &pend) {
+    cudaStreamSynchronize(ws.st);  // nothing may still write the entries freed below
+    for (auto &q : pend) {
+        auto it = cat.prof.find(q.key);
+        if (it == cat.prof.end()) continue;
+        free_prof_entry(ctx, it->second);
+        cat.prof.erase(it);
+    }
+    pend.clear();
 }
 
 }  // namespace
@@ -1380,19 +1420,36 @@ int backward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, int precision) {
         reinterpret_cast<const double *const *>(ws.hstage + sizeof(double) * 12 * H + 8 * (size_t)H);
     const double **hO = reinterpret_cast<const double **>(ws.ahstage);
     const double **hP = hO + H;
-    std::map<uint64_t, std::pair<const double *, const double *>> byOm;
+    // distinct Om values: their dD/dOm tables (batched), then their dG/dOm
+    // profiles (new mixed ones batched)
+    std::map<uint64_t, int> slot;
+    std::vector<double> oms;
+    std::vector<const double *> fws;
     for (int h = 0; h < H; h++) {
         const double Om = th[12 * h + 1];
-        const uint64_t key = bits_of(Om);
-        auto it = byOm.find(key);
-        if (it == byOm.end()) {
-            const double *fO = nullptr, *dG = nullptr;
-            RC(fwdO_table(ctx, Om, ws.st, &fO));
-            RC(dprofile(ctx, cat, ws, L, Om, f64, fw[h], fO, &dG));
-            it = byOm.emplace(key, std::make_pair(fO, dG)).first;
+        if (slot.emplace(bits_of(Om), (int)oms.size()).second) {
+            oms.push_back(Om);
+            fws.push_back(fw[h]);
         }
-        hO[h] = it->second.first;
-        hP[h] = it->second.second;
+    }
+    std::vector<const double *> fOs(oms.size()), dGs(oms.size());
+    RC(fwd_tables(ctx, oms.data(), (int)oms.size(), ws.st, fOs.data(), true));
+    std::vector<PendingDprof> pend;
+    for (size_t i = 0; i < oms.size(); i++) {
+        int rc = dprofile(ctx, cat, ws, L, oms[i], f64, fws[i], fOs[i], &dGs[i], &pend);
+        if (rc != CHIMERA_OK) {
+            drop_dpending(ctx, cat, ws, pend);
+            return rc;
+        }
+    }
+    if (int rc = flush_dprofiles(cat, ws, L, pend)) {
+        drop_dpending(ctx, cat, ws, pend);
+        return rc;
+    }
+    for (int h = 0; h < H; h++) {
+        const int i = slot.at(bits_of(th[12 * h + 1]));
+        hO[h] = fOs[i];
+        hP[h] = dGs[i];
     }
     CK(cudaMemcpyAsync(ws.gscr + L.o_ptrs, ws.ahstage, hb, cudaMemcpyHostToDevice, ws.st));
     AdjPtrs q;

@@ -227,6 +227,8 @@ int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat) {
         {(void **)&ws.dv, (sizeof(double) + sizeof(float)) * nz},
         {(void **)&ws.invZ64, sizeof(double) * (size_t)std::max<int64_t>(ng, 1)},
         {(void **)&ws.invZ32, sizeof(float) * (size_t)std::max<int64_t>(ng, 1)},
+        {(void **)&ws.dvm, 2 * sizeof(float) * PROF_MB * ((size_t)nz + 1)},
+        {(void **)&ws.invZm, 2 * sizeof(float) * PROF_MB * (size_t)std::max<int64_t>(ng, 1)},
         {(void **)&ws.grad, sizeof(double) * 12 * (size_t)Hn},
         {(void **)&ws.pairs, sizeof(unsigned long long) * (size_t)Hn},
         {(void **)&ws.dk, sizeof(float) * 2 * (size_t)Hn * NT_FWD},
@@ -270,22 +272,51 @@ uint64_t bits_of(double x) {
     return b;
 }
 
-int fwd_table(Ctx &ctx, double Om, cudaStream_t st, const double **out) {
-    uint64_t key = bits_of(Om);
-    auto it = ctx.fwd.find(key);
-    if (it == ctx.fwd.end()) {
-        FwdEntry e;
-        RC(cache_alloc(ctx, (void **)&e.table, sizeof(double) * NT_FWD, st));
-        CK(cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming));
-        launch_fwd_table(Om, e.table, st);
+// The distance tables (dOm: their Om derivatives) of n distinct Om values:
+// cached ones are waited for, new ones built FWD_MB at a time (one launch
+// pair per batch).
+int fwd_tables(Ctx &ctx, const double *Om, int n, cudaStream_t st, const double **out, bool dOm) {
+    FwdBatch b{};
+    std::vector<FwdEntry *> fresh;
+    auto flush = [&]() -> int {
+        if (b.n == 0) return CHIMERA_OK;
+        launch_fwd_tables(b, dOm, st);
         CK(cudaGetLastError());
-        CK(cudaEventRecord(e.ready, st));
-        it = ctx.fwd.emplace(key, e).first;
-    } else {
-        CK(cudaStreamWaitEvent(st, it->second.ready, 0));
+        for (FwdEntry *e : fresh) CK(cudaEventRecord(e->ready, st));
+        b.n = 0;
+        fresh.clear();
+        return CHIMERA_OK;
+    };
+    for (int i = 0; i < n; i++) {
+        const uint64_t key = bits_of(Om[i]);
+        auto &cache = dOm ? ctx.fwdO : ctx.fwd;
+        auto it = cache.find(key);
+        if (it == cache.end()) {
+            FwdEntry e;
+            int rc = cache_alloc(ctx, (void **)&e.table, sizeof(double) * NT_FWD, st);
+            if (rc == CHIMERA_OK && cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming) != cudaSuccess) {
+                cache_free(ctx, e.table, sizeof(double) * NT_FWD);
+                rc = cuda_check(cudaGetLastError(), "cudaEventCreate");
+            }
+            if (rc != CHIMERA_OK) {
+                flush();  // the entries already made get their tables
+                return rc;
+            }
+            it = cache.emplace(key, e).first;
+            b.Om[b.n] = Om[i];
+            b.out[b.n++] = it->second.table;
+            fresh.push_back(&it->second);
+            if (b.n == FWD_MB) RC(flush());
+        } else {
+            CK(cudaStreamWaitEvent(st, it->second.ready, 0));
+        }
+        out[i] = it->second.table;
     }
-    *out = it->second.table;
-    return CHIMERA_OK;
+    return flush();
+}
+
+int fwd_table(Ctx &ctx, double Om, cudaStream_t st, const double **out) {
+    return fwd_tables(ctx, &Om, 1, st, out, false);
 }
 
 void free_prof_entry(Ctx &ctx, ProfEntry &e) {
@@ -312,12 +343,84 @@ void evict_profiles(Ctx &ctx, Catalog &cat, size_t need) {
     }
 }
 
+// A mixed profile whose entry exists but whose kernels are still to be
+// launched (batched by flush_profiles).
+struct PendingProf {
+    double Om;
+    const double *fwd;
+    std::pair<uint64_t, int> key;
+};
+
+// Launch the pending mixed profiles: PROF_MB Om values per batched pass (one
+// Om alone takes the one-Om kernels; both give the same values).
+static int flush_profiles(Ctx &ctx, Catalog &cat, Workspace &ws, std::vector<PendingProf> &pend) {
+    const DevCatalog &c = cat.d;
+    for (size_t b = 0; b < pend.size(); b += PROF_MB) {
+        const int n = (int)std::min<size_t>(PROF_MB, pend.size() - b);
+        if (n == 1) {
+            ProfEntry &e = cat.prof.at(pend[b].key);
+            launch_galaxy_profile(c, pend[b].fwd, pend[b].Om, ws.dv, ws.invZ64, ws.invZ32, nullptr, (float *)e.G,
+                                  ws.st);
+        } else {
+            MultiOm m{};
+            m.n = n;
+            for (int j = 0; j < PROF_MB; j++) {
+                const PendingProf &q = pend[b + (j < n ? j : 0)];
+                m.fwd[j] = q.fwd;
+                m.fwdO[j] = nullptr;
+                m.Om[j] = q.Om;
+                m.out[j] = j < n ? (float *)cat.prof.at(q.key).G : nullptr;
+            }
+            launch_galaxy_profile_multi(c, m, false, ws.dvm, ws.invZm, ws.st);
+        }
+        for (int j = 0; j < n; j++) {
+            ProfEntry &e = cat.prof.at(pend[b + j].key);
+            if (e.Gh) launch_profile_sum(c, nullptr, (float *)e.G, nullptr, (float *)e.Gh, ws.st);
+            CK(cudaGetLastError());
+            CK(cudaEventRecord(e.ready, ws.st));
+        }
+    }
+    pend.clear();
+    return CHIMERA_OK;
+}
+
+// Drop pending entries (after an error: their kernels never ran).
+static void drop_pending(Ctx &ctx, Catalog &cat, Workspace &ws, std::vector<PendingProf> &pend) {
+    cudaStreamSynchronize(ws.st);  // nothing may still write the entries freed below
+    for (auto &q : pend) {
+        auto it = cat.prof.find(q.key);
+        if (it == cat.prof.end()) continue;
+        free_prof_entry(ctx, it->second);
+        cat.prof.erase(it);
+    }
+    pend.clear();
+}
+
+// The profile of (Om, kind), from the cache or computed; with `defer`, a new
+// mixed profile is only allocated and queued for flush_profiles.
 static int profile(Ctx &ctx, Catalog &cat, Workspace &ws, double Om, int kind, const double *fwd,
-                   const void **out) {
+                   const void **out, std::vector<PendingProf> *defer) {
     auto key = std::make_pair(bits_of(Om), kind);
     auto it = cat.prof.find(key);
     const DevCatalog &c = cat.d;
-    if (it == cat.prof.end()) {
+    if (it == cat.prof.end() && defer && kind == 1) {
+        ProfEntry e;
+        e.bytes = sizeof(float) * (size_t)c.n_pix * c.n_z;
+        const size_t hb = c.kde_mode == CHIMERA_KDE_SINGLE_1D ? sizeof(float) * (size_t)c.n_events * c.n_z : 0;
+        evict_profiles(ctx, cat, e.bytes + hb);
+        RC(cache_alloc(ctx, &e.G, e.bytes, ws.st));
+        if (hb) {
+            int rc = cache_alloc(ctx, &e.Gh, hb, ws.st);
+            if (rc) { cache_free(ctx, e.G, e.bytes); return rc; }
+            e.hbytes = hb;
+        }
+        if (cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming) != cudaSuccess) {
+            free_prof_entry(ctx, e);
+            return cuda_check(cudaGetLastError(), "cudaEventCreate");
+        }
+        it = cat.prof.emplace(key, e).first;
+        defer->push_back({Om, fwd, key});
+    } else if (it == cat.prof.end()) {
         ProfEntry e;
         size_t esz = kind == 0 ? sizeof(double) : sizeof(float);
         e.bytes = esz * (size_t)c.n_pix * c.n_z;
@@ -387,20 +490,33 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
         memcpy(th + 12 * h, ok ? t : kSafeTheta, sizeof(double) * 12);
         st[h] = ok ? 0 : CHIMERA_PT_OUT_OF_SUPPORT;
     }
-    std::map<uint64_t, std::pair<const double *, const void *>> byOm;
+    // distinct Om values in order of first appearance: their distance tables
+    // (batched), then their profiles (new mixed ones batched)
+    std::map<uint64_t, int> slot;
+    std::vector<double> oms;
     for (int h = 0; h < H; h++) {
-        double Om = th[12 * h + 1];
-        uint64_t k = bits_of(Om);
-        auto it = byOm.find(k);
-        if (it == byOm.end()) {
-            const double *f = nullptr;
-            const void *g = nullptr;
-            RC(fwd_table(ctx, Om, ws.st, &f));
-            RC(profile(ctx, cat, ws, Om, kind, f, &g));
-            it = byOm.emplace(k, std::make_pair(f, g)).first;
+        const double Om = th[12 * h + 1];
+        if (slot.emplace(bits_of(Om), (int)oms.size()).second) oms.push_back(Om);
+    }
+    std::vector<const double *> fws(oms.size());
+    std::vector<const void *> prs(oms.size());
+    RC(fwd_tables(ctx, oms.data(), (int)oms.size(), ws.st, fws.data(), false));
+    std::vector<PendingProf> pend;
+    for (size_t i = 0; i < oms.size(); i++) {
+        int rc = profile(ctx, cat, ws, oms[i], kind, fws[i], &prs[i], &pend);
+        if (rc != CHIMERA_OK) {
+            drop_pending(ctx, cat, ws, pend);
+            return rc;
         }
-        fw[h] = it->second.first;
-        pr[h] = it->second.second;
+    }
+    for (int h = 0; h < H; h++) {
+        const int i = slot.at(bits_of(th[12 * h + 1]));
+        fw[h] = fws[i];
+        pr[h] = prs[i];
+    }
+    if (int rc = flush_profiles(ctx, cat, ws, pend)) {
+        drop_pending(ctx, cat, ws, pend);
+        return rc;
     }
     if (ws.trace) CK(cudaEventRecord(ws.tev[1], ws.st));
     CK(cudaMemcpyAsync(ws.param, ws.hstage, ws.param_bytes(H), cudaMemcpyHostToDevice, ws.st));

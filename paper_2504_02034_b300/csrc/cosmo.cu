@@ -36,10 +36,13 @@ __device__ __forceinline__ double fwd_integrand(double z, double Om) {
 }
 
 // One panel [z_k, z_k+1] per thread, 5-point Gauss-Legendre (nodes and
-// weights in closed form); out[k+1] = the block's inclusive prefix.
+// weights in closed form); out[k+1] = the block's inclusive prefix.  The
+// tables of a batch of Om values are built side by side (blockIdx.y).
 template <int KIND>
-__global__ void __launch_bounds__(FWD_THREADS) k_fwd_panels(double Om, double *out) {
+__global__ void __launch_bounds__(FWD_THREADS) k_fwd_panels(FwdBatch b) {
     __shared__ double warp_tot[FWD_THREADS / 32];
+    const double Om = b.Om[blockIdx.y];
+    double *out = b.out[blockIdx.y];
     const int t = threadIdx.x, k = blockIdx.x * FWD_THREADS + t;
     const double x1 = sqrt(5.0 - 2.0 * sqrt(10.0 / 7.0)) / 3.0;
     const double x2 = sqrt(5.0 + 2.0 * sqrt(10.0 / 7.0)) / 3.0;
@@ -69,8 +72,9 @@ __global__ void __launch_bounds__(FWD_THREADS) k_fwd_panels(double Om, double *o
 
 // Adds to every block's entries the totals of the blocks before it (the
 // totals are read in parallel, then added in block order).
-__global__ void __launch_bounds__(1024) k_fwd_offsets(double *out) {
+__global__ void __launch_bounds__(1024) k_fwd_offsets(FwdBatch b) {
     __shared__ double tot[FWD_BLOCKS], off[FWD_BLOCKS];
+    double *out = b.out[blockIdx.x];
     if (threadIdx.x + 1 < FWD_BLOCKS) tot[threadIdx.x] = out[(threadIdx.x + 1) * FWD_THREADS];  // block's total
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -328,14 +332,19 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
 
 }  // namespace
 
-void launch_fwd_table(double Om, double *out, cudaStream_t st) {
-    k_fwd_panels<0><<<FWD_BLOCKS, FWD_THREADS, 0, st>>>(Om, out);
-    k_fwd_offsets<<<1, 1024, 0, st>>>(out);
+void launch_fwd_tables(const FwdBatch &b, bool dOm, cudaStream_t st) {
+    if (b.n <= 0) return;
+    if (dOm) k_fwd_panels<1><<<dim3(FWD_BLOCKS, b.n), FWD_THREADS, 0, st>>>(b);
+    else k_fwd_panels<0><<<dim3(FWD_BLOCKS, b.n), FWD_THREADS, 0, st>>>(b);
+    k_fwd_offsets<<<b.n, 1024, 0, st>>>(b);
 }
 
-void launch_fwd_table_dOm(double Om, double *out, cudaStream_t st) {
-    k_fwd_panels<1><<<FWD_BLOCKS, FWD_THREADS, 0, st>>>(Om, out);
-    k_fwd_offsets<<<1, 1024, 0, st>>>(out);
+void launch_fwd_table(double Om, double *out, cudaStream_t st) {
+    FwdBatch b{};
+    b.n = 1;
+    b.Om[0] = Om;
+    b.out[0] = out;
+    launch_fwd_tables(b, false, st);
 }
 
 void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, double *dk,

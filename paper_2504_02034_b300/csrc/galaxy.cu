@@ -47,9 +47,7 @@ constexpr int GAL_THREADS = 256;
 __global__ void k_dvdz(const double *fwd, double Om, double dz, int nz, double *dv, float *dv32) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a < nz) {
-        double z = a * dz;
-        double D = chimd::dc_hermite(fwd, z, Om);
-        dv[a] = D * D / chimd::E_of(z, Om);
+        dv[a] = chimd::dv_of(fwd, a * dz, Om);
         dv32[a] = (float)dv[a];
     }
 }
@@ -307,6 +305,23 @@ void launch_profile_t(const DevCatalog &c, const typename Gal<F64>::T *dv, const
     }
 }
 
+// f_R G + (m c) dv with every rounding explicit (no contraction), so the
+// one-Om and batched launches agree bit for bit.
+__device__ __forceinline__ float miss_update(float fR, float G, float m, float c, float dv) {
+    return __fadd_rn(__fmul_rn(fR, G), __fmul_rn(__fmul_rn(m, c), dv));
+}
+__device__ __forceinline__ double miss_update(double fR, double G, double m, double c, double dv) {
+    return __dadd_rn(__dmul_rn(fR, G), __dmul_rn(__dmul_rn(m, c), dv));
+}
+// Its Om derivative form: f_R dG + m (c1 dv' + c2 dv).
+__device__ __forceinline__ float miss_update_O(float fR, float G, float m, float c1, float dvO, float c2, float dv) {
+    return __fadd_rn(__fmul_rn(fR, G), __fmul_rn(m, __fadd_rn(__fmul_rn(c1, dvO), __fmul_rn(c2, dv))));
+}
+__device__ __forceinline__ double miss_update_O(double fR, double G, double m, double c1, double dvO, double c2,
+                                                double dv) {
+    return __dadd_rn(__dmul_rn(fR, G), __dmul_rn(m, __dadd_rn(__dmul_rn(c1, dvO), __dmul_rn(c2, dv))));
+}
+
 // The missing-galaxy term of an incomplete catalog, over the whole profile
 // (grid-stride); WITH_O writes its Om derivative, f_R dG + 3 N m (dv' -
 // 3 dv D_max'/D_max) / D_max^3, into the dG/dOm rows.  Thread 0 of each
@@ -319,10 +334,10 @@ __global__ void __launch_bounds__(GAL_THREADS) k_gal_missing(DevCatalog c, const
     using T = typename Gal<F64>::T;
     __shared__ T s_c[2];
     if (threadIdx.x == 0) {
-        const double D = chimd::dc_hermite(fwd, c.z_max, Om), D3 = D * D * D;
-        const double c1 = 3.0 * c.n_gal_total / D3;
+        double c1, c2;
+        chimd::miss_scales(fwd, WITH_O ? fwdO : nullptr, c.z_max, Om, c.n_gal_total, c1, c2);
         s_c[0] = T(c1);
-        s_c[1] = WITH_O ? T(-3.0 * c1 * chimd::dcO_hermite(fwdO, c.z_max, Om) / D) : T(0);
+        s_c[1] = T(c2);
     }
     __syncthreads();
     const T c1 = s_c[0], c2 = s_c[1], fR = T(c.f_R);
@@ -331,8 +346,8 @@ __global__ void __launch_bounds__(GAL_THREADS) k_gal_missing(DevCatalog c, const
     const int64_t n = c.n_pix * nz;
     for (int64_t i = blockIdx.x * (int64_t)GAL_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * GAL_THREADS) {
         const int a = (int)(i % nz);
-        const T add = WITH_O ? m[i] * (c1 * dvO[a] + c2 * dv[a]) : m[i] * c1 * dv[a];
-        out[i] = fR * out[i] + add;
+        if (WITH_O) out[i] = miss_update_O(fR, out[i], m[i], c1, dvO[a], c2, dv[a]);
+        else out[i] = miss_update(fR, out[i], m[i], c1, dv[a]);
     }
 }
 
@@ -344,6 +359,295 @@ void launch_missing_t(const DevCatalog &c, const double *fwd, const double *fwdO
     const int64_t n = c.n_pix * c.n_z;
     const int64_t nb = std::min<int64_t>((n + GAL_THREADS - 1) / GAL_THREADS, 148 * 8);
     k_gal_missing<F64, WITH_O><<<(unsigned)nb, GAL_THREADS, 0, st>>>(c, fwd, fwdO, Om, dv, dvO, out);
+}
+
+// ---- batched profiles of PROF_MB Om values (mixed path).  The same
+// arithmetic as the kernels above, per column j, in the same order, so the
+// results equal the one-Om launches bit for bit; only the Gaussian of each
+// (galaxy, grid point) pair is shared by the columns.  WITH_O: the dG/dOm
+// rows (two sums per column, as in the one-Om WITH_O kernels).
+
+// dV_c/dz of every column, [(n_z + 1) x PROF_MB] (the columns of a grid
+// point side by side, two float4), row n_z the missing-galaxy scale c1;
+// WITH_O also dV_c/dz' into dvOm (row n_z: c2).
+template <bool WITH_O>
+__global__ void k_dvdz_multi(MultiOm m, DevCatalog c, float *dvm, float *dvOm) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, nz = c.n_z;
+    const int64_t o = (int64_t)a * PROF_MB + j;
+    if (a < nz) {
+        if (WITH_O) {
+            double dv, dvO;
+            chimd::dv_pair(m.fwd[j], m.fwdO[j], a * c.dz, m.Om[j], dv, dvO);
+            dvm[o] = (float)dv;
+            dvOm[o] = (float)dvO;
+        } else {
+            dvm[o] = (float)chimd::dv_of(m.fwd[j], a * c.dz, m.Om[j]);
+        }
+    } else if (a == nz) {
+        double c1, c2;
+        chimd::miss_scales(m.fwd[j], WITH_O ? m.fwdO[j] : nullptr, c.z_max, m.Om[j], c.n_gal_total, c1, c2);
+        dvm[o] = (float)c1;
+        if (WITH_O) dvOm[o] = (float)c2;
+    }
+}
+
+__device__ __forceinline__ void load8(const float *src, float *v) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+    for (int q = 0; q < PROF_MB / 4; q++) {
+        const float4 x = s4[q];
+        v[4 * q] = x.x;
+        v[4 * q + 1] = x.y;
+        v[4 * q + 2] = x.z;
+        v[4 * q + 3] = x.w;
+    }
+}
+
+__device__ __forceinline__ void store8(float *dst, const float *v) {
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+    for (int q = 0; q < PROF_MB / 4; q++) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+template <bool WITH_O>
+__global__ void __launch_bounds__(GAL_CHUNK) k_gal_norm_multi(DevCatalog c, const float *dvm, const float *dvOm,
+                                                             float *invZm, float *ZOm) {
+    using G = Gal<false>;
+    const int p = c.gw_pix[blockIdx.x];
+    const int64_t g = c.gw_g0[blockIdx.x] + threadIdx.x;
+    if (g >= c.gal_off[p + 1]) return;
+    const int nz = c.n_z;
+    const float dz = G::step(c), norm = 0.39894228040143267794f;
+    float zg, sg;
+    G::read(c, p, g, zg, sg);
+    int lo, hi;
+    G::win(c, zg, sg, lo, hi);
+    const float isg = 1.f / sg;
+    float Z[PROF_MB], Zp[PROF_MB];
+#pragma unroll
+    for (int j = 0; j < PROF_MB; j++) Z[j] = Zp[j] = 0.f;
+    for (int a = lo; a <= hi; a++) {
+        const float u = (a * dz - zg) * isg;
+        const float Nv = ((a == 0 || a == nz - 1) ? 0.5f * dz : dz) * G::gauss(u);
+        float d[PROF_MB];
+        load8(dvm + (int64_t)a * PROF_MB, d);
+#pragma unroll
+        for (int j = 0; j < PROF_MB; j++) Z[j] += Nv * d[j];
+        if (WITH_O) {
+            load8(dvOm + (int64_t)a * PROF_MB, d);
+#pragma unroll
+            for (int j = 0; j < PROF_MB; j++) Zp[j] += Nv * d[j];
+        }
+    }
+    float v[PROF_MB];
+#pragma unroll
+    for (int j = 0; j < PROF_MB; j++) {
+        const float Zj = Z[j] * (norm * isg);
+        v[j] = Zj > 0.f ? 1.f / Zj : 0.f;
+    }
+    store8(invZm + g * PROF_MB, v);
+    if (WITH_O) {
+#pragma unroll
+        for (int j = 0; j < PROF_MB; j++) v[j] = Zp[j] * norm * isg;
+        store8(ZOm + g * PROF_MB, v);
+    }
+}
+
+// Adds one galaxy's terms to the column sums (skipping columns with 1/Z = 0,
+// as the one-Om kernels skip the galaxy).
+template <bool WITH_O>
+__device__ __forceinline__ void add_multi(float Nv, const float *iz, const float *zo, float *s1, float *s2) {
+#pragma unroll
+    for (int j = 0; j < PROF_MB; j++)
+        if (iz[j] != 0.f) {
+            s1[j] += Nv * iz[j];
+            if (WITH_O) s2[j] += Nv * zo[j] * iz[j] * iz[j];
+        }
+}
+
+template <bool WITH_O>
+__device__ __forceinline__ void store_multi(const MultiOm &m, const float *dvm, const float *dvOm, int64_t p, int nz,
+                                            int a, const float *s1, const float *s2) {
+    const float norm = 0.39894228040143267794f;
+    float d[PROF_MB], dO[PROF_MB];
+    load8(dvm + (int64_t)a * PROF_MB, d);
+    if (WITH_O) load8(dvOm + (int64_t)a * PROF_MB, dO);
+#pragma unroll
+    for (int j = 0; j < PROF_MB; j++)
+        if (m.out[j]) m.out[j][p * nz + a] = WITH_O ? norm * (dO[j] * s1[j] - d[j] * s2[j]) : norm * s1[j] * d[j];
+}
+
+// Pixels of at most GAL_DENSE galaxies: block per pixel, point per thread,
+// galaxies staged in (dynamic) shared memory (dense pixels' rows are zeroed).
+template <bool WITH_O>
+__global__ void __launch_bounds__(GAL_THREADS) k_gal_gather_multi(DevCatalog c, MultiOm m, const float *dvm,
+                                                                 const float *dvOm, const float *invZm,
+                                                                 const float *ZOm) {
+    using G = Gal<false>;
+    extern __shared__ float4 gm_smem[];
+    float4 *siz = gm_smem;                              // [GAL_DENSE x PROF_MB]
+    float4 *szo = siz + GAL_DENSE * PROF_MB / 4;        // WITH_O
+    float *sz = reinterpret_cast<float *>(siz + (WITH_O ? 2 : 1) * GAL_DENSE * PROF_MB / 4);
+    float *ss = sz + GAL_DENSE;
+    const int64_t p = blockIdx.x;
+    const int64_t g0 = c.gal_off[p], g1 = c.gal_off[p + 1];
+    const int ng = (int)(g1 - g0), nz = c.n_z;
+    if (ng > GAL_DENSE) {
+        for (int a = threadIdx.x; a < nz; a += GAL_THREADS)
+#pragma unroll
+            for (int j = 0; j < PROF_MB; j++)
+                if (m.out[j]) m.out[j][p * nz + a] = 0.f;
+        return;
+    }
+    for (int i = threadIdx.x; i < ng; i += GAL_THREADS) G::read(c, p, g0 + i, sz[i], ss[i]);
+    const float4 *src = reinterpret_cast<const float4 *>(invZm + g0 * PROF_MB);
+    for (int i = threadIdx.x; i < ng * (PROF_MB / 4); i += GAL_THREADS) siz[i] = src[i];
+    if (WITH_O) {
+        const float4 *so = reinterpret_cast<const float4 *>(ZOm + g0 * PROF_MB);
+        for (int i = threadIdx.x; i < ng * (PROF_MB / 4); i += GAL_THREADS) szo[i] = so[i];
+    }
+    __syncthreads();
+    const float *sizf = reinterpret_cast<const float *>(siz), *szof = reinterpret_cast<const float *>(szo);
+    const float dz = G::step(c), reach = G::reach(c, p);
+    for (int a = threadIdx.x; a < nz; a += GAL_THREADS) {
+        const float za = a * dz;
+        int l = 0, r = ng;
+        while (l < r) {
+            const int mid = (l + r) >> 1;
+            if (sz[mid] < za - reach) l = mid + 1; else r = mid;
+        }
+        float s1[PROF_MB], s2[PROF_MB];
+#pragma unroll
+        for (int j = 0; j < PROF_MB; j++) s1[j] = s2[j] = 0.f;
+        for (int i = l; i < ng && sz[i] <= za + reach; i++) {
+            int lo, hi;
+            G::win(c, sz[i], ss[i], lo, hi);
+            if (a < lo || a > hi) continue;
+            const float isg = 1.f / ss[i], u = (za - sz[i]) * isg;
+            const float Nv = isg * G::gauss(u);
+            float iz[PROF_MB], zo[PROF_MB];
+            load8(sizf + i * PROF_MB, iz);
+            if (WITH_O) load8(szof + i * PROF_MB, zo);
+            add_multi<WITH_O>(Nv, iz, zo, s1, s2);
+        }
+        store_multi<WITH_O>(m, dvm, dvOm, p, nz, a, s1, s2);
+    }
+}
+
+constexpr size_t gather_multi_smem(bool with_o) {
+    return (with_o ? 2 : 1) * sizeof(float) * GAL_DENSE * PROF_MB + 2 * sizeof(float) * GAL_DENSE;
+}
+
+// Dense pixels over the load-time item lists (HEAVY: block per item).
+template <bool WITH_O, bool HEAVY>
+__global__ void __launch_bounds__(GAL_THREADS) k_gal_gather_dense_multi(DevCatalog c, MultiOm m, const float *dvm,
+                                                                       const float *dvOm, const float *invZm,
+                                                                       const float *ZOm) {
+    using G = Gal<false>;
+    __shared__ float red[2][PROF_MB][GAL_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t idx = HEAVY ? (int64_t)blockIdx.x
+                              : c.n_dheavy32 + (int64_t)blockIdx.x * (GAL_THREADS / 32) + wid;
+    if (!HEAVY && idx >= c.n_ditems32) return;
+    const int2 item = c.dense_items32[idx];
+    const int64_t p = c.dense_pix[item.x];
+    const int a = item.y, nz = c.n_z;
+    const int64_t g0 = c.gal_off[p];
+    const int2 lr = c.dense_lr32[(int64_t)item.x * nz + a];
+    float s1[PROF_MB], s2[PROF_MB];
+#pragma unroll
+    for (int j = 0; j < PROF_MB; j++) s1[j] = s2[j] = 0.f;
+    const float za = a * G::step(c);
+    const int stride = HEAVY ? GAL_THREADS : 32;
+    for (int64_t g = g0 + lr.x + (HEAVY ? threadIdx.x : lane); g < g0 + lr.y; g += stride) {
+        float zg, sg;
+        G::read(c, p, g, zg, sg);
+        int lo, hi;
+        G::win(c, zg, sg, lo, hi);
+        if (a < lo || a > hi) continue;
+        const float isg = 1.f / sg, u = (za - zg) * isg;
+        const float Nv = isg * G::gauss(u);
+        float iz[PROF_MB], zo[PROF_MB];
+        load8(invZm + g * PROF_MB, iz);
+        if (WITH_O) load8(ZOm + g * PROF_MB, zo);
+        add_multi<WITH_O>(Nv, iz, zo, s1, s2);
+    }
+#pragma unroll
+    for (int j = 0; j < PROF_MB; j++)
+        for (int o = 16; o > 0; o >>= 1) {
+            s1[j] += __shfl_xor_sync(0xffffffffu, s1[j], o);
+            if (WITH_O) s2[j] += __shfl_xor_sync(0xffffffffu, s2[j], o);
+        }
+    if (!HEAVY) {
+        if (lane == 0) store_multi<WITH_O>(m, dvm, dvOm, p, nz, a, s1, s2);
+        return;
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < PROF_MB; j++) {
+            red[0][j][wid] = s1[j];
+            red[1][j][wid] = s2[j];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t1[PROF_MB], t2[PROF_MB];
+#pragma unroll
+        for (int j = 0; j < PROF_MB; j++) {
+            t1[j] = t2[j] = 0.f;
+            for (int w = 0; w < GAL_THREADS / 32; w++) {
+                t1[j] += red[0][j][w];
+                t2[j] += red[1][j][w];
+            }
+        }
+        store_multi<WITH_O>(m, dvm, dvOm, p, nz, a, t1, t2);
+    }
+}
+
+// The missing-galaxy term of an incomplete catalog for every column.
+template <bool WITH_O>
+__global__ void __launch_bounds__(GAL_THREADS) k_gal_missing_multi(DevCatalog c, MultiOm m, const float *dvm,
+                                                                  const float *dvOm) {
+    const float fR = (float)c.f_R;
+    const int nz = c.n_z;
+    const int64_t n = c.n_pix * nz;
+    for (int64_t i = blockIdx.x * (int64_t)GAL_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * GAL_THREADS) {
+        const int a = (int)(i % nz);
+        const float mi = c.miss32[i];
+        const int64_t oa = (int64_t)a * PROF_MB, oz = (int64_t)nz * PROF_MB;
+#pragma unroll
+        for (int j = 0; j < PROF_MB; j++) {
+            if (!m.out[j]) continue;
+            m.out[j][i] = WITH_O ? miss_update_O(fR, m.out[j][i], mi, dvm[oz + j], dvOm[oa + j], dvOm[oz + j], dvm[oa + j])
+                                 : miss_update(fR, m.out[j][i], mi, dvm[oz + j], dvm[oa + j]);
+        }
+    }
+}
+
+template <bool WITH_O>
+void launch_multi_t(const DevCatalog &c, const MultiOm &m, float *dvm, float *invZm, cudaStream_t st) {
+    float *dvOm = WITH_O ? dvm + (size_t)(c.n_z + 1) * PROF_MB : nullptr;
+    float *ZOm = WITH_O ? invZm + (size_t)std::max<int64_t>(c.n_gal, 1) * PROF_MB : nullptr;
+    k_dvdz_multi<WITH_O><<<dim3((unsigned)((c.n_z + 1 + 63) / 64), PROF_MB), 64, 0, st>>>(m, c, dvm, dvOm);
+    if (c.n_gw > 0) k_gal_norm_multi<WITH_O><<<(unsigned)c.n_gw, GAL_CHUNK, 0, st>>>(c, dvm, dvOm, invZm, ZOm);
+    constexpr size_t smem = gather_multi_smem(WITH_O);
+    static bool attr = false;  // opt in to more than 48 KB of dynamic shared memory once
+    if (!attr) {
+        cudaFuncSetAttribute(k_gal_gather_multi<WITH_O>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    k_gal_gather_multi<WITH_O><<<(unsigned)c.n_pix, GAL_THREADS, smem, st>>>(c, m, dvm, dvOm, invZm, ZOm);
+    const int64_t nh = c.n_dheavy32, nl = c.n_ditems32 - nh;
+    const int wpb = GAL_THREADS / 32;
+    if (nh > 0)
+        k_gal_gather_dense_multi<WITH_O, true><<<(unsigned)nh, GAL_THREADS, 0, st>>>(c, m, dvm, dvOm, invZm, ZOm);
+    if (nl > 0)
+        k_gal_gather_dense_multi<WITH_O, false>
+            <<<(unsigned)((nl + wpb - 1) / wpb), GAL_THREADS, 0, st>>>(c, m, dvm, dvOm, invZm, ZOm);
+    if (c.incomplete) {
+        const int64_t n = c.n_pix * c.n_z;
+        const int64_t nb = std::min<int64_t>((n + GAL_THREADS - 1) / GAL_THREADS, 148 * 8);
+        k_gal_missing_multi<WITH_O><<<(unsigned)nb, GAL_THREADS, 0, st>>>(c, m, dvm, dvOm);
+    }
 }
 
 // Single-1D: sum_k S_k G_k(z_a) per event.
@@ -380,6 +684,13 @@ void launch_galaxy_profile(const DevCatalog &c, const double *fwd, double Om, do
         launch_profile_t<false, false>(c, dv32, nullptr, invZ32, nullptr, out32, st);
         launch_missing_t<false, false>(c, fwd, nullptr, Om, dv32, nullptr, out32, st);
     }
+}
+
+void launch_galaxy_profile_multi(const DevCatalog &c, const MultiOm &m, bool dOm, float *dvm, float *invZm,
+                                 cudaStream_t st) {
+    if (c.n_pix == 0) return;
+    if (dOm) launch_multi_t<true>(c, m, dvm, invZm, st);
+    else launch_multi_t<false>(c, m, dvm, invZm, st);
 }
 
 void launch_dense_ranges(const DevCatalog &c, cudaStream_t st) {

@@ -27,6 +27,7 @@ constexpr float KWG32 = 6.0f;
 constexpr int GAL_CHUNK = 256;   // galaxies per normalisation block
 constexpr int GAL_DENSE = 1024;  // pixels above this gather per grid point by blocks
 constexpr int GAL_HEAVY = 256;   // dense-pixel points with more candidates: a block each
+constexpr int PROF_MB = 8;       // Om values per batched (mixed) profile pass
 // Each KDE is zero outside the grid segment holding its samples, widened by
 // KDE_MARGIN bandwidths (Sec. 2.3: evaluated only where the samples are).
 constexpr double KDE_MARGIN = 6.0;
@@ -171,8 +172,16 @@ struct CallPtrs {
 // ---- launch wrappers (host) ----
 // K1a: forward table D_c(z_k) / (c/H0) for one Om into `out` [NT_FWD].
 void launch_fwd_table(double Om, double *out, cudaStream_t st);
-// Its Om derivative, d/dOm of D_c(z_k)/(c/H0), into `out` [NT_FWD] (adjoint).
-void launch_fwd_table_dOm(double Om, double *out, cudaStream_t st);
+// The tables (or, dOm, their Om derivatives d/dOm of D_c(z_k)/(c/H0), for
+// the adjoint) of up to FWD_MB Om values in one launch pair; each equals the
+// one-Om launch's.
+constexpr int FWD_MB = 32;
+struct FwdBatch {
+    int n;
+    double Om[FWD_MB];
+    double *out[FWD_MB];
+};
+void launch_fwd_tables(const FwdBatch &b, bool dOm, cudaStream_t st);
 // K1b: per-hyperpoint parameters, inverse tables, grid factors (F64 for
 // fp64, normalised F32 otherwise), status.  dk: scratch of at least
 // H x NT_FWD x 8 bytes (FP32 d_L^gw and J at the forward nodes),
@@ -185,6 +194,23 @@ void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp6
 void launch_galaxy_profile(const DevCatalog &c, const double *fwd, double Om, double *dv,
                            double *invZ64, float *invZ32, double *out64, float *out32,
                            cudaStream_t st);
+// The mixed-path profiles of up to PROF_MB Om values in one pass: the
+// galaxies' Gaussians (Om-independent) are evaluated once and contracted with
+// the PROF_MB columns of dV_c/dz and 1/Z_g.  Unused slots repeat slot 0 and
+// have out = nullptr.  dvm: [(n_z + 1) x PROF_MB] floats scratch, invZm:
+// [n_gal x PROF_MB] floats scratch; each out[j] [n_pix x n_z].  Every value
+// equals the one-Om launch's bit for bit (same operations in the same order).
+// With fwdO set (dOm), the dG/dOm rows instead (invZm then [2 x n_gal x
+// PROF_MB], dvm [2 x (n_z + 1) x PROF_MB]).
+struct MultiOm {
+    int n;
+    const double *fwd[PROF_MB];
+    const double *fwdO[PROF_MB];
+    double Om[PROF_MB];
+    float *out[PROF_MB];
+};
+void launch_galaxy_profile_multi(const DevCatalog &c, const MultiOm &m, bool dOm, float *dvm, float *invZm,
+                                 cudaStream_t st);
 // dG/dOm of the galaxy profile (FP64 from dv, dvO, or FP32 from their FP32
 // copies); invZ, ZO: [n_gal] scratch of the precision's type; out [n_pix x n_z].
 // fwd, fwdO: the D_c table and its Om derivative (the missing-galaxy term of
@@ -261,6 +287,30 @@ __device__ __forceinline__ double dcO_hermite(const double *fwdO, double z, doub
     double f2 = f * f, f3 = f2 * f;
     return (2 * f3 - 3 * f2 + 1) * fwdO[k] + (f3 - 2 * f2 + f) * m0 + (-2 * f3 + 3 * f2) * fwdO[k + 1] +
            (f3 - f2) * m1;
+}
+
+// dV_c/dz up to constants, D^2/E (D = D_c/(c/H0)), and with fwdO its Om
+// derivative.  Shared by every kernel that builds a galaxy profile so that
+// they agree bit for bit.
+__device__ __forceinline__ double dv_of(const double *fwd, double z, double Om) {
+    const double D = dc_hermite(fwd, z, Om);
+    return D * D / E_of(z, Om);
+}
+__device__ __forceinline__ void dv_pair(const double *fwd, const double *fwdO, double z, double Om, double &dv,
+                                        double &dvO) {
+    const double ap = 1.0 + z;
+    const double D = dc_hermite(fwd, z, Om), DO = dcO_hermite(fwdO, z, Om), E = E_of(z, Om);
+    dv = D * D / E;
+    dvO = 2.0 * D * DO / E - D * D * (ap * ap * ap - 1.0) * 0.5 / (E * E * E);
+}
+// Scales of the missing-galaxy term of an incomplete catalog:
+// c1 = 3 N_gal,tot / D_max^3 (so that c1 dv = N_gal,tot dV_c/dz / V_c(z_max))
+// and, with fwdO, c2 = -3 c1 D_max'/D_max (d/dOm of c1 dv = c1 dv' + c2 dv).
+__device__ __forceinline__ void miss_scales(const double *fwd, const double *fwdO, double zmax, double Om, double N,
+                                            double &c1, double &c2) {
+    const double D = dc_hermite(fwd, zmax, Om), D3 = D * D * D;
+    c1 = 3.0 * N / D3;
+    c2 = fwdO ? -3.0 * c1 * dcO_hermite(fwdO, zmax, Om) / D : 0.0;
 }
 
 __device__ __forceinline__ double xi_of(double z, double xi0, double n) {

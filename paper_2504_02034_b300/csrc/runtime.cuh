@@ -74,6 +74,9 @@ struct Workspace {
     int64_t zpad_cap = 0;
     unsigned long long *fmax_bits = nullptr;  // [H]
     float *invZ32 = nullptr;
+    // batched mixed profiles (and their Om derivatives):
+    // [2 x (n_z+1) x PROF_MB], [2 x n_gal x PROF_MB]
+    float *dvm = nullptr, *invZm = nullptr;
     // adjoint buffers
     double *grad = nullptr;       // [H x 12]
     char *gscr = nullptr;         // adjoint scratch (allocated on the first gradient call)
@@ -154,6 +157,7 @@ void adjoint_release(Ctx &ctx, Workspace &ws);
 // Cache helpers shared by the forward and adjoint orchestration.
 uint64_t bits_of(double x);
 int fwd_table(Ctx &ctx, double Om, cudaStream_t st, const double **out);
+int fwd_tables(Ctx &ctx, const double *Om, int n, cudaStream_t st, const double **out, bool dOm);
 void evict_profiles(Ctx &ctx, Catalog &cat, size_t need);
 void free_prof_entry(Ctx &ctx, ProfEntry &e);
 

@@ -467,6 +467,9 @@ def main():
                     help="run W warm-up launches and one more launch of the timed step, then exit (for ncu)")
     ap.add_argument("--profile-grad", action="store_true",
                     help="run W warm-up gradient calls (mixed, the benchmark batch) and one more, then exit (for ncu)")
+    ap.add_argument("--profile-om", action="store_true",
+                    help="run W warm-up ln L calls and one more, each bringing 16 new Om values "
+                         "(mixed, the benchmark batch; two batched profile passes per call), then exit (for ncu)")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -487,7 +490,7 @@ def main():
     H, NE = theta.shape[0], cat["n_events"]
     ctx = pkg.Context(local)
     cid = ctx.load(cat)
-    peaks = None if (args.profile or args.profile_grad) else pkg.chimera_peaks(ctx.h)
+    peaks = None if (args.profile or args.profile_grad or args.profile_om) else pkg.chimera_peaks(ctx.h)
 
     th_dev = torch.tensor(theta, device=dev, dtype=torch.float64)
     out = torch.empty(H, device=dev, dtype=torch.float64)
@@ -508,6 +511,13 @@ def main():
     if args.profile_grad:
         for _ in range(args.warmup + 1):
             pkg.chimera_grad(ctx.h, cid, theta, pkg.MIXED)
+        ctx.close()
+        return
+    if args.profile_om:
+        for k in range(args.warmup + 1):
+            t = theta.copy()
+            t[:, 1] = 0.28 + 0.04 * np.random.default_rng(500 + k).random(H)
+            pkg.chimera_loglike(ctx.h, cid, t, pkg.MIXED)
         ctx.close()
         return
     pkg.chimera_set_trace(ctx.h, True)

@@ -16,6 +16,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 
 OK, OUT_OF_SUPPORT, NONMONOTONE, NEFF_LOW = 0, 1, 2, 4
 GAUSSIAN, EPANECHNIKOV = 0, 1  # KDE kernel shapes
+JACOBIAN_GRID, JACOBIAN_PER_SAMPLE = 0, 1  # placement of the Jacobian of Eq. jacobian
 
 
 def build(force=False):
@@ -54,6 +55,7 @@ class _Cat(C.Structure):
         ("f_R", C.c_double),
         ("pix_area", C.POINTER(C.c_double)),
         ("completeness", C.POINTER(C.c_double)),
+        ("jacobian", C.c_int32),
     ]
 
 
@@ -117,7 +119,7 @@ def hooks(psi_scale=1.0, mass_scale=1.0, flags=0):
 class Catalog:
     """Oracle view of a catalog dict (see synth.catalog.make_catalog)."""
 
-    def __init__(self, cat, kde_mode=None, kernel=0):
+    def __init__(self, cat, kde_mode=None, kernel=0, jacobian=0):
         self.keep = {}
 
         def arr(key, dt):
@@ -148,6 +150,7 @@ class Catalog:
             float(cat.get("f_R", 1.0)),
             _p(arr("pix_area", np.float64)) if cat.get("completeness") is not None else None,
             _p(arr("completeness", np.float64)) if cat.get("completeness") is not None else None,
+            int(jacobian),
         )
 
     @property

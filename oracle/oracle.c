@@ -20,6 +20,9 @@
  *    to the analysis; f_R is a full-sky integral); the pixel's galaxy mass is
  *    f_R G_cat + (dOmega/4 pi)(1 - P_compl) dV_c/dz / V_c(z_max)
  *  - sky factor S_ik is an input density per steradian  (Eq. gw-kernel-many1d)
+ *  - the Jacobian (1+z)^3 |J| on the grid (Eq. like-integrals), or, as a
+ *    variant, on each sample's KDE weight w_j / [(1+z_j)^3 |J(z_j)|] with the
+ *    bandwidth of the weights w_j and psi alone on the grid      (Eq. jacobian)
  *  - PE priors uniform: pi_PE = 1                                (Sec. 3.2)
  *  - mass model without low-edge smoothing; lambda_g, beta fixed (Sec. 3.1)
  *  - selection: s_j carries the injection draw density and the homogeneous
@@ -287,6 +290,18 @@ static double bandwidth_of(int64_t n, const double *z, const double *w,
     return fallback;
 }
 
+/* The per-sample Jacobian variant: after the bandwidth, each valid sample's
+ * KDE weight is divided by (1+z_j)^3 |J(z_j)|                 (Eq. jacobian) */
+static void jacobian_per_sample(const orc_catalog *c, const double *th, int64_t n, const double *z,
+                                double *w, const int32_t *valid) {
+    if (c->jacobian != ORC_JACOBIAN_PER_SAMPLE) return;
+    for (int64_t j = 0; j < n; j++) {
+        if (!valid[j] || w[j] == 0.0) continue;
+        double ap = 1.0 + z[j];
+        w[j] /= ap * ap * ap * fabs(orc_J(z[j], th));
+    }
+}
+
 int orc_event_bandwidth(const orc_catalog *c, const double *th, int64_t ev, double *b) {
     int64_t n = c->sample_off[ev + 1] - c->sample_off[ev];
     double *z = malloc(sizeof(double) * (n + 1)), *w = malloc(sizeof(double) * (n + 1));
@@ -412,6 +427,7 @@ static int event_kde_impl(const orc_catalog *c, const double *th, int64_t ev,
     int32_t *v = malloc(sizeof(int32_t) * (n + 1));
     samples_h(c, th, ev, &default_hooks, z, w, v);
     double b = bandwidth_of(n, z, w, v, grid_dz(c));
+    jacobian_per_sample(c, th, n, z, w, v);
     kde_grid(c, ev, pixel, z, w, v, b, binned, K);
     free(z); free(w); free(v);
     return 0;
@@ -483,14 +499,16 @@ int orc_galaxy_profile(const orc_catalog *c, const double *th, int64_t ev,
 }
 
 /* Redshift part of the integrand of Eq. like-integrals:
- * F(z) = psi(z) / [(1+z)^3 |d d_L^gw / dz|]                  (Eq. jacobian) */
+ * F(z) = psi(z) / [(1+z)^3 |d d_L^gw / dz|]                  (Eq. jacobian),
+ * or psi(z) alone when the Jacobian sits on the samples.                  */
 int orc_grid_factor(const orc_catalog *c, const double *th,
                     const orc_hooks *hk, double *F) {
     if (!hk) hk = &default_hooks;
     for (int64_t a = 0; a < c->n_z; a++) {
         if (hk->flags & 1) { F[a] = 1.0; continue; }
         double z = grid_z(c, a), ap = 1.0 + z;
-        F[a] = hk->psi_scale * orc_psi(z, th) / (ap * ap * ap * fabs(orc_J(z, th)));
+        F[a] = hk->psi_scale * orc_psi(z, th);
+        if (c->jacobian != ORC_JACOBIAN_PER_SAMPLE) F[a] /= ap * ap * ap * fabs(orc_J(z, th));
     }
     return 0;
 }
@@ -510,6 +528,7 @@ static double event_lnI_impl(const orc_catalog *c, const double *th, int64_t ev,
     double *Gs = calloc((size_t)nz, sizeof(double));
     samples_h(c, th, ev, hk, z, w, v);
     double b = bandwidth_of(n, z, w, v, grid_dz(c));
+    jacobian_per_sample(c, th, n, z, w, v);
     double I = 0.0;
     if (c->kde_mode == ORC_KDE_MANY_1D) {
         for (int32_t k = 0; k < npix; k++) {

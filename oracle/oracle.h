@@ -36,6 +36,11 @@ enum { ORC_KDE_SINGLE_1D = 0, ORC_KDE_MANY_1D = 1 };
  * the Epanechnikov kernel (3/4)(1 - u^2) on |u| <= 1, u = (z - z_j)/h, with
  * h = sqrt(5) b, the width whose variance equals the Gaussian's b^2. */
 enum { ORC_KERNEL_GAUSSIAN = 0, ORC_KERNEL_EPANECHNIKOV = 1 };
+/* Jacobian placement variant.  Reading: per sample, the KDE weight of
+ * sample j becomes w_j / [(1+z_j)^3 |J(z_j)|] while the bandwidth keeps
+ * Scott's rule of the weights w_j of Eq. gw-kernel, and the grid factor
+ * keeps psi(z) alone; the two placements differ to first order in b. */
+enum { ORC_JACOBIAN_GRID = 0, ORC_JACOBIAN_PER_SAMPLE = 1 };
 
 /* Test hooks.  Defaults (psi_scale = mass_scale = 1, flags = 0) give the
  * paper's likelihood; the others exist so that tests can check invariants and
@@ -71,6 +76,10 @@ typedef struct {
     double f_R;
     const double *pix_area;
     const double *completeness;
+    /* placement of the Jacobian (1+z)^3 |d d_L^gw/dz| of Eq. jacobian in
+     * Eq. like-integrals: ORC_JACOBIAN_GRID (on the grid, the paper's form)
+     * or ORC_JACOBIAN_PER_SAMPLE (on each PE sample's KDE weight) */
+    int32_t jacobian;
 } orc_catalog;
 
 /* ---- cosmology (Eqs. dL-em, dL-mg, jacobian) ---- */

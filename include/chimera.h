@@ -77,6 +77,17 @@ extern "C" {
  * CHIMERA_MIXED (one evaluation per sample and grid point in FP32) and
  * CHIMERA_MIXED_BINNED; chimera_grad and serving reject it (INVALID_ARG). */
 #define CHIMERA_KERNEL_EPANECHNIKOV 0x10
+/* Jacobian-placement flag, OR'ed into the precision of chimera_loglike,
+ * chimera_loglike_device and chimera_terms (Eq. jacobian inside Eq.
+ * like-integrals).  Without it the Jacobian (1+z)^3 |d d_L^gw/dz| divides
+ * the integrand on the redshift grid (the paper's form); with it, it divides
+ * each PE sample's KDE weight at the sample's own redshift,
+ * w_j / [(1+z_j)^3 |d d_L^gw/dz (z_j)|], the bandwidth keeping Scott's rule
+ * of the weights w_j and the grid factor keeping psi(z) alone.  The two
+ * placements differ to first order in the bandwidth.  Works with every
+ * precision and with CHIMERA_KERNEL_EPANECHNIKOV; chimera_grad and serving
+ * reject it (INVALID_ARG). */
+#define CHIMERA_JACOBIAN_PER_SAMPLE 0x20
 
 /* ---- KDE variant, fixed per catalog (Sec. 2.3) ---- */
 #define CHIMERA_KDE_SINGLE_1D 0 /* one redshift KDE per event, Eq. gw-kernel-single1d */

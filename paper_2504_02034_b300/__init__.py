@@ -30,6 +30,7 @@ CHIMERA_ERR_UNSUPPORTED = -7
 PT_OK, PT_OUT_OF_SUPPORT, PT_NONMONOTONE, PT_NEFF_LOW = 0, 1, 2, 4
 FP64, MIXED, MIXED_BINNED = 0, 1, 2
 KERNEL_EPANECHNIKOV = 0x10  # OR'ed into the precision: Epanechnikov KDE kernel
+JACOBIAN_PER_SAMPLE = 0x20  # OR'ed into the precision: the Jacobian of Eq. jacobian on each sample
 KDE_SINGLE_1D, KDE_MANY_1D = 0, 1
 GAL_F32, GAL_F16, GAL_BF16 = 0, 1, 2
 SERVE_GRAD, SERVE_MIXED = 1, 2

@@ -465,7 +465,8 @@ static bool admissible(const double *t) {
 int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, int precision,
             double *out_lnL, double *out_neff, int32_t *out_status) {
     const bool epan = (precision & CHIMERA_KERNEL_EPANECHNIKOV) != 0;
-    precision &= ~CHIMERA_KERNEL_EPANECHNIKOV;  // the base precision below
+    const bool jac_ps = (precision & CHIMERA_JACOBIAN_PER_SAMPLE) != 0;
+    precision &= ~(CHIMERA_KERNEL_EPANECHNIKOV | CHIMERA_JACOBIAN_PER_SAMPLE);  // the base precision below
     RC(ws_ensure(ctx, ws, H, cat));
     ctx.tick++;
     const DevCatalog &c = cat.d;
@@ -522,6 +523,7 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
     CK(cudaMemcpyAsync(ws.param, ws.hstage, ws.param_bytes(H), cudaMemcpyHostToDevice, ws.st));
     CallPtrs p = ws.ptrs(H, c);
     p.kshape = epan ? 1 : 0;
+    p.jac_ps = jac_ps ? 1 : 0;
     if (p.pairs) CK(cudaMemsetAsync(p.pairs, 0, sizeof(unsigned long long) * H, ws.st));
     launch_hyper_tables(c, p, H, precision == CHIMERA_FP64, ws.dk, ws.fmax_bits, ws.st);
     if (ws.trace) CK(cudaEventRecord(ws.tev[2], ws.st));
@@ -1204,7 +1206,7 @@ int chimera_catalog_info(chimera_ctx *h, int32_t id, chimera_catalog_info_t *inf
 static int check_call(chimera_ctx *h, int32_t n, const void *theta, int32_t prec, const void *out) {
     if (!h || !theta || !out) { set_error("null argument"); return CHIMERA_ERR_INVALID_ARG; }
     if (n <= 0) { set_error("n_points must be positive"); return CHIMERA_ERR_INVALID_ARG; }
-    const int base = prec & ~CHIMERA_KERNEL_EPANECHNIKOV;
+    const int base = prec & ~(CHIMERA_KERNEL_EPANECHNIKOV | CHIMERA_JACOBIAN_PER_SAMPLE);
     if (base != CHIMERA_FP64 && base != CHIMERA_MIXED && base != CHIMERA_MIXED_BINNED) {
         set_error("bad precision");
         return CHIMERA_ERR_INVALID_ARG;

@@ -108,7 +108,8 @@ __device__ __forceinline__ void dgw_J32(float z, float D, float cH, float om, fl
 //  * blocks x < nbn: d_L^gw and J at the forward nodes, in FP32 (they seed
 //    the FP64 inversion and carry the monotonicity check: J <= 0 on z <= 10
 //    sets the NONMONOTONE bit);
-//  * blocks x >= nbn: the grid factor F(z_a) = psi / ((1+z)^3 |J|) and its
+//  * blocks x >= nbn: the grid factor F(z_a) = psi / ((1+z)^3 |J|) (psi alone
+//    when the Jacobian sits on the samples, p.jac_ps) and its
 //    maximum, in FP64 for FP64 calls (F64), in FP32 for mixed ones (F32, not
 //    yet normalised).
 __global__ void __launch_bounds__(HYP_THREADS) k_nodes_grid(DevCatalog c, CallPtrs p, float2 *djall,
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(HYP_THREADS) k_nodes_grid(DevCatalog c, CallPt
             double z = a * c.dz, d, J;
             chimd::dgw_J(z, cH * chimd::dc_hermite(fwd, z, th[1]), th, cH, &d, &J);
             const double ap = 1.0 + z;
-            double F = chimd::psi_of(z, th) / (ap * ap * ap * fabs(J));
+            double F = p.jac_ps ? chimd::psi_of(z, th) : chimd::psi_of(z, th) / (ap * ap * ap * fabs(J));
             if (!isfinite(F)) F = 0.0;
             p.F64[(size_t)h * c.n_z + a] = F;
             bits = (unsigned long long)__double_as_longlong(F);
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(HYP_THREADS) k_nodes_grid(DevCatalog c, CallPt
             const float ap = 1.f + z, l2a = log2f(ap);
             const float gam = (float)th[9], gk = (float)(th[9] + th[10]);
             const float psi = exp2f(gam * l2a) / (1.f + exp2f(gk * (l2a - (float)log2(1.0 + th[11]))));
-            float F = psi / (ap * ap * ap * fabsf(J));
+            float F = p.jac_ps ? psi : psi / (ap * ap * ap * fabsf(J));
             if (!isfinite(F)) F = 0.f;
             p.F32[(size_t)h * c.n_z + a] = F;
             bits = (unsigned long long)__float_as_uint(F);

@@ -314,6 +314,19 @@ __device__ __forceinline__ float lane_chain(const float *Hc, const float *CT, in
 // the event's median d_L give the FP32 Scott bandwidth.  Many small blocks
 // keep the SMs full while the loads of the inverse-table nodes are in flight.
 constexpr int RW_THREADS = 256;
+// 1 / [(1+z)^3 |d d_L^gw/dz|] at a sample (Eq. jacobian), FP32, from its
+// d_L (D_c = d_L / ((1+z) Xi)) and lz = log2(1+z).
+__device__ __forceinline__ float jac_inv32(const HP &hp, float z, float lz, float d) {
+    const float ap = 1.f + z, rap = __fdividef(1.f, ap);
+    const float pw = ex2(-hp.n32 * lz);  // (1+z)^-n
+    const float xi = hp.xi0_32 + (1.f - hp.xi0_32) * pw;
+    const float dxi = -hp.n32 * (1.f - hp.xi0_32) * pw * rap;
+    const float Dc = __fdividef(d * rap, xi);
+    const float rE = rsqrtf(hp.om32 * ap * ap * ap + 1.f - hp.om32);
+    const float J = (Dc + ap * hp.cH32 * rE) * xi + ap * Dc * dxi;
+    return __fdividef(rap * rap * rap, fabsf(J));
+}
+
 __global__ void __launch_bounds__(RW_THREADS) k_reweight(DevCatalog c, CallPtrs p, int h0, int nh) {
     __shared__ double red[8 + (RW_THREADS / 32) * 8];
     const int hl = blockIdx.x % nh, h = h0 + hl;
@@ -337,6 +350,8 @@ __global__ void __launch_bounds__(RW_THREADS) k_reweight(DevCatalog c, CallPtrs 
         if (!isfinite(zref)) zref = 0.f;
     }
     float m[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // W1, Wd, Wd2, W2, n, Sd, Sd2
+    const bool jac_ps = p.jac_ps != 0;
+    const float dtop = (float)c.d_top;
     // one sample: table coordinate -> z (Hermite on the node pair), log2
     // source masses, weight, moments; invalid samples (beyond d_L^gw(10))
     // get z = inf and w = 0 and stay out of the moments
@@ -351,6 +366,10 @@ __global__ void __launch_bounds__(RW_THREADS) k_reweight(DevCatalog c, CallPtrs 
         m[0] += w; m[1] += wd_; m[2] = fmaf(wd_, d, m[2]); m[3] = fmaf(w, w, m[3]);
         m[4] += ok ? 1.f : 0.f; m[5] += d; m[6] = fmaf(d, d, m[6]);
         zd[j] = ok ? z : CUDART_INF_F;
+        if (jac_ps && ok) {  // the Jacobian on the sample (the moments above keep w)
+            const float t = (float)__float_as_int(sv.x) + sv.y, u = t * (1.f / NU);
+            w *= jac_inv32(hp, z, lz, dtop * u * u);
+        }
         wd[j] = w;
     };
     auto node = [&](const float4 &sv) {
@@ -871,6 +890,12 @@ __global__ void __launch_bounds__(EV64_THREADS) k_event_fp64(DevCatalog c, CallP
         if (j - lo >= segv[l]) continue;  // beyond d_L^gw(10)
         double z = zs[j], w = ws[j];
         if (w == 0.0) continue;
+        if (p.jac_ps) {  // the Jacobian on the sample, after the bandwidth (Eq. jacobian)
+            double dd, J;
+            chimd::dgw_J(z, hp.cH * chimd::dc_hermite(p.fwd[h], z, hp.th[1]), hp.th, hp.cH, &dd, &J);
+            const double ap = 1.0 + z;
+            w /= ap * ap * ap * fabs(J);
+        }
         const int64_t row = c.kde_mode == CHIMERA_KDE_MANY_1D ? (int64_t)(sg0 + l) : (int64_t)ev;
         const double *G = prof + row * nz;
         // window +-KW64 b (Gaussian) or +-h = sqrt(5) b (Epanechnikov),

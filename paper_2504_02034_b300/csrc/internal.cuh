@@ -160,6 +160,7 @@ struct CallPtrs {
                               // tile of hyperpoints (mixed path)
     int32_t n_chunk;
     int32_t kshape;           // KDE kernel: 0 Gaussian, 1 Epanechnikov
+    int32_t jac_ps;           // 1: the Jacobian of Eq. jacobian on each sample's weight, not on the grid
     double *lnL, *neff, *xi;  // [H]
     int32_t *status;          // [H]
     unsigned long long *pairs;  // [H] windowed-pair counter, or nullptr

@@ -71,6 +71,6 @@ def test_epanechnikov_differs_from_gaussian_and_rules(chim, ctx, orc):
                 ctx.grad(cid, th[:1], prec)
             assert e.value.code == chim.CHIMERA_ERR_INVALID_ARG
         with pytest.raises(chim.ChimeraError):
-            ctx.loglike(cid, th[:1], chim.MIXED | 0x20)  # unknown flag
+            ctx.loglike(cid, th[:1], chim.MIXED | 0x40)  # unknown flag
     finally:
         ctx.unload(cid)

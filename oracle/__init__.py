@@ -17,6 +17,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 OK, OUT_OF_SUPPORT, NONMONOTONE, NEFF_LOW = 0, 1, 2, 4
 GAUSSIAN, EPANECHNIKOV = 0, 1  # KDE kernel shapes
 JACOBIAN_GRID, JACOBIAN_PER_SAMPLE = 0, 1  # placement of the Jacobian of Eq. jacobian
+KDE_SINGLE_1D, KDE_MANY_1D, KDE_3D = 0, 1, 2  # KDE variants (Sec. 2.3)
 
 
 def build(force=False):
@@ -56,6 +57,8 @@ class _Cat(C.Structure):
         ("pix_area", C.POINTER(C.c_double)),
         ("completeness", C.POINTER(C.c_double)),
         ("jacobian", C.c_int32),
+        ("sky_xy", C.POINTER(C.c_double)),
+        ("pix_xy", C.POINTER(C.c_double)),
     ]
 
 
@@ -98,6 +101,8 @@ def lib():
         L.orc_linear_bins.argtypes = [C.c_int64, pd, pd, d, C.c_int64, C.c_int64, pd]
         L.orc_linear_bins.restype = C.c_int64
         L.orc_kde_arrays.argtypes = [C.c_int64, pd, pd, d, C.c_int64, d, C.c_int32, C.c_int32, pd]
+        L.orc_event_kde3_bandwidth.argtypes = [pc, pd, C.c_int64, pd]
+        L.orc_event_kde3.argtypes = [pc, pd, C.c_int64, C.c_int32, pd]
         _lib = L
     return _lib
 
@@ -151,6 +156,8 @@ class Catalog:
             _p(arr("pix_area", np.float64)) if cat.get("completeness") is not None else None,
             _p(arr("completeness", np.float64)) if cat.get("completeness") is not None else None,
             int(jacobian),
+            _p(arr("sky_xy", np.float64)) if cat.get("sky_xy") is not None else None,
+            _p(arr("pix_xy", np.float64)) if cat.get("pix_xy") is not None else None,
         )
 
     @property
@@ -178,6 +185,18 @@ class Catalog:
         K = np.zeros(self.n_z)
         f = lib().orc_event_kde_binned if binned else lib().orc_event_kde
         f(self.ref, _p(_th(theta)), ev, pixel, _p(K))
+        return K
+
+    def kde3_bandwidth(self, theta, ev):
+        """Bandwidth matrix of the "3D" kernel over (z, x, y) (None if degenerate)."""
+        H = np.zeros(9)
+        rc = lib().orc_event_kde3_bandwidth(self.ref, _p(_th(theta)), ev, _p(H))
+        return None if rc else H.reshape(3, 3)
+
+    def kde3(self, theta, ev, pixel):
+        """The "3D" KDE at the grid points of one pixel's centre."""
+        K = np.zeros(self.n_z)
+        lib().orc_event_kde3(self.ref, _p(_th(theta)), ev, pixel, _p(K))
         return K
 
     def galaxy_profile(self, theta, ev, pixel, hk=None):

@@ -20,6 +20,13 @@
  *    to the analysis; f_R is a full-sky integral); the pixel's galaxy mass is
  *    f_R G_cat + (dOmega/4 pi)(1 - P_compl) dV_c/dz / V_c(z_max)
  *  - sky factor S_ik is an input density per steradian  (Eq. gw-kernel-many1d)
+ *  - the "3D" kernel (Sec. 2.3) as a cross-check variant: a weighted Gaussian
+ *    KDE over (z, x, y), (x, y) a flat local sky chart of the event, with the
+ *    bandwidth matrix of Scott's rule in three dimensions, n_eff^(-2/7) times
+ *    the weighted sample covariance (unbiased weighting, as in the usual
+ *    weighted gaussian_kde), evaluated at (z_a, pixel centre) on the grid
+ *    portion that holds the samples (their range +- ORC_KDE_MARGIN sqrt(H_zz));
+ *    it replaces K_k(z) S_k in Eq. like-integrals
  *  - the Jacobian (1+z)^3 |J| on the grid (Eq. like-integrals), or, as a
  *    variant, on each sample's KDE weight w_j / [(1+z_j)^3 |J(z_j)|] with the
  *    bandwidth of the weights w_j and psi alone on the grid      (Eq. jacobian)
@@ -443,6 +450,123 @@ int orc_event_kde_binned(const orc_catalog *c, const double *th, int64_t ev,
     return event_kde_impl(c, th, ev, pixel, 1, K);
 }
 
+/* ---- the "3D" kernel ---------------------------------------------------- */
+
+static double det3(const double *A) {
+    return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+           A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+
+/* Covariance of the valid samples' (z, x, y): weighted (weights w, unbiased
+ * normalisation sum w - sum w^2 / sum w) or, with w = NULL, plain (n - 1).  */
+static void cov3(int64_t n, const double *z, const double *xy, const double *w, const int32_t *valid,
+                 double *C) {
+    double V1 = 0.0, V2 = 0.0, m[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = 0; j < n; j++) {
+        if (!valid[j]) continue;
+        double wj = w ? w[j] : 1.0, v[3] = {z[j], xy[2 * j], xy[2 * j + 1]};
+        V1 += wj;
+        V2 += wj * wj;
+        for (int r = 0; r < 3; r++) m[r] += wj * v[r];
+    }
+    for (int r = 0; r < 9; r++) C[r] = 0.0;
+    if (!(V1 > 0.0)) return;
+    for (int r = 0; r < 3; r++) m[r] /= V1;
+    for (int64_t j = 0; j < n; j++) {
+        if (!valid[j]) continue;
+        double wj = w ? w[j] : 1.0, v[3] = {z[j] - m[0], xy[2 * j] - m[1], xy[2 * j + 1] - m[2]};
+        for (int r = 0; r < 3; r++)
+            for (int s = 0; s < 3; s++) C[3 * r + s] += wj * v[r] * v[s];
+    }
+    double fact = V1 - V2 / V1;
+    for (int r = 0; r < 9; r++) C[r] = fact > 0.0 ? C[r] / fact : 0.0;
+}
+
+/* H = Scott factor^2 x covariance, Scott factor n_eff^(-1/7) (d = 3): the
+ * weighted covariance with n_eff = (sum w)^2 / sum w^2, else the plain one
+ * with n = the valid samples; 1 if both are degenerate.                   */
+static int kde3_bandwidth(int64_t n, const double *z, const double *xy, const double *w,
+                          const int32_t *valid, double *H) {
+    double W1 = 0.0, W2 = 0.0;
+    int64_t nv = 0;
+    for (int64_t j = 0; j < n; j++)
+        if (valid[j]) { W1 += w[j]; W2 += w[j] * w[j]; nv++; }
+    double C[9];
+    if (W1 > 0.0 && W1 * W1 / W2 >= 2.0) {
+        cov3(n, z, xy, w, valid, C);
+        if (det3(C) > 0.0) {
+            double f2 = pow(W1 * W1 / W2, -2.0 / 7.0);
+            for (int r = 0; r < 9; r++) H[r] = f2 * C[r];
+            return 0;
+        }
+    }
+    if (nv >= 4) {
+        cov3(n, z, xy, NULL, valid, C);
+        if (det3(C) > 0.0) {
+            double f2 = pow((double)nv, -2.0 / 7.0);
+            for (int r = 0; r < 9; r++) H[r] = f2 * C[r];
+            return 0;
+        }
+    }
+    return 1;
+}
+
+/* K(z_a) = (1/N) sum_j w_j N3((z_a, X_k, Y_k) - (z_j, x_j, y_j); H) on the
+ * support, N the event's sample count.                                    */
+static void kde3_pixel(const orc_catalog *c, int64_t ev, int32_t pixel, const double *z,
+                       const double *w, const int32_t *valid, const double *H, double *K) {
+    int64_t j0 = c->sample_off[ev], n = c->sample_off[ev + 1] - j0;
+    const double *xy = c->sky_xy + 2 * j0, *P = c->pix_xy + 2 * (c->pix_off[ev] + pixel);
+    double d = det3(H), Hi[9];
+    Hi[0] = (H[4] * H[8] - H[5] * H[7]) / d; Hi[1] = (H[2] * H[7] - H[1] * H[8]) / d;
+    Hi[2] = (H[1] * H[5] - H[2] * H[4]) / d; Hi[3] = (H[5] * H[6] - H[3] * H[8]) / d;
+    Hi[4] = (H[0] * H[8] - H[2] * H[6]) / d; Hi[5] = (H[2] * H[3] - H[0] * H[5]) / d;
+    Hi[6] = (H[3] * H[7] - H[4] * H[6]) / d; Hi[7] = (H[1] * H[6] - H[0] * H[7]) / d;
+    Hi[8] = (H[0] * H[4] - H[1] * H[3]) / d;
+    double zlo = INFINITY, zhi = -INFINITY;
+    for (int64_t j = 0; j < n; j++)
+        if (valid[j]) { if (z[j] < zlo) zlo = z[j]; if (z[j] > zhi) zhi = z[j]; }
+    zlo -= ORC_KDE_MARGIN * sqrt(H[0]);
+    zhi += ORC_KDE_MARGIN * sqrt(H[0]);
+    double norm = 1.0 / (pow(2.0 * M_PI, 1.5) * sqrt(d) * (double)n);
+    for (int64_t a = 0; a < c->n_z; a++) {
+        double za = grid_z(c, a), s = 0.0;
+        K[a] = 0.0;
+        if (!(za >= zlo && za <= zhi)) continue;
+        for (int64_t j = 0; j < n; j++) {
+            if (!valid[j] || w[j] == 0.0) continue;
+            double v[3] = {za - z[j], P[0] - xy[2 * j], P[1] - xy[2 * j + 1]}, q = 0.0;
+            for (int r = 0; r < 3; r++)
+                for (int t = 0; t < 3; t++) q += v[r] * Hi[3 * r + t] * v[t];
+            s += w[j] * exp(-0.5 * q);
+        }
+        K[a] = s * norm;
+    }
+}
+
+int orc_event_kde3_bandwidth(const orc_catalog *c, const double *th, int64_t ev, double *H) {
+    int64_t j0 = c->sample_off[ev], n = c->sample_off[ev + 1] - j0;
+    double *z = malloc(sizeof(double) * (n + 1)), *w = malloc(sizeof(double) * (n + 1));
+    int32_t *v = malloc(sizeof(int32_t) * (n + 1));
+    samples_h(c, th, ev, &default_hooks, z, w, v);
+    int rc = kde3_bandwidth(n, z, c->sky_xy + 2 * j0, w, v, H);
+    free(z); free(w); free(v);
+    return rc;
+}
+
+int orc_event_kde3(const orc_catalog *c, const double *th, int64_t ev, int32_t pixel, double *K) {
+    int64_t j0 = c->sample_off[ev], n = c->sample_off[ev + 1] - j0;
+    double *z = malloc(sizeof(double) * (n + 1)), *w = malloc(sizeof(double) * (n + 1)), H[9];
+    int32_t *v = malloc(sizeof(int32_t) * (n + 1));
+    samples_h(c, th, ev, &default_hooks, z, w, v);
+    int rc = kde3_bandwidth(n, z, c->sky_xy + 2 * j0, w, v, H);
+    jacobian_per_sample(c, th, n, z, w, v);
+    if (rc == 0) kde3_pixel(c, ev, pixel, z, w, v, H, K);
+    else for (int64_t a = 0; a < c->n_z; a++) K[a] = 0.0;
+    free(z); free(w); free(v);
+    return rc;
+}
+
 /* Galaxy prior of one pixel on the grid (Eq. p-cat, complete catalog):
  * G(z_a) = (1/N_gal,tot) dV_c/dz(z_a) sum_g N(z_a; z_g, s_g) / Z_g,
  * Z_g = sum_a w_a N(z_a; z_g, s_g) dV_c/dz(z_a); galaxies with Z_g = 0
@@ -527,10 +651,19 @@ static double event_lnI_impl(const orc_catalog *c, const double *th, int64_t ev,
     double *K = malloc(sizeof(double) * nz), *G = malloc(sizeof(double) * nz);
     double *Gs = calloc((size_t)nz, sizeof(double));
     samples_h(c, th, ev, hk, z, w, v);
-    double b = bandwidth_of(n, z, w, v, grid_dz(c));
+    double b = bandwidth_of(n, z, w, v, grid_dz(c)), H[9];
+    int degenerate3 = c->kde_mode == ORC_KDE_3D &&
+                      kde3_bandwidth(n, z, c->sky_xy + 2 * c->sample_off[ev], w, v, H);
     jacobian_per_sample(c, th, n, z, w, v);
     double I = 0.0;
-    if (c->kde_mode == ORC_KDE_MANY_1D) {
+    if (c->kde_mode == ORC_KDE_3D) {
+        /* I = sum_k sum_a w_a K3(z_a, pixel centre k) F(z_a) G_k(z_a) */
+        for (int32_t k = 0; k < npix && !degenerate3; k++) {
+            kde3_pixel(c, ev, k, z, w, v, H, K);
+            galaxy_profile_dv(c, ev, k, dv, vmax, G);
+            for (int64_t a = 0; a < nz; a++) I += grid_w(c, a) * K[a] * F[a] * G[a];
+        }
+    } else if (c->kde_mode == ORC_KDE_MANY_1D) {
         for (int32_t k = 0; k < npix; k++) {
             double S = c->sky_S[c->pix_off[ev] + k];
             kde_grid(c, ev, k, z, w, v, b, binned, K);

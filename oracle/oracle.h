@@ -31,7 +31,7 @@ extern "C" {
 #define ORC_KDE_MARGIN 6.0      /* KDE support: sample range +- 6 bandwidths */
 
 enum { ORC_OK = 0, ORC_OUT_OF_SUPPORT = 1, ORC_NONMONOTONE = 2, ORC_NEFF_LOW = 4 };
-enum { ORC_KDE_SINGLE_1D = 0, ORC_KDE_MANY_1D = 1 };
+enum { ORC_KDE_SINGLE_1D = 0, ORC_KDE_MANY_1D = 1, ORC_KDE_3D = 2 };
 /* KDE kernel shape (Sec. 2.3 offers Gaussian and Epanechnikov).  Reading:
  * the Epanechnikov kernel (3/4)(1 - u^2) on |u| <= 1, u = (z - z_j)/h, with
  * h = sqrt(5) b, the width whose variance equals the Gaussian's b^2. */
@@ -80,6 +80,11 @@ typedef struct {
      * Eq. like-integrals: ORC_JACOBIAN_GRID (on the grid, the paper's form)
      * or ORC_JACOBIAN_PER_SAMPLE (on each PE sample's KDE weight) */
     int32_t jacobian;
+    /* the "3D" kernel (kde_mode ORC_KDE_3D): each sample's sky position and
+     * each flat pixel's centre in a flat local chart of the event's sky
+     * (x, y) [rad], [n_samples x 2] and [n_pix_total x 2] */
+    const double *sky_xy;
+    const double *pix_xy;
 } orc_catalog;
 
 /* ---- cosmology (Eqs. dL-em, dL-mg, jacobian) ---- */
@@ -123,6 +128,11 @@ int64_t orc_linear_bins(int64_t n, const double *z, const double *w, double dz,
                         int64_t b0, int64_t nb, double *cb);
 int orc_kde_arrays(int64_t n, const double *z, const double *w, double b, int64_t nz,
                    double z_max, int32_t binned, int32_t kernel, double *K);
+/* The "3D" kernel (Sec. 2.3, kde_mode ORC_KDE_3D): the bandwidth matrix H
+ * (row-major 3 x 3 over (z, x, y); returns 1 when the sample covariance is
+ * degenerate) and the KDE at the grid points of one pixel's centre. */
+int orc_event_kde3_bandwidth(const orc_catalog *c, const double *th, int64_t ev, double *H);
+int orc_event_kde3(const orc_catalog *c, const double *th, int64_t ev, int32_t pixel, double *K);
 int orc_event_kde_binned(const orc_catalog *c, const double *th, int64_t ev,
                          int32_t pixel, double *K);
 int orc_event_lnI_binned(const orc_catalog *c, const double *th, int64_t ev,

@@ -51,6 +51,7 @@ SEED_BASE = 2504020340
 
 KDE_SINGLE_1D = 0
 KDE_MANY_1D = 1
+KDE_3D = 2  # the "3D" kernel over (z, sky), a cross-check variant
 GAL_F32 = 0
 GAL_F16 = 1
 GAL_BF16 = 2
@@ -160,6 +161,8 @@ def make_catalog(*, n_events, n_pe, n_inj, n_z, Xi0, photo=False,
     pix_of_sample = np.empty(n_events * n_pe, dtype=np.int32)
     pix_off = [0]
     sky_S = []
+    sky_xy = np.empty((n_events * n_pe, 2))  # flat local sky chart per event [rad]
+    pix_xy = []                               # pixel centres in the same chart
     gal_off = [0]
     gal_z = []
     gal_sigma = []
@@ -208,6 +211,11 @@ def make_catalog(*, n_events, n_pe, n_inj, n_z, Xi0, photo=False,
             host_key = int(hit[0]) if hit.size else int(np.argmax(counts))
         npix = keys.size
         pix_of_sample[sl] = pix.astype(np.int32)
+        sky_xy[sl, 0], sky_xy[sl, 1] = x, y
+        if single_pixel:
+            pix_xy.append((0.0, 0.0))
+        else:
+            pix_xy.extend(zip(((keys // 8192) - 4096) * side, ((keys % 8192) - 4096) * side))
         S = counts / (n_pe * side * side)
         sky_S.extend(S.tolist())
         pix_off.append(pix_off[-1] + npix)
@@ -260,6 +268,7 @@ def make_catalog(*, n_events, n_pe, n_inj, n_z, Xi0, photo=False,
         sample_off=sample_off,
         dL=dL, m1_det=m1d, m2_det=m2d, ra=ra, dec=dec,
         pix_of_sample=pix_of_sample,
+        sky_xy=sky_xy, pix_xy=np.asarray(pix_xy, dtype=np.float64).reshape(-1, 2),
         pix_off=np.asarray(pix_off, dtype=np.int64),
         sky_S=np.asarray(sky_S, dtype=np.float64),
         gal_off=np.asarray(gal_off, dtype=np.int64),

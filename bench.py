@@ -318,8 +318,9 @@ def binned_stats(pkg, ctx, torch, dev, theta, steps):
 
 
 def kernel_option_stats(pkg, ctx, torch, dev, cid, theta, NE, steps):
-    """The Epanechnikov kernel option (CHIMERA_KERNEL_EPANECHNIKOV, mixed) on
-    the benchmark catalog and batch, device-timed as the main step."""
+    """The kernel options on the benchmark catalog and batch, device-timed as
+    the main step: the Epanechnikov kernel (CHIMERA_KERNEL_EPANECHNIKOV) and
+    the per-sample Jacobian (CHIMERA_JACOBIAN_PER_SAMPLE), mixed precision."""
     H = theta.shape[0]
     th_dev = torch.tensor(theta, device=dev, dtype=torch.float64)
     out = torch.empty(H, device=dev, dtype=torch.float64)
@@ -327,24 +328,54 @@ def kernel_option_stats(pkg, ctx, torch, dev, cid, theta, NE, steps):
     st = torch.empty(H, device=dev, dtype=torch.int32)
     flush = torch.empty(256 << 20, device=dev, dtype=torch.uint8)
     stream = torch.cuda.current_stream(dev)
-    prec = pkg.MIXED | pkg.KERNEL_EPANECHNIKOV
-    for _ in range(3):
-        pkg.chimera_loglike_device(ctx.h, cid, th_dev, prec, out, neff, st, stream)
-    torch.cuda.synchronize()
-    ms, ev_ms = [], []
-    for _ in range(steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        pkg.chimera_loglike_device(ctx.h, cid, th_dev, prec, out, neff, st, stream)
-        e1.record(stream)
-        ev_ms.append(pkg.chimera_stage_ms(ctx.h)["event"])
+
+    def timed(prec):
+        for _ in range(3):
+            pkg.chimera_loglike_device(ctx.h, cid, th_dev, prec, out, neff, st, stream)
         torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    t = sum(ms) / len(ms)
-    return {"epanechnikov_mixed": {"value": H * NE / (t * 1e-3), "unit": UNIT, "ms_per_step": t,
-                                   "event_kernel_ms": sum(ev_ms) / len(ev_ms),
-                                   "window": "|z - z_j| <= sqrt(5) b, one evaluation per pair"}}
+        ms, ev_ms, rw_ms = [], [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pkg.chimera_loglike_device(ctx.h, cid, th_dev, prec, out, neff, st, stream)
+            e1.record(stream)
+            sm = pkg.chimera_stage_ms(ctx.h)
+            ev_ms.append(sm["event"])
+            rw_ms.append(sm["reweight"])
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = sum(ms) / len(ms)
+        return {"value": H * NE / (t * 1e-3), "unit": UNIT, "ms_per_step": t,
+                "event_kernel_ms": sum(ev_ms) / len(ev_ms), "reweight_ms": sum(rw_ms) / len(rw_ms)}
+
+    epan = timed(pkg.MIXED | pkg.KERNEL_EPANECHNIKOV)
+    epan["window"] = "|z - z_j| <= sqrt(5) b, one evaluation per pair"
+    jac = timed(pkg.MIXED | pkg.JACOBIAN_PER_SAMPLE)
+    jac["note"] = "the Jacobian evaluated per sample in the reweighting kernel, psi alone on the grid"
+    return {"epanechnikov_mixed": epan, "jacobian_per_sample_mixed": jac}
+
+
+def kde3_stats(pkg, ctx, cat, theta, calls=2):
+    """The "3D" kernel (CHIMERA_KDE_3D, FP64, the cross-check variant) on the
+    benchmark catalog loaded as a 3D-kernel catalog: one point per call
+    through chimera_loglike, wall time per call (the FP64 many-1D path is
+    fp64_single_point)."""
+    c3 = dict(cat)
+    c3["kde_mode"] = pkg.KDE_3D
+    cid = ctx.load(c3)
+    try:
+        ts = []
+        for k in range(calls + 1):
+            t0 = time.perf_counter()
+            pkg.chimera_loglike(ctx.h, cid, theta[k % theta.shape[0]:k % theta.shape[0] + 1], pkg.FP64)
+            if k > 0:
+                ts.append(time.perf_counter() - t0)
+    finally:
+        ctx.unload(cid)
+    ms = 1e3 * sum(ts) / len(ts)
+    return {"value": cat["n_events"] / (ms * 1e-3), "unit": UNIT, "ms_per_call": ms, "hyperpoints": 1,
+            "precision": "FP64"}
 
 
 def om_varying_stats(pkg, ctx, cid, theta, NE, calls=3):
@@ -575,6 +606,7 @@ def main():
     binned = binned_stats(pkg, ctx, torch, dev, theta, max(3, args.steps // 2)) if rank == 0 else None
     om_var = om_varying_stats(pkg, ctx, cid, theta, NE) if rank == 0 else None
     kern_opt = kernel_option_stats(pkg, ctx, torch, dev, cid, theta, NE, max(3, args.steps // 2)) if rank == 0 else None
+    kde3 = kde3_stats(pkg, ctx, cat, theta) if rank == 0 else None
     serving = serving_stream(pkg, ctx, cid, cat, args.serve_requests) if args.serve_requests > 0 and rank == 0 else None
 
     kern = sum(kern_ms) / len(kern_ms)
@@ -614,6 +646,7 @@ def main():
         "binned_kde": binned,
         "om_varying": om_var,
         "kernel_options": kern_opt,
+        "kde_3d_fp64": kde3,
         "serving": serving,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(theta.nbytes),
                 "d2h_bytes_per_step": int(H * (8 + 8 + 4))},

@@ -92,6 +92,18 @@ extern "C" {
 /* ---- KDE variant, fixed per catalog (Sec. 2.3) ---- */
 #define CHIMERA_KDE_SINGLE_1D 0 /* one redshift KDE per event, Eq. gw-kernel-single1d */
 #define CHIMERA_KDE_MANY_1D 1   /* one redshift KDE per pixel, Eq. gw-kernel-many1d */
+/* The "3D" kernel, a cross-check variant: one weighted Gaussian KDE per event
+ * over (z, x, y), (x, y) the event's flat sky chart (descriptor sky_xy,
+ * pix_xy), with the bandwidth matrix of Scott's rule in three dimensions
+ * (n_eff^(-2/7) times the weighted sample covariance, unbiased weighting;
+ * the plain covariance of the valid samples if the weighted one is
+ * degenerate), evaluated at (z_a, pixel centre) on the grid portion holding
+ * the samples (their range +- 6 sqrt(H_zz)); it replaces K_k(z) S_k, so
+ * sky_S is not used.  CHIMERA_FP64 only (with or without
+ * CHIMERA_JACOBIAN_PER_SAMPLE); other precisions, the Epanechnikov flag,
+ * chimera_grad and serving reject it (INVALID_ARG).  An event whose sample
+ * covariance is degenerate in both forms has ln I = -inf. */
+#define CHIMERA_KDE_3D 2
 
 /* ---- device storage of galaxy redshifts and widths ---- */
 #define CHIMERA_GAL_F32 0  /* z and sigma as float */
@@ -147,6 +159,10 @@ typedef struct chimera_ctx chimera_ctx;
  *                  missing galaxies homogeneous in comoving volume (Eq.
  *                  p-miss), so a pixel's galaxy term is
  *                  f_R G_cat(z) + (pix_area/4 pi)(1 - P_compl(z)) dV_c/dz / V_c(z_max).
+ *  sky_xy, pix_xy  CHIMERA_KDE_3D catalogs only (NULL otherwise): each PE
+ *                  sample's sky position [n_samples x 2] and each pixel's
+ *                  centre [pix_off[n_events] x 2] in a flat local chart of
+ *                  the event's sky (x, y) [rad], finite.
  */
 typedef struct {
     int32_t n_events;
@@ -169,6 +185,8 @@ typedef struct {
     double f_R;
     const double *pix_area;
     const double *completeness;
+    const double *sky_xy;
+    const double *pix_xy;
 } chimera_catalog_desc;
 
 /* Footprint and sizes of a resident catalog (chimera_catalog_info_t). */

@@ -31,7 +31,7 @@ PT_OK, PT_OUT_OF_SUPPORT, PT_NONMONOTONE, PT_NEFF_LOW = 0, 1, 2, 4
 FP64, MIXED, MIXED_BINNED = 0, 1, 2
 KERNEL_EPANECHNIKOV = 0x10  # OR'ed into the precision: Epanechnikov KDE kernel
 JACOBIAN_PER_SAMPLE = 0x20  # OR'ed into the precision: the Jacobian of Eq. jacobian on each sample
-KDE_SINGLE_1D, KDE_MANY_1D = 0, 1
+KDE_SINGLE_1D, KDE_MANY_1D, KDE_3D = 0, 1, 2
 GAL_F32, GAL_F16, GAL_BF16 = 0, 1, 2
 SERVE_GRAD, SERVE_MIXED = 1, 2
 NPARAM = 12
@@ -75,6 +75,8 @@ class CatalogDesc(C.Structure):
         ("f_R", C.c_double),
         ("pix_area", C.POINTER(C.c_double)),
         ("completeness", C.POINTER(C.c_double)),
+        ("sky_xy", C.POINTER(C.c_double)),
+        ("pix_xy", C.POINTER(C.c_double)),
     ]
 
 
@@ -192,7 +194,9 @@ def make_desc(cat):
         int(cat.get("kde_mode", KDE_MANY_1D)), int(cat.get("gal_storage", GAL_F32)),
         float(cat.get("f_R", 1.0)),
         arr("pix_area", np.float64) if cat.get("completeness") is not None else None,
-        arr("completeness", np.float64) if cat.get("completeness") is not None else None)
+        arr("completeness", np.float64) if cat.get("completeness") is not None else None,
+        arr("sky_xy", np.float64) if int(cat.get("kde_mode", KDE_MANY_1D)) == KDE_3D else None,
+        arr("pix_xy", np.float64) if int(cat.get("kde_mode", KDE_MANY_1D)) == KDE_3D else None)
     return d, keep
 
 

@@ -467,6 +467,10 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
     const bool epan = (precision & CHIMERA_KERNEL_EPANECHNIKOV) != 0;
     const bool jac_ps = (precision & CHIMERA_JACOBIAN_PER_SAMPLE) != 0;
     precision &= ~(CHIMERA_KERNEL_EPANECHNIKOV | CHIMERA_JACOBIAN_PER_SAMPLE);  // the base precision below
+    if (cat.d.kde_mode == CHIMERA_KDE_3D && (precision != CHIMERA_FP64 || epan)) {
+        set_error("CHIMERA_KDE_3D catalogs take CHIMERA_FP64 with the Gaussian kernel");
+        return CHIMERA_ERR_INVALID_ARG;
+    }
     RC(ws_ensure(ctx, ws, H, cat));
     ctx.tick++;
     const DevCatalog &c = cat.d;
@@ -543,8 +547,10 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
     launch_selection(c, p, H, precision == CHIMERA_FP64, ws.st2);
     if (ws.trace) CK(cudaEventRecord(ws.tev[9], ws.st2));
     CK(cudaEventRecord(ws.ev_join, ws.st2));
-    if (precision == CHIMERA_FP64) launch_event_fp64(c, p, H, ws.st);
-    else {
+    if (precision == CHIMERA_FP64) {
+        if (c.kde_mode == CHIMERA_KDE_3D) launch_event_3d(c, p, H, ws.st);
+        else launch_event_fp64(c, p, H, ws.st);
+    } else {
         // reweighting and event integrals by tiles of hyperpoints
         const int tile = std::max(1, std::min(H, ws.zw_tile));
         const int ntiles = (H + tile - 1) / tile;
@@ -620,7 +626,10 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         return bad("null injection array");
     if (!(d->lambda_g >= 0.0 && d->lambda_g <= 1.0) || !std::isfinite(d->beta))
         return bad("lambda_g must lie in [0, 1] and beta be finite");
-    if (d->kde_mode != CHIMERA_KDE_SINGLE_1D && d->kde_mode != CHIMERA_KDE_MANY_1D) return bad("bad kde_mode");
+    if (d->kde_mode != CHIMERA_KDE_SINGLE_1D && d->kde_mode != CHIMERA_KDE_MANY_1D && d->kde_mode != CHIMERA_KDE_3D)
+        return bad("bad kde_mode");
+    if (d->kde_mode == CHIMERA_KDE_3D && (!d->sky_xy || !d->pix_xy))
+        return bad("a CHIMERA_KDE_3D catalog needs sky_xy and pix_xy");
     if (d->gal_storage < 0 || d->gal_storage > 2) return bad("bad gal_storage");
     if (d->completeness) {
         if (!d->pix_area) return bad("an incomplete catalog needs pix_area");
@@ -903,6 +912,21 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     std::vector<int64_t> ev_poff(d->pix_off, d->pix_off + ne + 1);
     std::vector<int64_t> goff(d->gal_off, d->gal_off + np + 1);
     std::vector<double> pixS(d->sky_S, d->sky_S + np);
+    // the "3D" kernel's sky chart: samples in device order, pixels as given
+    std::vector<double2> sxy, pxy;
+    if (d->kde_mode == CHIMERA_KDE_3D) {
+        sxy.resize(ns);
+        pxy.resize(np);
+        for (int64_t j = 0; j < ns; j++) {
+            const int64_t o = order[j];
+            sxy[j] = make_double2(d->sky_xy[2 * o], d->sky_xy[2 * o + 1]);
+            if (!std::isfinite(sxy[j].x) || !std::isfinite(sxy[j].y)) return bad("sky_xy must be finite");
+        }
+        for (int64_t q = 0; q < np; q++) {
+            pxy[q] = make_double2(d->pix_xy[2 * q], d->pix_xy[2 * q + 1]);
+            if (!std::isfinite(pxy[q].x) || !std::isfinite(pxy[q].y)) return bad("pix_xy must be finite");
+        }
+    }
     // incomplete catalog: the missing-galaxy weight (1 - P_compl) pix_area / 4 pi
     std::vector<double> miss64;
     std::vector<float> miss32;
@@ -958,6 +982,8 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         {(void **)&c.gw_pix, gw_pix.data(), 4 * gw_pix.size()},
         {(void **)&c.miss64, miss64.data(), 8 * miss64.size()},
         {(void **)&c.miss32, miss32.data(), 4 * miss32.size()},
+        {(void **)&c.sky_xy, sxy.data(), 16 * sxy.size()},
+        {(void **)&c.pix_xy, pxy.data(), 16 * pxy.size()},
         {(void **)&c.gw_g0, gw_g0.data(), 8 * gw_g0.size()},
         {(void **)&c.dense_pix, dense_pix.data(), 4 * dense_pix.size()},
         {(void **)&c.gz64, gz.data(), 8 * gz.size()},
@@ -1057,7 +1083,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx.device);
     if ((int)event_mixed_smem(c) > maxsm || (int)event_fp64_smem(c) > maxsm ||
-        (int)event_binned_smem(c) > maxsm) {
+        (int)event_binned_smem(c) > maxsm || (int)event_3d_smem(c) > maxsm) {
         for (void *a : cat->allocs) cudaFree(a);
         ctx.used -= cat->bytes;
         set_error("catalog needs more shared memory per block than the device offers");
@@ -1286,6 +1312,10 @@ int chimera_grad(chimera_ctx *h, int32_t id, int32_t n, const double *theta, int
     std::lock_guard<std::recursive_mutex> lk(ctx.mu);
     auto cat = find_catalog(ctx, id);
     if (!cat) { set_error("unknown catalog id"); return CHIMERA_ERR_NOT_FOUND; }
+    if (cat->d.kde_mode == CHIMERA_KDE_3D) {
+        set_error("the adjoint covers the 1-D kernels: CHIMERA_KDE_3D catalogs have no gradient");
+        return CHIMERA_ERR_INVALID_ARG;
+    }
     CK(cudaSetDevice(ctx.device));
     RC(forward(ctx, *cat, ctx.ws, n, theta, prec));
     RC(backward(ctx, *cat, ctx.ws, n, prec));
@@ -1303,6 +1333,14 @@ int chimera_grad(chimera_ctx *h, int32_t id, int32_t n, const double *theta, int
 int chimera_serve_submit(chimera_ctx *h, int32_t id, int32_t n, const double *theta, int32_t flags,
                          uint64_t *ticket) {
     if (!h || !theta || !ticket || n <= 0) { set_error("bad argument"); return CHIMERA_ERR_INVALID_ARG; }
+    {
+        std::lock_guard<std::recursive_mutex> lk(h->c.mu);
+        auto cat = find_catalog(h->c, id);
+        if (cat && cat->d.kde_mode == CHIMERA_KDE_3D) {
+            set_error("serving runs the mixed 1-D kernels: CHIMERA_KDE_3D catalogs are not served");
+            return CHIMERA_ERR_INVALID_ARG;
+        }
+    }
     return serve_submit(h->c, id, n, theta, flags, ticket);
 }
 

@@ -126,6 +126,9 @@ struct DevCatalog {
     int2 *dense_items64, *dense_items32;
     // incomplete catalog: f_R and, per pixel and grid point, the missing-
     // galaxy weight (1 - P_compl) pix_area / 4 pi (nullptr when complete)
+    // the "3D" kernel: samples' sky positions (device order) and pixel
+    // centres in the event's flat sky chart [rad] (nullptr otherwise)
+    double2 *sky_xy, *pix_xy;
     int32_t incomplete;
     double f_R;
     double *miss64;
@@ -239,6 +242,9 @@ void launch_event_binned(const DevCatalog &c, const CallPtrs &p, int h0, int nh,
 size_t event_binned_smem(const DevCatalog &c);
 size_t event_mixed_smem(const DevCatalog &c);
 size_t event_fp64_smem(const DevCatalog &c);
+// The "3D" kernel of CHIMERA_KDE_3D catalogs (FP64 only).
+size_t event_3d_smem(const DevCatalog &c);
+void launch_event_3d(const DevCatalog &c, const CallPtrs &p, int H, cudaStream_t st);
 // K5: selection partial sums; K6: combine into ln L.
 void launch_selection(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, cudaStream_t st);
 // raw: the mixed event kernel left raw integrals in lnI (K6 takes the log).

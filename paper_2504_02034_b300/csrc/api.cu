@@ -466,7 +466,8 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
             double *out_lnL, double *out_neff, int32_t *out_status) {
     const bool epan = (precision & CHIMERA_KERNEL_EPANECHNIKOV) != 0;
     const bool jac_ps = (precision & CHIMERA_JACOBIAN_PER_SAMPLE) != 0;
-    precision &= ~(CHIMERA_KERNEL_EPANECHNIKOV | CHIMERA_JACOBIAN_PER_SAMPLE);  // the base precision below
+    const bool for_grad = (precision & PREC_WITH_GRAD) != 0;
+    precision &= ~(CHIMERA_KERNEL_EPANECHNIKOV | CHIMERA_JACOBIAN_PER_SAMPLE | PREC_WITH_GRAD);  // the base precision
     if (cat.d.kde_mode == CHIMERA_KDE_3D && (precision != CHIMERA_FP64 || epan)) {
         set_error("CHIMERA_KDE_3D catalogs take CHIMERA_FP64 with the Gaussian kernel");
         return CHIMERA_ERR_INVALID_ARG;
@@ -529,7 +530,7 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
     p.kshape = epan ? 1 : 0;
     p.jac_ps = jac_ps ? 1 : 0;
     if (p.pairs) CK(cudaMemsetAsync(p.pairs, 0, sizeof(unsigned long long) * H, ws.st));
-    launch_hyper_tables(c, p, H, precision == CHIMERA_FP64, ws.dk, ws.fmax_bits, ws.st);
+    launch_hyper_tables(c, p, H, precision == CHIMERA_FP64, for_grad, ws.dk, ws.fmax_bits, ws.st);
     if (ws.trace) CK(cudaEventRecord(ws.tev[2], ws.st));
     // the selection term needs only the per-point tables: it runs on a side
     // stream of the lowest priority beside the event kernels, whose blocks
@@ -1317,7 +1318,7 @@ int chimera_grad(chimera_ctx *h, int32_t id, int32_t n, const double *theta, int
         return CHIMERA_ERR_INVALID_ARG;
     }
     CK(cudaSetDevice(ctx.device));
-    RC(forward(ctx, *cat, ctx.ws, n, theta, prec));
+    RC(forward(ctx, *cat, ctx.ws, n, theta, prec | PREC_WITH_GRAD));
     RC(backward(ctx, *cat, ctx.ws, n, prec));
     cudaStream_t st = ctx.ws.st;
     CK(cudaMemcpyAsync(lnL, ctx.ws.lnL, sizeof(double) * n, cudaMemcpyDeviceToHost, st));

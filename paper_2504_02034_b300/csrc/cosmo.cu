@@ -104,6 +104,20 @@ __device__ __forceinline__ void dgw_J32(float z, float D, float cH, float om, fl
     J = (D + a * cH / E) * xi + a * D * dxi;
 }
 
+// D_c/(c/H0) by cubic Hermite on the forward table, in FP32.
+__device__ __forceinline__ float dc_hermite32(const double *fwd, float z, float om) {
+    const float ht = (float)HT;
+    const float t = z / ht;
+    const int k = min(max((int)floorf(t), 0), NT_FWD - 2);
+    const float f = t - k, f2 = f * f, f3 = f2 * f;
+    auto slope = [om, ht](float zz) {
+        const float aa = 1.f + zz;
+        return ht / sqrtf(om * aa * aa * aa + 1.f - om);
+    };
+    return (2.f * f3 - 3.f * f2 + 1.f) * (float)fwd[k] + (f3 - 2.f * f2 + f) * slope(k * ht) +
+           (-2.f * f3 + 3.f * f2) * (float)fwd[k + 1] + (f3 - f2) * slope((k + 1) * ht);
+}
+
 // K1b.1, one launch for two independent parts per hyperpoint (blockIdx.y):
 //  * blocks x < nbn: d_L^gw and J at the forward nodes, in FP32 (they seed
 //    the FP64 inversion and carry the monotonicity check: J <= 0 on z <= 10
@@ -139,17 +153,8 @@ __global__ void __launch_bounds__(HYP_THREADS) k_nodes_grid(DevCatalog c, CallPt
             p.F64[(size_t)h * c.n_z + a] = F;
             bits = (unsigned long long)__double_as_longlong(F);
         } else {
-            // D_c by cubic Hermite on the forward table, in FP32
-            const float z = a * c.dz32, om = (float)th[1], ht = (float)HT;
-            const float t = z / ht;
-            const int k = min(max((int)floorf(t), 0), NT_FWD - 2);
-            const float f = t - k, f2 = f * f, f3 = f2 * f;
-            auto slope = [om, ht](float zz) {
-                const float aa = 1.f + zz;
-                return ht / sqrtf(om * aa * aa * aa + 1.f - om);
-            };
-            const float Dh = (2.f * f3 - 3.f * f2 + 1.f) * (float)fwd[k] + (f3 - 2.f * f2 + f) * slope(k * ht) +
-                             (-2.f * f3 + 3.f * f2) * (float)fwd[k + 1] + (f3 - f2) * slope((k + 1) * ht);
+            const float z = a * c.dz32, om = (float)th[1];
+            const float Dh = dc_hermite32(fwd, z, om);
             float d, J;
             dgw_J32(z, (float)cH * Dh, (float)cH, om, (float)th[2], (float)th[3], d, J);
             const float ap = 1.f + z, l2a = log2f(ap);
@@ -168,14 +173,18 @@ __global__ void __launch_bounds__(HYP_THREADS) k_nodes_grid(DevCatalog c, CallPt
 
 // K1b.2: inverse nodes z(u_k), d = d_top u_k^2: bracketing on the forward
 // nodes (staged in shared memory), cubic Hermite of z(d) between the two
-// bracketing nodes (slopes 1/J), then one FP64 Newton step on the
-// Hermite-interpolated forward relation.  A block computes the nodes
-// base .. base+256 (one more than it owns) so that it also writes the FP32
-// node pairs of its intervals.
-constexpr int INV_THREADS = 128;  // FP64-bound: 2049 nodes x H spread over every SM
+// bracketing nodes (slopes 1/J), then one Newton step on the
+// Hermite-interpolated forward relation: in FP32 for the FP32 node pairs
+// (inv32, all the mixed forward path reads), and with NODES64 also in FP64
+// for the FP64 nodes (inv64: the FP64 path and the adjoint).  The FP32 pairs
+// do not depend on NODES64, so a mixed ln L is the same with or without a
+// gradient.  A block computes the nodes base .. base+INV_THREADS (one more
+// than it owns) so that it also writes the FP32 pairs of its intervals.
+constexpr int INV_THREADS = 128;  // 2049 nodes x H spread over every SM
+template <bool NODES64>
 __global__ void __launch_bounds__(INV_THREADS) k_inv_nodes(DevCatalog c, CallPtrs p, const float2 *djall) {
     __shared__ float sdk[NT_FWD];
-    __shared__ double2 snd[INV_THREADS + 1];
+    __shared__ float2 snd32[INV_THREADS + 1];
     const int h = blockIdx.y;
     const int base = blockIdx.x * INV_THREADS;
     const float2 *dj = djall + (size_t)h * NT_FWD;
@@ -185,15 +194,19 @@ __global__ void __launch_bounds__(INV_THREADS) k_inv_nodes(DevCatalog c, CallPtr
     const double *fwd = p.fwd[h];
     const double cH = C_KMS / th[0], Om = th[1];
     const double dtop = c.d_top;
+    const float cH32 = (float)cH, om32 = (float)Om, xi32 = (float)th[2], n32 = (float)th[3];
     for (int t = threadIdx.x; t <= INV_THREADS; t += INV_THREADS) {
         const int k = base + t;
         if (k > NU) break;
         const double u = (double)k / NU, d = dtop * u * u;
         double z = 0.0, dzdu = 0.0;
+        float z32 = 0.f, dzdu32 = 0.f;
         if (k > 0) {
             if (!(d <= (double)sdk[NT_FWD - 1])) {
                 z = CUDART_NAN;
                 dzdu = CUDART_NAN;
+                z32 = CUDART_NAN_F;
+                dzdu32 = CUDART_NAN_F;
             } else {
                 int lo = 0, hi = NT_FWD - 1;  // sdk[lo] <= d < sdk[hi]
                 while (hi - lo > 1) {
@@ -203,24 +216,35 @@ __global__ void __launch_bounds__(INV_THREADS) k_inv_nodes(DevCatalog c, CallPtr
                 const double dl = sdk[lo], dh = sdk[hi], den = dh - dl;
                 const double tt = den > 0.0 ? (d - dl) / den : 0.0;
                 const double t2 = tt * tt, t3 = t2 * tt;
-                z = (2 * t3 - 3 * t2 + 1) * (lo * HT) + (t3 - 2 * t2 + tt) * den / (double)dj[lo].y +
-                    (-2 * t3 + 3 * t2) * (hi * HT) + (t3 - t2) * den / (double)dj[hi].y;
-                double dd, J;
-                chimd::dgw_J(z, cH * chimd::dc_hermite(fwd, z, Om), th, cH, &dd, &J);
-                const double step = (dd - d) / J;
-                if (isfinite(step)) z -= step;
-                dzdu = 2.0 * u * dtop / J;
+                const double z0 = (2 * t3 - 3 * t2 + 1) * (lo * HT) + (t3 - 2 * t2 + tt) * den / (double)dj[lo].y +
+                                  (-2 * t3 + 3 * t2) * (hi * HT) + (t3 - t2) * den / (double)dj[hi].y;
+                {  // FP32 Newton step from the seed
+                    const float zs = (float)z0, d32 = (float)d;
+                    float dd, J;
+                    dgw_J32(zs, cH32 * dc_hermite32(fwd, zs, om32), cH32, om32, xi32, n32, dd, J);
+                    const float step = (dd - d32) / J;
+                    z32 = isfinite(step) ? zs - step : zs;
+                    dzdu32 = 2.f * (float)u * (float)dtop / J;
+                }
+                if (NODES64) {
+                    z = z0;
+                    double dd, J;
+                    chimd::dgw_J(z, cH * chimd::dc_hermite(fwd, z, Om), th, cH, &dd, &J);
+                    const double step = (dd - d) / J;
+                    if (isfinite(step)) z -= step;
+                    dzdu = 2.0 * u * dtop / J;
+                }
             }
         }
-        snd[t] = make_double2(z, dzdu);
-        if (t < INV_THREADS || k == NU) p.inv64[(size_t)h * (NU + 1) + k] = snd[t];
+        snd32[t] = make_float2(z32, dzdu32);
+        if (NODES64 && (t < INV_THREADS || k == NU)) p.inv64[(size_t)h * (NU + 1) + k] = make_double2(z, dzdu);
     }
     __syncthreads();
     const int k = base + threadIdx.x;
     if (k < NU) {
-        const double inv_nu = 1.0 / NU;  // exact: NU is a power of two
-        const double2 a = snd[threadIdx.x], b = snd[threadIdx.x + 1];
-        p.inv32[(size_t)h * NU + k] = make_float4((float)a.x, (float)(a.y * inv_nu), (float)b.x, (float)(b.y * inv_nu));
+        const float inv_nu = 1.f / NU;  // exact: NU is a power of two
+        const float2 a = snd32[threadIdx.x], b = snd32[threadIdx.x + 1];
+        p.inv32[(size_t)h * NU + k] = make_float4(a.x, a.y * inv_nu, b.x, b.y * inv_nu);
     }
 }
 
@@ -348,14 +372,16 @@ void launch_fwd_table(double Om, double *out, cudaStream_t st) {
     launch_fwd_tables(b, false, st);
 }
 
-void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, double *dk,
+void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, bool nodes64, double *dk,
                          unsigned long long *fmax_bits, cudaStream_t st) {
     float2 *dj = reinterpret_cast<float2 *>(dk);  // (d, J) of the forward nodes, FP32
     cudaMemsetAsync(fmax_bits, 0, sizeof(unsigned long long) * H, st);
     const int nbn = (NT_FWD + HYP_THREADS - 1) / HYP_THREADS;
     const int nbg = (c.n_z + HYP_THREADS - 1) / HYP_THREADS;
     k_nodes_grid<<<dim3(nbn + nbg, H), HYP_THREADS, 0, st>>>(c, p, dj, fmax_bits, nbn, fp64);
-    k_inv_nodes<<<dim3((NU + INV_THREADS - 1) / INV_THREADS, H), INV_THREADS, 0, st>>>(c, p, dj);
+    const dim3 gi((NU + INV_THREADS - 1) / INV_THREADS, H);
+    if (fp64 || nodes64) k_inv_nodes<true><<<gi, INV_THREADS, 0, st>>>(c, p, dj);
+    else k_inv_nodes<false><<<gi, INV_THREADS, 0, st>>>(c, p, dj);
     k_hyper_final<<<dim3(fp64 ? 1 : nbg, H), HYP_THREADS, 0, st>>>(c, p, fmax_bits, fp64);
 }
 

@@ -190,7 +190,8 @@ void launch_fwd_tables(const FwdBatch &b, bool dOm, cudaStream_t st);
 // fp64, normalised F32 otherwise), status.  dk: scratch of at least
 // H x NT_FWD x 8 bytes (FP32 d_L^gw and J at the forward nodes),
 // fmax_bits: [H] scratch.
-void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, double *dk,
+// nodes64: also the FP64 inverse nodes (inv64; FP64 calls and gradients).
+void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, bool nodes64, double *dk,
                          unsigned long long *fmax_bits, cudaStream_t st);
 // K3: galaxy redshift prior on the grid for one Om.  dv: scratch of n_z
 // doubles followed by n_z floats, invZ: [n_gal] scratch; out64 (FP64

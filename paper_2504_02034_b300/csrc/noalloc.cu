@@ -225,7 +225,7 @@ extern "C" int chimera_selection_static(int32_t n_points, const double *theta, i
     p.F32 = reinterpret_cast<float *>(S + OFF_F32);
     p.selp = reinterpret_cast<double *>(S + OFF_SELP);
     p.n_chunk = selection_chunks(c);
-    launch_hyper_tables(c, p, H, true, reinterpret_cast<double *>(S + OFF_DK),
+    launch_hyper_tables(c, p, H, true, true, reinterpret_cast<double *>(S + OFF_DK),
                         reinterpret_cast<unsigned long long *>(S + OFF_FMAX), st);
     launch_selection(c, p, H, true, st);
     k_static_reduce<<<H, 256, 0, st>>>(p.selp, p.n_chunk, (double)n_inj_total, p.hp, xi, neff);

@@ -146,6 +146,10 @@ void ws_destroy_streams(Workspace &ws);
 // device in `ws`.  Returns a CHIMERA_ERR_* code.
 // The forward pass; out_* (device, may be nullptr) also receive ln L, N_eff
 // and the status words from the combine kernel.
+// PREC_WITH_GRAD, OR'ed into the precision by the gradient entry points only:
+// the forward pass of a gradient call (keeps the FP64 inverse nodes the
+// adjoint reads).
+constexpr int PREC_WITH_GRAD = 0x1000;
 int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, int precision,
             double *out_lnL = nullptr, double *out_neff = nullptr, int32_t *out_status = nullptr);
 // Adjoint after forward() on the same workspace (reads the sanitised theta

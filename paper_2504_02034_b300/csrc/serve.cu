@@ -128,7 +128,7 @@ int Server::launch(Lane &L, std::vector<std::shared_ptr<Request>> &b) {
         cudaGetLastError();
         return CHIMERA_ERR_CUDA;
     }
-    rc = forward(c, *cat, L.ws, H, th.data(), prec);
+    rc = forward(c, *cat, L.ws, H, th.data(), grad ? prec | PREC_WITH_GRAD : prec);
     if (rc) return rc;
     if (grad) {
         rc = backward(c, *cat, L.ws, H, prec);

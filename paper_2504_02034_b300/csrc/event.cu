@@ -327,6 +327,9 @@ __device__ __forceinline__ float jac_inv32(const HP &hp, float z, float lz, floa
     return __fdividef(rap * rap * rap, fabsf(J));
 }
 
+// JAC: the per-sample Jacobian option (a template parameter so that the
+// default kernel keeps its registers and occupancy).
+template <bool JAC>
 __global__ void __launch_bounds__(RW_THREADS) k_reweight(DevCatalog c, CallPtrs p, int h0, int nh) {
     __shared__ double red[8 + (RW_THREADS / 32) * 8];
     const int hl = blockIdx.x % nh, h = h0 + hl;
@@ -350,7 +353,6 @@ __global__ void __launch_bounds__(RW_THREADS) k_reweight(DevCatalog c, CallPtrs 
         if (!isfinite(zref)) zref = 0.f;
     }
     float m[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // W1, Wd, Wd2, W2, n, Sd, Sd2
-    const bool jac_ps = p.jac_ps != 0;
     const float dtop = (float)c.d_top;
     // one sample: table coordinate -> z (Hermite on the node pair), log2
     // source masses, weight, moments; invalid samples (beyond d_L^gw(10))
@@ -366,7 +368,7 @@ __global__ void __launch_bounds__(RW_THREADS) k_reweight(DevCatalog c, CallPtrs 
         m[0] += w; m[1] += wd_; m[2] = fmaf(wd_, d, m[2]); m[3] = fmaf(w, w, m[3]);
         m[4] += ok ? 1.f : 0.f; m[5] += d; m[6] = fmaf(d, d, m[6]);
         zd[j] = ok ? z : CUDART_INF_F;
-        if (jac_ps && ok) {  // the Jacobian on the sample (the moments above keep w)
+        if (JAC && ok) {  // the Jacobian on the sample (the moments above keep w)
             const float t = (float)__float_as_int(sv.x) + sv.y, u = t * (1.f / NU);
             w *= jac_inv32(hp, z, lz, dtop * u * u);
         }
@@ -1117,7 +1119,8 @@ size_t event_fp64_smem(const DevCatalog &c) {
 
 void launch_reweight(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cudaStream_t st) {
     const unsigned nb = (unsigned)((int64_t)c.n_events * nh);
-    if (nb) k_reweight<<<nb, RW_THREADS, 0, st>>>(c, p, h0, nh);
+    if (nb && p.jac_ps) k_reweight<true><<<nb, RW_THREADS, 0, st>>>(c, p, h0, nh);
+    else if (nb) k_reweight<false><<<nb, RW_THREADS, 0, st>>>(c, p, h0, nh);
 }
 
 void launch_event_mixed(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cudaStream_t st) {

@@ -194,10 +194,13 @@ def measured_peaks():
 
 def traffic_from_profiles():
     """DRAM bytes per event-kernel launch from the committed ncu summary, if
-    it was taken on the current kernel source."""
+    it was taken on the current kernel source (event.cu with the headers it
+    includes, whose constants set the kernel's windows and layout)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2504_02034_b300", "csrc", "event.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("event.cu", "internal.cuh", "mass.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2504_02034_b300", "csrc", name), "rb").read())
+    sha = h.hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", "event_mixed_o5_c2.txt")
     if not os.path.exists(path):
         return None
@@ -206,7 +209,7 @@ def traffic_from_profiles():
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("event_cu_sha256_16") != sha:
+    if vals.get("kernel_source_sha256_16") != sha:
         return None
     try:
         return float(vals["traffic_bytes_per_launch_full_size"])

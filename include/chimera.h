@@ -333,7 +333,7 @@ int chimera_stage_ms(chimera_ctx *ctx, double *ms);
 /*
  * chimera_kde_pairs: algorithmic work of the mixed-precision event kernel,
  * for the roofline: for each of the n_points hyperpoints, the number of
- * (PE sample, grid point) pairs with w_j > 0 and |z_a - z_j| <= 6 b_i,
+ * (PE sample, grid point) pairs with w_j > 0 and |z_a - z_j| <= 5.5 b_i,
  * summed over all events.  pairs: host [n_points] int64 out.
  */
 int chimera_kde_pairs(chimera_ctx *ctx, int32_t catalog_id, int32_t n_points, const double *theta,

@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
 //
 // The grid term, sum_a M(a) Q_k(a) = sum_j pf w_j sum_a e_ja H(a) Q_k(a),
 // needs per sample sum_a e_ja H(a) Q_k(a).  Q_k = d ln F / dtheta_k is a
-// smooth function of z (Q for H0 is exactly 1/H0); over a window of +-6 b
+// smooth function of z (Q for H0 is exactly 1/H0); over a window of +-KW32 b
 // it is replaced by its second-order Taylor polynomial about the sample's
 // grid point a_j, so that
 //   sum_a e H Q_k = Q_k S0 + Q_k' m1 + (Q_k''/2) m2,

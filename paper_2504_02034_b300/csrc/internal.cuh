@@ -21,7 +21,7 @@ constexpr int NT_FWD = 4918;
 // Inverse table: NU intervals uniform in u = sqrt(d_L / d_top).
 constexpr int NU = 2048;
 // KDE window half-widths in bandwidths (mixed / FP64) and galaxy window in sigmas.
-constexpr float KW32 = 6.0f;
+constexpr float KW32 = 5.5f;
 constexpr double KW64 = 9.0;
 constexpr float KWG32 = 6.0f;
 constexpr int GAL_CHUNK = 256;   // galaxies per normalisation block

@@ -50,6 +50,8 @@ def test_static_selection_matches_catalog_path():
 def test_static_selection_rejects_oversize():
     import torch
 
+    from paper_2504_02034_b300 import build
+    build.build()
     import paper_2504_02034_b300 as pkg
     dev = torch.device("cuda", 0)
     z = torch.ones(4, device=dev, dtype=torch.float64)

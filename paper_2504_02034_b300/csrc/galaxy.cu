@@ -630,11 +630,9 @@ void launch_multi_t(const DevCatalog &c, const MultiOm &m, float *dvm, float *in
     k_dvdz_multi<WITH_O><<<dim3((unsigned)((c.n_z + 1 + 63) / 64), PROF_MB), 64, 0, st>>>(m, c, dvm, dvOm);
     if (c.n_gw > 0) k_gal_norm_multi<WITH_O><<<(unsigned)c.n_gw, GAL_CHUNK, 0, st>>>(c, dvm, dvOm, invZm, ZOm);
     constexpr size_t smem = gather_multi_smem(WITH_O);
-    static bool attr = false;  // opt in to more than 48 KB of dynamic shared memory once
-    if (!attr) {
-        cudaFuncSetAttribute(k_gal_gather_multi<WITH_O>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    // the opt-in to more than 48 KB of dynamic shared memory is per device:
+    // set it on every launch (the current device may change between calls)
+    cudaFuncSetAttribute(k_gal_gather_multi<WITH_O>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_gal_gather_multi<WITH_O><<<(unsigned)c.n_pix, GAL_THREADS, smem, st>>>(c, m, dvm, dvOm, invZm, ZOm);
     const int64_t nh = c.n_dheavy32, nl = c.n_ditems32 - nh;
     const int wpb = GAL_THREADS / 32;

@@ -180,6 +180,9 @@ def make_desc(cat):
         keep[key] = a
         return a.ctypes.data_as(C.POINTER(np.ctypeslib.as_ctypes_type(dt)))
 
+    def opt(key):  # optional array: NULL when absent (the library reports what is missing)
+        return arr(key, np.float64) if cat.get(key) is not None else None
+
     ndet = int(np.asarray(cat["inj_dL"]).size)
     d = CatalogDesc(
         int(cat["n_events"]), arr("sample_off", np.int64),
@@ -193,10 +196,10 @@ def make_desc(cat):
         float(cat["lambda_g"]), float(cat["beta"]),
         int(cat.get("kde_mode", KDE_MANY_1D)), int(cat.get("gal_storage", GAL_F32)),
         float(cat.get("f_R", 1.0)),
-        arr("pix_area", np.float64) if cat.get("completeness") is not None else None,
-        arr("completeness", np.float64) if cat.get("completeness") is not None else None,
-        arr("sky_xy", np.float64) if int(cat.get("kde_mode", KDE_MANY_1D)) == KDE_3D else None,
-        arr("pix_xy", np.float64) if int(cat.get("kde_mode", KDE_MANY_1D)) == KDE_3D else None)
+        opt("pix_area") if cat.get("completeness") is not None else None,
+        opt("completeness"),
+        opt("sky_xy") if int(cat.get("kde_mode", KDE_MANY_1D)) == KDE_3D else None,
+        opt("pix_xy") if int(cat.get("kde_mode", KDE_MANY_1D)) == KDE_3D else None)
     return d, keep
 
 

@@ -503,7 +503,7 @@ def main():
                     help="run W warm-up gradient calls (mixed, the benchmark batch) and one more, then exit (for ncu)")
     ap.add_argument("--profile-om", action="store_true",
                     help="run W warm-up ln L calls and one more, each bringing 16 new Om values "
-                         "(mixed, the benchmark batch; two batched profile passes per call), then exit (for ncu)")
+                         "(mixed, the benchmark batch; one batched profile pass per call), then exit (for ncu)")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":

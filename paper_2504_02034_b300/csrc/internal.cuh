@@ -27,7 +27,7 @@ constexpr float KWG32 = 6.0f;
 constexpr int GAL_CHUNK = 256;   // galaxies per normalisation block
 constexpr int GAL_DENSE = 1024;  // pixels above this gather per grid point by blocks
 constexpr int GAL_HEAVY = 256;   // dense-pixel points with more candidates: a block each
-constexpr int PROF_MB = 8;       // Om values per batched (mixed) profile pass
+constexpr int PROF_MB = 16;      // Om values per batched (mixed) profile pass
 // Each KDE is zero outside the grid segment holding its samples, widened by
 // KDE_MARGIN bandwidths (Sec. 2.3: evaluated only where the samples are).
 constexpr double KDE_MARGIN = 6.0;

@@ -1,10 +1,10 @@
-"""The batched mixed-path galaxy profiles (up to PROF_MB = 8 new Om values per
+"""The batched mixed-path galaxy profiles (up to PROF_MB = 16 new Om values per
 pass, the Om-independent Gaussians shared by the columns; Eq. p-cat as a
 contraction over galaxies) against the one-Om launches and the oracle.
 
 The batched kernels repeat the one-Om arithmetic per column in the same
 order, so ln L and every ln I_i must be bit-identical between a call that
-brings 13 new Om values at once (batches of 8 and 5) and calls that bring
+brings 19 new Om values at once (batches of 16 and 3) and calls that bring
 them one by one; and both must match the oracle at the mixed tolerance
 (per event 1e-4, ln L 1e-3).  Covers many-1D and single-1D, F32 and BF16
 galaxy storage, sparse and dense pixels, and an incomplete catalog.
@@ -55,8 +55,8 @@ def test_batched_profiles_equal_one_om_and_oracle(chim, ctx, orc, name, kw, inco
     a, b = ctx.load(cat), ctx.load(cat)
     try:
         for k, prec in enumerate((chim.MIXED, chim.MIXED_BINNED)):
-            th = _points(13, seed=100 * k + len(name))  # new Om values for each precision
-            lb, _, sb = ctx.loglike(b, th, prec)            # 13 new Om: batches of 8 and 5
+            th = _points(19, seed=100 * k + len(name))  # new Om values for each precision
+            lb, _, sb = ctx.loglike(b, th, prec)            # 19 new Om: batches of 16 and 3
             tb = ctx.terms(b, th, prec)["lnI"]
             la = np.empty_like(lb)
             ta = np.empty_like(tb)
@@ -67,7 +67,7 @@ def test_batched_profiles_equal_one_om_and_oracle(chim, ctx, orc, name, kw, inco
             np.testing.assert_array_equal(tb, ta)
         # 16-bit storage: the oracle reads the stored (decoded) galaxy values
         oc = orc.Catalog(sc.quantize_galaxies(cat, cat["gal_storage"]) if cat.get("gal_storage", 0) else cat)
-        for h in (0, 5, 12):
+        for h in (0, 5, 18):
             ref = oc.loglike(th[h], binned=True)
             assert abs(lb[h] - ref["lnL"]) <= 1e-3, (h, lb[h] - ref["lnL"])
             np.testing.assert_allclose(tb[h], ref["lnI"], rtol=0, atol=1e-4)
@@ -101,7 +101,7 @@ def test_batched_gradient_profiles_equal_one_om(chim, ctx, kde_mode, incomplete)
     cat = sc.config_catalog(2, n_events=5, n_pe=700, n_inj=10000, gal_median=1500, kde_mode=kde_mode)
     if incomplete:
         cat = sc.add_completeness(cat, seed=41, f_R=0.8)
-    th = _points(11, seed=5 + kde_mode + 2 * incomplete)
+    th = _points(19, seed=5 + kde_mode + 2 * incomplete)  # batches of 16 and 3
     a, b = ctx.load(cat), ctx.load(cat)
     try:
         lb, gb, _ = ctx.grad(b, th, chim.MIXED)

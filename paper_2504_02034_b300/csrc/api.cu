@@ -1196,6 +1196,7 @@ void chimera_destroy(chimera_ctx *h) {
     for (auto &e : ctx.ws.tile_ev) cudaEventDestroy(e);
     ctx.ws.tile_ev.clear();
     if (ctx.dev_done) cudaEventDestroy(ctx.dev_done);
+    if (ctx.dev_theta_h) cudaFreeHost(ctx.dev_theta_h);
     cudaStreamSynchronize(ctx.stream);  // the pool's frees are ordered on it
     if (ctx.pool) cudaMemPoolDestroy(ctx.pool);
     cudaStreamDestroy(ctx.stream);
@@ -1271,11 +1272,24 @@ int chimera_loglike_device(chimera_ctx *h, int32_t id, int32_t n, const double *
     if (!cat) { set_error("unknown catalog id"); return CHIMERA_ERR_NOT_FOUND; }
     CK(cudaSetDevice(ctx.device));
     cudaStream_t us = stream ? (cudaStream_t)stream : ctx.stream;
-    std::vector<double> th(12 * (size_t)n);
-    CK(cudaMemcpyAsync(th.data(), theta_dev, sizeof(double) * 12 * n, cudaMemcpyDeviceToHost, us));
+    // theta comes back to the host (the Om caches are looked up there) through
+    // a pinned buffer, a direct DMA instead of a staged pageable copy
+    const size_t nth = 12 * (size_t)n;
+    if (ctx.dev_theta_cap < nth) {
+        if (ctx.dev_theta_h) cudaFreeHost(ctx.dev_theta_h);
+        ctx.dev_theta_h = nullptr;
+        ctx.dev_theta_cap = 0;
+        if (cudaMallocHost((void **)&ctx.dev_theta_h, sizeof(double) * nth) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMallocHost failed for the theta staging buffer");
+            return CHIMERA_ERR_CUDA;
+        }
+        ctx.dev_theta_cap = nth;
+    }
+    CK(cudaMemcpyAsync(ctx.dev_theta_h, theta_dev, sizeof(double) * nth, cudaMemcpyDeviceToHost, us));
     CK(cudaStreamSynchronize(us));
     // the combine kernel writes the caller's buffers directly
-    RC(forward(ctx, *cat, ctx.ws, n, th.data(), prec, lnL_dev, neff_dev, status_dev));
+    RC(forward(ctx, *cat, ctx.ws, n, ctx.dev_theta_h, prec, lnL_dev, neff_dev, status_dev));
     if (!ctx.dev_done) CK(cudaEventCreateWithFlags(&ctx.dev_done, cudaEventDisableTiming));
     CK(cudaEventRecord(ctx.dev_done, ctx.ws.st));
     CK(cudaStreamWaitEvent(us, ctx.dev_done, 0));

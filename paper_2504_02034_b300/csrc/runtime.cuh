@@ -110,6 +110,8 @@ struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t dev_done = nullptr;  // device entry point: the caller's stream waits on it
+    double *dev_theta_h = nullptr;   // device entry point: pinned host copy of theta
+    size_t dev_theta_cap = 0;        // its capacity in doubles
     cudaMemPool_t pool = nullptr;    // cache entries (cache_alloc)
     size_t budget = 0;
     std::atomic<size_t> used{0};

@@ -3,7 +3,7 @@
  * arXiv 2504.02034 (CHIMERA 2.0).  TEST INFRASTRUCTURE ONLY: the product
  * library never links or calls this file; see oracle.h.
  *
- * Readings of the paper that this file fixes (each also listed in the design doc):
+ * Readings of the paper that this file fixes:
  *  - KDE normalisation: mean-weight estimator c * sum_j w_j phi_b, with
  *    c = 1/N_s (single-1D) or 1/N_k (many-1D)            (Eqs. gw-kernel-*)
  *  - bandwidth: Scott's rule with the weighted n_eff, one b per event and

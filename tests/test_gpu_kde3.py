@@ -78,3 +78,31 @@ def test_kde3_is_its_own_kernel_and_rules(chim, ctx, cat3):
     finally:
         ctx.unload(a)
         ctx.unload(b)
+
+
+def test_kde3_degenerate_event(chim, ctx, orc):
+    """An event with three PE samples has no positive-definite covariance
+    over (z, x, y) in either form: its ln I is -inf on both sides, the other
+    events keep their values."""
+    cat = sc.config_catalog(2, n_events=3, n_pe=400, n_inj=8000, gal_median=30, kde_mode=sc.KDE_3D)
+    so = cat["sample_off"]
+    keep = np.ones(int(so[-1]), bool)
+    keep[so[0] + 3:so[1]] = False           # event 0 keeps 3 samples
+    out = dict(cat)
+    counts = np.array([keep[so[e]:so[e + 1]].sum() for e in range(cat["n_events"])])
+    out["sample_off"] = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    for k in ("dL", "m1_det", "m2_det", "pix_of_sample", "sky_xy"):
+        out[k] = np.ascontiguousarray(cat[k][keep])
+    th = sc.config_hyperpoints(2, n=1)
+    oc = orc.Catalog(out)
+    ref = oc.loglike(th[0])
+    cid = ctx.load(out)
+    try:
+        lnI = ctx.terms(cid, th, chim.FP64)["lnI"][0]
+        assert ref["lnI"][0] == -np.inf and lnI[0] == -np.inf
+        np.testing.assert_allclose(lnI[1:], ref["lnI"][1:], rtol=0, atol=1e-7)
+        lnL, _, st = ctx.loglike(cid, th, chim.FP64)
+        assert lnL[0] == -np.inf and ref["lnL"] == -np.inf
+        assert st[0] == ref["status"], (st[0], ref["status"])
+    finally:
+        ctx.unload(cid)

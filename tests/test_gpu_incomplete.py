@@ -129,3 +129,23 @@ def test_incomplete_descriptor_rules(chim, ctx):
     bad["pix_area"][1] = 0.0
     with pytest.raises(chim.ChimeraError):
         ctx.load(bad)
+
+
+def test_empty_catalog_limit_matches_oracle(chim, ctx, orc):
+    """f_R = 0 and P_compl = 0 everywhere: the galaxy term is the homogeneous
+    prior alone (the catalog's galaxies drop out), in FP64 and mixed."""
+    cat = sc.config_catalog(2, n_events=4, n_pe=800, n_inj=10000, gal_median=40)
+    ic = sc.add_completeness(cat, seed=9)
+    ic["completeness"] = np.zeros_like(ic["completeness"])
+    ic["f_R"] = 0.0
+    th = sc.config_hyperpoints(2, n=2)
+    th[1, 1] = 0.33
+    oc = orc.Catalog(ic)
+    cid = ctx.load(ic)
+    try:
+        for prec, ev_tol in ((chim.FP64, 1e-7), (chim.MIXED, 1e-4)):
+            terms = ctx.terms(cid, th, prec)
+            for h in range(th.shape[0]):
+                np.testing.assert_allclose(terms["lnI"][h], oc.loglike(th[h])["lnI"], rtol=0, atol=ev_tol)
+    finally:
+        ctx.unload(cid)

@@ -77,17 +77,20 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_mixed(DevCatalog c, Call
             if (!((k < K.q.kv) || (k == K.q.kv && a.y <= K.q.fv))) continue;
             const float z = chimd::hermite4(__ldg(K.inv + k), a.y);
             if (!(z <= zmax)) continue;
-            const float ap = 1.f + z, lz2 = __log2f(ap), rap = __fdividef(1.f, ap);
+            const float ap = 1.f + z, lz2 = __log2f(ap);
             const float w = mass_weight32(K.q, a.z - lz2, a.w - lz2);
             const float pw = ex2(-K.n * lz2);  // (1+z)^-n
             const float xi = K.xi0 + (1.f - K.xi0) * pw;
-            const float dxi = -K.n * (1.f - K.xi0) * pw * rap;
-            const float Dc = __fdividef(bq.x * rap, xi);  // D_c = d_L / ((1+z) Xi)
+            const float Dc = __fdividef(bq.x, ap * xi);  // D_c = d_L / ((1+z) Xi)
             const float rE = rsqrtf(K.om * ap * ap * ap + 1.f - K.om);
-            const float J = (Dc + ap * K.cH * rE) * xi + ap * Dc * dxi;
-            const float psi = __fdividef(ex2(K.gam * lz2), 1.f + ex2(K.gk * (lz2 - K.l2zp)));
+            // J = (D_c + (1+z) c/H0 / E) Xi + (1+z) D_c dXi/dz, where
+            // (1+z) dXi/dz = -n (1 - Xi0) (1+z)^-n
+            const float J = (Dc + ap * K.cH * rE) * xi - K.n * (1.f - K.xi0) * pw * Dc;
             const float pz = K.k3 * Dc * Dc * rE;
-            const float sv = __fdividef(w * psi * pz * rap * rap * rap, fabsf(J)) * ipi;
+            // s = w psi p_z / ((1+z)^3 |J| pi_inj), psi's denominator folded
+            // into the one division
+            const float psi_num = ex2(K.gam * lz2), psi_den = 1.f + ex2(K.gk * (lz2 - K.l2zp));
+            const float sv = __fdividef(w * psi_num * pz * ipi, ap * ap * ap * fabsf(J) * psi_den);
             s1[hb] += sv;
             s2[hb] = fmaf(sv, sv, s2[hb]);
         }

@@ -62,6 +62,17 @@ namespace {
 using chimd::dcO_hermite;
 constexpr int ADJ_THREADS = 256;
 
+// Transcendentals of the derivative helpers below: libm in FP64, the SFU
+// intrinsics in FP32.  The mixed gradient is held to 2e-3 of the FP64 one,
+// far above the intrinsics' ~1e-6 relative error, and they cost a few
+// instructions instead of tens.
+__device__ __forceinline__ double ax_exp(double x) { return exp(x); }
+__device__ __forceinline__ float ax_exp(float x) { return __expf(x); }
+__device__ __forceinline__ double ax_log(double x) { return log(x); }
+__device__ __forceinline__ float ax_log(float x) { return __logf(x); }
+__device__ __forceinline__ double ax_pow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float ax_pow(float x, float y) { return __powf(x, y); }
+
 // Derivatives of the distance relation at redshift z for one hyperpoint
 // (Eq. dL-mg and its z-derivative J), given Dh = D_c / (c/H0) and
 // DhO = dDh/dOm at z.
@@ -81,7 +92,7 @@ __device__ ZDerT<T> zder_t(T z, T H0, T Om, T Xi0, T n, T Dh, T DhO, T dlpz_zmax
     const T one = T(1), cH = T(C_KMS) / H0, a = one + z;
     const T E = sqrt(Om * a * a * a + one - Om), iE = one / E;
     const T D = cH * Dh, DO = cH * DhO;
-    const T la = log(a), pw = exp(-n * la);
+    const T la = ax_log(a), pw = ax_exp(-n * la);
     const T xi = Xi0 + (one - Xi0) * pw, dxi = -n * (one - Xi0) * pw / a;
     const T P = D + a * cH * iE;  // d d_L^em / dz
     const T J = P * xi + a * D * dxi;
@@ -111,10 +122,10 @@ __device__ ZDer zder(double z, const double *th, const double *fwd, const double
 template <typename T>
 __device__ void dlnpsi_t(T z, T gam, T kap, T zp, T *g3, T *dz) {
     const T one = T(1), a = one + z;
-    const T L = log(a / (one + zp));
-    const T x = exp((gam + kap) * L);
+    const T L = ax_log(a / (one + zp));
+    const T x = ax_exp((gam + kap) * L);
     const T r = x / (one + x);
-    g3[0] = log(a) - r * L;
+    g3[0] = ax_log(a) - r * L;
     g3[1] = -r * L;
     g3[2] = r * (gam + kap) / (one + zp);
     *dz = gam / a - r * (gam + kap) / a;
@@ -139,11 +150,11 @@ __device__ void dlnpm_t(const MassDer<T> &md, T m1, T m2, T a, T *d5, T *ddz) {
     const T one = T(1);
     if (!(m1 >= md.mmin && m1 <= md.mmax && m2 >= md.mmin && m2 <= m1) || !(m1 > md.mmin)) return;
     const T isg = one / md.sg, x = (m1 - md.mu) * isg;
-    const T PL = md.c_pl * pow(m1, -md.alpha), GG = md.c_g * exp(T(-0.5) * x * x);
+    const T PL = md.c_pl * ax_pow(m1, -md.alpha), GG = md.c_g * ax_exp(T(-0.5) * x * x);
     const T p1 = PL + GG;
     if (!(p1 > T(0))) return;
     const T ip1 = one / p1;
-    d5[0] = PL * (md.dlc_pl[0] - log(m1)) * ip1;
+    d5[0] = PL * (md.dlc_pl[0] - ax_log(m1)) * ip1;
     d5[1] = GG * (md.dlc_g[0] + x * isg) * ip1;
     d5[2] = GG * (md.dlc_g[1] + x * x * isg) * ip1;
     d5[3] = (PL * md.dlc_pl[1] + GG * md.dlc_g[2]) * ip1;
@@ -151,15 +162,15 @@ __device__ void dlnpm_t(const MassDer<T> &md, T m1, T m2, T a, T *d5, T *ddz) {
     const T dp1_dm1 = (-md.alpha * PL / m1 - GG * x * isg) * ip1;
     T dp2_dm1, dp2_dm2, dp2_dmin;
     if (fabs(md.b1) < T(1e-6)) {
-        const T L = log(m1 / md.mmin);
+        const T L = ax_log(m1 / md.mmin);
         dp2_dm1 = -one / (m1 * L);
         dp2_dm2 = -one / m2;
         dp2_dmin = one / (md.mmin * L);
     } else {
-        const T q = pow(m1, md.b1) - md.mmin_b1;
-        dp2_dm1 = -md.b1 * pow(m1, md.beta) / q;
+        const T q = ax_pow(m1, md.b1) - md.mmin_b1;
+        dp2_dm1 = -md.b1 * ax_pow(m1, md.beta) / q;
         dp2_dm2 = md.beta / m2;
-        dp2_dmin = md.b1 * pow(md.mmin, md.beta) / q;
+        dp2_dmin = md.b1 * ax_pow(md.mmin, md.beta) / q;
     }
     d5[3] += dp2_dmin;
     *ddz = -(m1 * (dp1_dm1 + dp2_dm1) + m2 * dp2_dm2) / a;
@@ -1083,24 +1094,25 @@ __global__ void __launch_bounds__(ADJ_THREADS, F64 ? 1 : 4) k_select_adj(DevCata
             if (!((k < mp.kv) || (k == mp.kv && a4.y <= mp.fv))) continue;
             const float zz = chimd::hermite4(p.inv32[(size_t)h * NU + k], a4.y);
             if (!(zz <= c.z_max32)) continue;
-            const float a1 = 1.f + zz, lz = log1pf(zz);
+            const float a1 = 1.f + zz, lz = __logf(a1);
             const float lz2 = lz * 1.44269504088896340736f;
-            const float fm1 = exp2f(a4.z - lz2), fm2 = exp2f(a4.w - lz2);
+            const float l1 = a4.z - lz2, l2 = a4.w - lz2;  // log2 of the source masses
+            const float fm1 = ex2(l1), fm2 = ex2(l2);
             const float mmin = hp.mmin32, mmax = hp.mmax32;
             if (!(fm1 >= mmin && fm1 <= mmax && fm2 >= mmin && fm2 <= fm1) || !(fm1 > mmin)) continue;
             const float x = (fm1 - hp.mu32) * hp.inv_sg32;
-            const float p1 = hp.c_pl32 * powf(fm1, -hp.alpha32) + hp.c_g32 * expf(-0.5f * x * x);
-            const float p2 = fabsf(hp.b1_32) < 1e-6f ? 1.f / (fm2 * logf(fm1 / mmin))
-                                                    : hp.b1_32 * powf(fm2, hp.beta32) / (powf(fm1, hp.b1_32) - hp.mmin_b1_32);
-            const float fn = hp.n32, fxi0 = hp.xi0_32, pwz = expf(-fn * lz);
+            const float p1 = hp.c_pl32 * ex2(-hp.alpha32 * l1) + hp.c_g32 * __expf(-0.5f * x * x);
+            const float p2 = fabsf(hp.b1_32) < 1e-6f ? __fdividef(1.f, fm2 * __logf(fm1 / mmin))
+                                                    : __fdividef(hp.b1_32 * ex2(hp.beta32 * l2), ex2(hp.b1_32 * l1) - hp.mmin_b1_32);
+            const float fn = hp.n32, fxi0 = hp.xi0_32, pwz = ex2(-fn * lz2);
             const float xi = fxi0 + (1.f - fxi0) * pwz, dxi = -fn * (1.f - fxi0) * pwz / a1;
             const float Dc = c.i32b[j].x / (a1 * xi);
             const float fom = hp.om32, E = sqrtf(fom * a1 * a1 * a1 + 1.f - fom);
             const float fcH = hp.cH32;
             const float J = (Dc + a1 * fcH / E) * xi + a1 * Dc * dxi;
             const float pz = 3.f * fcH * Dc * Dc / E * hp.inv_dc3_32;
-            const float psi = expf(hp.gam32 * lz) / (1.f + expf((hp.gam32 + hp.kap32) * (lz - hp.l1zp32)));
-            s = T(p1 * p2 * psi * pz / (a1 * a1 * a1 * fabsf(J) * expf(c.i32b[j].y)));
+            const float psi = __fdividef(__expf(hp.gam32 * lz), 1.f + __expf((hp.gam32 + hp.kap32) * (lz - hp.l1zp32)));
+            s = T(__fdividef(p1 * p2 * psi * pz, a1 * a1 * a1 * fabsf(J) * __expf(c.i32b[j].y)));
             const float DhO = dcO_hermite32(q.fwdO[h], zz, fom);
             const ZDerT<float> r32 = zder_t<float>(zz, hp.h0_32, fom, fxi0, fn, Dc / fcH, DhO, hd.dlpz_zmax32);
             r = r32;

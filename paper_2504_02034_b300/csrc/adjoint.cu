@@ -467,13 +467,23 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_event_adj(DevCatalog c, CallPtr
         const int ia0 = a0 < 0.0 ? 0 : (a0 > nz ? nz : (int)a0);
         const int ia1 = aa1 > nz - 1 ? nz - 1 : (aa1 < -1.0 ? -1 : (int)aa1);
         double S0 = 0.0, S1 = 0.0, S2 = 0.0;
-        for (int a = ia0; a <= ia1; a++) {
-            const double Hh = Fw(a) * Gv(row, a);
-            const double u = (a * dz - z) * ib;
-            const double e = exp(-0.5 * u * u) * Hh;
-            S0 += e;
-            S1 += e * u;
-            S2 += e * u * u;
+        if (ia0 <= ia1) {
+            // exp(-u^2/2) along the window by the Gaussian recurrence
+            // g_{a+1} = g_a r_a, r_{a+1} = r_a e^{-delta^2}, delta = dz / b
+            // (two exponentials per sample; relative drift ~1e-14)
+            const double dlt = dz * ib, u0 = (ia0 * dz - z) * ib;
+            double g = exp(-0.5 * u0 * u0), r = exp(-u0 * dlt - 0.5 * dlt * dlt);
+            const double qq = exp(-dlt * dlt);
+            for (int a = ia0; a <= ia1; a++) {
+                const double Hh = Fw(a) * Gv(row, a);
+                const double u = (a * dz - z) * ib;
+                const double e = g * Hh;
+                S0 += e;
+                S1 += e * u;
+                S2 += e * u * u;
+                g *= r;
+                r *= qq;
+            }
         }
         const double pw = pf * w;
         I0 += pw * S0;

@@ -98,13 +98,13 @@ inline __device__ bool invert64(const DevCatalog &c, const CallPtrs &p, int h, c
     double z = (2 * f3 - 3 * f2 + 1) * a.x + (f3 - 2 * f2 + f) * a.y / NU + (-2 * f3 + 3 * f2) * b.x +
                (f3 - f2) * b.y / NU;
     if (!isfinite(z)) return false;
+    // one Newton step: the Hermite seed on the FP64 node pairs is already
+    // good to ~1e-14, and the step brings it to the forward relation's root
     const double *fwd = p.fwd[h];
-    for (int it = 0; it < 2; it++) {
-        double dd, J;
-        chimd::dgw_J(z, hp.cH * chimd::dc_hermite(fwd, z, hp.th[1]), hp.th, hp.cH, &dd, &J);
-        double step = (dd - d) / J;
-        if (isfinite(step)) z -= step;
-    }
+    double dd, J;
+    chimd::dgw_J(z, hp.cH * chimd::dc_hermite(fwd, z, hp.th[1]), hp.th, hp.cH, &dd, &J);
+    const double step = (dd - d) / J;
+    if (isfinite(step)) z -= step;
     *zout = z;
     return true;
 }

@@ -340,8 +340,10 @@ int chimera_kde_pairs(chimera_ctx *ctx, int32_t catalog_id, int32_t n_points, co
                       int64_t *pairs);
 
 /*
- * chimera_selection_static: the selection term xi and N_eff (same FP64
- * arithmetic as the catalog path) for callers that cannot allocate device
+ * chimera_selection_static: the selection term xi and N_eff (the FP64
+ * arithmetic of the catalog path, with the inverse distance table spanning
+ * the injections alone, so the results agree with the catalog path to
+ * ~1e-10 relative rather than bit for bit) for callers that cannot allocate device
  * memory, e.g. code whose memory pool owns the whole device, code that must
  * stay inside another framework's allocator, or loops that must not let
  * cudaMalloc / cudaFree synchronise the device.  The paper has no
@@ -362,7 +364,8 @@ int chimera_kde_pairs(chimera_ctx *ctx, int32_t catalog_id, int32_t n_points, co
  * should come before any stream capture; it also reads the largest d_L back
  * to the host, so every call synchronises `stream` once.  Calls share the
  * array: calls that overlap on the GPU race and must be serialised by the
- * caller.  Errors: INVALID_ARG, UNSUPPORTED, CUDA.
+ * caller.  Errors: INVALID_ARG (also when inj_dL holds no positive finite
+ * distance), UNSUPPORTED, CUDA.
  */
 int chimera_selection_static(int32_t n_points, const double *theta, int64_t n_det,
                              int64_t n_inj_total, const double *inj_dL, const double *inj_m1d,

@@ -336,13 +336,26 @@ def chimera_selection_static(theta, inj, n_inj_total, lambda_g, beta, z_max, xi_
     [n_points] written on `stream` (torch stream or None = current)."""
     import torch
     t = _th(theta)
-    s = stream if stream is not None else torch.cuda.current_stream(xi_t.device)
-    sh = s.cuda_stream if s.cuda_stream != 0 else 0x1
+    dev = xi_t.device
+    n = int(inj["dL"].numel())
+    for name in ("dL", "m1d", "m2d", "log_pi"):
+        x = inj[name]
+        if x.dtype != torch.float64 or not x.is_contiguous() or x.device != dev or x.numel() != n:
+            raise ValueError("inj[%r] must be a contiguous float64 tensor of %d elements on %s"
+                             % (name, n, dev))
+    for name, x in (("xi_t", xi_t), ("neff_t", neff_t)):
+        if x.dtype != torch.float64 or not x.is_contiguous() or x.device != dev or x.numel() < t.shape[0]:
+            raise ValueError("%s must be a contiguous float64 tensor of >= %d elements on %s"
+                             % (name, t.shape[0], dev))
     ptr = lambda x: C.c_void_p(x.data_ptr())
-    _ck(lib().chimera_selection_static(t.shape[0], _dp(t), int(inj["dL"].numel()), int(n_inj_total),
-                                       ptr(inj["dL"]), ptr(inj["m1d"]), ptr(inj["m2d"]), ptr(inj["log_pi"]),
-                                       float(lambda_g), float(beta), float(z_max), ptr(xi_t), ptr(neff_t),
-                                       C.c_void_p(sh)), "chimera_selection_static")
+    # the C call runs on the calling thread's current device: make it the outputs' one
+    with torch.cuda.device(dev):
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        sh = s.cuda_stream if s.cuda_stream != 0 else 0x1
+        _ck(lib().chimera_selection_static(t.shape[0], _dp(t), n, int(n_inj_total),
+                                           ptr(inj["dL"]), ptr(inj["m1d"]), ptr(inj["m2d"]), ptr(inj["log_pi"]),
+                                           float(lambda_g), float(beta), float(z_max), ptr(xi_t), ptr(neff_t),
+                                           C.c_void_p(sh)), "chimera_selection_static")
 
 
 def chimera_strerror(code):

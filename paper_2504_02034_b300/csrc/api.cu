@@ -144,6 +144,7 @@ CallPtrs Workspace::ptrs(int H, const DevCatalog &c) const {
     p.hp = hp;
     p.inv64 = inv64;
     p.inv32 = inv32;
+    p.linv32 = linv32;
     p.F64 = F64;
     p.F32 = F32;
     p.lnI = lnI;
@@ -216,6 +217,7 @@ int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat) {
         {(void **)&ws.hp, sizeof(HP) * Hn},
         {(void **)&ws.inv64, sizeof(double2) * (size_t)Hn * (NU + 1)},
         {(void **)&ws.inv32, sizeof(float4) * (size_t)Hn * NU},
+        {(void **)&ws.linv32, sizeof(float4) * (size_t)Hn * NU},
         {(void **)&ws.F64, sizeof(double) * (size_t)Hn * nz},
         {(void **)&ws.F32, sizeof(float) * (size_t)Hn * nz},
         {(void **)&ws.lnI, sizeof(double) * (size_t)Hn * nev},
@@ -453,15 +455,6 @@ static int profile(Ctx &ctx, Catalog &cat, Workspace &ws, double Om, int kind, c
 }
 
 // ----------------------------------------------------------- forward ----
-static const double kSafeTheta[12] = {70.0, 0.3, 1.0, 1.91, 3.4, 34.0, 3.6, 5.0, 100.0, 2.7, 3.0, 2.0};
-
-static bool admissible(const double *t) {
-    for (int k = 0; k < 12; k++)
-        if (!std::isfinite(t[k])) return false;
-    return t[0] > 0.0 && t[1] >= 0.0 && t[1] <= 1.0 && t[2] > 0.0 && t[6] > 0.0 && t[7] > 0.0 &&
-           t[8] > t[7] && t[11] > -1.0;
-}
-
 int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, int precision,
             double *out_lnL, double *out_neff, int32_t *out_status) {
     const bool epan = (precision & CHIMERA_KERNEL_EPANECHNIKOV) != 0;
@@ -492,7 +485,7 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
     memset(st, 0, 8 * (size_t)H);
     for (int h = 0; h < H; h++) {
         const double *t = theta + 12 * h;
-        bool ok = admissible(t);
+        bool ok = theta_admissible(t);
         memcpy(th + 12 * h, ok ? t : kSafeTheta, sizeof(double) * 12);
         st[h] = ok ? 0 : CHIMERA_PT_OUT_OF_SUPPORT;
     }
@@ -530,7 +523,7 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
     p.kshape = epan ? 1 : 0;
     p.jac_ps = jac_ps ? 1 : 0;
     if (p.pairs) CK(cudaMemsetAsync(p.pairs, 0, sizeof(unsigned long long) * H, ws.st));
-    launch_hyper_tables(c, p, H, precision == CHIMERA_FP64, for_grad, ws.dk, ws.fmax_bits, ws.st);
+    launch_hyper_tables(c, p, H, precision == CHIMERA_FP64, ws.dk, ws.fmax_bits, ws.st);
     if (ws.trace) CK(cudaEventRecord(ws.tev[2], ws.st));
     // the selection term needs only the per-point tables: it runs on a side
     // stream of the lowest priority beside the event kernels, whose blocks
@@ -692,6 +685,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     c.dz = d->z_max / (d->n_z - 1);
     c.z_max32 = (float)c.z_max;
     c.dz32 = (float)c.dz;
+    c.dz_lo32 = (float)(c.dz - (double)c.dz32);
     c.n_gal_total = d->n_gal_total;
     c.lambda_g = d->lambda_g;
     c.beta = d->beta;
@@ -715,6 +709,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         });
     }
     std::vector<float4> s32(ns);
+    std::vector<float2> s32lo(ns);
     std::vector<double> sd(ns), sm1(ns), sm2(ns);
     auto tcoord = [&](double dl, int &k, float &f) {
         double t = std::sqrt(dl / c.d_top) * NU;
@@ -729,7 +724,9 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         tcoord(d->dL_Mpc[o], k, f);
         float kb;
         memcpy(&kb, &k, 4);
-        s32[j] = make_float4(kb, f, (float)std::log2(d->m1_det[o]), (float)std::log2(d->m2_det[o]));
+        const double l1 = std::log2(d->m1_det[o]), l2 = std::log2(d->m2_det[o]);
+        s32[j] = make_float4(kb, f, (float)l1, (float)l2);
+        s32lo[j] = make_float2((float)(l1 - (double)(float)l1), (float)(l2 - (double)(float)l2));
         sd[j] = d->dL_Mpc[o];
         sm1[j] = d->m1_det[o];
         sm2[j] = d->m2_det[o];
@@ -899,14 +896,33 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     // ---- injections
     const int64_t nd = d->n_det;
     std::vector<float4> i32a(nd);
+    std::vector<float2> i32lo(nd);
     std::vector<float2> i32b(nd);
+    std::vector<float> iipi(nd);
+    // 1 / pi_inj for the mixed selection, in FP64 and rounded once, scaled
+    // by 2^-K with K the middle of the catalog's range of -log2 pi_inj so
+    // that every value fits the float range; K ln 2 is carried in FP64
+    {
+        double lo = 0.0, hi = 0.0;
+        for (int64_t j = 0; j < nd; j++) {
+            const double l2 = -d->inj_log_pi[j] * 1.4426950408889634074;
+            lo = j ? std::min(lo, l2) : l2;
+            hi = j ? std::max(hi, l2) : l2;
+        }
+        const double K = std::floor(0.5 * (lo + hi));
+        c.ln_ipi_shift = K * 0.69314718055994530942;
+        for (int64_t j = 0; j < nd; j++)
+            iipi[j] = (float)std::exp2(-d->inj_log_pi[j] * 1.4426950408889634074 - K);
+    }
     for (int64_t j = 0; j < nd; j++) {
         int k;
         float f;
         tcoord(d->inj_dL[j], k, f);
         float kb;
         memcpy(&kb, &k, 4);
-        i32a[j] = make_float4(kb, f, (float)std::log2(d->inj_m1d[j]), (float)std::log2(d->inj_m2d[j]));
+        const double l1 = std::log2(d->inj_m1d[j]), l2 = std::log2(d->inj_m2d[j]);
+        i32a[j] = make_float4(kb, f, (float)l1, (float)l2);
+        i32lo[j] = make_float2((float)(l1 - (double)(float)l1), (float)(l2 - (double)(float)l2));
         i32b[j] = make_float2((float)d->inj_dL[j], (float)d->inj_log_pi[j]);
     }
     std::vector<int64_t> ev_soff(d->sample_off, d->sample_off + ne + 1);
@@ -990,6 +1006,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         {(void **)&c.gz64, gz.data(), 8 * gz.size()},
         {(void **)&c.gs64, gs.data(), 8 * gs.size()},
         {(void **)&c.s32, s32.data(), 16 * s32.size()},
+        {(void **)&c.s32lo, s32lo.data(), 8 * s32lo.size()},
         {(void **)&c.sd64, sd.data(), 8 * sd.size()},
         {(void **)&c.sm1_64, sm1.data(), 8 * sm1.size()},
         {(void **)&c.sm2_64, sm2.data(), 8 * sm2.size()},
@@ -998,7 +1015,9 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
                            d->inj_dL ? d->inj_dL + nd : (const double *)nullptr);
     if (nd > 0) {
         ups.push_back({(void **)&c.i32a, i32a.data(), 16 * (size_t)nd});
+        ups.push_back({(void **)&c.i32lo, i32lo.data(), 8 * (size_t)nd});
         ups.push_back({(void **)&c.i32b, i32b.data(), 8 * (size_t)nd});
+        ups.push_back({(void **)&c.iipi32, iipi.data(), 4 * (size_t)nd});
         ups.push_back({(void **)&c.id64, d->inj_dL, 8 * (size_t)nd});
         ups.push_back({(void **)&c.im1_64, d->inj_m1d, 8 * (size_t)nd});
         ups.push_back({(void **)&c.im2_64, d->inj_m2d, 8 * (size_t)nd});

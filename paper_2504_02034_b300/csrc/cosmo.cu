@@ -17,6 +17,7 @@
 #include <math_constants.h>
 
 #include "internal.cuh"
+#include "mass.cuh"
 
 namespace chim {
 
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(1024) k_fwd_offsets(FwdBatch b) {
 
 constexpr int HYP_THREADS = 256;
 
+
 __device__ double std_normal_cdf(double x) { return 0.5 * erfc(-x * 0.70710678118654752440); }
 
 // FP32 forward relation at z from D = D_c [Mpc]: d_L^gw and its z-derivative J.
@@ -104,18 +106,53 @@ __device__ __forceinline__ void dgw_J32(float z, float D, float cH, float om, fl
     J = (D + a * cH / E) * xi + a * D * dxi;
 }
 
-// D_c/(c/H0) by cubic Hermite on the forward table, in FP32.
-__device__ __forceinline__ float dc_hermite32(const double *fwd, float z, float om) {
+// The mixed path's FP32 forward relation for the grid factor: the
+// hyperpoint's constants as float pairs (built once per block in FP64), so
+// that F carries only errors that differ from point to point of the grid (a
+// constant rounded to float would scale every event integral of the
+// hyperpoint alike).
+struct FwdC32 {
+    F2 cH;              // c / H0 [Mpc]
+    F2 xi0, omx;        // Xi0, 1 - Xi0
+    F2 nn, nomx;        // -n, n (1 - Xi0)
+    F2 om, omc;         // Om, 1 - Om
+    F2 gam, gkp, l2zp;  // gamma, gamma + kappa, log2(1 + z_p)
+};
+__device__ FwdC32 fwd_consts32(const double *th) {
+    FwdC32 k;
+    k.cH = split_f2(C_KMS / th[0]);
+    k.xi0 = split_f2(th[2]);
+    k.omx = split_f2(1.0 - th[2]);
+    k.nn = split_f2(-th[3]);
+    k.nomx = split_f2(th[3] * (1.0 - th[2]));
+    k.om = split_f2(th[1]);
+    k.omc = split_f2(1.0 - th[1]);
+    k.gam = split_f2(th[9]);
+    k.gkp = split_f2(th[9] + th[10]);
+    k.l2zp = split_f2(log1p(th[11]) * 1.4426950408889634074);
+    return k;
+}
+__device__ __forceinline__ float E32p(const FwdC32 &k, float a) {
+    const float a3 = a * a * a;
+    return sqrtf(fmaf(k.om.hi, a3, k.omc.hi) + fmaf(k.om.lo, a3, k.omc.lo));
+}
+// Dhat = D_c H0 / c by cubic Hermite on the FP64 forward table (node values
+// rounded to float, slopes 1/E with the pair constants).
+__device__ __forceinline__ float dc_hermite32p(const double *fwd, float z, const FwdC32 &kc) {
     const float ht = (float)HT;
-    const float t = z / ht;
+    const float t = z * (1.f / (float)HT);  // HT is a power of two: exact
     const int k = min(max((int)floorf(t), 0), NT_FWD - 2);
     const float f = t - k, f2 = f * f, f3 = f2 * f;
-    auto slope = [om, ht](float zz) {
-        const float aa = 1.f + zz;
-        return ht / sqrtf(om * aa * aa * aa + 1.f - om);
-    };
-    return (2.f * f3 - 3.f * f2 + 1.f) * (float)fwd[k] + (f3 - 2.f * f2 + f) * slope(k * ht) +
-           (-2.f * f3 + 3.f * f2) * (float)fwd[k + 1] + (f3 - f2) * slope((k + 1) * ht);
+    return (2.f * f3 - 3.f * f2 + 1.f) * (float)fwd[k] + (f3 - 2.f * f2 + f) * (ht / E32p(kc, 1.f + k * ht)) +
+           (-2.f * f3 + 3.f * f2) * (float)fwd[k + 1] + (f3 - f2) * (ht / E32p(kc, 1.f + (k + 1) * ht));
+}
+// At z (lz = log2(1+z)) from Dhat: pw = (1+z)^-n, Xi, and Jh = J H0 / c =
+// (Dhat + (1+z)/E) Xi - n (1 - Xi0) (1+z)^-n Dhat.
+__device__ __forceinline__ void fwd32p(const FwdC32 &k, float z, float lz, float Dh, float &xi, float &Jh) {
+    const float a = 1.f + z;
+    const float pw = ex2_mul_n(k.nn, lz);
+    xi = fmaf(k.omx.hi, pw, k.xi0.hi) + fmaf(k.omx.lo, pw, k.xi0.lo);
+    Jh = (Dh + a / E32p(k, a)) * xi - mul_f2(k.nomx, pw) * Dh;
 }
 
 // K1b.1, one launch for two independent parts per hyperpoint (blockIdx.y):
@@ -141,6 +178,9 @@ __global__ void __launch_bounds__(HYP_THREADS) k_nodes_grid(DevCatalog c, CallPt
         if (k <= K_Z10 && !(J > 0.f)) atomicOr(p.status + h, CHIMERA_PT_NONMONOTONE);
         return;
     }
+    __shared__ FwdC32 kc;
+    if (!f64 && threadIdx.x == 0) kc = fwd_consts32(th);
+    __syncthreads();
     const int a = (blockIdx.x - nbn) * HYP_THREADS + threadIdx.x;
     unsigned long long bits = 0;
     if (a < c.n_z) {
@@ -153,14 +193,19 @@ __global__ void __launch_bounds__(HYP_THREADS) k_nodes_grid(DevCatalog c, CallPt
             p.F64[(size_t)h * c.n_z + a] = F;
             bits = (unsigned long long)__double_as_longlong(F);
         } else {
-            const float z = a * c.dz32, om = (float)th[1];
-            const float Dh = dc_hermite32(fwd, z, om);
-            float d, J;
-            dgw_J32(z, (float)cH * Dh, (float)cH, om, (float)th[2], (float)th[3], d, J);
-            const float ap = 1.f + z, l2a = log2f(ap);
-            const float gam = (float)th[9], gk = (float)(th[9] + th[10]);
-            const float psi = exp2f(gam * l2a) / (1.f + exp2f(gk * (l2a - (float)log2(1.0 + th[11]))));
-            float F = p.jac_ps ? psi : psi / (ap * ap * ap * fabsf(J));
+            // mixed: F' = F c / H0 = psi / ((1+z)^3 |J H0/c|) in FP32 with the
+            // pair constants (H0 / c goes into the FP64 log offset ln_k0);
+            // psi alone with the Jacobian on the samples
+            const float z = (float)(a * c.dz), ap = 1.f + z;
+            const F2 l2e{L2E_HI, L2E_LO};
+            const float lz = mul_f2(l2e, log1pf(z));
+            const float psi = ex2_mul_n(kc.gam, lz) / (1.f + ex2_mul(kc.gkp, (lz - kc.l2zp.hi) - kc.l2zp.lo));
+            float F = psi;
+            if (!p.jac_ps) {
+                float xi, Jh;
+                fwd32p(kc, z, lz, dc_hermite32p(fwd, z, kc), xi, Jh);
+                F = psi / (ap * ap * ap * fabsf(Jh));
+            }
             if (!isfinite(F)) F = 0.f;
             p.F32[(size_t)h * c.n_z + a] = F;
             bits = (unsigned long long)__float_as_uint(F);
@@ -173,18 +218,20 @@ __global__ void __launch_bounds__(HYP_THREADS) k_nodes_grid(DevCatalog c, CallPt
 
 // K1b.2: inverse nodes z(u_k), d = d_top u_k^2: bracketing on the forward
 // nodes (staged in shared memory), cubic Hermite of z(d) between the two
-// bracketing nodes (slopes 1/J), then one Newton step on the
-// Hermite-interpolated forward relation: in FP32 for the FP32 node pairs
-// (inv32, all the mixed forward path reads), and with NODES64 also in FP64
-// for the FP64 nodes (inv64: the FP64 path and the adjoint).  The FP32 pairs
-// do not depend on NODES64, so a mixed ln L is the same with or without a
-// gradient.  A block computes the nodes base .. base+INV_THREADS (one more
-// than it owns) so that it also writes the FP32 pairs of its intervals.
+// bracketing nodes (slopes 1/J), then one FP64 Newton step on the Hermite-
+// interpolated forward relation.  The FP64 nodes (inv64) serve the FP64
+// path and the adjoint; the FP32 node pairs that the mixed kernels
+// interpolate (inv32) are those nodes rounded, and beside them go the pairs
+// of log2(1+z) (linv32), which the mixed kernels interpolate in place of a
+// log per sample.  (Measured on the benchmark catalogs: FP32 Newton nodes,
+// even with the hyperpoint's constants as float pairs, shift every event of
+// a hyperpoint by up to 1e-7 in ln I alike; the rounded FP64 nodes do not.)
+// A block computes the nodes base .. base+INV_THREADS (one more than it
+// owns) so that it also writes the FP32 pairs of its intervals.
 constexpr int INV_THREADS = 128;  // 2049 nodes x H spread over every SM
-template <bool NODES64>
 __global__ void __launch_bounds__(INV_THREADS) k_inv_nodes(DevCatalog c, CallPtrs p, const float2 *djall) {
     __shared__ float sdk[NT_FWD];
-    __shared__ float2 snd32[INV_THREADS + 1];
+    __shared__ float4 snd32[INV_THREADS + 1];  // z, dz/du, lz, dlz/du
     const int h = blockIdx.y;
     const int base = blockIdx.x * INV_THREADS;
     const float2 *dj = djall + (size_t)h * NT_FWD;
@@ -194,19 +241,16 @@ __global__ void __launch_bounds__(INV_THREADS) k_inv_nodes(DevCatalog c, CallPtr
     const double *fwd = p.fwd[h];
     const double cH = C_KMS / th[0], Om = th[1];
     const double dtop = c.d_top;
-    const float cH32 = (float)cH, om32 = (float)Om, xi32 = (float)th[2], n32 = (float)th[3];
+    const F2 l2e{L2E_HI, L2E_LO};
     for (int t = threadIdx.x; t <= INV_THREADS; t += INV_THREADS) {
         const int k = base + t;
         if (k > NU) break;
         const double u = (double)k / NU, d = dtop * u * u;
         double z = 0.0, dzdu = 0.0;
-        float z32 = 0.f, dzdu32 = 0.f;
         if (k > 0) {
             if (!(d <= (double)sdk[NT_FWD - 1])) {
                 z = CUDART_NAN;
                 dzdu = CUDART_NAN;
-                z32 = CUDART_NAN_F;
-                dzdu32 = CUDART_NAN_F;
             } else {
                 int lo = 0, hi = NT_FWD - 1;  // sdk[lo] <= d < sdk[hi]
                 while (hi - lo > 1) {
@@ -216,35 +260,29 @@ __global__ void __launch_bounds__(INV_THREADS) k_inv_nodes(DevCatalog c, CallPtr
                 const double dl = sdk[lo], dh = sdk[hi], den = dh - dl;
                 const double tt = den > 0.0 ? (d - dl) / den : 0.0;
                 const double t2 = tt * tt, t3 = t2 * tt;
-                const double z0 = (2 * t3 - 3 * t2 + 1) * (lo * HT) + (t3 - 2 * t2 + tt) * den / (double)dj[lo].y +
-                                  (-2 * t3 + 3 * t2) * (hi * HT) + (t3 - t2) * den / (double)dj[hi].y;
-                {  // FP32 Newton step from the seed
-                    const float zs = (float)z0, d32 = (float)d;
-                    float dd, J;
-                    dgw_J32(zs, cH32 * dc_hermite32(fwd, zs, om32), cH32, om32, xi32, n32, dd, J);
-                    const float step = (dd - d32) / J;
-                    z32 = isfinite(step) ? zs - step : zs;
-                    dzdu32 = 2.f * (float)u * (float)dtop / J;
-                }
-                if (NODES64) {
-                    z = z0;
-                    double dd, J;
-                    chimd::dgw_J(z, cH * chimd::dc_hermite(fwd, z, Om), th, cH, &dd, &J);
-                    const double step = (dd - d) / J;
-                    if (isfinite(step)) z -= step;
-                    dzdu = 2.0 * u * dtop / J;
-                }
+                z = (2 * t3 - 3 * t2 + 1) * (lo * HT) + (t3 - 2 * t2 + tt) * den / (double)dj[lo].y +
+                    (-2 * t3 + 3 * t2) * (hi * HT) + (t3 - t2) * den / (double)dj[hi].y;
+                double dd, J;
+                chimd::dgw_J(z, cH * chimd::dc_hermite(fwd, z, Om), th, cH, &dd, &J);
+                const double step = (dd - d) / J;
+                if (isfinite(step)) z -= step;
+                dzdu = 2.0 * u * dtop / J;
             }
         }
-        snd32[t] = make_float2(z32, dzdu32);
-        if (NODES64 && (t < INV_THREADS || k == NU)) p.inv64[(size_t)h * (NU + 1) + k] = make_double2(z, dzdu);
+        const float z32 = (float)z, dzdu32 = (float)dzdu;
+        // log2(1+z) and its u-derivative at the node
+        const float lzn = mul_f2(l2e, log1pf(z32));
+        const float dlz = dzdu32 * L2E_HI / (1.f + z32);
+        snd32[t] = make_float4(z32, dzdu32, lzn, dlz);
+        if (t < INV_THREADS || k == NU) p.inv64[(size_t)h * (NU + 1) + k] = make_double2(z, dzdu);
     }
     __syncthreads();
     const int k = base + threadIdx.x;
     if (k < NU) {
         const float inv_nu = 1.f / NU;  // exact: NU is a power of two
-        const float2 a = snd32[threadIdx.x], b = snd32[threadIdx.x + 1];
+        const float4 a = snd32[threadIdx.x], b = snd32[threadIdx.x + 1];
         p.inv32[(size_t)h * NU + k] = make_float4(a.x, a.y * inv_nu, b.x, b.y * inv_nu);
+        if (p.linv32) p.linv32[(size_t)h * NU + k] = make_float4(a.z, a.w * inv_nu, b.z, b.w * inv_nu);
     }
 }
 
@@ -255,7 +293,11 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
     const int h = blockIdx.y, t = threadIdx.x;
     const double Fm = f64 ? __longlong_as_double((long long)fmax_bits[h])
                           : (double)__uint_as_float((unsigned)fmax_bits[h]);
-    const double Fs = Fm > 0.0 ? Fm : 1.0;
+    // F_scale: the power of two just above the maximum, so that F / F_scale
+    // in FP32 is exact (no rounded scale shared by every grid point)
+    int fe = 0;
+    if (Fm > 0.0) frexp(Fm, &fe);
+    const double Fs = Fm > 0.0 ? ldexp(1.0, fe) : 1.0;
     if (!f64) {
         const float iFs = (float)(1.0 / Fs);
         const int a = blockIdx.x * HYP_THREADS + t;
@@ -298,7 +340,9 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
                 v = log2(mmax);
                 // ln of the constant factor of the mixed path's raw event
                 // integral: dz F_scale / (N_gal,tot sqrt(2 pi)), times 1/b per event
-                sc[11] = log(c.dz * Fs / (c.n_gal_total * 2.50662827463100050242));
+                // (the mixed F32 holds F c / H0 unless the Jacobian sits on the samples)
+                sc[11] = log(c.dz * Fs / (c.n_gal_total * 2.50662827463100050242)) -
+                         (p.jac_ps ? 0.0 : log(cH));
                 break;
         }
         sc[w] = v;
@@ -326,7 +370,37 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
             hp.k_valid = (int)floor(tv);
             hp.f_valid = (float)(tv - hp.k_valid);
         }
-        hp.ln_k0 = sc[11];
+        // the mixed path's mass model relative to its shared normalisation
+        const bool logp2 = fabs(hp.b1) < 1e-12;
+        double C1 = hp.c_pl > 0.0 ? hp.c_pl : hp.c_g;
+        if (!(C1 > 0.0)) C1 = 1.0;
+        const double mmin_a = pow(mmin, alpha);  // m_min^alpha
+        const double wscale = C1 / (mmin_a * mmin) * (logp2 ? 1.4426950408889634074 : fabs(hp.b1));
+        hp.ln_wscale = log(wscale);
+        hp.inv_wscale = 1.0 / wscale;
+        hp.ln_k0 = sc[11] + hp.ln_wscale;
+        // s_j = w_scale (3 / Dhat(z_max)^3) (H0 / c) x the mixed selection
+        // kernel's relative term (Dhat = D_c H0 / c)
+        hp.ln_sel = hp.ln_wscale + log(3.0 / (sc[3] * sc[3] * sc[3])) + log(th[0] / C_KMS);
+        hp.r_pl32 = (float)(hp.c_pl / C1);
+        hp.r_g32 = (float)(hp.c_g / C1 * mmin_a);
+        hp.na2 = split_f2(-alpha);
+        hp.gk2 = split_f2(-0.72134752044448170368 / (sg * sg));
+        hp.beta2 = split_f2(beta);
+        hp.b1_2 = split_f2(hp.b1);
+        hp.l2min2 = split_f2(sc[6]);
+        hp.l2max2 = split_f2(sc[7]);
+        hp.b1ln2_2 = split_f2(hp.b1 * 0.69314718055994530942);
+        hp.kH2 = split_f2(th[0] / C_KMS);
+        hp.xi0_2 = split_f2(th[2]);
+        hp.omx2 = split_f2(1.0 - th[2]);
+        hp.nn2 = split_f2(-th[3]);
+        hp.nomx2 = split_f2(th[3] * (1.0 - th[2]));
+        hp.om2 = split_f2(th[1]);
+        hp.omc2 = split_f2(1.0 - th[1]);
+        hp.gam2 = split_f2(th[9]);
+        hp.gk_psi2 = split_f2(th[9] + th[10]);
+        hp.l2zp2 = split_f2(sc[9] * 1.4426950408889634074);
         hp.status = p.status[h];
         hp.c_pl32 = (float)hp.c_pl;
         hp.c_g32 = (float)hp.c_g;
@@ -372,7 +446,7 @@ void launch_fwd_table(double Om, double *out, cudaStream_t st) {
     launch_fwd_tables(b, false, st);
 }
 
-void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, bool nodes64, double *dk,
+void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, double *dk,
                          unsigned long long *fmax_bits, cudaStream_t st) {
     float2 *dj = reinterpret_cast<float2 *>(dk);  // (d, J) of the forward nodes, FP32
     cudaMemsetAsync(fmax_bits, 0, sizeof(unsigned long long) * H, st);
@@ -380,8 +454,7 @@ void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp6
     const int nbg = (c.n_z + HYP_THREADS - 1) / HYP_THREADS;
     k_nodes_grid<<<dim3(nbn + nbg, H), HYP_THREADS, 0, st>>>(c, p, dj, fmax_bits, nbn, fp64);
     const dim3 gi((NU + INV_THREADS - 1) / INV_THREADS, H);
-    if (fp64 || nodes64) k_inv_nodes<true><<<gi, INV_THREADS, 0, st>>>(c, p, dj);
-    else k_inv_nodes<false><<<gi, INV_THREADS, 0, st>>>(c, p, dj);
+    k_inv_nodes<<<gi, INV_THREADS, 0, st>>>(c, p, dj);
     k_hyper_final<<<dim3(fp64 ? 1 : nbg, H), HYP_THREADS, 0, st>>>(c, p, fmax_bits, fp64);
 }
 

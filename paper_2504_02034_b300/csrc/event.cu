@@ -143,14 +143,18 @@ struct MixLayout {
 // before the chains, so a sample holds five registers through the loop.
 template <int R>
 __device__ __forceinline__ float union_samples(const float *D, int nq, const float *z, const float *w, int cnt,
-                                               int lane, float zo, float inv_s2b, float ds, float lnscale) {
+                                               int lane, float zo, float inv_s2b, float ds, float iscale) {
     float cw[R], B[R], Bi[R], af[R], ab[R];
 #pragma unroll
     for (int r = 0; r < R; r++) {
         const int j = lane + 32 * r;
         const bool in = j < cnt;
         const float u = in ? (z[j] - zo) * inv_s2b : 0.f;
-        cw[r] = in ? w[j] * __expf(-u * u - lnscale) : 0.f;
+        // iscale: 1 or 2^-29, exact (it undoes the table's power-of-two scale)
+        // SFU exponentials here: measured on the benchmark catalogs, the
+        // accurate expc gave no smaller shared error at this spot (the per-
+        // sample factors' errors differ between samples) and cost 6 % of K4
+        cw[r] = in ? w[j] * (__expf(-u * u) * iscale) : 0.f;
         B[r] = __expf(2.f * u * ds);
         Bi[r] = __expf(-2.f * u * ds);
         af[r] = 0.f;
@@ -216,18 +220,18 @@ __device__ __forceinline__ void stage_table4(float *D, int nq, int a_first, int 
 // exponential per pair); cheaper than a table for so few samples.
 constexpr int SMALL_CNT = 12;  // measured: 12 beats 6, 16 and 24 on the 300-event catalog
 __device__ __forceinline__ float small_group(const float *z, const float *w, int cnt, int A0, int A1,
-                                             const float *G, const float *Fs, float dz, float inv_s2b,
-                                             float halfk, int lane) {
+                                             const float *G, const float *Fs, float dz, float dz_lo,
+                                             float inv_s2b, float halfk, int lane) {
     float acc = 0.f;
 #pragma unroll 2
     for (int a = A0 + lane; a <= A1; a += 32) {
-        const float za = a * dz;
+        const float za = fmaf((float)a, dz, (float)a * dz_lo);
         const float h = Fs[a] * __ldg(G + a);
         float k = 0.f;
         for (int j = 0; j < cnt; j++) {
             const float d = za - z[j];
             const float x = d * inv_s2b;
-            const float e = ex2(-1.44269504088896340736f * x * x);
+            const float e = expc(-x * x);
             k = fabsf(d) <= halfk ? fmaf(w[j], e, k) : k;
         }
         acc = fmaf(k, h, acc);
@@ -295,8 +299,8 @@ __device__ __forceinline__ void stage_table(float *D, int len, int a_first, int 
 // exp(-u^2) B^t C_t with |u| <= ds/2, as two Horner chains in B and 1/B
 // over the group's H' (staged with zero padding, so no bounds tests).
 __device__ __forceinline__ float lane_chain(const float *Hc, const float *CT, int Tw, float z,
-                                            int ts, float dz, float inv_s2b, float ds) {
-    const float u = (z - ts * dz) * inv_s2b;
+                                            int ts, float dz, float dz_lo, float inv_s2b, float ds) {
+    const float u = (z - fmaf((float)ts, dz, (float)ts * dz_lo)) * inv_s2b;
     const float A = __expf(-u * u), B = __expf(2.f * u * ds), Bi = __expf(-2.f * u * ds);
     float af = CT[Tw] * Hc[Tw], ab = CT[Tw + 1] * Hc[-Tw - 1];
 #pragma unroll 2
@@ -314,6 +318,17 @@ __device__ __forceinline__ float lane_chain(const float *Hc, const float *CT, in
 // the event's median d_L give the FP32 Scott bandwidth.  Many small blocks
 // keep the SMs full while the loads of the inverse-table nodes are in flight.
 constexpr int RW_THREADS = 256;
+#ifndef CHIM_RW_INFLIGHT
+#define CHIM_RW_INFLIGHT 2
+#endif
+#ifndef CHIM_RW_MINB
+#define CHIM_RW_MINB 3
+#endif
+#ifndef CHIM_RW_SMEMQ
+#define CHIM_RW_SMEMQ 0
+#endif
+constexpr int RW_INFLIGHT = CHIM_RW_INFLIGHT;  // samples per thread in flight
+constexpr int RW_MINB = CHIM_RW_MINB;          // resident blocks per SM asked of the compiler
 // 1 / [(1+z)^3 |d d_L^gw/dz|] at a sample (Eq. jacobian), FP32, from its
 // d_L (D_c = d_L / ((1+z) Xi)) and lz = log2(1+z).
 __device__ __forceinline__ float jac_inv32(const HP &hp, float z, float lz, float d) {
@@ -330,19 +345,27 @@ __device__ __forceinline__ float jac_inv32(const HP &hp, float z, float lz, floa
 // JAC: the per-sample Jacobian option (a template parameter so that the
 // default kernel keeps its registers and occupancy).
 template <bool JAC>
-__global__ void __launch_bounds__(RW_THREADS) k_reweight(DevCatalog c, CallPtrs p, int h0, int nh) {
+__global__ void __launch_bounds__(RW_THREADS, RW_MINB) k_reweight(DevCatalog c, CallPtrs p, int h0, int nh) {
     __shared__ double red[8 + (RW_THREADS / 32) * 8];
     const int hl = blockIdx.x % nh, h = h0 + hl;
     const int ev = blockIdx.x / nh;  // natural order: consecutive blocks stream neighbouring samples
     const int tid = threadIdx.x;
     const HP &hp = p.hp[h];
     if (hp.status & (CHIMERA_PT_OUT_OF_SUPPORT | CHIMERA_PT_NONMONOTONE)) return;
-    const MixParams q = mix_params(hp);
+#if CHIM_RW_SMEMQ
+    __shared__ WParams sq;
+    if (tid == 0) sq = w_params(hp);
+    __syncthreads();
+    const WParams &q = sq;
+#else
+    const WParams q = w_params(hp);
+#endif
     const int64_t s0 = c.ev_soff[ev];
     const int ns = (int)(c.ev_soff[ev + 1] - s0);
     float *zd = p.zw + (size_t)hl * 2 * c.n_zpad + c.ev_zoff[ev];
     float *wd = zd + c.n_zpad;
     const float4 *inv = p.inv32 + (size_t)h * NU;
+    const float4 *linv = p.linv32 + (size_t)h * NU;
     const float4 *sp = c.s32 + s0;
     float zref;
     {
@@ -355,14 +378,25 @@ __global__ void __launch_bounds__(RW_THREADS) k_reweight(DevCatalog c, CallPtrs 
     float m[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // W1, Wd, Wd2, W2, n, Sd, Sd2
     const float dtop = (float)c.d_top;
     // one sample: table coordinate -> z (Hermite on the node pair), log2
-    // source masses, weight, moments; invalid samples (beyond d_L^gw(10))
-    // get z = inf and w = 0 and stay out of the moments
-    auto sample = [&](const float4 &sv, const float4 &nd, int j) {
+    // source masses, weight relative to the point's shared normalisation
+    // (mass.cuh), moments; invalid samples (beyond d_L^gw(10)) get z = inf
+    // and w = 0 and stay out of the moments.  Near a mass edge the in-range
+    // test is taken in FP64 from the sample's FP64 distance and masses.
+    auto sample = [&](const float4 &sv, const float4 &nd, const float4 &ndl, int j) {
         const float z = chimd::hermite4(nd, sv.y);
         const bool ok = z < CUDART_INF_F;  // false for inf and NaN
-        const float lz = __log2f(1.f + z);
-        float w = mass_weight32(q, sv.z - lz, sv.w - lz);
-        w = ok ? w : 0.f;
+        const float lz = chimd::hermite4(ndl, sv.y);  // log2(1+z) from its own node pairs
+        LogMass lm = log_mass(q, sv.z, sv.w, __ldg(c.s32lo + s0 + j), lz);
+        float w = 0.f;
+        if (ok && w_needs64(lm)) {
+            w = mass_weight_rel64(p, h, hp, c.beta, z, c.sd64[s0 + j], c.sm1_64[s0 + j], c.sm2_64[s0 + j]);
+        } else if (ok && w_in_range(lm)) {
+            if (lm.d1 < W_FP64) lm.d1 = corner_d1(p, h, hp, z, c.sd64[s0 + j], c.sm1_64[s0 + j], lm.d1);
+            // rcp.approx: mean relative error +4e-9 on B300 (measured), no shared bias to speak of
+            const WQuot wq = mass_weight_rel(q, lm);
+            w = __fdividef(wq.num, wq.den);
+            w = w > 0.f ? w : 0.f;
+        }
         const float d = ok ? z - zref : 0.f;
         const float wd_ = w * d;
         m[0] += w; m[1] += wd_; m[2] = fmaf(wd_, d, m[2]); m[3] = fmaf(w, w, m[3]);
@@ -374,44 +408,50 @@ __global__ void __launch_bounds__(RW_THREADS) k_reweight(DevCatalog c, CallPtrs 
         }
         wd[j] = w;
     };
-    auto node = [&](const float4 &sv) {
+    auto node = [&](const float4 &sv, float4 &nl) {
         const int k = __float_as_int(sv.x);
         const bool valid = (k < q.kv) || (k == q.kv && sv.y <= q.fv);
+        nl = valid ? __ldg(linv + k) : make_float4(0.f, 0.f, 0.f, 0.f);
         return valid ? __ldg(inv + k) : make_float4(CUDART_INF_F, 0.f, 0.f, 0.f);
     };
     int j = tid;
-    // four samples per thread in flight: loads first, then the arithmetic
-    for (; j + 3 * RW_THREADS < ns; j += 4 * RW_THREADS) {
-        float4 sv[4], nd[4];
+    // RW_INFLIGHT samples per thread in flight: loads first, then the arithmetic
+    for (; j + (RW_INFLIGHT - 1) * RW_THREADS < ns; j += RW_INFLIGHT * RW_THREADS) {
+        float4 sv[RW_INFLIGHT], nd[RW_INFLIGHT], nl[RW_INFLIGHT];
 #pragma unroll
-        for (int uu = 0; uu < 4; uu++) sv[uu] = __ldg(sp + j + uu * RW_THREADS);
+        for (int uu = 0; uu < RW_INFLIGHT; uu++) sv[uu] = __ldg(sp + j + uu * RW_THREADS);
 #pragma unroll
-        for (int uu = 0; uu < 4; uu++) nd[uu] = node(sv[uu]);
+        for (int uu = 0; uu < RW_INFLIGHT; uu++) nd[uu] = node(sv[uu], nl[uu]);
 #pragma unroll
-        for (int uu = 0; uu < 4; uu++) sample(sv[uu], nd[uu], j + uu * RW_THREADS);
+        for (int uu = 0; uu < RW_INFLIGHT; uu++) sample(sv[uu], nd[uu], nl[uu], j + uu * RW_THREADS);
     }
     for (; j < ns; j += RW_THREADS) {
         const float4 sv = __ldg(sp + j);
-        sample(sv, node(sv), j);
+        float4 nl;
+        const float4 nd = node(sv, nl);
+        sample(sv, nd, nl, j);
     }
     block_sum<7, RW_THREADS>(m, red);
     if (tid == 0) {
-        // Scott's rule in FP32 (the mixed path's precision) from the block
-        // sums: weighted, then unweighted, then the grid spacing
+        // Scott's rule from the FP64 block sums: the moments' difference
+        // E[d^2] - E[d]^2 in FP64 (no cancellation in FP32), the rest in FP32
+        // (errors that differ between events; B300's FP64 pipe would make a
+        // double pow this block's longest step): weighted, then unweighted,
+        // then the grid spacing
         float bl = c.dz32;
-        const float W1 = (float)red[0], n = (float)red[4];
+        const double W1 = red[0], n = red[4];
         bool done = false;
-        if (W1 > 0.f) {
-            const float mw = (float)red[1] / W1, var = (float)red[2] / W1 - mw * mw;
-            const float neff = W1 * W1 / (float)red[3];
-            if (neff >= 2.f && var > 0.f) {
-                bl = sqrtf(var) * exp2f(-0.2f * log2f(neff));
+        if (W1 > 0.0) {
+            const double mw = red[1] / W1, var = red[2] / W1 - mw * mw;
+            const double neff = W1 * W1 / red[3];
+            if (neff >= 2.0 && var > 0.0) {
+                bl = sqrtf((float)var) * exp2f(-0.2f * log2f((float)neff));
                 done = true;
             }
         }
-        if (!done && n >= 2.f) {
-            const float mu = (float)red[5] / n, var = (float)red[6] / n - mu * mu;
-            if (var > 0.f) bl = sqrtf(var) * exp2f(-0.2f * log2f(n));
+        if (!done && n >= 2.0) {
+            const double mu = red[5] / n, var = red[6] / n - mu * mu;
+            if (var > 0.0) bl = sqrtf((float)var) * exp2f(-0.2f * log2f((float)n));
         }
         p.bw[(size_t)h * c.n_events + ev] = (double)bl;
     }
@@ -488,14 +528,18 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
     __syncthreads();
     const double bd = p.bw[out];  // the reweighting kernel's FP32 bandwidth
     const float b = (float)bd;
-    const float inv_s2b = 0.70710678f / b;
-    const float ds = dz * inv_s2b;
+    // 1/(sqrt2 b) and dz/(sqrt2 b) from FP64 (rounded once; their float
+    // products would scale every Gaussian of the event alike)
+    const double is2b = 0.70710678118654752440 / bd;
+    const float inv_s2b = (float)is2b;
+    const float ds = (float)(c.dz * is2b);
+    const float dz_lo = c.dz_lo32;
     const float halfk = KW32 * b;
 
     // ---- Gaussian factor table C_t = exp(-(ds t)^2) and segment valid counts
     for (int t = tid; t < 2 * CCAP; t += EV_THREADS) {
         float x = ds * (float)(t - CCAP);
-        CT2[t] = __expf(-x * x);
+        CT2[t] = expc(-x * x);
     }
     for (int k = tid; k < nseg; k += EV_THREADS) {
         int lo = seglo[k], hi = seglo[k + 1];
@@ -557,7 +601,7 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
             const int A1 = fA1 > (float)s_hi ? s_hi : (int)fA1;
             if (A0 <= A1 && cnt <= SMALL_CNT) {
                 // a few samples: lanes over the grid points, direct exponentials
-                v = small_group(zs + lo, ws + lo, cnt, A0, A1, G, Fs, dz, inv_s2b, halfk, lane);
+                v = small_group(zs + lo, ws + lo, cnt, A0, A1, G, Fs, dz, dz_lo, inv_s2b, halfk, lane);
             } else if (A0 <= A1) {
                 // group origin; a multiple of 4 when the profile rows are
                 // 16-byte aligned, so that the table is staged as float4
@@ -568,19 +612,19 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
                 const int nqb = tlo >= 1 ? (tlo + 3) >> 2 : 0;
                 const int nq = max(nqf, nqb);  // symmetric table, zero-padded
                 // shared origin for spreads up to 16 b; beyond 8 b the table is
-                // scaled by e^20 (undone in A) to keep every relevant
+                // scaled by 2^29 (undone in A, exactly) to keep every relevant
                 // coefficient and Horner intermediate in the normal float range
                 const bool uni = ds <= 0.5f && spread <= 16.f * b && thi >= -1 && tlo >= 0 &&
                                  8 * nq <= DCAP && 4 * nq < CCAP;
                 if (uni) {
-                    const float lnscale = spread > 8.f * b ? 20.f : 0.f;
-                    const float scale = spread > 8.f * b ? 4.85165195e8f : 1.f;  // e^20
+                    const float iscale = spread > 8.f * b ? 1.862645149230957e-9f : 1.f;  // 2^-29
+                    const float scale = spread > 8.f * b ? 536870912.f : 1.f;             // 2^29
                     __syncwarp();
                     if (vec4) stage_table4(D, nq, t_o - 4 * nq, A0, A1, G, Fs, CT - 4 * nq, scale, lane);
                     else stage_table<true>(D, 8 * nq, t_o - 4 * nq, A0, A1, G, Fs, CT, 4 * nq, scale, lane);
                     __syncwarp();
-                    const float zo = t_o * dz;
-#define CHIM_UNION(R) v = union_samples<R>(D, nq, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, lnscale)
+                    const float zo = fmaf((float)t_o, dz, (float)t_o * dz_lo);  // t_o dz without dz's rounding
+#define CHIM_UNION(R) v = union_samples<R>(D, nq, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, iscale)
                     switch ((cnt + 31) >> 5) {
                         case 1: CHIM_UNION(1); break;
                         case 2: CHIM_UNION(2); break;
@@ -603,7 +647,7 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
                         // a sample further than its window from [A0, A1] adds nothing
                         // (and would push exp(2 u ds) out of range)
                         if (fabsf(z - ts * dz) > halfk + dz) continue;
-                        v += w * lane_chain(D + (ts - base), CT, Tw, z, ts, dz, inv_s2b, ds);
+                        v += w * lane_chain(D + (ts - base), CT, Tw, z, ts, dz, dz_lo, inv_s2b, ds);
                     }
                 } else {
                     for (int j = lane; j < cnt; j += 32) {
@@ -613,7 +657,7 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
                         int a1 = min(A1, (int)floorf((z + halfk) * inv_dz));
                         float sacc = 0.f;
                         for (int a = a0; a <= a1; a++) {
-                            float x = (a * dz - z) * inv_s2b;
+                            float x = (fmaf((float)a, dz, (float)a * dz_lo) - z) * inv_s2b;
                             sacc += expf(-x * x) * Fs[a] * G[a];
                         }
                         v += w * sacc;

@@ -45,6 +45,18 @@ constexpr int SEL_THREADS = 256;
 constexpr int SEL_PER_THREAD = 8;
 constexpr int SEL_CHUNK = SEL_THREADS * SEL_PER_THREAD;
 
+// A double constant as an unevaluated pair of floats, x = hi + lo (the
+// mixed kernels multiply by it without the float rounding of the constant).
+struct F2 {
+    float hi, lo;
+};
+inline __host__ __device__ F2 split_f2(double x) {
+    F2 r;
+    r.hi = (float)x;
+    r.lo = (float)(x - (double)r.hi);
+    return r;
+}
+
 // Per-hyperpoint parameters, written by the cosmology kernel (FP64).
 struct HP {
     double th[12];
@@ -68,6 +80,20 @@ struct HP {
         lmmin32, xi0_32, n32, om32, gam32, kap32, l1zp32, cH32, inv_dc3_32;
     float l2min32, l2max32;  // log2 m_min, log2 m_max
     float h0_32, zp32;
+    // mixed forward path (K2, K5): the mass model relative to its shared
+    // normalisation w_scale = C1 m_min^-(alpha+1) |1 + beta| (log2 e in
+    // place of |1 + beta| when beta = -1), C1 = c_pl (c_g when c_pl = 0),
+    // and the constants of the weight and of the selection term as float pairs
+    double ln_wscale;        // ln w_scale
+    double inv_wscale;       // 1 / w_scale
+    double ln_sel;           // ln(w_scale 3 / Dhat(z_max)^3): the selection terms' shared factor
+    float r_pl32, r_g32;     // c_pl / C1, m_min^alpha c_g / C1
+    F2 na2, gk2, beta2, b1_2, l2min2;  // -alpha, -log2 e / (2 sigma^2), beta, 1 + beta, log2 m_min
+    F2 l2max2, b1ln2_2;                // log2 m_max, (1 + beta) ln 2
+    F2 kH2;                  // H0 / c [1/Mpc]
+    F2 xi0_2, omx2, nn2, nomx2;  // Xi0, 1 - Xi0, -n, n (1 - Xi0)
+    F2 om2, omc2;            // Om, 1 - Om
+    F2 gam2, gk_psi2, l2zp2; // gamma, gamma + kappa, log2(1 + z_p)
 };
 
 // Resident catalog (device pointers unless noted).
@@ -76,6 +102,7 @@ struct DevCatalog {
     int64_t n_samples, n_pix, n_gal, n_det, n_inj_total;
     double z_max, dz, n_gal_total, lambda_g, beta, d_top;
     float z_max32, dz32;  // float copies for the mixed kernels
+    float dz_lo32;        // dz - dz32: grid positions a dz in FP32 as fmaf(a, dz32, a dz_lo32)
     int32_t max_ns, max_seg, max_npix;
     // events
     int64_t *ev_soff;     // [n_events+1] sample offsets (sorted storage)
@@ -139,10 +166,14 @@ struct DevCatalog {
     uint16_t *gzq, *gsq;  // F16/BF16 storage (z as offset from pix_zref)
     // PE samples
     float4 *s32;          // (inverse-table interval k as int bits, fraction f, log2 m1_det, log2 m2_det)
+    float2 *s32lo;        // low parts of log2 m1_det, log2 m2_det (value - the float above)
     double *sd64, *sm1_64, *sm2_64;
     // detected injections
     float4 *i32a;         // (k bits, f, log2 m1_det, log2 m2_det)
+    float2 *i32lo;        // low parts of log2 m1_det, log2 m2_det
     float2 *i32b;         // (d_L, ln pi_inj)
+    float *iipi32;        // 2^-K / pi_inj, computed in FP64 and rounded (mixed selection)
+    double ln_ipi_shift;  // K ln 2
     double *id64, *im1_64, *im2_64, *ilp64;
 };
 
@@ -153,6 +184,7 @@ struct CallPtrs {
     const double *const *fwd; // [H] forward table of h's Om (device pointer array)
     double2 *inv64;           // [H x (NU+1)] (z_k, dz/du_k)
     float4 *inv32;            // [H x NU] (z_k, dz/du_k / NU, z_k+1, dz/du_k+1 / NU)
+    float4 *linv32;           // [H x NU] the same for log2(1 + z), or nullptr
     double *F64;              // [H x n_z]
     float *F32;               // [H x n_z], F / F_scale
     const void *const *prof;  // [H] galaxy profile base (double* or float*) of h's Om
@@ -190,8 +222,9 @@ void launch_fwd_tables(const FwdBatch &b, bool dOm, cudaStream_t st);
 // fp64, normalised F32 otherwise), status.  dk: scratch of at least
 // H x NT_FWD x 8 bytes (FP32 d_L^gw and J at the forward nodes),
 // fmax_bits: [H] scratch.
-// nodes64: also the FP64 inverse nodes (inv64; FP64 calls and gradients).
-void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, bool nodes64, double *dk,
+// Every call gets the FP64 inverse nodes (inv64) and their rounded FP32
+// pairs (inv32, and linv32 for log2(1+z) when given).
+void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, double *dk,
                          unsigned long long *fmax_bits, cudaStream_t st);
 // K3: galaxy redshift prior on the grid for one Om.  dv: scratch of n_z
 // doubles followed by n_z floats, invZ: [n_gal] scratch; out64 (FP64

@@ -10,15 +10,20 @@
 // its fixed-order reduction) but keeps every intermediate in one file-scope
 // device array of fixed size, so it calls no cudaMalloc, cudaFree or other
 // allocating routine.  The caller passes its own device buffers for the
-// injections and for the outputs.
+// injections and for the outputs.  Its inverse distance table spans the
+// injections' own largest d_L (the catalog path's spans the PE samples too),
+// so the nodes differ and xi, N_eff agree with the catalog path to ~1e-10
+// relative, not bit for bit.
 //
 // Host code never dereferences the array's symbol: the first call on a
 // device asks the runtime for its device address (cudaGetSymbolAddress) and
 // remembers it for that device; that first call should come before any
-// stream capture.  All calls share the array and it keeps the previous
-// call's contents, so everything that must start at zero is cleared on the
-// call's stream, and calls whose work overlaps on the GPU (different streams
-// or threads at the same time) race on it.
+// stream capture.  Every call also reads the largest injection distance back
+// to the host, which synchronises `stream` once per call.  All calls share
+// the array and it keeps the previous call's contents, so everything that
+// must start at zero is cleared on the call's stream, and calls whose work
+// overlaps on the GPU (different streams or threads at the same time) race
+// on it.
 #include <mutex>
 
 #include "runtime.cuh"
@@ -110,15 +115,6 @@ int scratch_address(void **out) {
     return CHIMERA_OK;
 }
 
-bool admissible(const double *t) {
-    for (int k = 0; k < 12; k++)
-        if (!(t[k] == t[k]) || t[k] == 1.0 / 0.0 || t[k] == -1.0 / 0.0) return false;
-    return t[0] > 0.0 && t[1] >= 0.0 && t[1] <= 1.0 && t[2] > 0.0 && t[6] > 0.0 && t[7] > 0.0 &&
-           t[8] > t[7] && t[11] > -1.0;
-}
-
-const double kSafe[12] = {70.0, 0.3, 1.0, 1.91, 3.4, 34.0, 3.6, 5.0, 100.0, 2.7, 3.0, 2.0};
-
 }  // namespace
 
 }  // namespace chim
@@ -167,6 +163,12 @@ extern "C" int chimera_selection_static(int32_t n_points, const double *theta, i
     if (e != cudaSuccess) return cuda_check(e, "chimera_selection_static: d_top");
     double dmax;
     memcpy(&dmax, &bits, 8);
+    if (!(dmax > 0.0) || !std::isfinite(dmax)) {
+        // no positive finite distance: the inverse table u = sqrt(d / d_top)
+        // would have no range
+        set_error("chimera_selection_static: inj_dL holds no positive finite distance");
+        return CHIMERA_ERR_INVALID_ARG;
+    }
 
     DevCatalog c{};
     c.n_z = ST_NZ;
@@ -195,8 +197,8 @@ extern "C" int chimera_selection_static(int32_t n_points, const double *theta, i
     double oms[ST_HMAX];
     int nom = 0;
     for (int h = 0; h < H; h++) {
-        bool ok = admissible(theta + 12 * h);
-        memcpy(th + 12 * h, ok ? theta + 12 * h : kSafe, sizeof(double) * 12);
+        bool ok = theta_admissible(theta + 12 * h);
+        memcpy(th + 12 * h, ok ? theta + 12 * h : kSafeTheta, sizeof(double) * 12);
         status[h] = ok ? 0 : CHIMERA_PT_OUT_OF_SUPPORT;
         double Om = th[12 * h + 1];
         int slot = -1;
@@ -225,7 +227,7 @@ extern "C" int chimera_selection_static(int32_t n_points, const double *theta, i
     p.F32 = reinterpret_cast<float *>(S + OFF_F32);
     p.selp = reinterpret_cast<double *>(S + OFF_SELP);
     p.n_chunk = selection_chunks(c);
-    launch_hyper_tables(c, p, H, true, true, reinterpret_cast<double *>(S + OFF_DK),
+    launch_hyper_tables(c, p, H, true, reinterpret_cast<double *>(S + OFF_DK),
                         reinterpret_cast<unsigned long long *>(S + OFF_FMAX), st);
     launch_selection(c, p, H, true, st);
     k_static_reduce<<<H, 256, 0, st>>>(p.selp, p.n_chunk, (double)n_inj_total, p.hp, xi, neff);

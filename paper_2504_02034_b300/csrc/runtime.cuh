@@ -3,6 +3,7 @@
 #pragma once
 
 #include <atomic>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -19,6 +20,18 @@
 namespace chim {
 
 void set_error(const std::string &msg);
+
+// Admissibility of a hyperparameter point (every component finite, H0 > 0,
+// Om in [0, 1], Xi0 > 0, sigma_g > 0, 0 < m_min < m_max, z_p > -1); an
+// inadmissible point is evaluated at kSafeTheta instead and reported as
+// OUT_OF_SUPPORT with ln L = -inf.
+inline bool theta_admissible(const double *t) {
+    for (int k = 0; k < 12; k++)
+        if (!std::isfinite(t[k])) return false;
+    return t[0] > 0.0 && t[1] >= 0.0 && t[1] <= 1.0 && t[2] > 0.0 && t[6] > 0.0 && t[7] > 0.0 &&
+           t[8] > t[7] && t[11] > -1.0;
+}
+inline constexpr double kSafeTheta[12] = {70.0, 0.3, 1.0, 1.91, 3.4, 34.0, 3.6, 5.0, 100.0, 2.7, 3.0, 2.0};
 
 struct Ctx;
 
@@ -63,6 +76,7 @@ struct Workspace {
     HP *hp = nullptr;
     double2 *inv64 = nullptr;
     float4 *inv32 = nullptr;
+    float4 *linv32 = nullptr;
     double *F64 = nullptr;
     float *F32 = nullptr;
     double *lnI = nullptr, *bw = nullptr, *selp = nullptr;

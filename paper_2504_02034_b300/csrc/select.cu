@@ -28,90 +28,24 @@ __device__ __forceinline__ float warp_sumf(float v) {
     return v;
 }
 
-// mixed: FP32 per term in the log2 domain with SFU exp2 / log2 / reciprocal
-// (relative error ~1e-6 per term, independent between injections), FP64
-// across warps.  The mass model is the event kernel's (mass_weight32).  A
-// block takes one chunk of injections for SEL_HB hyperpoints: every
-// injection is read once and evaluated for all of them.
+// mixed: each term in FP32 with the injection's own rounding errors only
+// (they differ between injections and average out in the sum): the
+// hyperpoint's constants enter as float pairs or through the FP64 factor
+// hp.ln_sel, 1/pi_inj comes rounded from FP64, logs are the accurate log2f,
+// exponentials split off their integer part before the SFU (mass.cuh), and
+// the test whether an injection lies inside the mass range and below z_max is
+// taken again in FP64 where the FP32 one could differ (as the FP64 path and
+// the oracle take it).  Partial sums in FP64 across warps.  A block takes one
+// chunk of injections for SEL_HB hyperpoints: every injection is read once
+// and evaluated for all of them.
 constexpr int SEL_HB = 2;
 
 struct SelConst {
-    MixParams q;
-    const float4 *inv;
-    float xi0, n, om, gam, gk, l2zp, cH, k3;
+    WParams q;
+    const float4 *inv, *linv;
+    F2 kH, xi0, omx, nn, nomx, om, omc, gam, gkp, l2zp;
+    double cfac;  // exp(hp.ln_sel + K ln 2): the shared factor of every term
 };
-
-__global__ void __launch_bounds__(SEL_THREADS) k_select_mixed(DevCatalog c, CallPtrs p, int H) {
-    __shared__ double red[2 * SEL_HB * (SEL_THREADS / 32)];
-    __shared__ SelConst scs[SEL_HB];
-    const int chunk = blockIdx.x, h0 = blockIdx.y * SEL_HB;
-    const int nh = min(SEL_HB, H - h0);
-    if (threadIdx.x < nh) {
-        const HP &hp = p.hp[h0 + threadIdx.x];
-        SelConst k;
-        k.q = mix_params(hp);
-        k.inv = p.inv32 + (size_t)(h0 + threadIdx.x) * NU;
-        k.xi0 = hp.xi0_32; k.n = hp.n32; k.om = hp.om32;
-        k.gam = hp.gam32; k.gk = hp.gam32 + hp.kap32;
-        k.l2zp = hp.l1zp32 * 1.44269504088896340736f;
-        k.cH = hp.cH32; k.k3 = 3.f * hp.cH32 * hp.inv_dc3_32;
-        scs[threadIdx.x] = k;
-    }
-    __syncthreads();
-    const float zmax = c.z_max32;
-    float s1[SEL_HB], s2[SEL_HB];
-#pragma unroll
-    for (int hb = 0; hb < SEL_HB; hb++) s1[hb] = s2[hb] = 0.f;
-    const int64_t base = (int64_t)chunk * SEL_CHUNK;
-    for (int qq = 0; qq < SEL_PER_THREAD; qq++) {
-        const int64_t j = base + qq * SEL_THREADS + threadIdx.x;
-        if (j >= c.n_det) break;
-        const float4 a = __ldg(c.i32a + j);
-        const float2 bq = __ldg(c.i32b + j);
-        const int k = __float_as_int(a.x);
-        const float ipi = ex2(-bq.y * 1.44269504088896340736f);  // 1 / pi_inj
-#pragma unroll
-        for (int hb = 0; hb < SEL_HB; hb++) {
-            if (hb >= nh) break;
-            const SelConst &K = scs[hb];
-            if (!((k < K.q.kv) || (k == K.q.kv && a.y <= K.q.fv))) continue;
-            const float z = chimd::hermite4(__ldg(K.inv + k), a.y);
-            if (!(z <= zmax)) continue;
-            const float ap = 1.f + z, lz2 = __log2f(ap);
-            const float w = mass_weight32(K.q, a.z - lz2, a.w - lz2);
-            const float pw = ex2(-K.n * lz2);  // (1+z)^-n
-            const float xi = K.xi0 + (1.f - K.xi0) * pw;
-            const float Dc = __fdividef(bq.x, ap * xi);  // D_c = d_L / ((1+z) Xi)
-            const float rE = rsqrtf(K.om * ap * ap * ap + 1.f - K.om);
-            // J = (D_c + (1+z) c/H0 / E) Xi + (1+z) D_c dXi/dz, where
-            // (1+z) dXi/dz = -n (1 - Xi0) (1+z)^-n
-            const float J = (Dc + ap * K.cH * rE) * xi - K.n * (1.f - K.xi0) * pw * Dc;
-            const float pz = K.k3 * Dc * Dc * rE;
-            // s = w psi p_z / ((1+z)^3 |J| pi_inj), psi's denominator folded
-            // into the one division
-            const float psi_num = ex2(K.gam * lz2), psi_den = 1.f + ex2(K.gk * (lz2 - K.l2zp));
-            const float sv = __fdividef(w * psi_num * pz * ipi, ap * ap * ap * fabsf(J) * psi_den);
-            s1[hb] += sv;
-            s2[hb] = fmaf(sv, sv, s2[hb]);
-        }
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int hb = 0; hb < SEL_HB; hb++) {
-        const float a1 = warp_sumf(s1[hb]), a2 = warp_sumf(s2[hb]);
-        if (lane == 0) {
-            red[(2 * hb) * (SEL_THREADS / 32) + wid] = a1;
-            red[(2 * hb + 1) * (SEL_THREADS / 32) + wid] = a2;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < 2 * nh) {
-        double acc = 0.0;
-        for (int w = 0; w < SEL_THREADS / 32; w++) acc += red[threadIdx.x * (SEL_THREADS / 32) + w];
-        const int hb = threadIdx.x >> 1;
-        p.selp[((size_t)(h0 + hb) * p.n_chunk + chunk) * 2 + (threadIdx.x & 1)] = acc;
-    }
-}
 
 __device__ bool invert64_sel(const DevCatalog &c, const CallPtrs &p, int h, const HP &hp, double d,
                              double *zout) {
@@ -134,6 +68,100 @@ __device__ bool invert64_sel(const DevCatalog &c, const CallPtrs &p, int h, cons
     if (isfinite(step)) z -= step;
     *zout = z;
     return true;
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) k_select_mixed(DevCatalog c, CallPtrs p, int H) {
+    __shared__ double red[2 * SEL_HB * (SEL_THREADS / 32)];
+    __shared__ SelConst scs[SEL_HB];
+    const int chunk = blockIdx.x, h0 = blockIdx.y * SEL_HB;
+    const int nh = min(SEL_HB, H - h0);
+    if (threadIdx.x < nh) {
+        const HP &hp = p.hp[h0 + threadIdx.x];
+        SelConst k;
+        k.q = w_params(hp);
+        k.inv = p.inv32 + (size_t)(h0 + threadIdx.x) * NU;
+        k.linv = p.linv32 + (size_t)(h0 + threadIdx.x) * NU;
+        k.kH = hp.kH2; k.xi0 = hp.xi0_2; k.omx = hp.omx2; k.nn = hp.nn2; k.nomx = hp.nomx2;
+        k.om = hp.om2; k.omc = hp.omc2; k.gam = hp.gam2; k.gkp = hp.gk_psi2; k.l2zp = hp.l2zp2;
+        k.cfac = exp(hp.ln_sel + c.ln_ipi_shift);
+        scs[threadIdx.x] = k;
+    }
+    __syncthreads();
+    const float zmax = c.z_max32;
+    float s1[SEL_HB], s2[SEL_HB];
+#pragma unroll
+    for (int hb = 0; hb < SEL_HB; hb++) s1[hb] = s2[hb] = 0.f;
+    const int64_t base = (int64_t)chunk * SEL_CHUNK;
+    for (int qq = 0; qq < SEL_PER_THREAD; qq++) {
+        const int64_t j = base + qq * SEL_THREADS + threadIdx.x;
+        if (j >= c.n_det) break;
+        const float4 a = __ldg(c.i32a + j);
+        const float dL = __ldg(&c.i32b[j].x);
+        const float ipi = __ldg(c.iipi32 + j);
+        const float2 lo = __ldg(c.i32lo + j);
+        const int k = __float_as_int(a.x);
+#pragma unroll
+        for (int hb = 0; hb < SEL_HB; hb++) {
+            if (hb >= nh) break;
+            const SelConst &K = scs[hb];
+            if (!((k < K.q.kv) || (k == K.q.kv && a.y <= K.q.fv))) continue;
+            const float z = chimd::hermite4(__ldg(K.inv + k), a.y);
+            if (!(z < CUDART_INF_F)) continue;
+            const float ap = 1.f + z, lz = chimd::hermite4(__ldg(K.linv + k), a.y);  // log2(1+z)
+            LogMass lm = log_mass(K.q, a.z, a.w, lo, lz);
+            float wn, wd;  // the weight as a quotient
+            if (w_needs64(lm) || fabsf(z - zmax) < ZMAX_GUARD) {
+                // FP64: range and z_max tests as the oracle takes them, and
+                // the weight itself
+                const int h = h0 + hb;
+                const HP &hp = p.hp[h];
+                double z64;
+                if (!refine64(p, h, hp, z, c.id64[j], &z64) || !(z64 <= c.z_max)) continue;
+                const double a64 = 1.0 + z64;
+                wn = (float)(mass_weight64(hp, c.beta, c.im1_64[j] / a64, c.im2_64[j] / a64) * hp.inv_wscale);
+                wd = 1.f;
+            } else {
+                if (!(w_in_range(lm) && z <= zmax)) continue;
+                if (lm.d1 < W_FP64) lm.d1 = corner_d1(p, h0 + hb, p.hp[h0 + hb], z, c.id64[j], c.im1_64[j], lm.d1);
+                const WQuot wq = mass_weight_rel(K.q, lm);
+                wn = wq.num;
+                wd = wq.den;
+            }
+            const float pw = ex2_mul_n(K.nn, lz);  // (1+z)^-n
+            const float xi = fmaf(K.omx.hi, pw, K.xi0.hi) + fmaf(K.omx.lo, pw, K.xi0.lo);
+            const float N = mul_f2(K.kH, dL);  // d_L H0 / c
+            const float axi = ap * xi;       // Dhat = D_c H0 / c = N / ((1+z) Xi)
+            const float a3 = ap * ap * ap;
+            const float E = sqrtf(fmaf(K.om.hi, a3, K.omc.hi) + fmaf(K.om.lo, a3, K.omc.lo));
+            // J H0 / c = (Dhat + (1+z)/E) Xi - n (1 - Xi0) (1+z)^-n Dhat; times E (1+z) Xi:
+            const float JE = fmaf(N, E, ap * axi) * xi - mul_f2(K.nomx, pw) * N * E;
+            const float r = ex2_mul_n(K.gkp, (lz - K.l2zp.hi) - K.l2zp.lo);  // ((1+z)/(1+z_p))^(gamma+kappa)
+            // s / cfac = w' psi Dhat^2 / (E (1+z)^3 |J H0/c|) 2^-K / pi_inj
+            //          = w' (1+z)^gamma N^2 2^-K / pi_inj / ((1+z) Xi (1 + r) (1+z)^3 |JE|)
+            const float sv = __fdividef(wn * ex2_mul_n(K.gam, lz) * N * N * ipi, wd * axi * (1.f + r) * a3 * fabsf(JE));
+            if (!(sv > 0.f)) continue;
+            s1[hb] += sv;
+            s2[hb] = fmaf(sv, sv, s2[hb]);
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int hb = 0; hb < SEL_HB; hb++) {
+        const float a1 = warp_sumf(s1[hb]), a2 = warp_sumf(s2[hb]);
+        if (lane == 0) {
+            red[(2 * hb) * (SEL_THREADS / 32) + wid] = a1;
+            red[(2 * hb + 1) * (SEL_THREADS / 32) + wid] = a2;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * nh) {
+        double acc = 0.0;
+        for (int w = 0; w < SEL_THREADS / 32; w++) acc += red[threadIdx.x * (SEL_THREADS / 32) + w];
+        const int hb = threadIdx.x >> 1;
+        const double cf = scs[hb].cfac;
+        acc *= (threadIdx.x & 1) ? cf * cf : cf;
+        p.selp[((size_t)(h0 + hb) * p.n_chunk + chunk) * 2 + (threadIdx.x & 1)] = acc;
+    }
 }
 
 __global__ void __launch_bounds__(SEL_THREADS) k_select_fp64(DevCatalog c, CallPtrs p, int H) {

@@ -1,0 +1,107 @@
+"""Whole-catalog ln L at full size against the FP64 oracle (Eq. hyperlike).
+
+The summed ln L of every tested hyperpoint, taken from the launch
+configuration of its workload, must match the oracle's to
+
+  FP64 path : |Delta ln L| <= 1e-6 N_obs
+  mixed path: |Delta ln L| <= 1e-3 absolute per catalog
+
+* 300-event catalog (5000 PE, 1000-point grid, 2e6 injections): all 16
+  hyperpoints of the launch, FP64 and mixed.
+* photometric catalog (300 events, sigma_z = 0.05(1+z), x3 galaxies, BF16
+  storage): 4 of the 512 hyperpoints of the mixed launch; the oracle reads the
+  BF16-rounded galaxies (the storage error itself is stated separately).
+* differentiation catalog (5000 events x 4000 PE, 5e6 injections, Om varying):
+  2 of the 64 hyperpoints of the mixed launch, and the same 2 in FP64.
+
+Each measured difference is printed (lines starting "MEASURED") so that a run
+with -s records the error statement.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from synth import catalog as sc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def chim():
+    from paper_2504_02034_b300 import build
+    build.build()
+    import paper_2504_02034_b300 as pkg
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def ctx(chim):
+    c = chim.Context(0)
+    yield c
+    c.close()
+
+
+def _check(tag, lnL, st, ref, n_obs, prec):
+    assert st == ref["status"], (tag, st, ref["status"])
+    if not math.isfinite(ref["lnL"]):
+        assert lnL == -math.inf, (tag, lnL)
+        return 0.0
+    d = lnL - ref["lnL"]
+    tol = 1e-6 * n_obs if prec == 0 else 1e-3
+    print("MEASURED %s prec=%d lnL=%.9f oracle=%.9f delta=%.3e tol=%.1e"
+          % (tag, prec, lnL, ref["lnL"], d, tol))
+    assert abs(d) <= tol, (tag, prec, d)
+    return d
+
+
+def test_o5_catalog_all_16_points(chim, ctx, orc):
+    cat = sc.config_catalog(2)
+    th = sc.config_hyperpoints(2)
+    assert th.shape[0] == 16
+    oc = orc.Catalog(cat)
+    refs = [oc.loglike(t) for t in th]
+    cid = ctx.load(cat)
+    try:
+        for prec in (chim.FP64, chim.MIXED):
+            lnL, neff, st = ctx.loglike(cid, th, prec)
+            ds = [_check("o5_c2[h=%d]" % h, lnL[h], st[h], refs[h], cat["n_events"], prec)
+                  for h in range(16)]
+            print("MEASURED o5_c2 prec=%d max|delta|=%.3e" % (prec, np.max(np.abs(ds))))
+    finally:
+        ctx.unload(cid)
+
+
+def test_photometric_bf16_catalog_4_of_512_points(chim, ctx, orc):
+    cat = sc.config_catalog(3)
+    th = sc.config_hyperpoints(3)
+    assert th.shape[0] == 512 and cat["gal_storage"] == sc.GAL_BF16
+    cid = ctx.load(cat)
+    try:
+        lnL, neff, st = ctx.loglike(cid, th, chim.MIXED)
+    finally:
+        ctx.unload(cid)
+    oc = orc.Catalog(sc.quantize_galaxies(cat, sc.GAL_BF16))
+    ok = [h for h in range(512) if np.isfinite(lnL[h])]
+    hs = [ok[0], ok[len(ok) // 3], ok[2 * len(ok) // 3], ok[-1]]
+    for h in hs:
+        _check("photo_c3[h=%d]" % h, lnL[h], st[h], oc.loglike(th[h]), cat["n_events"], chim.MIXED)
+
+
+def test_differentiation_catalog_2_of_64_points(chim, ctx, orc):
+    cat = sc.config_catalog(4)
+    th = sc.config_hyperpoints(4)
+    assert th.shape[0] == 64
+    cid = ctx.load(cat)
+    try:
+        lnL, neff, st = ctx.loglike(cid, th, chim.MIXED)
+        hs = [h for h in (1, 40) if np.isfinite(lnL[h])]
+        assert hs
+        lnL64, _, st64 = ctx.loglike(cid, th[hs], chim.FP64)
+    finally:
+        ctx.unload(cid)
+    oc = orc.Catalog(cat)
+    for q, h in enumerate(hs):
+        ref = oc.loglike(th[h])
+        _check("diff_c4[h=%d]" % h, lnL[h], st[h], ref, cat["n_events"], chim.MIXED)
+        _check("diff_c4[h=%d]" % h, lnL64[q], st64[q], ref, cat["n_events"], chim.FP64)

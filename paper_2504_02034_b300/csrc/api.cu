@@ -766,14 +766,28 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     }
     c.n_seg = (int64_t)seg_pf.size();
     c.max_seg = max_seg;
-    // ---- warp groups and the per-event redshift reference (mixed kernel)
+    // ---- warp groups, the per-event redshift reference and inverse-table
+    // range (mixed kernels)
     std::vector<int4> groups;
     std::vector<int32_t> ev_goff(ne + 1, 0);
     std::vector<float2> ev_ref(ne);
+    std::vector<int2> ev_krange(ne);
     std::vector<int64_t> ev_zoff(ne + 1, 0);
-    int max_groups = 1;
+    int max_groups = 1, max_krange = 1;
     for (int i = 0; i < ne; i++) {
         const int64_t a = d->sample_off[i], n = d->sample_off[i + 1] - a;
+        {
+            int kmin = NU, kmax = 0;
+            for (int64_t j = a; j < a + n; j++) {
+                int k;
+                memcpy(&k, &s32[j].x, 4);
+                kmin = std::min(kmin, k);
+                kmax = std::max(kmax, k);
+            }
+            if (kmin > kmax) kmin = kmax = 0;
+            ev_krange[i] = make_int2(kmin, kmax);
+            max_krange = std::max(max_krange, kmax - kmin + 1);
+        }
         double m = 0, m2 = 0;
         for (int64_t j = a; j < a + n; j++) {
             double l = std::log(sd[j]);
@@ -832,6 +846,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         ev_zoff[i + 1] = ev_zoff[i] + ((d->sample_off[i + 1] - d->sample_off[i] + 3) & ~(int64_t)3);
     c.n_zpad = std::max<int64_t>(ev_zoff[ne], 4);
     c.max_groups = max_groups;
+    c.max_krange = max_krange;
     // ---- heavy-first event order: cost ~ N_s x spread of ln d_L
     std::vector<double> cost(ne);
     for (int i = 0; i < ne; i++) {
@@ -893,8 +908,20 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
             sigmax32[p] = std::max(sigmax32[p], sdec);
         }
     }
-    // ---- injections
+    // ---- injections, stored sorted by d_L: the selection kernel's chunks of
+    // consecutive injections then read a few neighbouring inverse-table
+    // intervals (the sum does not depend on the order beyond rounding)
     const int64_t nd = d->n_det;
+    std::vector<int64_t> iord(nd);
+    std::iota(iord.begin(), iord.end(), 0);
+    std::stable_sort(iord.begin(), iord.end(), [&](int64_t x, int64_t y) { return d->inj_dL[x] < d->inj_dL[y]; });
+    std::vector<double> idL(nd), im1(nd), im2(nd), ilp(nd);
+    for (int64_t j = 0; j < nd; j++) {
+        idL[j] = d->inj_dL[iord[j]];
+        im1[j] = d->inj_m1d[iord[j]];
+        im2[j] = d->inj_m2d[iord[j]];
+        ilp[j] = d->inj_log_pi[iord[j]];
+    }
     std::vector<float4> i32a(nd);
     std::vector<float2> i32lo(nd);
     std::vector<float2> i32b(nd);
@@ -905,25 +932,24 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     {
         double lo = 0.0, hi = 0.0;
         for (int64_t j = 0; j < nd; j++) {
-            const double l2 = -d->inj_log_pi[j] * 1.4426950408889634074;
+            const double l2 = -ilp[j] * 1.4426950408889634074;
             lo = j ? std::min(lo, l2) : l2;
             hi = j ? std::max(hi, l2) : l2;
         }
         const double K = std::floor(0.5 * (lo + hi));
         c.ln_ipi_shift = K * 0.69314718055994530942;
-        for (int64_t j = 0; j < nd; j++)
-            iipi[j] = (float)std::exp2(-d->inj_log_pi[j] * 1.4426950408889634074 - K);
+        for (int64_t j = 0; j < nd; j++) iipi[j] = (float)std::exp2(-ilp[j] * 1.4426950408889634074 - K);
     }
     for (int64_t j = 0; j < nd; j++) {
         int k;
         float f;
-        tcoord(d->inj_dL[j], k, f);
+        tcoord(idL[j], k, f);
         float kb;
         memcpy(&kb, &k, 4);
-        const double l1 = std::log2(d->inj_m1d[j]), l2 = std::log2(d->inj_m2d[j]);
+        const double l1 = std::log2(im1[j]), l2 = std::log2(im2[j]);
         i32a[j] = make_float4(kb, f, (float)l1, (float)l2);
         i32lo[j] = make_float2((float)(l1 - (double)(float)l1), (float)(l2 - (double)(float)l2));
-        i32b[j] = make_float2((float)d->inj_dL[j], (float)d->inj_log_pi[j]);
+        i32b[j] = make_float2((float)idL[j], (float)ilp[j]);
     }
     std::vector<int64_t> ev_soff(d->sample_off, d->sample_off + ne + 1);
     std::vector<int64_t> ev_poff(d->pix_off, d->pix_off + ne + 1);
@@ -990,6 +1016,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         {(void **)&c.groups, groups.data(), 16 * groups.size()},
         {(void **)&c.ev_goff, ev_goff.data(), 4 * ev_goff.size()},
         {(void **)&c.ev_ref, ev_ref.data(), 8 * ev_ref.size()},
+        {(void **)&c.ev_krange, ev_krange.data(), 8 * ev_krange.size()},
         {(void **)&c.ev_zoff, ev_zoff.data(), 8 * ev_zoff.size()},
         {(void **)&c.pix_S, pixS.data(), 8 * pixS.size()},
         {(void **)&c.gal_off, goff.data(), 8 * goff.size()},
@@ -1011,17 +1038,15 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         {(void **)&c.sm1_64, sm1.data(), 8 * sm1.size()},
         {(void **)&c.sm2_64, sm2.data(), 8 * sm2.size()},
     };
-    std::vector<double> id(d->inj_dL ? d->inj_dL : (const double *)nullptr,
-                           d->inj_dL ? d->inj_dL + nd : (const double *)nullptr);
     if (nd > 0) {
         ups.push_back({(void **)&c.i32a, i32a.data(), 16 * (size_t)nd});
         ups.push_back({(void **)&c.i32lo, i32lo.data(), 8 * (size_t)nd});
         ups.push_back({(void **)&c.i32b, i32b.data(), 8 * (size_t)nd});
         ups.push_back({(void **)&c.iipi32, iipi.data(), 4 * (size_t)nd});
-        ups.push_back({(void **)&c.id64, d->inj_dL, 8 * (size_t)nd});
-        ups.push_back({(void **)&c.im1_64, d->inj_m1d, 8 * (size_t)nd});
-        ups.push_back({(void **)&c.im2_64, d->inj_m2d, 8 * (size_t)nd});
-        ups.push_back({(void **)&c.ilp64, d->inj_log_pi, 8 * (size_t)nd});
+        ups.push_back({(void **)&c.id64, idL.data(), 8 * (size_t)nd});
+        ups.push_back({(void **)&c.im1_64, im1.data(), 8 * (size_t)nd});
+        ups.push_back({(void **)&c.im2_64, im2.data(), 8 * (size_t)nd});
+        ups.push_back({(void **)&c.ilp64, ilp.data(), 8 * (size_t)nd});
     }
     if (d->gal_storage == CHIMERA_GAL_F32) {
         ups.push_back({(void **)&c.gz32, gz32.data(), 4 * gz32.size()});

@@ -344,9 +344,16 @@ __device__ __forceinline__ float jac_inv32(const HP &hp, float z, float lz, floa
 
 // JAC: the per-sample Jacobian option (a template parameter so that the
 // default kernel keeps its registers and occupancy).
-template <bool JAC>
+// The event's slice of the inverse tables (its samples' intervals
+// kmin .. kmax, z and log2(1+z) node pairs) is staged in shared memory when
+// it fits RW_STAGE_MAX intervals, so that each sample's table lookup is a
+// shared-memory read instead of a global gather that waits on the sample's
+// own load.
+constexpr int RW_STAGE_MAX = 768;  // 24 KB of node pairs per block
+template <bool JAC, bool STAGE>
 __global__ void __launch_bounds__(RW_THREADS, RW_MINB) k_reweight(DevCatalog c, CallPtrs p, int h0, int nh) {
     __shared__ double red[8 + (RW_THREADS / 32) * 8];
+    extern __shared__ float4 rw_nodes[];  // STAGE: [2 x nk] node pairs of z, then of log2(1+z)
     const int hl = blockIdx.x % nh, h = h0 + hl;
     const int ev = blockIdx.x / nh;  // natural order: consecutive blocks stream neighbouring samples
     const int tid = threadIdx.x;
@@ -366,13 +373,26 @@ __global__ void __launch_bounds__(RW_THREADS, RW_MINB) k_reweight(DevCatalog c, 
     float *wd = zd + c.n_zpad;
     const float4 *inv = p.inv32 + (size_t)h * NU;
     const float4 *linv = p.linv32 + (size_t)h * NU;
+    int koff = 0;
+    if (STAGE) {
+        const int2 kr = c.ev_krange[ev];
+        const int nk = kr.y - kr.x + 1;
+        for (int i = tid; i < nk; i += RW_THREADS) {
+            rw_nodes[i] = __ldg(inv + kr.x + i);
+            rw_nodes[nk + i] = __ldg(linv + kr.x + i);
+        }
+        __syncthreads();
+        inv = rw_nodes;
+        linv = rw_nodes + nk;
+        koff = kr.x;
+    }
     const float4 *sp = c.s32 + s0;
     float zref;
     {
         const float2 zr = c.ev_ref[ev];
         const int k = __float_as_int(zr.x);
         const bool ok = (k < q.kv) || (k == q.kv && zr.y <= q.fv);
-        zref = ok ? chimd::hermite4(__ldg(inv + k), zr.y) : 0.f;
+        zref = ok ? chimd::hermite4(inv[k - koff], zr.y) : 0.f;
         if (!isfinite(zref)) zref = 0.f;
     }
     float m[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // W1, Wd, Wd2, W2, n, Sd, Sd2
@@ -411,8 +431,8 @@ __global__ void __launch_bounds__(RW_THREADS, RW_MINB) k_reweight(DevCatalog c, 
     auto node = [&](const float4 &sv, float4 &nl) {
         const int k = __float_as_int(sv.x);
         const bool valid = (k < q.kv) || (k == q.kv && sv.y <= q.fv);
-        nl = valid ? __ldg(linv + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-        return valid ? __ldg(inv + k) : make_float4(CUDART_INF_F, 0.f, 0.f, 0.f);
+        nl = valid ? linv[k - koff] : make_float4(0.f, 0.f, 0.f, 0.f);
+        return valid ? inv[k - koff] : make_float4(CUDART_INF_F, 0.f, 0.f, 0.f);
     };
     int j = tid;
     // RW_INFLIGHT samples per thread in flight: loads first, then the arithmetic
@@ -1001,8 +1021,16 @@ size_t event_fp64_smem(const DevCatalog &c) {
 
 void launch_reweight(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cudaStream_t st) {
     const unsigned nb = (unsigned)((int64_t)c.n_events * nh);
-    if (nb && p.jac_ps) k_reweight<true><<<nb, RW_THREADS, 0, st>>>(c, p, h0, nh);
-    else if (nb) k_reweight<false><<<nb, RW_THREADS, 0, st>>>(c, p, h0, nh);
+    const bool stage = c.max_krange <= RW_STAGE_MAX;
+    const size_t smem = stage ? 2 * sizeof(float4) * (size_t)c.max_krange : 0;
+    if (!nb) return;
+    if (p.jac_ps) {
+        if (stage) k_reweight<true, true><<<nb, RW_THREADS, smem, st>>>(c, p, h0, nh);
+        else k_reweight<true, false><<<nb, RW_THREADS, 0, st>>>(c, p, h0, nh);
+    } else {
+        if (stage) k_reweight<false, true><<<nb, RW_THREADS, smem, st>>>(c, p, h0, nh);
+        else k_reweight<false, false><<<nb, RW_THREADS, 0, st>>>(c, p, h0, nh);
+    }
 }
 
 void launch_event_mixed(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cudaStream_t st) {

@@ -124,6 +124,8 @@ struct DevCatalog {
     int32_t *ev_goff;     // [n_events+1] group offsets per event
     int32_t max_groups;   // most groups of any event
     float2 *ev_ref;       // [n_events] inverse-table (k bits, f) of the event's median d_L
+    int2 *ev_krange;      // [n_events] smallest and largest inverse-table interval of the event's samples
+    int32_t max_krange;   // most intervals any event spans (kmax - kmin + 1)
     int64_t *ev_zoff;     // [n_events+1] offsets of the events in a reweighted-sample row
                           // (each a multiple of 4 floats)
     int64_t n_zpad;       // length of a reweighted-sample row

@@ -70,11 +70,19 @@ __device__ bool invert64_sel(const DevCatalog &c, const CallPtrs &p, int h, cons
     return true;
 }
 
+// Injections are stored sorted by d_L, so a chunk spans a narrow slice of
+// the inverse tables: up to SEL_STAGE intervals of it (z and log2(1+z) node
+// pairs of each hyperpoint) are staged in shared memory.
+constexpr int SEL_STAGE = 128;
+
 __global__ void __launch_bounds__(SEL_THREADS) k_select_mixed(DevCatalog c, CallPtrs p, int H) {
     __shared__ double red[2 * SEL_HB * (SEL_THREADS / 32)];
     __shared__ SelConst scs[SEL_HB];
+    __shared__ float4 snode[SEL_HB][2][SEL_STAGE];
     const int chunk = blockIdx.x, h0 = blockIdx.y * SEL_HB;
     const int nh = min(SEL_HB, H - h0);
+    const int64_t base = (int64_t)chunk * SEL_CHUNK;
+    const int64_t last = min(base + SEL_CHUNK, c.n_det) - 1;
     if (threadIdx.x < nh) {
         const HP &hp = p.hp[h0 + threadIdx.x];
         SelConst k;
@@ -86,12 +94,33 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_mixed(DevCatalog c, Call
         k.cfac = exp(hp.ln_sel + c.ln_ipi_shift);
         scs[threadIdx.x] = k;
     }
+    // the chunk's interval range (sorted by d_L; the last valid interval is NU - 1)
+    int klo = 0, nk = 0;
+    if (base <= last) {
+        int k0, k1;
+        const float a0 = __ldg(&c.i32a[base].x), a1 = __ldg(&c.i32a[last].x);
+        k0 = __float_as_int(a0);
+        k1 = __float_as_int(a1);
+        if (k1 - k0 + 1 <= SEL_STAGE) {
+            klo = k0;
+            nk = k1 - k0 + 1;
+        }
+    }
+    for (int i = threadIdx.x; i < nh * nk; i += SEL_THREADS) {
+        const int hb = i / nk, r = i - hb * nk;
+        snode[hb][0][r] = __ldg(p.inv32 + (size_t)(h0 + hb) * NU + klo + r);
+        snode[hb][1][r] = __ldg(p.linv32 + (size_t)(h0 + hb) * NU + klo + r);
+    }
+    __syncthreads();
+    if (nk > 0 && threadIdx.x < nh) {  // the kernel reads the staged pairs at k - klo
+        scs[threadIdx.x].inv = snode[threadIdx.x][0] - klo;
+        scs[threadIdx.x].linv = snode[threadIdx.x][1] - klo;
+    }
     __syncthreads();
     const float zmax = c.z_max32;
     float s1[SEL_HB], s2[SEL_HB];
 #pragma unroll
     for (int hb = 0; hb < SEL_HB; hb++) s1[hb] = s2[hb] = 0.f;
-    const int64_t base = (int64_t)chunk * SEL_CHUNK;
     for (int qq = 0; qq < SEL_PER_THREAD; qq++) {
         const int64_t j = base + qq * SEL_THREADS + threadIdx.x;
         if (j >= c.n_det) break;
@@ -105,9 +134,9 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_mixed(DevCatalog c, Call
             if (hb >= nh) break;
             const SelConst &K = scs[hb];
             if (!((k < K.q.kv) || (k == K.q.kv && a.y <= K.q.fv))) continue;
-            const float z = chimd::hermite4(__ldg(K.inv + k), a.y);
+            const float z = chimd::hermite4(K.inv[k], a.y);
             if (!(z < CUDART_INF_F)) continue;
-            const float ap = 1.f + z, lz = chimd::hermite4(__ldg(K.linv + k), a.y);  // log2(1+z)
+            const float ap = 1.f + z, lz = chimd::hermite4(K.linv[k], a.y);  // log2(1+z)
             LogMass lm = log_mass(K.q, a.z, a.w, lo, lz);
             float wn, wd;  // the weight as a quotient
             if (w_needs64(lm) || fabsf(z - zmax) < ZMAX_GUARD) {

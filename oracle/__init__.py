@@ -103,6 +103,9 @@ def lib():
         L.orc_kde_arrays.argtypes = [C.c_int64, pd, pd, d, C.c_int64, d, C.c_int32, C.c_int32, pd]
         L.orc_event_kde3_bandwidth.argtypes = [pc, pd, C.c_int64, pd]
         L.orc_event_kde3.argtypes = [pc, pd, C.c_int64, C.c_int32, pd]
+        L.orc_dDc_dOm.argtypes = [d, d, d]
+        L.orc_dDc_dOm.restype = d
+        L.orc_grad.argtypes = [pc, pd, C.c_int, pd, pd, pi32]
         _lib = L
     return _lib
 
@@ -234,6 +237,15 @@ class Catalog:
         return dict(lnL=lnL.value, lnI=lnI[: self.n_events], xi=xi.value, neff=ne.value,
                     status=st.value)
 
+    def grad(self, theta, nthreads=0):
+        """ln L and its analytic gradient (12), the hand-derived FP64 chain
+        (Gaussian kernel, Jacobian on the grid): returns (lnL, grad, status)."""
+        lnL = C.c_double()
+        st = C.c_int32()
+        g = np.zeros(12)
+        lib().orc_grad(self.ref, _p(_th(theta)), nthreads, C.byref(lnL), _p(g), C.byref(st))
+        return lnL.value, g, st.value
+
     def grad_fd(self, theta, rel_step=1e-4, nthreads=0, hk=None):
         """Central finite differences of the oracle ln L, step rel_step*|theta_k|
         (the definition of the derivative; the oracle's gradient)."""
@@ -279,6 +291,10 @@ def dVc_dz(z, H0, Om):
 
 def Vc(z, H0, Om):
     return lib().orc_Vc(z, H0, Om)
+
+
+def dDc_dOm(z, H0, Om):
+    return lib().orc_dDc_dOm(z, H0, Om)
 
 
 def z_of_dL(d, theta):

@@ -801,3 +801,459 @@ int orc_loglike_binned(const orc_catalog *c, const double *th, const orc_hooks *
                        double *neff_out, int32_t *status) {
     return loglike_impl(c, th, hk, nthreads, 1, lnL, lnI_out, xi_out, neff_out, status);
 }
+
+/* ====================================================================== */
+/* Analytic gradient of ln L (the chain rule through Eqs. hyperlike,      */
+/* like-integrals, gw-kernel-many1d/single1d, p-cat, jacobian, bias and   */
+/* the Sec. 3.1 population), FP64, Gaussian kernel, Jacobian on the grid. */
+/* The almost-everywhere derivative: samples or injections crossing a     */
+/* mass edge or z_max, and grid points crossing a KDE support edge, make  */
+/* jumps that it does not contain.                                        */
+/* ====================================================================== */
+
+enum { P_H0 = 0, P_OM, P_XI0, P_N, P_ALPHA, P_MU, P_SG, P_MMIN, P_MMAX, P_GAM, P_KAP, P_ZP, NP = 12 };
+
+/* d D_c / d Om = (c/H0) int_0^z d(1/E)/dOm dz', d(1/E)/dOm = -((1+z)^3 - 1) / (2 E^3),
+ * with (1+z)^3 - 1 = z (3 + 3z + z^2) written without cancellation (the
+ * adaptive rule's relative tolerance would otherwise chase rounding noise) */
+static double dinvE_dOm(double z, double Om) {
+    double E = orc_E(z, Om);
+    return -0.5 * z * (3.0 + z * (3.0 + z)) / (E * E * E);
+}
+
+static double gl_seg_om(double a, double b, double Om) {
+    double m = 0.5 * (a + b), h = 0.5 * (b - a), s = 0.0;
+    for (int i = 0; i < GL_N; i++) s += gl_w[i] * dinvE_dOm(m + h * gl_x[i], Om);
+    return s * h;
+}
+
+static double gl_adapt_om(double a, double b, double whole, double Om, int depth) {
+    double m = 0.5 * (a + b);
+    double l = gl_seg_om(a, m, Om), r = gl_seg_om(m, b, Om);
+    if (depth >= 30 || fabs(l + r - whole) <= 4e-15 * fabs(l + r) + 1e-300) return l + r;
+    return gl_adapt_om(a, m, l, Om, depth + 1) + gl_adapt_om(m, b, r, Om, depth + 1);
+}
+
+double orc_dDc_dOm(double z, double H0, double Om) {
+    if (!(z > 0.0)) return 0.0;
+    return ORC_C_KMS / H0 * gl_adapt_om(0.0, z, gl_seg_om(0.0, z, Om), Om, 0);
+}
+
+/* The distance relation and its derivatives at redshift z (Eqs. dL-em,
+ * dL-mg, jacobian): d = d_L^gw, J = dd/dz, Jz = d^2 d / dz^2, and at fixed
+ * z the derivatives dd[k], dJ[k] with respect to (H0, Om, Xi0, n).        */
+typedef struct {
+    double a, E, Dc, dDc_Om, xi, d, J, Jz;
+    double dd[4], dJ[4];
+    double dv, dv_Om, dlndv_dz;   /* full-sky dV_c/dz, its Om derivative, d ln dV_c/dz / dz */
+} cosmo_d;
+
+static void cosmo_at(double z, const double *th, cosmo_d *o) {
+    const double H0 = th[P_H0], Om = th[P_OM], X0 = th[P_XI0], n = th[P_N];
+    const double cH = ORC_C_KMS / H0;
+    const double a = 1.0 + z, E = orc_E(z, Om);
+    const double Dc = orc_Dc(z, H0, Om), dDc = orc_dDc_dOm(z, H0, Om);
+    const double an = pow(a, -n);                       /* (1+z)^-n */
+    const double xi = X0 + (1.0 - X0) * an;
+    const double xi1 = -n * (1.0 - X0) * an / a;        /* dXi/dz */
+    const double xi2 = n * (n + 1.0) * (1.0 - X0) * an / (a * a);
+    const double Dc1 = cH / E;                           /* dD_c/dz */
+    const double E1 = 1.5 * Om * a * a / E;              /* dE/dz */
+    const double Dc2 = -cH * E1 / (E * E);
+    const double dinvE = dinvE_dOm(z, Om);               /* d(1/E)/dOm */
+    o->a = a; o->E = E; o->Dc = Dc; o->dDc_Om = dDc; o->xi = xi;
+    o->d = a * Dc * xi;
+    o->J = (Dc + a * Dc1) * xi + a * Dc * xi1;
+    o->Jz = 2.0 * Dc1 * xi + 2.0 * Dc * xi1 + a * Dc2 * xi + 2.0 * a * Dc1 * xi1 + a * Dc * xi2;
+    /* at fixed z: d_gw = a Dc Xi */
+    o->dd[P_H0] = -o->d / H0;
+    o->dd[P_OM] = a * dDc * xi;
+    o->dd[P_XI0] = a * Dc * (1.0 - an);
+    o->dd[P_N] = -a * Dc * (1.0 - X0) * an * log(a);
+    /* J = (Dc + a cH / E) Xi + a Dc Xi' */
+    o->dJ[P_H0] = -o->J / H0;
+    o->dJ[P_OM] = (dDc + a * cH * dinvE) * xi + a * dDc * xi1;
+    o->dJ[P_XI0] = (Dc + a * Dc1) * (1.0 - an) + a * Dc * n * an / a;
+    {
+        const double dxi_dn = -(1.0 - X0) * an * log(a);
+        const double dxi1_dn = (1.0 - X0) * an / a * (n * log(a) - 1.0);
+        o->dJ[P_N] = (Dc + a * Dc1) * dxi_dn + a * Dc * dxi1_dn;
+    }
+    o->dv = 4.0 * M_PI * cH * Dc * Dc / E;
+    o->dv_Om = 4.0 * M_PI * cH * (2.0 * Dc * dDc / E + Dc * Dc * dinvE);
+    o->dlndv_dz = Dc > 0.0 ? 2.0 * Dc1 / Dc - E1 / E : 0.0;
+}
+
+/* Mass model (Sec. 3.1) with derivatives: returns w = p(m1) p(m2|m1) (0
+ * outside the support), dlw[k] = d ln w / d theta_k at fixed source-frame
+ * masses, and *dlna = d ln w / d ln(1+z) at fixed detector-frame masses
+ * (m = m_det / (1+z)).                                                    */
+static double mass_dlog(double m1, double m2, const double *th, double lambda_g, double beta,
+                        double *dlw, double *dlna) {
+    for (int k = 0; k < NP; k++) dlw[k] = 0.0;
+    *dlna = 0.0;
+    const double alpha = th[P_ALPHA], mu = th[P_MU], sg = th[P_SG], mmin = th[P_MMIN], mmax = th[P_MMAX];
+    if (!(m1 >= mmin && m1 <= mmax && m2 >= mmin && m2 <= m1) || !(m1 > mmin)) return 0.0;
+    /* power law: m1^-alpha / Z_PL */
+    double Zpl, dZpl_da;
+    if (fabs(1.0 - alpha) < 1e-12) {
+        Zpl = log(mmax / mmin);
+        dZpl_da = -0.5 * (log(mmax) * log(mmax) - log(mmin) * log(mmin));
+    } else {
+        const double num = pow(mmax, 1.0 - alpha) - pow(mmin, 1.0 - alpha);
+        Zpl = num / (1.0 - alpha);
+        const double dnum = -log(mmax) * pow(mmax, 1.0 - alpha) + log(mmin) * pow(mmin, 1.0 - alpha);
+        dZpl_da = dnum / (1.0 - alpha) + Zpl / (1.0 - alpha);
+    }
+    const double PL = pow(m1, -alpha) / Zpl;
+    /* truncated Gaussian: N(m1; mu, sg) / [Phi(b) - Phi(a)] */
+    const double ua = (mmin - mu) / sg, ub = (mmax - mu) / sg;
+    const double phia = exp(-0.5 * ua * ua) / sqrt(2.0 * M_PI), phib = exp(-0.5 * ub * ub) / sqrt(2.0 * M_PI);
+    const double ZG = std_normal_cdf(ub) - std_normal_cdf(ua);
+    const double x = (m1 - mu) / sg;
+    const double G = ZG > 0.0 ? exp(-0.5 * x * x) / (sg * sqrt(2.0 * M_PI)) / ZG : 0.0;
+    const double p1 = (1.0 - lambda_g) * PL + lambda_g * G;
+    if (!(p1 > 0.0)) return 0.0;
+    const double cpl = (1.0 - lambda_g) / p1, cg = lambda_g / p1;  /* d p1 = cpl dPL + cg dG, over p1 */
+    /* p(m2|m1) = m2^beta / Z2, Z2 = int_{m_min}^{m1} m^beta dm */
+    double Z2;
+    if (fabs(1.0 + beta) < 1e-12) Z2 = log(m1 / mmin);
+    else Z2 = (pow(m1, 1.0 + beta) - pow(mmin, 1.0 + beta)) / (1.0 + beta);
+    const double p2 = pow(m2, beta) / Z2;
+    /* explicit parameter derivatives of ln w */
+    dlw[P_ALPHA] = cpl * PL * (-log(m1) - dZpl_da / Zpl);
+    dlw[P_MU] = cg * G * (x / sg - (phia - phib) / (sg * ZG));
+    dlw[P_SG] = cg * G * (-1.0 / sg + x * x / sg - (ua * phia - ub * phib) / (sg * ZG));
+    dlw[P_MMIN] = cpl * PL * pow(mmin, -alpha) / Zpl + cg * G * phia / (sg * ZG) + pow(mmin, beta) / Z2;
+    dlw[P_MMAX] = -cpl * PL * pow(mmax, -alpha) / Zpl - cg * G * phib / (sg * ZG);
+    /* mass derivatives: d ln w / d m1, d ln w / d m2 */
+    const double dl_dm1 = (cpl * PL * (-alpha / m1) + cg * G * (-x / sg)) - pow(m1, beta) / Z2;
+    const double dl_dm2 = beta / m2;
+    /* m = m_det / (1+z): d m / d ln(1+z) = -m */
+    *dlna = -(m1 * dl_dm1 + m2 * dl_dm2);
+    return p1 * p2;
+}
+
+/* ln psi and its derivatives (Sec. 3.1): dl[0..2] with respect to
+ * (gamma, kappa, z_p) at fixed z, *dz = d ln psi / dz.                    */
+static double psi_dlog(double z, const double *th, double *dl, double *dz) {
+    const double gam = th[P_GAM], kap = th[P_KAP], zp = th[P_ZP];
+    const double a = 1.0 + z, r = a / (1.0 + zp), rk = pow(r, gam + kap), q = rk / (1.0 + rk);
+    dl[0] = log(a) - q * log(r);
+    dl[1] = -q * log(r);
+    dl[2] = (gam + kap) * q / (1.0 + zp);
+    *dz = gam / a - (gam + kap) * q / a;
+    return pow(a, gam) / (1.0 + rk);
+}
+
+/* The Scott bandwidth of Eq. gw-kernel's reading and its derivative from
+ * the samples' dz[j][k] and dw[j][k] = d w_j / d theta_k (the same rule
+ * and fallbacks as bandwidth_of). */
+static double bandwidth_grad(int64_t n, const double *z, const double *w, const int32_t *valid,
+                             const double *dz, const double *dw, double fallback, double *dlnb) {
+    for (int k = 0; k < NP; k++) dlnb[k] = 0.0;
+    double W1 = 0.0, W2 = 0.0, Wz = 0.0;
+    for (int64_t j = 0; j < n; j++) {
+        if (!valid[j]) continue;
+        W1 += w[j]; W2 += w[j] * w[j]; Wz += w[j] * z[j];
+    }
+    if (W1 > 0.0) {
+        double mean = Wz / W1, var = 0.0;
+        for (int64_t j = 0; j < n; j++)
+            if (valid[j]) var += w[j] * (z[j] - mean) * (z[j] - mean);
+        var /= W1;
+        double neff = W1 * W1 / W2;
+        if (neff >= 2.0 && var > 0.0) {
+            for (int k = 0; k < NP; k++) {
+                double dW1 = 0.0, dW2 = 0.0, dV = 0.0;
+                for (int64_t j = 0; j < n; j++) {
+                    if (!valid[j]) continue;
+                    const double dwj = dw[j * NP + k], dzj = k < 4 ? dz[j * 4 + k] : 0.0, u = z[j] - mean;
+                    dW1 += dwj;
+                    dW2 += 2.0 * w[j] * dwj;
+                    dV += dwj * u * u + 2.0 * w[j] * u * dzj;
+                }
+                const double dvar = dV / W1 - var * dW1 / W1;
+                dlnb[k] = 0.5 * dvar / var - 0.2 * (2.0 * dW1 / W1 - dW2 / W2);
+            }
+            return sqrt(var) * pow(neff, -0.2);
+        }
+    }
+    int64_t nv = 0;
+    double s = 0.0;
+    for (int64_t j = 0; j < n; j++)
+        if (valid[j]) { nv++; s += z[j]; }
+    if (nv >= 2) {
+        double mean = s / nv, var = 0.0;
+        for (int64_t j = 0; j < n; j++)
+            if (valid[j]) var += (z[j] - mean) * (z[j] - mean);
+        var /= nv;
+        if (var > 0.0) {
+            for (int k = 0; k < 4; k++) {
+                double dV = 0.0;
+                for (int64_t j = 0; j < n; j++)
+                    if (valid[j]) dV += 2.0 * (z[j] - mean) * dz[j * 4 + k];
+                dlnb[k] = 0.5 * (dV / nv) / var;
+            }
+            return sqrt(var) * pow((double)nv, -0.2);
+        }
+    }
+    return fallback;
+}
+
+/* KDE of one sample set on the grid with its derivatives (the same sum,
+ * normalisation and support as kde_set, Gaussian kernel):
+ * dK[a*NP + k] = d K(z_a) / d theta_k.  idx: the set's sample indices.   */
+static void kde_set_grad(int64_t m, const int64_t *idx, const double *z, const double *w,
+                         const int32_t *valid, const double *dz, const double *dw, double b,
+                         const double *dlnb, int64_t nz, double z_max, double *K, double *dK) {
+    double zlo = INFINITY, zhi = -INFINITY;
+    for (int64_t q = 0; q < m; q++) {
+        int64_t j = idx[q];
+        if (valid[j]) { if (z[j] < zlo) zlo = z[j]; if (z[j] > zhi) zhi = z[j]; }
+    }
+    zlo -= ORC_KDE_MARGIN * b;
+    zhi += ORC_KDE_MARGIN * b;
+    const double norm = m > 0 ? 1.0 / (sqrt(2.0 * M_PI) * b * (double)m) : 0.0;
+    for (int64_t a = 0; a < nz; a++) {
+        double za = z_max * (double)a / (double)(nz - 1), s = 0.0, ds[NP];
+        for (int k = 0; k < NP; k++) ds[k] = 0.0;
+        if (za >= zlo && za <= zhi) {
+            for (int64_t q = 0; q < m; q++) {
+                int64_t j = idx[q];
+                if (!valid[j] || w[j] == 0.0) continue;
+                const double u = za - z[j], e = exp(-0.5 * u * u / (b * b));
+                s += w[j] * e;
+                for (int k = 0; k < NP; k++) {
+                    double t = dw[j * NP + k] + w[j] * (u * u / (b * b) - 1.0) * dlnb[k];
+                    if (k < 4) t += w[j] * u / (b * b) * dz[j * 4 + k];
+                    ds[k] += e * t;
+                }
+            }
+        }
+        K[a] = s * norm;
+        for (int k = 0; k < NP; k++) dK[a * NP + k] = ds[k] * norm;
+    }
+}
+
+/* Galaxy term of one pixel and its Om derivative (Eq. p-cat as
+ * galaxy_profile_dv; H0 cancels between dV_c/dz and Z_g). */
+static void galaxy_profile_grad(const orc_catalog *c, int64_t ev, int32_t pixel, const double *dv,
+                                const double *dv_Om, double vmax, double dlnvmax, double *G, double *dG) {
+    int64_t p = c->pix_off[ev] + pixel;
+    for (int64_t a = 0; a < c->n_z; a++) { G[a] = 0.0; dG[a] = 0.0; }
+    for (int64_t g = c->gal_off[p]; g < c->gal_off[p + 1]; g++) {
+        double zg = c->gal_z[g], sg = c->gal_sigma[g];
+        double norm = 1.0 / (sqrt(2.0 * M_PI) * sg);
+        double Z = 0.0, Zp = 0.0;
+        for (int64_t a = 0; a < c->n_z; a++) {
+            double u = (grid_z(c, a) - zg) / sg, Na = norm * exp(-0.5 * u * u);
+            Z += grid_w(c, a) * Na * dv[a];
+            Zp += grid_w(c, a) * Na * dv_Om[a];
+        }
+        if (!(Z > 0.0)) continue;
+        for (int64_t a = 0; a < c->n_z; a++) {
+            double u = (grid_z(c, a) - zg) / sg, Na = norm * exp(-0.5 * u * u);
+            G[a] += Na / Z;
+            dG[a] -= Na * Zp / (Z * Z);
+        }
+    }
+    for (int64_t a = 0; a < c->n_z; a++) {
+        const double S = G[a], dS = dG[a];
+        G[a] = dv[a] * S / c->n_gal_total;
+        dG[a] = (dv_Om[a] * S + dv[a] * dS) / c->n_gal_total;
+    }
+    if (c->completeness) {
+        const double area = c->pix_area[p] / (4.0 * M_PI);
+        const double *P = c->completeness + p * c->n_z;
+        for (int64_t a = 0; a < c->n_z; a++) {
+            const double miss = area * (1.0 - P[a]) * dv[a] / vmax;
+            const double dmiss = area * (1.0 - P[a]) * (dv_Om[a] / vmax - dv[a] / vmax * dlnvmax);
+            G[a] = c->f_R * G[a] + miss;
+            dG[a] = c->f_R * dG[a] + dmiss;
+        }
+    }
+}
+
+/* ln I_i and d ln I_i / d theta (Eq. like-integrals). */
+static double event_grad(const orc_catalog *c, const double *th, int64_t ev, const double *F,
+                         const double *dlnF, const double *dv, const double *dv_Om, double vmax,
+                         double dlnvmax, double *dlnI) {
+    const int64_t j0 = c->sample_off[ev], n = c->sample_off[ev + 1] - j0, nz = c->n_z;
+    const int32_t npix = (int32_t)(c->pix_off[ev + 1] - c->pix_off[ev]);
+    double *z = malloc(sizeof(double) * (n + 1)), *w = malloc(sizeof(double) * (n + 1));
+    int32_t *v = malloc(sizeof(int32_t) * (n + 1));
+    double *dz = calloc((size_t)(n + 1) * 4, sizeof(double)), *dw = calloc((size_t)(n + 1) * NP, sizeof(double));
+    int64_t *idx = malloc(sizeof(int64_t) * (n + 1));
+    double *K = malloc(sizeof(double) * nz), *dK = malloc(sizeof(double) * nz * NP);
+    double *G = malloc(sizeof(double) * nz), *dG = malloc(sizeof(double) * nz);
+    double *Gs = calloc((size_t)nz, sizeof(double)), *dGs = calloc((size_t)nz, sizeof(double));
+    for (int64_t j = 0; j < n; j++) {
+        double zj = 0.0;
+        v[j] = orc_z_of_dL(c->dL[j0 + j], th, &zj) == 0;
+        z[j] = v[j] ? zj : 0.0;
+        w[j] = 0.0;
+        if (!v[j]) continue;
+        cosmo_d cd;
+        cosmo_at(zj, th, &cd);
+        for (int k = 0; k < 4; k++) dz[j * 4 + k] = -cd.dd[k] / cd.J;   /* d_gw(z_j) = d_L,j */
+        double dlw[NP], dlna;
+        const double a = 1.0 + zj;
+        w[j] = mass_dlog(c->m1d[j0 + j] / a, c->m2d[j0 + j] / a, th, c->lambda_g, c->beta, dlw, &dlna);
+        for (int k = 0; k < NP; k++) {
+            double t = dlw[k];
+            if (k < 4) t += dlna / a * dz[j * 4 + k];
+            dw[j * NP + k] = w[j] * t;
+        }
+    }
+    double dlnb[NP];
+    const double b = bandwidth_grad(n, z, w, v, dz, dw, grid_dz(c), dlnb);
+    double I = 0.0, dI[NP];
+    for (int k = 0; k < NP; k++) dI[k] = 0.0;
+    if (c->kde_mode == ORC_KDE_MANY_1D) {
+        for (int32_t k = 0; k < npix; k++) {
+            int64_t m = 0;
+            for (int64_t j = 0; j < n; j++)
+                if (c->pix_of_sample[j0 + j] == k) idx[m++] = j;
+            const double S = c->sky_S[c->pix_off[ev] + k];
+            kde_set_grad(m, idx, z, w, v, dz, dw, b, dlnb, nz, c->z_max, K, dK);
+            galaxy_profile_grad(c, ev, k, dv, dv_Om, vmax, dlnvmax, G, dG);
+            for (int64_t a = 0; a < nz; a++) {
+                const double wa = grid_w(c, a) * S;
+                I += wa * K[a] * F[a] * G[a];
+                for (int q = 0; q < NP; q++) {
+                    double t = dK[a * NP + q] * F[a] * G[a] + K[a] * F[a] * dlnF[a * NP + q] * G[a];
+                    if (q == P_OM) t += K[a] * F[a] * dG[a];
+                    dI[q] += wa * t;
+                }
+            }
+        }
+    } else {
+        for (int64_t j = 0; j < n; j++) idx[j] = j;
+        kde_set_grad(n, idx, z, w, v, dz, dw, b, dlnb, nz, c->z_max, K, dK);
+        for (int32_t k = 0; k < npix; k++) {
+            const double S = c->sky_S[c->pix_off[ev] + k];
+            galaxy_profile_grad(c, ev, k, dv, dv_Om, vmax, dlnvmax, G, dG);
+            for (int64_t a = 0; a < nz; a++) { Gs[a] += S * G[a]; dGs[a] += S * dG[a]; }
+        }
+        for (int64_t a = 0; a < nz; a++) {
+            const double wa = grid_w(c, a);
+            I += wa * K[a] * F[a] * Gs[a];
+            for (int q = 0; q < NP; q++) {
+                double t = dK[a * NP + q] * F[a] * Gs[a] + K[a] * F[a] * dlnF[a * NP + q] * Gs[a];
+                if (q == P_OM) t += K[a] * F[a] * dGs[a];
+                dI[q] += wa * t;
+            }
+        }
+    }
+    for (int q = 0; q < NP; q++) dlnI[q] = I > 0.0 ? dI[q] / I : 0.0;
+    free(z); free(w); free(v); free(dz); free(dw); free(idx); free(K); free(dK); free(G); free(dG);
+    free(Gs); free(dGs);
+    return (I > 0.0 && isfinite(I)) ? log(I) : -INFINITY;
+}
+
+/* xi (Eq. bias, Monte Carlo sum) and d ln xi / d theta. */
+static double selection_grad(const orc_catalog *c, const double *th, double vmax, double dlnvmax,
+                             int nthreads, double *dlnxi) {
+    const int64_t n = c->n_det;
+    double *s = malloc(sizeof(double) * (n + 1)), *ds = calloc((size_t)(n + 1) * NP, sizeof(double));
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 256)
+#endif
+    for (int64_t j = 0; j < n; j++) {
+        s[j] = 0.0;
+        double z = 0.0;
+        if (orc_z_of_dL(c->inj_dL[j], th, &z) != 0 || !(z <= c->z_max)) continue;
+        const double a = 1.0 + z;
+        double dlw[NP], dlna, dpsi[3], dpsi_z;
+        const double w = mass_dlog(c->inj_m1d[j] / a, c->inj_m2d[j] / a, th, c->lambda_g, c->beta, dlw, &dlna);
+        if (!(w > 0.0)) continue;
+        cosmo_d cd;
+        cosmo_at(z, th, &cd);
+        const double psi = psi_dlog(z, th, dpsi, &dpsi_z);
+        const double pz = cd.dv / vmax;
+        s[j] = w * psi * pz / (a * a * a * fabs(cd.J) * exp(c->inj_log_pi[j]));
+        /* d ln s / dz at fixed theta and detector-frame masses */
+        const double dls_dz = dlna / a + dpsi_z + cd.dlndv_dz - 3.0 / a - cd.Jz / cd.J;
+        double g[NP];
+        for (int k = 0; k < NP; k++) g[k] = dlw[k];
+        g[P_GAM] += dpsi[0];
+        g[P_KAP] += dpsi[1];
+        g[P_ZP] += dpsi[2];
+        g[P_OM] += (cd.Dc > 0.0 ? cd.dv_Om / cd.dv : 0.0) - dlnvmax;  /* p_z at fixed z */
+        for (int k = 0; k < 4; k++) {
+            const double dzk = -cd.dd[k] / cd.J;
+            g[k] += -cd.dJ[k] / cd.J + dls_dz * dzk;
+        }
+        for (int k = 0; k < NP; k++) ds[j * NP + k] = s[j] * g[k];
+    }
+    double S1 = neumaier(s, n);
+    for (int k = 0; k < NP; k++) {
+        double acc = 0.0, comp = 0.0;
+        for (int64_t j = 0; j < n; j++) {  /* Neumaier over the column */
+            double x = ds[j * NP + k], t = acc + x;
+            if (fabs(acc) >= fabs(x)) comp += (acc - t) + x; else comp += (x - t) + acc;
+            acc = t;
+        }
+        dlnxi[k] = S1 > 0.0 ? (acc + comp) / S1 : 0.0;
+    }
+    free(s); free(ds);
+    return S1 / (double)c->n_inj_total;
+}
+
+/* ln L (Eq. hyperlike) and its gradient with respect to the 12 parameters.
+ * Gaussian kernel with the Jacobian on the grid, many-1D or single-1D,
+ * complete or incomplete catalog; an inadmissible or non-monotone point has
+ * ln L = -inf and gradient 0. */
+int orc_grad(const orc_catalog *c, const double *th, int nthreads, double *lnL, double *grad,
+             int32_t *status) {
+    for (int k = 0; k < NP; k++) grad[k] = 0.0;
+    *status = ORC_OK;
+    if (orc_check_theta(th)) { *lnL = -INFINITY; *status = ORC_OUT_OF_SUPPORT; return 0; }
+    if (!orc_monotone(th)) { *lnL = -INFINITY; *status = ORC_NONMONOTONE; return 0; }
+    const int64_t ne = c->n_events, nz = c->n_z;
+    double *F = malloc(sizeof(double) * nz), *dlnF = calloc((size_t)nz * NP, sizeof(double));
+    double *dv = malloc(sizeof(double) * nz), *dv_Om = malloc(sizeof(double) * nz);
+    for (int64_t a = 0; a < nz; a++) {
+        const double za = grid_z(c, a);
+        cosmo_d cd;
+        cosmo_at(za, th, &cd);
+        double dpsi[3], dpsi_z;
+        const double psi = psi_dlog(za, th, dpsi, &dpsi_z), ap = 1.0 + za;
+        F[a] = psi / (ap * ap * ap * fabs(cd.J));
+        for (int k = 0; k < 4; k++) dlnF[a * NP + k] = -cd.dJ[k] / cd.J;
+        dlnF[a * NP + P_GAM] = dpsi[0];
+        dlnF[a * NP + P_KAP] = dpsi[1];
+        dlnF[a * NP + P_ZP] = dpsi[2];
+        dv[a] = cd.dv;
+        dv_Om[a] = cd.dv_Om;
+    }
+    const double Dm = orc_Dc(c->z_max, th[P_H0], th[P_OM]);
+    const double vmax = orc_Vc(c->z_max, th[P_H0], th[P_OM]);
+    const double dlnvmax = 3.0 * orc_dDc_dOm(c->z_max, th[P_H0], th[P_OM]) / Dm;
+    double *lnI = malloc(sizeof(double) * (ne + 1)), *dlnI = malloc(sizeof(double) * (ne + 1) * NP);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t i = 0; i < ne; i++)
+        lnI[i] = event_grad(c, th, i, F, dlnF, dv, dv_Om, vmax, dlnvmax, dlnI + i * NP);
+    double dlnxi[NP];
+    const double xi = selection_grad(c, th, vmax, dlnvmax, nthreads, dlnxi);
+    int bad = !(xi > 0.0);
+    for (int64_t i = 0; i < ne; i++) bad |= !isfinite(lnI[i]);
+    if (bad) {
+        *lnL = -INFINITY;
+        *status = ORC_OUT_OF_SUPPORT;
+    } else {
+        *lnL = neumaier(lnI, ne) - (double)ne * log(xi);
+        for (int k = 0; k < NP; k++) {
+            double acc = 0.0;
+            for (int64_t i = 0; i < ne; i++) acc += dlnI[i * NP + k];
+            grad[k] = acc - (double)ne * dlnxi[k];
+        }
+    }
+    free(F); free(dlnF); free(dv); free(dv_Om); free(lnI); free(dlnI);
+    return 0;
+}

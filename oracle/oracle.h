@@ -150,6 +150,16 @@ int orc_loglike_binned(const orc_catalog *c, const double *th, const orc_hooks *
                        int nthreads, double *lnL, double *lnI, double *xi,
                        double *neff, int32_t *status);
 
+/* ---- analytic gradient (Gaussian kernel, Jacobian on the grid) ----
+ * ln L and d ln L / d theta (12) by the chain rule written out in FP64:
+ * the distance relation and its inversion, the mass model, Scott's rule,
+ * the KDE, the galaxy term, the grid factor and the selection term.  The
+ * almost-everywhere derivative (mass-edge, z_max and KDE-support jumps are
+ * not contained).  orc_dDc_dOm: d D_c / d Om by adaptive quadrature. */
+double orc_dDc_dOm(double z, double H0, double Om);
+int orc_grad(const orc_catalog *c, const double *th, int nthreads, double *lnL, double *grad,
+             int32_t *status);
+
 #ifdef __cplusplus
 }
 #endif

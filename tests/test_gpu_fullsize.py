@@ -11,7 +11,8 @@ properties that hold at any size.
   Sampled events (with their own Om) against the oracle; the gradient is
   additive over disjoint event sets sharing the injections,
   grad(A u B) = grad(A) + grad(B), which checks the full-size adjoint launch
-  against two independent half-size launches.
+  against two independent half-size launches; the first 50 events with
+  all the injections are compared with the oracle's analytic gradient.
 Tolerances are those of the mixed path (per event |Delta ln I| <= 1e-4,
 |Delta ln xi| <= 3e-6).
 """
@@ -127,6 +128,31 @@ def test_differentiation_catalog_sampled_events(chim, ctx, orc, c4):
                 assert abs(terms["lnI"][h, ev] - ref) <= MIX_EV, (h, ev, terms["lnI"][h, ev] - ref)
         xi, _ = oc.selection(th[40])
         assert abs(math.log(terms["xi"][40]) - math.log(xi)) <= 3e-6
+    finally:
+        ctx.unload(cid)
+
+
+def test_differentiation_subset_gradient_vs_oracle_gradient(chim, ctx, orc, c4):
+    """The first 50 events of the differentiation catalog with all its
+    injections: ln L and the 12-component gradient of two hyperpoints (Om
+    varying) against the oracle's analytic gradient, FP64 and mixed."""
+    cat = _subset(c4, list(range(50)))
+    th = sc.config_hyperpoints(4)
+    oc = orc.Catalog(cat)
+    cid = ctx.load(cat)
+    try:
+        for h in (1, 40):
+            t = th[h]
+            lo, go, so = oc.grad(t)
+            if not math.isfinite(lo):
+                continue
+            l64, g64, s64 = ctx.grad(cid, t[None, :], chim.FP64)
+            lm, gm, sm = ctx.grad(cid, t[None, :], chim.MIXED)
+            assert s64[0] == so and sm[0] == so
+            assert abs(l64[0] - lo) <= 1e-6 * cat["n_events"] and abs(lm[0] - lo) <= 1e-3
+            for k in range(12):
+                assert abs(g64[0, k] - go[k]) <= 1e-6 * abs(go[k]) + 1e-6 / abs(t[k]), ("fp64", h, k, g64[0, k], go[k])
+                assert abs(gm[0, k] - go[k]) <= 2e-3 * abs(go[k]) + 1e-2 / abs(t[k]), ("mixed", h, k, gm[0, k], go[k])
     finally:
         ctx.unload(cid)
 

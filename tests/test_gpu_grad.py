@@ -1,4 +1,6 @@
-"""GPU adjoint (chimera_grad) against the oracle's central finite differences.
+"""GPU adjoint (chimera_grad) against the oracle's gradient: the analytic one
+(orc_grad, the hand-derived FP64 chain) and the central finite differences of
+the oracle's ln L.
 
 The adjoint returns the almost-everywhere derivative: samples or injections
 that cross a mass edge (m_min, m_max) or the selection's z_max under a
@@ -15,7 +17,11 @@ that crosses them, i.e. <= ~1e-8 / (2 h theta_k) in the derivative.  We
 require |g_gpu - g_fd| <= 2e-5 |g_fd| + 1e-4 / |theta_k| (FP64 path).  The
 mixed path follows its own computed ln L (FP32 z and weights, FP32 KDE and
 profile); its gradient must match the FP64 adjoint to 2e-3 relative plus
-1e-2 / |theta_k|.
+1e-2 / |theta_k|.  Against the analytic oracle gradient (both FP64, both the
+almost-everywhere derivative): the FP64 adjoint within 1e-6 relative +
+1e-6 / |theta_k| (the GPU's windows and interpolated distance tables against
+the oracle's full grid and adaptive quadrature), the mixed adjoint within the
+mixed tolerance above.
 """
 import math
 
@@ -23,6 +29,7 @@ import numpy as np
 import pytest
 
 from synth import catalog as sc
+from _edges import edge_free
 
 pytestmark = pytest.mark.gpu
 
@@ -42,48 +49,6 @@ def ctx(chim):
     c = chim.Context(0)
     yield c
     c.close()
-
-
-def _z_of_dgw(d, th, zmax=12.0, npts=400001):
-    """Generous numerical inverse of Eq. dL-mg (trapezoid table), used only to
-    decide which samples sit near an edge."""
-    H0, Om, Xi0, n = th[:4]
-    z = np.linspace(0.0, zmax, npts)
-    inv_e = 1.0 / np.sqrt(Om * (1.0 + z) ** 3 + 1.0 - Om)
-    dc = np.concatenate([[0.0], np.cumsum(0.5 * (inv_e[1:] + inv_e[:-1]) * np.diff(z))]) * C_KMS / H0
-    dgw = (1.0 + z) * dc * (Xi0 + (1.0 - Xi0) / (1.0 + z) ** n)
-    return np.interp(d, dgw, z)
-
-
-def edge_free(cat, th, margin=0.01):
-    """Copy of `cat` without the samples / injections near a mass or z_max edge."""
-    mmin, mmax = th[7], th[8]
-
-    def near(m1d, m2d, dL):
-        a = 1.0 + _z_of_dgw(dL, th)
-        m1, m2 = m1d / a, m2d / a
-        bad = np.zeros(m1.shape, bool)
-        for m in (m1, m2):
-            for e in (mmin, mmax):
-                bad |= np.abs(m / e - 1.0) < margin
-        return bad, a - 1.0
-
-    out = dict(cat)
-    bad, _ = near(cat["m1_det"], cat["m2_det"], cat["dL"])
-    so = cat["sample_off"]
-    keep = ~bad
-    # keep at least two samples per event
-    for e in range(cat["n_events"]):
-        assert keep[so[e]:so[e + 1]].sum() >= 2
-    counts = np.array([keep[so[e]:so[e + 1]].sum() for e in range(cat["n_events"])])
-    out["sample_off"] = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
-    for k in ("dL", "m1_det", "m2_det", "pix_of_sample"):
-        out[k] = np.ascontiguousarray(cat[k][keep])
-    ibad, zi = near(cat["inj_m1d"], cat["inj_m2d"], cat["inj_dL"])
-    ibad |= np.abs(zi / cat["z_max"] - 1.0) < margin
-    for k in ("inj_dL", "inj_m1d", "inj_m2d", "inj_log_pi"):
-        out[k] = np.ascontiguousarray(cat[k][~ibad])
-    return out
 
 
 def _check_fd(g, gfd, th, rtol, atol_scale, what):
@@ -112,8 +77,11 @@ def test_fp64_adjoint_matches_oracle_fd_many1d(chim, ctx, orc, xi0):
         ref = oc.loglike(t)
         assert abs(lnL[0] - ref["lnL"]) <= 1e-6 * cat["n_events"]
         _check_fd(g[0], gfd, t, 2e-5, 1e-4, "fp64-many1d")
-        # mixed adjoint against the FP64 adjoint
+        lo, go, so = oc.grad(t)
+        _check_fd(g[0], go, t, 1e-6, 1e-6, "fp64-vs-oracle-grad")
+        # mixed adjoint against the oracle's gradient and the FP64 adjoint
         lnLm, gm, stm = ctx.grad(cid, t[None, :], chim.MIXED)
+        _check_fd(gm[0], go, t, 2e-3, 1e-2, "mixed-vs-oracle-grad")
         _check_fd(gm[0], g[0], t, 2e-3, 1e-2, "mixed-vs-fp64")
     finally:
         ctx.unload(cid)
@@ -132,7 +100,10 @@ def test_fp64_adjoint_matches_oracle_fd_single1d(chim, ctx, orc):
     try:
         lnL, g, st = ctx.grad(cid, t[None, :], chim.FP64)
         _check_fd(g[0], gfd, t, 2e-5, 1e-4, "fp64-single1d")
+        lo, go, so = oc.grad(t)
+        _check_fd(g[0], go, t, 1e-6, 1e-6, "fp64-vs-oracle-grad-single1d")
         lnLm, gm, stm = ctx.grad(cid, t[None, :], chim.MIXED)
+        _check_fd(gm[0], go, t, 2e-3, 1e-2, "mixed-vs-oracle-grad-single1d")
         _check_fd(gm[0], g[0], t, 2e-3, 1e-2, "mixed-vs-fp64-single1d")
     finally:
         ctx.unload(cid)

@@ -14,7 +14,8 @@ import pytest
 
 from synth import catalog as sc
 
-from test_gpu_grad import _check_fd, edge_free
+from _edges import edge_free
+from test_gpu_grad import _check_fd
 
 pytestmark = pytest.mark.gpu
 
@@ -104,7 +105,10 @@ def test_incomplete_adjoint_matches_oracle_fd(chim, ctx, orc):
         lnL, g, st = ctx.grad(cid, t[None, :], chim.FP64)
         assert abs(lnL[0] - oc.loglike(t)["lnL"]) <= 1e-6 * cat["n_events"]
         _check_fd(g[0], gfd, t, 2e-5, 1e-4, "fp64-incomplete")
+        _, go, _ = oc.grad(t)
+        _check_fd(g[0], go, t, 1e-6, 1e-6, "fp64-vs-oracle-grad-incomplete")
         _, gm, _ = ctx.grad(cid, t[None, :], chim.MIXED)
+        _check_fd(gm[0], go, t, 2e-3, 1e-2, "mixed-vs-oracle-grad-incomplete")
         _check_fd(gm[0], g[0], t, 2e-3, 1e-2, "mixed-vs-fp64-incomplete")
     finally:
         ctx.unload(cid)

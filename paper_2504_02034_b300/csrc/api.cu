@@ -688,6 +688,8 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     c.dz_lo32 = (float)(c.dz - (double)c.dz32);
     c.n_gal_total = d->n_gal_total;
     c.lambda_g = d->lambda_g;
+    c.ln_lambda = d->lambda_g > 0.0 ? std::log(d->lambda_g) : 0.0;
+    c.ln1m_lambda = d->lambda_g < 1.0 ? std::log1p(-d->lambda_g) : 0.0;
     c.beta = d->beta;
     c.max_ns = max_ns;
     c.max_npix = max_np;

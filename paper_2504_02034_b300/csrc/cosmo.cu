@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
     if (blockIdx.x != 0) return;
     // the FP64 scalars, one warp each (lane 0), so that their transcendental
     // chains run side by side instead of serialised by divergence
-    __shared__ double sc[12];
+    __shared__ double sc[20];
     const double *th = p.theta + 12 * h;
     const double alpha = th[4], mu = th[5], sg = th[6], mmin = th[7], mmax = th[8];
     const double lam = c.lambda_g, beta = c.beta;
@@ -318,10 +318,20 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
             case 0:
                 v = fabs(1.0 - alpha) < 1e-12 ? log(mmax / mmin)
                                               : (pow(mmax, 1.0 - alpha) - pow(mmin, 1.0 - alpha)) / (1.0 - alpha);
+                sc[12] = log(v);  // ln of the power law's normalisation integral
                 break;
-            case 1: v = std_normal_cdf((mmax - mu) / sg) - std_normal_cdf((mmin - mu) / sg); break;
-            case 2: v = pow(mmin, 1.0 + beta); break;
-            case 3: v = chimd::dc_hermite(p.fwd[h], c.z_max, th[1]); break;
+            case 1:
+                v = std_normal_cdf((mmax - mu) / sg) - std_normal_cdf((mmin - mu) / sg);
+                sc[13] = v > 0.0 ? log(v) : 0.0;
+                break;
+            case 2:
+                v = pow(mmin, 1.0 + beta);
+                sc[14] = log(fabs(1.0 + beta) < 1e-12 ? 1.4426950408889634074 : fabs(1.0 + beta));
+                break;
+            case 3:
+                v = chimd::dc_hermite(p.fwd[h], c.z_max, th[1]);
+                sc[15] = log(3.0 / (v * v * v));
+                break;
             case 4: {  // d_L^gw at the end of the redshift range, z = 10, in FP64
                 double J;
                 chimd::dgw_J(K_Z10 * HT, cH * p.fwd[h][K_Z10], th, cH, &v, &J);
@@ -331,18 +341,21 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
             case 5:
                 v = log(mmin);
                 sc[9] = log1p(th[11]);
+                sc[16] = log(th[0] / C_KMS);
                 break;
             case 6:
                 v = log2(mmin);
                 sc[10] = 1.0 / sg;
+                sc[17] = pow(mmin, alpha);
+                sc[18] = log(sg);
                 break;
             default:
                 v = log2(mmax);
                 // ln of the constant factor of the mixed path's raw event
                 // integral: dz F_scale / (N_gal,tot sqrt(2 pi)), times 1/b per event
                 // (the mixed F32 holds F c / H0 unless the Jacobian sits on the samples)
-                sc[11] = log(c.dz * Fs / (c.n_gal_total * 2.50662827463100050242)) -
-                         (p.jac_ps ? 0.0 : log(cH));
+                sc[11] = log(c.dz * Fs / (c.n_gal_total * 2.50662827463100050242)) +
+                         (p.jac_ps ? 0.0 : log(th[0] / C_KMS));
                 break;
         }
         sc[w] = v;
@@ -371,17 +384,22 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
             hp.f_valid = (float)(tv - hp.k_valid);
         }
         // the mixed path's mass model relative to its shared normalisation
+        // (the logs come from the warps above; only sums and products here)
         const bool logp2 = fabs(hp.b1) < 1e-12;
-        double C1 = hp.c_pl > 0.0 ? hp.c_pl : hp.c_g;
-        if (!(C1 > 0.0)) C1 = 1.0;
-        const double mmin_a = pow(mmin, alpha);  // m_min^alpha
+        const bool use_pl = hp.c_pl > 0.0;
+        double C1 = use_pl ? hp.c_pl : hp.c_g;
+        double lnC1 = use_pl ? c.ln1m_lambda - sc[12]
+                             : c.ln_lambda - sc[18] - 0.91893853320467274178 - sc[13];  // ln(lam / (sg sqrt(2 pi) den))
+        if (!(C1 > 0.0)) { C1 = 1.0; lnC1 = 0.0; }
+        const double mmin_a = sc[17];  // m_min^alpha
         const double wscale = C1 / (mmin_a * mmin) * (logp2 ? 1.4426950408889634074 : fabs(hp.b1));
-        hp.ln_wscale = log(wscale);
+        hp.ln_wscale = lnC1 - alpha * sc[5] - sc[5] + sc[14];
         hp.inv_wscale = 1.0 / wscale;
         hp.ln_k0 = sc[11] + hp.ln_wscale;
         // s_j = w_scale (3 / Dhat(z_max)^3) (H0 / c) x the mixed selection
         // kernel's relative term (Dhat = D_c H0 / c)
-        hp.ln_sel = hp.ln_wscale + log(3.0 / (sc[3] * sc[3] * sc[3])) + log(th[0] / C_KMS);
+        hp.ln_sel = hp.ln_wscale + sc[15] + sc[16];
+        hp.sel_cfac = exp(hp.ln_sel + c.ln_ipi_shift);
         hp.r_pl32 = (float)(hp.c_pl / C1);
         hp.r_g32 = (float)(hp.c_g / C1 * mmin_a);
         hp.na2 = split_f2(-alpha);

@@ -230,8 +230,10 @@ __device__ __forceinline__ float small_group(const float *z, const float *w, int
         float k = 0.f;
         for (int j = 0; j < cnt; j++) {
             const float d = za - z[j];
-            const float x = d * inv_s2b;
-            const float e = expc(-x * x);
+            const float x = d * inv_s2b, x2 = x * x;
+            // SFU ex2 with log2 e as a pair (these groups hold ~0.5 % of the
+            // pairs: the SFU's own mean error is immaterial here)
+            const float e = ex2(fmaf(-x2, L2E_HI, -x2 * L2E_LO));
             k = fabsf(d) <= halfk ? fmaf(w[j], e, k) : k;
         }
         acc = fmaf(k, h, acc);
@@ -322,12 +324,13 @@ constexpr int RW_THREADS = 256;
 #define CHIM_RW_INFLIGHT 2
 #endif
 #ifndef CHIM_RW_MINB
-#define CHIM_RW_MINB 3
+#define CHIM_RW_MINB 4
 #endif
 #ifndef CHIM_RW_SMEMQ
 #define CHIM_RW_SMEMQ 0
 #endif
 constexpr int RW_INFLIGHT = CHIM_RW_INFLIGHT;  // samples per thread in flight
+constexpr int RW_SPEC_CAP = 256;               // deferred (FP64-weight) samples listed per block
 constexpr int RW_MINB = CHIM_RW_MINB;          // resident blocks per SM asked of the compiler
 // 1 / [(1+z)^3 |d d_L^gw/dz|] at a sample (Eq. jacobian), FP32, from its
 // d_L (D_c = d_L / ((1+z) Xi)) and lz = log2(1+z).
@@ -402,16 +405,32 @@ __global__ void __launch_bounds__(RW_THREADS, RW_MINB) k_reweight(DevCatalog c, 
     // (mass.cuh), moments; invalid samples (beyond d_L^gw(10)) get z = inf
     // and w = 0 and stay out of the moments.  Near a mass edge the in-range
     // test is taken in FP64 from the sample's FP64 distance and masses.
+    // Samples whose weight needs FP64 (guard bands at the mass edges, the
+    // corner band above m_min; a few in a thousand at most) are deferred to
+    // a list and taken after the loop, so that the loop itself carries no
+    // FP64 call (whose register saves would cost every sample).
+    __shared__ int s_nspec;
+    __shared__ int s_spec[RW_SPEC_CAP];
+    if (tid == 0) s_nspec = 0;
+    __syncthreads();
+    auto jac = [&](float w, float z, float lz, const float4 &sv) {
+        if (JAC) {  // the Jacobian on the sample (the moments keep w)
+            const float t = (float)__float_as_int(sv.x) + sv.y, u = t * (1.f / NU);
+            w *= jac_inv32(hp, z, lz, dtop * u * u);
+        }
+        return w;
+    };
     auto sample = [&](const float4 &sv, const float4 &nd, const float4 &ndl, int j) {
         const float z = chimd::hermite4(nd, sv.y);
         const bool ok = z < CUDART_INF_F;  // false for inf and NaN
         const float lz = chimd::hermite4(ndl, sv.y);  // log2(1+z) from its own node pairs
-        LogMass lm = log_mass(q, sv.z, sv.w, __ldg(c.s32lo + s0 + j), lz);
+        const LogMass lm = log_mass(q, sv.z, sv.w, __ldg(c.s32lo + s0 + j), lz);
+        const bool inr = w_in_range(lm);
         float w = 0.f;
-        if (ok && w_needs64(lm)) {
-            w = mass_weight_rel64(p, h, hp, c.beta, z, c.sd64[s0 + j], c.sm1_64[s0 + j], c.sm2_64[s0 + j]);
-        } else if (ok && w_in_range(lm)) {
-            if (lm.d1 < W_FP64) lm.d1 = corner_d1(p, h, hp, z, c.sd64[s0 + j], c.sm1_64[s0 + j], lm.d1);
+        if (ok && (w_needs64(lm) || (inr && lm.d1 < W_FP64))) {
+            const int slot = atomicAdd(&s_nspec, 1);
+            if (slot < RW_SPEC_CAP) s_spec[slot] = j;  // beyond the cap: the rescan below
+        } else if (ok && inr) {
             // rcp.approx: mean relative error +4e-9 on B300 (measured), no shared bias to speak of
             const WQuot wq = mass_weight_rel(q, lm);
             w = __fdividef(wq.num, wq.den);
@@ -422,17 +441,33 @@ __global__ void __launch_bounds__(RW_THREADS, RW_MINB) k_reweight(DevCatalog c, 
         m[0] += w; m[1] += wd_; m[2] = fmaf(wd_, d, m[2]); m[3] = fmaf(w, w, m[3]);
         m[4] += ok ? 1.f : 0.f; m[5] += d; m[6] = fmaf(d, d, m[6]);
         zd[j] = ok ? z : CUDART_INF_F;
-        if (JAC && ok) {  // the Jacobian on the sample (the moments above keep w)
-            const float t = (float)__float_as_int(sv.x) + sv.y, u = t * (1.f / NU);
-            w *= jac_inv32(hp, z, lz, dtop * u * u);
-        }
-        wd[j] = w;
+        wd[j] = ok ? jac(w, z, lz, sv) : 0.f;
     };
     auto node = [&](const float4 &sv, float4 &nl) {
         const int k = __float_as_int(sv.x);
         const bool valid = (k < q.kv) || (k == q.kv && sv.y <= q.fv);
         nl = valid ? linv[k - koff] : make_float4(0.f, 0.f, 0.f, 0.f);
         return valid ? inv[k - koff] : make_float4(CUDART_INF_F, 0.f, 0.f, 0.f);
+    };
+    // the deferred weight of sample j (in FP64 where needed) and its moments
+    auto special = [&](int j) {
+        const float4 sv = __ldg(sp + j);
+        float4 nl;
+        const float4 nd = node(sv, nl);
+        const float z = chimd::hermite4(nd, sv.y), lz = chimd::hermite4(nl, sv.y);
+        LogMass lm = log_mass(q, sv.z, sv.w, __ldg(c.s32lo + s0 + j), lz);
+        float w = 0.f;
+        if (w_needs64(lm)) {
+            w = mass_weight_rel64(p, h, hp, c.beta, z, c.sd64[s0 + j], c.sm1_64[s0 + j], c.sm2_64[s0 + j]);
+        } else {
+            lm.d1 = corner_d1(p, h, hp, z, c.sd64[s0 + j], c.sm1_64[s0 + j], lm.d1);
+            const WQuot wq = mass_weight_rel(q, lm);
+            w = __fdividef(wq.num, wq.den);
+            w = w > 0.f ? w : 0.f;
+        }
+        const float d = z - zref, wd_ = w * d;
+        m[0] += w; m[1] += wd_; m[2] = fmaf(wd_, d, m[2]); m[3] = fmaf(w, w, m[3]);
+        wd[j] = jac(w, z, lz, sv);
     };
     int j = tid;
     // RW_INFLIGHT samples per thread in flight: loads first, then the arithmetic
@@ -450,6 +485,22 @@ __global__ void __launch_bounds__(RW_THREADS, RW_MINB) k_reweight(DevCatalog c, 
         float4 nl;
         const float4 nd = node(sv, nl);
         sample(sv, nd, nl, j);
+    }
+    __syncthreads();
+    const int nspec = s_nspec;
+    if (nspec <= RW_SPEC_CAP) {
+        for (int i = tid; i < nspec; i += RW_THREADS) special(s_spec[i]);
+    } else {
+        // more deferred samples than the list holds: find them all again
+        for (int jj = tid; jj < ns; jj += RW_THREADS) {
+            const float4 sv = __ldg(sp + jj);
+            float4 nl;
+            const float4 nd = node(sv, nl);
+            const float z = chimd::hermite4(nd, sv.y);
+            if (!(z < CUDART_INF_F)) continue;
+            const LogMass lm = log_mass(q, sv.z, sv.w, __ldg(c.s32lo + s0 + jj), chimd::hermite4(nl, sv.y));
+            if (w_needs64(lm) || (w_in_range(lm) && lm.d1 < W_FP64)) special(jj);
+        }
     }
     block_sum<7, RW_THREADS>(m, red);
     if (tid == 0) {
@@ -548,12 +599,14 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
     __syncthreads();
     const double bd = p.bw[out];  // the reweighting kernel's FP32 bandwidth
     const float b = (float)bd;
-    // 1/(sqrt2 b) and dz/(sqrt2 b) from FP64 (rounded once; their float
-    // products would scale every Gaussian of the event alike)
-    const double is2b = 0.70710678118654752440 / bd;
-    const float inv_s2b = (float)is2b;
-    const float ds = (float)(c.dz * is2b);
+    // 1/(sqrt2 b) and dz/(sqrt2 b) with 1/sqrt2 and dz as float pairs, so
+    // that no constant rounded to float scales every Gaussian of the event
+    // alike (FP32 only: an FP64 division in every thread would cost B300's
+    // FP64 pipe more than the rest of the prologue)
+    const float ib = 1.f / b;
+    const float inv_s2b = fmaf(0.707106769084930419921875f, ib, 1.2101617042e-8f * ib);
     const float dz_lo = c.dz_lo32;
+    const float ds = fmaf(dz, inv_s2b, dz_lo * inv_s2b);
     const float halfk = KW32 * b;
 
     // ---- Gaussian factor table C_t = exp(-(ds t)^2) and segment valid counts

@@ -86,7 +86,8 @@ struct HP {
     // and the constants of the weight and of the selection term as float pairs
     double ln_wscale;        // ln w_scale
     double inv_wscale;       // 1 / w_scale
-    double ln_sel;           // ln(w_scale 3 / Dhat(z_max)^3): the selection terms' shared factor
+    double ln_sel;           // ln(w_scale (3 / Dhat(z_max)^3) H0 / c): the selection terms' shared factor
+    double sel_cfac;         // exp(ln_sel + the catalog's 1/pi_inj scale K ln 2)
     float r_pl32, r_g32;     // c_pl / C1, m_min^alpha c_g / C1
     F2 na2, gk2, beta2, b1_2, l2min2;  // -alpha, -log2 e / (2 sigma^2), beta, 1 + beta, log2 m_min
     F2 l2max2, b1ln2_2;                // log2 m_max, (1 + beta) ln 2
@@ -101,6 +102,7 @@ struct DevCatalog {
     int32_t n_events, n_z, kde_mode, gal_storage;
     int64_t n_samples, n_pix, n_gal, n_det, n_inj_total;
     double z_max, dz, n_gal_total, lambda_g, beta, d_top;
+    double ln_lambda, ln1m_lambda;  // ln lambda_g, ln(1 - lambda_g) (0 when the argument is 0)
     float z_max32, dz32;  // float copies for the mixed kernels
     float dz_lo32;        // dz - dz32: grid positions a dz in FP32 as fmaf(a, dz32, a dz_lo32)
     int32_t max_ns, max_seg, max_npix;

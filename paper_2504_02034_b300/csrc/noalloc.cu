@@ -177,6 +177,8 @@ extern "C" int chimera_selection_static(int32_t n_points, const double *theta, i
     c.z_max32 = (float)z_max;
     c.dz32 = (float)c.dz;
     c.lambda_g = lambda_g;
+    c.ln_lambda = lambda_g > 0.0 ? std::log(lambda_g) : 0.0;
+    c.ln1m_lambda = lambda_g < 1.0 ? std::log1p(-lambda_g) : 0.0;
     c.beta = beta;
     c.d_top = dmax * (1.0 + 1e-9);
     c.n_det = n_det;

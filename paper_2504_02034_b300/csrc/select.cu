@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_mixed(DevCatalog c, Call
         k.linv = p.linv32 + (size_t)(h0 + threadIdx.x) * NU;
         k.kH = hp.kH2; k.xi0 = hp.xi0_2; k.omx = hp.omx2; k.nn = hp.nn2; k.nomx = hp.nomx2;
         k.om = hp.om2; k.omc = hp.omc2; k.gam = hp.gam2; k.gkp = hp.gk_psi2; k.l2zp = hp.l2zp2;
-        k.cfac = exp(hp.ln_sel + c.ln_ipi_shift);
+        k.cfac = hp.sel_cfac;
         scs[threadIdx.x] = k;
     }
     // the chunk's interval range (sorted by d_L; the last valid interval is NU - 1)

@@ -38,20 +38,32 @@ int cuda_check(cudaError_t e, const char *what) {
     } while (0)
 
 // ------------------------------------------------------- allocation ----
-// CHIMERA_FAULT_ALLOC=N makes the N-th device allocation of the process fail
-// (host-side fault injection for tests).
-static std::atomic<long> g_alloc_count{0};
+// CHIMERA_FAULT_ALLOC=N makes the N-th device allocation fail, counted from
+// the moment the variable took its current value (host-side fault injection
+// for tests: a test sets it to 1 and the next budgeted allocation fails).
+static std::mutex g_fault_mu;
+static std::string g_fault_val;
+static long g_alloc_count = 0;
+
+static bool injected_alloc_failure() {
+    const char *f = getenv("CHIMERA_FAULT_ALLOC");
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    const std::string v = f ? f : "";
+    if (v != g_fault_val) {
+        g_fault_val = v;
+        g_alloc_count = 0;
+    }
+    const long n = ++g_alloc_count;
+    return f && atol(f) == n;
+}
 
 int dev_alloc(Ctx &ctx, void **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
     bytes = (bytes + 255) & ~(size_t)255;
-    long n = ++g_alloc_count;
-    if (const char *f = getenv("CHIMERA_FAULT_ALLOC")) {
-        if (atol(f) == n) {
-            set_error("injected allocation failure (CHIMERA_FAULT_ALLOC)");
-            return CHIMERA_ERR_CUDA;
-        }
+    if (injected_alloc_failure()) {
+        set_error("injected allocation failure (CHIMERA_FAULT_ALLOC)");
+        return CHIMERA_ERR_CUDA;
     }
     if (ctx.used.load() + bytes > ctx.budget) {
         set_error("allocation of " + std::to_string(bytes) + " bytes exceeds the HBM budget");

@@ -12,9 +12,13 @@ ln L copied out) end to end.  L2 is flushed (a 256 MiB write) between timed
 steps because the catalog (~100 MB) would otherwise stay L2-resident.
 
 Beside the headline: the plain FP64 one-point-per-call path, ln L with its
-gradient (chimera_grad, mixed and FP64), and a serving stream (Poisson
-arrivals over four resident catalogs of 100 to 5000 events, 1-512 points per
-request, a quarter with gradients) with its p50/p99 latency.
+gradient (chimera_grad, mixed and FP64), serving streams (Poisson arrivals
+over four resident catalogs of 100 to 5000 events, 1-512 points per request,
+a quarter with gradients: one at the configuration's 2 ms mean interarrival,
+beyond one GPU's capacity, and one offered at 0.7 x the capacity that run
+measures) with their p50/p99 latency, the batched photometric workload (512
+points per launch, BF16 galaxies; Om fixed and Om varying) and the
+differentiation workload (5000 events, 64 points, ln L + gradient).
 
 Run: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Multi-GPU (torchrun): every rank evaluates its own walkers on its own GPU
@@ -425,11 +429,17 @@ def om_varying_stats(pkg, ctx, cid, theta, NE, calls=3):
     return out
 
 
-def serving_stream(pkg, ctx, bench_cid, bench_cat, n_req, seed=2504020345):
-    """Request stream over four resident catalogs (spectroscopic 100 / 300 /
+def serving_stream(pkg, ctx, bench_cid, bench_cat, n_req, n_paced, fp64_evals_per_s, seed=2504020345):
+    """Request streams over four resident catalogs (spectroscopic 100 / 300 /
     1000 events at Xi0 = 0.6 / 1 / 1.8, photometric 5000 events x 4000 PE with
-    x3 galaxies in BF16): Poisson arrivals with mean 2 ms, 1-512 hyperpoints
-    (log-uniform), gradient flag with probability 0.25, mixed precision."""
+    x3 galaxies in BF16), 1-512 hyperpoints per request (log-uniform),
+    gradient flag with probability 0.25, mixed precision:
+    * "overloaded": n_req requests with Poisson arrivals of mean 2 ms (the
+      configuration's rate, more than one GPU carries), whose achieved request
+      rate measures the capacity and whose latencies are queue backlog;
+    * "paced": n_paced requests offered at 0.7 x that capacity, where the
+      latencies show the batching loop rather than a queue.
+    Beside them, the plain FP64 one-point-per-call path in the same unit."""
     from synth import catalog as sc
     t_gen = time.perf_counter()
     cats = [(sc.config_catalog(2, variant=0, n_events=100), 0.6),
@@ -439,40 +449,136 @@ def serving_stream(pkg, ctx, bench_cid, bench_cat, n_req, seed=2504020345):
     cids = [ctx.load(c) if c is not bench_cat else bench_cid for c, _ in cats]
     nev = [c["n_events"] for c, _ in cats]
     t_gen = time.perf_counter() - t_gen
-    rng = np.random.default_rng(seed)
-    arrive = np.cumsum(rng.exponential(2e-3, n_req))
-    which = rng.integers(0, len(cats), n_req)
-    npts = np.clip(np.floor(np.exp(rng.uniform(0.0, np.log(513.0), n_req))), 1, 512).astype(int)
-    want_grad = rng.random(n_req) < 0.25
-    thetas = [sc.make_hyperpoints(int(n), seed=seed + 7 * i, Xi0=cats[w][1]) for i, (n, w) in enumerate(zip(npts, which))]
     # warm the per-catalog caches (galaxy profiles and their Om derivatives)
     for cid, (c, xi0) in zip(cids, cats):
         for flags in (pkg.SERVE_MIXED, pkg.SERVE_MIXED | pkg.SERVE_GRAD):
             tk = pkg.chimera_serve_submit(ctx.h, cid, sc.make_hyperpoints(1, seed=seed, Xi0=xi0), flags)
             pkg.chimera_serve_poll(ctx.h, tk, 1, grad=bool(flags & pkg.SERVE_GRAD))
-    pkg.chimera_serve_reset_stats(ctx.h)
-    t0 = time.perf_counter()
-    tickets = []
-    for i in range(n_req):
-        dt = t0 + arrive[i] - time.perf_counter()
-        if dt > 0:
-            time.sleep(dt)
-        flags = pkg.SERVE_MIXED | (pkg.SERVE_GRAD if want_grad[i] else 0)
-        tickets.append(pkg.chimera_serve_submit(ctx.h, cids[which[i]], thetas[i], flags))
-    for i, tk in enumerate(tickets):
-        pkg.chimera_serve_poll(ctx.h, tk, int(npts[i]), grad=bool(want_grad[i]))
-    wall = time.perf_counter() - t0
-    st = pkg.chimera_serve_stats(ctx.h)
-    evals = int(sum(int(n) * nev[w] for n, w in zip(npts, which)))
+
+    def run(n, mean_s, sd):
+        rng = np.random.default_rng(sd)
+        arrive = np.cumsum(rng.exponential(mean_s, n))
+        which = rng.integers(0, len(cats), n)
+        npts = np.clip(np.floor(np.exp(rng.uniform(0.0, np.log(513.0), n))), 1, 512).astype(int)
+        want_grad = rng.random(n) < 0.25
+        thetas = [sc.make_hyperpoints(int(k), seed=sd + 7 * i, Xi0=cats[w][1]) for i, (k, w) in enumerate(zip(npts, which))]
+        pkg.chimera_serve_reset_stats(ctx.h)
+        t0 = time.perf_counter()
+        tickets = []
+        for i in range(n):
+            dt = t0 + arrive[i] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            flags = pkg.SERVE_MIXED | (pkg.SERVE_GRAD if want_grad[i] else 0)
+            tickets.append(pkg.chimera_serve_submit(ctx.h, cids[which[i]], thetas[i], flags))
+        for i, tk in enumerate(tickets):
+            pkg.chimera_serve_poll(ctx.h, tk, int(npts[i]), grad=bool(want_grad[i]))
+        wall = time.perf_counter() - t0
+        st = pkg.chimera_serve_stats(ctx.h)
+        evals = int(sum(int(k) * nev[w] for k, w in zip(npts, which)))
+        return {"requests": n, "gradient_requests": int(want_grad.sum()), "hyperpoints": int(npts.sum()),
+                "mean_interarrival_ms": 1e3 * mean_s, "offered_req_per_s": n / float(arrive[-1]),
+                "achieved_req_per_s": n / wall, "evals_per_s": evals / wall, "unit": "evals/s",
+                "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+                "batches": st["batches"], "wall_s": wall}
+
+    over = run(n_req, 2e-3, seed)
+    out = {"catalog_events": nev, "precision": "mixed", "catalog_setup_s": t_gen, "overloaded": over,
+           "fp64_single_point_evals_per_s": fp64_evals_per_s}
+    if n_paced > 0:
+        cap = over["achieved_req_per_s"]
+        out["paced"] = run(n_paced, 1.0 / (0.7 * cap), seed + 1)
+        out["paced"]["offered_fraction_of_capacity"] = 0.7
     for cid, (c, _) in zip(cids, cats):
         if c is not bench_cat:
             ctx.unload(cid)
-    return {"requests": n_req, "catalog_events": nev, "gradient_requests": int(want_grad.sum()),
-            "hyperpoints": int(npts.sum()), "offered_req_per_s": n_req / float(arrive[-1]),
-            "achieved_req_per_s": n_req / wall, "evals_per_s": evals / wall, "unit": "evals/s",
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
-            "batches": st["batches"], "wall_s": wall, "catalog_setup_s": t_gen,
-            "precision": "mixed"}
+    return out
+
+
+def launch_stats(times_ms):
+    t = np.sort(np.asarray(times_ms))
+    return {"p50_ms": float(np.percentile(t, 50)), "p99_ms": float(np.percentile(t, 99)),
+            "mean_ms": float(t.mean()), "launches": int(t.size)}
+
+
+def config3_stats(pkg, ctx, torch, dev, flush, launches):
+    """The batched photometric workload: 512 walker points per launch over
+    the 300-event catalog with sigma_z = 0.05(1+z), x3 galaxies in BF16,
+    mixed: per-launch time (device entry, CUDA events, L2 flushed) with Om
+    fixed, and with a new Om at every point (the Om-varying run: 512
+    profiles built per call, host entry, wall time)."""
+    from synth import catalog as sc
+    cat = sc.config_catalog(3)
+    th = sc.config_hyperpoints(3)
+    H, NE = th.shape[0], cat["n_events"]
+    cid = ctx.load(cat)
+    stream = torch.cuda.current_stream(dev)
+    tt = torch.tensor(th, device=dev, dtype=torch.float64)
+    out_t = torch.empty(H, device=dev, dtype=torch.float64)
+    for _ in range(2):
+        pkg.chimera_loglike_device(ctx.h, cid, tt, pkg.MIXED, out_t, None, None, stream)
+    times = []
+    for _ in range(launches):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pkg.chimera_loglike_device(ctx.h, cid, tt, pkg.MIXED, out_t, None, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    pkg.chimera_set_trace(ctx.h, True)
+    pkg.chimera_loglike_device(ctx.h, cid, tt, pkg.MIXED, out_t, None, None, stream)
+    torch.cuda.synchronize()
+    stage = pkg.chimera_stage_ms(ctx.h)
+    fixed = launch_stats(times)
+    fixed.update(evals_per_s=H * NE / (1e-3 * fixed["mean_ms"]), stage_ms=stage,
+                 tile_buffer_bytes_per_launch=int(2 * 8 * int(cat["sample_off"][-1]) * H))
+    # Om varying: every point brings a new Om
+    rng = np.random.default_rng(91)
+    wall = []
+    for k in range(2):
+        t2 = th.copy()
+        t2[:, 1] = 0.25 + 0.1 * rng.random(H)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pkg.chimera_loglike(ctx.h, cid, t2, pkg.MIXED)
+        wall.append(time.perf_counter() - t0)
+    stage_om = pkg.chimera_stage_ms(ctx.h)
+    pkg.chimera_set_trace(ctx.h, False)
+    ctx.unload(cid)
+    return {"workload": "300 events x 5000 PE, photometric sigma_z = 0.05(1+z), x3 galaxies (BF16), "
+                        "512 walker points per launch, mixed",
+            "om_fixed": fixed,
+            "om_varying": {"ms_per_call": 1e3 * float(np.mean(wall)), "calls": len(wall),
+                           "evals_per_s": H * NE / float(np.mean(wall)), "stage_ms": stage_om}}
+
+
+def config4_stats(pkg, ctx, calls):
+    """The differentiation workload: ln L and the 12-component gradient at 64
+    points (Om varying) over the 5000-event catalog (4000 PE, 5e6
+    injections), mixed; and ln L alone at the same points."""
+    from synth import catalog as sc
+    cat = sc.config_catalog(4)
+    th = sc.config_hyperpoints(4)
+    H, NE = th.shape[0], cat["n_events"]
+    cid = ctx.load(cat)
+    pkg.chimera_grad(ctx.h, cid, th, pkg.MIXED)
+    pkg.chimera_loglike(ctx.h, cid, th, pkg.MIXED)
+    g, l = [], []
+    for _ in range(calls):
+        t0 = time.perf_counter()
+        pkg.chimera_grad(ctx.h, cid, th, pkg.MIXED)
+        g.append(1e3 * (time.perf_counter() - t0))
+    for _ in range(calls):
+        t0 = time.perf_counter()
+        pkg.chimera_loglike(ctx.h, cid, th, pkg.MIXED)
+        l.append(1e3 * (time.perf_counter() - t0))
+    ctx.unload(cid)
+    gs, ls = launch_stats(g), launch_stats(l)
+    gs["evals_per_s"] = H * NE / (1e-3 * gs["mean_ms"])
+    ls["evals_per_s"] = H * NE / (1e-3 * ls["mean_ms"])
+    return {"workload": "5000 events x 4000 PE, 5e6 injections, 64 points with Om varying, mixed, host entry",
+            "gradient": gs, "loglike": ls}
 
 
 def run_reference(args, ws, rank):
@@ -517,7 +623,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--serve-requests", type=int, default=120,
-                    help="length of the serving stream (0 skips it)")
+                    help="length of the overloaded serving stream (0 skips serving)")
+    ap.add_argument("--serve-paced", type=int, default=2000,
+                    help="length of the serving stream offered at 0.7 x capacity (0 skips it)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the photometric 512-point and 5000-event gradient workloads")
     ap.add_argument("--profile", action="store_true",
                     help="run W warm-up launches and one more launch of the timed step, then exit (for ncu)")
     ap.add_argument("--profile-grad", action="store_true",
@@ -631,7 +741,10 @@ def main():
     om_var = om_varying_stats(pkg, ctx, cid, theta, NE) if rank == 0 else None
     kern_opt = kernel_option_stats(pkg, ctx, torch, dev, cid, theta, NE, max(3, args.steps // 2)) if rank == 0 else None
     kde3 = kde3_stats(pkg, ctx, cat, theta) if rank == 0 else None
-    serving = serving_stream(pkg, ctx, cid, cat, args.serve_requests) if args.serve_requests > 0 and rank == 0 else None
+    serving = (serving_stream(pkg, ctx, cid, cat, args.serve_requests, args.serve_paced, fp64_val)
+               if args.serve_requests > 0 and rank == 0 else None)
+    c3 = config3_stats(pkg, ctx, torch, dev, flush, 10) if rank == 0 and not args.no_configs else None
+    c4 = config4_stats(pkg, ctx, 3) if rank == 0 and not args.no_configs else None
 
     kern = sum(kern_ms) / len(kern_ms)
     clock_mhz = (clk or {}).get("sm_max_mhz") or 2032.0
@@ -679,6 +792,9 @@ def main():
         "kernel_options": kern_opt,
         "kde_3d_fp64": kde3,
         "serving": serving,
+        "photometric_512": c3,
+        "differentiation_5000": c4,
+        "device_memory_end": pkg.chimera_memory(ctx.h),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(theta.nbytes),
                 "d2h_bytes_per_step": int(H * (8 + 8 + 4))},
         # per step: k_nodes_grid, k_inv_nodes, k_hyper_final, k_reweight,

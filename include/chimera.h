@@ -210,7 +210,11 @@ typedef struct {
 /*
  * chimera_create: open a context on CUDA device `device`.  hbm_budget_bytes
  * bounds everything the context allocates (catalogs, caches, workspaces);
- * 0 means 90 % of the device's free memory at creation.  *out receives the
+ * 0 means 90 % of the device's free memory at creation.  The per-Om caches
+ * (distance tables, galaxy profiles of every resident catalog) fill what the
+ * budget leaves free; an allocation that would exceed the budget first frees
+ * cache entries that the running call does not use, least recently used
+ * first, and fails with ADMISSION only when that is not enough.  *out receives the
  * context.  Errors: INVALID_ARG (out == NULL, bad device), CUDA.
  */
 int chimera_create(chimera_ctx **out, int device, size_t hbm_budget_bytes);
@@ -327,6 +331,16 @@ int chimera_serve_reset_stats(chimera_ctx *ctx);
  * ms[4] combine (K6), ms[5] adjoint (K7, gradient calls only), ms[6]
  * reweighting (K2, mixed path).
  */
+/*
+ * chimera_memory: the context's device-memory accounting (no counterpart in
+ * the paper; for operators sizing a budget).  out: host int64[5] receives
+ * out[0] the budget, out[1] the bytes held against it, and of those out[2]
+ * the resident catalogs, out[3] the per-Om caches (distance tables, galaxy
+ * profiles and their Om derivatives) and out[4] the workspaces (the
+ * context's and the serving lanes').  Errors: INVALID_ARG.
+ */
+int chimera_memory(chimera_ctx *ctx, int64_t *out);
+
 int chimera_set_trace(chimera_ctx *ctx, int enable);
 int chimera_stage_ms(chimera_ctx *ctx, double *ms);
 

@@ -121,6 +121,7 @@ ABI = {
     "chimera_stage_ms": (C.c_int, [_P, _pd]),
     "chimera_kde_pairs": (C.c_int, [_P, C.c_int32, C.c_int32, _pd, _pi64]),
     "chimera_peaks": (C.c_int, [_P, _pd]),
+    "chimera_memory": (C.c_int, [_P, _pi64]),
     "chimera_selection_static": (C.c_int, [C.c_int32, _pd, C.c_int64, C.c_int64, _P, _P, _P, _P,
                                            C.c_double, C.c_double, C.c_double, _P, _P, _P]),
 }
@@ -322,6 +323,14 @@ def chimera_kde_pairs(h, cid, theta):
     _ck(lib().chimera_kde_pairs(h, cid, t.shape[0], _dp(t), out.ctypes.data_as(_pi64)),
         "chimera_kde_pairs")
     return out
+
+
+def chimera_memory(h):
+    """Device-memory accounting of a context: budget, held, catalogs, caches,
+    workspaces (bytes)."""
+    out = np.zeros(5, dtype=np.int64)
+    _ck(lib().chimera_memory(h, out.ctypes.data_as(_pi64)), "chimera_memory")
+    return dict(zip(("budget", "held", "catalogs", "caches", "workspaces"), (int(x) for x in out)))
 
 
 def chimera_peaks(h):

@@ -1267,7 +1267,7 @@ size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Layout of the adjoint scratch for H points of catalog c.
 struct AdjLayout {
-    size_t o_ptrs, o_hpd, o_dzn, o_dzn32, o_Q, o_QT, o_dlnI, o_selg, o_dv, o_dvO, o_invZ, o_ZO, total;
+    size_t o_ptrs, o_hpd, o_dzn, o_dzn32, o_Q, o_QT, o_dlnI, o_selg, total;
     AdjLayout(const DevCatalog &c, int H, int nchunk) {
         size_t o = 0;
         auto take = [&](size_t b) { size_t r = o; o += al256(b); return r; };
@@ -1279,10 +1279,6 @@ struct AdjLayout {
         o_QT = take(sizeof(float) * AM_QT * (size_t)H * c.n_z);
         o_dlnI = take(sizeof(double) * 12 * (size_t)H * c.n_events);
         o_selg = take(sizeof(double) * 13 * (size_t)H * std::max(nchunk, 1));
-        o_dv = take((sizeof(double) + sizeof(float)) * c.n_z);  // FP64 values, then their FP32 copy
-        o_dvO = take((sizeof(double) + sizeof(float)) * c.n_z);
-        o_invZ = take(sizeof(double) * (size_t)std::max<int64_t>(c.n_gal, 1));
-        o_ZO = take(sizeof(double) * (size_t)std::max<int64_t>(c.n_gal, 1));
         total = o;
     }
 };
@@ -1295,12 +1291,10 @@ struct PendingDprof {
 };
 
 // The one-Om dG/dOm kernels into entry e.
-int dprofile_one(Workspace &ws, const AdjLayout &L, const DevCatalog &c, double Om, bool f64, const double *fwd,
+// (v: the context's profile scratch, acquired by the caller)
+int dprofile_one(Workspace &ws, const ProfView &v, const DevCatalog &c, double Om, bool f64, const double *fwd,
                  const double *fwdO, ProfEntry &e) {
-    double *dv = reinterpret_cast<double *>(ws.gscr + L.o_dv);
-    double *dvO = reinterpret_cast<double *>(ws.gscr + L.o_dvO);
-    double *invZ = reinterpret_cast<double *>(ws.gscr + L.o_invZ);
-    double *ZO = reinterpret_cast<double *>(ws.gscr + L.o_ZO);
+    double *dv = v.adv, *dvO = v.advO, *invZ = v.ainvZ, *ZO = v.aZO;
     float *dv32 = reinterpret_cast<float *>(dv + c.n_z), *dvO32 = reinterpret_cast<float *>(dvO + c.n_z);
     k_dv_pair<<<(c.n_z + 63) / 64, 64, 0, ws.st>>>(fwd, fwdO, Om, c.dz, c.n_z, dv, dvO, dv32, dvO32);
     launch_galaxy_dOm(c, fwd, fwdO, Om, dv, dvO, dv32, dvO32, f64, invZ, ZO, e.G, ws.st);
@@ -1321,7 +1315,7 @@ int dprofile_finish(Workspace &ws, const DevCatalog &c, bool f64, ProfEntry &e) 
 // dG/dOm profile for (Om, precision), cached with the forward profiles
 // (FP64 rows for FP64 calls, FP32 rows for mixed ones).  With `defer`, a new
 // mixed profile is only allocated and queued for flush_dprofiles.
-int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double Om, bool f64, const double *fwd,
+int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, double Om, bool f64, const double *fwd,
              const double *fwdO, const double **out, std::vector<PendingDprof> *defer) {
     const int kind = f64 ? 2 : 3;
     auto key = std::make_pair(bits_of(Om), kind);
@@ -1347,8 +1341,14 @@ int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double O
             it = cat.prof.emplace(key, e).first;
             defer->push_back({Om, fwd, fwdO, key});
         } else {
-            RC(dprofile_one(ws, L, c, Om, f64, fwd, fwdO, e));
+            ProfView v;
+            if (int rc = prof_scratch_acquire(ctx, c, ws.st, &v)) {
+                free_prof_entry(ctx, e);
+                return rc;
+            }
+            RC(dprofile_one(ws, v, c, Om, f64, fwd, fwdO, e));
             RC(dprofile_finish(ws, c, f64, e));
+            RC(prof_scratch_release(ctx, ws.st));
             it = cat.prof.emplace(key, e).first;
         }
     } else {
@@ -1362,13 +1362,16 @@ int dprofile(Ctx &ctx, Catalog &cat, Workspace &ws, const AdjLayout &L, double O
 
 // Launch the pending mixed dG/dOm profiles, PROF_MB Om values per batched
 // pass (one alone takes the one-Om kernels; both give the same values).
-int flush_dprofiles(Catalog &cat, Workspace &ws, const AdjLayout &L, std::vector<PendingDprof> &pend) {
+int flush_dprofiles(Ctx &ctx, Catalog &cat, Workspace &ws, std::vector<PendingDprof> &pend) {
     const DevCatalog &c = cat.d;
+    if (pend.empty()) return CHIMERA_OK;
+    ProfView v;
+    RC(prof_scratch_acquire(ctx, c, ws.st, &v));
     for (size_t b = 0; b < pend.size(); b += PROF_MB) {
         const int n = (int)std::min<size_t>(PROF_MB, pend.size() - b);
         if (n == 1) {
             const PendingDprof &q = pend[b];
-            RC(dprofile_one(ws, L, c, q.Om, false, q.fwd, q.fwdO, cat.prof.at(q.key)));
+            RC(dprofile_one(ws, v, c, q.Om, false, q.fwd, q.fwdO, cat.prof.at(q.key)));
         } else {
             MultiOm m{};
             m.n = n;
@@ -1379,12 +1382,12 @@ int flush_dprofiles(Catalog &cat, Workspace &ws, const AdjLayout &L, std::vector
                 m.Om[j] = q.Om;
                 m.out[j] = j < n ? (float *)cat.prof.at(q.key).G : nullptr;
             }
-            launch_galaxy_profile_multi(c, m, true, ws.dvm, ws.invZm, ws.st);
+            launch_galaxy_profile_multi(c, m, true, v.dvm, v.invZm, ws.st);
         }
         for (int j = 0; j < n; j++) RC(dprofile_finish(ws, c, false, cat.prof.at(pend[b + j].key)));
     }
     pend.clear();
-    return CHIMERA_OK;
+    return prof_scratch_release(ctx, ws.st);
 }
 
 void drop_dpending(Ctx &ctx, Catalog &cat, Workspace &ws, std::vector<PendingDprof> &pend) {
@@ -1458,13 +1461,13 @@ int backward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, int precision) {
     RC(fwd_tables(ctx, oms.data(), (int)oms.size(), ws.st, fOs.data(), true));
     std::vector<PendingDprof> pend;
     for (size_t i = 0; i < oms.size(); i++) {
-        int rc = dprofile(ctx, cat, ws, L, oms[i], f64, fws[i], fOs[i], &dGs[i], &pend);
+        int rc = dprofile(ctx, cat, ws, oms[i], f64, fws[i], fOs[i], &dGs[i], &pend);
         if (rc != CHIMERA_OK) {
             drop_dpending(ctx, cat, ws, pend);
             return rc;
         }
     }
-    if (int rc = flush_dprofiles(cat, ws, L, pend)) {
+    if (int rc = flush_dprofiles(ctx, cat, ws, pend)) {
         drop_dpending(ctx, cat, ws, pend);
         return rc;
     }

@@ -65,7 +65,7 @@ int dev_alloc(Ctx &ctx, void **p, size_t bytes) {
         set_error("injected allocation failure (CHIMERA_FAULT_ALLOC)");
         return CHIMERA_ERR_CUDA;
     }
-    if (ctx.used.load() + bytes > ctx.budget) {
+    if (ctx.used.load() + bytes > ctx.budget && !make_room(ctx, bytes)) {
         set_error("allocation of " + std::to_string(bytes) + " bytes exceeds the HBM budget");
         return CHIMERA_ERR_ADMISSION;
     }
@@ -98,7 +98,7 @@ int cache_alloc(Ctx &ctx, void **p, size_t bytes, cudaStream_t st) {
             return CHIMERA_ERR_CUDA;
         }
     }
-    if (ctx.used.load() + bytes > ctx.budget) {
+    if (ctx.used.load() + bytes > ctx.budget && !make_room(ctx, bytes)) {
         set_error("allocation of " + std::to_string(bytes) + " bytes exceeds the HBM budget");
         return CHIMERA_ERR_ADMISSION;
     }
@@ -193,34 +193,30 @@ void ws_release(Ctx &ctx, Workspace &ws) {
     ws.nev_cap = 0;
     ws.nz_cap = 0;
     ws.nchunk_cap = 0;
-    ws.ngal_cap = 0;
-    ws.zw_tile = 0;
-    ws.zpad_cap = 0;
+    ws.zw_bytes = 0;
 }
 
-// Hyperpoints per reweighting tile: the tile buffer holds z and w of every
-// sample for that many points, at most 1 GiB.
-static int zw_tile_for(int H, int64_t n_zpad) {
-    const int64_t cap = (int64_t)1 << 30;
-    const int64_t t = cap / (8 * std::max<int64_t>(n_zpad, 1));
-    return (int)std::max<int64_t>(1, std::min<int64_t>(H, t));
+// Bytes of the reweighting tile buffer for H points of a catalog: z and w of
+// every sample for as many points as fit 1 GiB (at least one point).
+static size_t zw_bytes_for(int H, int64_t n_zpad) {
+    const int64_t per = 8 * std::max<int64_t>(n_zpad, 1);
+    const int64_t t = std::max<int64_t>(1, std::min<int64_t>(H, ((int64_t)1 << 30) / per));
+    return (size_t)(t * per);
 }
 
 int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat) {
     const DevCatalog &c = cat.d;
     int nch = selection_chunks(c);
-    const int tile = zw_tile_for(H, c.n_zpad);
+    const size_t zwb = zw_bytes_for(H, c.n_zpad);
     if (H <= ws.Hcap && c.n_events <= ws.nev_cap && c.n_z <= ws.nz_cap && nch <= ws.nchunk_cap &&
-        c.n_gal <= ws.ngal_cap && tile <= ws.zw_tile && c.n_zpad <= ws.zpad_cap)
+        zwb <= ws.zw_bytes)
         return CHIMERA_OK;
     // grow (with some headroom) and re-allocate everything
     int Hn = std::max(H, ws.Hcap);
     int64_t nev = std::max<int64_t>(c.n_events, ws.nev_cap);
     int nz = std::max(c.n_z, ws.nz_cap);
     int nc = std::max(nch, ws.nchunk_cap);
-    int64_t ng = std::max<int64_t>(c.n_gal, ws.ngal_cap);
-    const int ztile = std::max(tile, ws.zw_tile);
-    const int64_t zpad = std::max<int64_t>(c.n_zpad, ws.zpad_cap);
+    const size_t zw_bytes = std::max(zwb, ws.zw_bytes);
     if (ws.st) cudaStreamSynchronize(ws.st);
     ws_release(ctx, ws);
     struct Item { void **p; size_t b; };
@@ -238,17 +234,15 @@ int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat) {
         {(void **)&ws.lnL, sizeof(double) * Hn},
         {(void **)&ws.neff, sizeof(double) * Hn},
         {(void **)&ws.xi, sizeof(double) * Hn},
-        {(void **)&ws.dv, (sizeof(double) + sizeof(float)) * nz},
-        {(void **)&ws.invZ64, sizeof(double) * (size_t)std::max<int64_t>(ng, 1)},
-        {(void **)&ws.invZ32, sizeof(float) * (size_t)std::max<int64_t>(ng, 1)},
-        {(void **)&ws.dvm, 2 * sizeof(float) * PROF_MB * ((size_t)nz + 1)},
-        {(void **)&ws.invZm, 2 * sizeof(float) * PROF_MB * (size_t)std::max<int64_t>(ng, 1)},
         {(void **)&ws.grad, sizeof(double) * 12 * (size_t)Hn},
         {(void **)&ws.pairs, sizeof(unsigned long long) * (size_t)Hn},
         {(void **)&ws.dk, sizeof(float) * 2 * (size_t)Hn * NT_FWD},
         {(void **)&ws.fmax_bits, sizeof(unsigned long long) * (size_t)Hn},
-        {(void **)&ws.zw, sizeof(float) * 2 * (size_t)zpad * ztile},
+        {(void **)&ws.zw, zw_bytes},
     };
+    // ws_release freed the old buffers: forget their addresses, so that a
+    // failure below frees only what this attempt allocated
+    for (auto &it : items) *it.p = nullptr;
     for (auto &it : items) {
         int rc = dev_alloc(ctx, it.p, it.b);
         if (rc) {
@@ -273,9 +267,7 @@ int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat) {
     ws.nev_cap = nev;
     ws.nz_cap = nz;
     ws.nchunk_cap = nc;
-    ws.ngal_cap = ng;
-    ws.zw_tile = ztile;
-    ws.zpad_cap = zpad;
+    ws.zw_bytes = zw_bytes;
     return CHIMERA_OK;
 }
 
@@ -316,12 +308,14 @@ int fwd_tables(Ctx &ctx, const double *Om, int n, cudaStream_t st, const double 
                 flush();  // the entries already made get their tables
                 return rc;
             }
+            e.last_use = ctx.tick;
             it = cache.emplace(key, e).first;
             b.Om[b.n] = Om[i];
             b.out[b.n++] = it->second.table;
             fresh.push_back(&it->second);
             if (b.n == FWD_MB) RC(flush());
         } else {
+            it->second.last_use = ctx.tick;
             CK(cudaStreamWaitEvent(st, it->second.ready, 0));
         }
         out[i] = it->second.table;
@@ -341,20 +335,111 @@ void free_prof_entry(Ctx &ctx, ProfEntry &e) {
     e.ready = nullptr;
 }
 
-void evict_profiles(Ctx &ctx, Catalog &cat, size_t need) {
-    // least recently used first, never the ones touched by the current call
-    while (ctx.used.load() + need > ctx.budget && !cat.prof.empty()) {
-        auto victim = cat.prof.end();
-        for (auto it = cat.prof.begin(); it != cat.prof.end(); ++it)
-            if (it->second.last_use < ctx.tick &&
-                (victim == cat.prof.end() || it->second.last_use < victim->second.last_use))
-                victim = it;
-        if (victim == cat.prof.end()) return;
-        cudaDeviceSynchronize();
-        free_prof_entry(ctx, victim->second);
-        cat.prof.erase(victim);
-        trim_cache_pool(ctx);
+// Frees cache entries that the running call has not touched, least recently
+// used first (the galaxy profiles of every resident catalog, then the
+// distance tables), until `need` more bytes fit the budget.  Every call of
+// the context runs under its mutex, and the device is idled before the first
+// entry is freed, so no kernel still reads a freed entry.  Returns whether
+// the bytes fit.
+bool make_room(Ctx &ctx, size_t need) {
+    bool synced = false, freed = false;
+    while (ctx.used.load() + need > ctx.budget) {
+        Catalog *vc = nullptr;
+        std::map<std::pair<uint64_t, int>, ProfEntry>::iterator victim;
+        for (auto &kv : ctx.cats) {
+            Catalog &cat = *kv.second;
+            for (auto it = cat.prof.begin(); it != cat.prof.end(); ++it)
+                if (it->second.last_use < ctx.tick && (!vc || it->second.last_use < victim->second.last_use)) {
+                    vc = &cat;
+                    victim = it;
+                }
+        }
+        std::unordered_map<uint64_t, FwdEntry> *fc = nullptr;
+        std::unordered_map<uint64_t, FwdEntry>::iterator fvictim;
+        if (!vc)
+            for (auto *cache : {&ctx.fwd, &ctx.fwdO})
+                for (auto it = cache->begin(); it != cache->end(); ++it)
+                    if (it->second.last_use < ctx.tick && (!fc || it->second.last_use < fvictim->second.last_use)) {
+                        fc = cache;
+                        fvictim = it;
+                    }
+        if (!vc && !fc) {
+            // last, the profile scratch, when this call has not used it
+            if (ctx.ps.base && ctx.ps.last_use < ctx.tick) {
+                cudaDeviceSynchronize();
+                synced = true;
+                prof_scratch_free(ctx);
+                continue;
+            }
+            break;
+        }
+        if (!synced) {
+            cudaDeviceSynchronize();
+            synced = true;
+        }
+        if (vc) {
+            free_prof_entry(ctx, victim->second);
+            vc->prof.erase(victim);
+        } else {
+            cache_free(ctx, fvictim->second.table, sizeof(double) * NT_FWD);
+            if (fvictim->second.ready) cudaEventDestroy(fvictim->second.ready);
+            fc->erase(fvictim);
+        }
+        freed = true;
     }
+    if (freed) trim_cache_pool(ctx);
+    return ctx.used.load() + need <= ctx.budget;
+}
+
+void evict_profiles(Ctx &ctx, Catalog &, size_t need) { make_room(ctx, need); }
+
+static size_t ps_al(size_t b) { return (std::max<size_t>(b, 16) + 255) & ~(size_t)255; }
+
+int prof_scratch_acquire(Ctx &ctx, const DevCatalog &c, cudaStream_t st, ProfView *v) {
+    const size_t nz = (size_t)c.n_z, ng = (size_t)std::max<int64_t>(c.n_gal, 1);
+    const size_t s_one = ps_al(12 * nz) + ps_al(8 * ng) + ps_al(4 * ng);
+    const size_t s_multi = ps_al(2 * sizeof(float) * PROF_MB * (nz + 1)) + ps_al(2 * sizeof(float) * PROF_MB * ng);
+    const size_t s_adj = 2 * ps_al(12 * nz) + 2 * ps_al(8 * ng);
+    const size_t need = std::max(s_one, std::max(s_multi, s_adj));
+    ProfScratch &ps = ctx.ps;
+    ps.last_use = ctx.tick;
+    if (!ps.done) CK(cudaEventCreateWithFlags(&ps.done, cudaEventDisableTiming));
+    if (need > ps.bytes) {
+        if (ps.recorded) CK(cudaEventSynchronize(ps.done));  // the last use has ended
+        if (ps.base) dev_free(ctx, ps.base, ps.bytes);
+        ps.base = nullptr;
+        ps.bytes = 0;
+        RC(dev_alloc(ctx, (void **)&ps.base, need));
+        ps.bytes = need;
+        ps.last_use = ctx.tick;
+    }
+    if (ps.recorded) CK(cudaStreamWaitEvent(st, ps.done, 0));
+    char *b = ps.base;
+    v->dv = reinterpret_cast<double *>(b);
+    v->invZ64 = reinterpret_cast<double *>(b + ps_al(12 * nz));
+    v->invZ32 = reinterpret_cast<float *>(b + ps_al(12 * nz) + ps_al(8 * ng));
+    v->dvm = reinterpret_cast<float *>(b);
+    v->invZm = reinterpret_cast<float *>(b + ps_al(2 * sizeof(float) * PROF_MB * (nz + 1)));
+    v->adv = reinterpret_cast<double *>(b);
+    v->advO = reinterpret_cast<double *>(b + ps_al(12 * nz));
+    v->ainvZ = reinterpret_cast<double *>(b + 2 * ps_al(12 * nz));
+    v->aZO = reinterpret_cast<double *>(b + 2 * ps_al(12 * nz) + ps_al(8 * ng));
+    return CHIMERA_OK;
+}
+
+int prof_scratch_release(Ctx &ctx, cudaStream_t st) {
+    CK(cudaEventRecord(ctx.ps.done, st));
+    ctx.ps.recorded = true;
+    return CHIMERA_OK;
+}
+
+// Frees the profile scratch; the device must be idle.
+void prof_scratch_free(Ctx &ctx) {
+    ProfScratch &ps = ctx.ps;
+    if (ps.base) dev_free(ctx, ps.base, ps.bytes);
+    ps.base = nullptr;
+    ps.bytes = 0;
+    ps.recorded = false;
 }
 
 // A mixed profile whose entry exists but whose kernels are still to be
@@ -369,11 +454,14 @@ struct PendingProf {
 // Om alone takes the one-Om kernels; both give the same values).
 static int flush_profiles(Ctx &ctx, Catalog &cat, Workspace &ws, std::vector<PendingProf> &pend) {
     const DevCatalog &c = cat.d;
+    if (pend.empty()) return CHIMERA_OK;
+    ProfView v;
+    RC(prof_scratch_acquire(ctx, c, ws.st, &v));
     for (size_t b = 0; b < pend.size(); b += PROF_MB) {
         const int n = (int)std::min<size_t>(PROF_MB, pend.size() - b);
         if (n == 1) {
             ProfEntry &e = cat.prof.at(pend[b].key);
-            launch_galaxy_profile(c, pend[b].fwd, pend[b].Om, ws.dv, ws.invZ64, ws.invZ32, nullptr, (float *)e.G,
+            launch_galaxy_profile(c, pend[b].fwd, pend[b].Om, v.dv, v.invZ64, v.invZ32, nullptr, (float *)e.G,
                                   ws.st);
         } else {
             MultiOm m{};
@@ -385,7 +473,7 @@ static int flush_profiles(Ctx &ctx, Catalog &cat, Workspace &ws, std::vector<Pen
                 m.Om[j] = q.Om;
                 m.out[j] = j < n ? (float *)cat.prof.at(q.key).G : nullptr;
             }
-            launch_galaxy_profile_multi(c, m, false, ws.dvm, ws.invZm, ws.st);
+            launch_galaxy_profile_multi(c, m, false, v.dvm, v.invZm, ws.st);
         }
         for (int j = 0; j < n; j++) {
             ProfEntry &e = cat.prof.at(pend[b + j].key);
@@ -395,7 +483,7 @@ static int flush_profiles(Ctx &ctx, Catalog &cat, Workspace &ws, std::vector<Pen
         }
     }
     pend.clear();
-    return CHIMERA_OK;
+    return prof_scratch_release(ctx, ws.st);
 }
 
 // Drop pending entries (after an error: their kernels never ran).
@@ -447,16 +535,22 @@ static int profile(Ctx &ctx, Catalog &cat, Workspace &ws, double Om, int kind, c
             e.hbytes = hb;
         }
         CK(cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming));
+        ProfView v;
+        if (int rc = prof_scratch_acquire(ctx, c, ws.st, &v)) {
+            free_prof_entry(ctx, e);
+            return rc;
+        }
         if (kind == 0)
-            launch_galaxy_profile(c, fwd, Om, ws.dv, ws.invZ64, ws.invZ32, (double *)e.G, nullptr, ws.st);
+            launch_galaxy_profile(c, fwd, Om, v.dv, v.invZ64, v.invZ32, (double *)e.G, nullptr, ws.st);
         else
-            launch_galaxy_profile(c, fwd, Om, ws.dv, ws.invZ64, ws.invZ32, nullptr, (float *)e.G, ws.st);
+            launch_galaxy_profile(c, fwd, Om, v.dv, v.invZ64, v.invZ32, nullptr, (float *)e.G, ws.st);
         if (hb) {
             if (kind == 0) launch_profile_sum(c, (double *)e.G, nullptr, (double *)e.Gh, nullptr, ws.st);
             else launch_profile_sum(c, nullptr, (float *)e.G, nullptr, (float *)e.Gh, ws.st);
         }
         CK(cudaGetLastError());
         CK(cudaEventRecord(e.ready, ws.st));
+        RC(prof_scratch_release(ctx, ws.st));
         it = cat.prof.emplace(key, e).first;
     } else {
         CK(cudaStreamWaitEvent(ws.st, it->second.ready, 0));
@@ -477,8 +571,8 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
         set_error("CHIMERA_KDE_3D catalogs take CHIMERA_FP64 with the Gaussian kernel");
         return CHIMERA_ERR_INVALID_ARG;
     }
+    ctx.tick++;  // before the workspace grows: the previous call's cache entries may go
     RC(ws_ensure(ctx, ws, H, cat));
-    ctx.tick++;
     const DevCatalog &c = cat.d;
     // stage: theta (admissible copy) | status | fwd ptrs | prof ptrs
     char *q = ws.hstage;
@@ -558,7 +652,8 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
         else launch_event_fp64(c, p, H, ws.st);
     } else {
         // reweighting and event integrals by tiles of hyperpoints
-        const int tile = std::max(1, std::min(H, ws.zw_tile));
+        const int64_t fit = (int64_t)(ws.zw_bytes / (8 * (size_t)std::max<int64_t>(c.n_zpad, 1)));
+        const int tile = (int)std::max<int64_t>(1, std::min<int64_t>(H, fit));
         const int ntiles = (H + tile - 1) / tile;
         if (ws.trace) {
             while ((int)ws.tile_ev.size() < 2 * ntiles) {
@@ -1077,7 +1172,8 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     }
     size_t total = 0;
     for (auto &u : ups) total += (std::max<size_t>(u.bytes, 16) + 255) & ~(size_t)255;
-    if (ctx.used.load() + total > ctx.budget) {
+    ctx.tick++;  // a load reads no cache entry: every one may make room
+    if (ctx.used.load() + total > ctx.budget && !make_room(ctx, total)) {
         set_error("catalog footprint " + std::to_string(total) + " bytes exceeds the HBM budget");
         return CHIMERA_ERR_ADMISSION;
     }
@@ -1248,6 +1344,8 @@ void chimera_destroy(chimera_ctx *h) {
     }
     ctx.fwdO.clear();
     ws_release(ctx, ctx.ws);
+    prof_scratch_free(ctx);
+    if (ctx.ps.done) cudaEventDestroy(ctx.ps.done);
     ws_destroy_streams(ctx.ws);
     for (auto &e : ctx.ws.tev)
         if (e) cudaEventDestroy(e);
@@ -1492,6 +1590,25 @@ int chimera_kde_pairs(chimera_ctx *h, int32_t id, int32_t n, const double *theta
     CK(cudaMemcpyAsync(v.data(), ctx.ws.pairs, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, ctx.ws.st));
     CK(cudaStreamSynchronize(ctx.ws.st));
     for (int i = 0; i < n; i++) pairs[i] = (int64_t)v[i];
+    return CHIMERA_OK;
+}
+
+int chimera_memory(chimera_ctx *h, int64_t *out) {
+    if (!h || !out) { set_error("bad argument"); return CHIMERA_ERR_INVALID_ARG; }
+    Ctx &ctx = h->c;
+    std::lock_guard<std::recursive_mutex> lk(ctx.mu);
+    auto r = [](size_t b) { return (std::max<size_t>(b, 16) + 255) & ~(size_t)255; };
+    size_t cats = 0, cache = 0;
+    for (auto &kv : ctx.cats) {
+        cats += kv.second->bytes;
+        for (auto &pe : kv.second->prof) cache += r(pe.second.bytes) + (pe.second.Gh ? r(pe.second.hbytes) : 0);
+    }
+    cache += (ctx.fwd.size() + ctx.fwdO.size()) * r(sizeof(double) * NT_FWD);
+    out[0] = (int64_t)ctx.budget;
+    out[1] = (int64_t)ctx.used.load();
+    out[2] = (int64_t)cats;
+    out[3] = (int64_t)cache;
+    out[4] = (int64_t)(ctx.ws.bytes + ctx.ws.gscr_bytes + serve_ws_bytes(ctx) + ctx.ps.bytes);
     return CHIMERA_OK;
 }
 

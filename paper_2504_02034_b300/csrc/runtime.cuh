@@ -39,6 +39,7 @@ struct Ctx;
 struct FwdEntry {
     double *table = nullptr;
     cudaEvent_t ready = nullptr;
+    uint64_t last_use = 0;  // Ctx::tick of the last call that read it
 };
 
 // Galaxy profile cache entry for one (Om, kind) of one catalog.  Kinds:
@@ -69,7 +70,6 @@ struct Workspace {
     int64_t nev_cap = 0;
     int nz_cap = 0;
     int nchunk_cap = 0;
-    int64_t ngal_cap = 0;
     size_t bytes = 0;
     // device
     char *param = nullptr;  // theta | status | fwd ptrs | prof ptrs
@@ -81,16 +81,10 @@ struct Workspace {
     float *F32 = nullptr;
     double *lnI = nullptr, *bw = nullptr, *selp = nullptr;
     double *lnL = nullptr, *neff = nullptr, *xi = nullptr;
-    double *dv = nullptr, *invZ64 = nullptr;
     double *dk = nullptr;                  // [H x NT_FWD] forward-node scratch (FP32 d, J)
-    float *zw = nullptr;                   // [zw_tile x 2 x zpad_cap] reweighted samples (mixed)
-    int zw_tile = 0;                       // hyperpoints per reweighting tile
-    int64_t zpad_cap = 0;
+    float *zw = nullptr;                   // [tile x 2 x n_zpad] reweighted samples (mixed)
+    size_t zw_bytes = 0;                   // its size; a call's tile is zw_bytes / (8 n_zpad) points
     unsigned long long *fmax_bits = nullptr;  // [H]
-    float *invZ32 = nullptr;
-    // batched mixed profiles (and their Om derivatives):
-    // [2 x (n_z+1) x PROF_MB], [2 x n_gal x PROF_MB]
-    float *dvm = nullptr, *invZm = nullptr;
     // adjoint buffers
     double *grad = nullptr;       // [H x 12]
     char *gscr = nullptr;         // adjoint scratch (allocated on the first gradient call)
@@ -120,6 +114,32 @@ struct Workspace {
 
 struct Server;
 
+// Scratch of the galaxy-profile kernels: the dV_c/dz column(s) and the
+// per-galaxy normalisations 1/Z_g of one Om, or of PROF_MB Om values at a
+// time on the batched path, and for the adjoint Z_g' and dV_c/dz'.  One per
+// context, shared by its workspace and the serving lanes': profiles are
+// computed only on a cache miss, and the batched part alone takes
+// 2 x 4 x PROF_MB = 128 bytes per galaxy.  Uses are enqueued under the
+// context's mutex; each waits on `done` of the previous use and records it
+// after its own kernels.
+struct ProfScratch {
+    char *base = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t done = nullptr;
+    bool recorded = false;
+    uint64_t last_use = 0;
+};
+// The scratch's regions for one catalog (they alias: the one-Om, batched
+// and adjoint kernels of a call run one after another on one stream).
+struct ProfView {
+    double *dv;           // [n_z] FP64, then [n_z] FP32
+    double *invZ64;       // [n_gal]
+    float *invZ32;        // [n_gal]
+    float *dvm, *invZm;   // [2 x (n_z+1) x PROF_MB], [2 x n_gal x PROF_MB]
+    double *adv, *advO;   // adjoint: [n_z] FP64 then [n_z] FP32, each
+    double *ainvZ, *aZO;  // adjoint: [n_gal] each
+};
+
 struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -137,6 +157,7 @@ struct Ctx {
     Workspace ws;
     uint64_t tick = 0;
     Server *server = nullptr;
+    ProfScratch ps;
 };
 
 // Budgeted allocation; returns a CHIMERA_ERR_* code.
@@ -179,6 +200,12 @@ uint64_t bits_of(double x);
 int fwd_table(Ctx &ctx, double Om, cudaStream_t st, const double **out);
 int fwd_tables(Ctx &ctx, const double *Om, int n, cudaStream_t st, const double **out, bool dOm);
 void evict_profiles(Ctx &ctx, Catalog &cat, size_t need);
+bool make_room(Ctx &ctx, size_t need);
+// The profile scratch sized for catalog c, after the previous use on any
+// stream (st waits on it); release records the end of this use on st.
+int prof_scratch_acquire(Ctx &ctx, const DevCatalog &c, cudaStream_t st, ProfView *v);
+int prof_scratch_release(Ctx &ctx, cudaStream_t st);
+void prof_scratch_free(Ctx &ctx);
 void free_prof_entry(Ctx &ctx, ProfEntry &e);
 
 std::shared_ptr<Catalog> find_catalog(Ctx &ctx, int32_t id);
@@ -194,5 +221,7 @@ int serve_cancel(Ctx &ctx, uint64_t ticket);
 int serve_stats(Ctx &ctx, chimera_serve_stats_t *out);
 int serve_reset_stats(Ctx &ctx);
 void serve_shutdown(Ctx &ctx);
+// Bytes held by the serving lanes' workspaces (called under ctx.mu).
+size_t serve_ws_bytes(Ctx &ctx);
 
 }  // namespace chim

@@ -343,6 +343,13 @@ int serve_cancel(Ctx &ctx, uint64_t ticket) {
     return CHIMERA_OK;
 }
 
+size_t serve_ws_bytes(Ctx &ctx) {
+    if (!ctx.server) return 0;
+    size_t b = 0;
+    for (auto &L : ctx.server->lanes) b += L.ws.bytes + L.ws.gscr_bytes;
+    return b;
+}
+
 int serve_stats(Ctx &ctx, chimera_serve_stats_t *out) {
     Server *s = get_server(ctx);
     std::lock_guard<std::mutex> lk(s->m);

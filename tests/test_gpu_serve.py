@@ -109,3 +109,34 @@ def test_admission_by_hbm_footprint(chim):
         t = chim.chimera_serve_submit(ctx.h, cid, small, chim.SERVE_MIXED)
         lnL2, _, _ = chim.chimera_serve_poll(ctx.h, t, 2)
         assert np.array_equal(lnL, lnL2)
+
+
+def test_cache_of_one_catalog_makes_room_for_another(chim):
+    """The per-Om galaxy-profile caches of catalog A fill the budget; a later
+    call on catalog B that needs a larger workspace frees A's least recently
+    used entries instead of failing, and both catalogs' results stay those of
+    a context without a budget."""
+    ca, cb = _cats()
+    with chim.Context(0) as probe:
+        ia, ib = probe.load(ca), probe.load(cb)
+        fa, fb = probe.info(ia), probe.info(ib)
+        pa = _points(16, 31, 1.0)
+        pb = _points(64, 32, 1.0)
+        ref_a, _, _ = probe.loglike(ia, pa, chim.MIXED)
+        ref_b, _, _ = probe.loglike(ib, pb, chim.MIXED)
+    per_entry = 4 * fa["n_pixels"] * fa["n_z"]
+    room = 32 * 2 ** 20
+    budget = fa["device_bytes"] + fb["device_bytes"] + room
+    with chim.Context(0, hbm_budget_bytes=budget) as ctx:
+        ia, ib = ctx.load(ca), ctx.load(cb)
+        rng = np.random.default_rng(33)
+        # more distinct Om values than the room holds profiles of catalog A
+        for _ in range(int(2 * room / (16 * per_entry)) + 2):
+            t = pa.copy()
+            t[:, 1] = 0.2 + 0.2 * rng.random(16)
+            lnL, _, _ = ctx.loglike(ia, t, chim.MIXED)
+            assert np.all(np.isfinite(lnL))
+        lnL_b, _, _ = ctx.loglike(ib, pb, chim.MIXED)
+        np.testing.assert_array_equal(lnL_b, ref_b)
+        lnL_a, _, _ = ctx.loglike(ia, pa, chim.MIXED)
+        np.testing.assert_array_equal(lnL_a, ref_a)

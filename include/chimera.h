@@ -200,7 +200,19 @@ typedef struct {
     int64_t device_bytes;   /* resident bytes of the catalog itself */
     int32_t max_samples_per_event;
     int32_t max_pixels_per_event;
+    /* how the mixed-precision galaxy profiles of Eq. p-cat are built:
+     * CHIMERA_PROFILE_CUDA_CORES (FP32 kernels) or CHIMERA_PROFILE_TENSOR_CORES
+     * (photometric catalogs: every galaxy's sigma >= 0.02 and >= 8 grid
+     * steps, complete, at least 4096 galaxies; FP16 Gaussians contracted
+     * with split-FP16 columns on tcgen05 MMAs, FP32 accumulation).  Setting
+     * CHIMERA_PROFILE_FP32=1 in the environment before a load keeps that
+     * catalog on the FP32 kernels. */
+    int32_t profile_path;
+    int32_t reserved;
 } chimera_catalog_info_t;
+
+#define CHIMERA_PROFILE_CUDA_CORES 0
+#define CHIMERA_PROFILE_TENSOR_CORES 1
 
 /* Compiled-in limits (CHIMERA_ERR_UNSUPPORTED beyond them). */
 #define CHIMERA_MAX_SAMPLES_PER_EVENT 12288

@@ -31,6 +31,7 @@ PT_OK, PT_OUT_OF_SUPPORT, PT_NONMONOTONE, PT_NEFF_LOW = 0, 1, 2, 4
 FP64, MIXED, MIXED_BINNED = 0, 1, 2
 KERNEL_EPANECHNIKOV = 0x10  # OR'ed into the precision: Epanechnikov KDE kernel
 JACOBIAN_PER_SAMPLE = 0x20  # OR'ed into the precision: the Jacobian of Eq. jacobian on each sample
+PROFILE_CUDA_CORES, PROFILE_TENSOR_CORES = 0, 1  # catalog info "profile_path"
 KDE_SINGLE_1D, KDE_MANY_1D, KDE_3D = 0, 1, 2
 GAL_F32, GAL_F16, GAL_BF16 = 0, 1, 2
 SERVE_GRAD, SERVE_MIXED = 1, 2
@@ -84,7 +85,7 @@ class CatalogInfo(C.Structure):
     _fields_ = [("n_events", C.c_int32), ("n_z", C.c_int32), ("n_samples", C.c_int64),
                 ("n_pixels", C.c_int64), ("n_galaxies", C.c_int64), ("n_det", C.c_int64),
                 ("device_bytes", C.c_int64), ("max_samples_per_event", C.c_int32),
-                ("max_pixels_per_event", C.c_int32)]
+                ("max_pixels_per_event", C.c_int32), ("profile_path", C.c_int32), ("reserved", C.c_int32)]
 
 
 class ServeStats(C.Structure):

@@ -395,12 +395,13 @@ void evict_profiles(Ctx &ctx, Catalog &, size_t need) { make_room(ctx, need); }
 
 static size_t ps_al(size_t b) { return (std::max<size_t>(b, 16) + 255) & ~(size_t)255; }
 
-int prof_scratch_acquire(Ctx &ctx, const DevCatalog &c, cudaStream_t st, ProfView *v) {
+int prof_scratch_acquire(Ctx &ctx, const DevCatalog &c, cudaStream_t st, ProfView *v, const TcHost *tc) {
     const size_t nz = (size_t)c.n_z, ng = (size_t)std::max<int64_t>(c.n_gal, 1);
     const size_t s_one = ps_al(12 * nz) + ps_al(8 * ng) + ps_al(4 * ng);
     const size_t s_multi = ps_al(2 * sizeof(float) * PROF_MB * (nz + 1)) + ps_al(2 * sizeof(float) * PROF_MB * ng);
     const size_t s_adj = 2 * ps_al(12 * nz) + 2 * ps_al(8 * ng);
-    const size_t need = std::max(s_one, std::max(s_multi, s_adj));
+    const size_t s_tc = tc ? tc_scratch_bytes(c, *tc) : 0;
+    const size_t need = std::max(std::max(s_one, s_tc), std::max(s_multi, s_adj));
     ProfScratch &ps = ctx.ps;
     ps.last_use = ctx.tick;
     if (!ps.done) CK(cudaEventCreateWithFlags(&ps.done, cudaEventDisableTiming));
@@ -424,6 +425,7 @@ int prof_scratch_acquire(Ctx &ctx, const DevCatalog &c, cudaStream_t st, ProfVie
     v->advO = reinterpret_cast<double *>(b + ps_al(12 * nz));
     v->ainvZ = reinterpret_cast<double *>(b + 2 * ps_al(12 * nz));
     v->aZO = reinterpret_cast<double *>(b + 2 * ps_al(12 * nz) + ps_al(8 * ng));
+    v->tc = b;
     return CHIMERA_OK;
 }
 
@@ -456,7 +458,33 @@ static int flush_profiles(Ctx &ctx, Catalog &cat, Workspace &ws, std::vector<Pen
     const DevCatalog &c = cat.d;
     if (pend.empty()) return CHIMERA_OK;
     ProfView v;
-    RC(prof_scratch_acquire(ctx, c, ws.st, &v));
+    RC(prof_scratch_acquire(ctx, c, ws.st, &v, c.tc_ok ? &cat.tc : nullptr));
+    if (c.tc_ok) {
+        // photometric catalog: every mixed profile on the tensor cores, up to
+        // TC_COLS Om values per batch (a profile is a function of its Om
+        // alone, whatever the batch)
+        for (size_t b = 0; b < pend.size(); b += TC_COLS) {
+            const int n = (int)std::min<size_t>(TC_COLS, pend.size() - b);
+            TcCols m{};
+            m.n = n;
+            for (int j = 0; j < n; j++) {
+                m.fwd[j] = pend[b + j].fwd;
+                m.Om[j] = pend[b + j].Om;
+            }
+            // the launcher takes the outputs through the columns' entries
+            std::vector<float *> outs(n);
+            for (int j = 0; j < n; j++) outs[j] = (float *)cat.prof.at(pend[b + j].key).G;
+            RC(launch_galaxy_profile_tc(c, cat.tc, m, outs.data(), v.tc, ws.st));
+            for (int j = 0; j < n; j++) {
+                ProfEntry &e = cat.prof.at(pend[b + j].key);
+                if (e.Gh) launch_profile_sum(c, nullptr, (float *)e.G, nullptr, (float *)e.Gh, ws.st);
+                CK(cudaGetLastError());
+                CK(cudaEventRecord(e.ready, ws.st));
+            }
+        }
+        pend.clear();
+        return prof_scratch_release(ctx, ws.st);
+    }
     for (size_t b = 0; b < pend.size(); b += PROF_MB) {
         const int n = (int)std::min<size_t>(PROF_MB, pend.size() - b);
         if (n == 1) {
@@ -989,6 +1017,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     std::vector<double> gz(ng), gs(ng), sigmax(np, 0.0);
     std::vector<float> gz32, gs32, zref(np, 0.f), sigmax32(np, 0.f);
     std::vector<uint16_t> gzq, gsq;
+    std::vector<float> zdec_all(ng), sdec_all(ng);  // the stored values as the kernels decode them
     if (d->gal_storage == CHIMERA_GAL_F32) { gz32.resize(ng); gs32.resize(ng); }
     else { gzq.resize(ng); gsq.resize(ng); }
     for (int64_t p = 0; p < np; p++) {
@@ -1004,6 +1033,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
                 gz32[g] = (float)gz[g];
                 gs32[g] = (float)gs[g];
                 sdec = gs32[g];
+                zdec_all[g] = gz32[g];
             } else {
                 float off = (float)gz[g] - zref[p];
                 bool h16 = d->gal_storage == CHIMERA_GAL_F16;
@@ -1012,10 +1042,23 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
                 sdec = h16 ? half_bits_to_f32(gsq[g]) : bf16_bits_to_f32(gsq[g]);
                 float zdec = zref[p] + (h16 ? half_bits_to_f32(gzq[g]) : bf16_bits_to_f32(gzq[g]));
                 if (!std::isfinite(zdec)) return bad("galaxy z offset not representable in 16-bit storage");
+                zdec_all[g] = zdec;
             }
+            sdec_all[g] = sdec;
             if (!(sdec > 0.f) || !std::isfinite(sdec)) return bad("galaxy sigma not representable in the storage type");
             sigmax32[p] = std::max(sigmax32[p], sdec);
         }
+    }
+    // ---- tensor-core profile plan (photometric catalogs)
+    std::vector<int2> tc_blk;
+    std::vector<float2> tc_coef;
+    std::vector<int4> tc_items, tc_reds;
+    std::vector<int32_t> tc_islot;
+    {
+        const char *f32 = getenv("CHIMERA_PROFILE_FP32");
+        if (!(f32 && f32[0] == '1'))
+            tc_plan(np, d->gal_off, zdec_all.data(), sdec_all.data(), sigmax32.data(), d->n_z, c.dz,
+                    d->completeness != nullptr, d->kde_mode, c, cat->tc, tc_blk, tc_coef, tc_items, tc_islot, tc_reds);
     }
     // ---- injections, stored sorted by d_L: the selection kernel's chunks of
     // consecutive injections then read a few neighbouring inverse-table
@@ -1157,6 +1200,13 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
         ups.push_back({(void **)&c.im2_64, im2.data(), 8 * (size_t)nd});
         ups.push_back({(void **)&c.ilp64, ilp.data(), 8 * (size_t)nd});
     }
+    if (c.tc_ok) {
+        ups.push_back({(void **)&c.tc_blk, tc_blk.data(), 8 * tc_blk.size()});
+        ups.push_back({(void **)&c.tc_coef, tc_coef.data(), 8 * tc_coef.size()});
+        ups.push_back({(void **)&c.tc_items, tc_items.data(), 16 * tc_items.size()});
+        ups.push_back({(void **)&c.tc_islot, tc_islot.data(), 4 * tc_islot.size()});
+        ups.push_back({(void **)&c.tc_reds, tc_reds.data(), 16 * tc_reds.size()});
+    }
     if (d->gal_storage == CHIMERA_GAL_F32) {
         ups.push_back({(void **)&c.gz32, gz32.data(), 4 * gz32.size()});
         ups.push_back({(void **)&c.gs32, gs32.data(), 4 * gs32.size()});
@@ -1253,6 +1303,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     cat->info.device_bytes = (int64_t)cat->bytes;
     cat->info.max_samples_per_event = max_ns;
     cat->info.max_pixels_per_event = max_np;
+    cat->info.profile_path = c.tc_ok ? CHIMERA_PROFILE_TENSOR_CORES : CHIMERA_PROFILE_CUDA_CORES;
     int32_t id_ = ctx.next_id++;
     ctx.cats[id_] = cat;
     *out_id = id_;

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cstdint>
+#include <vector>
 
 #include "chimera.h"
 
@@ -179,6 +180,19 @@ struct DevCatalog {
     float *iipi32;        // 2^-K / pi_inj, computed in FP64 and rounded (mixed selection)
     double ln_ipi_shift;  // K ln 2
     double *id64, *im1_64, *im2_64, *ilp64;
+    // tensor-core galaxy profiles (photometric catalogs; tc_ok = 0 when the
+    // catalog takes the FP32 kernels): the padded 64-galaxy blocks (pixel,
+    // first galaxy), the gather items (pixel, grid tile, first and end block
+    // relative to the item's group) with their partial slot (or -1), and the
+    // reductions of split items (pixel, grid tile, first slot, slots)
+    int32_t tc_ok;
+    float tc_sc;  // scale of the 1/Z operand (a power of two)
+    int64_t tc_nblk;
+    int2 *tc_blk;
+    float2 *tc_coef;  // [tc_nblk x 64] each slot's Gaussian coefficients (c_g, d_g); (0, -1e4) for no galaxy
+    int4 *tc_items;
+    int32_t *tc_islot;
+    int4 *tc_reds;
 };
 
 // Per-call views the kernels need for hyperpoint h.
@@ -253,6 +267,50 @@ struct MultiOm {
 };
 void launch_galaxy_profile_multi(const DevCatalog &c, const MultiOm &m, bool dOm, float *dvm, float *invZm,
                                  cudaStream_t st);
+// The mixed-path profiles of up to TC_COLS Om values on the tensor cores
+// (galaxy_tc.cu), for catalogs whose galaxies are all wide (photometric):
+// two tcgen05 contractions of the FP16 Gaussians with the Om-dependent
+// columns split in two FP16 terms, FP32 accumulation with the tensor-memory
+// partial sums promoted into an FP32 running sum every TC_PROMO stages.
+constexpr int TC_M = 128;               // Om columns per batch (the MMA's M)
+constexpr int TC_N = 256;               // galaxies (norm pass) or grid points (gather pass) per tile
+constexpr int TC_K = 64;                // K per stage (one 128-byte row of FP16)
+constexpr int TC_COLS = TC_M;           // Om columns per batch
+constexpr int TC_PROMO = 1;             // stages accumulated in tensor memory before each promotion
+constexpr int64_t TC_MIN_GAL = 4096;    // smaller catalogs take the FP32 kernels
+constexpr double TC_SIGMA_MIN = 0.02;   // narrowest galaxy of a tensor-core catalog
+constexpr int64_t TC_GRP_BLK = 16384;   // 64-galaxy blocks per group of pixels (operand images: 512 MiB)
+constexpr int TC_KSPLIT = 128;          // blocks per gather item; longer ranges are split
+struct TcBatch {
+    int n_cols, nkc;
+    float sc, gfac;     // 1/Z scale; 2^12 / (dz sc)
+    uint4 *vimg;        // [nkc][hi, lo] 16 KB images of the norm pass's column operand
+    float *dvT;         // [TC_COLS][n_z] dv_j(z_a)
+    uint4 *cimg;        // [group blocks][hi, lo] 16 KB images of 1/Z
+    float *part;        // [slots][TC_M][TC_N] partial sums of split items
+    int *err;           // [16]: [0] timeout flag, [4..7] item counters
+    float *out[TC_COLS];
+};
+struct TcCols {
+    int n;
+    const double *fwd[TC_COLS];
+    double Om[TC_COLS];
+};
+struct TcHost {
+    std::vector<int64_t> gblk, gitem, gred;  // [groups + 1] offsets of blocks, items, reductions
+    int64_t max_gblk = 0;
+    int32_t max_slots = 0;
+};
+size_t tc_scratch_bytes(const DevCatalog &c, const TcHost &h);
+int launch_galaxy_profile_tc(const DevCatalog &c, const TcHost &h, const TcCols &m, float *const *out, char *scratch,
+                             cudaStream_t st);
+// Load-time plan from the galaxies' stored (z, sigma) as the kernels decode
+// them (sorted by z inside a pixel) and each pixel's widest stored sigma;
+// sets c.tc_ok, c.tc_sc, c.tc_nblk and fills the lists.
+void tc_plan(int64_t np, const int64_t *goff, const float *zs, const float *ss, const float *smax, int n_z,
+             double dz, bool incomplete, int kde_mode, DevCatalog &c, TcHost &h, std::vector<int2> &blk,
+             std::vector<float2> &coef, std::vector<int4> &items, std::vector<int32_t> &islot,
+             std::vector<int4> &reds);
 // dG/dOm of the galaxy profile (FP64 from dv, dvO, or FP32 from their FP32
 // copies); invZ, ZO: [n_gal] scratch of the precision's type; out [n_pix x n_z].
 // fwd, fwdO: the D_c table and its Om derivative (the missing-galaxy term of

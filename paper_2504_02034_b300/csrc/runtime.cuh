@@ -61,6 +61,7 @@ struct Catalog {
     chimera_catalog_info_t info{};
     std::map<std::pair<uint64_t, int>, ProfEntry> prof;
     std::atomic<int> in_use{0};
+    TcHost tc;  // tensor-core profile plan (used when d.tc_ok)
 };
 
 // Device and pinned buffers for one stream of likelihood calls.
@@ -138,6 +139,7 @@ struct ProfView {
     float *dvm, *invZm;   // [2 x (n_z+1) x PROF_MB], [2 x n_gal x PROF_MB]
     double *adv, *advO;   // adjoint: [n_z] FP64 then [n_z] FP32, each
     double *ainvZ, *aZO;  // adjoint: [n_gal] each
+    char *tc;             // tensor-core profiles: tc_scratch_bytes
 };
 
 struct Ctx {
@@ -203,7 +205,7 @@ void evict_profiles(Ctx &ctx, Catalog &cat, size_t need);
 bool make_room(Ctx &ctx, size_t need);
 // The profile scratch sized for catalog c, after the previous use on any
 // stream (st waits on it); release records the end of this use on st.
-int prof_scratch_acquire(Ctx &ctx, const DevCatalog &c, cudaStream_t st, ProfView *v);
+int prof_scratch_acquire(Ctx &ctx, const DevCatalog &c, cudaStream_t st, ProfView *v, const TcHost *tc = nullptr);
 int prof_scratch_release(Ctx &ctx, cudaStream_t st);
 void prof_scratch_free(Ctx &ctx);
 void free_prof_entry(Ctx &ctx, ProfEntry &e);

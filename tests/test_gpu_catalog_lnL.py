@@ -105,3 +105,35 @@ def test_differentiation_catalog_2_of_64_points(chim, ctx, orc):
         ref = oc.loglike(th[h])
         _check("diff_c4[h=%d]" % h, lnL[h], st[h], ref, cat["n_events"], chim.MIXED)
         _check("diff_c4[h=%d]" % h, lnL64[q], st64[q], ref, cat["n_events"], chim.FP64)
+
+
+def test_photometric_storage_rounding_is_stated(chim, ctx, orc):
+    """Error of the 16-bit galaxy storage on the photometric catalog (300
+    events, x3 galaxies), against the unrounded FP64 galaxies, for BF16 (the
+    configuration's storage) and F16: ln L of the mixed path minus the oracle
+    on the unrounded catalog, split into the storage part (the oracle on the
+    rounded galaxies minus the oracle on the unrounded ones: a property of
+    the input) and the kernel part (the mixed path minus the oracle on the
+    rounded galaxies, within the mixed path's 1e-3).  The storage parts are
+    printed (MEASURED) and bounded loosely: BF16 keeps 8 bits of the z offset
+    from the pixel's smallest z (~1e-4 in ln I per event), F16 11."""
+    base = sc.config_catalog(3)
+    th = sc.config_hyperpoints(3)
+    hs = [0, 255]
+    raw = orc.Catalog(base)
+    ref_raw = [raw.loglike(th[h])["lnL"] for h in hs]
+    for storage, name, bound in ((sc.GAL_BF16, "bf16", 0.05), (sc.GAL_F16, "f16", 5e-3)):
+        cat = dict(base)
+        cat["gal_storage"] = storage
+        cid = ctx.load(cat)
+        try:
+            lnL, _, _ = ctx.loglike(cid, th[hs], chim.MIXED)
+        finally:
+            ctx.unload(cid)
+        q = orc.Catalog(sc.quantize_galaxies(cat, storage))
+        for k, h in enumerate(hs):
+            rq = q.loglike(th[h])["lnL"]
+            print("MEASURED photo_c3 storage=%s h=%d storage part %.3e kernel part %.3e total %.3e"
+                  % (name, h, rq - ref_raw[k], lnL[k] - rq, lnL[k] - ref_raw[k]))
+            assert abs(lnL[k] - rq) <= 1e-3, (name, h)
+            assert abs(rq - ref_raw[k]) <= bound, (name, h)

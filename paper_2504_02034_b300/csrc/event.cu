@@ -142,14 +142,13 @@ struct MixLayout {
         seg_pad = pad4(max_seg + 1);
         gmax_pad = pad4(max_groups);
     }
-    // int4: group metadata; floats: zs, ws, Fs, D tables, C table (both
-    // signs of tau), group results, segment prefactors; ints: segment valid
-    // counts, starts and KDE support ranges
+    // int4: group metadata and descriptors (two per group); floats: zs, ws,
+    // Fs, D tables, C table (both signs of tau), group prefactors / results;
+    // staged segment offsets and prefactors; the reduction scratch
     __host__ __device__ size_t bytes() const {
-        return sizeof(int4) * (size_t)gmax_pad +
-               sizeof(float) * (2 * (size_t)ns_pad + nz_pad + (size_t)EV_WARPS * DCAP + 2 * CCAP + gmax_pad + seg_pad) +
-               sizeof(int) * 4 * (size_t)seg_pad + sizeof(double) * 2 * (size_t)seg_pad +
-               sizeof(double) * (8 + EV_WARPS * 8);
+        return sizeof(int4) * 2 * (size_t)gmax_pad +
+               sizeof(float) * (2 * (size_t)ns_pad + nz_pad + (size_t)EV_WARPS * DCAP + 2 * CCAP + gmax_pad) +
+               sizeof(double) * 2 * (size_t)seg_pad + sizeof(double) * (8 + EV_WARPS * 8);
     }
 };
 
@@ -550,23 +549,24 @@ __global__ void __launch_bounds__(RW_THREADS, RW_MINB) k_reweight(DevCatalog c, 
 
 // K4 (mixed): the event integral for hyperpoints h0 .. h0+nh-1 from the
 // reweighted samples of the tile buffer, one block per (event, point).
+// The block first describes every warp group once, one thread per group
+// (valid count, grid range, origin, table length and evaluation path), so
+// that the warps of phase B do not each repeat that bookkeeping on all of
+// their lanes.
+enum : int { GP_NONE = 0, GP_SMALL = 1, GP_UNION = 2, GP_LANE = 3, GP_DIRECT = 4, GP_BIG = 16 };
 __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, CallPtrs p, int h0, int nh) {
     extern __shared__ float4 smem4[];
     const MixLayout L(c.max_ns, c.n_z, c.max_seg, c.max_groups);
-    int4 *grp = reinterpret_cast<int4 *>(smem4);
-    float *zs = reinterpret_cast<float *>(grp + L.gmax_pad);
+    int4 *grp = reinterpret_cast<int4 *>(smem4);  // group metadata, then (lo, cnt, A0, A1)
+    int4 *gd1 = grp + L.gmax_pad;                   // (t_o, nq, path | GP_BIG, profile row)
+    float *zs = reinterpret_cast<float *>(gd1 + L.gmax_pad);
     float *ws = zs + L.ns_pad;
     float *Fs = ws + L.ns_pad;
     float *Dt = Fs + L.nz_pad;
     float *CT2 = Dt + EV_WARPS * DCAP;  // C at tau = t - CCAP, t in [0, 2 CCAP)
     float *CT = CT2 + CCAP;             // C at tau, tau in [-CCAP, CCAP)
-    float *gres = CT2 + 2 * CCAP;
-    float *segpf = gres + L.gmax_pad;
-    int *segv = reinterpret_cast<int *>(segpf + L.seg_pad);
-    int *seglo = segv + L.seg_pad;
-    int *segA0 = seglo + L.seg_pad;  // KDE support of each segment on the grid
-    int *segA1 = segA0 + L.seg_pad;
-    long long *seg64 = reinterpret_cast<long long *>(segA1 + L.seg_pad);  // staged segment offsets
+    float *gres = CT2 + 2 * CCAP;       // per group: its prefactor, then its value
+    long long *seg64 = reinterpret_cast<long long *>(gres + L.gmax_pad);  // staged segment offsets
     double *spf64 = reinterpret_cast<double *>(seg64 + L.seg_pad);        // staged prefactors
     double *red = spf64 + L.seg_pad;
     __shared__ int s_gctr;
@@ -578,6 +578,7 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const size_t out = (size_t)h * c.n_events + ev;
     const HP &hp = p.hp[h];
+    const double bd = p.bw[out];  // the reweighting kernel's FP32 bandwidth (in flight with the status)
     if (hp.status & (CHIMERA_PT_OUT_OF_SUPPORT | CHIMERA_PT_NONMONOTONE)) {
         if (tid == 0) { p.lnI[out] = 0.0; p.bw[out] = 0.0; }
         return;
@@ -608,48 +609,88 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
     // F(z_a) (the trapezoid weight of the two end points is applied below)
     for (int a = tid; a < nz; a += EV_THREADS) cp_async4(Fs + a, p.F32 + (size_t)h * nz + a);
     cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
-    if (tid == 0) Fs[0] *= 0.5f;
-    if (tid == 1 && nz > 1) Fs[nz - 1] *= 0.5f;
-    for (int k = tid; k <= nseg; k += EV_THREADS) {
-        seglo[k] = (int)(seg64[k] - s0);
-        if (k < nseg) segpf[k] = (float)spf64[k];
-    }
-    __syncthreads();
-    const double bd = p.bw[out];  // the reweighting kernel's FP32 bandwidth
-    const float b = (float)bd;
+    // per-point constants while the copies are in flight:
     // 1/(sqrt2 b) and dz/(sqrt2 b) with 1/sqrt2 and dz as float pairs, so
     // that no constant rounded to float scales every Gaussian of the event
     // alike (FP32 only: an FP64 division in every thread would cost B300's
     // FP64 pipe more than the rest of the prologue)
+    const float b = (float)bd;
     const float ib = 1.f / b;
     const float inv_s2b = fmaf(0.707106769084930419921875f, ib, 1.2101617042e-8f * ib);
     const float dz_lo = c.dz_lo32;
     const float ds = fmaf(dz, inv_s2b, dz_lo * inv_s2b);
     const float halfk = KW32 * b;
+    const int Tw = (int)ceilf(halfk * inv_dz + 0.5f);
+    const bool vec4 = (nz & 3) == 0;  // profile rows 16-byte aligned
+    cp_async_wait<0>();
+    __syncthreads();
 
-    // ---- Gaussian factor table C_t = exp(-(ds t)^2) and segment valid counts
+    // ---- the Gaussian factor table C_t = exp(-(ds t)^2), the trapezoid
+    // end weights and one descriptor per warp group
     for (int t = tid; t < 2 * CCAP; t += EV_THREADS) {
         float x = ds * (float)(t - CCAP);
         CT2[t] = expc(-x * x);
     }
-    for (int k = tid; k < nseg; k += EV_THREADS) {
-        int lo = seglo[k], hi = seglo[k + 1];
-        int l = lo, r = hi;
-        while (l < r) {
-            int mm = (l + r) >> 1;
-            if (zs[mm] < CUDART_INF_F) l = mm + 1; else r = mm;
+    if (tid == 0) Fs[0] *= 0.5f;
+    if (tid == 1 && nz > 1) Fs[nz - 1] *= 0.5f;
+    for (int g = tid; g < ngroups; g += EV_THREADS) {
+        const int4 gi = grp[g];  // (first sample, samples, segment, -)
+        const int sk = gi.z;
+        const int seg_lo = (int)(seg64[sk] - s0), seg_hi = (int)(seg64[sk + 1] - s0);
+        // the segment's valid samples are a prefix (redshifts beyond the
+        // table are +inf and sort last)
+        int nv = seg_hi - seg_lo;
+        if (nv > 0 && !(zs[seg_hi - 1] < CUDART_INF_F)) {
+            int l = seg_lo, r = seg_hi;
+            while (l < r) {
+                const int mm = (l + r) >> 1;
+                if (zs[mm] < CUDART_INF_F) l = mm + 1; else r = mm;
+            }
+            nv = l - seg_lo;
         }
-        segv[k] = l - lo;
-        // KDE support: the segment's samples' range +- KDE_MARGIN b
-        if (l > lo) {
-            segA0[k] = max(0, (int)ceilf((zs[lo] - (float)KDE_MARGIN * b) * inv_dz));
-            segA1[k] = min(nz - 1, (int)floorf((zs[l - 1] + (float)KDE_MARGIN * b) * inv_dz));
-        } else {
-            segA0[k] = 0;
-            segA1[k] = -1;
+        const int lo = gi.x;
+        const int cnt = min(gi.y, nv - (lo - seg_lo));  // valid samples only
+        int A0 = 0, A1 = -1, t_o = 0, nq = 0, path = GP_NONE;
+        if (cnt > 0) {
+            // KDE support of the segment: its samples' range +- KDE_MARGIN b
+            const int s_lo = max(0, (int)ceilf((zs[seg_lo] - (float)KDE_MARGIN * b) * inv_dz));
+            const int s_hi = min(nz - 1, (int)floorf((zs[seg_lo + nv - 1] + (float)KDE_MARGIN * b) * inv_dz));
+            const float zlo = zs[lo], zhi = zs[lo + cnt - 1];
+            const float spread = zhi - zlo;
+            // grid range the group can touch
+            const float fA0 = floorf((zlo - halfk) * inv_dz), fA1 = ceilf((zhi + halfk) * inv_dz);
+            A0 = fA0 < (float)s_lo ? s_lo : (int)fA0;
+            A1 = fA1 > (float)s_hi ? s_hi : (int)fA1;
+            if (A0 <= A1) {
+                if (cnt <= SMALL_CNT) {
+                    path = GP_SMALL;
+                } else {
+                    // group origin; a multiple of 4 when the profile rows are
+                    // 16-byte aligned, so that the table is staged as float4
+                    const float tof = vec4 ? 4.f * rintf(0.125f * (zlo + zhi) * inv_dz)
+                                           : rintf(0.5f * (zlo + zhi) * inv_dz);
+                    t_o = tof > 1e8f ? 100000000 : (int)tof;
+                    const int thi = A1 - t_o, tlo = t_o - A0;  // tau in [-tlo, thi]
+                    const int nqf = thi >= 0 ? (thi + 4) >> 2 : 0;
+                    const int nqb = tlo >= 1 ? (tlo + 3) >> 2 : 0;
+                    nq = max(nqf, nqb);  // symmetric table, zero-padded
+                    // shared origin for spreads up to 16 b; beyond 8 b the table is
+                    // scaled by 2^29 (undone in A, exactly) to keep every relevant
+                    // coefficient and Horner intermediate in the normal float range
+                    if (ds <= 0.5f && spread <= 16.f * b && thi >= -1 && tlo >= 0 && 8 * nq <= DCAP &&
+                        4 * nq < CCAP)
+                        path = GP_UNION | (spread > 8.f * b ? GP_BIG : 0);
+                    else if (ds <= 2.f && Tw + 2 < CCAP && (A1 - A0 + 1) + 2 * Tw + 4 <= DCAP)
+                        path = GP_LANE;
+                    else
+                        path = GP_DIRECT;
+                }
+            }
         }
+        const int row = c.kde_mode == CHIMERA_KDE_MANY_1D ? sg0 + sk : ev;
+        grp[g] = make_int4(lo, cnt, A0, A1);
+        gd1[g] = make_int4(t_o, nq, path, row);
+        gres[g] = (float)spf64[sk];
     }
     __syncthreads();
 
@@ -658,103 +699,78 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
     // slots are added in group order, so the result does not depend on timing.
     float *D = Dt + wid * DCAP;
     const float *prof = reinterpret_cast<const float *>(p.prof[h]);
-    const int Tw = (int)ceilf(halfk * inv_dz + 0.5f);
-    const bool vec4 = (nz & 3) == 0;  // profile rows 16-byte aligned
     unsigned long long npairs = 0;  // algorithmic pair count (roofline only)
     while (true) {
         int g = 0;
         if (lane == 0) g = atomicAdd(&s_gctr, 1);
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= ngroups) break;
-        const int4 gi = grp[g];
-        const int sk = gi.z;
-        const int seg_lo = seglo[sk];
-        const int lo = gi.x;
-        const int cnt = min(gi.y, segv[sk] - (lo - seg_lo));  // valid samples only
+        const int4 d0 = grp[g], d1 = gd1[g];
+        const int lo = d0.x, cnt = d0.y, A0 = d0.z, A1 = d0.w;
+        const int path = d1.z & 15;
         float v = 0.f;
-        if (cnt > 0) {
-            const float pf = segpf[sk];
-            const int64_t row = c.kde_mode == CHIMERA_KDE_MANY_1D ? (int64_t)(sg0 + sk) : (int64_t)ev;
-            const float *G = prof + row * nz;
-            const int s_lo = segA0[sk], s_hi = segA1[sk];  // KDE support of the segment
-            const float zlo = zs[lo], zhi = zs[lo + cnt - 1];
-            const float spread = zhi - zlo;
+        if (path != GP_NONE) {
+            const float pf = gres[g];
+            const float *G = prof + (int64_t)d1.w * nz;
             if (p.pairs) {
                 for (int j = lane; j < cnt; j += 32) {
                     float z = zs[lo + j];
                     if (ws[lo + j] == 0.f) continue;
-                    int a0 = max(s_lo, (int)ceilf((z - halfk) * inv_dz));
-                    int a1 = min(s_hi, (int)floorf((z + halfk) * inv_dz));
+                    int a0 = max(A0, (int)ceilf((z - halfk) * inv_dz));
+                    int a1 = min(A1, (int)floorf((z + halfk) * inv_dz));
                     if (a1 >= a0) npairs += (unsigned long long)(a1 - a0 + 1);
                 }
             }
-            // grid range the group can touch
-            const float fA0 = floorf((zlo - halfk) * inv_dz), fA1 = ceilf((zhi + halfk) * inv_dz);
-            const int A0 = fA0 < (float)s_lo ? s_lo : (int)fA0;
-            const int A1 = fA1 > (float)s_hi ? s_hi : (int)fA1;
-            if (A0 <= A1 && cnt <= SMALL_CNT) {
+            if (path == GP_SMALL) {
                 // a few samples: lanes over the grid points, direct exponentials
                 v = small_group(zs + lo, ws + lo, cnt, A0, A1, G, Fs, dz, dz_lo, inv_s2b, halfk, lane);
-            } else if (A0 <= A1) {
-                // group origin; a multiple of 4 when the profile rows are
-                // 16-byte aligned, so that the table is staged as float4
-                const float tof = vec4 ? 4.f * rintf(0.125f * (zlo + zhi) * inv_dz) : rintf(0.5f * (zlo + zhi) * inv_dz);
-                const int t_o = tof > 1e8f ? 100000000 : (int)tof;
-                const int thi = A1 - t_o, tlo = t_o - A0;  // tau in [-tlo, thi]
-                const int nqf = thi >= 0 ? (thi + 4) >> 2 : 0;
-                const int nqb = tlo >= 1 ? (tlo + 3) >> 2 : 0;
-                const int nq = max(nqf, nqb);  // symmetric table, zero-padded
-                // shared origin for spreads up to 16 b; beyond 8 b the table is
-                // scaled by 2^29 (undone in A, exactly) to keep every relevant
-                // coefficient and Horner intermediate in the normal float range
-                const bool uni = ds <= 0.5f && spread <= 16.f * b && thi >= -1 && tlo >= 0 &&
-                                 8 * nq <= DCAP && 4 * nq < CCAP;
-                if (uni) {
-                    const float iscale = spread > 8.f * b ? 1.862645149230957e-9f : 1.f;  // 2^-29
-                    const float scale = spread > 8.f * b ? 536870912.f : 1.f;             // 2^29
-                    __syncwarp();
-                    if (vec4) stage_table4(D, nq, t_o - 4 * nq, A0, A1, G, Fs, CT - 4 * nq, scale, lane);
-                    else stage_table<true>(D, 8 * nq, t_o - 4 * nq, A0, A1, G, Fs, CT, 4 * nq, scale, lane);
-                    __syncwarp();
-                    const float zo = fmaf((float)t_o, dz, (float)t_o * dz_lo);  // t_o dz without dz's rounding
+            } else if (path == GP_UNION) {
+                const int t_o = d1.x, nq = d1.y;
+                const bool big = (d1.z & GP_BIG) != 0;
+                const float iscale = big ? 1.862645149230957e-9f : 1.f;  // 2^-29
+                const float scale = big ? 536870912.f : 1.f;             // 2^29
+                __syncwarp();
+                if (vec4) stage_table4(D, nq, t_o - 4 * nq, A0, A1, G, Fs, CT - 4 * nq, scale, lane);
+                else stage_table<true>(D, 8 * nq, t_o - 4 * nq, A0, A1, G, Fs, CT, 4 * nq, scale, lane);
+                __syncwarp();
+                const float zo = fmaf((float)t_o, dz, (float)t_o * dz_lo);  // t_o dz without dz's rounding
 #define CHIM_UNION(R) v = union_samples<R>(D, nq, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, iscale)
-                    switch ((cnt + 31) >> 5) {
-                        case 1: CHIM_UNION(1); break;
-                        case 2: CHIM_UNION(2); break;
-                        case 3: CHIM_UNION(3); break;
-                        default: CHIM_UNION(4); break;
-                    }
+                switch ((cnt + 31) >> 5) {
+                    case 1: CHIM_UNION(1); break;
+                    case 2: CHIM_UNION(2); break;
+                    case 3: CHIM_UNION(3); break;
+                    default: CHIM_UNION(4); break;
+                }
 #undef CHIM_UNION
-                } else if (ds <= 2.f && Tw + 2 < CCAP && (A1 - A0 + 1) + 2 * Tw + 4 <= DCAP) {
-                    // stage H' on [base, base + span) with zeros outside [A0, A1]
-                    const int base = A0 - Tw - 2, span = (A1 - A0 + 1) + 2 * Tw + 4;
-                    __syncwarp();
-                    stage_table<false>(D, span, base, A0, A1, G, Fs, CT, 0, 1.f, lane);
-                    __syncwarp();
-                    for (int j = lane; j < cnt; j += 32) {
-                        float w = ws[lo + j];
-                        if (w == 0.f) continue;
-                        float z = zs[lo + j];
-                        int ts = (int)rintf(fminf(z * inv_dz, 1e8f));
-                        ts = min(max(ts, A0 - 1), A1 + 1);
-                        // a sample further than its window from [A0, A1] adds nothing
-                        // (and would push exp(2 u ds) out of range)
-                        if (fabsf(z - ts * dz) > halfk + dz) continue;
-                        v += w * lane_chain(D + (ts - base), CT, Tw, z, ts, dz, dz_lo, inv_s2b, ds);
+            } else if (path == GP_LANE) {
+                // stage H' on [base, base + span) with zeros outside [A0, A1]
+                const int base = A0 - Tw - 2, span = (A1 - A0 + 1) + 2 * Tw + 4;
+                __syncwarp();
+                stage_table<false>(D, span, base, A0, A1, G, Fs, CT, 0, 1.f, lane);
+                __syncwarp();
+                for (int j = lane; j < cnt; j += 32) {
+                    float w = ws[lo + j];
+                    if (w == 0.f) continue;
+                    float z = zs[lo + j];
+                    int ts = (int)rintf(fminf(z * inv_dz, 1e8f));
+                    ts = min(max(ts, A0 - 1), A1 + 1);
+                    // a sample further than its window from [A0, A1] adds nothing
+                    // (and would push exp(2 u ds) out of range)
+                    if (fabsf(z - ts * dz) > halfk + dz) continue;
+                    v += w * lane_chain(D + (ts - base), CT, Tw, z, ts, dz, dz_lo, inv_s2b, ds);
+                }
+            } else {
+                for (int j = lane; j < cnt; j += 32) {
+                    float z = zs[lo + j], w = ws[lo + j];
+                    if (w == 0.f) continue;
+                    int a0 = max(A0, (int)ceilf((z - halfk) * inv_dz));
+                    int a1 = min(A1, (int)floorf((z + halfk) * inv_dz));
+                    float sacc = 0.f;
+                    for (int a = a0; a <= a1; a++) {
+                        float x = (fmaf((float)a, dz, (float)a * dz_lo) - z) * inv_s2b;
+                        sacc += expf(-x * x) * Fs[a] * G[a];
                     }
-                } else {
-                    for (int j = lane; j < cnt; j += 32) {
-                        float z = zs[lo + j], w = ws[lo + j];
-                        if (w == 0.f) continue;
-                        int a0 = max(A0, (int)ceilf((z - halfk) * inv_dz));
-                        int a1 = min(A1, (int)floorf((z + halfk) * inv_dz));
-                        float sacc = 0.f;
-                        for (int a = a0; a <= a1; a++) {
-                            float x = (fmaf((float)a, dz, (float)a * dz_lo) - z) * inv_s2b;
-                            sacc += expf(-x * x) * Fs[a] * G[a];
-                        }
-                        v += w * sacc;
-                    }
+                    v += w * sacc;
                 }
             }
             // within a group a plain tree (32 lanes; compensating it too was

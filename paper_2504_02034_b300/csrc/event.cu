@@ -153,17 +153,25 @@ struct MixLayout {
 };
 
 // The per-sample sums are polynomials in B = exp(2 u ds):
+// The per-sample sums are polynomials in B = exp(2 u ds):
 //   sum_{tau >= 0} D_tau B^tau      and      sum_{tau >= 1} D_-tau B^-tau,
 // evaluated by Horner's rule from the highest power down: one FMA per
 // (sample, grid point).  The intermediates are partial sums divided by
 // exp(-u^2) B^tau, so they stay within the float range for |u| <= 3.1.
+// The two chains of a sample run side by side as one float2 (the forward
+// and backward partial sums, multipliers B and 1/B), one paired FFMA2 of
+// sm_100+ per step of both, on a table that stores the coefficients of a
+// step in pairs: P_k = (D_k, D_-k-1), k in [0, 4 nq), read as float4 from
+// the top down.  Each element rounds as a scalar fmaf would, so the sums
+// are those of two scalar chains.
 // R samples per lane (lane, lane+32, ...) of a group share one table; each
 // sample's weight and its factor exp(-u^2) are folded into one coefficient
-// before the chains, so a sample holds five registers through the loop.
+// before the chains.
 template <int R>
 __device__ __forceinline__ float union_samples(const float *D, int nq, const float *z, const float *w, int cnt,
                                                int lane, float zo, float inv_s2b, float ds, float iscale) {
-    float cw[R], B[R], Bi[R], af[R], ab[R];
+    float cw[R];
+    float2 m[R], s[R];
 #pragma unroll
     for (int r = 0; r < R; r++) {
         const int j = lane + 32 * r;
@@ -174,53 +182,43 @@ __device__ __forceinline__ float union_samples(const float *D, int nq, const flo
         // accurate expc gave no smaller shared error at this spot (the per-
         // sample factors' errors differ between samples) and cost 6 % of K4
         cw[r] = in ? w[j] * (__expf(-u * u) * iscale) : 0.f;
-        B[r] = __expf(2.f * u * ds);
-        Bi[r] = __expf(-2.f * u * ds);
-        af[r] = 0.f;
-        ab[r] = 0.f;
+        m[r] = make_float2(__expf(2.f * u * ds), __expf(-2.f * u * ds));
+        s[r] = make_float2(0.f, 0.f);
     }
-    // the table holds tau in [-4 nq, 4 nq): forward coefficients
-    // tau = 4q .. 4q+3 from q = nq-1 down, backward tau = -4q-4 .. -4q-1
-    // from q = nq-1 down, consumed together (two independent chains)
-    const float4 *pf = reinterpret_cast<const float4 *>(D) + 2 * nq - 1;
-    const float4 *pb = reinterpret_cast<const float4 *>(D);
+    const float4 *P4 = reinterpret_cast<const float4 *>(D);
 #pragma unroll 2
-    for (int it = 0; it < nq; it++) {
-        const float4 d = pf[-it], e = pb[it];
+    for (int it = nq - 1; it >= 0; it--) {
+        const float4 q1 = P4[2 * it + 1], q0 = P4[2 * it];  // k = 4 it + 2, +3 and k = 4 it, +1
 #pragma unroll
-        for (int r = 0; r < R; r++) {
-            af[r] = fmaf(af[r], B[r], d.w);
-            ab[r] = fmaf(ab[r], Bi[r], e.x);
-            af[r] = fmaf(af[r], B[r], d.z);
-            ab[r] = fmaf(ab[r], Bi[r], e.y);
-            af[r] = fmaf(af[r], B[r], d.y);
-            ab[r] = fmaf(ab[r], Bi[r], e.z);
-            af[r] = fmaf(af[r], B[r], d.x);
-            ab[r] = fmaf(ab[r], Bi[r], e.w);
-        }
+        for (int r = 0; r < R; r++) s[r] = __ffma2_rn(s[r], m[r], make_float2(q1.z, q1.w));
+#pragma unroll
+        for (int r = 0; r < R; r++) s[r] = __ffma2_rn(s[r], m[r], make_float2(q1.x, q1.y));
+#pragma unroll
+        for (int r = 0; r < R; r++) s[r] = __ffma2_rn(s[r], m[r], make_float2(q0.z, q0.w));
+#pragma unroll
+        for (int r = 0; r < R; r++) s[r] = __ffma2_rn(s[r], m[r], make_float2(q0.x, q0.y));
     }
     float v = 0.f;
 #pragma unroll
-    for (int r = 0; r < R; r++) v = fmaf(cw[r], fmaf(Bi[r], ab[r], af[r]), v);
+    for (int r = 0; r < R; r++) v = fmaf(cw[r], fmaf(m[r].y, s[r].y, s[r].x), v);
     return v;
 }
 
-// As stage_table<true>, as float4: a_first and the C-table pointer Cq
-// (C at tau = -4 nq) are multiples of 4, G and Fs are 16-byte aligned, so
-// each lane builds four entries from one 128-bit load of each operand.
-__device__ __forceinline__ void stage_table4(float *D, int nq, int a_first, int A0, int A1, const float *G,
-                                             const float *Fs, const float *Cq, float scale, int lane) {
+// The paired table of union_samples for a group with origin t_o (a multiple
+// of 4; G and Fs 16-byte aligned): D_tau = C_|tau| scale F'(z_a) G(z_a) at
+// a = t_o + tau, zero outside [A0, A1].  Each lane builds four forward
+// (tau = 4i .. 4i+3) and four backward (tau = -4i-4 .. -4i-1) entries from
+// one 128-bit load of each operand and interleaves them into P.
+__device__ __forceinline__ void stage_table4(float *D, int nq, int t_o, int A0, int A1, const float *G,
+                                             const float *Fs, const float *CT, float scale, int lane) {
     float4 *D4 = reinterpret_cast<float4 *>(D);
-    const float4 *C4 = reinterpret_cast<const float4 *>(Cq);
-#pragma unroll 2
-    for (int i = lane; i < 2 * nq; i += 32) {
-        const int a4 = a_first + 4 * i;
+    auto quad = [&](int a4, const float *cq) {
         float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
         if (a4 + 3 >= A0 && a4 <= A1) {
             // a4 >= A0 - 3 >= -3 and a4 is a multiple of 4, so a4 >= 0; a4 <= A1 < nz
             float4 g = __ldg(reinterpret_cast<const float4 *>(G + a4));
             const float4 f = *reinterpret_cast<const float4 *>(Fs + a4);
-            const float4 cc = C4[i];
+            const float4 cc = *reinterpret_cast<const float4 *>(cq);
             val = make_float4(cc.x * scale * f.x * g.x, cc.y * scale * f.y * g.y, cc.z * scale * f.z * g.z,
                               cc.w * scale * f.w * g.w);
             if (a4 < A0 || a4 + 3 > A1) {
@@ -230,11 +228,44 @@ __device__ __forceinline__ void stage_table4(float *D, int nq, int a_first, int 
                 if (a4 + 3 < A0 || a4 + 3 > A1) val.w = 0.f;
             }
         }
-        D4[i] = val;
+        return val;
+    };
+#pragma unroll 2
+    for (int i = lane; i < nq; i += 32) {
+        const float4 hf = quad(t_o + 4 * i, CT + 4 * i);          // tau = 4i .. 4i+3
+        const float4 hb = quad(t_o - 4 * i - 4, CT - 4 * i - 4);  // tau = -4i-4 .. -4i-1
+        D4[2 * i] = make_float4(hf.x, hb.w, hf.y, hb.z);
+        D4[2 * i + 1] = make_float4(hf.z, hb.y, hf.w, hb.x);
     }
 }
 
-// A group of at most SMALL_CNT samples: lanes take the grid points of the
+// The same table without the 16-byte alignment (n_z not a multiple of 4):
+// element 2k holds D_k and element 2k+1 holds D_-k-1; the profile loads of
+// up to eight entries per lane are issued before any of them is used.
+__device__ __forceinline__ void stage_table_p(float *D, int nq, int t_o, int A0, int A1, const float *G,
+                                              const float *Fs, const float *CT, float scale, int lane) {
+    const int len = 8 * nq;
+    for (int i0 = 0; i0 < len; i0 += 8 * 32) {
+        float gv[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int idx = i0 + u * 32 + lane;
+            const int k = idx >> 1, tau = (idx & 1) ? -k - 1 : k;
+            const int a = t_o + tau;
+            gv[u] = (idx < len && a >= A0 && a <= A1) ? __ldg(G + a) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int idx = i0 + u * 32 + lane;
+            if (idx < len) {
+                const int k = idx >> 1, tau = (idx & 1) ? -k - 1 : k;
+                const int a = t_o + tau;
+                const float f = (a >= A0 && a <= A1) ? Fs[a] : 0.f;
+                D[idx] = f * gv[u] * (CT[tau < 0 ? -tau : tau] * scale);
+            }
+        }
+    }
+}
 // group's range, each sums the samples whose window holds it (one SFU
 // exponential per pair); cheaper than a table for so few samples.
 constexpr int SMALL_CNT = 12;  // measured: 12 beats 6, 16 and 24 on the 300-event catalog
@@ -281,15 +312,14 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 
-// Warp-cooperative staging of a coefficient table: for idx < len and grid
-// point a = a_first + idx, D[idx] = C_|idx - tau0| * scale * F'(z_a) G(z_a)
-// (with the Gaussian factor when WITH_C, F' carrying the trapezoid weight),
-// zero outside [A0, A1].  The profile loads of up to eight entries per lane
-// are issued before any of them is used, so a table costs about one memory
-// latency per 256 entries instead of one per 32.
-template <bool WITH_C>
+// Warp-cooperative staging of the profile product of the per-lane path:
+// for idx < len and grid point a = a_first + idx, D[idx] = F'(z_a) G(z_a)
+// (F' carrying the trapezoid weight), zero outside [A0, A1].  The profile
+// loads of up to eight entries per lane are issued before any of them is
+// used, so a table costs about one memory latency per 256 entries instead
+// of one per 32.
 __device__ __forceinline__ void stage_table(float *D, int len, int a_first, int A0, int A1, const float *G,
-                                            const float *Fs, const float *CT, int tau0, float scale, int lane) {
+                                            const float *Fs, int lane) {
     for (int i0 = 0; i0 < len; i0 += 8 * 32) {
         float gv[8];
 #pragma unroll
@@ -304,12 +334,7 @@ __device__ __forceinline__ void stage_table(float *D, int len, int a_first, int 
             if (idx < len) {
                 const int a = a_first + idx;
                 const float f = (a >= A0 && a <= A1) ? Fs[a] : 0.f;
-                float val = f * gv[u];
-                if (WITH_C) {
-                    const int tau = idx - tau0;
-                    val *= CT[tau < 0 ? -tau : tau] * scale;
-                }
-                D[idx] = val;
+                D[idx] = f * gv[u];
             }
         }
     }
@@ -730,8 +755,8 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
                 const float iscale = big ? 1.862645149230957e-9f : 1.f;  // 2^-29
                 const float scale = big ? 536870912.f : 1.f;             // 2^29
                 __syncwarp();
-                if (vec4) stage_table4(D, nq, t_o - 4 * nq, A0, A1, G, Fs, CT - 4 * nq, scale, lane);
-                else stage_table<true>(D, 8 * nq, t_o - 4 * nq, A0, A1, G, Fs, CT, 4 * nq, scale, lane);
+                if (vec4) stage_table4(D, nq, t_o, A0, A1, G, Fs, CT, scale, lane);
+                else stage_table_p(D, nq, t_o, A0, A1, G, Fs, CT, scale, lane);
                 __syncwarp();
                 const float zo = fmaf((float)t_o, dz, (float)t_o * dz_lo);  // t_o dz without dz's rounding
 #define CHIM_UNION(R) v = union_samples<R>(D, nq, zs + lo, ws + lo, cnt, lane, zo, inv_s2b, ds, iscale)
@@ -746,7 +771,7 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
                 // stage H' on [base, base + span) with zeros outside [A0, A1]
                 const int base = A0 - Tw - 2, span = (A1 - A0 + 1) + 2 * Tw + 4;
                 __syncwarp();
-                stage_table<false>(D, span, base, A0, A1, G, Fs, CT, 0, 1.f, lane);
+                stage_table(D, span, base, A0, A1, G, Fs, lane);
                 __syncwarp();
                 for (int j = lane; j < cnt; j += 32) {
                     float w = ws[lo + j];

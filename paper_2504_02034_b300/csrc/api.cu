@@ -175,9 +175,11 @@ void ws_destroy_streams(Workspace &ws) {
     if (ws.st2) cudaStreamSynchronize(ws.st2);
     if (ws.ev_fork) cudaEventDestroy(ws.ev_fork);
     if (ws.ev_join) cudaEventDestroy(ws.ev_join);
+    if (ws.ev_tab_fork) cudaEventDestroy(ws.ev_tab_fork);
+    if (ws.ev_tab_join) cudaEventDestroy(ws.ev_tab_join);
     if (ws.st2) cudaStreamDestroy(ws.st2);
     ws.st2 = nullptr;
-    ws.ev_fork = ws.ev_join = nullptr;
+    ws.ev_fork = ws.ev_join = ws.ev_tab_fork = ws.ev_tab_join = nullptr;
 }
 
 void ws_release(Ctx &ctx, Workspace &ws) {
@@ -666,18 +668,23 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
     p.kshape = epan ? 1 : 0;
     p.jac_ps = jac_ps ? 1 : 0;
     if (p.pairs) CK(cudaMemsetAsync(p.pairs, 0, sizeof(unsigned long long) * H, ws.st));
-    launch_hyper_tables(c, p, H, precision == CHIMERA_FP64, ws.dk, ws.fmax_bits, ws.st);
-    if (ws.trace) CK(cudaEventRecord(ws.tev[2], ws.st));
-    // the selection term needs only the per-point tables: it runs on a side
-    // stream of the lowest priority beside the event kernels, whose blocks
-    // are dispatched first (the library streams have the highest priority)
+    // the side stream, of the lowest priority: the per-point FP64 scalars
+    // beside the inverse nodes, then the selection term beside the event
+    // kernels, whose blocks are dispatched first (the library streams have
+    // the highest priority)
     if (!ws.st2) {
         int lo = 0, hi = 0;
         CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
         CK(cudaStreamCreateWithPriority(&ws.st2, cudaStreamNonBlocking, lo));
         CK(cudaEventCreateWithFlags(&ws.ev_fork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&ws.ev_join, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ws.ev_tab_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ws.ev_tab_join, cudaEventDisableTiming));
     }
+    CK(launch_hyper_tables(c, p, H, precision == CHIMERA_FP64, ws.dk, ws.fmax_bits, ws.st, ws.st2,
+                           ws.ev_tab_fork, ws.ev_tab_join));
+    if (ws.trace) CK(cudaEventRecord(ws.tev[2], ws.st));
+    // the selection term needs only the per-point tables
     CK(cudaEventRecord(ws.ev_fork, ws.st));
     CK(cudaStreamWaitEvent(ws.st2, ws.ev_fork, 0));
     if (ws.trace) CK(cudaEventRecord(ws.tev[8], ws.st2));

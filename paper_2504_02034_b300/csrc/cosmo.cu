@@ -252,21 +252,31 @@ __global__ void __launch_bounds__(INV_THREADS) k_inv_nodes(DevCatalog c, CallPtr
                 z = CUDART_NAN;
                 dzdu = CUDART_NAN;
             } else {
+                // the bracket compares floats with fd, the largest float <= d
+                // (x <= d holds for a float x exactly when x <= fd), so the
+                // search needs no FP64 conversion per step
+                float fd = (float)d;
+                if ((double)fd > d) fd = __int_as_float(__float_as_int(fd) - 1);
                 int lo = 0, hi = NT_FWD - 1;  // sdk[lo] <= d < sdk[hi]
                 while (hi - lo > 1) {
                     const int mid = (lo + hi) >> 1;
-                    if ((double)sdk[mid] <= d) lo = mid; else hi = mid;
+                    if (sdk[mid] <= fd) lo = mid; else hi = mid;
                 }
-                const double dl = sdk[lo], dh = sdk[hi], den = dh - dl;
-                const double tt = den > 0.0 ? (d - dl) / den : 0.0;
-                const double t2 = tt * tt, t3 = t2 * tt;
-                z = (2 * t3 - 3 * t2 + 1) * (lo * HT) + (t3 - 2 * t2 + tt) * den / (double)dj[lo].y +
-                    (-2 * t3 + 3 * t2) * (hi * HT) + (t3 - t2) * den / (double)dj[hi].y;
+                // Hermite seed of z(d) between the bracketing nodes in FP32: the
+                // node values are FP32, so the seed carries their ~1e-7 error
+                // in any precision, and the FP64 Newton step below squares it
+                const float dl = sdk[lo], dh = sdk[hi], den = dh - dl;
+                const float tt = den > 0.f ? (float)(d - (double)dl) / den : 0.f;
+                const float t2 = tt * tt, t3 = t2 * tt;
+                const float HTf = (float)HT;  // 10 / 4096, exact in FP32
+                z = (double)((2.f * t3 - 3.f * t2 + 1.f) * ((float)lo * HTf) + (t3 - 2.f * t2 + tt) * den / dj[lo].y +
+                             (-2.f * t3 + 3.f * t2) * ((float)hi * HTf) + (t3 - t2) * den / dj[hi].y);
                 double dd, J;
                 chimd::dgw_J(z, cH * chimd::dc_hermite(fwd, z, Om), th, cH, &dd, &J);
-                const double step = (dd - d) / J;
+                const double rJ = 1.0 / J;
+                const double step = (dd - d) * rJ;
                 if (isfinite(step)) z -= step;
-                dzdu = 2.0 * u * dtop / J;
+                dzdu = 2.0 * u * dtop * rJ;
             }
         }
         const float z32 = (float)z, dzdu32 = (float)dzdu;
@@ -464,16 +474,37 @@ void launch_fwd_table(double Om, double *out, cudaStream_t st) {
     launch_fwd_tables(b, false, st);
 }
 
-void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, double *dk,
-                         unsigned long long *fmax_bits, cudaStream_t st) {
+cudaError_t launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, double *dk,
+                                unsigned long long *fmax_bits, cudaStream_t st, cudaStream_t side,
+                                cudaEvent_t ev_fork, cudaEvent_t ev_join) {
     float2 *dj = reinterpret_cast<float2 *>(dk);  // (d, J) of the forward nodes, FP32
-    cudaMemsetAsync(fmax_bits, 0, sizeof(unsigned long long) * H, st);
+    cudaError_t e = cudaMemsetAsync(fmax_bits, 0, sizeof(unsigned long long) * H, st);
+    if (e != cudaSuccess) return e;
     const int nbn = (NT_FWD + HYP_THREADS - 1) / HYP_THREADS;
     const int nbg = (c.n_z + HYP_THREADS - 1) / HYP_THREADS;
     k_nodes_grid<<<dim3(nbn + nbg, H), HYP_THREADS, 0, st>>>(c, p, dj, fmax_bits, nbn, fp64);
     const dim3 gi((NU + INV_THREADS - 1) / INV_THREADS, H);
+    const dim3 gf(fp64 ? 1 : nbg, H);
+    if (side) {
+        // k_hyper_final needs only the grid factor's maximum and the
+        // forward tables, not the inverse nodes: its per-point FP64 chains
+        // (a few threads each, latency-bound on B300's FP64 pipe) run on the
+        // side stream beside k_inv_nodes
+        if ((e = cudaEventRecord(ev_fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(side, ev_fork, 0)) != cudaSuccess) return e;
+        k_hyper_final<<<gf, HYP_THREADS, 0, side>>>(c, p, fmax_bits, fp64);
+        if ((e = cudaEventRecord(ev_join, side)) != cudaSuccess) return e;
+        k_inv_nodes<<<gi, INV_THREADS, 0, st>>>(c, p, dj);
+        return cudaStreamWaitEvent(st, ev_join, 0);
+    }
     k_inv_nodes<<<gi, INV_THREADS, 0, st>>>(c, p, dj);
-    k_hyper_final<<<dim3(fp64 ? 1 : nbg, H), HYP_THREADS, 0, st>>>(c, p, fmax_bits, fp64);
+    k_hyper_final<<<gf, HYP_THREADS, 0, st>>>(c, p, fmax_bits, fp64);
+    return cudaSuccess;
+}
+
+void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, double *dk,
+                         unsigned long long *fmax_bits, cudaStream_t st) {
+    launch_hyper_tables(c, p, H, fp64, dk, fmax_bits, st, nullptr, nullptr, nullptr);
 }
 
 }  // namespace chim

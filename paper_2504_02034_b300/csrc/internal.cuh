@@ -244,6 +244,11 @@ void launch_fwd_tables(const FwdBatch &b, bool dOm, cudaStream_t st);
 // pairs (inv32, and linv32 for log2(1+z) when given).
 void launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, double *dk,
                          unsigned long long *fmax_bits, cudaStream_t st);
+// The same with k_hyper_final on a side stream beside k_inv_nodes (forked
+// after the forward nodes with ev_fork, joined back into st with ev_join).
+cudaError_t launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, bool fp64, double *dk,
+                                unsigned long long *fmax_bits, cudaStream_t st, cudaStream_t side,
+                                cudaEvent_t ev_fork, cudaEvent_t ev_join);
 // K3: galaxy redshift prior on the grid for one Om.  dv: scratch of n_z
 // doubles followed by n_z floats, invZ: [n_gal] scratch; out64 (FP64
 // values) or out32 (stored values).

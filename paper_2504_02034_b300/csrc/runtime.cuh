@@ -99,6 +99,7 @@ struct Workspace {
     // kernels (fork after the per-point tables, join before the combine)
     cudaStream_t st2 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_tab_fork = nullptr, ev_tab_join = nullptr;  // per-point tables: k_hyper_final on st2
     // stage tracing (CUDA events around K1, K3, K4, K5, K6, K7)
     bool trace = false;
     cudaEvent_t tev[10] = {};

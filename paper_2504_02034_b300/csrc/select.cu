@@ -245,57 +245,77 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_fp64(DevCatalog c, CallP
 
 constexpr int CMB_THREADS = 256;
 
-// Block sum in a fixed order: thread t adds elements t, t+256, ... in
-// sequence, then a pairwise tree over the 256 partial sums.
-__device__ double fixed_order_sum(const double *x, int64_t n, int64_t stride, double *sh) {
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += CMB_THREADS) s += x[i * stride];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = CMB_THREADS / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
-    }
-    double r = sh[0];
-    __syncthreads();
-    return r;
-}
-
+// K6, one block per hyperpoint: the three sums (ln I over the events, and
+// the selection partials sum s and sum s^2 over the chunks) in one pass and
+// a fixed order - thread t adds elements t, t+256, ... in sequence, a warp
+// butterfly adds its 32 lanes, then the 8 warp values are added in warp
+// order - so the result does not depend on timing.  The last steps (xi,
+// N_eff, ln xi) run on two warps side by side: every FP64 operation waits on
+// B300's narrow FP64 pipe, so the block's time is its longest FP64 chain.
 __global__ void __launch_bounds__(CMB_THREADS) k_combine(DevCatalog c, CallPtrs p, int H) {
-    __shared__ double sh[2 * CMB_THREADS];
+    __shared__ double sh[3][CMB_THREADS / 32];
+    __shared__ double s_lnxi, s_xi, s_neff;
     __shared__ int s_bad;
-    const int h = blockIdx.x;
-    const HP &hp = p.hp[h];
-    if (threadIdx.x == 0) s_bad = 0;
+    const int h = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    if (t == 0) s_bad = 0;
     __syncthreads();
     const double *lnI = p.lnI + (size_t)h * c.n_events;
-    for (int i = threadIdx.x; i < c.n_events; i += CMB_THREADS)
-        if (!isfinite(lnI[i])) s_bad = 1;
-    double sI = fixed_order_sum(lnI, c.n_events, 1, sh);
-    double S1 = fixed_order_sum(p.selp + (size_t)h * p.n_chunk * 2, p.n_chunk, 2, sh);
-    double S2 = fixed_order_sum(p.selp + (size_t)h * p.n_chunk * 2 + 1, p.n_chunk, 2, sh);
-    if (threadIdx.x == 0) {
-        int st = hp.status;
-        double N = (double)c.n_inj_total;
-        double xi = S1 / N;
-        double neff = S1 > 0.0 ? S1 * S1 / (S2 - S1 * S1 / N) : 0.0;
-        if (st & (CHIMERA_PT_OUT_OF_SUPPORT | CHIMERA_PT_NONMONOTONE)) {
-            xi = 0.0;
-            neff = 0.0;
+    const double *sp = p.selp + (size_t)h * p.n_chunk * 2;
+    double a = 0.0, b1 = 0.0, b2 = 0.0;
+    bool bad = false;
+    for (int i = t; i < c.n_events; i += CMB_THREADS) {
+        const double v = lnI[i];
+        bad |= !isfinite(v);
+        a += v;
+    }
+    for (int i = t; i < p.n_chunk; i += CMB_THREADS) {
+        b1 += sp[2 * i];
+        b2 += sp[2 * i + 1];
+    }
+    if (bad) s_bad = 1;
+    a = warp_sumd(a);
+    b1 = warp_sumd(b1);
+    b2 = warp_sumd(b2);
+    if (lane == 0) {
+        sh[0][wid] = a;
+        sh[1][wid] = b1;
+        sh[2][wid] = b2;
+    }
+    __syncthreads();
+    const int st0 = p.hp[h].status;
+    const bool dead = (st0 & (CHIMERA_PT_OUT_OF_SUPPORT | CHIMERA_PT_NONMONOTONE)) != 0;
+    const double N = (double)c.n_inj_total;
+    if (t == 0) {  // xi and its log
+        double S1 = 0.0;
+        for (int w = 0; w < CMB_THREADS / 32; w++) S1 += sh[1][w];
+        const double xi = dead ? 0.0 : S1 / N;
+        s_xi = xi;
+        s_lnxi = xi > 0.0 ? log(xi) : 0.0;
+    } else if (t == 32) {  // N_eff beside it
+        double S1 = 0.0, S2 = 0.0;
+        for (int w = 0; w < CMB_THREADS / 32; w++) {
+            S1 += sh[1][w];
+            S2 += sh[2][w];
         }
+        s_neff = dead ? 0.0 : (S1 > 0.0 ? S1 * S1 / (S2 - S1 * S1 / N) : 0.0);
+    }
+    __syncthreads();
+    if (t == 0) {
+        double sI = 0.0;
+        for (int w = 0; w < CMB_THREADS / 32; w++) sI += sh[0][w];
+        int st = st0;
+        const double xi = s_xi, neff = s_neff;
         double lnL;
-        if (st & (CHIMERA_PT_OUT_OF_SUPPORT | CHIMERA_PT_NONMONOTONE)) {
+        if (dead) {
             lnL = -CUDART_INF;
         } else if (s_bad || !(xi > 0.0)) {
             lnL = -CUDART_INF;
             st |= CHIMERA_PT_OUT_OF_SUPPORT;
         } else {
-            lnL = sI - (double)c.n_events * log(xi);
+            lnL = sI - (double)c.n_events * s_lnxi;
         }
         // the effective-count warning is only meaningful for an admissible point
-        if (!(hp.status & (CHIMERA_PT_OUT_OF_SUPPORT | CHIMERA_PT_NONMONOTONE)) &&
-            !(neff >= 5.0 * c.n_events))
-            st |= CHIMERA_PT_NEFF_LOW;
+        if (!dead && !(neff >= 5.0 * c.n_events)) st |= CHIMERA_PT_NEFF_LOW;
         p.lnL[h] = lnL;
         p.neff[h] = neff;
         p.xi[h] = xi;

@@ -906,11 +906,16 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
                 Bf[r] = __expf(2.f * u[r] * ds);
                 Bb[r] = __expf(-2.f * u[r] * ds);
             }
-            float af[R][AM_NP], ab[R][AM_NP];
+            // the forward (powers of B) and backward (powers of 1/B) chains of
+            // each polynomial run side by side as one float2: one paired
+            // FFMA2 per step of both, each element rounded as a scalar fmaf
+            float2 m2[R], s2[R][AM_NP];
 #pragma unroll
-            for (int r = 0; r < R; r++)
+            for (int r = 0; r < R; r++) {
+                m2[r] = make_float2(Bf[r], Bb[r]);
 #pragma unroll
-                for (int k = 0; k < AM_NP; k++) { af[r][k] = 0.f; ab[r][k] = 0.f; }
+                for (int k = 0; k < AM_NP; k++) s2[r][k] = make_float2(0.f, 0.f);
+            }
             // Horner from the outermost offsets in, AM_CH offsets per side at
             // a time (slot i: the rows of +m and -m, m = mhi - i); the last
             // chunk also stages tau = 0, which closes the forward chain
@@ -923,7 +928,7 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
                     int tau;
                     float *dst;
                     if (i < nr) { tau = mhi - i; dst = twf + 4 * AM_SLOT * i; }
-                    else if (i < 2 * nr) { tau = -(mhi - (i - nr)); dst = twf + 4 * AM_SLOT * (i - nr) + AM_NP; }
+                    else if (i < 2 * nr) { tau = -(mhi - (i - nr)); dst = twf + 4 * AM_SLOT * (i - nr) + 1; }
                     else { tau = 0; dst = twf + 4 * AM_SLOT * AM_CH; }
                     const int a = t_o + tau;
                     float2 r0 = make_float2(0.f, 0.f), r1 = r0;
@@ -935,24 +940,30 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
                         r0 = make_float2(hh, tt * hh);
                         r1 = make_float2(tt * tt * hh, cf * __ldg(dG + a));
                     }
-                    float2 *d2 = reinterpret_cast<float2 *>(dst);
-                    d2[0] = r0;
-                    d2[1] = r1;
+                    if (i < 2 * nr) {
+                        // forward and backward coefficients of a polynomial
+                        // side by side (the paired chains read them as one float2)
+                        dst[0] = r0.x;
+                        dst[2] = r0.y;
+                        dst[4] = r1.x;
+                        dst[6] = r1.y;
+                    } else {
+                        float2 *d2 = reinterpret_cast<float2 *>(dst);
+                        d2[0] = r0;
+                        d2[1] = r1;
+                    }
                 }
                 __syncwarp();
 #pragma unroll 2
                 for (int i = 0; i < nr; i++) {
                     const float4 *sl = tw + AM_SLOT * i;
-                    const float4 v0 = sl[0], v1 = sl[1];
-                    const float cf_[AM_NP] = {v0.x, v0.y, v0.z, v0.w};
-                    const float cb_[AM_NP] = {v1.x, v1.y, v1.z, v1.w};
+                    const float4 v0 = sl[0], v1 = sl[1];  // (f0, b0, f1, b1), (f2, b2, f3, b3)
+                    const float2 c_[AM_NP] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w),
+                                              make_float2(v1.x, v1.y), make_float2(v1.z, v1.w)};
 #pragma unroll
                     for (int r = 0; r < R; r++)
 #pragma unroll
-                        for (int k = 0; k < AM_NP; k++) {
-                            af[r][k] = fmaf(af[r][k], Bf[r], cf_[k]);
-                            ab[r][k] = fmaf(ab[r][k], Bb[r], cb_[k]);
-                        }
+                        for (int k = 0; k < AM_NP; k++) s2[r][k] = __ffma2_rn(s2[r][k], m2[r], c_[k]);
                 }
                 if (last) {
                     const float4 v0 = tw[AM_SLOT * AM_CH];
@@ -960,7 +971,7 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
 #pragma unroll
                     for (int r = 0; r < R; r++)
 #pragma unroll
-                        for (int k = 0; k < AM_NP; k++) af[r][k] = fmaf(af[r][k], Bf[r], c0_[k]);
+                        for (int k = 0; k < AM_NP; k++) s2[r][k].x = fmaf(s2[r][k].x, Bf[r], c0_[k]);
                     break;
                 }
             }
@@ -972,7 +983,7 @@ __global__ void __launch_bounds__(AM_THREADS, 2) k_event_adj_mixed(DevCatalog c,
                 const float uu = u[r], E = __expf(-uu * uu - lnscale);
                 float P[AM_NP];
 #pragma unroll
-                for (int k = 0; k < AM_NP; k++) P[k] = E * fmaf(Bb[r], ab[r][k], af[r][k]);
+                for (int k = 0; k < AM_NP; k++) P[k] = E * fmaf(Bb[r], s2[r][k].y, s2[r][k].x);
                 buf[idx] = P[0];
                 buf[AM_RUN + idx] = 1.41421356f * (ds * P[1] - uu * P[0]);
                 buf[2 * AM_RUN + idx] = 2.f * (ds * ds * P[2] - 2.f * ds * uu * P[1] + uu * uu * P[0]);

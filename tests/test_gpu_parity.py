@@ -78,6 +78,18 @@ def test_scaled_o5_catalog(chim, ctx, orc, mode, xi0_variant):
     _compare(chim, ctx, orc, cat, th)
 
 
+@pytest.mark.parametrize("n_z", [999, 1001, 998])
+def test_grid_not_multiple_of_four(chim, ctx, orc, n_z):
+    """Grids whose length is not a multiple of 4: the profile rows are not
+    16-byte aligned, so the mixed event kernel stages its paired Horner
+    tables element by element instead of as float4 (both layouts must give
+    the oracle's ln I)."""
+    from synth import catalog as sc
+    cat = sc.config_catalog(2, n_events=10, n_pe=1500, n_inj=20000, gal_median=200, n_z=n_z)
+    th = sc.config_hyperpoints(2, n=3)
+    _compare(chim, ctx, orc, cat, th)
+
+
 @pytest.mark.parametrize("storage", [0, 1, 2])
 def test_photometric_16bit_storage(chim, ctx, orc, storage):
     """Photo-z galaxies (sigma = 0.05(1+z)) stored as F32 / F16 / BF16: the

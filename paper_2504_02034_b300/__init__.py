@@ -85,7 +85,8 @@ class CatalogInfo(C.Structure):
     _fields_ = [("n_events", C.c_int32), ("n_z", C.c_int32), ("n_samples", C.c_int64),
                 ("n_pixels", C.c_int64), ("n_galaxies", C.c_int64), ("n_det", C.c_int64),
                 ("device_bytes", C.c_int64), ("max_samples_per_event", C.c_int32),
-                ("max_pixels_per_event", C.c_int32), ("profile_path", C.c_int32), ("reserved", C.c_int32)]
+                ("max_pixels_per_event", C.c_int32), ("profile_path", C.c_int32),
+                ("event_kernel_warps", C.c_int32)]
 
 
 class ServeStats(C.Structure):

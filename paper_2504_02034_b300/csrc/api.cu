@@ -1303,13 +1303,14 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     // event kernels need their shared memory
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx.device);
-    if ((int)event_mixed_smem(c) > maxsm || (int)event_fp64_smem(c) > maxsm ||
+    if ((int)event_mixed_smem(c, 1) > maxsm || (int)event_fp64_smem(c) > maxsm ||
         (int)event_binned_smem(c) > maxsm || (int)event_3d_smem(c) > maxsm) {
         for (void *a : cat->allocs) cudaFree(a);
         ctx.used -= cat->bytes;
         set_error("catalog needs more shared memory per block than the device offers");
         return CHIMERA_ERR_UNSUPPORTED;
     }
+    c.ev_geom = event_mixed_pick(c);  // the mixed event kernel's block geometry
     cat->info.n_events = ne;
     cat->info.n_z = c.n_z;
     cat->info.n_samples = ns;
@@ -1320,6 +1321,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     cat->info.max_samples_per_event = max_ns;
     cat->info.max_pixels_per_event = max_np;
     cat->info.profile_path = c.tc_ok ? CHIMERA_PROFILE_TENSOR_CORES : CHIMERA_PROFILE_CUDA_CORES;
+    cat->info.event_kernel_warps = c.ev_geom == 1 ? EV_WARPS_3 : EV_WARPS_2;
     int32_t id_ = ctx.next_id++;
     ctx.cats[id_] = cat;
     *out_id = id_;

@@ -132,23 +132,24 @@ __device__ __forceinline__ double bandwidth_rule(double W1, double W2, double Vw
     return dz;
 }
 
-// Shared layout of the mixed kernel.
+// Shared layout of the mixed kernel (nw warps per block).
 struct MixLayout {
-    int ns_pad, nz_pad, seg_pad, gmax_pad;
+    int ns_pad, nz_pad, seg_pad, gmax_pad, nw;
     __host__ __device__ static int pad4(int x) { return (x + 3) & ~3; }
-    __host__ __device__ MixLayout(int max_ns, int nz, int max_seg, int max_groups) {
+    __host__ __device__ MixLayout(int max_ns, int nz, int max_seg, int max_groups, int nw_) {
         ns_pad = pad4(max_ns);
         nz_pad = pad4(nz);
         seg_pad = pad4(max_seg + 1);
         gmax_pad = pad4(max_groups);
+        nw = nw_;
     }
     // int4: group metadata and descriptors (two per group); floats: zs, ws,
     // Fs, D tables, C table (both signs of tau), group prefactors / results;
     // staged segment offsets and prefactors; the reduction scratch
     __host__ __device__ size_t bytes() const {
         return sizeof(int4) * 2 * (size_t)gmax_pad +
-               sizeof(float) * (2 * (size_t)ns_pad + nz_pad + (size_t)EV_WARPS * DCAP + 2 * CCAP + gmax_pad) +
-               sizeof(double) * 2 * (size_t)seg_pad + sizeof(double) * (8 + EV_WARPS * 8);
+               sizeof(float) * (2 * (size_t)ns_pad + nz_pad + (size_t)nw * DCAP + 2 * CCAP + gmax_pad) +
+               sizeof(double) * 2 * (size_t)seg_pad + sizeof(double) * (8 + nw * 8);
     }
 };
 
@@ -583,16 +584,18 @@ __global__ void __launch_bounds__(RW_THREADS, RW_MINB) k_reweight(DevCatalog c, 
 // that the warps of phase B do not each repeat that bookkeeping on all of
 // their lanes.
 enum : int { GP_NONE = 0, GP_SMALL = 1, GP_UNION = 2, GP_LANE = 3, GP_DIRECT = 4, GP_BIG = 16 };
-__global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, CallPtrs p, int h0, int nh) {
+template <int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) k_event_mixed(DevCatalog c, CallPtrs p, int h0, int nh) {
+    constexpr int NT = NW * 32;
     extern __shared__ float4 smem4[];
-    const MixLayout L(c.max_ns, c.n_z, c.max_seg, c.max_groups);
+    const MixLayout L(c.max_ns, c.n_z, c.max_seg, c.max_groups, NW);
     int4 *grp = reinterpret_cast<int4 *>(smem4);  // group metadata, then (lo, cnt, A0, A1)
     int4 *gd1 = grp + L.gmax_pad;                   // (t_o, nq, path | GP_BIG, profile row)
     float *zs = reinterpret_cast<float *>(gd1 + L.gmax_pad);
     float *ws = zs + L.ns_pad;
     float *Fs = ws + L.ns_pad;
     float *Dt = Fs + L.nz_pad;
-    float *CT2 = Dt + EV_WARPS * DCAP;  // C at tau = t - CCAP, t in [0, 2 CCAP)
+    float *CT2 = Dt + NW * DCAP;        // C at tau = t - CCAP, t in [0, 2 CCAP)
     float *CT = CT2 + CCAP;             // C at tau, tau in [-CCAP, CCAP)
     float *gres = CT2 + 2 * CCAP;       // per group: its prefactor, then its value
     long long *seg64 = reinterpret_cast<long long *>(gres + L.gmax_pad);  // staged segment offsets
@@ -625,18 +628,18 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
     {
         const float *zsrc = p.zw + (size_t)hl * 2 * c.n_zpad + ei.w;
         const float *wsrc = zsrc + c.n_zpad;
-        for (int i = tid; i < (ns + 3) >> 2; i += EV_THREADS) {
+        for (int i = tid; i < (ns + 3) >> 2; i += NT) {
             cp_async16(zs + 4 * i, zsrc + 4 * i);
             cp_async16(ws + 4 * i, wsrc + 4 * i);
         }
     }
-    for (int g = tid; g < ngroups; g += EV_THREADS) cp_async16(grp + g, c.groups + g0 + g);
-    for (int k = tid; k <= nseg; k += EV_THREADS) {
+    for (int g = tid; g < ngroups; g += NT) cp_async16(grp + g, c.groups + g0 + g);
+    for (int k = tid; k <= nseg; k += NT) {
         cp_async8(seg64 + k, c.seg_soff + sg0 + k);
         if (k < nseg) cp_async8(spf64 + k, c.seg_pf + sg0 + k);
     }
     // F(z_a) (the trapezoid weight of the two end points is applied below)
-    for (int a = tid; a < nz; a += EV_THREADS) cp_async4(Fs + a, p.F32 + (size_t)h * nz + a);
+    for (int a = tid; a < nz; a += NT) cp_async4(Fs + a, p.F32 + (size_t)h * nz + a);
     cp_async_commit();
     // per-point constants while the copies are in flight:
     // 1/(sqrt2 b) and dz/(sqrt2 b) with 1/sqrt2 and dz as float pairs, so
@@ -656,13 +659,13 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
 
     // ---- the Gaussian factor table C_t = exp(-(ds t)^2), the trapezoid
     // end weights and one descriptor per warp group
-    for (int t = tid; t < 2 * CCAP; t += EV_THREADS) {
+    for (int t = tid; t < 2 * CCAP; t += NT) {
         float x = ds * (float)(t - CCAP);
         CT2[t] = expc(-x * x);
     }
     if (tid == 0) Fs[0] *= 0.5f;
     if (tid == 1 && nz > 1) Fs[nz - 1] *= 0.5f;
-    for (int g = tid; g < ngroups; g += EV_THREADS) {
+    for (int g = tid; g < ngroups; g += NT) {
         const int4 gi = grp[g];  // (first sample, samples, segment, -)
         const int sk = gi.z;
         const int seg_lo = (int)(seg64[sk] - s0), seg_hi = (int)(seg64[sk + 1] - s0);
@@ -812,10 +815,11 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
     // the event's sum of the group values in a fixed order, compensated at
     // every step (FP32 with the rounding errors carried: a double reduction
     // would be the block's longest step at B300's FP64 rate), then ln I
-    // (ln_mixed)
+    // (ln_mixed); the first EV_RED threads take the groups, whatever the
+    // block size, so both geometries add them in the same order
     {
         float sacc = 0.f, cacc = 0.f;
-        for (int g = tid; g < ngroups; g += EV_THREADS) {
+        for (int g = tid; tid < EV_RED && g < ngroups; g += EV_RED) {
             float sm, e;
             two_sum(sacc, gres[g], sm, e);
             sacc = sm;
@@ -827,7 +831,7 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_event_mixed(DevCatalog c, Cal
         __syncthreads();
         if (tid == 0) {
             float I = 0.f, cI = 0.f;
-            for (int w = 0; w < EV_WARPS; w++) {
+            for (int w = 0; w < EV_RED / 32; w++) {
                 float sm, e;
                 two_sum(I, redf[w], sm, e);
                 I = sm;
@@ -1144,7 +1148,27 @@ __global__ void __launch_bounds__(EV64_THREADS) k_event_fp64(DevCatalog c, CallP
 
 }  // namespace
 
-size_t event_mixed_smem(const DevCatalog &c) { return MixLayout(c.max_ns, c.n_z, c.max_seg, c.max_groups).bytes(); }
+size_t event_mixed_smem(const DevCatalog &c, int geom) {
+    return MixLayout(c.max_ns, c.n_z, c.max_seg, c.max_groups, geom == 1 ? EV_WARPS_3 : EV_WARPS_2).bytes();
+}
+
+// Three resident blocks of 10 warps when they fit the SM's shared memory and
+// registers, else two of 16.
+int event_mixed_pick(const DevCatalog &c) {
+    const size_t smem = event_mixed_smem(c, 1);
+    if (cudaFuncSetAttribute(k_event_mixed<EV_WARPS_3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_event_mixed<EV_WARPS_3, 3>, EV_WARPS_3 * 32, smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb >= 3 ? 1 : 0;
+}
 
 size_t event_fp64_smem(const DevCatalog &c) {
     return sizeof(double) * 2 * (size_t)c.max_ns + sizeof(int) * (size_t)((c.max_seg + 2) & ~1) +
@@ -1166,10 +1190,15 @@ void launch_reweight(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cud
 }
 
 void launch_event_mixed(const DevCatalog &c, const CallPtrs &p, int h0, int nh, cudaStream_t st) {
-    size_t smem = event_mixed_smem(c);
-    cudaFuncSetAttribute(k_event_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = event_mixed_smem(c, c.ev_geom);
     const unsigned nb = (unsigned)((int64_t)c.n_events * nh);
-    if (nb) k_event_mixed<<<nb, EV_THREADS, smem, st>>>(c, p, h0, nh);
+    if (c.ev_geom == 1) {
+        cudaFuncSetAttribute(k_event_mixed<EV_WARPS_3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (nb) k_event_mixed<EV_WARPS_3, 3><<<nb, EV_WARPS_3 * 32, smem, st>>>(c, p, h0, nh);
+    } else {
+        cudaFuncSetAttribute(k_event_mixed<EV_WARPS_2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (nb) k_event_mixed<EV_WARPS_2, 2><<<nb, EV_WARPS_2 * 32, smem, st>>>(c, p, h0, nh);
+    }
 }
 
 size_t event_binned_smem(const DevCatalog &c) { return BinLayout(c.max_ns, c.n_z, c.max_seg).bytes(); }

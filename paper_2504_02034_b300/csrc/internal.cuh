@@ -33,10 +33,16 @@ constexpr int PROF_MB = 16;      // Om values per batched (mixed) profile pass
 // KDE_MARGIN bandwidths (Sec. 2.3: evaluated only where the samples are).
 constexpr double KDE_MARGIN = 6.0;
 constexpr double KWG64 = 9.0;
-// Mixed event kernel geometry.
-constexpr int EV_WARPS = 16;          // warps per block
-constexpr int EV_THREADS = EV_WARPS * 32;
-constexpr int DCAP = 768;             // D-table floats per warp
+// Mixed event kernel geometry: two instantiations, chosen per catalog at
+// load time (DevCatalog::ev_geom): 10 warps with three blocks per SM when the
+// catalog's largest event leaves room for three in shared memory (measured
+// on the 300-event catalog: 3.7 % faster than 16 warps with two, the extra
+// resident block covering the prologue and tail of the other two), else 16
+// warps with two.  Both use the same table capacity and the same partition
+// of the event sum, so they give the same results bit for bit.
+constexpr int EV_WARPS_3 = 10, EV_WARPS_2 = 16;
+constexpr int EV_RED = 256;           // threads of the event's fixed-order group sum
+constexpr int DCAP = 512;             // D-table floats per warp
 constexpr int GROUP_MAX = 128;        // samples per warp group (up to 4 per lane)
 constexpr int CCAP = DCAP / 2 + 8;    // entries of the Gaussian factor table exp(-(ds t)^2)
 // FP64 event kernel.
@@ -107,6 +113,7 @@ struct DevCatalog {
     float z_max32, dz32;  // float copies for the mixed kernels
     float dz_lo32;        // dz - dz32: grid positions a dz in FP32 as fmaf(a, dz32, a dz_lo32)
     int32_t max_ns, max_seg, max_npix;
+    int32_t ev_geom;      // mixed event kernel: 1 = 10 warps x 3 blocks per SM, 0 = 16 warps x 2
     // events
     int64_t *ev_soff;     // [n_events+1] sample offsets (sorted storage)
     int64_t *ev_poff;     // [n_events+1] flat pixel offsets
@@ -341,7 +348,9 @@ void launch_event_fp64(const DevCatalog &c, const CallPtrs &p, int H, cudaStream
 void launch_event_binned(const DevCatalog &c, const CallPtrs &p, int h0, int nh, bool binned,
                          cudaStream_t st);
 size_t event_binned_smem(const DevCatalog &c);
-size_t event_mixed_smem(const DevCatalog &c);
+size_t event_mixed_smem(const DevCatalog &c, int geom);
+// The mixed event kernel's geometry for a catalog (DevCatalog::ev_geom).
+int event_mixed_pick(const DevCatalog &c);
 size_t event_fp64_smem(const DevCatalog &c);
 // The "3D" kernel of CHIMERA_KDE_3D catalogs (FP64 only).
 size_t event_3d_smem(const DevCatalog &c);

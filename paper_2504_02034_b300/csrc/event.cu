@@ -1155,8 +1155,15 @@ size_t event_mixed_smem(const DevCatalog &c, int geom) {
 }
 
 // Three resident blocks of 10 warps when they fit the SM's shared memory and
-// registers, else two of 16.
+// registers, else two of 16 (10 again if a 16-warp block would not fit the
+// device's shared memory per block at all).
 int event_mixed_pick(const DevCatalog &c) {
+    int dev = 0, maxsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+        event_mixed_smem(c, 0) > (size_t)maxsm)
+        return 1;
+    cudaGetLastError();
     const size_t smem = event_mixed_smem(c, 1);
     if (cudaFuncSetAttribute(k_event_mixed<EV_WARPS_3, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {

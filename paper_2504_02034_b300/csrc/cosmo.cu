@@ -94,6 +94,40 @@ constexpr int HYP_THREADS = 256;
 
 __device__ double std_normal_cdf(double x) { return 0.5 * erfc(-x * 0.70710678118654752440); }
 
+// 1 / sqrt(x) in FP64 for x of order one to a few hundred: the SFU's FP32
+// estimate (rsqrtf, relative error ~2^-22) refined by two Newton-Raphson
+// steps on f(y) = y^-2 - x, y <- y (3 - x y^2) / 2, each of which squares
+// the relative error (2^-43, then below FP64 rounding): a handful of FP64
+// operations in place of a square root and a division, which matter on
+// B300's narrow FP64 pipe.
+__device__ __forceinline__ double rsqrt64(double x) {
+    double y = (double)rsqrtf((float)x);
+    y = y * (1.5 - 0.5 * x * y * y);
+    return y * (1.5 - 0.5 * x * y * y);
+}
+// The FP64 forward relation of the inverse-node kernel with 1/E from rsqrt64:
+// D_c by cubic Hermite on the forward table (slopes HT / E at the nodes),
+// d_L^gw and J = d d_L^gw / dz (Eqs. dL-em, dL-mg).
+__device__ __forceinline__ double dc_hermite_r(const double *fwd, double z, double Om) {
+    const double t = z / HT;
+    int k = (int)floor(t);
+    if (k < 0) k = 0;
+    if (k > NT_FWD - 2) k = NT_FWD - 2;
+    const double f = t - k, a0 = 1.0 + k * HT, a1 = 1.0 + (k + 1) * HT;
+    const double m0 = HT * rsqrt64(Om * a0 * a0 * a0 + 1.0 - Om), m1 = HT * rsqrt64(Om * a1 * a1 * a1 + 1.0 - Om);
+    const double f2 = f * f, f3 = f2 * f;
+    return (2 * f3 - 3 * f2 + 1) * fwd[k] + (f3 - 2 * f2 + f) * m0 + (-2 * f3 + 3 * f2) * fwd[k + 1] + (f3 - f2) * m1;
+}
+__device__ __forceinline__ void dgw_J_r(double z, double Dc, const double *th, double cH, double *d, double *J) {
+    const double a = 1.0 + z;
+    const double p = exp(-th[3] * log(a));  // (1+z)^-n
+    const double xi = th[2] + (1.0 - th[2]) * p;
+    const double dxi = -th[3] * (1.0 - th[2]) * p / a;
+    const double rE = rsqrt64(th[1] * a * a * a + 1.0 - th[1]);
+    *d = a * Dc * xi;
+    *J = (Dc + a * cH * rE) * xi + a * Dc * dxi;
+}
+
 // FP32 forward relation at z from D = D_c [Mpc]: d_L^gw and its z-derivative J.
 __device__ __forceinline__ void dgw_J32(float z, float D, float cH, float om, float xi0, float n, float &d,
                                        float &J) {
@@ -272,7 +306,7 @@ __global__ void __launch_bounds__(INV_THREADS) k_inv_nodes(DevCatalog c, CallPtr
                 z = (double)((2.f * t3 - 3.f * t2 + 1.f) * ((float)lo * HTf) + (t3 - 2.f * t2 + tt) * den / dj[lo].y +
                              (-2.f * t3 + 3.f * t2) * ((float)hi * HTf) + (t3 - t2) * den / dj[hi].y);
                 double dd, J;
-                chimd::dgw_J(z, cH * chimd::dc_hermite(fwd, z, Om), th, cH, &dd, &J);
+                dgw_J_r(z, cH * dc_hermite_r(fwd, z, Om), th, cH, &dd, &J);
                 const double rJ = 1.0 / J;
                 const double step = (dd - d) * rJ;
                 if (isfinite(step)) z -= step;
@@ -296,71 +330,67 @@ __global__ void __launch_bounds__(INV_THREADS) k_inv_nodes(DevCatalog c, CallPtr
     }
 }
 
-// K1b.3: per-hyperpoint constants (block x = 0, the independent FP64 scalars
-// one per lane) and, for mixed calls, F normalised by its maximum.
-__global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallPtrs p,
-                                                            const unsigned long long *fmax_bits, bool f64) {
+// K1b.3: per-hyperpoint constants (block x = 0: the independent FP64
+// transcendentals one per warp, then the quantities built from them) and, for
+// mixed calls, F normalised by its maximum.  Every FP64 operation waits on
+// B300's narrow FP64 pipe, so the block's time is its longest dependent FP64
+// chain: one transcendental per warp (16 warps), two short follow-ups, then
+// the assembly of the point's constants.
+constexpr int HF_THREADS = 512;
+__global__ void __launch_bounds__(HF_THREADS) k_hyper_final(DevCatalog c, CallPtrs p,
+                                                           const unsigned long long *fmax_bits, bool f64) {
     const int h = blockIdx.y, t = threadIdx.x;
-    const double Fm = f64 ? __longlong_as_double((long long)fmax_bits[h])
-                          : (double)__uint_as_float((unsigned)fmax_bits[h]);
-    // F_scale: the power of two just above the maximum, so that F / F_scale
-    // in FP32 is exact (no rounded scale shared by every grid point)
-    int fe = 0;
-    if (Fm > 0.0) frexp(Fm, &fe);
-    const double Fs = Fm > 0.0 ? ldexp(1.0, fe) : 1.0;
+    // F_scale: the power of two just above the maximum (2^e with Fm = m 2^e,
+    // m in [0.5, 1), from the exponent field of its bit pattern), so that
+    // F / F_scale in FP32 is exact (no rounded scale shared by every grid point)
+    const unsigned long long fb = fmax_bits[h];
+    const int fe = fb == 0 ? 0 : (f64 ? (int)((fb >> 52) & 0x7ff) - 1022 : (int)((fb >> 23) & 0xff) - 126);
     if (!f64) {
-        const float iFs = (float)(1.0 / Fs);
-        const int a = blockIdx.x * HYP_THREADS + t;
+        const float iFs = __int_as_float((127 - fe) << 23);  // 2^-fe, exact
+        const int a = blockIdx.x * HF_THREADS + t;
         if (a < c.n_z) p.F32[(size_t)h * c.n_z + a] *= iFs;
     }
     if (blockIdx.x != 0) return;
-    // the FP64 scalars, one warp each (lane 0), so that their transcendental
-    // chains run side by side instead of serialised by divergence
-    __shared__ double sc[20];
+    const double Fs = __longlong_as_double((long long)(1023 + fe) << 52);  // 2^fe, exact
+    __shared__ double sc[20], sx[4];
     const double *th = p.theta + 12 * h;
     const double alpha = th[4], mu = th[5], sg = th[6], mmin = th[7], mmax = th[8];
     const double lam = c.lambda_g, beta = c.beta;
     const double cH = C_KMS / th[0];
     const int w = t >> 5;
+    const bool alpha1 = fabs(1.0 - alpha) < 1e-12;
     if ((t & 31) == 0) {
-        double v = 0.0;
         switch (w) {
-            case 0:
-                v = fabs(1.0 - alpha) < 1e-12 ? log(mmax / mmin)
-                                              : (pow(mmax, 1.0 - alpha) - pow(mmin, 1.0 - alpha)) / (1.0 - alpha);
-                sc[12] = log(v);  // ln of the power law's normalisation integral
-                break;
-            case 1:
-                v = std_normal_cdf((mmax - mu) / sg) - std_normal_cdf((mmin - mu) / sg);
-                sc[13] = v > 0.0 ? log(v) : 0.0;
-                break;
-            case 2:
-                v = pow(mmin, 1.0 + beta);
-                sc[14] = log(fabs(1.0 + beta) < 1e-12 ? 1.4426950408889634074 : fabs(1.0 + beta));
-                break;
-            case 3:
-                v = chimd::dc_hermite(p.fwd[h], c.z_max, th[1]);
+            case 0: sx[0] = alpha1 ? log(mmax / mmin) : pow(mmax, 1.0 - alpha); break;
+            case 1: sx[1] = alpha1 ? 0.0 : pow(mmin, 1.0 - alpha); break;
+            case 2: sx[2] = std_normal_cdf((mmax - mu) / sg); break;
+            case 3: sx[3] = std_normal_cdf((mmin - mu) / sg); break;
+            case 4: sc[2] = pow(mmin, 1.0 + beta); break;
+            case 5: sc[14] = log(fabs(1.0 + beta) < 1e-12 ? 1.4426950408889634074 : fabs(1.0 + beta)); break;
+            case 6: {
+                const double v = chimd::dc_hermite(p.fwd[h], c.z_max, th[1]);
+                sc[3] = v;
                 sc[15] = log(3.0 / (v * v * v));
                 break;
-            case 4: {  // d_L^gw at the end of the redshift range, z = 10, in FP64
-                double J;
+            }
+            case 7: {  // d_L^gw at the end of the redshift range, z = 10, in FP64
+                double v, J;
                 chimd::dgw_J(K_Z10 * HT, cH * p.fwd[h][K_Z10], th, cH, &v, &J);
+                sc[4] = v;
                 sc[8] = sqrt(v / c.d_top) * NU;  // its inverse-table coordinate
                 break;
             }
-            case 5:
-                v = log(mmin);
-                sc[9] = log1p(th[11]);
-                sc[16] = log(th[0] / C_KMS);
-                break;
-            case 6:
-                v = log2(mmin);
+            case 8: sc[5] = log(mmin); break;
+            case 9: sc[9] = log1p(th[11]); break;
+            case 10: sc[16] = log(th[0] / C_KMS); break;
+            case 11:
+                sc[6] = log2(mmin);
                 sc[10] = 1.0 / sg;
-                sc[17] = pow(mmin, alpha);
-                sc[18] = log(sg);
                 break;
+            case 12: sc[17] = pow(mmin, alpha); break;
+            case 13: sc[18] = log(sg); break;
+            case 14: sc[7] = log2(mmax); break;
             default:
-                v = log2(mmax);
                 // ln of the constant factor of the mixed path's raw event
                 // integral: dz F_scale / (N_gal,tot sqrt(2 pi)), times 1/b per event
                 // (the mixed F32 holds F c / H0 unless the Jacobian sits on the samples)
@@ -368,7 +398,16 @@ __global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallP
                          (p.jac_ps ? 0.0 : log(th[0] / C_KMS));
                 break;
         }
-        sc[w] = v;
+    }
+    __syncthreads();
+    if (t == 0) {  // the power law's normalisation integral and its log
+        const double v = alpha1 ? sx[0] : (sx[0] - sx[1]) / (1.0 - alpha);
+        sc[0] = v;
+        sc[12] = log(v);
+    } else if (t == 32) {  // the truncated Gaussian's mass and its log
+        const double v = sx[2] - sx[3];
+        sc[1] = v;
+        sc[13] = v > 0.0 ? log(v) : 0.0;
     }
     __syncthreads();
     if (t == 0) {
@@ -484,7 +523,7 @@ cudaError_t launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, b
     const int nbg = (c.n_z + HYP_THREADS - 1) / HYP_THREADS;
     k_nodes_grid<<<dim3(nbn + nbg, H), HYP_THREADS, 0, st>>>(c, p, dj, fmax_bits, nbn, fp64);
     const dim3 gi((NU + INV_THREADS - 1) / INV_THREADS, H);
-    const dim3 gf(fp64 ? 1 : nbg, H);
+    const dim3 gf(fp64 ? 1 : (c.n_z + HF_THREADS - 1) / HF_THREADS, H);
     if (side) {
         // k_hyper_final needs only the grid factor's maximum and the
         // forward tables, not the inverse nodes: its per-point FP64 chains
@@ -492,13 +531,13 @@ cudaError_t launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, b
         // side stream beside k_inv_nodes
         if ((e = cudaEventRecord(ev_fork, st)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(side, ev_fork, 0)) != cudaSuccess) return e;
-        k_hyper_final<<<gf, HYP_THREADS, 0, side>>>(c, p, fmax_bits, fp64);
+        k_hyper_final<<<gf, HF_THREADS, 0, side>>>(c, p, fmax_bits, fp64);
         if ((e = cudaEventRecord(ev_join, side)) != cudaSuccess) return e;
         k_inv_nodes<<<gi, INV_THREADS, 0, st>>>(c, p, dj);
         return cudaStreamWaitEvent(st, ev_join, 0);
     }
     k_inv_nodes<<<gi, INV_THREADS, 0, st>>>(c, p, dj);
-    k_hyper_final<<<gf, HYP_THREADS, 0, st>>>(c, p, fmax_bits, fp64);
+    k_hyper_final<<<gf, HF_THREADS, 0, st>>>(c, p, fmax_bits, fp64);
     return cudaSuccess;
 }
 

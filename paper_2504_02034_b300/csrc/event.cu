@@ -540,7 +540,19 @@ __global__ void __launch_bounds__(RW_THREADS, RW_MINB) k_reweight(DevCatalog c, 
     __syncthreads();
     const int nspec = s_nspec;
     if (nspec <= RW_SPEC_CAP) {
-        for (int i = tid; i < nspec; i += RW_THREADS) special(s_spec[i]);
+        // the list fills in the order of the atomic increments, which varies
+        // from run to run: sort it by sample index (each entry's rank among
+        // the others), so that every deferred sample goes to the same thread
+        // and into the same partial moment sums on every run
+        __shared__ int s_sorted[RW_SPEC_CAP];
+        for (int i = tid; i < nspec; i += RW_THREADS) {
+            const int v = s_spec[i];
+            int r = 0;
+            for (int k = 0; k < nspec; k++) r += s_spec[k] < v ? 1 : 0;
+            s_sorted[r] = v;
+        }
+        __syncthreads();
+        for (int i = tid; i < nspec; i += RW_THREADS) special(s_sorted[i]);
     } else {
         // more deferred samples than the list holds: find them all again
         for (int jj = tid; jj < ns; jj += RW_THREADS) {

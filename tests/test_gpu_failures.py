@@ -80,3 +80,28 @@ def test_serve_poll_times_out_while_pending_then_completes(chim):
             chim.chimera_serve_poll(ctx.h, ticket, th.shape[0], timeout_us=0, grad=True)
         assert e.value.code == chim.CHIMERA_ERR_NOT_FOUND
         ctx.unload(cid)
+
+
+def test_results_reproducible_between_interleaved_calls(chim):
+    """ln L and the mixed gradient of a batch are the same bit for bit when
+    calls on another catalog run in between (the reweighting kernel sorts
+    its deferred FP64 samples, whose list fills in atomic order, before
+    adding their moments, so the bandwidths do not depend on timing)."""
+    a = sc.config_catalog(2, n_events=40, n_pe=3000, n_inj=100000, gal_median=300)
+    b = sc.config_catalog(2, variant=2, n_events=60, n_pe=2500, n_inj=80000, gal_median=300)
+    th = sc.make_hyperpoints(16, seed=5, Xi0=1.0)
+    thb = sc.make_hyperpoints(16, seed=6, Xi0=1.8)
+    with chim.Context(0) as ctx:
+        ia, ib = ctx.load(a), ctx.load(b)
+        lnL0, g0, st0 = ctx.grad(ia, th, chim.MIXED)
+        terms0 = ctx.terms(ia, th, chim.MIXED)
+        for _ in range(3):
+            ctx.grad(ib, thb, chim.MIXED)
+            ctx.loglike(ib, thb[:7], chim.MIXED)
+            lnL, g, st = ctx.grad(ia, th, chim.MIXED)
+            terms = ctx.terms(ia, th, chim.MIXED)
+            np.testing.assert_array_equal(lnL, lnL0)
+            np.testing.assert_array_equal(g, g0)
+            np.testing.assert_array_equal(st, st0)
+            np.testing.assert_array_equal(terms["bw"], terms0["bw"])
+            np.testing.assert_array_equal(terms["lnI"], terms0["lnI"])

@@ -330,67 +330,71 @@ __global__ void __launch_bounds__(INV_THREADS) k_inv_nodes(DevCatalog c, CallPtr
     }
 }
 
-// K1b.3: per-hyperpoint constants (block x = 0: the independent FP64
-// transcendentals one per warp, then the quantities built from them) and, for
-// mixed calls, F normalised by its maximum.  Every FP64 operation waits on
-// B300's narrow FP64 pipe, so the block's time is its longest dependent FP64
-// chain: one transcendental per warp (16 warps), two short follow-ups, then
-// the assembly of the point's constants.
-constexpr int HF_THREADS = 512;
-__global__ void __launch_bounds__(HF_THREADS) k_hyper_final(DevCatalog c, CallPtrs p,
-                                                           const unsigned long long *fmax_bits, bool f64) {
+// K1b.3: per-hyperpoint constants (block x = 0, the independent FP64 scalars
+// one per lane) and, for mixed calls, F normalised by its maximum.
+__global__ void __launch_bounds__(HYP_THREADS) k_hyper_final(DevCatalog c, CallPtrs p,
+                                                            const unsigned long long *fmax_bits, bool f64) {
     const int h = blockIdx.y, t = threadIdx.x;
-    // F_scale: the power of two just above the maximum (2^e with Fm = m 2^e,
-    // m in [0.5, 1), from the exponent field of its bit pattern), so that
-    // F / F_scale in FP32 is exact (no rounded scale shared by every grid point)
-    const unsigned long long fb = fmax_bits[h];
-    const int fe = fb == 0 ? 0 : (f64 ? (int)((fb >> 52) & 0x7ff) - 1022 : (int)((fb >> 23) & 0xff) - 126);
+    const double Fm = f64 ? __longlong_as_double((long long)fmax_bits[h])
+                          : (double)__uint_as_float((unsigned)fmax_bits[h]);
+    // F_scale: the power of two just above the maximum, so that F / F_scale
+    // in FP32 is exact (no rounded scale shared by every grid point)
+    int fe = 0;
+    if (Fm > 0.0) frexp(Fm, &fe);
+    const double Fs = Fm > 0.0 ? ldexp(1.0, fe) : 1.0;
     if (!f64) {
-        const float iFs = __int_as_float((127 - fe) << 23);  // 2^-fe, exact
-        const int a = blockIdx.x * HF_THREADS + t;
+        const float iFs = (float)(1.0 / Fs);
+        const int a = blockIdx.x * HYP_THREADS + t;
         if (a < c.n_z) p.F32[(size_t)h * c.n_z + a] *= iFs;
     }
     if (blockIdx.x != 0) return;
-    const double Fs = __longlong_as_double((long long)(1023 + fe) << 52);  // 2^fe, exact
-    __shared__ double sc[20], sx[4];
+    // the FP64 scalars, one warp each (lane 0), so that their transcendental
+    // chains run side by side instead of serialised by divergence
+    __shared__ double sc[20];
     const double *th = p.theta + 12 * h;
     const double alpha = th[4], mu = th[5], sg = th[6], mmin = th[7], mmax = th[8];
     const double lam = c.lambda_g, beta = c.beta;
     const double cH = C_KMS / th[0];
     const int w = t >> 5;
-    const bool alpha1 = fabs(1.0 - alpha) < 1e-12;
     if ((t & 31) == 0) {
+        double v = 0.0;
         switch (w) {
-            case 0: sx[0] = alpha1 ? log(mmax / mmin) : pow(mmax, 1.0 - alpha); break;
-            case 1: sx[1] = alpha1 ? 0.0 : pow(mmin, 1.0 - alpha); break;
-            case 2: sx[2] = std_normal_cdf((mmax - mu) / sg); break;
-            case 3: sx[3] = std_normal_cdf((mmin - mu) / sg); break;
-            case 4: sc[2] = pow(mmin, 1.0 + beta); break;
-            case 5: sc[14] = log(fabs(1.0 + beta) < 1e-12 ? 1.4426950408889634074 : fabs(1.0 + beta)); break;
-            case 6: {
-                const double v = chimd::dc_hermite(p.fwd[h], c.z_max, th[1]);
-                sc[3] = v;
+            case 0:
+                v = fabs(1.0 - alpha) < 1e-12 ? log(mmax / mmin)
+                                              : (pow(mmax, 1.0 - alpha) - pow(mmin, 1.0 - alpha)) / (1.0 - alpha);
+                sc[12] = log(v);  // ln of the power law's normalisation integral
+                break;
+            case 1:
+                v = std_normal_cdf((mmax - mu) / sg) - std_normal_cdf((mmin - mu) / sg);
+                sc[13] = v > 0.0 ? log(v) : 0.0;
+                break;
+            case 2:
+                v = pow(mmin, 1.0 + beta);
+                sc[14] = log(fabs(1.0 + beta) < 1e-12 ? 1.4426950408889634074 : fabs(1.0 + beta));
+                break;
+            case 3:
+                v = chimd::dc_hermite(p.fwd[h], c.z_max, th[1]);
                 sc[15] = log(3.0 / (v * v * v));
                 break;
-            }
-            case 7: {  // d_L^gw at the end of the redshift range, z = 10, in FP64
-                double v, J;
+            case 4: {  // d_L^gw at the end of the redshift range, z = 10, in FP64
+                double J;
                 chimd::dgw_J(K_Z10 * HT, cH * p.fwd[h][K_Z10], th, cH, &v, &J);
-                sc[4] = v;
                 sc[8] = sqrt(v / c.d_top) * NU;  // its inverse-table coordinate
                 break;
             }
-            case 8: sc[5] = log(mmin); break;
-            case 9: sc[9] = log1p(th[11]); break;
-            case 10: sc[16] = log(th[0] / C_KMS); break;
-            case 11:
-                sc[6] = log2(mmin);
-                sc[10] = 1.0 / sg;
+            case 5:
+                v = log(mmin);
+                sc[9] = log1p(th[11]);
+                sc[16] = log(th[0] / C_KMS);
                 break;
-            case 12: sc[17] = pow(mmin, alpha); break;
-            case 13: sc[18] = log(sg); break;
-            case 14: sc[7] = log2(mmax); break;
+            case 6:
+                v = log2(mmin);
+                sc[10] = 1.0 / sg;
+                sc[17] = pow(mmin, alpha);
+                sc[18] = log(sg);
+                break;
             default:
+                v = log2(mmax);
                 // ln of the constant factor of the mixed path's raw event
                 // integral: dz F_scale / (N_gal,tot sqrt(2 pi)), times 1/b per event
                 // (the mixed F32 holds F c / H0 unless the Jacobian sits on the samples)
@@ -398,16 +402,7 @@ __global__ void __launch_bounds__(HF_THREADS) k_hyper_final(DevCatalog c, CallPt
                          (p.jac_ps ? 0.0 : log(th[0] / C_KMS));
                 break;
         }
-    }
-    __syncthreads();
-    if (t == 0) {  // the power law's normalisation integral and its log
-        const double v = alpha1 ? sx[0] : (sx[0] - sx[1]) / (1.0 - alpha);
-        sc[0] = v;
-        sc[12] = log(v);
-    } else if (t == 32) {  // the truncated Gaussian's mass and its log
-        const double v = sx[2] - sx[3];
-        sc[1] = v;
-        sc[13] = v > 0.0 ? log(v) : 0.0;
+        sc[w] = v;
     }
     __syncthreads();
     if (t == 0) {
@@ -523,7 +518,7 @@ cudaError_t launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, b
     const int nbg = (c.n_z + HYP_THREADS - 1) / HYP_THREADS;
     k_nodes_grid<<<dim3(nbn + nbg, H), HYP_THREADS, 0, st>>>(c, p, dj, fmax_bits, nbn, fp64);
     const dim3 gi((NU + INV_THREADS - 1) / INV_THREADS, H);
-    const dim3 gf(fp64 ? 1 : (c.n_z + HF_THREADS - 1) / HF_THREADS, H);
+    const dim3 gf(fp64 ? 1 : nbg, H);
     if (side) {
         // k_hyper_final needs only the grid factor's maximum and the
         // forward tables, not the inverse nodes: its per-point FP64 chains
@@ -531,13 +526,13 @@ cudaError_t launch_hyper_tables(const DevCatalog &c, const CallPtrs &p, int H, b
         // side stream beside k_inv_nodes
         if ((e = cudaEventRecord(ev_fork, st)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(side, ev_fork, 0)) != cudaSuccess) return e;
-        k_hyper_final<<<gf, HF_THREADS, 0, side>>>(c, p, fmax_bits, fp64);
+        k_hyper_final<<<gf, HYP_THREADS, 0, side>>>(c, p, fmax_bits, fp64);
         if ((e = cudaEventRecord(ev_join, side)) != cudaSuccess) return e;
         k_inv_nodes<<<gi, INV_THREADS, 0, st>>>(c, p, dj);
         return cudaStreamWaitEvent(st, ev_join, 0);
     }
     k_inv_nodes<<<gi, INV_THREADS, 0, st>>>(c, p, dj);
-    k_hyper_final<<<gf, HF_THREADS, 0, st>>>(c, p, fmax_bits, fp64);
+    k_hyper_final<<<gf, HYP_THREADS, 0, st>>>(c, p, fmax_bits, fp64);
     return cudaSuccess;
 }
 

@@ -378,6 +378,8 @@ constexpr int RW_THREADS = 128;
 #endif
 constexpr int RW_INFLIGHT = CHIM_RW_INFLIGHT;  // samples per thread in flight
 constexpr int RW_SPEC_CAP = 256;               // deferred (FP64-weight) samples listed per block
+constexpr int RW_CHUNKS = CHIMERA_MAX_SAMPLES_PER_EVENT / 32;  // 32-sample chunks of the largest event
+static_assert(RW_CHUNKS % RW_THREADS == 0, "chunks spread evenly over the threads");
 constexpr int RW_MINB = CHIM_RW_MINB;          // resident blocks per SM asked of the compiler
 // 1 / [(1+z)^3 |d d_L^gw/dz|] at a sample (Eq. jacobian), FP32, from its
 // d_L (D_c = d_L / ((1+z) Xi)) and lz = log2(1+z).
@@ -456,9 +458,13 @@ __global__ void __launch_bounds__(RW_THREADS, RW_MINB) k_reweight(DevCatalog c, 
     // corner band above m_min; a few in a thousand at most) are deferred to
     // a list and taken after the loop, so that the loop itself carries no
     // FP64 call (whose register saves would cost every sample).
-    __shared__ int s_nspec;
+    // Each deferred sample sets its bit in the mask of its 32-sample chunk
+    // (an atomic OR: the result does not depend on the order); after the
+    // loop the masks give the list of deferred samples in index order.
+    __shared__ unsigned s_smask[RW_CHUNKS];
     __shared__ int s_spec[RW_SPEC_CAP];
-    if (tid == 0) s_nspec = 0;
+    __shared__ int s_wtot[RW_THREADS / 32];
+    for (int cc = tid; cc < RW_CHUNKS; cc += RW_THREADS) s_smask[cc] = 0u;
     __syncthreads();
     auto jac = [&](float w, float z, float lz, const float4 &sv) {
         if (JAC) {  // the Jacobian on the sample (the moments keep w)
@@ -475,8 +481,7 @@ __global__ void __launch_bounds__(RW_THREADS, RW_MINB) k_reweight(DevCatalog c, 
         const bool inr = w_in_range(lm);
         float w = 0.f;
         if (ok && (w_needs64(lm) || (inr && lm.d1 < W_FP64))) {
-            const int slot = atomicAdd(&s_nspec, 1);
-            if (slot < RW_SPEC_CAP) s_spec[slot] = j;  // beyond the cap: the rescan below
+            atomicOr(&s_smask[j >> 5], 1u << (j & 31));
         } else if (ok && inr) {
             // rcp.approx: mean relative error +4e-9 on B300 (measured), no shared bias to speak of
             const WQuot wq = mass_weight_rel(q, lm);
@@ -538,21 +543,36 @@ __global__ void __launch_bounds__(RW_THREADS, RW_MINB) k_reweight(DevCatalog c, 
         sample(sv, nd, nl, lo2, j);
     }
     __syncthreads();
-    const int nspec = s_nspec;
+    // the deferred samples in index order: thread t counts the chunks
+    // 3t .. 3t+2, an exclusive scan over the threads gives its offset, and it
+    // writes its chunks' samples there; the list is then shared out over the
+    // threads, so the same thread adds the same sample's moments on every run
+    // (the order of the atomic updates varies from run to run)
+    const int lane = tid & 31, wid = tid >> 5;
+    constexpr int CPT = RW_CHUNKS / RW_THREADS;
+    int cnt = 0;
+#pragma unroll
+    for (int u = 0; u < CPT; u++) cnt += __popc(s_smask[CPT * tid + u]);
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_wtot[wid] = incl;
+    __syncthreads();
+    int pos = incl - cnt, nspec = 0;
+    for (int w = 0; w < RW_THREADS / 32; w++) {
+        if (w < wid) pos += s_wtot[w];
+        nspec += s_wtot[w];
+    }
     if (nspec <= RW_SPEC_CAP) {
-        // the list fills in the order of the atomic increments, which varies
-        // from run to run: sort it by sample index (each entry's rank among
-        // the others), so that every deferred sample goes to the same thread
-        // and into the same partial moment sums on every run
-        __shared__ int s_sorted[RW_SPEC_CAP];
-        for (int i = tid; i < nspec; i += RW_THREADS) {
-            const int v = s_spec[i];
-            int r = 0;
-            for (int k = 0; k < nspec; k++) r += s_spec[k] < v ? 1 : 0;
-            s_sorted[r] = v;
+#pragma unroll
+        for (int u = 0; u < CPT; u++) {
+            const int cc = CPT * tid + u;
+            for (unsigned m = s_smask[cc]; m; m &= m - 1) s_spec[pos++] = 32 * cc + __ffs(m) - 1;
         }
         __syncthreads();
-        for (int i = tid; i < nspec; i += RW_THREADS) special(s_sorted[i]);
+        for (int i = tid; i < nspec; i += RW_THREADS) special(s_spec[i]);
     } else {
         // more deferred samples than the list holds: find them all again
         for (int jj = tid; jj < ns; jj += RW_THREADS) {

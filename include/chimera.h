@@ -208,10 +208,12 @@ typedef struct {
      * CHIMERA_PROFILE_FP32=1 in the environment before a load keeps that
      * catalog on the FP32 kernels. */
     int32_t profile_path;
-    /* warps per block of the mixed event kernel for this catalog: 10 (three
-     * blocks per SM) when the largest event's samples leave room for three
-     * blocks in shared memory, else 16 (two per SM).  Both give the same
-     * results bit for bit; this is for performance reports only. */
+    /* warps per block of the mixed event kernel for this catalog: at load,
+     * 10 (three blocks per SM) when the largest event's samples leave room
+     * for three blocks in shared memory, else 16 (two per SM); the catalog's
+     * first mixed call times both on its first tile and keeps the faster.
+     * Both give the same results bit for bit; this is for performance
+     * reports only. */
     int32_t event_kernel_warps;
 } chimera_catalog_info_t;
 

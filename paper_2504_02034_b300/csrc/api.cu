@@ -599,6 +599,46 @@ static int profile(Ctx &ctx, Catalog &cat, Workspace &ws, double Om, int kind, c
     return CHIMERA_OK;
 }
 
+// The mixed event kernel's block geometry, timed once per catalog: on the
+// catalog's first mixed call, both instantiations (10 warps, three blocks
+// per SM; 16 warps, two) run on the call's first tile, twice each in
+// alternation, and the faster is kept for the catalog.  They write the same
+// values (the event kernel reads the reweighting kernel's bandwidth and
+// writes ln I and the same bandwidth back), so the call's results do not
+// depend on the choice.  The load-time choice by occupancy stands when the
+// 16-warp form does not fit, and while windowed pairs are being counted.
+static int tune_event_geometry(Catalog &cat, const CallPtrs &p, int h0, int nh, Workspace &ws) {
+    cat.ev_tuned = true;
+    int dev = 0, maxsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if ((int)event_mixed_smem(cat.d, 0) > maxsm) return CHIMERA_OK;
+    cudaEvent_t e[5] = {};
+    for (auto &x : e)
+        if (cudaEventCreate(&x) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto &y : e)
+                if (y) cudaEventDestroy(y);
+            return CHIMERA_OK;  // timing unavailable: keep the load-time choice
+        }
+    DevCatalog cg = cat.d;
+    cudaError_t err = cudaEventRecord(e[0], ws.st);
+    for (int k = 0; k < 4 && err == cudaSuccess; k++) {
+        cg.ev_geom = k & 1;
+        launch_event_mixed(cg, p, h0, nh, ws.st);
+        err = cudaEventRecord(e[k + 1], ws.st);
+    }
+    if (err == cudaSuccess) err = cudaEventSynchronize(e[4]);
+    float t[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < 4 && err == cudaSuccess; k++) err = cudaEventElapsedTime(&t[k], e[k], e[k + 1]);
+    for (auto &x : e) cudaEventDestroy(x);
+    if (err != cudaSuccess) return cuda_check(err, "event kernel geometry timing");
+    const float t16 = std::min(t[0], t[2]), t10 = std::min(t[1], t[3]);
+    cat.d.ev_geom = t10 <= t16 ? 1 : 0;
+    cat.info.event_kernel_warps = cat.d.ev_geom == 1 ? EV_WARPS_3 : EV_WARPS_2;
+    return CHIMERA_OK;
+}
+
 // ----------------------------------------------------------- forward ----
 int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, int precision,
             double *out_lnL, double *out_neff, int32_t *out_status) {
@@ -711,9 +751,12 @@ int forward(Ctx &ctx, Catalog &cat, Workspace &ws, int H, const double *theta, i
             const int h0 = t * tile, nh = std::min(tile, H - h0);
             launch_reweight(c, p, h0, nh, ws.st);
             if (ws.trace) CK(cudaEventRecord(ws.tile_ev[2 * t], ws.st));
-            if (precision == CHIMERA_MIXED_BINNED || epan)
+            if (precision == CHIMERA_MIXED_BINNED || epan) {
                 launch_event_binned(c, p, h0, nh, precision == CHIMERA_MIXED_BINNED, ws.st);
-            else launch_event_mixed(c, p, h0, nh, ws.st);
+            } else {
+                if (!cat.ev_tuned && !p.pairs) RC(tune_event_geometry(cat, p, h0, nh, ws));
+                launch_event_mixed(c, p, h0, nh, ws.st);
+            }
             if (ws.trace) CK(cudaEventRecord(ws.tile_ev[2 * t + 1], ws.st));
         }
     }

@@ -62,6 +62,7 @@ struct Catalog {
     std::map<std::pair<uint64_t, int>, ProfEntry> prof;
     std::atomic<int> in_use{0};
     TcHost tc;  // tensor-core profile plan (used when d.tc_ok)
+    bool ev_tuned = false;  // the mixed event kernel's geometry timed on a first call
 };
 
 // Device and pinned buffers for one stream of likelihood calls.

@@ -1,7 +1,8 @@
 """The mixed event kernel's two block geometries (10 warps with three blocks
-per SM, 16 warps with two, chosen per catalog by the shared memory its
-largest event needs): the same events give the same ln I bit for bit under
-either, and an event too large for three blocks per SM matches the oracle."""
+per SM, 16 warps with two; chosen per catalog at load by the shared memory
+its largest event needs, then by timing both on the first mixed call): the
+same events give the same ln I bit for bit under either, and an event too
+large for three blocks per SM matches the oracle."""
 import numpy as np
 import pytest
 
@@ -51,6 +52,12 @@ def test_geometries_agree_and_large_event_matches_oracle(chim, ctx, orc):
         assert ctx.info(ids[1])["event_kernel_warps"] == 16
         ta = ctx.terms(ids[0], th, chim.MIXED)
         tb = ctx.terms(ids[1], th, chim.MIXED)
+        # the first mixed call timed both geometries and kept one of them;
+        # later calls give the same values
+        for cid, t in zip(ids, (ta, tb)):
+            assert ctx.info(cid)["event_kernel_warps"] in (10, 16)
+            again = ctx.terms(cid, th, chim.MIXED)
+            assert np.array_equal(again["lnI"], t["lnI"]) and np.array_equal(again["bw"], t["bw"])
         ne = small["n_events"]
         assert np.array_equal(ta["lnI"], tb["lnI"][:, :ne])
         assert np.array_equal(ta["bw"], tb["bw"][:, :ne])

@@ -94,40 +94,6 @@ constexpr int HYP_THREADS = 256;
 
 __device__ double std_normal_cdf(double x) { return 0.5 * erfc(-x * 0.70710678118654752440); }
 
-// 1 / sqrt(x) in FP64 for x of order one to a few hundred: the SFU's FP32
-// estimate (rsqrtf, relative error ~2^-22) refined by two Newton-Raphson
-// steps on f(y) = y^-2 - x, y <- y (3 - x y^2) / 2, each of which squares
-// the relative error (2^-43, then below FP64 rounding): a handful of FP64
-// operations in place of a square root and a division, which matter on
-// B300's narrow FP64 pipe.
-__device__ __forceinline__ double rsqrt64(double x) {
-    double y = (double)rsqrtf((float)x);
-    y = y * (1.5 - 0.5 * x * y * y);
-    return y * (1.5 - 0.5 * x * y * y);
-}
-// The FP64 forward relation of the inverse-node kernel with 1/E from rsqrt64:
-// D_c by cubic Hermite on the forward table (slopes HT / E at the nodes),
-// d_L^gw and J = d d_L^gw / dz (Eqs. dL-em, dL-mg).
-__device__ __forceinline__ double dc_hermite_r(const double *fwd, double z, double Om) {
-    const double t = z / HT;
-    int k = (int)floor(t);
-    if (k < 0) k = 0;
-    if (k > NT_FWD - 2) k = NT_FWD - 2;
-    const double f = t - k, a0 = 1.0 + k * HT, a1 = 1.0 + (k + 1) * HT;
-    const double m0 = HT * rsqrt64(Om * a0 * a0 * a0 + 1.0 - Om), m1 = HT * rsqrt64(Om * a1 * a1 * a1 + 1.0 - Om);
-    const double f2 = f * f, f3 = f2 * f;
-    return (2 * f3 - 3 * f2 + 1) * fwd[k] + (f3 - 2 * f2 + f) * m0 + (-2 * f3 + 3 * f2) * fwd[k + 1] + (f3 - f2) * m1;
-}
-__device__ __forceinline__ void dgw_J_r(double z, double Dc, const double *th, double cH, double *d, double *J) {
-    const double a = 1.0 + z;
-    const double p = exp(-th[3] * log(a));  // (1+z)^-n
-    const double xi = th[2] + (1.0 - th[2]) * p;
-    const double dxi = -th[3] * (1.0 - th[2]) * p / a;
-    const double rE = rsqrt64(th[1] * a * a * a + 1.0 - th[1]);
-    *d = a * Dc * xi;
-    *J = (Dc + a * cH * rE) * xi + a * Dc * dxi;
-}
-
 // FP32 forward relation at z from D = D_c [Mpc]: d_L^gw and its z-derivative J.
 __device__ __forceinline__ void dgw_J32(float z, float D, float cH, float om, float xi0, float n, float &d,
                                        float &J) {
@@ -306,7 +272,7 @@ __global__ void __launch_bounds__(INV_THREADS) k_inv_nodes(DevCatalog c, CallPtr
                 z = (double)((2.f * t3 - 3.f * t2 + 1.f) * ((float)lo * HTf) + (t3 - 2.f * t2 + tt) * den / dj[lo].y +
                              (-2.f * t3 + 3.f * t2) * ((float)hi * HTf) + (t3 - t2) * den / dj[hi].y);
                 double dd, J;
-                dgw_J_r(z, cH * dc_hermite_r(fwd, z, Om), th, cH, &dd, &J);
+                chimd::dgw_J_r(z, cH * chimd::dc_hermite_r(fwd, z, Om), th, cH, &dd, &J);
                 const double rJ = 1.0 / J;
                 const double step = (dd - d) * rJ;
                 if (isfinite(step)) z -= step;

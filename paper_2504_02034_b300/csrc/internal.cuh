@@ -436,6 +436,41 @@ __device__ __forceinline__ double xi_of(double z, double xi0, double n) {
 
 // d_L^gw and its z-derivative J from D_c (Mpc) at z, Eq. dL-mg and its
 // product-rule derivative.
+// 1 / sqrt(x) in FP64 for x of order one to a few hundred: the SFU's FP32
+// estimate (rsqrtf, relative error ~2^-22) refined by two Newton-Raphson
+// steps on f(y) = y^-2 - x, y <- y (3 - x y^2) / 2, each of which squares
+// the relative error (2^-43, then below FP64 rounding): a handful of FP64
+// operations in place of a square root and a division, which matter on
+// B300's narrow FP64 pipe.
+__device__ __forceinline__ double rsqrt64(double x) {
+    double y = (double)rsqrtf((float)x);
+    y = y * (1.5 - 0.5 * x * y * y);
+    return y * (1.5 - 0.5 * x * y * y);
+}
+// The FP64 forward relation (as dc_hermite and dgw_J) with 1/E from
+// rsqrt64, for the inverse nodes and the Newton steps of the FP64 redshifts:
+// D_c by cubic Hermite on the forward table (slopes HT / E at the nodes),
+// d_L^gw and J = d d_L^gw / dz (Eqs. dL-em, dL-mg).
+__device__ __forceinline__ double dc_hermite_r(const double *fwd, double z, double Om) {
+    const double t = z * (4096.0 / 10.0);  // z / HT (a product: no FP64 division)
+    int k = (int)floor(t);
+    if (k < 0) k = 0;
+    if (k > chim::NT_FWD - 2) k = chim::NT_FWD - 2;
+    const double f = t - k, a0 = 1.0 + k * chim::HT, a1 = 1.0 + (k + 1) * chim::HT;
+    const double m0 = chim::HT * rsqrt64(Om * a0 * a0 * a0 + 1.0 - Om), m1 = chim::HT * rsqrt64(Om * a1 * a1 * a1 + 1.0 - Om);
+    const double f2 = f * f, f3 = f2 * f;
+    return (2 * f3 - 3 * f2 + 1) * fwd[k] + (f3 - 2 * f2 + f) * m0 + (-2 * f3 + 3 * f2) * fwd[k + 1] + (f3 - f2) * m1;
+}
+__device__ __forceinline__ void dgw_J_r(double z, double Dc, const double *th, double cH, double *d, double *J) {
+    const double a = 1.0 + z;
+    const double p = exp(-th[3] * log(a));  // (1+z)^-n
+    const double xi = th[2] + (1.0 - th[2]) * p;
+    const double dxi = -th[3] * (1.0 - th[2]) * p / a;
+    const double rE = rsqrt64(th[1] * a * a * a + 1.0 - th[1]);
+    *d = a * Dc * xi;
+    *J = (Dc + a * cH * rE) * xi + a * Dc * dxi;
+}
+
 __device__ __forceinline__ void dgw_J(double z, double Dc, const double *th, double cH, double *d,
                                       double *J) {
     double a = 1.0 + z;

@@ -295,7 +295,7 @@ inline __device__ bool invert64(const DevCatalog &c, const CallPtrs &p, int h, c
 static __device__ bool refine64(const CallPtrs &p, int h, const HP &hp, float z32, double d, double *zout) {
     if (!(d > 0.0) || !(d <= hp.d_valid) || !(z32 < CUDART_INF_F)) return false;
     double z = z32, dd, J;
-    chimd::dgw_J(z, hp.cH * chimd::dc_hermite(p.fwd[h], z, hp.th[1]), hp.th, hp.cH, &dd, &J);
+    chimd::dgw_J_r(z, hp.cH * chimd::dc_hermite_r(p.fwd[h], z, hp.th[1]), hp.th, hp.cH, &dd, &J);
     const double step = (dd - d) / J;
     if (isfinite(step)) z -= step;
     *zout = z;

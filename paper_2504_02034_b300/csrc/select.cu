@@ -74,11 +74,15 @@ __device__ bool invert64_sel(const DevCatalog &c, const CallPtrs &p, int h, cons
 // the inverse tables: up to SEL_STAGE intervals of it (z and log2(1+z) node
 // pairs of each hyperpoint) are staged in shared memory.
 constexpr int SEL_STAGE = 128;
+constexpr int SEL_DEF_CAP = 512;  // deferred FP64 pairs listed per block (more: taken by their words' threads)
 
 __global__ void __launch_bounds__(SEL_THREADS) k_select_mixed(DevCatalog c, CallPtrs p, int H) {
     __shared__ double red[2 * SEL_HB * (SEL_THREADS / 32)];
     __shared__ SelConst scs[SEL_HB];
     __shared__ float4 snode[SEL_HB][2][SEL_STAGE];
+    __shared__ unsigned s_dm[SEL_HB][SEL_CHUNK / 32];  // deferred (point, injection) pairs of the chunk
+    __shared__ int s_dl[SEL_DEF_CAP];                  // their list, in (point, injection) order
+    __shared__ int s_dwt[SEL_THREADS / 32];
     const int chunk = blockIdx.x, h0 = blockIdx.y * SEL_HB;
     const int nh = min(SEL_HB, H - h0);
     const int64_t base = (int64_t)chunk * SEL_CHUNK;
@@ -106,6 +110,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_mixed(DevCatalog c, Call
             nk = k1 - k0 + 1;
         }
     }
+    for (int i = threadIdx.x; i < SEL_HB * (SEL_CHUNK / 32); i += SEL_THREADS) (&s_dm[0][0])[i] = 0u;
     for (int i = threadIdx.x; i < nh * nk; i += SEL_THREADS) {
         const int hb = i / nk, r = i - hb * nk;
         snode[hb][0][r] = __ldg(p.inv32 + (size_t)(h0 + hb) * NU + klo + r);
@@ -121,56 +126,113 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_mixed(DevCatalog c, Call
     float s1[SEL_HB], s2[SEL_HB];
 #pragma unroll
     for (int hb = 0; hb < SEL_HB; hb++) s1[hb] = s2[hb] = 0.f;
-    for (int qq = 0; qq < SEL_PER_THREAD; qq++) {
-        const int64_t j = base + qq * SEL_THREADS + threadIdx.x;
-        if (j >= c.n_det) break;
+    // The few (injection, point) pairs that need FP64 (guard bands at the
+    // mass edges and z_max, the corner band above m_min) are deferred: a bit
+    // per pair in the chunk's masks (atomic OR, order-free), then after the
+    // loop the list in (point, injection) order shared out over the threads,
+    // so that their FP64 chains, long on B300's narrow FP64 pipe, run side by
+    // side instead of stalling a warp each inside the loop, and every pair
+    // goes to the same thread on every run.
+    auto sel_term = [&](int hb, int64_t j, bool deferred) -> float {
         const float4 a = __ldg(c.i32a + j);
         const float dL = __ldg(&c.i32b[j].x);
         const float ipi = __ldg(c.iipi32 + j);
         const float2 lo = __ldg(c.i32lo + j);
         const int k = __float_as_int(a.x);
+        const SelConst &K = scs[hb];
+        if (!((k < K.q.kv) || (k == K.q.kv && a.y <= K.q.fv))) return 0.f;
+        const float z = chimd::hermite4(K.inv[k], a.y);
+        if (!(z < CUDART_INF_F)) return 0.f;
+        const float ap = 1.f + z, lz = chimd::hermite4(K.linv[k], a.y);  // log2(1+z)
+        LogMass lm = log_mass(K.q, a.z, a.w, lo, lz);
+        float wn, wd;  // the weight as a quotient
+        const bool f64 = w_needs64(lm) || fabsf(z - zmax) < ZMAX_GUARD;
+        if (!f64 && !(w_in_range(lm) && z <= zmax)) return 0.f;
+        if (!deferred && (f64 || lm.d1 < W_FP64)) {
+            const int li = (int)(j - base);
+            atomicOr(&s_dm[hb][li >> 5], 1u << (li & 31));
+            return 0.f;
+        }
+        if (f64) {
+            // FP64: range and z_max tests as the oracle takes them, and
+            // the weight itself
+            const int h = h0 + hb;
+            const HP &hp = p.hp[h];
+            double z64;
+            if (!refine64(p, h, hp, z, c.id64[j], &z64) || !(z64 <= c.z_max)) return 0.f;
+            const double a64 = 1.0 + z64;
+            wn = (float)(mass_weight64(hp, c.beta, c.im1_64[j] / a64, c.im2_64[j] / a64) * hp.inv_wscale);
+            wd = 1.f;
+        } else {
+            if (lm.d1 < W_FP64) lm.d1 = corner_d1(p, h0 + hb, p.hp[h0 + hb], z, c.id64[j], c.im1_64[j], lm.d1);
+            const WQuot wq = mass_weight_rel(K.q, lm);
+            wn = wq.num;
+            wd = wq.den;
+        }
+        const float pw = ex2_mul_n(K.nn, lz);  // (1+z)^-n
+        const float xi = fmaf(K.omx.hi, pw, K.xi0.hi) + fmaf(K.omx.lo, pw, K.xi0.lo);
+        const float N = mul_f2(K.kH, dL);  // d_L H0 / c
+        const float axi = ap * xi;       // Dhat = D_c H0 / c = N / ((1+z) Xi)
+        const float a3 = ap * ap * ap;
+        const float E = sqrtf(fmaf(K.om.hi, a3, K.omc.hi) + fmaf(K.om.lo, a3, K.omc.lo));
+        // J H0 / c = (Dhat + (1+z)/E) Xi - n (1 - Xi0) (1+z)^-n Dhat; times E (1+z) Xi:
+        const float JE = fmaf(N, E, ap * axi) * xi - mul_f2(K.nomx, pw) * N * E;
+        const float r = ex2_mul_n(K.gkp, (lz - K.l2zp.hi) - K.l2zp.lo);  // ((1+z)/(1+z_p))^(gamma+kappa)
+        // s / cfac = w' psi Dhat^2 / (E (1+z)^3 |J H0/c|) 2^-K / pi_inj
+        //          = w' (1+z)^gamma N^2 2^-K / pi_inj / ((1+z) Xi (1 + r) (1+z)^3 |JE|)
+        const float sv = __fdividef(wn * ex2_mul_n(K.gam, lz) * N * N * ipi, wd * axi * (1.f + r) * a3 * fabsf(JE));
+        return sv > 0.f ? sv : 0.f;
+    };
+    for (int qq = 0; qq < SEL_PER_THREAD; qq++) {
+        const int64_t j = base + qq * SEL_THREADS + threadIdx.x;
+        if (j >= c.n_det) break;
 #pragma unroll
         for (int hb = 0; hb < SEL_HB; hb++) {
             if (hb >= nh) break;
-            const SelConst &K = scs[hb];
-            if (!((k < K.q.kv) || (k == K.q.kv && a.y <= K.q.fv))) continue;
-            const float z = chimd::hermite4(K.inv[k], a.y);
-            if (!(z < CUDART_INF_F)) continue;
-            const float ap = 1.f + z, lz = chimd::hermite4(K.linv[k], a.y);  // log2(1+z)
-            LogMass lm = log_mass(K.q, a.z, a.w, lo, lz);
-            float wn, wd;  // the weight as a quotient
-            if (w_needs64(lm) || fabsf(z - zmax) < ZMAX_GUARD) {
-                // FP64: range and z_max tests as the oracle takes them, and
-                // the weight itself
-                const int h = h0 + hb;
-                const HP &hp = p.hp[h];
-                double z64;
-                if (!refine64(p, h, hp, z, c.id64[j], &z64) || !(z64 <= c.z_max)) continue;
-                const double a64 = 1.0 + z64;
-                wn = (float)(mass_weight64(hp, c.beta, c.im1_64[j] / a64, c.im2_64[j] / a64) * hp.inv_wscale);
-                wd = 1.f;
-            } else {
-                if (!(w_in_range(lm) && z <= zmax)) continue;
-                if (lm.d1 < W_FP64) lm.d1 = corner_d1(p, h0 + hb, p.hp[h0 + hb], z, c.id64[j], c.im1_64[j], lm.d1);
-                const WQuot wq = mass_weight_rel(K.q, lm);
-                wn = wq.num;
-                wd = wq.den;
-            }
-            const float pw = ex2_mul_n(K.nn, lz);  // (1+z)^-n
-            const float xi = fmaf(K.omx.hi, pw, K.xi0.hi) + fmaf(K.omx.lo, pw, K.xi0.lo);
-            const float N = mul_f2(K.kH, dL);  // d_L H0 / c
-            const float axi = ap * xi;       // Dhat = D_c H0 / c = N / ((1+z) Xi)
-            const float a3 = ap * ap * ap;
-            const float E = sqrtf(fmaf(K.om.hi, a3, K.omc.hi) + fmaf(K.om.lo, a3, K.omc.lo));
-            // J H0 / c = (Dhat + (1+z)/E) Xi - n (1 - Xi0) (1+z)^-n Dhat; times E (1+z) Xi:
-            const float JE = fmaf(N, E, ap * axi) * xi - mul_f2(K.nomx, pw) * N * E;
-            const float r = ex2_mul_n(K.gkp, (lz - K.l2zp.hi) - K.l2zp.lo);  // ((1+z)/(1+z_p))^(gamma+kappa)
-            // s / cfac = w' psi Dhat^2 / (E (1+z)^3 |J H0/c|) 2^-K / pi_inj
-            //          = w' (1+z)^gamma N^2 2^-K / pi_inj / ((1+z) Xi (1 + r) (1+z)^3 |JE|)
-            const float sv = __fdividef(wn * ex2_mul_n(K.gam, lz) * N * N * ipi, wd * axi * (1.f + r) * a3 * fabsf(JE));
-            if (!(sv > 0.f)) continue;
+            const float sv = sel_term(hb, j, false);
             s1[hb] += sv;
             s2[hb] = fmaf(sv, sv, s2[hb]);
+        }
+    }
+    __syncthreads();
+    {
+        // the deferred pairs: word w of the masks (point w / (SEL_CHUNK/32))
+        // counted by thread w, an exclusive scan, the list written in order
+        constexpr int NWD = SEL_HB * (SEL_CHUNK / 32);
+        static_assert(NWD <= SEL_THREADS, "one mask word per thread");
+        const unsigned *dmf = &s_dm[0][0];
+        const int ln = threadIdx.x & 31, wi = threadIdx.x >> 5;
+        const unsigned mw = threadIdx.x < NWD ? dmf[threadIdx.x] : 0u;
+        const int cnt = __popc(mw);
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (ln >= o) incl += v;
+        }
+        if (ln == 31) s_dwt[wi] = incl;
+        __syncthreads();
+        int pos = incl - cnt, nd = 0;
+        for (int w = 0; w < SEL_THREADS / 32; w++) {
+            if (w < wi) pos += s_dwt[w];
+            nd += s_dwt[w];
+        }
+        auto take = [&](int e) {  // e = word * 32 + bit
+            const int hb = e / SEL_CHUNK, li = e - hb * SEL_CHUNK;
+            const float sv = sel_term(hb, base + li, true);
+#pragma unroll
+            for (int q = 0; q < SEL_HB; q++)
+                if (q == hb) {
+                    s1[q] += sv;
+                    s2[q] = fmaf(sv, sv, s2[q]);
+                }
+        };
+        if (nd <= SEL_DEF_CAP) {
+            for (unsigned m = mw; m; m &= m - 1) s_dl[pos++] = 32 * threadIdx.x + __ffs(m) - 1;
+            __syncthreads();
+            for (int i = threadIdx.x; i < nd; i += SEL_THREADS) take(s_dl[i]);
+        } else {
+            // more than the list holds: each thread takes the pairs of its own word
+            for (unsigned m = mw; m; m &= m - 1) take(32 * threadIdx.x + __ffs(m) - 1);
         }
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

@@ -891,6 +891,7 @@ static int load_catalog(Ctx &ctx, const chimera_catalog_desc *d, int32_t *out_id
     for (int64_t j = 0; j < ns; j++) dmax = std::max(dmax, d->dL_Mpc[j]);
     for (int64_t j = 0; j < d->n_det; j++) dmax = std::max(dmax, d->inj_dL[j]);
     c.d_top = dmax * (1.0 + 1e-9);
+    c.inv_d_top = 1.0 / c.d_top;
 
     // ---- samples: sort inside each event
     std::vector<int64_t> order(ns);

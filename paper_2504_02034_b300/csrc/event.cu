@@ -510,9 +510,9 @@ __global__ void __launch_bounds__(RW_THREADS, RW_MINB) k_reweight(DevCatalog c, 
         LogMass lm = log_mass(q, sv.z, sv.w, __ldg(c.s32lo + s0 + j), lz);
         float w = 0.f;
         if (w_needs64(lm)) {
-            w = mass_weight_rel64(p, h, hp, c.beta, z, c.sd64[s0 + j], c.sm1_64[s0 + j], c.sm2_64[s0 + j]);
+            w = mass_weight_rel64(p, h, hp, c.inv_d_top, c.beta, z, c.sd64[s0 + j], c.sm1_64[s0 + j], c.sm2_64[s0 + j]);
         } else {
-            lm.d1 = corner_d1(p, h, hp, z, c.sd64[s0 + j], c.sm1_64[s0 + j], lm.d1);
+            lm.d1 = corner_d1(p, h, hp, c.inv_d_top, z, c.sd64[s0 + j], c.sm1_64[s0 + j], lm.d1);
             const WQuot wq = mass_weight_rel(q, lm);
             w = __fdividef(wq.num, wq.den);
             w = w > 0.f ? w : 0.f;

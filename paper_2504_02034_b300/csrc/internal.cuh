@@ -109,6 +109,7 @@ struct DevCatalog {
     int32_t n_events, n_z, kde_mode, gal_storage;
     int64_t n_samples, n_pix, n_gal, n_det, n_inj_total;
     double z_max, dz, n_gal_total, lambda_g, beta, d_top;
+    double inv_d_top;  // 1 / d_top
     double ln_lambda, ln1m_lambda;  // ln lambda_g, ln(1 - lambda_g) (0 when the argument is 0)
     float z_max32, dz32;  // float copies for the mixed kernels
     float dz_lo32;        // dz - dz32: grid positions a dz in FP32 as fmaf(a, dz32, a dz_lo32)

@@ -159,12 +159,12 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_mixed(DevCatalog c, Call
             const int h = h0 + hb;
             const HP &hp = p.hp[h];
             double z64;
-            if (!refine64(p, h, hp, z, c.id64[j], &z64) || !(z64 <= c.z_max)) return 0.f;
+            if (!refine64(p, h, hp, c.inv_d_top, z, c.id64[j], &z64) || !(z64 <= c.z_max)) return 0.f;
             const double a64 = 1.0 + z64;
             wn = (float)(mass_weight64(hp, c.beta, c.im1_64[j] / a64, c.im2_64[j] / a64) * hp.inv_wscale);
             wd = 1.f;
         } else {
-            if (lm.d1 < W_FP64) lm.d1 = corner_d1(p, h0 + hb, p.hp[h0 + hb], z, c.id64[j], c.im1_64[j], lm.d1);
+            if (lm.d1 < W_FP64) lm.d1 = corner_d1(p, h0 + hb, p.hp[h0 + hb], c.inv_d_top, z, c.id64[j], c.im1_64[j], lm.d1);
             const WQuot wq = mass_weight_rel(K.q, lm);
             wn = wq.num;
             wd = wq.den;

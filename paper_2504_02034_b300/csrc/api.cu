@@ -600,9 +600,10 @@ static int profile(Ctx &ctx, Catalog &cat, Workspace &ws, double Om, int kind, c
 }
 
 // The mixed event kernel's block geometry, timed once per catalog: on the
-// catalog's first mixed call, both instantiations (10 warps, three blocks
-// per SM; 16 warps, two) run on the call's first tile, twice each in
-// alternation, and the faster is kept for the catalog.  They write the same
+// catalog's first mixed call, once the selection term on the side stream has
+// finished, both instantiations (10 warps, three blocks per SM; 16 warps,
+// two) run on the call's first tile, twice each in alternation, and the
+// faster is kept for the catalog.  They write the same
 // values (the event kernel reads the reweighting kernel's bandwidth and
 // writes ln I and the same bandwidth back), so the call's results do not
 // depend on the choice.  The load-time choice by occupancy stands when the
@@ -622,7 +623,10 @@ static int tune_event_geometry(Catalog &cat, const CallPtrs &p, int h0, int nh, 
             return CHIMERA_OK;  // timing unavailable: keep the load-time choice
         }
     DevCatalog cg = cat.d;
-    cudaError_t err = cudaEventRecord(e[0], ws.st);
+    // the selection term on the side stream would run beside the timed
+    // launches and load them unevenly: wait for it first
+    cudaError_t err = ws.ev_join ? cudaStreamWaitEvent(ws.st, ws.ev_join, 0) : cudaSuccess;
+    if (err == cudaSuccess) err = cudaEventRecord(e[0], ws.st);
     for (int k = 0; k < 4 && err == cudaSuccess; k++) {
         cg.ev_geom = k & 1;
         launch_event_mixed(cg, p, h0, nh, ws.st);

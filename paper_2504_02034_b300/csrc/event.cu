@@ -766,11 +766,16 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_event_mixed(DevCatalog c, Cal
     float *D = Dt + wid * DCAP;
     const float *prof = reinterpret_cast<const float *>(p.prof[h]);
     unsigned long long npairs = 0;  // algorithmic pair count (roofline only)
+    // a warp claims its next group as it starts the current one, so that the
+    // shared-memory atomic's round trip is hidden behind the group's work
+    int gnext = 0;
+    if (lane == 0) gnext = atomicAdd(&s_gctr, 1);
+    gnext = __shfl_sync(0xffffffffu, gnext, 0);
     while (true) {
-        int g = 0;
-        if (lane == 0) g = atomicAdd(&s_gctr, 1);
-        g = __shfl_sync(0xffffffffu, g, 0);
+        const int g = gnext;
         if (g >= ngroups) break;
+        int gclaim = 0;
+        if (lane == 0) gclaim = atomicAdd(&s_gctr, 1);
         const int4 d0 = grp[g], d1 = gd1[g];
         const int lo = d0.x, cnt = d0.y, A0 = d0.z, A1 = d0.w;
         const int path = d1.z & 15;
@@ -844,6 +849,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_event_mixed(DevCatalog c, Cal
             v = warp_sum(v) * pf;
         }
         if (lane == 0) gres[g] = v;
+        gnext = __shfl_sync(0xffffffffu, gclaim, 0);
     }
     __syncthreads();
     // the event's sum of the group values in a fixed order, compensated at

@@ -392,9 +392,9 @@ int chimera_kde_pairs(chimera_ctx *ctx, int32_t catalog_id, int32_t n_points, co
  *                device [n_det] double, as in chimera_catalog_desc.
  *   lambda_g, beta, z_max  as in chimera_catalog_desc.
  *   xi, neff     device [n_points] double out (0 for an inadmissible point).
- * The first call on a device looks up the array's device address and
- * should come before any stream capture; it also reads the largest d_L back
- * to the host, so every call synchronises `stream` once.  Calls share the
+ * The first call on a device looks up the array's device address; every
+ * call reads the largest d_L back to the host, so it synchronises `stream`
+ * once.  Calls share the
  * array: calls that overlap on the GPU race and must be serialised by the
  * caller.  Errors: INVALID_ARG (also when inj_dL holds no positive finite
  * distance), UNSUPPORTED, CUDA.

@@ -17,9 +17,8 @@
 //
 // Host code never dereferences the array's symbol: the first call on a
 // device asks the runtime for its device address (cudaGetSymbolAddress) and
-// remembers it for that device; that first call should come before any
-// stream capture.  Every call also reads the largest injection distance back
-// to the host, which synchronises `stream` once per call.  All calls share
+// remembers it for that device.  Every call also reads the largest injection
+// distance back to the host, which synchronises `stream` once per call.  All calls share
 // the array and it keeps the previous call's contents, so everything that
 // must start at zero is cleared on the call's stream, and calls whose work
 // overlaps on the GPU (different streams or threads at the same time) race

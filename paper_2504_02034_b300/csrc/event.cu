@@ -366,9 +366,12 @@ __device__ __forceinline__ float lane_chain(const float *Hc, const float *CT, in
 // keep the SMs full while the loads of the inverse-table nodes are in flight
 // (measured on the 300-event catalog: 128 threads with eight blocks per SM
 // 0.177 ms, 256 with four 0.190, 96 with ten 0.196, 64 with sixteen 0.244).
+// Each thread has three samples' loads in flight (0.161 ms against 0.171 ms
+// with two, whose register allocation at the 64-register cap spilled a few
+// bytes; four spill more).
 constexpr int RW_THREADS = 128;
 #ifndef CHIM_RW_INFLIGHT
-#define CHIM_RW_INFLIGHT 2
+#define CHIM_RW_INFLIGHT 3
 #endif
 #ifndef CHIM_RW_MINB
 #define CHIM_RW_MINB 8

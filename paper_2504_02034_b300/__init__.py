@@ -358,6 +358,8 @@ def chimera_selection_static(theta, inj, n_inj_total, lambda_g, beta, z_max, xi_
         if x.dtype != torch.float64 or not x.is_contiguous() or x.device != dev or x.numel() < t.shape[0]:
             raise ValueError("%s must be a contiguous float64 tensor of >= %d elements on %s"
                              % (name, t.shape[0], dev))
+    if dev.type != "cuda":
+        raise ValueError("xi_t, neff_t and the injection tensors must be CUDA tensors (got %s)" % dev)
     ptr = lambda x: C.c_void_p(x.data_ptr())
     # the C call runs on the calling thread's current device: make it the outputs' one
     with torch.cuda.device(dev):

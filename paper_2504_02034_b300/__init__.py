@@ -240,7 +240,17 @@ def chimera_loglike_device(h, cid, theta_t, precision, lnL_t, neff_t=None, statu
     torch.cuda.Stream or None for the current torch stream."""
     import torch
     n = theta_t.shape[0]
-    s = stream if stream is not None else torch.cuda.current_stream(theta_t.device)
+    dev = theta_t.device
+    # the C side writes n elements of each output through raw pointers: check
+    # types, lengths and placement here (a few microseconds of host time)
+    if (theta_t.dtype != torch.float64 or theta_t.dim() != 2 or theta_t.shape[1] != NPARAM
+            or not theta_t.is_contiguous() or dev.type != "cuda"):
+        raise ValueError("theta_t must be a contiguous float64 CUDA tensor of shape [n, %d]" % NPARAM)
+    for name, x, dt in (("lnL_t", lnL_t, torch.float64), ("neff_t", neff_t, torch.float64),
+                        ("status_t", status_t, torch.int32)):
+        if x is not None and (x.dtype != dt or x.device != dev or x.numel() < n or not x.is_contiguous()):
+            raise ValueError("%s must be a contiguous %s tensor of >= %d elements on %s" % (name, dt, n, dev))
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
     # torch's default stream has handle 0, which the C ABI would read as "the
     # context's own stream"; pass the legacy default stream handle instead
     sh = s.cuda_stream if s.cuda_stream != 0 else 0x1

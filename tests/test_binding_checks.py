@@ -1,7 +1,8 @@
 """Argument checks of the Python binding that run before any device work, on
 the CPU: the no-allocation selection entry rejects injection tensors of the
 wrong type, length or layout, output tensors that are too short, and tensors
-that are not on a CUDA device."""
+that are not on a CUDA device; the device-pointer ln L entry rejects a
+hyperpoint tensor that is not a float64 [n, 12] CUDA tensor."""
 import numpy as np
 import pytest
 import torch
@@ -50,3 +51,13 @@ def test_short_output_rejected(which):
 def test_host_tensors_rejected():
     with pytest.raises(ValueError, match="CUDA"):
         _call(_inj())
+
+
+def test_device_entry_rejects_host_or_misshaped_theta():
+    out = torch.zeros(3, dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA tensor of shape"):
+        pkg.chimera_loglike_device(None, 0, torch.zeros(3, 12, dtype=torch.float64), pkg.MIXED, out)
+    with pytest.raises(ValueError, match="CUDA tensor of shape"):
+        pkg.chimera_loglike_device(None, 0, torch.zeros(3, 11, dtype=torch.float64), pkg.MIXED, out)
+    with pytest.raises(ValueError, match="CUDA tensor of shape"):
+        pkg.chimera_loglike_device(None, 0, torch.zeros(3, 12, dtype=torch.float32), pkg.MIXED, out)

@@ -90,3 +90,25 @@ def test_no_cpu_fallback_without_gpu(chim):
     with pytest.raises(chim.ChimeraError) as e:
         chim.chimera_create(0)
     assert e.value.code == chim.CHIMERA_ERR_CUDA
+
+
+def test_every_field_offset_matches_header(chim, tmp_path):
+    """Each ctypes mirror of a header struct has the header's fields at the
+    header's offsets, field by field."""
+    structs = [("chimera_catalog_desc", chim.CatalogDesc), ("chimera_catalog_info_t", chim.CatalogInfo),
+               ("chimera_serve_stats_t", chim.ServeStats)]
+    lines = []
+    for cname, py in structs:
+        for f in py._fields_:
+            lines.append('  printf("%%zu\\n", offsetof(%s, %s));' % (cname, f[0]))
+        lines.append('  printf("%%zu\\n", sizeof(%s));' % cname)
+    prog = tmp_path / "fields.c"
+    prog.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"chimera.h\"\nint main(void) {\n"
+                    + "\n".join(lines) + "\n  return 0;\n}\n")
+    exe = tmp_path / "fields"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    got = list(map(int, subprocess.check_output([str(exe)]).decode().split()))
+    want = []
+    for _, py in structs:
+        want += [getattr(py, f[0]).offset for f in py._fields_] + [C.sizeof(py)]
+    assert got == want

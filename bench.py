@@ -584,7 +584,7 @@ def config4_stats(pkg, ctx, calls):
 
 
 def run_reference(args, ws, rank):
-    """Reference arm: the FP64 CPU oracle on this machine's host cores."""
+    """Reference arm: the FP64 CPU oracle on the host cores."""
     if rank != 0:
         return
     from synth import catalog as sc

@@ -1,6 +1,6 @@
 """The multi-GPU form of bench.py is independent replicas: only a barrier and a
-max of the per-rank times cross ranks (the path shards by events and
-injections, but every box has one GPU, so no data-path collective is built).
+max of the per-rank times cross ranks (each rank evaluates its own walkers
+over the whole catalog, so no data-path collective is built).
 This checks those cross-rank pieces with two gloo ranks on the CPU: the
 environment is read as torchrun sets it, the barrier holds every rank, and
 the time each rank reports is the slowest rank's (the job's time), so that
